@@ -1,0 +1,565 @@
+"""MF and HIF-DE, written out step by step in FP64.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).  Slow on purpose: the
+active matrix A_l is a dict of sparse rows, every block operation is a plain
+dense numpy call, and the loops follow the paper's order.
+
+What each function follows:
+
+* :func:`tree_levels`, :func:`separators` -- the cell partition of Section 3.1
+  (separators every ``2^l m h``); grids whose ``n`` is not ``2^L m`` use the
+  rounded separator positions ``round(i n / 2^L)``.
+* :func:`eliminate` -- Lemma 2.1 (sparse elimination), with ``A_pp`` factored by
+  Cholesky, ``A_pp = L L^T`` (so ``D_p = I``), as Section 5 does for SPD ``A``.
+* :func:`interp_decomp` -- Lemma 2.2 / Corollary 2.3: ID by column-pivoted
+  Householder QR, rank chosen adaptively from the pivot magnitudes (Section 2.2).
+* :func:`skeletonize` -- Lemma 2.4 (skeletonization) with the implicit
+  truncation of ``A_{q, r}`` described after it.
+* :func:`factor` -- Algorithm 3.1 (MF, ``eps = 0``) and Algorithm 4.1 (HIF-DE in
+  2D, and in 3D with face skeletonization, Section 4.2), with the accelerated
+  compression of Section 4.3 (fronts hold only the strict interior of an edge
+  or face; the ID compresses ``(A_{l+1/2})_{c^N, c}``).
+* :func:`Factor.apply_inverse`, :func:`Factor.apply` -- Eq. (4.2):
+  ``F^-1 = V_0 V_1/2 ... D^-1 ... V_1/2^T V_0^T`` and ``F`` itself.
+* :func:`pcg` -- preconditioned CG of Section 5 (relative residual 1e-12).
+* :func:`power_estimates` -- the a posteriori estimates ``e_a``, ``e_s`` of
+  Section 5 by power iteration to 1e-2 relative precision.
+
+Readings where the paper leaves a choice (each also listed in the design doc):
+
+* index sets are ordered by ascending global index; the skeleton set is kept
+  in pivot order; ``T`` has rows in skeleton order and columns in ascending
+  redundant order;
+* pivot = the remaining column with the smallest original position whose
+  squared residual norm is at least ``(1 - 1e-10)`` times the largest one;
+  residual norms are recomputed at every step (no downdating);
+* rank = number of pivots with ``|R_ii| > eps |R_11|``, stopping at the first
+  failure; an empty or zero block has rank 0;
+* all fronts of one fractional level compress blocks of ``A_{l+1/2}`` (the
+  matrix before any front of that level is skeletonized);
+* corners (2D) and cell edges / corners (3D) belong to no front (Section 4.3).
+
+Parity status: MF, the stencil, Lemma 2.1, Lemma 2.4, the ID, F and F^-1 are
+pinned by the ``-m "not gpu"`` tests (dense LU, closed forms, exact low rank,
+LAPACK's pivoted QR, invariants).
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import Dict, List, Optional, Tuple
+
+import numpy as np
+import scipy.linalg as sla
+
+PIVOT_TIE_REL = 1e-10
+
+
+# --------------------------------------------------------------------------
+# geometry (Section 3.1, 3.2)
+# --------------------------------------------------------------------------
+
+def tree_levels(n: int, leaf: int = 8) -> int:
+    """Tree depth L: ``n = 2^L m`` with leaf width ``m``; otherwise the nearest
+    integer to ``log2(n / leaf)``, at least 1."""
+    return max(1, int(round(np.log2(n / leaf))))
+
+
+def separators(n: int, L: int) -> np.ndarray:
+    """Separator positions ``p_i = round(i n / 2^L)`` (half up), i = 1..2^L-1.
+
+    For ``n = 2^L m`` these are the multiples of ``m`` of Section 3.1."""
+    i = np.arange(1, 2 ** L, dtype=np.int64)
+    return (2 * i * n + 2 ** L) // (2 ** (L + 1))
+
+
+def level_separators(n: int, L: int, ell: int) -> np.ndarray:
+    """Positions of the level-``ell`` separators: every ``2^ell``-th one."""
+    p = separators(n, L)
+    i = np.arange(1, 2 ** L)
+    return p[(i % (2 ** ell)) == 0]
+
+
+def _interval_index(x: np.ndarray, seps: np.ndarray) -> np.ndarray:
+    """Index of the open interval between consecutive separators containing x
+    (x not on a separator)."""
+    return np.searchsorted(seps, x)
+
+
+# --------------------------------------------------------------------------
+# active matrix A_l: dict of sparse symmetric rows
+# --------------------------------------------------------------------------
+
+class ActiveMatrix:
+    """Symmetric sparse matrix stored as ``rows[i] = {j: A_ij}`` (both halves).
+
+    The structural pattern is what the paper's neighbour set refers to:
+    ``c^N = {i not in c : A_ic != 0}`` (Section 2) with "nonzero" meaning stored.
+    """
+
+    def __init__(self, A_csr):
+        A = A_csr.tocsr()
+        self.rows: Dict[int, Dict[int, float]] = {}
+        for i in range(A.shape[0]):
+            lo, hi = A.indptr[i], A.indptr[i + 1]
+            self.rows[i] = dict(zip(A.indices[lo:hi].tolist(), A.data[lo:hi].tolist()))
+
+    def active(self) -> List[int]:
+        return sorted(self.rows)
+
+    def block(self, r: List[int], c: List[int]) -> np.ndarray:
+        out = np.zeros((len(r), len(c)))
+        for a, i in enumerate(r):
+            row = self.rows[i]
+            for b, j in enumerate(c):
+                v = row.get(j)
+                if v is not None:
+                    out[a, b] = v
+        return out
+
+    def neighbors(self, c: List[int]) -> List[int]:
+        cs = set(c)
+        nb = set()
+        for i in c:
+            nb.update(self.rows[i].keys())
+        return sorted(nb - cs)
+
+    def add_block(self, r: List[int], c: List[int], M: np.ndarray) -> None:
+        for a, i in enumerate(r):
+            row = self.rows[i]
+            for b, j in enumerate(c):
+                row[j] = row.get(j, 0.0) + M[a, b]
+
+    def set_block(self, r: List[int], c: List[int], M: np.ndarray) -> None:
+        for a, i in enumerate(r):
+            row = self.rows[i]
+            for b, j in enumerate(c):
+                row[j] = M[a, b]
+
+    def remove(self, dofs: List[int]) -> None:
+        """Decouple and drop ``dofs`` (rows and columns)."""
+        ds = set(dofs)
+        touched = set()
+        for i in dofs:
+            touched.update(self.rows[i].keys())
+        for j in touched - ds:
+            row = self.rows[j]
+            for i in dofs:
+                row.pop(i, None)
+        for i in dofs:
+            del self.rows[i]
+
+
+# --------------------------------------------------------------------------
+# Lemma 2.1: sparse elimination
+# --------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class CellRecord:
+    """Elimination operator S_p of Lemma 2.1 with A_pp = L L^T (D_p = I)."""
+    p: np.ndarray      # eliminated indices (ascending)
+    q: np.ndarray      # neighbour indices c^N (ascending)
+    L: np.ndarray      # lower Cholesky factor of A_pp
+    Aqp: np.ndarray    # A_qp at the time of elimination
+
+
+def eliminate(A: ActiveMatrix, p: List[int]) -> CellRecord:
+    """Lemma 2.1 with q = p^N: B_qq = A_qq - A_qp A_pp^{-1} A_qp^T; p decoupled."""
+    q = A.neighbors(p)
+    App = A.block(p, p)
+    Aqp = A.block(q, p)
+    L = np.linalg.cholesky(App)
+    if q:
+        # A_qp A_pp^{-1} A_qp^T through the Cholesky factor: (A_qp L^-T)(A_qp L^-T)^T
+        Y = sla.solve_triangular(L, Aqp.T, lower=True)        # L^-1 A_qp^T
+        A.add_block(q, q, -(Y.T @ Y))
+    A.remove(p)
+    return CellRecord(np.array(p, dtype=np.int64), np.array(q, dtype=np.int64), L, Aqp)
+
+
+def apply_S_T(rec: CellRecord, x: np.ndarray) -> None:
+    """x <- S_p^T x  (in place, x may have several columns).
+
+    S_p^T = [[L^-1, 0], [-A_qp A_pp^-1, I]] on (p, q)."""
+    xp = sla.solve_triangular(rec.L, x[rec.p], lower=True)
+    if len(rec.q):
+        x[rec.q] -= rec.Aqp @ sla.solve_triangular(rec.L, xp, lower=True, trans="T")
+    x[rec.p] = xp
+
+
+def apply_S(rec: CellRecord, x: np.ndarray) -> None:
+    """x <- S_p x:  x_p <- L^-T (x_p - L^-1 A_qp^T x_q)."""
+    xp = x[rec.p]
+    if len(rec.q):
+        xp = xp - sla.solve_triangular(rec.L, rec.Aqp.T @ x[rec.q], lower=True)
+    x[rec.p] = sla.solve_triangular(rec.L, xp, lower=True, trans="T")
+
+
+def apply_S_inv(rec: CellRecord, x: np.ndarray) -> None:
+    """x <- S_p^{-1} x with S_p^{-1} = [[L^T, L^-1 A_qp^T], [0, I]]."""
+    xp = rec.L.T @ x[rec.p]
+    if len(rec.q):
+        xp = xp + sla.solve_triangular(rec.L, rec.Aqp.T @ x[rec.q], lower=True)
+    x[rec.p] = xp
+
+
+def apply_S_inv_T(rec: CellRecord, x: np.ndarray) -> None:
+    """x <- S_p^{-T} x with S_p^{-T} = [[L, 0], [A_qp L^-T, I]]."""
+    xp = x[rec.p].copy()
+    if len(rec.q):
+        x[rec.q] += rec.Aqp @ sla.solve_triangular(rec.L, xp, lower=True, trans="T")
+    x[rec.p] = rec.L @ xp
+
+
+# --------------------------------------------------------------------------
+# Lemma 2.2 / Corollary 2.3: interpolative decomposition
+# --------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class IDResult:
+    sk: np.ndarray        # skeleton column positions, pivot order
+    rd: np.ndarray        # redundant column positions, ascending
+    T: np.ndarray         # k x |rd|:  M[:, rd] ~ M[:, sk] T
+    pivots: np.ndarray    # |R_ii| for i < k, plus the first rejected one (if any)
+    near_threshold: bool  # a pivot ratio within 1e-8 (relative) of eps
+
+
+def interp_decomp(M: np.ndarray, eps: float) -> IDResult:
+    """Adaptive-rank ID of M (m x n) by column-pivoted Householder QR.
+
+    Step i works on the residual rows i..m-1.  Residual column norms are
+    recomputed at every step.  The pivot is the remaining column of smallest
+    original position whose squared norm is within a factor (1 - 1e-10) of
+    the largest; the iteration stops when |R_ii| <= eps |R_11|.  Then
+    T = R_11^{-1} R_12 (Lemma 2.2)."""
+    m, n = M.shape
+    R = np.array(M, dtype=np.float64, copy=True)
+    remaining = list(range(n))
+    chosen: List[int] = []
+    pivots: List[float] = []
+    nu1sq = None
+    near = False
+    for i in range(min(m, n)):
+        sq = {j: float(np.dot(R[i:, j], R[i:, j])) for j in remaining}
+        mx = max(sq.values())
+        if nu1sq is None:
+            nu1sq = mx
+        if mx == 0.0:
+            break
+        ratio = np.sqrt(mx / nu1sq)
+        if abs(ratio - eps) <= 1e-8 * eps:
+            near = True
+        pivots.append(np.sqrt(mx))
+        if mx <= eps * eps * nu1sq:
+            break
+        piv = min(j for j in remaining if sq[j] >= (1.0 - PIVOT_TIE_REL) * mx)
+        chosen.append(piv)
+        remaining.remove(piv)
+        x = R[i:, piv].copy()
+        alpha = -np.sqrt(sq[piv]) if x[0] >= 0 else np.sqrt(sq[piv])
+        v = x.copy()
+        v[0] -= alpha
+        vv = float(np.dot(v, v))
+        if vv > 0.0:
+            for j in remaining:
+                R[i:, j] -= (2.0 * np.dot(v, R[i:, j]) / vv) * v
+        R[i:, piv] = 0.0
+        R[i, piv] = alpha
+    k = len(chosen)
+    rd = np.array(remaining, dtype=np.int64)
+    if k and len(rd):
+        R11 = R[:k, chosen]
+        R12 = R[:k, remaining]
+        T = sla.solve_triangular(R11, R12, lower=False)
+    else:
+        T = np.zeros((k, len(rd)))
+    return IDResult(np.array(chosen, dtype=np.int64), rd, T, np.array(pivots), near)
+
+
+# --------------------------------------------------------------------------
+# Lemma 2.4: skeletonization
+# --------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class FrontRecord:
+    """U_c = Q_c S_r of Lemma 2.4 (S_r is Lemma 2.1 with p = r, q = s)."""
+    c: np.ndarray      # front indices (ascending)
+    sk: np.ndarray     # skeleton indices (global, pivot order)
+    rd: np.ndarray     # redundant indices (global, ascending)
+    T: np.ndarray      # k x |rd|
+    L: np.ndarray      # Cholesky factor of B_rr
+    Bsr: np.ndarray    # B_sr
+    near_threshold: bool = False
+
+
+def skeletonize(A: ActiveMatrix, c: List[int], idr: IDResult) -> FrontRecord:
+    """Z_c(A) of Lemma 2.4: Q_c^T A Q_c with A_{q,r} truncated, then Lemma 2.1
+    on the redundant set r (whose only remaining neighbours are the skeletons)."""
+    c_arr = np.array(c, dtype=np.int64)
+    sk = c_arr[idr.sk]
+    rd = c_arr[idr.rd]
+    sk_l, rd_l = sk.tolist(), rd.tolist()
+    Ass = A.block(sk_l, sk_l)
+    Asr = A.block(sk_l, rd_l)
+    Arr = A.block(rd_l, rd_l)
+    T = idr.T
+    Brr = Arr - T.T @ Asr - Asr.T @ T + T.T @ Ass @ T
+    Bsr = Asr - Ass @ T
+    L = np.linalg.cholesky(Brr) if len(rd_l) else np.zeros((0, 0))
+    if len(rd_l) and len(sk_l):
+        Y = sla.solve_triangular(L, Bsr.T, lower=True)          # L^-1 B_sr^T
+        A.set_block(sk_l, sk_l, Ass - Y.T @ Y)
+    A.remove(rd_l)
+    return FrontRecord(c_arr, sk, rd, T, L, Bsr, idr.near_threshold)
+
+
+def _front_as_cell(fr: FrontRecord) -> CellRecord:
+    return CellRecord(fr.rd, fr.sk, fr.L, fr.Bsr)
+
+
+def apply_U_T(fr: FrontRecord, x: np.ndarray) -> None:
+    """x <- U_c^T x = S_r^T Q_c^T x;  Q_c^T: x_r <- x_r - T^T x_s."""
+    if len(fr.rd) == 0:
+        return
+    if len(fr.sk):
+        x[fr.rd] -= fr.T.T @ x[fr.sk]
+    apply_S_T(_front_as_cell(fr), x)
+
+
+def apply_U(fr: FrontRecord, x: np.ndarray) -> None:
+    """x <- U_c x = Q_c S_r x;  Q_c: x_s <- x_s - T x_r."""
+    if len(fr.rd) == 0:
+        return
+    apply_S(_front_as_cell(fr), x)
+    if len(fr.sk):
+        x[fr.sk] -= fr.T @ x[fr.rd]
+
+
+def apply_U_inv(fr: FrontRecord, x: np.ndarray) -> None:
+    """x <- U_c^{-1} x = S_r^{-1} Q_c^{-1} x;  Q_c^{-1}: x_s <- x_s + T x_r."""
+    if len(fr.rd) == 0:
+        return
+    if len(fr.sk):
+        x[fr.sk] += fr.T @ x[fr.rd]
+    apply_S_inv(_front_as_cell(fr), x)
+
+
+def apply_U_inv_T(fr: FrontRecord, x: np.ndarray) -> None:
+    """x <- U_c^{-T} x = Q_c^{-T} S_r^{-T} x;  Q_c^{-T}: x_r <- x_r + T^T x_s."""
+    if len(fr.rd) == 0:
+        return
+    apply_S_inv_T(_front_as_cell(fr), x)
+    if len(fr.sk):
+        x[fr.rd] += fr.T.T @ x[fr.sk]
+
+
+# --------------------------------------------------------------------------
+# Algorithms 3.1 / 4.1
+# --------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Level:
+    """One level of the factorization: V_l (cells) then V_{l+1/2} (fronts)."""
+    ell: int
+    cells: List[CellRecord]
+    fronts: List[FrontRecord]
+    front_keys: List[tuple]
+
+
+@dataclasses.dataclass
+class Factor:
+    dim: int
+    n: int
+    L: int
+    eps: float
+    levels: List[Level]
+    root: np.ndarray           # s_L (ascending)
+    D: np.ndarray              # A_L restricted to s_L
+    Dchol: np.ndarray          # its Cholesky factor
+
+    # ---- Eq. (4.2): F^-1 = V_0 V_1/2 ... D^-1 ... V_1/2^T V_0^T
+    def apply_inverse(self, b: np.ndarray) -> np.ndarray:
+        x = np.array(b, dtype=np.float64, copy=True)
+        for lev in self.levels:                       # V^T, finest first
+            for rec in lev.cells:
+                apply_S_T(rec, x)
+            for fr in lev.fronts:
+                apply_U_T(fr, x)
+        if len(self.root):
+            x[self.root] = sla.cho_solve((self.Dchol, True), x[self.root])
+        for lev in reversed(self.levels):             # V, coarsest first
+            for fr in lev.fronts:
+                apply_U(fr, x)
+            for rec in lev.cells:
+                apply_S(rec, x)
+        return x
+
+    # ---- F = V_0^-T ... V_{L-1/2}^-T D V_{L-1/2}^-1 ... V_0^-1
+    def apply(self, b: np.ndarray) -> np.ndarray:
+        x = np.array(b, dtype=np.float64, copy=True)
+        for lev in self.levels:                       # V^-1, finest first
+            for rec in lev.cells:
+                apply_S_inv(rec, x)
+            for fr in lev.fronts:
+                apply_U_inv(fr, x)
+        if len(self.root):
+            x[self.root] = self.D @ x[self.root]
+        for lev in reversed(self.levels):             # V^-T, coarsest first
+            for fr in lev.fronts:
+                apply_U_inv_T(fr, x)
+            for rec in lev.cells:
+                apply_S_inv_T(rec, x)
+        return x
+
+    # ---- structure for parity checks
+    def skeleton_structure(self):
+        """Per fractional level: {front key: (c, sk in pivot order, rank)} and |s_L|."""
+        out = []
+        for lev in self.levels:
+            d = {}
+            for key, fr in zip(lev.front_keys, lev.fronts):
+                d[key] = (fr.c.tolist(), fr.sk.tolist(), len(fr.sk))
+            out.append(d)
+        return out, len(self.root)
+
+
+def _front_key(dim, x, on_sep, seps):
+    """Front identity: (axis with the separator coordinate, separator ordinal,
+    interval index along each other axis)."""
+    axis = int(np.nonzero(on_sep)[0][0])
+    ordinal = int(np.searchsorted(seps, x[axis]))
+    others = tuple(int(_interval_index(np.array([x[a]]), seps)[0]) for a in range(dim) if a != axis)
+    return (axis, ordinal) + others
+
+
+def factor(A_csr, dim: int, n: int, eps: float, leaf: int = 8,
+           skip_levels: int = 0) -> Factor:
+    """Algorithm 4.1 (HIF-DE; ``eps > 0``) or Algorithm 3.1 (MF; ``eps == 0``).
+
+    Level l: eliminate the active DOFs strictly inside each level-l cell
+    (Lemma 2.1, cells in ascending linear index, x fastest).  Level l + 1/2
+    (skipped when ``eps == 0`` or ``l < skip_levels``): group the active DOFs
+    with exactly one coordinate on a level-l separator by front (2D edge or
+    3D face interior), compute every front's ID from ``A_{l+1/2}``, then
+    skeletonize the fronts (Lemma 2.4).  Finally ``D = A_L`` on ``s_L``."""
+    from .stencil import coords as _coords
+    A = ActiveMatrix(A_csr)
+    X = _coords(dim, n)
+    L = tree_levels(n, leaf)
+    levels: List[Level] = []
+    for ell in range(L):
+        seps = level_separators(n, L, ell)
+        act = np.array(A.active(), dtype=np.int64)
+        Xa = X[act]
+        on = np.isin(Xa, seps)
+        non = on.sum(axis=1)
+        # ---- level l: cells
+        inside = act[non == 0]
+        cell_dofs: Dict[int, List[int]] = {}
+        if len(inside):
+            iv = np.searchsorted(seps, X[inside])              # interval per axis
+            ncell = len(seps) + 1
+            lin = np.zeros(len(inside), dtype=np.int64)
+            for a in reversed(range(dim)):
+                lin = lin * ncell + iv[:, a]
+            for d, cidx in zip(inside.tolist(), lin.tolist()):
+                cell_dofs.setdefault(cidx, []).append(d)
+        cells = [eliminate(A, sorted(cell_dofs[k])) for k in sorted(cell_dofs)]
+        # ---- level l + 1/2: fronts
+        fronts: List[FrontRecord] = []
+        keys: List[tuple] = []
+        if eps > 0 and ell >= skip_levels:
+            act = np.array(A.active(), dtype=np.int64)
+            Xa = X[act]
+            on = np.isin(Xa, seps)
+            one = act[on.sum(axis=1) == 1]
+            groups: Dict[tuple, List[int]] = {}
+            for d in one.tolist():
+                key = _front_key(dim, X[d], np.isin(X[d], seps), seps)
+                groups.setdefault(key, []).append(d)
+            keys = sorted(groups)
+            ids = []
+            for key in keys:                           # all IDs from A_{l+1/2}
+                c = sorted(groups[key])
+                nb = A.neighbors(c)
+                ids.append(interp_decomp(A.block(nb, c), eps))
+            for key, idr in zip(keys, ids):
+                fronts.append(skeletonize(A, sorted(groups[key]), idr))
+        levels.append(Level(ell, cells, fronts, keys))
+    root = np.array(A.active(), dtype=np.int64)
+    D = A.block(root.tolist(), root.tolist())
+    Dchol = np.linalg.cholesky(D) if len(root) else np.zeros((0, 0))
+    return Factor(dim, n, L, eps, levels, root, D, Dchol)
+
+
+# --------------------------------------------------------------------------
+# Section 5: PCG and the power-method error estimates
+# --------------------------------------------------------------------------
+
+def pcg(A_csr, F: Factor, b: np.ndarray, tol: float = 1e-12, maxit: int = 200):
+    """Preconditioned CG with M^-1 = F^-1 on each column of b (textbook
+    recurrences).  When the recursive residual reaches tol, the true residual
+    b - A x is computed; if it is still above tol, CG restarts from it.
+    Returns (x, iters, relres) with relres the true FP64 relative residual."""
+    b2 = b.reshape(b.shape[0], -1)
+    X = np.zeros_like(b2)
+    iters, relres = [], []
+    for col in range(b2.shape[1]):
+        bb = b2[:, col]
+        nb = np.linalg.norm(bb)
+        x = np.zeros_like(bb)
+        r = bb.copy()
+        it = 0
+        restarts = 0
+        while it < maxit:
+            z = F.apply_inverse(r)
+            p = z.copy()
+            rz = float(r @ z)
+            while np.linalg.norm(r) > tol * nb and it < maxit:
+                q = A_csr @ p
+                alpha = rz / float(p @ q)
+                x += alpha * p
+                r = r - alpha * q
+                it += 1
+                z = F.apply_inverse(r)
+                rz_new = float(r @ z)
+                p = z + (rz_new / rz) * p
+                rz = rz_new
+            r = bb - A_csr @ x
+            if np.linalg.norm(r) <= tol * nb or restarts >= 5:
+                break
+            restarts += 1
+        X[:, col] = x
+        iters.append(it)
+        relres.append(np.linalg.norm(bb - A_csr @ x) / nb)
+    return X.reshape(b.shape), iters, relres
+
+
+def power_norm(op, x0: np.ndarray, rtol: float = 1e-2, maxit: int = 200) -> float:
+    """||op|| by power iteration ||op x|| / ||x|| from x0, stopped at rtol
+    relative change (Section 5)."""
+    x = x0 / np.linalg.norm(x0)
+    est = 0.0
+    for _ in range(maxit):
+        y = op(x)
+        ny = float(np.linalg.norm(y))
+        if ny == 0.0:
+            return 0.0
+        if est > 0 and abs(ny - est) <= rtol * ny:
+            return ny
+        est = ny
+        x = y / ny
+    return est
+
+
+def power_estimates(A_csr, F: Factor, x0: np.ndarray):
+    """(e_a, e_s): e_a ~ ||A - F|| / ||A||,  e_s ~ ||I - A F^-1||
+    (the latter through (I - F^-1 A)(I - A F^-1), whose norm is its square)."""
+    nA = power_norm(lambda v: A_csr @ v, x0)
+    nE = power_norm(lambda v: A_csr @ v - F.apply(v), x0)
+
+    def MtM(v):
+        w = v - A_csr @ F.apply_inverse(v)
+        return w - F.apply_inverse(A_csr @ w)
+
+    es = np.sqrt(power_norm(MtM, x0))
+    return nE / nA, es

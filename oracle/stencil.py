@@ -1,0 +1,82 @@
+"""Five-point (2D) and seven-point (3D) variable-coefficient stencil.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+Section 3.1 (2D) and Section 3.2 (3D): at every interior node ``x_j``
+
+    (1/h^2) * sum_e [ a_{j-e/2} (u_j - u_{j-e}) + a_{j+e/2} (u_j - u_{j+e}) ] + b_j u_j = f_j
+
+with ``a`` sampled on the staggered grid, ``b`` at the nodes, ``h = 1/n`` and zero
+Dirichlet values at the boundary nodes (a neighbour on the boundary contributes
+only to the diagonal).  Unknowns are ordered lexicographically with x fastest.
+
+Pinned by: the closed-form eigenpairs of the constant-coefficient Laplacian
+(``tests/test_oracle_stencil.py``) and symmetry / row-sum identities.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+
+
+def _stag_blocks(dim, n, a_stag):
+    m = n - 1
+    if dim == 2:
+        shapes = [(m, n), (n, m)]
+    else:
+        shapes = [(m, m, n), (m, n, m), (n, m, m)]
+    out, off = [], 0
+    for s in shapes:
+        size = int(np.prod(s))
+        out.append(np.asarray(a_stag[off:off + size], dtype=np.float64).reshape(s))
+        off += size
+    assert off == len(a_stag), "a_stag has the wrong length"
+    return out
+
+
+def assemble(dim: int, n: int, a_stag, b) -> sp.csr_matrix:
+    """Sparse matrix A of the stencil above, as a CSR matrix (N x N, FP64)."""
+    m = n - 1
+    N = m ** dim
+    inv_h2 = float(n) ** 2
+    blocks = _stag_blocks(dim, n, a_stag)
+    idx = np.arange(N).reshape((m,) * dim)     # axis order (.., j2, j1): x fastest
+    rows, cols, vals = [], [], []
+    diag = np.asarray(b, dtype=np.float64).reshape((m,) * dim).copy()
+    for axis in range(dim):                    # axis 0 = x, 1 = y, 2 = z
+        arr_axis = dim - 1 - axis              # numpy axis of this coordinate
+        a = blocks[axis] * inv_h2              # shape has n along arr_axis
+        # bond between node j and j+e sits at staggered index j (0..n-1) along arr_axis
+        lo = [slice(None)] * dim
+        hi = [slice(None)] * dim
+        lo[arr_axis] = slice(0, m)             # bond to the lower neighbour: a_{j-e/2}
+        hi[arr_axis] = slice(1, n)             # bond to the upper neighbour: a_{j+e/2}
+        diag += a[tuple(lo)] + a[tuple(hi)]
+        # off-diagonal coupling between interior nodes j and j+e (bond index j+1 .. )
+        inner = [slice(None)] * dim
+        inner[arr_axis] = slice(1, m)          # bonds strictly between two interior nodes
+        w = a[tuple(inner)]
+        left = [slice(None)] * dim
+        right = [slice(None)] * dim
+        left[arr_axis] = slice(0, m - 1)
+        right[arr_axis] = slice(1, m)
+        i0 = idx[tuple(left)].ravel()
+        i1 = idx[tuple(right)].ravel()
+        rows += [i0, i1]
+        cols += [i1, i0]
+        vals += [-w.ravel(), -w.ravel()]
+    rows.append(np.arange(N))
+    cols.append(np.arange(N))
+    vals.append(diag.ravel())
+    A = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(N, N))
+    return A.tocsr()
+
+
+def coords(dim: int, n: int) -> np.ndarray:
+    """Integer grid coordinates (j1, j2[, j3]) of every unknown, shape (N, dim)."""
+    m = n - 1
+    g = np.meshgrid(*[np.arange(1, n)] * dim, indexing="ij")
+    # meshgrid 'ij' gives axis0 = first coordinate; our order is x fastest
+    out = np.stack([gi.transpose(*reversed(range(dim))).ravel() for gi in g], axis=1)
+    return out.astype(np.int64)

@@ -1,0 +1,80 @@
+"""Pins of the oracle's stencil (Section 3.1 / 3.2) and of the input generators."""
+import numpy as np
+import pytest
+
+from oracle import stencil
+from paper_1307_2895_gb300 import inputs
+
+
+def _mode(dim, n, idx):
+    """Discrete sine mode prod_a sin(i_a pi x_a) on the interior nodes."""
+    X = stencil.coords(dim, n) / n
+    v = np.ones(X.shape[0])
+    for a, i in enumerate(idx):
+        v *= np.sin(i * np.pi * X[:, a])
+    return v
+
+
+@pytest.mark.parametrize("dim,n", [(2, 16), (2, 33), (3, 8), (3, 11)])
+def test_closed_form_eigenpairs(dim, n):
+    """a = 1, b = 0: A v = lambda v with lambda = (4/h^2) sum_a sin^2(i_a pi h / 2)."""
+    a, b = inputs.constant_coefficients(dim, n)
+    A = stencil.assemble(dim, n, a, b)
+    h = 1.0 / n
+    rng = np.random.default_rng(1)
+    for _ in range(5):
+        idx = rng.integers(1, n, size=dim)
+        v = _mode(dim, n, idx)
+        lam = (4.0 / h ** 2) * np.sum(np.sin(idx * np.pi * h / 2) ** 2)
+        assert np.linalg.norm(A @ v - lam * v) <= 1e-10 * lam * np.linalg.norm(v)
+
+
+def test_extreme_eigenvalues_2d():
+    n = 16
+    a, b = inputs.constant_coefficients(2, n)
+    ev = np.linalg.eigvalsh(stencil.assemble(2, n, a, b).toarray())
+    h = 1.0 / n
+    assert ev[0] == pytest.approx(8.0 / h ** 2 * np.sin(np.pi * h / 2) ** 2, rel=1e-12)
+    assert ev[-1] == pytest.approx(8.0 / h ** 2 * np.sin((n - 1) * np.pi * h / 2) ** 2, rel=1e-12)
+
+
+@pytest.mark.parametrize("dim,n", [(2, 12), (3, 7)])
+def test_variable_coefficient_structure(dim, n):
+    """Symmetric, diagonal = b + sum of the 2d adjacent bond values / h^2, and
+    with b = 0 the row sums vanish away from the boundary."""
+    a, _ = inputs.high_contrast_coefficients(dim, n, seed=3, low=1e-2, high=1e2)
+    b = inputs.uniform01(9, (n - 1) ** dim)
+    A = stencil.assemble(dim, n, a, b)
+    assert abs(A - A.T).max() == 0.0
+    A0 = stencil.assemble(dim, n, a, np.zeros_like(b))
+    X = stencil.coords(dim, n)
+    interior = np.all((X > 1) & (X < n - 1), axis=1)
+    rs = np.asarray(A0.sum(axis=1)).ravel()
+    assert np.max(np.abs(rs[interior])) <= 1e-9 * n * n * a.max()
+    assert np.all(rs[~interior] > 0)
+    # one explicit bond: between node (1,1,..) and (2,1,..) the coupling is -a((1+1/2)h, h, ..) n^2
+    i0 = 0
+    i1 = 1
+    ax = a[: n * (n - 1) ** (dim - 1)].reshape(((n - 1),) * (dim - 1) + (n,))
+    expect = -ax[(0,) * (dim - 1) + (1,)] * n * n
+    assert A[i0, i1] == pytest.approx(expect, rel=1e-15)
+
+
+def test_splitmix64_published_vectors():
+    """splitmix64 outputs for seed 0 and 1234567 (published reference values)."""
+    assert [int(v) for v in inputs.splitmix64(0, 3)] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4,
+                                                          0x06C45D188009454F]
+    assert [int(v) for v in inputs.splitmix64(1234567, 3)] == [6457827717110365317, 3203168211198807973,
+                                                                9817491932198370423]
+
+
+def test_generators_deterministic_and_shaped():
+    a1, b1 = inputs.high_contrast_coefficients(2, 32, seed=5, low=1e-3, high=1e3)
+    a2, _ = inputs.high_contrast_coefficients(2, 32, seed=5, low=1e-3, high=1e3)
+    assert np.array_equal(a1, a2) and len(a1) == 2 * 32 * 31 and set(np.unique(a1)) <= {1e-3, 1e3}
+    frac = np.mean(a1 > 1)
+    assert 0.2 < frac < 0.8
+    z = inputs.standard_normal(0, 200000)
+    assert abs(z.mean()) < 0.01 and abs(z.std() - 1) < 0.01
+    r = inputs.rhs(2, 16, 3)
+    assert r.shape == (225, 3) and r.flags["C_CONTIGUOUS"]
