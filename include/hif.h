@@ -1,0 +1,172 @@
+/*
+ * hif.h -- C ABI of the GB300 implementation of the hierarchical interpolative
+ * factorization for elliptic differential operators (HIF-DE; Ho & Ying,
+ * arXiv:1307.2895).
+ *
+ * The operator (Eq. 1.1 discretized as in Sections 3.1 and 3.2): on the unit
+ * square (dim = 2) or cube (dim = 3) with zero Dirichlet data and an
+ * n x n (x n) grid, h = 1/n, unknowns at the N = (n-1)^dim interior nodes,
+ *
+ *   (1/h^2) sum_e [ a_{j-e/2}(u_j - u_{j-e}) + a_{j+e/2}(u_j - u_{j+e}) ] + b_j u_j = f_j.
+ *
+ * Unknowns are ordered lexicographically with x fastest.
+ *
+ * Array arguments:
+ *   a_stag  staggered coefficients: ax, ay (, az) concatenated, each block of
+ *           n*(n-1)^(dim-1) doubles.  2D: ax[(j2-1)*n + j1] = a((j1+1/2)h, j2 h),
+ *           ay[j2*(n-1) + (j1-1)] = a(j1 h, (j2+1/2)h).  3D: ax[((j3-1)*(n-1) +
+ *           (j2-1))*n + j1], ay[((j3-1)*n + j2)*(n-1) + (j1-1)],
+ *           az[(j3*(n-1) + (j2-1))*(n-1) + (j1-1)].
+ *   b       nodal reaction coefficient, N doubles.
+ *   vectors N rows x nrhs columns, row-major with row stride ld >= nrhs
+ *           (element (i, r) at v[i*ld + r]).
+ *
+ * Pointers may be host or device memory (any pointer the CUDA runtime does
+ * not report as device or managed memory is treated as host memory and is
+ * staged through the device).  The caller keeps ownership of every array it
+ * passes; arrays are only read (inputs) or written (outputs) during the call.
+ * Device work is issued on opts.stream (a cudaStream_t; NULL = legacy default
+ * stream) and every call returns after its results are complete.
+ *
+ * Errors: every call returns an hif_status.  Nothing aborts the process and no
+ * device code traps; hif_last_error() gives a message for the last failure on
+ * the calling thread.  A handle is not thread-safe.
+ */
+#ifndef HIF_H
+#define HIF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum hif_status {
+  HIF_OK = 0,
+  HIF_ERR_ARG = 1,       /* invalid argument (grid, sizes, pointers)            */
+  HIF_ERR_NOT_SPD = 2,   /* a non-positive pivot in a diagonal-block Cholesky   */
+  HIF_ERR_NOCONV = 3,    /* the iteration reached maxit; info is still filled   */
+  HIF_ERR_TIMEOUT = 4,   /* a bounded device wait ran out                       */
+  HIF_ERR_CUDA = 5,      /* a CUDA runtime call failed                          */
+  HIF_ERR_OOM = 6        /* device allocation failed                            */
+} hif_status;
+
+/* Variants (Section 5 names): MF = mf2/mf3 (Algorithm 3.1, exact),
+ * HIFDE = hifde2/hifde3 (Algorithm 4.1; faces only in 3D). */
+enum { HIF_VARIANT_MF = 0, HIF_VARIANT_HIFDE = 1 };
+
+/* Arithmetic of the factorization.  FP64: every block operation in double.
+ * MIXED: cell and front blocks, the factor and the apply of F^-1 in float;
+ * the root block D is factored in double; the ID's column norms and pivot
+ * tests are accumulated in double.  The CG driver is double in both. */
+enum { HIF_PREC_FP64 = 0, HIF_PREC_MIXED = 1 };
+
+/* hif_apply modes (Eq. 4.2): y = F x or y = F^-1 x. */
+enum { HIF_APPLY_F = 0, HIF_APPLY_FINV = 1 };
+
+typedef struct hif_grid {
+  int dim;      /* 2 or 3                                                       */
+  int n;        /* grid intervals per axis (N = (n-1)^dim), n >= 4              */
+  int leaf;     /* leaf cell width m (Section 3.1: n = 2^L m); 0 -> 8           */
+  int variant;  /* HIF_VARIANT_*                                                */
+} hif_grid;
+
+typedef struct hif_opts {
+  int precision;        /* HIF_PREC_*                                           */
+  int skip_levels;      /* fractional levels l + 1/2 skipped for l < skip_levels
+                           (Section 5: "the first few fractional levels ...")    */
+  int reserved0;
+  int reserved1;
+  void* stream;         /* cudaStream_t for all device work                     */
+} hif_opts;
+
+typedef struct hif_handle hif_handle;
+
+typedef struct hif_solve_info {
+  int iters;            /* inner CG iterations, all refinement steps            */
+  int outer;            /* refinement steps                                     */
+  int converged;        /* 1 if every column reached tol                        */
+  double relres_max;    /* max_r ||b_r - A x_r||_2 / ||b_r||_2 of the
+                           double-double iterate x = x_hi + x_lo                 */
+  double relres_fp64_max; /* the same for the FP64 iterate x_hi alone           */
+} hif_solve_info;
+
+typedef struct hif_stats_t {
+  int dim, n, levels;          /* L                                              */
+  int root_size;               /* |s_L| (Section 5)                              */
+  int n_cells, n_fronts;       /* blocks eliminated / skeletonized, all levels   */
+  int max_front_rank;          /* largest skeleton size k                        */
+  int near_threshold_fronts;   /* fronts with a pivot ratio within 1e-8 of eps   */
+  int clamped_pivots;          /* MIXED: Cholesky pivots raised to the floor     */
+  long long factor_bytes;      /* m_f: bytes of the stored factor                */
+  double factor_flops;         /* algorithmic flops of the factorization         */
+  double apply_bytes;          /* factor bytes read by one apply of F^-1         */
+  double t_factor_ms;          /* device time of the last hif_factor             */
+} hif_stats_t;
+
+/*
+ * hif_factor -- Algorithm 3.1 (variant MF) or Algorithm 4.1 (variant HIFDE):
+ * for l = 0..L-1, eliminate the interiors of the level-l cells (Lemma 2.1),
+ * then skeletonize the strict interiors of the level-l edges (2D) or faces
+ * (3D) with an ID of relative precision eps (Lemma 2.4, Section 4.3), and
+ * finally factor D = A_L (Cholesky).  eps must be > 0 for HIFDE; it is
+ * ignored for MF.  bc_vals must be NULL (zero Dirichlet data; nonzero data
+ * belong in the right-hand side).  On success *out owns the factor in
+ * device memory; release it with hif_free.
+ */
+int hif_factor(const hif_grid* grid, const double* a_stag, const double* b,
+               const double* bc_vals, double eps, const hif_opts* opts,
+               hif_handle** out);
+
+/*
+ * hif_apply -- y = F x (mode HIF_APPLY_F) or y = F^-1 x (HIF_APPLY_FINV),
+ * with F the generalized LDL^T factorization of Eq. (3.1) / (4.2).
+ * x and y: N x nrhs, row stride ld (see above); x and y may alias.
+ */
+int hif_apply(hif_handle* h, int mode, const double* x, double* y, int nrhs, int ld);
+
+/*
+ * hif_solve -- preconditioned CG (Section 5) on A x = rhs with F^-1 as the
+ * preconditioner, one independent iteration per column, started from x = 0,
+ * until ||rhs_r - A x_r||_2 <= tol ||rhs_r||_2 for every column, or maxit
+ * inner iterations.  The iterate is kept in double-double, x = x_hi + x_lo,
+ * and the residual is evaluated in double-double from the bond form of the
+ * stencil (exact coefficients a n^2): for high-contrast fields the rounding
+ * floor of the residual of an FP64 vector lies above 1e-12 (about 2e-10 for a
+ * contrast of 1e6 on a 511^2 grid), so the tolerance is certified on x_hi +
+ * x_lo.  CG runs in FP64 on corrections (iterative refinement, each step to
+ * max(tol ||rhs|| / (2 ||r||), 1e-9) relative).  x receives x_hi; x_lo may be
+ * NULL.  info may be NULL.  Returns HIF_ERR_NOCONV if maxit is reached (x
+ * then holds the last iterate).
+ */
+int hif_solve(hif_handle* h, const double* rhs, double* x, double* x_lo, int nrhs,
+              int ld, double tol, int maxit, hif_solve_info* info);
+
+/* hif_matvec -- y = A x with the stencil of the factored problem (FP64). */
+int hif_matvec(hif_handle* h, const double* x, double* y, int nrhs, int ld);
+
+/* hif_stats -- sizes and counts of the factorization (Section 5 columns). */
+int hif_stats(const hif_handle* h, hif_stats_t* st);
+
+/*
+ * hif_structure -- the skeleton structure, for parity checks against the
+ * oracle.  Writes int32 records, one per skeletonized front in level order:
+ *   level, |c|, k, c[0..|c|-1] (ascending global indices),
+ *   s[0..k-1] (skeleton global indices in pivot order)
+ * followed by the terminator -1 and then |s_L|.  If buf is NULL or cap is too
+ * small, nothing is written; *needed receives the number of int32 required.
+ */
+int hif_structure(const hif_handle* h, int32_t* buf, long long cap, long long* needed);
+
+/* hif_free -- release the factor (stream-ordered on the handle's stream). */
+void hif_free(hif_handle* h);
+
+/* hif_last_error -- message of the last failure on this thread ("" if none). */
+const char* hif_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HIF_H */

@@ -1,0 +1,161 @@
+// Dense block operations executed cooperatively by one thread block on a
+// matrix in shared or global memory (row-major, leading dimension ld).
+// Every routine ends with __syncthreads().
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace hif {
+
+template <typename T> __device__ __forceinline__ T dsqrt(T x);
+template <> __device__ __forceinline__ double dsqrt<double>(double x) { return sqrt(x); }
+template <> __device__ __forceinline__ float dsqrt<float>(float x) { return sqrtf(x); }
+
+// In-place lower Cholesky A = L L^T (right-looking).  Only the lower triangle
+// is read; the strict upper triangle is used as scratch (original diagonal).
+// tau == 0: a non-positive or non-finite pivot sets bit 0 of status[0] and is
+// replaced by 1.  tau > 0 (safeguarded form, used when the block carries FP32
+// rounding): a pivot below tau * d0 is raised to tau * d0 and counted in
+// status[1], where d0 is its original diagonal entry (or the largest original
+// diagonal entry of the block when that is not positive), so the factor stays
+// SPD; only a block without a positive finite diagonal sets bit 0.
+template <typename T>
+__device__ void blk_cholesky(T* A, int n, int ld, int* status, T tau = T(0)) {
+  __shared__ T s_piv, s_dmax;
+  if (tau > T(0)) {
+    for (int j = 1 + threadIdx.x; j < n; j += blockDim.x)
+      A[(int64_t)(j - 1) * ld + j] = A[(int64_t)j * ld + j];
+    if (threadIdx.x == 0) {
+      T dm = T(0);
+      for (int j = 0; j < n; ++j) {
+        const T d = A[(int64_t)j * ld + j];
+        if (d > dm && isfinite((double)d)) dm = d;
+      }
+      s_dmax = dm;
+    }
+    __syncthreads();
+  }
+  for (int j = 0; j < n; ++j) {
+    if (threadIdx.x == 0) {
+      T d = A[(int64_t)j * ld + j];
+      if (tau > T(0)) {
+        T d0 = (j == 0) ? d : A[(int64_t)(j - 1) * ld + j];
+        if (!(d0 > T(0)) || !isfinite((double)d0)) d0 = s_dmax;
+        if (!(d0 > T(0))) {
+          atomicOr(status, 1);
+          d = T(1);
+        } else if (!(d > tau * d0) || !isfinite((double)d)) {
+          atomicAdd(status + 1, 1);
+          d = tau * d0;
+        }
+      } else if (!(d > T(0)) || !isfinite((double)d)) {
+        atomicOr(status, 1);
+        d = T(1);
+      }
+      d = dsqrt(d);
+      A[(int64_t)j * ld + j] = d;
+      s_piv = T(1) / d;
+    }
+    __syncthreads();
+    const T r = s_piv;
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[(int64_t)i * ld + j] *= r;
+    __syncthreads();
+    const int m = n - j - 1;
+    const int64_t tot = (int64_t)m * m;
+    for (int64_t e = threadIdx.x; e < tot; e += blockDim.x) {
+      const int i = j + 1 + (int)(e / m);
+      const int k = j + 1 + (int)(e % m);
+      if (k <= i) A[(int64_t)i * ld + k] -= A[(int64_t)i * ld + j] * A[(int64_t)k * ld + j];
+    }
+    __syncthreads();
+  }
+}
+
+// X = L^{-1} for lower-triangular L (n x n).  X is written in full (zeros
+// above the diagonal).  Column-oriented forward substitution on the identity.
+template <typename T>
+__device__ void blk_tri_inverse(const T* L, int n, int ldl, T* X, int ldx) {
+  for (int64_t e = threadIdx.x; e < (int64_t)n * n; e += blockDim.x) {
+    const int i = (int)(e / n), c = (int)(e % n);
+    X[(int64_t)i * ldx + c] = (i == c) ? T(1) : T(0);
+  }
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    const T r = T(1) / L[(int64_t)k * ldl + k];
+    for (int c = threadIdx.x; c <= k; c += blockDim.x) X[(int64_t)k * ldx + c] *= r;
+    __syncthreads();
+    const int m = n - k - 1;
+    const int64_t tot = (int64_t)m * (k + 1);
+    for (int64_t e = threadIdx.x; e < tot; e += blockDim.x) {
+      const int i = k + 1 + (int)(e / (k + 1));
+      const int c = (int)(e % (k + 1));
+      X[(int64_t)i * ldx + c] -= L[(int64_t)i * ldl + k] * X[(int64_t)k * ldx + c];
+    }
+    __syncthreads();
+  }
+}
+
+// C (m x n) = A (m x kk) * Linv^T, Linv lower (n x n, kk == n): C[i][j] = sum_{t<=j} A[i][t] Linv[j][t].
+template <typename T>
+__device__ void blk_mul_linvT(const T* A, int lda, const T* Linv, int ldl, int m, int n, T* C, int ldc) {
+  for (int64_t e = threadIdx.x; e < (int64_t)m * n; e += blockDim.x) {
+    const int i = (int)(e / n), j = (int)(e % n);
+    const T* a = A + (int64_t)i * lda;
+    const T* l = Linv + (int64_t)j * ldl;
+    T s = T(0);
+    for (int t = 0; t <= j; ++t) s += a[t] * l[t];
+    C[(int64_t)i * ldc + j] = s;
+  }
+  __syncthreads();
+}
+
+// C (m x m, full symmetric) -= G G^T, G m x kk.
+template <typename T>
+__device__ void blk_syrk_sub(T* C, int ldc, const T* G, int ldg, int m, int kk) {
+  const int64_t tot = (int64_t)m * (m + 1) / 2;
+  for (int64_t e = threadIdx.x; e < tot; e += blockDim.x) {
+    // map e -> (i, j) with j <= i
+    int i = (int)((sqrt(8.0 * (double)e + 1.0) - 1.0) * 0.5);
+    while ((int64_t)(i + 1) * (i + 2) / 2 <= e) ++i;
+    while ((int64_t)i * (i + 1) / 2 > e) --i;
+    const int j = (int)(e - (int64_t)i * (i + 1) / 2);
+    const T* gi = G + (int64_t)i * ldg;
+    const T* gj = G + (int64_t)j * ldg;
+    T s = T(0);
+    for (int t = 0; t < kk; ++t) s += gi[t] * gj[t];
+    const T v = C[(int64_t)i * ldc + j] - s;
+    C[(int64_t)i * ldc + j] = v;
+    C[(int64_t)j * ldc + i] = v;
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__device__ void blk_copy(const T* A, int lda, T* B, int ldb, int m, int n) {
+  for (int64_t e = threadIdx.x; e < (int64_t)m * n; e += blockDim.x) {
+    const int i = (int)(e / n), j = (int)(e % n);
+    B[(int64_t)i * ldb + j] = A[(int64_t)i * lda + j];
+  }
+  __syncthreads();
+}
+
+// Copy the lower triangle of A into B and zero B's strict upper triangle.
+template <typename T>
+__device__ void blk_copy_lower(const T* A, int lda, T* B, int ldb, int n) {
+  for (int64_t e = threadIdx.x; e < (int64_t)n * n; e += blockDim.x) {
+    const int i = (int)(e / n), j = (int)(e % n);
+    B[(int64_t)i * ldb + j] = (j <= i) ? A[(int64_t)i * lda + j] : T(0);
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+}  // namespace hif

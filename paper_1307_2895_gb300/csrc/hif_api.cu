@@ -1,0 +1,846 @@
+// C ABI and host driver of the factorization, the apply and the CG solve.
+//
+// Factorization (Algorithm 3.1 / 4.1), per level l = 0..L-1:
+//   host  : index sets of the level-l cells (interior I, boundary B) from the
+//           DOFs still active, child maps into the level-(l-1) boundaries
+//   device: frontal assembly (stencil at l = 0, extend-add above), then the
+//           interior elimination of every cell (Lemma 2.1), one launch each
+//   host  : fronts of level l + 1/2
+//   device: one launch for every front: ID (Lemma 2.2) + Lemma 2.4
+//   host  : read back the ranks and skeletons, drop the redundant DOFs
+// then the root D = A_L (a level-L cell without boundary, always FP64).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/hif.h"
+#include "geometry.h"
+#include "hif_internal.h"
+#include "kernels.h"
+
+using namespace hif;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+struct HifError {
+  int code;
+  std::string msg;
+  HifError(int c, std::string m) : code(c), msg(std::move(m)) {}
+};
+
+#define CU(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess) {                                                              \
+      throw HifError(e_ == cudaErrorMemoryAllocation ? HIF_ERR_OOM : HIF_ERR_CUDA,        \
+                     std::string(#call) + ": " + cudaGetErrorString(e_));                 \
+    }                                                                                     \
+  } while (0)
+
+// Stream-ordered device buffer.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  cudaStream_t st = nullptr;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept { swap(o); }
+  ~DevBuf() { release(); }
+  void swap(DevBuf& o) {
+    std::swap(p, o.p);
+    std::swap(bytes, o.bytes);
+    std::swap(st, o.st);
+  }
+  void alloc(size_t b, cudaStream_t s) {
+    release();
+    st = s;
+    bytes = b;
+    if (b == 0) return;
+    CU(cudaMallocAsync(&p, b, s));
+  }
+  void release() {
+    if (p) cudaFreeAsync(p, st);
+    p = nullptr;
+    bytes = 0;
+  }
+  template <typename T> T* as() const { return reinterpret_cast<T*>(p); }
+};
+
+template <typename T>
+void upload(DevBuf& d, const std::vector<T>& h, cudaStream_t st) {
+  d.alloc(h.size() * sizeof(T), st);
+  if (!h.empty())
+    CU(cudaMemcpyAsync(d.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Apply-side view of one kind of block (cells or fronts) at one level.
+struct SweepLevel {
+  int nblocks = 0, max_np = 0, max_nq = 0;
+  DevBuf desc;    // ApplyDesc[nblocks]
+  DevBuf ipool;   // ids
+  DevBuf fac;     // factor pool
+  DevBuf fac32;   // float copy (root in mixed precision)
+};
+
+struct FrontInfo {
+  int level;
+  std::vector<int> c, sk;
+};
+
+}  // namespace
+
+struct hif_handle {
+  Geometry G;
+  GridInfo gi{};
+  int precision = HIF_PREC_FP64;
+  int variant = HIF_VARIANT_HIFDE;
+  int skip_levels = 0;
+  double eps = 0.0;
+  cudaStream_t st = nullptr;
+  DevBuf a_stag, bnode;
+  std::vector<SweepLevel> cells, fronts;   // levels 0..L-1
+  SweepLevel root;                         // level L
+  std::vector<FrontInfo> finfo;
+  int root_size = 0, n_cells = 0, n_fronts = 0, max_rank = 0, near = 0, clamped = 0;
+  long long factor_bytes = 0;
+  double factor_flops = 0.0, apply_bytes = 0.0, t_factor_ms = 0.0;
+};
+
+namespace {
+
+struct CellLevelDev {
+  std::vector<CellDesc> desc;
+  DevBuf d_desc;
+  int max_nI = 0;
+  void swap(CellLevelDev& o) {
+    desc.swap(o.desc);
+    d_desc.swap(o.d_desc);
+    std::swap(max_nI, o.max_nI);
+  }
+};
+
+void prepare_cells(const Geometry& G, int l, const std::vector<HostCell>& cells,
+                   const std::vector<HostCell>* prev, CellLevelDev& out, std::vector<int>& ipool,
+                   int64_t& work_elems, int64_t& fac_elems) {
+  out.desc.resize(cells.size());
+  ipool.clear();
+  work_elems = fac_elems = 0;
+  out.max_nI = 0;
+  std::vector<int> cmap;
+  for (size_t i = 0; i < cells.size(); ++i) {
+    const HostCell& c = cells[i];
+    CellDesc& d = out.desc[i];
+    d.nI = (int)c.I.size();
+    d.nB = (int)c.B.size();
+    d.cell_lin = (int)i;
+    d.ids = (int64_t)ipool.size();
+    ipool.insert(ipool.end(), c.I.begin(), c.I.end());
+    ipool.insert(ipool.end(), c.B.begin(), c.B.end());
+    d.F = work_elems;
+    work_elems += (int64_t)d.nI * d.nI + (int64_t)d.nB * d.nI + (int64_t)d.nB * d.nB;
+    d.fac = fac_elems;
+    fac_elems += 2 * (int64_t)d.nI * d.nI + (int64_t)d.nB * d.nI;
+    for (int s = 0; s < kMaxChild; ++s) d.child[s] = -1;
+    d.cmap = -1;
+    if (l > 0 && prev) {
+      build_child_map(G, l, c, (int)i, *prev, cmap, d.child);
+      d.cmap = (int64_t)ipool.size();
+      ipool.insert(ipool.end(), cmap.begin(), cmap.end());
+    }
+    out.max_nI = std::max(out.max_nI, d.nI);
+  }
+}
+
+void cell_apply_descs(SweepLevel& S, const std::vector<CellDesc>& cd, cudaStream_t st) {
+  std::vector<ApplyDesc> ad;
+  ad.reserve(cd.size());
+  S.max_np = S.max_nq = 0;
+  for (const CellDesc& c : cd) {
+    ApplyDesc a;
+    a.np = c.nI;
+    a.nq = c.nB;
+    a.ids = c.ids;
+    a.Linv = c.fac;
+    a.L = c.fac + (int64_t)c.nI * c.nI;
+    a.G = c.fac + 2 * (int64_t)c.nI * c.nI;
+    a.T = -1;
+    ad.push_back(a);
+    S.max_np = std::max(S.max_np, c.nI);
+    S.max_nq = std::max(S.max_nq, c.nB);
+  }
+  S.nblocks = (int)ad.size();
+  upload(S.desc, ad, st);
+}
+
+template <typename T>
+struct Factorizer {
+  hif_handle* h;
+  const Geometry& G;
+  cudaStream_t st;
+  DevBuf status, d_cls0;
+  std::vector<char> dead;
+  std::vector<int> mark;
+
+  // pivot floor of the safeguarded Cholesky: every block in mixed precision
+  // (including the FP64 root, whose entries carry FP32 rounding), none in FP64
+  double tau = 0.0;
+
+  explicit Factorizer(hif_handle* h_) : h(h_), G(h_->G), st(h_->st) {
+    tau = (h_->precision == HIF_PREC_MIXED) ? 4e-6 : 0.0;
+  }
+
+  void account_cells(const std::vector<CellDesc>& cd, size_t esz) {
+    for (const CellDesc& c : cd) {
+      const double nI = c.nI, nB = c.nB;
+      if (c.nI == 0) continue;
+      // Cholesky nI^3/3, triangular inverse nI^3/3, G = F_BI Linv^T nB nI^2, SYRK nB^2 nI
+      h->factor_flops += 2.0 * nI * nI * nI / 3.0 + nB * nI * nI + nB * nB * nI;
+      h->apply_bytes += 2.0 * (double)esz * (nI * (nI + 1) / 2 + nB * nI);
+      h->factor_bytes += (long long)(esz * (nI * (nI + 1) / 2 + nB * nI));
+      h->n_cells += 1;
+    }
+  }
+
+  void run() {
+    const int L = G.L, dim = G.dim, nchild = 1 << dim;
+    status.alloc(2 * sizeof(int), st);
+    CU(cudaMemsetAsync(status.p, 0, 2 * sizeof(int), st));
+    upload(d_cls0, G.cls[0], st);
+    dead.assign(G.N, 0);
+    std::vector<int> alive(G.N);
+    for (int64_t g = 0; g < G.N; ++g) alive[g] = (int)g;
+
+    std::vector<HostCell> prev_cells, cells;
+    CellLevelDev prev_dev, cur_dev;
+    DevBuf prev_work, work;
+    std::vector<int> ipool;
+    h->cells.resize(L);
+    h->fronts.resize(L);
+    const bool skel = (h->variant == HIF_VARIANT_HIFDE) && h->eps > 0.0;
+
+    for (int l = 0; l <= L; ++l) {
+      const bool is_root = (l == L);
+      build_cells(G, l, alive, cells);
+      int64_t work_elems = 0, fac_elems = 0;
+      SweepLevel& sw = is_root ? h->root : h->cells[l];
+      prepare_cells(G, l, cells, l > 0 ? &prev_cells : nullptr, cur_dev, ipool, work_elems,
+                    fac_elems);
+      upload(cur_dev.d_desc, cur_dev.desc, st);
+      upload(sw.ipool, ipool, st);
+      const int ncells = (int)cells.size();
+      const size_t esz = is_root ? sizeof(double) : sizeof(T);
+      work.alloc((size_t)work_elems * esz, st);
+      sw.fac.alloc((size_t)fac_elems * esz, st);
+      const CellDesc* dd = cur_dev.d_desc.as<CellDesc>();
+      if (is_root) {
+        launch_extend_add<T, double>(dd, ncells, sw.ipool.as<int>(), work.as<double>(),
+                                     prev_dev.d_desc.as<CellDesc>(), prev_work.as<T>(), nchild, st);
+        launch_cell_factor<double>(dd, ncells, work.as<double>(), sw.fac.as<double>(),
+                                   status.as<int>(), cur_dev.max_nI, tau, st);
+      } else if (l == 0) {
+        launch_leaf_assemble<T>(dd, ncells, sw.ipool.as<int>(), work.as<T>(), h->gi,
+                                h->a_stag.as<double>(), h->bnode.as<double>(), d_cls0.as<int>(),
+                                G.ncell[0], st);
+        launch_cell_factor<T>(dd, ncells, work.as<T>(), sw.fac.as<T>(), status.as<int>(),
+                              cur_dev.max_nI, tau, st);
+      } else {
+        launch_extend_add<T, T>(dd, ncells, sw.ipool.as<int>(), work.as<T>(),
+                                prev_dev.d_desc.as<CellDesc>(), prev_work.as<T>(), nchild, st);
+        launch_cell_factor<T>(dd, ncells, work.as<T>(), sw.fac.as<T>(), status.as<int>(),
+                              cur_dev.max_nI, tau, st);
+      }
+      CU(cudaGetLastError());
+      cell_apply_descs(sw, cur_dev.desc, st);
+      account_cells(cur_dev.desc, esz);
+      prev_work.release();           // the level l-1 updates have been consumed
+      if (is_root) {
+        h->root_size = cur_dev.desc.empty() ? 0 : cur_dev.desc[0].nI;
+        if (sizeof(T) == sizeof(float) && fac_elems > 0) {
+          sw.fac32.alloc((size_t)fac_elems * sizeof(float), st);
+          launch_convert<double, float>(fac_elems, 1, sw.fac.as<double>(), 1, sw.fac32.as<float>(), 1, st);
+        }
+        work.release();
+        break;
+      }
+      // the eliminated interiors leave the active set
+      {
+        std::vector<int> next;
+        next.reserve(alive.size());
+        for (const HostCell& c : cells)
+          for (int g : c.I) dead[g] = 1;
+        for (int g : alive)
+          if (!dead[g]) next.push_back(g);
+        alive.swap(next);
+      }
+      if (skel && l >= h->skip_levels) run_fronts(l, cells, cur_dev, work, alive);
+      prev_cells.swap(cells);
+      prev_dev.swap(cur_dev);
+      prev_work.swap(work);
+    }
+    int hs2[2] = {0, 0};
+    CU(cudaMemcpyAsync(hs2, status.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    const int hs = hs2[0];
+    h->clamped = hs2[1];
+    if (hs & 1) throw HifError(HIF_ERR_NOT_SPD, "non-positive pivot in a diagonal-block Cholesky");
+  }
+
+  void run_fronts(int l, const std::vector<HostCell>& cells, CellLevelDev& cdev, DevBuf& cwork,
+                  std::vector<int>& alive) {
+    std::vector<HostFront> fr;
+    build_fronts(G, l, alive, cells, fr, mark);
+    SweepLevel& sw = h->fronts[l];
+    if (fr.empty()) return;
+    const int nf = (int)fr.size();
+    std::vector<FrontDesc> fd(nf);
+    std::vector<int> ip;
+    int64_t work_elems = 0, fac_elems = 0;
+    int max_nc = 0, max_nN = 0;
+    for (int f = 0; f < nf; ++f) {
+      const HostFront& F = fr[f];
+      FrontDesc& d = fd[f];
+      d.nc = (int)F.c.size();
+      d.nN = (int)F.N.size();
+      d.P1 = F.P1;
+      d.P2 = F.P2;
+      d.ids = (int64_t)ip.size();
+      ip.insert(ip.end(), F.c.begin(), F.c.end());
+      ip.insert(ip.end(), F.pos1.begin(), F.pos1.end());
+      ip.insert(ip.end(), F.pos2.begin(), F.pos2.end());
+      d.out = (int64_t)ip.size();
+      ip.insert(ip.end(), 1 + 2 * d.nc, 0);
+      d.work = work_elems;
+      work_elems += (int64_t)d.nN * d.nc + 4 * (int64_t)d.nc * d.nc;
+      d.fac = fac_elems;
+      fac_elems += 4 * (int64_t)d.nc * d.nc;
+      max_nc = std::max(max_nc, d.nc);
+      max_nN = std::max(max_nN, d.nN);
+    }
+    DevBuf d_fd, d_ip, fwork;
+    upload(d_fd, fd, st);
+    upload(d_ip, ip, st);
+    fwork.alloc((size_t)work_elems * sizeof(T), st);
+    sw.fac.alloc((size_t)fac_elems * sizeof(T), st);
+    launch_front<T>(d_fd.as<FrontDesc>(), nf, cdev.d_desc.as<CellDesc>(), d_ip.as<int>(),
+                    fwork.as<T>(), sw.fac.as<T>(), cwork.as<T>(), h->eps, status.as<int>(), max_nc,
+                    max_nN, tau, st);
+    CU(cudaGetLastError());
+    std::vector<int> hip(ip.size());
+    CU(cudaMemcpyAsync(hip.data(), d_ip.p, ip.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
+    int hstat = 0;
+    CU(cudaMemcpyAsync(&hstat, status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    if (hstat & 2) {
+      h->near += 1;
+      const int keep = hstat & 1;
+      CU(cudaMemcpyAsync(status.p, &keep, sizeof(int), cudaMemcpyHostToDevice, st));
+      CU(cudaStreamSynchronize(st));
+    }
+    fwork.release();
+    // apply descriptors: p = redundant (ascending), q = skeletons (pivot order)
+    std::vector<ApplyDesc> ad(nf);
+    std::vector<int> aip;
+    sw.max_np = sw.max_nq = 0;
+    const double esz = (double)sizeof(T);
+    for (int f = 0; f < nf; ++f) {
+      const FrontDesc& d = fd[f];
+      const int* out = hip.data() + d.out;
+      const int k = out[0];
+      const int nR = d.nc - k;
+      const int* ids_sr = out + 1 + d.nc;
+      ApplyDesc& a = ad[f];
+      a.np = nR;
+      a.nq = k;
+      a.ids = (int64_t)aip.size();
+      aip.insert(aip.end(), ids_sr + k, ids_sr + d.nc);
+      aip.insert(aip.end(), ids_sr, ids_sr + k);
+      a.T = d.fac;
+      a.Linv = d.fac + (int64_t)d.nc * d.nc;
+      a.L = d.fac + 2 * (int64_t)d.nc * d.nc;
+      a.G = d.fac + 3 * (int64_t)d.nc * d.nc;
+      sw.max_np = std::max(sw.max_np, nR);
+      sw.max_nq = std::max(sw.max_nq, k);
+      for (int t = k; t < d.nc; ++t) dead[ids_sr[t]] = 1;
+      FrontInfo fi;
+      fi.level = l;
+      fi.c = fr[f].c;
+      fi.sk.assign(ids_sr, ids_sr + k);
+      h->finfo.push_back(std::move(fi));
+      h->n_fronts += 1;
+      h->max_rank = std::max(h->max_rank, k);
+      const double nc = d.nc, nN = d.nN, kk = k, nr = nR;
+      // QR (recomputed norms and reflections: ~4 nN nc per step), T, B_rr/B_sr, Cholesky,
+      // inverse, G and B_ss
+      h->factor_flops += 4.0 * nN * nc * (kk + 1) + kk * kk * nr + 2.0 * kk * kk * nr +
+                         2.0 * kk * nr * nr + 2.0 * nr * nr * nr / 3.0 + kk * nr * nr + kk * kk * nr;
+      h->apply_bytes += 2.0 * esz * (2 * kk * nr + nr * (nr + 1) / 2);
+      h->factor_bytes += (long long)(esz * (2 * kk * nr + nr * (nr + 1) / 2));
+    }
+    sw.nblocks = nf;
+    upload(sw.desc, ad, st);
+    upload(sw.ipool, aip, st);
+    std::vector<int> next;
+    next.reserve(alive.size());
+    for (int g : alive)
+      if (!dead[g]) next.push_back(g);
+    alive.swap(next);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// apply of F^-1 / F on a packed N x nrhs work vector of the factor's type
+// ---------------------------------------------------------------------------
+template <typename T>
+const T* level_fac(const SweepLevel& S) {
+  return S.fac.as<T>();
+}
+
+template <typename T>
+void run_apply(hif_handle* h, int mode, T* x, int nrhs) {
+  const int L = h->G.L;
+  cudaStream_t st = h->st;
+  const int up = (mode == HIF_APPLY_FINV) ? 0 : 2;
+  const int down = (mode == HIF_APPLY_FINV) ? 1 : 3;
+  auto sweep = [&](const SweepLevel& S, int op, int is_front, const T* fac) {
+    if (S.nblocks == 0) return;
+    launch_sweep<T>(op, S.desc.as<ApplyDesc>(), S.nblocks, S.ipool.as<int>(), fac, x, nrhs, nrhs,
+                    is_front, S.max_np, S.max_nq, st);
+  };
+  const T* root_fac = (sizeof(T) == sizeof(float)) ? reinterpret_cast<const T*>(h->root.fac32.p)
+                                                   : h->root.fac.as<T>();
+  for (int l = 0; l < L; ++l) {
+    sweep(h->cells[l], up, 0, h->cells[l].fac.as<T>());
+    sweep(h->fronts[l], up, 1, h->fronts[l].fac.as<T>());
+  }
+  sweep(h->root, up, 0, root_fac);
+  sweep(h->root, down, 0, root_fac);
+  for (int l = L - 1; l >= 0; --l) {
+    sweep(h->fronts[l], down, 1, h->fronts[l].fac.as<T>());
+    sweep(h->cells[l], down, 0, h->cells[l].fac.as<T>());
+  }
+}
+
+// z (double, packed N x nr) = F^-1 r (double, packed), via the factor's type
+void precondition(hif_handle* h, const double* r, double* z, float* wf, int nr) {
+  const int64_t N = h->G.N;
+  if (h->precision == HIF_PREC_MIXED) {
+    launch_convert<double, float>(N, nr, r, nr, wf, nr, h->st);
+    run_apply<float>(h, HIF_APPLY_FINV, wf, nr);
+    launch_convert<float, double>(N, nr, wf, nr, z, nr, h->st);
+  } else {
+    CU(cudaMemcpyAsync(z, r, sizeof(double) * N * nr, cudaMemcpyDeviceToDevice, h->st));
+    run_apply<double>(h, HIF_APPLY_FINV, z, nr);
+  }
+}
+
+// Stage a user vector (host or device, strided) into a packed device array.
+struct Staged {
+  DevBuf buf;
+};
+
+void stage_in(const double* user, int nr, int ld, int64_t N, double* packed, cudaStream_t st,
+              DevBuf& tmp) {
+  if (is_device_ptr(user)) {
+    launch_convert<double, double>(N, nr, user, ld, packed, nr, st);
+  } else {
+    if (ld == nr) {
+      CU(cudaMemcpyAsync(packed, user, sizeof(double) * N * nr, cudaMemcpyHostToDevice, st));
+    } else {
+      tmp.alloc(sizeof(double) * N * ld, st);
+      CU(cudaMemcpyAsync(tmp.p, user, sizeof(double) * ((N - 1) * ld + nr), cudaMemcpyHostToDevice, st));
+      launch_convert<double, double>(N, nr, tmp.as<double>(), ld, packed, nr, st);
+    }
+  }
+}
+
+void stage_out(const double* packed, int nr, int ld, int64_t N, double* user, cudaStream_t st,
+               DevBuf& tmp) {
+  if (is_device_ptr(user)) {
+    launch_convert<double, double>(N, nr, packed, nr, user, ld, st);
+  } else {
+    if (ld == nr) {
+      CU(cudaMemcpyAsync(user, packed, sizeof(double) * N * nr, cudaMemcpyDeviceToHost, st));
+    } else {
+      tmp.alloc(sizeof(double) * N * ld, st);
+      CU(cudaMemcpyAsync(tmp.p, user, sizeof(double) * ((N - 1) * ld + nr), cudaMemcpyHostToDevice, st));
+      launch_convert<double, double>(N, nr, packed, nr, tmp.as<double>(), ld, st);
+      CU(cudaMemcpyAsync(user, tmp.p, sizeof(double) * ((N - 1) * ld + nr), cudaMemcpyDeviceToHost, st));
+    }
+  }
+}
+
+// Solver workspace for one chunk of right-hand sides (N x nr, packed).
+struct SolveWork {
+  int64_t N = 0;
+  int nr = 0;
+  DevBuf b, xh, xl, D, R, Z, P, Q, WF, part, scal, cnt;
+  double *rz, *pq, *rr, *rzzq, *alpha, *thr2, *bn2, *rn2;
+  int* active;
+  void init(int64_t N_, int nr_, bool mixed, cudaStream_t st) {
+    N = N_;
+    nr = nr_;
+    const size_t vb = sizeof(double) * N * nr;
+    b.alloc(vb, st); xh.alloc(vb, st); xl.alloc(vb, st); D.alloc(vb, st);
+    R.alloc(vb, st); Z.alloc(vb, st); P.alloc(vb, st); Q.alloc(vb, st);
+    if (mixed) WF.alloc(sizeof(float) * N * nr, st);
+    const int nblocks = (int)((N + 255) / 256);
+    part.alloc(sizeof(double) * nblocks * 2 * nr, st);
+    scal.alloc(sizeof(double) * 10 * nr + sizeof(int) * nr, st);
+    cnt.alloc(sizeof(unsigned), st);
+    CU(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned), st));
+    double* s = scal.as<double>();
+    rz = s; pq = s + nr; rr = s + 2 * nr; rzzq = s + 3 * nr; alpha = s + 5 * nr;
+    thr2 = s + 6 * nr; bn2 = s + 7 * nr; rn2 = s + 8 * nr;
+    active = reinterpret_cast<int*>(s + 10 * nr);
+  }
+};
+
+// Inner PCG on A d = R (FP64, preconditioner F^-1), columns whose squared
+// residual is above thr2 are active.  Stops when every recursive residual is
+// below its threshold and the FP64 true residual confirms it (or after maxit).
+int inner_pcg(hif_handle* h, SolveWork& W, const std::vector<double>& hthr, int maxit) {
+  const int64_t N = W.N;
+  const int nr = W.nr;
+  cudaStream_t st = h->st;
+  double* partials = W.part.as<double>();
+  unsigned* counter = W.cnt.as<unsigned>();
+  const size_t vb = sizeof(double) * N * nr;
+  CU(cudaMemcpyAsync(W.thr2, hthr.data(), sizeof(double) * nr, cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(W.b.p, W.R.p, vb, cudaMemcpyDeviceToDevice, st));   // inner right-hand side
+  CU(cudaMemsetAsync(W.D.p, 0, vb, st));
+  launch_sqnorm(N, nr, W.R.as<double>(), partials, counter, W.rr, st);
+  launch_set_active(nr, W.rr, W.thr2, W.active, st);
+  std::vector<double> hr(nr);
+  int it = 0, restarts = 0;
+  bool restart = true;
+  while (true) {
+    precondition(h, W.R.as<double>(), W.Z.as<double>(), W.WF.as<float>(), nr);
+    launch_dot2(N, nr, W.R.as<double>(), W.Z.as<double>(), W.Q.as<double>(), partials, counter, W.rzzq, st);
+    launch_update_p(N, nr, W.P.as<double>(), W.Z.as<double>(), W.alpha, W.rz, W.rzzq, W.active,
+                    restart ? 1 : 0, st);
+    CU(cudaMemcpyAsync(W.rz, W.rzzq, sizeof(double) * nr, cudaMemcpyDeviceToDevice, st));
+    restart = false;
+    if (it >= maxit) break;
+    launch_mv_dot(h->gi, h->a_stag.as<double>(), h->bnode.as<double>(), W.P.as<double>(),
+                  W.Q.as<double>(), nr, partials, counter, W.pq, st);
+    launch_axpy2(N, nr, W.D.as<double>(), W.R.as<double>(), W.P.as<double>(), W.Q.as<double>(), W.rz,
+                 W.pq, W.active, W.alpha, partials, counter, W.rr, st);
+    launch_set_active(nr, W.rr, W.thr2, W.active, st);
+    ++it;
+    CU(cudaMemcpyAsync(hr.data(), W.rr, sizeof(double) * nr, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    bool all = true;
+    for (int c = 0; c < nr; ++c)
+      if (hr[c] > hthr[c]) all = false;
+    if (!all) continue;
+    // confirm with the FP64 true residual of the inner system
+    launch_residual(h->gi, h->a_stag.as<double>(), h->bnode.as<double>(), W.b.as<double>(),
+                    W.D.as<double>(), W.R.as<double>(), nr, partials, counter, W.rr, st);
+    CU(cudaMemcpyAsync(hr.data(), W.rr, sizeof(double) * nr, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    bool ok = true;
+    for (int c = 0; c < nr; ++c)
+      if (hr[c] > hthr[c]) ok = false;
+    if (ok || ++restarts > 3) break;
+    launch_set_active(nr, W.rr, W.thr2, W.active, st);
+    restart = true;
+  }
+  return it;
+}
+
+// Outer refinement: x = xh + xl (double-double), r = f - A x evaluated in
+// double-double; each step solves A d = r by inner_pcg to a relative
+// tolerance tau = max(tol ||f|| / (2 ||r||), 1e-9) and adds d to x.
+int solve_chunk(hif_handle* h, const double* rhs, double* x, double* xlo, int nr, double tol,
+                int maxit, hif_solve_info* info) {
+  const int64_t N = h->G.N;
+  cudaStream_t st = h->st;
+  const size_t vb = sizeof(double) * N * nr;
+  SolveWork W;
+  W.init(N, nr, h->precision == HIF_PREC_MIXED, st);
+  double* partials = W.part.as<double>();
+  unsigned* counter = W.cnt.as<unsigned>();
+  DevBuf f;
+  f.alloc(vb, st);
+  CU(cudaMemcpyAsync(f.p, rhs, vb, cudaMemcpyDeviceToDevice, st));
+  launch_sqnorm(N, nr, f.as<double>(), partials, counter, W.bn2, st);
+  std::vector<double> hb(nr), hr(nr), hthr(nr);
+  CU(cudaMemcpyAsync(hb.data(), W.bn2, sizeof(double) * nr, cudaMemcpyDeviceToHost, st));
+  CU(cudaMemsetAsync(W.xh.p, 0, vb, st));
+  CU(cudaMemsetAsync(W.xl.p, 0, vb, st));
+  CU(cudaMemcpyAsync(W.R.p, f.p, vb, cudaMemcpyDeviceToDevice, st));
+  CU(cudaStreamSynchronize(st));
+  hr = hb;
+  int iters = 0, outer = 0;
+  bool converged = false;
+  double relmax = 0.0;
+  while (true) {
+    bool all = true;
+    relmax = 0.0;
+    for (int c = 0; c < nr; ++c) {
+      const double rel = hb[c] > 0 ? std::sqrt(hr[c] / hb[c]) : 0.0;
+      relmax = std::max(relmax, rel);
+      if (hr[c] > tol * tol * hb[c]) all = false;
+    }
+    if (all) { converged = true; break; }
+    if (iters >= maxit || outer >= 8) break;
+    for (int c = 0; c < nr; ++c) {
+      if (hr[c] <= tol * tol * hb[c]) { hthr[c] = 1e300; continue; }   // column done
+      const double tau = std::max(0.5 * tol * std::sqrt(hb[c] / hr[c]), 1e-9);
+      hthr[c] = tau * tau * hr[c];
+    }
+    iters += inner_pcg(h, W, hthr, maxit - iters);
+    launch_dd_add(N, nr, W.xh.as<double>(), W.xl.as<double>(), W.D.as<double>(), st);
+    launch_dd_residual(h->gi, h->a_stag.as<double>(), h->bnode.as<double>(), f.as<double>(),
+                       W.xh.as<double>(), W.xl.as<double>(), W.R.as<double>(), nr, partials, counter,
+                       W.rn2, st);
+    CU(cudaMemcpyAsync(hr.data(), W.rn2, sizeof(double) * nr, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    ++outer;
+  }
+  // residual of the FP64-rounded iterate (x_lo dropped)
+  CU(cudaMemsetAsync(W.D.p, 0, vb, st));
+  launch_dd_residual(h->gi, h->a_stag.as<double>(), h->bnode.as<double>(), f.as<double>(),
+                     W.xh.as<double>(), W.D.as<double>(), W.Q.as<double>(), nr, partials, counter,
+                     W.rn2, st);
+  std::vector<double> h64(nr);
+  CU(cudaMemcpyAsync(h64.data(), W.rn2, sizeof(double) * nr, cudaMemcpyDeviceToHost, st));
+  CU(cudaMemcpyAsync(x, W.xh.p, vb, cudaMemcpyDeviceToDevice, st));
+  if (xlo) CU(cudaMemcpyAsync(xlo, W.xl.p, vb, cudaMemcpyDeviceToDevice, st));
+  CU(cudaStreamSynchronize(st));
+  double rel64 = 0.0;
+  for (int c = 0; c < nr; ++c) rel64 = std::max(rel64, hb[c] > 0 ? std::sqrt(h64[c] / hb[c]) : 0.0);
+  if (info) {
+    info->iters = std::max(info->iters, iters);
+    info->outer = std::max(info->outer, outer);
+    info->converged = info->converged && converged;
+    info->relres_max = std::max(info->relres_max, relmax);
+    info->relres_fp64_max = std::max(info->relres_fp64_max, rel64);
+  }
+  return converged ? HIF_OK : HIF_ERR_NOCONV;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char* hif_last_error(void) { return g_last_error.c_str(); }
+
+static int set_error(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+int hif_factor(const hif_grid* grid, const double* a_stag, const double* b, const double* bc_vals,
+               double eps, const hif_opts* opts, hif_handle** out) {
+  if (!out) return set_error(HIF_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!grid || !a_stag || !b) return set_error(HIF_ERR_ARG, "grid, a_stag and b are required");
+  if (grid->dim != 2 && grid->dim != 3) return set_error(HIF_ERR_ARG, "dim must be 2 or 3");
+  if (grid->n < 4 || grid->n > 1 << 15) return set_error(HIF_ERR_ARG, "n out of range");
+  if (grid->variant != HIF_VARIANT_MF && grid->variant != HIF_VARIANT_HIFDE)
+    return set_error(HIF_ERR_ARG, "unknown variant");
+  if (bc_vals) return set_error(HIF_ERR_ARG, "only zero Dirichlet data (bc_vals = NULL) is supported");
+  if (grid->variant == HIF_VARIANT_HIFDE && !(eps > 0.0 && eps < 1.0))
+    return set_error(HIF_ERR_ARG, "eps must be in (0, 1) for HIF-DE");
+  const int prec = opts ? opts->precision : HIF_PREC_FP64;
+  if (prec != HIF_PREC_FP64 && prec != HIF_PREC_MIXED) return set_error(HIF_ERR_ARG, "unknown precision");
+  const int leaf = grid->leaf > 0 ? grid->leaf : 8;
+  if (leaf < 2) return set_error(HIF_ERR_ARG, "leaf must be >= 2");
+  hif_handle* h = new hif_handle();
+  try {
+    h->G.init(grid->dim, grid->n, leaf);
+    if ((int64_t)h->G.N > (int64_t)0x7fffffff) throw HifError(HIF_ERR_ARG, "grid too large");
+    h->gi.dim = grid->dim;
+    h->gi.n = grid->n;
+    h->gi.m = grid->n - 1;
+    h->gi.inv_h2 = (double)grid->n * (double)grid->n;
+    h->precision = prec;
+    h->variant = grid->variant;
+    h->eps = grid->variant == HIF_VARIANT_HIFDE ? eps : 0.0;
+    h->skip_levels = opts ? std::max(0, opts->skip_levels) : 0;
+    h->st = opts ? (cudaStream_t)opts->stream : nullptr;
+    const int64_t na = (int64_t)grid->n * h->G.N / (grid->n - 1) * grid->dim;
+    h->a_stag.alloc(sizeof(double) * na, h->st);
+    h->bnode.alloc(sizeof(double) * h->G.N, h->st);
+    CU(cudaMemcpyAsync(h->a_stag.p, a_stag, sizeof(double) * na, cudaMemcpyDefault, h->st));
+    CU(cudaMemcpyAsync(h->bnode.p, b, sizeof(double) * h->G.N, cudaMemcpyDefault, h->st));
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    CU(cudaEventRecord(e0, h->st));
+    if (prec == HIF_PREC_MIXED) {
+      Factorizer<float> f(h);
+      f.run();
+    } else {
+      Factorizer<double> f(h);
+      f.run();
+    }
+    CU(cudaEventRecord(e1, h->st));
+    CU(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    h->t_factor_ms = ms;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  } catch (const HifError& e) {
+    delete h;
+    return set_error(e.code, e.msg);
+  } catch (const std::bad_alloc&) {
+    delete h;
+    return set_error(HIF_ERR_OOM, "host allocation failed");
+  }
+  *out = h;
+  g_last_error.clear();
+  return HIF_OK;
+}
+
+int hif_apply(hif_handle* h, int mode, const double* x, double* y, int nrhs, int ld) {
+  if (!h || !x || !y) return set_error(HIF_ERR_ARG, "NULL argument");
+  if (mode != HIF_APPLY_F && mode != HIF_APPLY_FINV) return set_error(HIF_ERR_ARG, "bad mode");
+  if (nrhs < 1 || ld < nrhs) return set_error(HIF_ERR_ARG, "need 1 <= nrhs <= ld");
+  try {
+    const int64_t N = h->G.N;
+    cudaStream_t st = h->st;
+    DevBuf w, tmp, wf;
+    w.alloc(sizeof(double) * N * nrhs, st);
+    stage_in(x, nrhs, ld, N, w.as<double>(), st, tmp);
+    if (h->precision == HIF_PREC_MIXED) {
+      wf.alloc(sizeof(float) * N * nrhs, st);
+      launch_convert<double, float>(N, nrhs, w.as<double>(), nrhs, wf.as<float>(), nrhs, st);
+      run_apply<float>(h, mode, wf.as<float>(), nrhs);
+      launch_convert<float, double>(N, nrhs, wf.as<float>(), nrhs, w.as<double>(), nrhs, st);
+    } else {
+      run_apply<double>(h, mode, w.as<double>(), nrhs);
+    }
+    stage_out(w.as<double>(), nrhs, ld, N, y, st, tmp);
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(st));
+  } catch (const HifError& e) {
+    return set_error(e.code, e.msg);
+  }
+  return HIF_OK;
+}
+
+int hif_matvec(hif_handle* h, const double* x, double* y, int nrhs, int ld) {
+  if (!h || !x || !y) return set_error(HIF_ERR_ARG, "NULL argument");
+  if (nrhs < 1 || ld < nrhs || nrhs > 32) return set_error(HIF_ERR_ARG, "need 1 <= nrhs <= min(ld, 32)");
+  try {
+    const int64_t N = h->G.N;
+    cudaStream_t st = h->st;
+    DevBuf w, v, tmp;
+    w.alloc(sizeof(double) * N * nrhs, st);
+    v.alloc(sizeof(double) * N * nrhs, st);
+    stage_in(x, nrhs, ld, N, w.as<double>(), st, tmp);
+    launch_matvec(h->gi, h->a_stag.as<double>(), h->bnode.as<double>(), w.as<double>(), nrhs,
+                  v.as<double>(), nrhs, nrhs, st);
+    stage_out(v.as<double>(), nrhs, ld, N, y, st, tmp);
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(st));
+  } catch (const HifError& e) {
+    return set_error(e.code, e.msg);
+  }
+  return HIF_OK;
+}
+
+int hif_solve(hif_handle* h, const double* rhs, double* x, double* x_lo, int nrhs, int ld, double tol,
+              int maxit, hif_solve_info* info) {
+  if (!h || !rhs || !x) return set_error(HIF_ERR_ARG, "NULL argument");
+  if (nrhs < 1 || ld < nrhs) return set_error(HIF_ERR_ARG, "need 1 <= nrhs <= ld");
+  if (!(tol > 0.0) || maxit < 0) return set_error(HIF_ERR_ARG, "need tol > 0 and maxit >= 0");
+  hif_solve_info loc{0, 0, 1, 0.0, 0.0};
+  int rc = HIF_OK;
+  try {
+    const int64_t N = h->G.N;
+    cudaStream_t st = h->st;
+    DevBuf pin, pout, plo, tmp;
+    for (int r0 = 0; r0 < nrhs; r0 += 32) {
+      const int nr = std::min(32, nrhs - r0);
+      pin.alloc(sizeof(double) * N * nr, st);
+      pout.alloc(sizeof(double) * N * nr, st);
+      if (x_lo) plo.alloc(sizeof(double) * N * nr, st);
+      stage_in(rhs + r0, nr, ld, N, pin.as<double>(), st, tmp);
+      const int rci = solve_chunk(h, pin.as<double>(), pout.as<double>(), x_lo ? plo.as<double>() : nullptr,
+                                  nr, tol, maxit, &loc);
+      if (rci != HIF_OK) rc = rci;
+      stage_out(pout.as<double>(), nr, ld, N, x + r0, st, tmp);
+      if (x_lo) stage_out(plo.as<double>(), nr, ld, N, x_lo + r0, st, tmp);
+    }
+    CU(cudaStreamSynchronize(st));
+  } catch (const HifError& e) {
+    return set_error(e.code, e.msg);
+  }
+  if (info) *info = loc;
+  if (rc == HIF_ERR_NOCONV) set_error(rc, "CG reached maxit before tol");
+  return rc;
+}
+
+int hif_stats(const hif_handle* h, hif_stats_t* s) {
+  if (!h || !s) return set_error(HIF_ERR_ARG, "NULL argument");
+  s->dim = h->G.dim;
+  s->n = h->G.n;
+  s->levels = h->G.L;
+  s->root_size = h->root_size;
+  s->n_cells = h->n_cells;
+  s->n_fronts = h->n_fronts;
+  s->max_front_rank = h->max_rank;
+  s->near_threshold_fronts = h->near;
+  s->clamped_pivots = h->clamped;
+  s->factor_bytes = h->factor_bytes;
+  s->factor_flops = h->factor_flops;
+  s->apply_bytes = h->apply_bytes;
+  s->t_factor_ms = h->t_factor_ms;
+  return HIF_OK;
+}
+
+int hif_structure(const hif_handle* h, int32_t* buf, long long cap, long long* needed) {
+  if (!h) return set_error(HIF_ERR_ARG, "NULL handle");
+  long long need = 2;
+  for (const FrontInfo& f : h->finfo) need += 3 + (long long)f.c.size() + (long long)f.sk.size();
+  if (needed) *needed = need;
+  if (!buf || cap < need) return HIF_OK;
+  long long p = 0;
+  for (const FrontInfo& f : h->finfo) {
+    buf[p++] = f.level;
+    buf[p++] = (int32_t)f.c.size();
+    buf[p++] = (int32_t)f.sk.size();
+    for (int g : f.c) buf[p++] = g;
+    for (int g : f.sk) buf[p++] = g;
+  }
+  buf[p++] = -1;
+  buf[p++] = h->root_size;
+  return HIF_OK;
+}
+
+void hif_free(hif_handle* h) {
+  if (!h) return;
+  cudaStream_t st = h->st;
+  delete h;
+  cudaStreamSynchronize(st);
+}
+
+}  // extern "C"

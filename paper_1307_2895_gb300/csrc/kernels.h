@@ -1,0 +1,54 @@
+// Host-side launchers of the device kernels.
+#pragma once
+#include "hif_internal.h"
+
+namespace hif {
+
+// factorization (kernels_factor.cu)
+template <typename T>
+void launch_leaf_assemble(const CellDesc* cells, int ncells, const int* ipool, T* work, GridInfo g,
+                          const double* a_stag, const double* bnode, const int* cls, int ncell_axis,
+                          cudaStream_t st);
+template <typename TU, typename TF>
+void launch_extend_add(const CellDesc* cells, int ncells, const int* ipool, TF* work,
+                       const CellDesc* pcells, const TU* pwork, int nchild, cudaStream_t st);
+template <typename T>
+void launch_cell_factor(const CellDesc* cells, int ncells, T* work, T* fac, int* status, int max_nI,
+                        double tau, cudaStream_t st);
+template <typename T>
+void launch_front(const FrontDesc* fronts, int nfronts, const CellDesc* cells, int* ipool, T* fwork,
+                  T* fac, T* cwork, double eps, int* status, int max_nc, int max_nN, double tau,
+                  cudaStream_t st);
+
+// apply sweeps (kernels_apply.cu); op: 0 up, 1 down, 2 fwd_up, 3 fwd_down
+template <typename T>
+void launch_sweep(int op, const ApplyDesc* blocks, int nblocks, const int* ipool, const T* fac, T* x,
+                  int nrhs, int ldx, int is_front, int max_np, int max_nq, cudaStream_t st);
+
+// stencil operator and CG vector operations (kernels_solve.cu)
+void launch_matvec(GridInfo g, const double* a_stag, const double* b, const double* x, int ldx,
+                   double* y, int ldy, int nr, cudaStream_t st);
+void launch_mv_dot(GridInfo g, const double* a_stag, const double* b, const double* p, double* q,
+                   int nr, double* partials, unsigned* counter, double* pq, cudaStream_t st);
+void launch_axpy2(int64_t N, int nr, double* x, double* r, const double* p, const double* q,
+                  const double* rz, const double* pq, const int* active, double* alpha,
+                  double* partials, unsigned* counter, double* rr, cudaStream_t st);
+void launch_dot2(int64_t N, int nr, const double* r, const double* z, const double* q,
+                 double* partials, unsigned* counter, double* out, cudaStream_t st);
+void launch_update_p(int64_t N, int nr, double* p, const double* z, const double* alpha,
+                     const double* rz_old, const double* rzzq, const int* active, int restart,
+                     cudaStream_t st);
+void launch_residual(GridInfo g, const double* a_stag, const double* bn, const double* rhs,
+                     const double* x, double* out, int nr, double* partials, unsigned* counter,
+                     double* nrm2, cudaStream_t st);
+void launch_sqnorm(int64_t N, int nr, const double* v, double* partials, unsigned* counter,
+                   double* out, cudaStream_t st);
+void launch_dd_residual(GridInfo g, const double* a_stag, const double* bn, const double* f,
+                        const double* xh, const double* xl, double* r, int nr, double* partials,
+                        unsigned* counter, double* nrm2, cudaStream_t st);
+void launch_dd_add(int64_t N, int nr, double* xh, double* xl, const double* d, cudaStream_t st);
+void launch_set_active(int nr, const double* rr, const double* thr2, int* active, cudaStream_t st);
+template <typename TI, typename TO>
+void launch_convert(int64_t N, int nr, const TI* in, int ldi, TO* out, int ldo, cudaStream_t st);
+
+}  // namespace hif

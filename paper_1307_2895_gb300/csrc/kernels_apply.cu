@@ -1,0 +1,359 @@
+// Apply sweeps of the factorization (Eq. 3.1 / 4.2).  One thread block per
+// block of the factor (cell or front) of one level; the right-hand sides are
+// processed R at a time.  Vectors: N x nrhs row-major, row stride ldx.
+//
+// F^-1 = V_0 V_1/2 ... D^-1 ... V_1/2^T V_0^T, per block (p eliminated,
+// q its neighbours; fronts carry T, cells do not):
+//   up   (V^T):  [front] x_p -= T^T x_q;  y_p = Linv x_p;  x_q -= G y_p
+//   down (V):    x_p = Linv^T (x_p - G^T x_q);  [front] x_q -= T x_p
+// F = V_0^-T ... D ... V_0^-1:
+//   fwd_up   (V^-1):  [front] x_q += T x_p;  x_p = L^T x_p + G^T x_q
+//   fwd_down (V^-T):  x_q += G x_p;  x_p = L x_p;  [front] x_p += T^T x_q
+// Cells of one level share boundary DOFs, so their x_q updates use atomics;
+// the DOFs of a front belong to it alone.
+#include "hif_internal.h"
+#include "blockops.cuh"
+#include "kernels.h"
+
+namespace hif {
+
+template <typename T, int R>
+__device__ __forceinline__ void gather(T* dst, const T* x, const int* ids, int n, int nr, int ldx) {
+  for (int e = threadIdx.x; e < n * R; e += blockDim.x) {
+    const int i = e / R, r = e % R;
+    dst[e] = (r < nr) ? x[(int64_t)ids[i] * ldx + r] : T(0);
+  }
+}
+
+template <typename T, int R>
+__global__ void k_apply_up(const ApplyDesc* __restrict__ blocks, const int* __restrict__ ipool,
+                           const T* __restrict__ fac, T* __restrict__ x, int nr, int ldx,
+                           int is_front) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const ApplyDesc bd = blocks[blockIdx.x];
+  const int np = bd.np, nq = bd.nq;
+  if (np == 0) return;
+  const int* idp = ipool + bd.ids;
+  const int* idq = idp + np;
+  T* xp = reinterpret_cast<T*>(smem_raw);
+  T* yp = xp + np * R;
+  T* xq = yp + np * R;
+  const T* Linv = fac + bd.Linv;
+  const T* G = fac + bd.G;
+  gather<T, R>(xp, x, idp, np, nr, ldx);
+  if (is_front) gather<T, R>(xq, x, idq, nq, nr, ldx);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  if (is_front && nq > 0) {
+    const T* Tm = fac + bd.T;            // nq x np
+    for (int i = threadIdx.x; i < np; i += blockDim.x) {
+      T acc[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc[r] = T(0);
+      for (int s = 0; s < nq; ++s) {
+        const T t = Tm[(int64_t)s * np + i];
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] += t * xq[s * R + r];
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) xp[i * R + r] -= acc[r];
+    }
+    __syncthreads();
+  }
+  // y_p = Linv x_p  (warp per row)
+  for (int i = warp; i < np; i += nw) {
+    const T* l = Linv + (int64_t)i * np;
+    T acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = T(0);
+    for (int t = lane; t <= i; t += 32) {
+      const T lv = l[t];
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc[r] += lv * xp[t * R + r];
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = warp_sum(acc[r]);
+    if (lane < R) {
+      T val = acc[0];
+#pragma unroll
+      for (int r = 1; r < R; ++r) if (lane == r) val = acc[r];
+      yp[i * R + lane] = val;
+      if (lane < nr) x[(int64_t)idp[i] * ldx + lane] = val;
+    }
+  }
+  __syncthreads();
+  // x_q -= G y_p  (warp per row)
+  for (int s = warp; s < nq; s += nw) {
+    const T* g = G + (int64_t)s * np;
+    T acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = T(0);
+    for (int t = lane; t < np; t += 32) {
+      const T gv = g[t];
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc[r] += gv * yp[t * R + r];
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = warp_sum(acc[r]);
+    if (lane < nr) {
+      T val = acc[0];
+#pragma unroll
+      for (int r = 1; r < R; ++r) if (lane == r) val = acc[r];
+      T* dst = x + (int64_t)idq[s] * ldx + lane;
+      if (is_front) *dst = xq[s * R + lane] - val;
+      else atomicAdd(dst, -val);
+    }
+  }
+}
+
+template <typename T, int R>
+__global__ void k_apply_down(const ApplyDesc* __restrict__ blocks, const int* __restrict__ ipool,
+                             const T* __restrict__ fac, T* __restrict__ x, int nr, int ldx,
+                             int is_front) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const ApplyDesc bd = blocks[blockIdx.x];
+  const int np = bd.np, nq = bd.nq;
+  if (np == 0) return;
+  const int* idp = ipool + bd.ids;
+  const int* idq = idp + np;
+  T* xp = reinterpret_cast<T*>(smem_raw);
+  T* zp = xp + np * R;
+  T* xq = zp + np * R;
+  const T* Linv = fac + bd.Linv;
+  const T* G = fac + bd.G;
+  gather<T, R>(xp, x, idp, np, nr, ldx);
+  gather<T, R>(xq, x, idq, nq, nr, ldx);
+  __syncthreads();
+  // w = x_p - G^T x_q  (thread per column, in place on xp)
+  if (nq > 0) {
+    for (int i = threadIdx.x; i < np; i += blockDim.x) {
+      T acc[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc[r] = T(0);
+      for (int s = 0; s < nq; ++s) {
+        const T gv = G[(int64_t)s * np + i];
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] += gv * xq[s * R + r];
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) xp[i * R + r] -= acc[r];
+    }
+    __syncthreads();
+  }
+  // z = Linv^T w (thread per column)
+  for (int i = threadIdx.x; i < np; i += blockDim.x) {
+    T acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = T(0);
+    for (int t = i; t < np; ++t) {
+      const T lv = Linv[(int64_t)t * np + i];
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc[r] += lv * xp[t * R + r];
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      zp[i * R + r] = acc[r];
+      if (r < nr) x[(int64_t)idp[i] * ldx + r] = acc[r];
+    }
+  }
+  __syncthreads();
+  if (is_front && nq > 0) {
+    const T* Tm = fac + bd.T;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int s = warp; s < nq; s += nw) {
+      const T* t = Tm + (int64_t)s * np;
+      T acc[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc[r] = T(0);
+      for (int c = lane; c < np; c += 32) {
+        const T tv = t[c];
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] += tv * zp[c * R + r];
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc[r] = warp_sum(acc[r]);
+      if (lane < nr) {
+        T val = acc[0];
+#pragma unroll
+        for (int r = 1; r < R; ++r) if (lane == r) val = acc[r];
+        x[(int64_t)idq[s] * ldx + lane] = xq[s * R + lane] - val;
+      }
+    }
+  }
+}
+
+// ---- forward operator F (used by the error estimates) ----------------------
+template <typename T, int R>
+__global__ void k_fwd_up(const ApplyDesc* __restrict__ blocks, const int* __restrict__ ipool,
+                         const T* __restrict__ fac, T* __restrict__ x, int nr, int ldx, int is_front) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const ApplyDesc bd = blocks[blockIdx.x];
+  const int np = bd.np, nq = bd.nq;
+  if (np == 0) return;
+  const int* idp = ipool + bd.ids;
+  const int* idq = idp + np;
+  T* xp = reinterpret_cast<T*>(smem_raw);
+  T* xq = xp + np * R;
+  const T* Lf = fac + bd.L;
+  const T* G = fac + bd.G;
+  gather<T, R>(xp, x, idp, np, nr, ldx);
+  gather<T, R>(xq, x, idq, nq, nr, ldx);
+  __syncthreads();
+  if (is_front && nq > 0) {       // x_q += T x_p
+    const T* Tm = fac + bd.T;
+    for (int s = threadIdx.x; s < nq; s += blockDim.x) {
+      T acc[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc[r] = T(0);
+      for (int c = 0; c < np; ++c) {
+        const T tv = Tm[(int64_t)s * np + c];
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] += tv * xp[c * R + r];
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        xq[s * R + r] += acc[r];
+        if (r < nr) x[(int64_t)idq[s] * ldx + r] = xq[s * R + r];
+      }
+    }
+    __syncthreads();
+  }
+  // x_p = L^T x_p + G^T x_q
+  for (int i = threadIdx.x; i < np; i += blockDim.x) {
+    T acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = T(0);
+    for (int t = i; t < np; ++t) {
+      const T lv = Lf[(int64_t)t * np + i];
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc[r] += lv * xp[t * R + r];
+    }
+    for (int s = 0; s < nq; ++s) {
+      const T gv = G[(int64_t)s * np + i];
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc[r] += gv * xq[s * R + r];
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      if (r < nr) x[(int64_t)idp[i] * ldx + r] = acc[r];
+  }
+}
+
+template <typename T, int R>
+__global__ void k_fwd_down(const ApplyDesc* __restrict__ blocks, const int* __restrict__ ipool,
+                           const T* __restrict__ fac, T* __restrict__ x, int nr, int ldx, int is_front) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const ApplyDesc bd = blocks[blockIdx.x];
+  const int np = bd.np, nq = bd.nq;
+  if (np == 0) return;
+  const int* idp = ipool + bd.ids;
+  const int* idq = idp + np;
+  T* xp = reinterpret_cast<T*>(smem_raw);
+  T* xq = xp + np * R;
+  const T* Lf = fac + bd.L;
+  const T* G = fac + bd.G;
+  gather<T, R>(xp, x, idp, np, nr, ldx);
+  if (is_front) gather<T, R>(xq, x, idq, nq, nr, ldx);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  // x_q += G x_p
+  for (int s = warp; s < nq; s += nw) {
+    const T* g = G + (int64_t)s * np;
+    T acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = T(0);
+    for (int c = lane; c < np; c += 32) {
+      const T gv = g[c];
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc[r] += gv * xp[c * R + r];
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = warp_sum(acc[r]);
+    if (lane < R) {
+      T val = acc[0];
+#pragma unroll
+      for (int r = 1; r < R; ++r) if (lane == r) val = acc[r];
+      if (is_front) {
+        xq[s * R + lane] += val;
+        if (lane < nr) x[(int64_t)idq[s] * ldx + lane] = xq[s * R + lane];
+      } else if (lane < nr) {
+        atomicAdd(x + (int64_t)idq[s] * ldx + lane, val);
+      }
+    }
+  }
+  __syncthreads();
+  // x_p = L x_p [+ T^T x_q]
+  for (int i = threadIdx.x; i < np; i += blockDim.x) {
+    T acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = T(0);
+    const T* l = Lf + (int64_t)i * np;
+    for (int t = 0; t <= i; ++t) {
+      const T lv = l[t];
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc[r] += lv * xp[t * R + r];
+    }
+    if (is_front) {
+      const T* Tm = fac + bd.T;
+      for (int s = 0; s < nq; ++s) {
+        const T tv = Tm[(int64_t)s * np + i];
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] += tv * xq[s * R + r];
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      if (r < nr) x[(int64_t)idp[i] * ldx + r] = acc[r];
+  }
+}
+
+// ---------------------------------------------------------------------------
+template <typename T, int R>
+static void launch_sweep_R(int op, const ApplyDesc* blocks, int nblocks, const int* ipool,
+                           const T* fac, T* x, int nr, int ldx, int is_front, int max_np,
+                           int max_nq, cudaStream_t st) {
+  const size_t smem = sizeof(T) * R * (size_t)(2 * max_np + max_nq);
+  void (*fn)(const ApplyDesc*, const int*, const T*, T*, int, int, int) = nullptr;
+  switch (op) {
+    case 0: fn = k_apply_up<T, R>; break;
+    case 1: fn = k_apply_down<T, R>; break;
+    case 2: fn = k_fwd_up<T, R>; break;
+    default: fn = k_fwd_down<T, R>; break;
+  }
+  if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  fn<<<nblocks, 256, smem, st>>>(blocks, ipool, fac, x, nr, ldx, is_front);
+}
+
+template <typename T>
+int sweep_chunk(int max_np, int max_nq, int nrhs) {
+  const size_t cap = 200 * 1024;
+  int R = 32;
+  while (R > 1 && (R / 2 >= nrhs || sizeof(T) * R * (size_t)(2 * max_np + max_nq) > cap)) R /= 2;
+  return R;
+}
+
+template <typename T>
+void launch_sweep(int op, const ApplyDesc* blocks, int nblocks, const int* ipool, const T* fac,
+                  T* x, int nrhs, int ldx, int is_front, int max_np, int max_nq, cudaStream_t st) {
+  if (nblocks == 0) return;
+  const int R = sweep_chunk<T>(max_np, max_nq, nrhs);
+  for (int r0 = 0; r0 < nrhs; r0 += R) {
+    const int nr = (nrhs - r0) < R ? (nrhs - r0) : R;
+    T* xr = x + r0;
+    switch (R) {
+      case 32: launch_sweep_R<T, 32>(op, blocks, nblocks, ipool, fac, xr, nr, ldx, is_front, max_np, max_nq, st); break;
+      case 16: launch_sweep_R<T, 16>(op, blocks, nblocks, ipool, fac, xr, nr, ldx, is_front, max_np, max_nq, st); break;
+      case 8: launch_sweep_R<T, 8>(op, blocks, nblocks, ipool, fac, xr, nr, ldx, is_front, max_np, max_nq, st); break;
+      case 4: launch_sweep_R<T, 4>(op, blocks, nblocks, ipool, fac, xr, nr, ldx, is_front, max_np, max_nq, st); break;
+      case 2: launch_sweep_R<T, 2>(op, blocks, nblocks, ipool, fac, xr, nr, ldx, is_front, max_np, max_nq, st); break;
+      default: launch_sweep_R<T, 1>(op, blocks, nblocks, ipool, fac, xr, nr, ldx, is_front, max_np, max_nq, st); break;
+    }
+  }
+}
+
+template void launch_sweep<double>(int, const ApplyDesc*, int, const int*, const double*, double*,
+                                   int, int, int, int, int, cudaStream_t);
+template void launch_sweep<float>(int, const ApplyDesc*, int, const int*, const float*, float*,
+                                  int, int, int, int, int, cudaStream_t);
+
+}  // namespace hif

@@ -1,0 +1,228 @@
+"""Python binding of the C ABI in ``include/hif.h`` (argument marshalling only).
+
+Every step of the factorization, the apply and the CG solve runs in the CUDA
+library ``_lib/libhif.so``; this module only converts arguments.  Arrays may
+be numpy arrays (host memory) or torch tensors (host or CUDA); results come
+back in the same kind of container as the input vector.  There is no CPU
+fallback: if the library is missing, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+HIF_OK, HIF_ERR_ARG, HIF_ERR_NOT_SPD, HIF_ERR_NOCONV, HIF_ERR_TIMEOUT, HIF_ERR_CUDA, HIF_ERR_OOM = range(7)
+VARIANTS = {"mf": 0, "hifde": 1}
+PRECISIONS = {"fp64": 0, "mixed": 1}
+APPLY_F, APPLY_FINV = 0, 1
+
+
+class HifError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"hif error {code}: {msg}")
+        self.code = code
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int), ("leaf", ctypes.c_int), ("variant", ctypes.c_int)]
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("skip_levels", ctypes.c_int), ("reserved0", ctypes.c_int),
+                ("reserved1", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class _SolveInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("outer", ctypes.c_int), ("converged", ctypes.c_int),
+                ("relres_max", ctypes.c_double), ("relres_fp64_max", ctypes.c_double)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int), ("levels", ctypes.c_int),
+                ("root_size", ctypes.c_int), ("n_cells", ctypes.c_int), ("n_fronts", ctypes.c_int),
+                ("max_front_rank", ctypes.c_int), ("near_threshold_fronts", ctypes.c_int),
+                ("clamped_pivots", ctypes.c_int),
+                ("factor_bytes", ctypes.c_longlong), ("factor_flops", ctypes.c_double),
+                ("apply_bytes", ctypes.c_double), ("t_factor_ms", ctypes.c_double)]
+
+
+_LIB = None
+EXPORTS = ["hif_factor", "hif_apply", "hif_solve", "hif_matvec", "hif_stats", "hif_structure",
+           "hif_free", "hif_last_error"]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load ``libhif.so`` (raises if it is not built)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"{path} is missing: build it with paper_1307_2895_gb300.build.build()")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    lib.hif_factor.argtypes = [ctypes.POINTER(_Grid), vp, vp, vp, d, ctypes.POINTER(_Opts), ctypes.POINTER(vp)]
+    lib.hif_factor.restype = i
+    lib.hif_apply.argtypes = [vp, i, vp, vp, i, i]
+    lib.hif_apply.restype = i
+    lib.hif_solve.argtypes = [vp, vp, vp, vp, i, i, d, i, ctypes.POINTER(_SolveInfo)]
+    lib.hif_solve.restype = i
+    lib.hif_matvec.argtypes = [vp, vp, vp, i, i]
+    lib.hif_matvec.restype = i
+    lib.hif_stats.argtypes = [vp, ctypes.POINTER(_Stats)]
+    lib.hif_stats.restype = i
+    lib.hif_structure.argtypes = [vp, vp, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)]
+    lib.hif_structure.restype = i
+    lib.hif_free.argtypes = [vp]
+    lib.hif_free.restype = None
+    lib.hif_last_error.argtypes = []
+    lib.hif_last_error.restype = ctypes.c_char_p
+    _LIB = lib
+    return lib
+
+
+def _check(rc: int, lib) -> None:
+    if rc != HIF_OK:
+        raise HifError(rc, lib.hif_last_error().decode())
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    """Raw address of a contiguous float64 numpy array or torch tensor."""
+    if x is None:
+        return None
+    if _is_torch(x):
+        import torch
+        if x.dtype != torch.float64 or not x.is_contiguous():
+            raise TypeError("tensors must be contiguous float64")
+        return x.data_ptr()
+    if x.dtype != np.float64 or not x.flags["C_CONTIGUOUS"]:
+        raise TypeError("arrays must be C-contiguous float64")
+    return x.ctypes.data
+
+
+def _as_2d(x):
+    return x.reshape(x.shape[0], -1)
+
+
+def _empty_like(x, shape):
+    if _is_torch(x):
+        import torch
+        return torch.empty(shape, dtype=torch.float64, device=x.device)
+    return np.empty(shape, dtype=np.float64)
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+class Factorization:
+    """Handle of one factorization (``hif_factor``); free with :meth:`free`."""
+
+    def __init__(self, handle, lib, N: int):
+        self._h = handle
+        self._lib = lib
+        self.N = N
+
+    def _live(self):
+        if not self._h:
+            raise RuntimeError("factorization already freed")
+        return self._h
+
+    def apply(self, x, inverse: bool = True):
+        """y = F^-1 x (inverse=True) or F x; x has shape (N,) or (N, nrhs)."""
+        x2 = _as_2d(x)
+        y = _empty_like(x, x2.shape)
+        rc = self._lib.hif_apply(self._live(), APPLY_FINV if inverse else APPLY_F, _ptr(x2), _ptr(y),
+                                 x2.shape[1], x2.shape[1])
+        _check(rc, self._lib)
+        return y.reshape(x.shape)
+
+    def matvec(self, x):
+        x2 = _as_2d(x)
+        y = _empty_like(x, x2.shape)
+        _check(self._lib.hif_matvec(self._live(), _ptr(x2), _ptr(y), x2.shape[1], x2.shape[1]), self._lib)
+        return y.reshape(x.shape)
+
+    def solve(self, rhs, tol: float = 1e-12, maxit: int = 200, raise_on_noconv: bool = False,
+              want_lo: bool = False):
+        """PCG with F^-1 as preconditioner (double-double refinement); returns
+        (x, info dict) or (x_hi, x_lo, info) with ``want_lo``."""
+        r2 = _as_2d(rhs)
+        x = _empty_like(rhs, r2.shape)
+        xlo = _empty_like(rhs, r2.shape) if want_lo else None
+        info = _SolveInfo()
+        rc = self._lib.hif_solve(self._live(), _ptr(r2), _ptr(x), _ptr(xlo), r2.shape[1], r2.shape[1], tol,
+                                 maxit, ctypes.byref(info))
+        if rc != HIF_ERR_NOCONV or raise_on_noconv:
+            _check(rc, self._lib)
+        d = dict(iters=info.iters, outer=info.outer, converged=bool(info.converged),
+                 relres_max=info.relres_max, relres_fp64_max=info.relres_fp64_max)
+        if want_lo:
+            return x.reshape(rhs.shape), xlo.reshape(rhs.shape), d
+        return x.reshape(rhs.shape), d
+
+    def stats(self) -> dict:
+        s = _Stats()
+        _check(self._lib.hif_stats(self._live(), ctypes.byref(s)), self._lib)
+        return {name: getattr(s, name) for name, _ in _Stats._fields_}
+
+    def structure(self):
+        """[(level, c, skeletons in pivot order)], |s_L|."""
+        need = ctypes.c_longlong(0)
+        _check(self._lib.hif_structure(self._live(), None, 0, ctypes.byref(need)), self._lib)
+        buf = np.zeros(need.value, dtype=np.int32)
+        _check(self._lib.hif_structure(self._live(), buf.ctypes.data, need.value, ctypes.byref(need)),
+               self._lib)
+        out, p = [], 0
+        while buf[p] != -1:
+            lev, nc, k = int(buf[p]), int(buf[p + 1]), int(buf[p + 2])
+            p += 3
+            c = buf[p:p + nc].tolist()
+            p += nc
+            sk = buf[p:p + k].tolist()
+            p += k
+            out.append((lev, c, sk))
+        return out, int(buf[p + 1])
+
+    def free(self) -> None:
+        if self._h:
+            self._lib.hif_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def factor(dim: int, n: int, a_stag, b, eps: float, variant: str = "hifde", precision: str = "fp64",
+           leaf: int = 8, skip_levels: int = 0, stream=None) -> Factorization:
+    """hif_factor: MF or HIF-DE of the stencil operator defined by (a_stag, b)."""
+    lib = load()
+    grid = _Grid(dim, n, leaf, VARIANTS[variant])
+    opts = _Opts(PRECISIONS[precision], skip_levels, 0, 0, _stream_ptr(stream))
+    h = ctypes.c_void_p()
+    rc = lib.hif_factor(ctypes.byref(grid), _ptr(a_stag), _ptr(b), None, float(eps), ctypes.byref(opts),
+                        ctypes.byref(h))
+    _check(rc, lib)
+    return Factorization(h, lib, (n - 1) ** dim)

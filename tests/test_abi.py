@@ -1,0 +1,55 @@
+"""The C-ABI library builds, loads and exports every entry point of
+include/hif.h; argument errors come back as status codes (no GPU needed:
+these calls return before any CUDA work)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1307_2895_gb300 import build, hif
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "hif.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char\*)\s+(hif_\w+)\s*\(", src, re.M)))
+
+
+def test_library_exports_header_symbols():
+    lib = hif.load(build_if_missing=True)
+    names = _declared()
+    assert set(names) == set(hif.EXPORTS)
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_argument_errors_without_gpu():
+    lib = hif.load(build_if_missing=True)
+    a, b = np.ones(2 * 16 * 15), np.zeros(225)
+    h = ctypes.c_void_p()
+    grid = hif._Grid(5, 16, 8, 1)
+    rc = lib.hif_factor(ctypes.byref(grid), a.ctypes.data, b.ctypes.data, None, 1e-6, None, ctypes.byref(h))
+    assert rc == hif.HIF_ERR_ARG and b"dim" in lib.hif_last_error()
+    grid = hif._Grid(2, 16, 8, 1)
+    rc = lib.hif_factor(ctypes.byref(grid), a.ctypes.data, b.ctypes.data, None, 0.0, None, ctypes.byref(h))
+    assert rc == hif.HIF_ERR_ARG and b"eps" in lib.hif_last_error()
+    rc = lib.hif_factor(ctypes.byref(grid), a.ctypes.data, b.ctypes.data, a.ctypes.data, 1e-6, None,
+                        ctypes.byref(h))
+    assert rc == hif.HIF_ERR_ARG
+    assert lib.hif_apply(None, 1, None, None, 1, 1) == hif.HIF_ERR_ARG
+    assert lib.hif_solve(None, None, None, None, 1, 1, 1e-12, 10, None) == hif.HIF_ERR_ARG
+    st = hif._Stats()
+    assert lib.hif_stats(None, ctypes.byref(st)) == hif.HIF_ERR_ARG
+    lib.hif_free(None)
+
+
+def test_product_path_does_not_import_oracle():
+    pkg = os.path.join(ROOT, "paper_1307_2895_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cpp", ".h", ".cuh")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(from|import)\s+oracle", txt, re.M), f
