@@ -1,0 +1,360 @@
+#!/usr/bin/env python
+"""Benchmark: factor + solve DOF/s at relative residual 1e-12 (HIF-DE, GB300).
+
+One step = one pass of the whole hot path on the 2D high-contrast workload
+(511 x 511 interior grid, quantized field of contrast 1e6, b = 1e-3,
+eps = 1e-6, 8 standard-normal right-hand sides): ``hif_factor`` (Algorithm 4.1)
+then ``hif_solve`` (PCG with F^-1 to ||b - A x|| <= 1e-12 ||b|| for every
+column), inputs resident in HBM.  The L2 cache is flushed (256 MB write)
+between timed steps, outside the timed region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.  With N > 1 (torchrun) every
+rank runs an independent replica of the workload (the method has no exchange
+step for one problem on one GPU): value = DOF of all ranks / max rank time.
+"""
+import os
+
+# the CPU oracle legs measure single-threaded numpy; set before numpy loads
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse
+import json
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "factor+solve DOF/s at rel. residual 1e-12: learned/mixed vs plain FP64 GPU"
+WORKLOAD = "2D high-contrast 511x511 (contrast 1e6, b=1e-3), eps=1e-6, 8 RHS, PCG to 1e-12"
+TOL = 1e-12
+ORACLE_SAMPLE_N = 128      # the CPU oracle's bounded sample: same recipe on a 127 x 127 grid
+ORACLE_SAMPLE_TOL = 1e-9   # FP64 CG floor of that sample is ~5e-11 (no double-double in the oracle)
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.samples = []
+        self._stop = threading.Event()
+        self._proc = None
+        self._thr = None
+
+    def start(self):
+        try:
+            self._proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self._proc = None
+            return
+
+        def reader():
+            for line in self._proc.stdout:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    self.samples.append(parts)
+                if self._stop.is_set():
+                    break
+
+        self._thr = threading.Thread(target=reader, daemon=True)
+        self._thr.start()
+
+    def stop(self):
+        self._stop.set()
+        if self._proc is not None:
+            self._proc.terminate()
+            try:
+                self._proc.wait(timeout=5)
+            except Exception:
+                self._proc.kill()
+        if self._thr is not None:
+            self._thr.join(timeout=2)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for s in self.samples:
+            for name, val in zip(names, s[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+def _workload_arrays():
+    from paper_1307_2895_gb300 import inputs
+    w = inputs.workload("contrast2d_n512")
+    f = inputs.rhs(w["dim"], w["n"], w["nrhs"], seed=0)
+    return w, f
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+def oracle_sample_step():
+    """One bounded oracle step: factor + PCG (1 RHS) on the same recipe at n = 128."""
+    from oracle import hifde, stencil
+    from paper_1307_2895_gb300 import inputs
+    n = ORACLE_SAMPLE_N
+    a, _ = inputs.high_contrast_coefficients(2, n, seed=2, low=1e-3, high=1e3)
+    b = np.full((n - 1) ** 2, 1e-3)
+    f = inputs.rhs(2, n, 1, seed=0)
+    A = stencil.assemble(2, n, a, b)
+    t0 = time.perf_counter()
+    F = hifde.factor(A, 2, n, 1e-6)
+    x, iters, rel = hifde.pcg(A, F, f, tol=ORACLE_SAMPLE_TOL, maxit=400)
+    dt = time.perf_counter() - t0
+    return (n - 1) ** 2 * 1, dt, iters[0], rel[0]
+
+
+def cpu_baseline(steps: int = 1):
+    dofs, secs, its, rels = 0, 0.0, [], []
+    for _ in range(steps):
+        d, s, it, rel = oracle_sample_step()
+        dofs += d
+        secs += s
+        its.append(it)
+        rels.append(rel)
+    return {"value": dofs / secs, "unit": "DOF/s", "cores": 1, "kind": "oracle",
+            "sample": f"FP64 numpy oracle, same recipe on a {ORACLE_SAMPLE_N - 1}^2 grid, 1 RHS, factor + PCG "
+                      f"to {ORACLE_SAMPLE_TOL:g} (its FP64 residual floor), {steps} step(s), "
+                      f"{secs:.1f} s, iters {its}, relres {max(rels):.1e}"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        oracle_sample_step()
+    dofs, secs = 0, 0.0
+    for _ in range(args.steps):
+        d, s, _, _ = oracle_sample_step()
+        dofs += d
+        secs += s
+    value = dofs / secs
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD + " (bounded CPU sample)",
+                                            "sample_grid": f"{ORACLE_SAMPLE_N - 1}^2", "nrhs": 1,
+                                            "tol": ORACLE_SAMPLE_TOL},
+            "cpu_baseline": {"value": value, "unit": "DOF/s", "cores": 1, "kind": "oracle",
+                             "sample": f"same recipe on a {ORACLE_SAMPLE_N - 1}^2 grid, 1 RHS, "
+                                       f"factor + PCG to {ORACLE_SAMPLE_TOL:g}"},
+            "e2e": {"value": value, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    from paper_1307_2895_gb300 import hif
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    hif.load()
+    w, f_np = _workload_arrays()
+    dim, n, eps, nrhs = w["dim"], w["n"], w["eps"], w["nrhs"]
+    N = (n - 1) ** dim
+    st = torch.cuda.Stream(device=dev)
+    a = torch.from_numpy(w["a_stag"]).to(dev)
+    b = torch.from_numpy(w["b"]).to(dev)
+    f = torch.from_numpy(f_np).to(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def one_step(precision, profile=False):
+        G = hif.factor(dim, n, a, b, eps, precision=precision, stream=st)
+        try:
+            if profile:
+                G.profile(True)
+            x, info = G.solve(f, tol=TOL, maxit=1000)
+            prof = G.profile(False) if profile else None
+            stats = G.stats()
+        finally:
+            G.free()
+        return info, stats, prof
+
+    def timed(precision, steps, warmup, profile=False):
+        for _ in range(warmup):
+            one_step(precision)
+        torch.cuda.synchronize()
+        ms, infos, profs, stats = [], [], [], None
+        l0 = hif.kernel_launches()
+        for _ in range(steps):
+            with torch.cuda.stream(st):
+                flush.fill_(1.0)
+            torch.cuda.synchronize()
+            barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            info, stats, prof = one_step(precision, profile)
+            e1.record(st)
+            torch.cuda.synchronize()
+            barrier()
+            ms.append(e0.elapsed_time(e1))
+            infos.append(info)
+            profs.append(prof)
+        launches = hif.kernel_launches() - l0
+        return ms, infos, profs, stats, launches
+
+    prec = args.precision
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    ms, infos, profs, stats, launches = timed(prec, args.steps, args.warmup, profile=True)
+    clocks.stop()
+    tot_s = sum(ms) / 1e3
+    tmax = tot_s
+    if world > 1:
+        t = torch.tensor([tot_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tmax = float(t.item())
+    dofs_per_step = N * nrhs
+    value = world * args.steps * dofs_per_step / tmax
+    conv = all(i["converged"] and i["relres_max"] <= TOL for i in infos)
+
+    # roofline of the dominant kernels (apply sweeps of F^-1), live events
+    sweep_ms = sum(p["sweep_ms"] for p in profs)
+    sweep_launches = sum(p["sweep_launches"] for p in profs)
+    sweep_bytes = sum(p["sweep_bytes"] for p in profs)
+    peak, peak_kind = _peaks()
+    achieved = (sweep_bytes / sweep_launches) / (sweep_ms / sweep_launches / 1e3) / 1e9 if sweep_ms > 0 else None
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": (achieved / peak) if achieved else None, "traffic": None,
+            "kernel": "k_apply_up/k_apply_down (F^-1 sweeps)", "peak_kind": peak_kind,
+            "avg_launch_us": 1e3 * sweep_ms / max(sweep_launches, 1),
+            "bytes_per_launch": sweep_bytes / max(sweep_launches, 1),
+            "share_of_step": sweep_ms / sum(ms) if sum(ms) > 0 else None}
+
+    # plain FP64 GPU path on the same workload (the comparison the metric names)
+    plain = None
+    if not args.skip_plain:
+        pms, pinfos, _, _, _ = timed("fp64", max(1, args.steps // 2), 1)
+        ptot = sum(pms) / 1e3
+        plain = {"value": len(pms) * dofs_per_step / ptot, "ms_per_step": 1e3 * ptot / len(pms),
+                 "iters": pinfos[-1]["iters"], "converged": all(i["converged"] for i in pinfos)}
+
+    # end-to-end through the C ABI with host buffers (pinned), copies inside the step
+    e2e = None
+    if not args.skip_e2e:
+        a_h = torch.from_numpy(w["a_stag"]).pin_memory()
+        b_h = torch.from_numpy(w["b"]).pin_memory()
+        f_h = torch.from_numpy(f_np).pin_memory()
+        x_h = torch.empty_like(f_h).pin_memory()
+        e_ms = []
+        for i in range(args.steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            G = hif.factor(dim, n, a_h, b_h, eps, precision=prec, stream=st)
+            try:
+                G.solve(f_h, tol=TOL, maxit=1000, out=x_h)
+            finally:
+                G.free()
+            torch.cuda.synchronize()
+            if i > 0:
+                e_ms.append(1e3 * (time.perf_counter() - t0))
+        e2e = {"value": world * len(e_ms) * dofs_per_step / (sum(e_ms) / 1e3), "unit": "DOF/s",
+               "h2d_bytes_per_step": int(a_h.numel() * 8 + b_h.numel() * 8 + f_h.numel() * 8),
+               "d2h_bytes_per_step": int(x_h.numel() * 8)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        try:
+            cpu = cpu_baseline(1)
+        except Exception as exc:  # the oracle leg must not hide the GPU result
+            cpu = {"error": repr(exc)}
+
+    if rank != 0:
+        return 0
+    last = infos[-1]
+    line = {
+        "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": sum(ms) / len(ms), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": N, "nrhs": nrhs, "eps": eps, "tol": TOL,
+                   "precision": prec, "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "flushed between steps (256 MB write, outside the timed region)",
+                   "arith": "factorization f64; factor stored and applied in f32; CG f64 with a "
+                            "double-double iterate and residual"},
+        "converged": conv, "relres_max": max(i["relres_max"] for i in infos),
+        "cg_iters": last["iters"], "refinement_steps": last["outer"],
+        "t_factor_ms": stats["t_factor_ms"] if stats else None,
+        "root_size": stats["root_size"] if stats else None,
+        "plain_fp64": plain,
+        "speedup_vs_plain_fp64": (value / world / plain["value"]) if plain else None,
+        "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu,
+        "clocks": clocks.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", default="fp32_apply", choices=["fp64", "mixed", "fp32_apply"])
+    ap.add_argument("--skip-plain", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    try:
+        return run_gpu(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -59,8 +59,11 @@ enum { HIF_VARIANT_MF = 0, HIF_VARIANT_HIFDE = 1 };
 /* Arithmetic of the factorization.  FP64: every block operation in double.
  * MIXED: cell and front blocks, the factor and the apply of F^-1 in float;
  * the root block D is factored in double; the ID's column norms and pivot
- * tests are accumulated in double.  The CG driver is double in both. */
-enum { HIF_PREC_FP64 = 0, HIF_PREC_MIXED = 1 };
+ * tests are accumulated in double; diagonal-block Cholesky pivots that fall
+ * into FP32 rounding noise are raised (counted in clamped_pivots).
+ * FP32_APPLY: the factorization runs in double, the factor is then stored and
+ * applied in float.  The CG driver is double(-double) in every mode. */
+enum { HIF_PREC_FP64 = 0, HIF_PREC_MIXED = 1, HIF_PREC_FP32_APPLY = 2 };
 
 /* hif_apply modes (Eq. 4.2): y = F x or y = F^-1 x. */
 enum { HIF_APPLY_F = 0, HIF_APPLY_FINV = 1 };
@@ -158,6 +161,24 @@ int hif_stats(const hif_handle* h, hif_stats_t* st);
  * small, nothing is written; *needed receives the number of int32 required.
  */
 int hif_structure(const hif_handle* h, int32_t* buf, long long cap, long long* needed);
+
+/*
+ * hif_profile -- event timing of the apply sweeps of F^-1 (the kernels that
+ * dominate the solve).  Returns in *out (may be NULL) the summed device time,
+ * launch count and algorithmic bytes (factor blocks read + vector rows
+ * gathered and written) of the sweep launches recorded since the previous
+ * call, resets them, and turns the recording on (enable != 0) or off for
+ * later calls on this handle.
+ */
+typedef struct hif_profile_t {
+  double sweep_ms;
+  long long sweep_launches;
+  double sweep_bytes;
+} hif_profile_t;
+int hif_profile(hif_handle* h, int enable, hif_profile_t* out);
+
+/* hif_kernel_launches -- kernels launched by this library in this process. */
+long long hif_kernel_launches(void);
 
 /* hif_free -- release the factor (stream-ordered on the handle's stream). */
 void hif_free(hif_handle* h);

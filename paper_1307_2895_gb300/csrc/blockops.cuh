@@ -15,10 +15,12 @@ template <> __device__ __forceinline__ float dsqrt<float>(float x) { return sqrt
 // is read; the strict upper triangle is used as scratch (original diagonal).
 // tau == 0: a non-positive or non-finite pivot sets bit 0 of status[0] and is
 // replaced by 1.  tau > 0 (safeguarded form, used when the block carries FP32
-// rounding): a pivot below tau * d0 is raised to tau * d0 and counted in
-// status[1], where d0 is its original diagonal entry (or the largest original
-// diagonal entry of the block when that is not positive), so the factor stays
-// SPD; only a block without a positive finite diagonal sets bit 0.
+// rounding): a pivot below tau * d0 is rounding noise; it is replaced by
+// max(|d|, sqrt(tau) d0), which keeps the factor SPD and bounds the growth of
+// the column below it (|l_ij| <= sqrt(d0_i / sqrt(tau))), and counted in
+// status[1].  d0 is the pivot's original diagonal entry (or the block's
+// largest original diagonal entry when that is not positive); only a block
+// without a positive finite diagonal sets bit 0.
 template <typename T>
 __device__ void blk_cholesky(T* A, int n, int ld, int* status, T tau = T(0)) {
   __shared__ T s_piv, s_dmax;
@@ -46,7 +48,8 @@ __device__ void blk_cholesky(T* A, int n, int ld, int* status, T tau = T(0)) {
           d = T(1);
         } else if (!(d > tau * d0) || !isfinite((double)d)) {
           atomicAdd(status + 1, 1);
-          d = tau * d0;
+          const T floor_d = dsqrt(tau) * d0;
+          d = (isfinite((double)d) && fabs((double)d) > (double)floor_d) ? (T)fabs((double)d) : floor_d;
         }
       } else if (!(d > T(0)) || !isfinite((double)d)) {
         atomicOr(status, 1);

@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -27,6 +28,12 @@
 #include "kernels.h"
 
 using namespace hif;
+
+namespace {
+std::atomic<long long> g_launches{0};
+}  // namespace
+
+void hif::note_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 namespace {
 
@@ -97,6 +104,8 @@ bool is_device_ptr(const void* p) {
 // Apply-side view of one kind of block (cells or fronts) at one level.
 struct SweepLevel {
   int nblocks = 0, max_np = 0, max_nq = 0;
+  double fac_elems = 0.0;   // factor elements one F^-1 sweep reads (Linv lower, G, T)
+  double vec_rows = 0.0;    // vector rows it gathers and writes back (sum of np + nq)
   DevBuf desc;    // ApplyDesc[nblocks]
   DevBuf ipool;   // ids
   DevBuf fac;     // factor pool
@@ -125,6 +134,15 @@ struct hif_handle {
   int root_size = 0, n_cells = 0, n_fronts = 0, max_rank = 0, near = 0, clamped = 0;
   long long factor_bytes = 0;
   double factor_flops = 0.0, apply_bytes = 0.0, t_factor_ms = 0.0;
+  // optional event timing of the F^-1 sweep launches
+  int profile = 0;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  double prof_ms = 0.0, prof_bytes = 0.0;
+  long long prof_launches = 0;
+  ~hif_handle() {
+    for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+  }
 };
 
 namespace {
@@ -188,6 +206,10 @@ void cell_apply_descs(SweepLevel& S, const std::vector<CellDesc>& cd, cudaStream
     ad.push_back(a);
     S.max_np = std::max(S.max_np, c.nI);
     S.max_nq = std::max(S.max_nq, c.nB);
+    if (c.nI > 0) {
+      S.fac_elems += 0.5 * c.nI * (c.nI + 1.0) + (double)c.nB * c.nI;
+      S.vec_rows += c.nI + c.nB;
+    }
   }
   S.nblocks = (int)ad.size();
   upload(S.desc, ad, st);
@@ -381,6 +403,10 @@ struct Factorizer {
       a.G = d.fac + 3 * (int64_t)d.nc * d.nc;
       sw.max_np = std::max(sw.max_np, nR);
       sw.max_nq = std::max(sw.max_nq, k);
+      if (nR > 0) {
+        sw.fac_elems += 0.5 * nR * (nR + 1.0) + 2.0 * k * nR;
+        sw.vec_rows += nR + k;
+      }
       for (int t = k; t < d.nc; ++t) dead[ids_sr[t]] = 1;
       FrontInfo fi;
       fi.level = l;
@@ -411,9 +437,25 @@ struct Factorizer {
 // ---------------------------------------------------------------------------
 // apply of F^-1 / F on a packed N x nrhs work vector of the factor's type
 // ---------------------------------------------------------------------------
-template <typename T>
-const T* level_fac(const SweepLevel& S) {
-  return S.fac.as<T>();
+// The factor as the float apply reads it: the float copy when there is one.
+const float* fac_f32(const SweepLevel& S) {
+  return S.fac32.p ? S.fac32.as<float>() : S.fac.as<float>();
+}
+
+// FP32_APPLY: keep a float copy of every block of the factor, drop the double one.
+void demote_factor(hif_handle* h) {
+  auto demote = [&](SweepLevel& S) {
+    if (!S.fac.p || S.fac32.p) return;
+    const int64_t ne = (int64_t)(S.fac.bytes / sizeof(double));
+    S.fac32.alloc((size_t)ne * sizeof(float), h->st);
+    launch_convert<double, float>(ne, 1, S.fac.as<double>(), 1, S.fac32.as<float>(), 1, h->st);
+    S.fac.release();
+  };
+  for (auto& S : h->cells) demote(S);
+  for (auto& S : h->fronts) demote(S);
+  demote(h->root);
+  h->factor_bytes /= 2;
+  h->apply_bytes /= 2.0;
 }
 
 template <typename T>
@@ -422,29 +464,57 @@ void run_apply(hif_handle* h, int mode, T* x, int nrhs) {
   cudaStream_t st = h->st;
   const int up = (mode == HIF_APPLY_FINV) ? 0 : 2;
   const int down = (mode == HIF_APPLY_FINV) ? 1 : 3;
+  const bool prof = h->profile && mode == HIF_APPLY_FINV;
   auto sweep = [&](const SweepLevel& S, int op, int is_front, const T* fac) {
     if (S.nblocks == 0) return;
+    if (prof) {
+      if (h->ev_used + 2 > h->ev_pool.size()) {
+        for (int k = 0; k < 64; ++k) {
+          cudaEvent_t e;
+          CU(cudaEventCreate(&e));
+          h->ev_pool.push_back(e);
+        }
+      }
+      CU(cudaEventRecord(h->ev_pool[h->ev_used], st));
+    }
     launch_sweep<T>(op, S.desc.as<ApplyDesc>(), S.nblocks, S.ipool.as<int>(), fac, x, nrhs, nrhs,
                     is_front, S.max_np, S.max_nq, st);
+    if (prof) {
+      CU(cudaEventRecord(h->ev_pool[h->ev_used + 1], st));
+      h->ev_used += 2;
+      h->prof_launches += 1;
+      h->prof_bytes += sizeof(T) * (S.fac_elems + 2.0 * S.vec_rows * nrhs);
+    }
   };
-  const T* root_fac = (sizeof(T) == sizeof(float)) ? reinterpret_cast<const T*>(h->root.fac32.p)
-                                                   : h->root.fac.as<T>();
+  auto facp = [&](const SweepLevel& S) -> const T* {
+    if (sizeof(T) == sizeof(float)) return reinterpret_cast<const T*>(fac_f32(S));
+    return S.fac.as<T>();
+  };
   for (int l = 0; l < L; ++l) {
-    sweep(h->cells[l], up, 0, h->cells[l].fac.as<T>());
-    sweep(h->fronts[l], up, 1, h->fronts[l].fac.as<T>());
+    sweep(h->cells[l], up, 0, facp(h->cells[l]));
+    sweep(h->fronts[l], up, 1, facp(h->fronts[l]));
   }
-  sweep(h->root, up, 0, root_fac);
-  sweep(h->root, down, 0, root_fac);
+  sweep(h->root, up, 0, facp(h->root));
+  sweep(h->root, down, 0, facp(h->root));
   for (int l = L - 1; l >= 0; --l) {
-    sweep(h->fronts[l], down, 1, h->fronts[l].fac.as<T>());
-    sweep(h->cells[l], down, 0, h->cells[l].fac.as<T>());
+    sweep(h->fronts[l], down, 1, facp(h->fronts[l]));
+    sweep(h->cells[l], down, 0, facp(h->cells[l]));
   }
+}
+
+// Sum the elapsed times of the recorded sweep events (stream already synced).
+void resolve_profile(hif_handle* h) {
+  for (size_t k = 0; k + 1 < h->ev_used; k += 2) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->ev_pool[k], h->ev_pool[k + 1]) == cudaSuccess) h->prof_ms += ms;
+  }
+  h->ev_used = 0;
 }
 
 // z (double, packed N x nr) = F^-1 r (double, packed), via the factor's type
 void precondition(hif_handle* h, const double* r, double* z, float* wf, int nr) {
   const int64_t N = h->G.N;
-  if (h->precision == HIF_PREC_MIXED) {
+  if (h->precision != HIF_PREC_FP64) {
     launch_convert<double, float>(N, nr, r, nr, wf, nr, h->st);
     run_apply<float>(h, HIF_APPLY_FINV, wf, nr);
     launch_convert<float, double>(N, nr, wf, nr, z, nr, h->st);
@@ -550,6 +620,7 @@ int inner_pcg(hif_handle* h, SolveWork& W, const std::vector<double>& hthr, int 
     ++it;
     CU(cudaMemcpyAsync(hr.data(), W.rr, sizeof(double) * nr, cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
+    if (h->profile) resolve_profile(h);
     bool all = true;
     for (int c = 0; c < nr; ++c)
       if (hr[c] > hthr[c]) all = false;
@@ -578,7 +649,7 @@ int solve_chunk(hif_handle* h, const double* rhs, double* x, double* xlo, int nr
   cudaStream_t st = h->st;
   const size_t vb = sizeof(double) * N * nr;
   SolveWork W;
-  W.init(N, nr, h->precision == HIF_PREC_MIXED, st);
+  W.init(N, nr, h->precision != HIF_PREC_FP64, st);
   double* partials = W.part.as<double>();
   unsigned* counter = W.cnt.as<unsigned>();
   DevBuf f;
@@ -668,7 +739,8 @@ int hif_factor(const hif_grid* grid, const double* a_stag, const double* b, cons
   if (grid->variant == HIF_VARIANT_HIFDE && !(eps > 0.0 && eps < 1.0))
     return set_error(HIF_ERR_ARG, "eps must be in (0, 1) for HIF-DE");
   const int prec = opts ? opts->precision : HIF_PREC_FP64;
-  if (prec != HIF_PREC_FP64 && prec != HIF_PREC_MIXED) return set_error(HIF_ERR_ARG, "unknown precision");
+  if (prec != HIF_PREC_FP64 && prec != HIF_PREC_MIXED && prec != HIF_PREC_FP32_APPLY)
+    return set_error(HIF_ERR_ARG, "unknown precision");
   const int leaf = grid->leaf > 0 ? grid->leaf : 8;
   if (leaf < 2) return set_error(HIF_ERR_ARG, "leaf must be >= 2");
   hif_handle* h = new hif_handle();
@@ -700,6 +772,7 @@ int hif_factor(const hif_grid* grid, const double* a_stag, const double* b, cons
       Factorizer<double> f(h);
       f.run();
     }
+    if (prec == HIF_PREC_FP32_APPLY) demote_factor(h);
     CU(cudaEventRecord(e1, h->st));
     CU(cudaEventSynchronize(e1));
     float ms = 0.f;
@@ -729,7 +802,7 @@ int hif_apply(hif_handle* h, int mode, const double* x, double* y, int nrhs, int
     DevBuf w, tmp, wf;
     w.alloc(sizeof(double) * N * nrhs, st);
     stage_in(x, nrhs, ld, N, w.as<double>(), st, tmp);
-    if (h->precision == HIF_PREC_MIXED) {
+    if (h->precision != HIF_PREC_FP64) {
       wf.alloc(sizeof(float) * N * nrhs, st);
       launch_convert<double, float>(N, nrhs, w.as<double>(), nrhs, wf.as<float>(), nrhs, st);
       run_apply<float>(h, mode, wf.as<float>(), nrhs);
@@ -740,6 +813,7 @@ int hif_apply(hif_handle* h, int mode, const double* x, double* y, int nrhs, int
     stage_out(w.as<double>(), nrhs, ld, N, y, st, tmp);
     CU(cudaGetLastError());
     CU(cudaStreamSynchronize(st));
+    if (h->profile) resolve_profile(h);
   } catch (const HifError& e) {
     return set_error(e.code, e.msg);
   }
@@ -778,8 +852,8 @@ int hif_solve(hif_handle* h, const double* rhs, double* x, double* x_lo, int nrh
     const int64_t N = h->G.N;
     cudaStream_t st = h->st;
     DevBuf pin, pout, plo, tmp;
-    for (int r0 = 0; r0 < nrhs; r0 += 32) {
-      const int nr = std::min(32, nrhs - r0);
+    for (int r0 = 0; r0 < nrhs; r0 += 16) {
+      const int nr = std::min(16, nrhs - r0);
       pin.alloc(sizeof(double) * N * nr, st);
       pout.alloc(sizeof(double) * N * nr, st);
       if (x_lo) plo.alloc(sizeof(double) * N * nr, st);
@@ -791,6 +865,7 @@ int hif_solve(hif_handle* h, const double* rhs, double* x, double* x_lo, int nrh
       if (x_lo) stage_out(plo.as<double>(), nr, ld, N, x_lo + r0, st, tmp);
     }
     CU(cudaStreamSynchronize(st));
+    if (h->profile) resolve_profile(h);
   } catch (const HifError& e) {
     return set_error(e.code, e.msg);
   }
@@ -835,6 +910,22 @@ int hif_structure(const hif_handle* h, int32_t* buf, long long cap, long long* n
   buf[p++] = h->root_size;
   return HIF_OK;
 }
+
+int hif_profile(hif_handle* h, int enable, hif_profile_t* out) {
+  if (!h) return set_error(HIF_ERR_ARG, "NULL handle");
+  if (out) {
+    out->sweep_ms = h->prof_ms;
+    out->sweep_launches = h->prof_launches;
+    out->sweep_bytes = h->prof_bytes;
+  }
+  h->prof_ms = 0.0;
+  h->prof_bytes = 0.0;
+  h->prof_launches = 0;
+  h->profile = enable ? 1 : 0;
+  return HIF_OK;
+}
+
+long long hif_kernel_launches(void) { return g_launches.load(); }
 
 void hif_free(hif_handle* h) {
   if (!h) return;

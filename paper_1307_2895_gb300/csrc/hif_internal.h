@@ -48,6 +48,9 @@ struct ApplyDesc {
   int64_t Linv, L, G, T;   // factor pool offsets (T = -1 for cells)
 };
 
+// Process-wide count of kernel launches issued by the library.
+void note_launches(long long n);
+
 struct GridInfo {
   int dim, n, m;       // m = n - 1 nodes per axis
   double inv_h2;

@@ -25,6 +25,10 @@ __device__ __forceinline__ void gather(T* dst, const T* x, const int* ids, int n
   }
 }
 
+// Every product below is a serial dot per (output row, right-hand side)
+// pair: one thread per pair, no cross-lane reductions (FP64 additions are
+// scarce on this GPU, so they are spent only on the products themselves).
+
 template <typename T, int R>
 __global__ void k_apply_up(const ApplyDesc* __restrict__ blocks, const int* __restrict__ ipool,
                            const T* __restrict__ fac, T* __restrict__ x, int nr, int ldx,
@@ -43,65 +47,34 @@ __global__ void k_apply_up(const ApplyDesc* __restrict__ blocks, const int* __re
   gather<T, R>(xp, x, idp, np, nr, ldx);
   if (is_front) gather<T, R>(xq, x, idq, nq, nr, ldx);
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  if (is_front && nq > 0) {
-    const T* Tm = fac + bd.T;            // nq x np
-    for (int i = threadIdx.x; i < np; i += blockDim.x) {
-      T acc[R];
-#pragma unroll
-      for (int r = 0; r < R; ++r) acc[r] = T(0);
-      for (int s = 0; s < nq; ++s) {
-        const T t = Tm[(int64_t)s * np + i];
-#pragma unroll
-        for (int r = 0; r < R; ++r) acc[r] += t * xq[s * R + r];
-      }
-#pragma unroll
-      for (int r = 0; r < R; ++r) xp[i * R + r] -= acc[r];
+  if (is_front && nq > 0) {                      // x_p -= T^T x_q
+    const T* Tm = fac + bd.T;                    // nq x np
+    for (int e = threadIdx.x; e < np * R; e += blockDim.x) {
+      const int i = e / R, r = e % R;
+      T acc = T(0);
+      for (int s2 = 0; s2 < nq; ++s2) acc += Tm[(int64_t)s2 * np + i] * xq[s2 * R + r];
+      xp[e] -= acc;
     }
     __syncthreads();
   }
-  // y_p = Linv x_p  (warp per row)
-  for (int i = warp; i < np; i += nw) {
+  for (int e = threadIdx.x; e < np * R; e += blockDim.x) {   // y_p = Linv x_p
+    const int i = e / R, r = e % R;
     const T* l = Linv + (int64_t)i * np;
-    T acc[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) acc[r] = T(0);
-    for (int t = lane; t <= i; t += 32) {
-      const T lv = l[t];
-#pragma unroll
-      for (int r = 0; r < R; ++r) acc[r] += lv * xp[t * R + r];
-    }
-#pragma unroll
-    for (int r = 0; r < R; ++r) acc[r] = warp_sum(acc[r]);
-    if (lane < R) {
-      T val = acc[0];
-#pragma unroll
-      for (int r = 1; r < R; ++r) if (lane == r) val = acc[r];
-      yp[i * R + lane] = val;
-      if (lane < nr) x[(int64_t)idp[i] * ldx + lane] = val;
-    }
+    T acc = T(0);
+    for (int t = 0; t <= i; ++t) acc += l[t] * xp[t * R + r];
+    yp[e] = acc;
+    if (r < nr) x[(int64_t)idp[i] * ldx + r] = acc;
   }
   __syncthreads();
-  // x_q -= G y_p  (warp per row)
-  for (int s = warp; s < nq; s += nw) {
-    const T* g = G + (int64_t)s * np;
-    T acc[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) acc[r] = T(0);
-    for (int t = lane; t < np; t += 32) {
-      const T gv = g[t];
-#pragma unroll
-      for (int r = 0; r < R; ++r) acc[r] += gv * yp[t * R + r];
-    }
-#pragma unroll
-    for (int r = 0; r < R; ++r) acc[r] = warp_sum(acc[r]);
-    if (lane < nr) {
-      T val = acc[0];
-#pragma unroll
-      for (int r = 1; r < R; ++r) if (lane == r) val = acc[r];
-      T* dst = x + (int64_t)idq[s] * ldx + lane;
-      if (is_front) *dst = xq[s * R + lane] - val;
-      else atomicAdd(dst, -val);
+  for (int e = threadIdx.x; e < nq * R; e += blockDim.x) {   // x_q -= G y_p
+    const int s2 = e / R, r = e % R;
+    const T* g = G + (int64_t)s2 * np;
+    T acc = T(0);
+    for (int t = 0; t < np; ++t) acc += g[t] * yp[t * R + r];
+    if (r < nr) {
+      T* dst = x + (int64_t)idq[s2] * ldx + r;
+      if (is_front) *dst = xq[e] - acc;
+      else atomicAdd(dst, -acc);
     }
   }
 }
@@ -124,60 +97,31 @@ __global__ void k_apply_down(const ApplyDesc* __restrict__ blocks, const int* __
   gather<T, R>(xp, x, idp, np, nr, ldx);
   gather<T, R>(xq, x, idq, nq, nr, ldx);
   __syncthreads();
-  // w = x_p - G^T x_q  (thread per column, in place on xp)
-  if (nq > 0) {
-    for (int i = threadIdx.x; i < np; i += blockDim.x) {
-      T acc[R];
-#pragma unroll
-      for (int r = 0; r < R; ++r) acc[r] = T(0);
-      for (int s = 0; s < nq; ++s) {
-        const T gv = G[(int64_t)s * np + i];
-#pragma unroll
-        for (int r = 0; r < R; ++r) acc[r] += gv * xq[s * R + r];
-      }
-#pragma unroll
-      for (int r = 0; r < R; ++r) xp[i * R + r] -= acc[r];
+  if (nq > 0) {                                  // w = x_p - G^T x_q (in place)
+    for (int e = threadIdx.x; e < np * R; e += blockDim.x) {
+      const int i = e / R, r = e % R;
+      T acc = T(0);
+      for (int s2 = 0; s2 < nq; ++s2) acc += G[(int64_t)s2 * np + i] * xq[s2 * R + r];
+      xp[e] -= acc;
     }
     __syncthreads();
   }
-  // z = Linv^T w (thread per column)
-  for (int i = threadIdx.x; i < np; i += blockDim.x) {
-    T acc[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) acc[r] = T(0);
-    for (int t = i; t < np; ++t) {
-      const T lv = Linv[(int64_t)t * np + i];
-#pragma unroll
-      for (int r = 0; r < R; ++r) acc[r] += lv * xp[t * R + r];
-    }
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      zp[i * R + r] = acc[r];
-      if (r < nr) x[(int64_t)idp[i] * ldx + r] = acc[r];
-    }
+  for (int e = threadIdx.x; e < np * R; e += blockDim.x) {   // z = Linv^T w
+    const int i = e / R, r = e % R;
+    T acc = T(0);
+    for (int t = i; t < np; ++t) acc += Linv[(int64_t)t * np + i] * xp[t * R + r];
+    zp[e] = acc;
+    if (r < nr) x[(int64_t)idp[i] * ldx + r] = acc;
   }
-  __syncthreads();
-  if (is_front && nq > 0) {
+  if (is_front && nq > 0) {                      // x_q -= T z
+    __syncthreads();
     const T* Tm = fac + bd.T;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int s = warp; s < nq; s += nw) {
-      const T* t = Tm + (int64_t)s * np;
-      T acc[R];
-#pragma unroll
-      for (int r = 0; r < R; ++r) acc[r] = T(0);
-      for (int c = lane; c < np; c += 32) {
-        const T tv = t[c];
-#pragma unroll
-        for (int r = 0; r < R; ++r) acc[r] += tv * zp[c * R + r];
-      }
-#pragma unroll
-      for (int r = 0; r < R; ++r) acc[r] = warp_sum(acc[r]);
-      if (lane < nr) {
-        T val = acc[0];
-#pragma unroll
-        for (int r = 1; r < R; ++r) if (lane == r) val = acc[r];
-        x[(int64_t)idq[s] * ldx + lane] = xq[s * R + lane] - val;
-      }
+    for (int e = threadIdx.x; e < nq * R; e += blockDim.x) {
+      const int s2 = e / R, r = e % R;
+      const T* t = Tm + (int64_t)s2 * np;
+      T acc = T(0);
+      for (int c = 0; c < np; ++c) acc += t[c] * zp[c * R + r];
+      if (r < nr) x[(int64_t)idq[s2] * ldx + r] = xq[e] - acc;
     }
   }
 }
@@ -201,41 +145,24 @@ __global__ void k_fwd_up(const ApplyDesc* __restrict__ blocks, const int* __rest
   __syncthreads();
   if (is_front && nq > 0) {       // x_q += T x_p
     const T* Tm = fac + bd.T;
-    for (int s = threadIdx.x; s < nq; s += blockDim.x) {
-      T acc[R];
-#pragma unroll
-      for (int r = 0; r < R; ++r) acc[r] = T(0);
-      for (int c = 0; c < np; ++c) {
-        const T tv = Tm[(int64_t)s * np + c];
-#pragma unroll
-        for (int r = 0; r < R; ++r) acc[r] += tv * xp[c * R + r];
-      }
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        xq[s * R + r] += acc[r];
-        if (r < nr) x[(int64_t)idq[s] * ldx + r] = xq[s * R + r];
-      }
+    T* tq = xq + nq * R;          // scratch: the launch reserves (2 np + 2 nq) R
+    for (int e = threadIdx.x; e < nq * R; e += blockDim.x) {
+      const int s2 = e / R, r = e % R;
+      T acc = T(0);
+      for (int c = 0; c < np; ++c) acc += Tm[(int64_t)s2 * np + c] * xp[c * R + r];
+      tq[e] = xq[e] + acc;
+      if (r < nr) x[(int64_t)idq[s2] * ldx + r] = tq[e];
     }
     __syncthreads();
+    for (int e = threadIdx.x; e < nq * R; e += blockDim.x) xq[e] = tq[e];
+    __syncthreads();
   }
-  // x_p = L^T x_p + G^T x_q
-  for (int i = threadIdx.x; i < np; i += blockDim.x) {
-    T acc[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) acc[r] = T(0);
-    for (int t = i; t < np; ++t) {
-      const T lv = Lf[(int64_t)t * np + i];
-#pragma unroll
-      for (int r = 0; r < R; ++r) acc[r] += lv * xp[t * R + r];
-    }
-    for (int s = 0; s < nq; ++s) {
-      const T gv = G[(int64_t)s * np + i];
-#pragma unroll
-      for (int r = 0; r < R; ++r) acc[r] += gv * xq[s * R + r];
-    }
-#pragma unroll
-    for (int r = 0; r < R; ++r)
-      if (r < nr) x[(int64_t)idp[i] * ldx + r] = acc[r];
+  for (int e = threadIdx.x; e < np * R; e += blockDim.x) {   // x_p = L^T x_p + G^T x_q
+    const int i = e / R, r = e % R;
+    T acc = T(0);
+    for (int t = i; t < np; ++t) acc += Lf[(int64_t)t * np + i] * xp[t * R + r];
+    for (int s2 = 0; s2 < nq; ++s2) acc += G[(int64_t)s2 * np + i] * xq[s2 * R + r];
+    if (r < nr) x[(int64_t)idp[i] * ldx + r] = acc;
   }
 }
 
@@ -255,55 +182,29 @@ __global__ void k_fwd_down(const ApplyDesc* __restrict__ blocks, const int* __re
   gather<T, R>(xp, x, idp, np, nr, ldx);
   if (is_front) gather<T, R>(xq, x, idq, nq, nr, ldx);
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  // x_q += G x_p
-  for (int s = warp; s < nq; s += nw) {
-    const T* g = G + (int64_t)s * np;
-    T acc[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) acc[r] = T(0);
-    for (int c = lane; c < np; c += 32) {
-      const T gv = g[c];
-#pragma unroll
-      for (int r = 0; r < R; ++r) acc[r] += gv * xp[c * R + r];
-    }
-#pragma unroll
-    for (int r = 0; r < R; ++r) acc[r] = warp_sum(acc[r]);
-    if (lane < R) {
-      T val = acc[0];
-#pragma unroll
-      for (int r = 1; r < R; ++r) if (lane == r) val = acc[r];
-      if (is_front) {
-        xq[s * R + lane] += val;
-        if (lane < nr) x[(int64_t)idq[s] * ldx + lane] = xq[s * R + lane];
-      } else if (lane < nr) {
-        atomicAdd(x + (int64_t)idq[s] * ldx + lane, val);
-      }
+  for (int e = threadIdx.x; e < nq * R; e += blockDim.x) {   // x_q += G x_p
+    const int s2 = e / R, r = e % R;
+    const T* g = G + (int64_t)s2 * np;
+    T acc = T(0);
+    for (int c = 0; c < np; ++c) acc += g[c] * xp[c * R + r];
+    if (is_front) {
+      xq[e] += acc;
+      if (r < nr) x[(int64_t)idq[s2] * ldx + r] = xq[e];
+    } else if (r < nr) {
+      atomicAdd(x + (int64_t)idq[s2] * ldx + r, acc);
     }
   }
   __syncthreads();
-  // x_p = L x_p [+ T^T x_q]
-  for (int i = threadIdx.x; i < np; i += blockDim.x) {
-    T acc[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) acc[r] = T(0);
+  for (int e = threadIdx.x; e < np * R; e += blockDim.x) {   // x_p = L x_p [+ T^T x_q]
+    const int i = e / R, r = e % R;
     const T* l = Lf + (int64_t)i * np;
-    for (int t = 0; t <= i; ++t) {
-      const T lv = l[t];
-#pragma unroll
-      for (int r = 0; r < R; ++r) acc[r] += lv * xp[t * R + r];
-    }
+    T acc = T(0);
+    for (int t = 0; t <= i; ++t) acc += l[t] * xp[t * R + r];
     if (is_front) {
       const T* Tm = fac + bd.T;
-      for (int s = 0; s < nq; ++s) {
-        const T tv = Tm[(int64_t)s * np + i];
-#pragma unroll
-        for (int r = 0; r < R; ++r) acc[r] += tv * xq[s * R + r];
-      }
+      for (int s2 = 0; s2 < nq; ++s2) acc += Tm[(int64_t)s2 * np + i] * xq[s2 * R + r];
     }
-#pragma unroll
-    for (int r = 0; r < R; ++r)
-      if (r < nr) x[(int64_t)idp[i] * ldx + r] = acc[r];
+    if (r < nr) x[(int64_t)idp[i] * ldx + r] = acc;
   }
 }
 
@@ -312,7 +213,7 @@ template <typename T, int R>
 static void launch_sweep_R(int op, const ApplyDesc* blocks, int nblocks, const int* ipool,
                            const T* fac, T* x, int nr, int ldx, int is_front, int max_np,
                            int max_nq, cudaStream_t st) {
-  const size_t smem = sizeof(T) * R * (size_t)(2 * max_np + max_nq);
+  const size_t smem = sizeof(T) * R * (size_t)(2 * max_np + 2 * max_nq);
   void (*fn)(const ApplyDesc*, const int*, const T*, T*, int, int, int) = nullptr;
   switch (op) {
     case 0: fn = k_apply_up<T, R>; break;
@@ -321,6 +222,7 @@ static void launch_sweep_R(int op, const ApplyDesc* blocks, int nblocks, const i
     default: fn = k_fwd_down<T, R>; break;
   }
   if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  note_launches(1);
   fn<<<nblocks, 256, smem, st>>>(blocks, ipool, fac, x, nr, ldx, is_front);
 }
 
@@ -328,7 +230,7 @@ template <typename T>
 int sweep_chunk(int max_np, int max_nq, int nrhs) {
   const size_t cap = 200 * 1024;
   int R = 32;
-  while (R > 1 && (R / 2 >= nrhs || sizeof(T) * R * (size_t)(2 * max_np + max_nq) > cap)) R /= 2;
+  while (R > 1 && (R / 2 >= nrhs || sizeof(T) * R * (size_t)(2 * max_np + 2 * max_nq) > cap)) R /= 2;
   return R;
 }
 

@@ -401,12 +401,14 @@ void launch_leaf_assemble(const CellDesc* cells, int ncells, const int* ipool, T
                           GridInfo g, const double* a_stag, const double* bnode, const int* cls,
                           int ncell_axis, cudaStream_t st) {
   LeafGeom L{g, a_stag, bnode, cls, ncell_axis};
+  note_launches(1);
   k_leaf_assemble<T><<<ncells, 256, 0, st>>>(cells, ipool, work, L);
 }
 
 template <typename TU, typename TF>
 void launch_extend_add(const CellDesc* cells, int ncells, const int* ipool, TF* work,
                        const CellDesc* pcells, const TU* pwork, int nchild, cudaStream_t st) {
+  note_launches(1);
   k_extend_add<TU, TF><<<ncells, 256, 0, st>>>(cells, ipool, work, pcells, pwork, nchild);
 }
 
@@ -420,6 +422,7 @@ void launch_cell_factor(const CellDesc* cells, int ncells, T* work, T* fac, int*
   const int smem = (int)need;
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(k_cell_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  note_launches(1);
   k_cell_factor<T><<<ncells, 256, smem, st>>>(cells, work, fac, status, smem / (int)sizeof(T), (T)tau);
 }
 
@@ -430,6 +433,7 @@ void launch_front(const FrontDesc* fronts, int nfronts, const CellDesc* cells, i
   const int smem = (int)(sizeof(double) * (max_nc + max_nN) + sizeof(int) * 2 * max_nc + 64);
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(k_front<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  note_launches(1);
   k_front<T><<<nfronts, 256, smem, st>>>(fronts, cells, ipool, fwork, fac, cwork, eps, status, (T)tau);
 }
 

@@ -1,49 +1,53 @@
-// Stencil operator and CG vector kernels (FP64).  One thread per unknown,
-// all right-hand sides per thread; vectors are N x nr row-major (stride ld).
-// Reductions: per-block partial sums, then the last block to finish sums the
-// partials in block order (deterministic for a fixed grid).
+// Stencil operator and CG vector kernels (FP64).  Vectors are N x nr
+// row-major (stride nr unless stated), nr <= 16.  Every kernel runs a fixed
+// grid of grid-stride threads that keep their partial sums in registers; a
+// reduction ends with a shared-memory tree per block and the last block to
+// finish sums the per-block partials in block order, so results do not depend
+// on scheduling.  (FP64 arithmetic is the scarce resource on this GPU: the
+// cross-thread part of a reduction costs ~255 additions per block, not per
+// element.)
 #include "hif_internal.h"
 #include "blockops.cuh"
 #include "kernels.h"
 
 namespace hif {
 
-__device__ __forceinline__ double block_sum(double v, double* sh) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  v = warp_sum(v);
-  __syncthreads();
-  if (lane == 0) sh[warp] = v;
-  __syncthreads();
-  double s = 0.0;
-  if (warp == 0) {
-    s = (lane < nw) ? sh[lane] : 0.0;
-    s = warp_sum(s);
-  }
-  return s;  // valid in thread 0
+constexpr int kVecThreads = 256;
+constexpr int kVecBlocksMax = 304;   // 2 blocks per SM
+
+static inline int vec_blocks(int64_t n) {
+  const int64_t b = (n + kVecThreads - 1) / kVecThreads;
+  return (int)(b < kVecBlocksMax ? (b > 0 ? b : 1) : kVecBlocksMax);
 }
 
-// Partials of nv values per block -> out[0..nv) by the last block.
-__device__ void finish_reduce(const double* vals, int nv, double* partials, unsigned* counter,
-                              double* out) {
-  __shared__ double sh[32];
+// Sum acc[0..nv) over the grid into out[0..nv).  Needs nv*blockDim.x doubles
+// of dynamic shared memory.
+template <int NV>
+__device__ void grid_reduce(const double (&acc)[NV], int nv, double* partials, unsigned* counter,
+                            double* out) {
+  extern __shared__ double shr[];
   __shared__ bool last;
-  for (int t = 0; t < nv; ++t) {
-    const double s = block_sum(vals[t], sh);
-    if (threadIdx.x == 0) partials[(int64_t)blockIdx.x * nv + t] = s;
+  const int tid = threadIdx.x;
+  for (int v = 0; v < nv; ++v) shr[tid * nv + v] = acc[v];
+  __syncthreads();
+  for (int s = blockDim.x >> 1; s > 0; s >>= 1) {
+    if (tid < s)
+      for (int v = 0; v < nv; ++v) shr[tid * nv + v] += shr[(tid + s) * nv + v];
+    __syncthreads();
   }
+  if (tid < nv) partials[(int64_t)blockIdx.x * nv + tid] = shr[tid];
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  if (tid == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
   __syncthreads();
   if (!last) return;
   __threadfence();
-  for (int t = 0; t < nv; ++t) {
+  for (int v = tid; v < nv; v += blockDim.x) {
     double s = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s += partials[(int64_t)b * nv + t];
-    s = block_sum(s, sh);
-    if (threadIdx.x == 0) out[t] = s;
+    for (int b = 0; b < (int)gridDim.x; ++b) s += partials[(int64_t)b * nv + v];
+    out[v] = s;
   }
-  if (threadIdx.x == 0) *counter = 0u;
+  if (tid == 0) *counter = 0u;
 }
 
 struct Stencil {
@@ -64,19 +68,18 @@ __device__ __forceinline__ double sbond(const Stencil& S, int axis, int j0, int 
   return S.a_stag[2 * blk + ((int64_t)j2 * m + (j1 - 1)) * m + (j0 - 1)];
 }
 
-// y = A x for one unknown g, all columns; optionally returns sum_r w_r * (x.y)_r style dots via acc.
-template <int MAXR>
+// y[0..R) = (A x)_gid for the columns r < nr of x (row stride ld).
+template <int R>
 __device__ __forceinline__ void stencil_row(const Stencil& S, int64_t gid, const double* x, int ld,
-                                            int nr, double* y) {
+                                            int nr, double (&y)[R]) {
   const int m = S.g.m, dim = S.g.dim;
-  const int j0 = (int)(gid % m) + 1;
-  const int j1 = (int)((gid / m) % m) + 1;
-  const int j2 = (dim == 3) ? (int)(gid / ((int64_t)m * m)) + 1 : 1;
+  const int jj[3] = {(int)(gid % m) + 1, (int)((gid / m) % m) + 1,
+                     dim == 3 ? (int)(gid / ((int64_t)m * m)) + 1 : 1};
+  const int64_t stride[3] = {1, m, (int64_t)m * m};
   const double h2 = S.g.inv_h2;
   double diag = S.bnode[gid];
-  for (int r = 0; r < nr; ++r) y[r] = 0.0;
-  int jj[3] = {j0, j1, j2};
-  int64_t stride[3] = {1, m, (int64_t)m * m};
+#pragma unroll
+  for (int r = 0; r < R; ++r) y[r] = 0.0;
   for (int ax = 0; ax < dim; ++ax) {
     int lo[3] = {jj[0], jj[1], jj[2]};
     lo[ax] -= 1;
@@ -85,132 +88,174 @@ __device__ __forceinline__ void stencil_row(const Stencil& S, int64_t gid, const
     diag += alo + ahi;
     if (jj[ax] > 1) {
       const double* xn = x + (gid - stride[ax]) * ld;
-      for (int r = 0; r < nr; ++r) y[r] -= alo * xn[r];
+#pragma unroll
+      for (int r = 0; r < R; ++r) if (r < nr) y[r] -= alo * xn[r];
     }
     if (jj[ax] < m) {
       const double* xn = x + (gid + stride[ax]) * ld;
-      for (int r = 0; r < nr; ++r) y[r] -= ahi * xn[r];
+#pragma unroll
+      for (int r = 0; r < R; ++r) if (r < nr) y[r] -= ahi * xn[r];
     }
   }
   const double* xs = x + gid * ld;
-  for (int r = 0; r < nr; ++r) y[r] += diag * xs[r];
+#pragma unroll
+  for (int r = 0; r < R; ++r) if (r < nr) y[r] += diag * xs[r];
 }
 
-constexpr int kMaxR = 32;
+#define GRID_LOOP(gid, N) for (int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gid < (N); \
+                               gid += (int64_t)gridDim.x * blockDim.x)
 
-// y = A x
+// y = A x (strided)
+template <int R>
 __global__ void k_matvec(Stencil S, int64_t N, const double* __restrict__ x, int ldx,
                          double* __restrict__ y, int ldy, int nr) {
-  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= N) return;
-  double t[kMaxR];
-  stencil_row<kMaxR>(S, gid, x, ldx, nr, t);
-  for (int r = 0; r < nr; ++r) y[gid * ldy + r] = t[r];
+  GRID_LOOP(gid, N) {
+    double t[R];
+    stencil_row<R>(S, gid, x, ldx, nr, t);
+#pragma unroll
+    for (int r = 0; r < R; ++r) if (r < nr) y[gid * ldy + r] = t[r];
+  }
 }
 
 // q = A p ; pq_r = p_r . q_r
+template <int R>
 __global__ void k_mv_dot(Stencil S, int64_t N, const double* __restrict__ p, double* __restrict__ q,
                          int nr, double* partials, unsigned* counter, double* pq) {
-  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  double vals[kMaxR];
-  for (int r = 0; r < nr; ++r) vals[r] = 0.0;
-  if (gid < N) {
-    double t[kMaxR];
-    stencil_row<kMaxR>(S, gid, p, nr, nr, t);
-    for (int r = 0; r < nr; ++r) {
-      q[gid * nr + r] = t[r];
-      vals[r] = t[r] * p[gid * nr + r];
-    }
+  double acc[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) acc[r] = 0.0;
+  GRID_LOOP(gid, N) {
+    double t[R];
+    stencil_row<R>(S, gid, p, nr, nr, t);
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      if (r < nr) {
+        q[gid * nr + r] = t[r];
+        acc[r] = fma(t[r], p[gid * nr + r], acc[r]);
+      }
   }
-  finish_reduce(vals, nr, partials, counter, pq);
+  grid_reduce<R>(acc, nr, partials, counter, pq);
 }
 
 // alpha = rz/pq (active columns); x += alpha p; r -= alpha q; rr = r.r
+template <int R>
 __global__ void k_axpy2(int64_t N, int nr, double* __restrict__ x, double* __restrict__ r,
                         const double* __restrict__ p, const double* __restrict__ q,
                         const double* rz, const double* pq, const int* active, double* alpha_out,
                         double* partials, unsigned* counter, double* rr) {
-  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  double vals[kMaxR];
-  for (int c = 0; c < nr; ++c) {
-    const double a = (active[c] && pq[c] != 0.0) ? rz[c] / pq[c] : 0.0;
-    if (gid == 0) alpha_out[c] = a;
-    double rv = 0.0;
-    if (gid < N) {
-      const int64_t o = gid * nr + c;
-      x[o] += a * p[o];
-      rv = r[o] - a * q[o];
-      r[o] = rv;
-    }
-    vals[c] = rv * rv;
+  double a[R], acc[R];
+#pragma unroll
+  for (int c = 0; c < R; ++c) {
+    a[c] = (c < nr && active[c] && pq[c] != 0.0) ? rz[c] / pq[c] : 0.0;
+    acc[c] = 0.0;
   }
-  finish_reduce(vals, nr, partials, counter, rr);
+  if (blockIdx.x == 0 && threadIdx.x < nr) {
+    const int c = threadIdx.x;
+    alpha_out[c] = (active[c] && pq[c] != 0.0) ? rz[c] / pq[c] : 0.0;
+  }
+  GRID_LOOP(gid, N) {
+#pragma unroll
+    for (int c = 0; c < R; ++c)
+      if (c < nr) {
+        const int64_t o = gid * nr + c;
+        x[o] = fma(a[c], p[o], x[o]);
+        const double rv = fma(-a[c], q[o], r[o]);
+        r[o] = rv;
+        acc[c] = fma(rv, rv, acc[c]);
+      }
+  }
+  grid_reduce<R>(acc, nr, partials, counter, rr);
 }
 
-// rz = r.z ; zq = z.q
+// rz = r.z ; zq = z.q   (out = [rz(0..nr) | zq(0..nr)])
+template <int R>
 __global__ void k_dot2(int64_t N, int nr, const double* __restrict__ r, const double* __restrict__ z,
                        const double* __restrict__ q, double* partials, unsigned* counter, double* out) {
-  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  double vals[2 * kMaxR];
-  for (int c = 0; c < nr; ++c) {
-    double a = 0.0, b = 0.0;
-    if (gid < N) {
-      const int64_t o = gid * nr + c;
-      a = r[o] * z[o];
-      b = z[o] * q[o];
-    }
-    vals[c] = a;
-    vals[nr + c] = b;
+  double acc[2 * R];
+#pragma unroll
+  for (int c = 0; c < 2 * R; ++c) acc[c] = 0.0;
+  GRID_LOOP(gid, N) {
+#pragma unroll
+    for (int c = 0; c < R; ++c)
+      if (c < nr) {
+        const int64_t o = gid * nr + c;
+        const double zv = z[o];
+        acc[c] = fma(r[o], zv, acc[c]);
+        acc[R + c] = fma(zv, q[o], acc[R + c]);
+      }
   }
-  finish_reduce(vals, 2 * nr, partials, counter, out);
+  double packed[2 * R];
+#pragma unroll
+  for (int c = 0; c < 2 * R; ++c) packed[c] = 0.0;
+#pragma unroll
+  for (int c = 0; c < R; ++c)
+    if (c < nr) {
+      packed[c] = acc[c];
+      packed[nr + c] = acc[R + c];
+    }
+  grid_reduce<2 * R>(packed, 2 * nr, partials, counter, out);
 }
 
 // beta = -alpha zq / rz_old (flexible / Polak-Ribiere form); p = z + beta p
+template <int R>
 __global__ void k_update_p(int64_t N, int nr, double* __restrict__ p, const double* __restrict__ z,
                            const double* alpha, const double* rz_old, const double* rzzq,
                            const int* active, int restart) {
-  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= N) return;
-  for (int c = 0; c < nr; ++c) {
-    if (!active[c]) continue;
-    const int64_t o = gid * nr + c;
-    if (restart || rz_old[c] == 0.0) {
-      p[o] = z[o];
-    } else {
-      const double beta = -alpha[c] * rzzq[nr + c] / rz_old[c];
-      p[o] = z[o] + beta * p[o];
-    }
+  double beta[R];
+  bool act[R], rs[R];
+#pragma unroll
+  for (int c = 0; c < R; ++c) {
+    act[c] = c < nr && active[c];
+    rs[c] = restart || (c < nr && rz_old[c] == 0.0);
+    beta[c] = (c < nr && !rs[c]) ? -alpha[c] * rzzq[nr + c] / rz_old[c] : 0.0;
+  }
+  GRID_LOOP(gid, N) {
+#pragma unroll
+    for (int c = 0; c < R; ++c)
+      if (act[c]) {
+        const int64_t o = gid * nr + c;
+        p[o] = rs[c] ? z[o] : fma(beta[c], p[o], z[o]);
+      }
   }
 }
 
-// out = b - A x (for the true residual), and its squared norms
+// out = b - A x (FP64) and its squared norms
+template <int R>
 __global__ void k_residual(Stencil S, int64_t N, const double* __restrict__ b, const double* __restrict__ x,
                            double* __restrict__ out, int nr, double* partials, unsigned* counter,
                            double* nrm2) {
-  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  double vals[kMaxR];
-  for (int r = 0; r < nr; ++r) vals[r] = 0.0;
-  if (gid < N) {
-    double t[kMaxR];
-    stencil_row<kMaxR>(S, gid, x, nr, nr, t);
-    for (int r = 0; r < nr; ++r) {
-      const double v = b[gid * nr + r] - t[r];
-      out[gid * nr + r] = v;
-      vals[r] = v * v;
-    }
+  double acc[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) acc[r] = 0.0;
+  GRID_LOOP(gid, N) {
+    double t[R];
+    stencil_row<R>(S, gid, x, nr, nr, t);
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      if (r < nr) {
+        const double v = b[gid * nr + r] - t[r];
+        out[gid * nr + r] = v;
+        acc[r] = fma(v, v, acc[r]);
+      }
   }
-  finish_reduce(vals, nr, partials, counter, nrm2);
+  grid_reduce<R>(acc, nr, partials, counter, nrm2);
 }
 
+template <int R>
 __global__ void k_sqnorm(int64_t N, int nr, const double* __restrict__ v, double* partials,
                          unsigned* counter, double* out) {
-  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  double vals[kMaxR];
-  for (int c = 0; c < nr; ++c) {
-    const double a = (gid < N) ? v[gid * nr + c] : 0.0;
-    vals[c] = a * a;
+  double acc[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) acc[r] = 0.0;
+  GRID_LOOP(gid, N) {
+#pragma unroll
+    for (int c = 0; c < R; ++c)
+      if (c < nr) {
+        const double a = v[gid * nr + c];
+        acc[c] = fma(a, a, acc[c]);
+      }
   }
-  finish_reduce(vals, nr, partials, counter, out);
+  grid_reduce<R>(acc, nr, partials, counter, out);
 }
 
 // ---- double-double outer iterate -------------------------------------------
@@ -229,33 +274,41 @@ __device__ __forceinline__ void two_prod(double a, double b, double& p, double& 
 // r = f - A (xh + xl) in the bond form of the stencil,
 //   (A x)_i = sum_e a_e n^2 (x_i - x_j) + b_i x_i  (x_j = 0 on the boundary),
 // accumulated in double-double and rounded once; also sum_r |r|^2.
+template <int R>
 __global__ void k_dd_residual(Stencil S, int64_t N, const double* __restrict__ f,
                               const double* __restrict__ xh, const double* __restrict__ xl,
                               double* __restrict__ rout, int nr, double* partials,
                               unsigned* counter, double* nrm2) {
-  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  double vals[kMaxR];
-  for (int c = 0; c < nr; ++c) vals[c] = 0.0;
-  if (gid < N) {
-    const int m = S.g.m, dim = S.g.dim;
+  double acc[R];
+#pragma unroll
+  for (int c = 0; c < R; ++c) acc[c] = 0.0;
+  const int m = S.g.m, dim = S.g.dim;
+  const int64_t stride[3] = {1, m, (int64_t)m * m};
+  const double n2 = S.g.inv_h2;   // n^2, exact for n <= 2^26
+  GRID_LOOP(gid, N) {
     const int jj[3] = {(int)(gid % m) + 1, (int)((gid / m) % m) + 1,
                        dim == 3 ? (int)(gid / ((int64_t)m * m)) + 1 : 1};
-    const int64_t stride[3] = {1, m, (int64_t)m * m};
-    const double n2 = S.g.inv_h2;   // n^2, exact for n <= 2^26
-    for (int c = 0; c < nr; ++c) {
-      const double xhi = xh[gid * nr + c], xli = xl[gid * nr + c];
-      double sh = f[gid * nr + c], sl = 0.0;
-      for (int ax = 0; ax < dim; ++ax) {
-        for (int side = 0; side < 2; ++side) {
-          int lo[3] = {jj[0], jj[1], jj[2]};
-          if (side == 0) lo[ax] -= 1;
-          const double a = sbond(S, ax, lo[0], lo[1], lo[2]);
-          double wh, wl;
-          two_prod(a, n2, wh, wl);
-          const bool inner = side == 0 ? jj[ax] > 1 : jj[ax] < m;
+    double sh[R], sl[R];
+#pragma unroll
+    for (int c = 0; c < R; ++c) {
+      sh[c] = c < nr ? f[gid * nr + c] : 0.0;
+      sl[c] = 0.0;
+    }
+    for (int ax = 0; ax < dim; ++ax) {
+      for (int side = 0; side < 2; ++side) {
+        int lo[3] = {jj[0], jj[1], jj[2]};
+        if (side == 0) lo[ax] -= 1;
+        const double a = sbond(S, ax, lo[0], lo[1], lo[2]);
+        double wh, wl;
+        two_prod(a, n2, wh, wl);
+        const bool inner = side == 0 ? jj[ax] > 1 : jj[ax] < m;
+        const int64_t nb = side == 0 ? gid - stride[ax] : gid + stride[ax];
+#pragma unroll
+        for (int c = 0; c < R; ++c) {
+          if (c >= nr) continue;
+          const double xhi = xh[gid * nr + c], xli = xl[gid * nr + c];
           double dh, dl;
           if (inner) {
-            const int64_t nb = side == 0 ? gid - stride[ax] : gid + stride[ax];
             two_sum(xhi, -xh[nb * nr + c], dh, dl);
             dl += xli - xl[nb * nr + c];
           } else {
@@ -266,50 +319,52 @@ __global__ void k_dd_residual(Stencil S, int64_t N, const double* __restrict__ f
           two_prod(wh, dh, ph, pl);
           pl += wh * dl + wl * dh;
           double t, e;
-          two_sum(sh, -ph, t, e);
-          sh = t;
-          sl += e - pl;
+          two_sum(sh[c], -ph, t, e);
+          sh[c] = t;
+          sl[c] += e - pl;
         }
       }
-      {
-        double ph, pl;
-        two_prod(S.bnode[gid], xhi, ph, pl);
-        pl += S.bnode[gid] * xli;
-        double t, e;
-        two_sum(sh, -ph, t, e);
-        sh = t;
-        sl += e - pl;
-      }
-      const double r = sh + sl;
+    }
+    const double bv = S.bnode[gid];
+#pragma unroll
+    for (int c = 0; c < R; ++c) {
+      if (c >= nr) continue;
+      const double xhi = xh[gid * nr + c], xli = xl[gid * nr + c];
+      double ph, pl;
+      two_prod(bv, xhi, ph, pl);
+      pl += bv * xli;
+      double t, e;
+      two_sum(sh[c], -ph, t, e);
+      const double r = t + (sl[c] + e - pl);
       rout[gid * nr + c] = r;
-      vals[c] = r * r;
+      acc[c] = fma(r, r, acc[c]);
     }
   }
-  finish_reduce(vals, nr, partials, counter, nrm2);
+  grid_reduce<R>(acc, nr, partials, counter, nrm2);
 }
 
-// (xh, xl) += d for the active columns
+// (xh, xl) += d
 __global__ void k_dd_add(int64_t N, int nr, double* __restrict__ xh, double* __restrict__ xl,
                          const double* __restrict__ d) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= N * nr) return;
-  double s, err;
-  two_sum(xh[e], d[e], s, err);
-  err += xl[e];
-  double hi, lo;
-  two_sum(s, err, hi, lo);
-  xh[e] = hi;
-  xl[e] = lo;
+  GRID_LOOP(e, N * nr) {
+    double s, err;
+    two_sum(xh[e], d[e], s, err);
+    err += xl[e];
+    double hi, lo;
+    two_sum(s, err, hi, lo);
+    xh[e] = hi;
+    xl[e] = lo;
+  }
 }
 
 // copies between a strided user layout and the packed N x nr layout, with type conversion
 template <typename TI, typename TO>
 __global__ void k_convert(int64_t N, int nr, const TI* __restrict__ in, int ldi, TO* __restrict__ out, int ldo) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= N * nr) return;
-  const int64_t i = e / nr;
-  const int c = (int)(e % nr);
-  out[i * ldo + c] = (TO)in[i * ldi + c];
+  GRID_LOOP(e, N * nr) {
+    const int64_t i = e / nr;
+    const int c = (int)(e % nr);
+    out[i * ldo + c] = (TO)in[i * ldi + c];
+  }
 }
 
 // active[c] = (rr[c] > thr2[c])
@@ -319,71 +374,109 @@ __global__ void k_set_active(int nr, const double* rr, const double* thr2, int* 
 }
 
 // ---------------------------------------------------------------------------
-static inline int nblk(int64_t n) { return (int)((n + 255) / 256); }
+static inline int64_t grid_n(GridInfo g) { return (int64_t)g.m * g.m * (g.dim == 3 ? g.m : 1); }
+
+template <typename K>
+static void set_smem(K kern, size_t smem) {
+  if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+#define DISPATCH_R(nr, ...)                                     \
+  do {                                                          \
+    if ((nr) <= 1) { constexpr int R = 1; __VA_ARGS__; }        \
+    else if ((nr) <= 2) { constexpr int R = 2; __VA_ARGS__; }   \
+    else if ((nr) <= 4) { constexpr int R = 4; __VA_ARGS__; }   \
+    else if ((nr) <= 8) { constexpr int R = 8; __VA_ARGS__; }   \
+    else { constexpr int R = 16; __VA_ARGS__; }                 \
+  } while (0)
 
 void launch_matvec(GridInfo g, const double* a_stag, const double* b, const double* x, int ldx,
                    double* y, int ldy, int nr, cudaStream_t st) {
-  const int64_t N = (int64_t)g.m * g.m * (g.dim == 3 ? g.m : 1);
+  const int64_t N = grid_n(g);
   Stencil S{g, a_stag, b};
-  k_matvec<<<nblk(N), 256, 0, st>>>(S, N, x, ldx, y, ldy, nr);
+  for (int r0 = 0; r0 < nr; r0 += 16) {
+    const int c = nr - r0 < 16 ? nr - r0 : 16;
+    note_launches(1);
+    DISPATCH_R(c, k_matvec<R><<<vec_blocks(N), kVecThreads, 0, st>>>(S, N, x + r0, ldx, y + r0, ldy, c));
+  }
 }
 
 void launch_mv_dot(GridInfo g, const double* a_stag, const double* b, const double* p, double* q,
                    int nr, double* partials, unsigned* counter, double* pq, cudaStream_t st) {
-  const int64_t N = (int64_t)g.m * g.m * (g.dim == 3 ? g.m : 1);
+  const int64_t N = grid_n(g);
   Stencil S{g, a_stag, b};
-  k_mv_dot<<<nblk(N), 256, 0, st>>>(S, N, p, q, nr, partials, counter, pq);
+  const size_t smem = sizeof(double) * kVecThreads * nr;
+  DISPATCH_R(nr, set_smem(k_mv_dot<R>, smem); note_launches(1);
+                  k_mv_dot<R><<<vec_blocks(N), kVecThreads, smem, st>>>(S, N, p, q, nr, partials, counter, pq));
 }
 
 void launch_axpy2(int64_t N, int nr, double* x, double* r, const double* p, const double* q,
                   const double* rz, const double* pq, const int* active, double* alpha,
                   double* partials, unsigned* counter, double* rr, cudaStream_t st) {
-  k_axpy2<<<nblk(N), 256, 0, st>>>(N, nr, x, r, p, q, rz, pq, active, alpha, partials, counter, rr);
+  const size_t smem = sizeof(double) * kVecThreads * nr;
+  DISPATCH_R(nr, set_smem(k_axpy2<R>, smem); note_launches(1);
+                  k_axpy2<R><<<vec_blocks(N), kVecThreads, smem, st>>>(N, nr, x, r, p, q, rz, pq, active,
+                                                                     alpha, partials, counter, rr));
 }
 
 void launch_dot2(int64_t N, int nr, const double* r, const double* z, const double* q,
                  double* partials, unsigned* counter, double* out, cudaStream_t st) {
-  k_dot2<<<nblk(N), 256, 0, st>>>(N, nr, r, z, q, partials, counter, out);
+  const size_t smem = sizeof(double) * kVecThreads * 2 * nr;
+  DISPATCH_R(nr, set_smem(k_dot2<R>, smem); note_launches(1);
+                  k_dot2<R><<<vec_blocks(N), kVecThreads, smem, st>>>(N, nr, r, z, q, partials, counter, out));
 }
 
 void launch_update_p(int64_t N, int nr, double* p, const double* z, const double* alpha,
                      const double* rz_old, const double* rzzq, const int* active, int restart,
                      cudaStream_t st) {
-  k_update_p<<<nblk(N), 256, 0, st>>>(N, nr, p, z, alpha, rz_old, rzzq, active, restart);
+  note_launches(1);
+  DISPATCH_R(nr, k_update_p<R><<<vec_blocks(N), kVecThreads, 0, st>>>(N, nr, p, z, alpha, rz_old, rzzq,
+                                                                     active, restart));
 }
 
 void launch_residual(GridInfo g, const double* a_stag, const double* bn, const double* rhs,
                      const double* x, double* out, int nr, double* partials, unsigned* counter,
                      double* nrm2, cudaStream_t st) {
-  const int64_t N = (int64_t)g.m * g.m * (g.dim == 3 ? g.m : 1);
+  const int64_t N = grid_n(g);
   Stencil S{g, a_stag, bn};
-  k_residual<<<nblk(N), 256, 0, st>>>(S, N, rhs, x, out, nr, partials, counter, nrm2);
+  const size_t smem = sizeof(double) * kVecThreads * nr;
+  DISPATCH_R(nr, set_smem(k_residual<R>, smem); note_launches(1);
+                  k_residual<R><<<vec_blocks(N), kVecThreads, smem, st>>>(S, N, rhs, x, out, nr, partials,
+                                                                        counter, nrm2));
 }
 
 void launch_sqnorm(int64_t N, int nr, const double* v, double* partials, unsigned* counter,
                    double* out, cudaStream_t st) {
-  k_sqnorm<<<nblk(N), 256, 0, st>>>(N, nr, v, partials, counter, out);
+  const size_t smem = sizeof(double) * kVecThreads * nr;
+  DISPATCH_R(nr, set_smem(k_sqnorm<R>, smem); note_launches(1);
+                  k_sqnorm<R><<<vec_blocks(N), kVecThreads, smem, st>>>(N, nr, v, partials, counter, out));
 }
 
 void launch_dd_residual(GridInfo g, const double* a_stag, const double* bn, const double* f,
                         const double* xh, const double* xl, double* r, int nr, double* partials,
                         unsigned* counter, double* nrm2, cudaStream_t st) {
-  const int64_t N = (int64_t)g.m * g.m * (g.dim == 3 ? g.m : 1);
+  const int64_t N = grid_n(g);
   Stencil S{g, a_stag, bn};
-  k_dd_residual<<<nblk(N), 256, 0, st>>>(S, N, f, xh, xl, r, nr, partials, counter, nrm2);
+  const size_t smem = sizeof(double) * kVecThreads * nr;
+  DISPATCH_R(nr, set_smem(k_dd_residual<R>, smem); note_launches(1);
+                  k_dd_residual<R><<<vec_blocks(N), kVecThreads, smem, st>>>(S, N, f, xh, xl, r, nr, partials,
+                                                                           counter, nrm2));
 }
 
 void launch_dd_add(int64_t N, int nr, double* xh, double* xl, const double* d, cudaStream_t st) {
-  k_dd_add<<<nblk(N * nr), 256, 0, st>>>(N, nr, xh, xl, d);
+  note_launches(1);
+  k_dd_add<<<vec_blocks(N * nr), kVecThreads, 0, st>>>(N, nr, xh, xl, d);
 }
 
 void launch_set_active(int nr, const double* rr, const double* thr2, int* active, cudaStream_t st) {
+  note_launches(1);
   k_set_active<<<1, 32, 0, st>>>(nr, rr, thr2, active);
 }
 
 template <typename TI, typename TO>
 void launch_convert(int64_t N, int nr, const TI* in, int ldi, TO* out, int ldo, cudaStream_t st) {
-  k_convert<TI, TO><<<nblk(N * nr), 256, 0, st>>>(N, nr, in, ldi, out, ldo);
+  note_launches(1);
+  k_convert<TI, TO><<<vec_blocks(N * nr), kVecThreads, 0, st>>>(N, nr, in, ldi, out, ldo);
 }
 template void launch_convert<double, double>(int64_t, int, const double*, int, double*, int, cudaStream_t);
 template void launch_convert<double, float>(int64_t, int, const double*, int, float*, int, cudaStream_t);

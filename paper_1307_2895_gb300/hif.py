@@ -18,7 +18,7 @@ from . import build as _build
 
 HIF_OK, HIF_ERR_ARG, HIF_ERR_NOT_SPD, HIF_ERR_NOCONV, HIF_ERR_TIMEOUT, HIF_ERR_CUDA, HIF_ERR_OOM = range(7)
 VARIANTS = {"mf": 0, "hifde": 1}
-PRECISIONS = {"fp64": 0, "mixed": 1}
+PRECISIONS = {"fp64": 0, "mixed": 1, "fp32_apply": 2}
 APPLY_F, APPLY_FINV = 0, 1
 
 
@@ -51,9 +51,14 @@ class _Stats(ctypes.Structure):
                 ("apply_bytes", ctypes.c_double), ("t_factor_ms", ctypes.c_double)]
 
 
+class _Profile(ctypes.Structure):
+    _fields_ = [("sweep_ms", ctypes.c_double), ("sweep_launches", ctypes.c_longlong),
+                ("sweep_bytes", ctypes.c_double)]
+
+
 _LIB = None
 EXPORTS = ["hif_factor", "hif_apply", "hif_solve", "hif_matvec", "hif_stats", "hif_structure",
-           "hif_free", "hif_last_error"]
+           "hif_profile", "hif_kernel_launches", "hif_free", "hif_last_error"]
 
 
 def library_path() -> str:
@@ -84,6 +89,10 @@ def load(build_if_missing: bool = False):
     lib.hif_stats.restype = i
     lib.hif_structure.argtypes = [vp, vp, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)]
     lib.hif_structure.restype = i
+    lib.hif_profile.argtypes = [vp, i, ctypes.POINTER(_Profile)]
+    lib.hif_profile.restype = i
+    lib.hif_kernel_launches.argtypes = []
+    lib.hif_kernel_launches.restype = ctypes.c_longlong
     lib.hif_free.argtypes = [vp]
     lib.hif_free.restype = None
     lib.hif_last_error.argtypes = []
@@ -163,11 +172,12 @@ class Factorization:
         return y.reshape(x.shape)
 
     def solve(self, rhs, tol: float = 1e-12, maxit: int = 200, raise_on_noconv: bool = False,
-              want_lo: bool = False):
+              want_lo: bool = False, out=None):
         """PCG with F^-1 as preconditioner (double-double refinement); returns
-        (x, info dict) or (x_hi, x_lo, info) with ``want_lo``."""
+        (x, info dict) or (x_hi, x_lo, info) with ``want_lo``.  ``out`` (same
+        shape as rhs, contiguous float64) receives x if given."""
         r2 = _as_2d(rhs)
-        x = _empty_like(rhs, r2.shape)
+        x = _empty_like(rhs, r2.shape) if out is None else out.reshape(r2.shape)
         xlo = _empty_like(rhs, r2.shape) if want_lo else None
         info = _SolveInfo()
         rc = self._lib.hif_solve(self._live(), _ptr(r2), _ptr(x), _ptr(xlo), r2.shape[1], r2.shape[1], tol,
@@ -179,6 +189,12 @@ class Factorization:
         if want_lo:
             return x.reshape(rhs.shape), xlo.reshape(rhs.shape), d
         return x.reshape(rhs.shape), d
+
+    def profile(self, enable: bool = True) -> dict:
+        """Sweep timing since the previous call (then reset); toggles recording."""
+        p = _Profile()
+        _check(self._lib.hif_profile(self._live(), 1 if enable else 0, ctypes.byref(p)), self._lib)
+        return dict(sweep_ms=p.sweep_ms, sweep_launches=p.sweep_launches, sweep_bytes=p.sweep_bytes)
 
     def stats(self) -> dict:
         s = _Stats()
@@ -213,6 +229,11 @@ class Factorization:
             self.free()
         except Exception:
             pass
+
+
+def kernel_launches() -> int:
+    """Kernels launched by the CUDA library so far in this process."""
+    return int(load().hif_kernel_launches())
 
 
 def factor(dim: int, n: int, a_stag, b, eps: float, variant: str = "hifde", precision: str = "fp64",

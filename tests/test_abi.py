@@ -15,7 +15,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def _declared():
     src = open(os.path.join(ROOT, "include", "hif.h")).read()
-    return sorted(set(re.findall(r"^\s*(?:int|void|const char\*)\s+(hif_\w+)\s*\(", src, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:int|void|long long|const char\*)\s+(hif_\w+)\s*\(", src, re.M)))
 
 
 def test_library_exports_header_symbols():
