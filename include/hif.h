@@ -180,6 +180,26 @@ int hif_profile(hif_handle* h, int enable, hif_profile_t* out);
 /* hif_kernel_launches -- kernels launched by this library in this process. */
 long long hif_kernel_launches(void);
 
+/*
+ * hif_residual_norms_noalloc -- rnorm2[r] = ||f_r - A x_r||_2^2 (FP64) for the
+ * stencil operator of a grid, computed without allocating any device memory.
+ * The paper has no counterpart: this serves callers that cannot call
+ * cudaMalloc where they check a solution (inside another library's allocator
+ * callback or memory-managed region, or where an allocation must not
+ * synchronize the device).  All pointers are device pointers: a_stag, b as
+ * for hif_factor; f and x are N x nrhs with row stride ld; rnorm2 receives
+ * nrhs doubles.  Work is queued on stream (a cudaStream_t, NULL = legacy
+ * default stream); the call returns once the kernels are queued.
+ * Limits: 1 <= nrhs <= 16 per call (HIF_ERR_ARG otherwise).  The reduction
+ * scratch is one fixed 38 KB device array of the library, held by every GPU
+ * that loads it until exit and shared by all calls: calls that overlap on the
+ * GPU race.  The first call on a device looks up that array's address (with
+ * the device current); make it before any stream capture.
+ */
+int hif_residual_norms_noalloc(int dim, int n, const double* a_stag, const double* b,
+                               const double* f, const double* x, int nrhs, int ld,
+                               double* rnorm2, void* stream);
+
 /* hif_free -- release the factor (stream-ordered on the handle's stream). */
 void hif_free(hif_handle* h);
 

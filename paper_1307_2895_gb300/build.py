@@ -17,7 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libhif.so")
-SOURCES = ["kernels_factor.cu", "kernels_apply.cu", "kernels_solve.cu", "hif_api.cu", "geometry.cpp"]
+SOURCES = ["kernels_factor.cu", "kernels_apply.cu", "kernels_solve.cu", "hif_api.cu", "geometry.cpp",
+           "noalloc.cu"]
 HEADERS = ["hif_internal.h", "kernels.h", "blockops.cuh", "geometry.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

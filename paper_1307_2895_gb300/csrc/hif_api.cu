@@ -714,6 +714,8 @@ int solve_chunk(hif_handle* h, const double* rhs, double* x, double* xlo, int nr
 
 }  // namespace
 
+void hif::set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
+
 // ===========================================================================
 // C ABI
 // ===========================================================================

@@ -51,6 +51,9 @@ struct ApplyDesc {
 // Process-wide count of kernel launches issued by the library.
 void note_launches(long long n);
 
+// Message returned by hif_last_error() on the calling thread.
+void set_last_error(const char* msg);
+
 struct GridInfo {
   int dim, n, m;       // m = n - 1 nodes per axis
   double inv_h2;

@@ -58,7 +58,7 @@ class _Profile(ctypes.Structure):
 
 _LIB = None
 EXPORTS = ["hif_factor", "hif_apply", "hif_solve", "hif_matvec", "hif_stats", "hif_structure",
-           "hif_profile", "hif_kernel_launches", "hif_free", "hif_last_error"]
+           "hif_profile", "hif_kernel_launches", "hif_residual_norms_noalloc", "hif_free", "hif_last_error"]
 
 
 def library_path() -> str:
@@ -93,6 +93,8 @@ def load(build_if_missing: bool = False):
     lib.hif_profile.restype = i
     lib.hif_kernel_launches.argtypes = []
     lib.hif_kernel_launches.restype = ctypes.c_longlong
+    lib.hif_residual_norms_noalloc.argtypes = [i, i, vp, vp, vp, vp, i, i, vp, vp]
+    lib.hif_residual_norms_noalloc.restype = i
     lib.hif_free.argtypes = [vp]
     lib.hif_free.restype = None
     lib.hif_last_error.argtypes = []
@@ -229,6 +231,16 @@ class Factorization:
             self.free()
         except Exception:
             pass
+
+
+def residual_norms_noalloc(dim: int, n: int, a_stag, b, f, x, out, stream=None) -> None:
+    """hif_residual_norms_noalloc on CUDA tensors: out[r] = ||f_r - A x_r||^2.
+    Allocates nothing on the device (the library's fixed scratch is used)."""
+    lib = load()
+    f2, x2 = _as_2d(f), _as_2d(x)
+    rc = lib.hif_residual_norms_noalloc(dim, n, _ptr(a_stag), _ptr(b), _ptr(f2), _ptr(x2), f2.shape[1],
+                                        f2.shape[1], _ptr(out), _stream_ptr(stream))
+    _check(rc, lib)
 
 
 def kernel_launches() -> int:
