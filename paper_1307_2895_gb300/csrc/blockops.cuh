@@ -133,6 +133,20 @@ __device__ void blk_syrk_sub(T* C, int ldc, const T* G, int ldg, int m, int kk) 
   __syncthreads();
 }
 
+// Pack the lower triangle of A (n x n, ld) by rows into P.
+template <typename T>
+__device__ void blk_pack_lower(const T* A, int lda, T* P, int n) {
+  const int64_t tot = (int64_t)n * (n + 1) / 2;
+  for (int64_t e = threadIdx.x; e < tot; e += blockDim.x) {
+    int i = (int)((sqrt(8.0 * (double)e + 1.0) - 1.0) * 0.5);
+    while ((int64_t)(i + 1) * (i + 2) / 2 <= e) ++i;
+    while ((int64_t)i * (i + 1) / 2 > e) --i;
+    const int t = (int)(e - (int64_t)i * (i + 1) / 2);
+    P[e] = A[(int64_t)i * lda + t];
+  }
+  __syncthreads();
+}
+
 template <typename T>
 __device__ void blk_copy(const T* A, int lda, T* B, int ldb, int m, int n) {
   for (int64_t e = threadIdx.x; e < (int64_t)m * n; e += blockDim.x) {

@@ -17,7 +17,12 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <tuple>
 #include <string>
 #include <utility>
 #include <vector>
@@ -106,15 +111,43 @@ struct SweepLevel {
   int nblocks = 0, max_np = 0, max_nq = 0;
   double fac_elems = 0.0;   // factor elements one F^-1 sweep reads (Linv lower, G, T)
   double vec_rows = 0.0;    // vector rows it gathers and writes back (sum of np + nq)
-  DevBuf desc;    // ApplyDesc[nblocks]
-  DevBuf ipool;   // ids
+  const ApplyDesc* desc = nullptr;   // device, ApplyDesc[nblocks]
+  const int* ipool = nullptr;        // device ids
+  DevBuf desc_own, ipool_own;        // owned storage behind desc / ipool when not shared
   DevBuf fac;     // factor pool
-  DevBuf fac32;   // float copy (root in mixed precision)
+  DevBuf fac32;   // float copy (FP32 apply of a double factor, or the root in mixed precision)
 };
 
-struct FrontInfo {
-  int level;
-  std::vector<int> c, sk;
+// Skeleton structure of one fractional level (for hif_structure).
+struct LevelFronts {
+  int level = 0;
+  std::shared_ptr<const std::vector<HostFront>> fr;
+  std::shared_ptr<const std::vector<FrontDesc>> fd;
+  std::vector<int> out;     // host copy of the front kernel's outputs
+};
+
+// Rank-independent structure of level 0 of one grid (cells and the fronts of
+// level 1/2 depend only on dim, n and the leaf size): built once, then shared
+// read-only by every factorization of that grid.  Device copies live for the
+// rest of the process.
+struct Level0 {
+  std::vector<HostCell> cells;
+  std::vector<CellDesc> cdesc;
+  int64_t work_elems = 0, fac_elems = 0;
+  int max_nI = 0;
+  int cap_max_np = 0, cap_max_nq = 0;
+  double cap_fac_elems = 0.0, cap_vec_rows = 0.0;
+  std::vector<int> alive1;   // DOFs active after the level-0 elimination
+  std::shared_ptr<std::vector<HostFront>> fronts;
+  std::shared_ptr<std::vector<FrontDesc>> fdesc;
+  int64_t fwork_elems = 0, ffac_elems = 0, fout_elems = 0;
+  int max_nc = 0, max_nN = 0;
+  int* d_cls0 = nullptr;
+  CellDesc* d_cdesc = nullptr;
+  int* d_cipool = nullptr;
+  ApplyDesc* d_capply = nullptr;
+  FrontDesc* d_fdesc = nullptr;
+  int* d_fip = nullptr;
 };
 
 }  // namespace
@@ -127,10 +160,12 @@ struct hif_handle {
   int skip_levels = 0;
   double eps = 0.0;
   cudaStream_t st = nullptr;
+  cudaStream_t own_stream = nullptr;   // created when the caller passes no stream
   DevBuf a_stag, bnode;
+  std::shared_ptr<const Level0> level0;
   std::vector<SweepLevel> cells, fronts;   // levels 0..L-1
   SweepLevel root;                         // level L
-  std::vector<FrontInfo> finfo;
+  std::vector<LevelFronts> finfo;
   int root_size = 0, n_cells = 0, n_fronts = 0, max_rank = 0, near = 0, clamped = 0;
   long long factor_bytes = 0;
   double factor_flops = 0.0, apply_bytes = 0.0, t_factor_ms = 0.0;
@@ -140,6 +175,9 @@ struct hif_handle {
   size_t ev_used = 0;
   double prof_ms = 0.0, prof_bytes = 0.0;
   long long prof_launches = 0;
+  // sweep bytes and launches of one replay of the preconditioner graph
+  double graph_bytes = 0.0;
+  long long graph_launches = 0;
   ~hif_handle() {
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
   }
@@ -147,28 +185,17 @@ struct hif_handle {
 
 namespace {
 
-struct CellLevelDev {
-  std::vector<CellDesc> desc;
-  DevBuf d_desc;
-  int max_nI = 0;
-  void swap(CellLevelDev& o) {
-    desc.swap(o.desc);
-    d_desc.swap(o.d_desc);
-    std::swap(max_nI, o.max_nI);
-  }
-};
-
 void prepare_cells(const Geometry& G, int l, const std::vector<HostCell>& cells,
-                   const std::vector<HostCell>* prev, CellLevelDev& out, std::vector<int>& ipool,
-                   int64_t& work_elems, int64_t& fac_elems) {
-  out.desc.resize(cells.size());
+                   const std::vector<HostCell>* prev, std::vector<CellDesc>& desc, std::vector<int>& ipool,
+                   int64_t& work_elems, int64_t& fac_elems, int& max_nI) {
+  desc.resize(cells.size());
   ipool.clear();
   work_elems = fac_elems = 0;
-  out.max_nI = 0;
+  max_nI = 0;
   std::vector<int> cmap;
   for (size_t i = 0; i < cells.size(); ++i) {
     const HostCell& c = cells[i];
-    CellDesc& d = out.desc[i];
+    CellDesc& d = desc[i];
     d.nI = (int)c.I.size();
     d.nB = (int)c.B.size();
     d.cell_lin = (int)i;
@@ -176,9 +203,9 @@ void prepare_cells(const Geometry& G, int l, const std::vector<HostCell>& cells,
     ipool.insert(ipool.end(), c.I.begin(), c.I.end());
     ipool.insert(ipool.end(), c.B.begin(), c.B.end());
     d.F = work_elems;
-    work_elems += (int64_t)d.nI * d.nI + (int64_t)d.nB * d.nI + (int64_t)d.nB * d.nB;
+    work_elems += 2 * (int64_t)d.nI * d.nI + (int64_t)d.nB * d.nI + (int64_t)d.nB * d.nB;
     d.fac = fac_elems;
-    fac_elems += 2 * (int64_t)d.nI * d.nI + (int64_t)d.nB * d.nI;
+    fac_elems += cell_fac_size(d.nI, d.nB);
     for (int s = 0; s < kMaxChild; ++s) d.child[s] = -1;
     d.cmap = -1;
     if (l > 0 && prev) {
@@ -186,33 +213,114 @@ void prepare_cells(const Geometry& G, int l, const std::vector<HostCell>& cells,
       d.cmap = (int64_t)ipool.size();
       ipool.insert(ipool.end(), cmap.begin(), cmap.end());
     }
-    out.max_nI = std::max(out.max_nI, d.nI);
+    max_nI = std::max(max_nI, d.nI);
   }
 }
 
-void cell_apply_descs(SweepLevel& S, const std::vector<CellDesc>& cd, cudaStream_t st) {
-  std::vector<ApplyDesc> ad;
+// Apply descriptors of the cells of a level and the sweep statistics.
+void cell_apply_descs(const std::vector<CellDesc>& cd, std::vector<ApplyDesc>& ad, int& max_np, int& max_nq,
+                      double& fac_elems, double& vec_rows) {
+  ad.clear();
   ad.reserve(cd.size());
-  S.max_np = S.max_nq = 0;
+  max_np = max_nq = 0;
+  fac_elems = vec_rows = 0.0;
   for (const CellDesc& c : cd) {
     ApplyDesc a;
     a.np = c.nI;
     a.nq = c.nB;
     a.ids = c.ids;
     a.Linv = c.fac;
-    a.L = c.fac + (int64_t)c.nI * c.nI;
-    a.G = c.fac + 2 * (int64_t)c.nI * c.nI;
+    a.G = c.fac + cell_fac_G(c.nI);
+    a.L = c.fac + cell_fac_L(c.nI, c.nB);
     a.T = -1;
     ad.push_back(a);
-    S.max_np = std::max(S.max_np, c.nI);
-    S.max_nq = std::max(S.max_nq, c.nB);
+    max_np = std::max(max_np, c.nI);
+    max_nq = std::max(max_nq, c.nB);
     if (c.nI > 0) {
-      S.fac_elems += 0.5 * c.nI * (c.nI + 1.0) + (double)c.nB * c.nI;
-      S.vec_rows += c.nI + c.nB;
+      fac_elems += 0.5 * c.nI * (c.nI + 1.0) + (double)c.nB * c.nI;
+      vec_rows += c.nI + c.nB;
     }
   }
-  S.nblocks = (int)ad.size();
-  upload(S.desc, ad, st);
+}
+
+// Descriptors of the fronts of one fractional level.
+void prepare_fronts(const std::vector<HostFront>& fr, std::vector<FrontDesc>& fd, std::vector<int>& ip,
+                    int64_t& work_elems, int64_t& fac_elems, int64_t& out_elems, int& max_nc, int& max_nN) {
+  const int nf = (int)fr.size();
+  fd.resize(nf);
+  ip.clear();
+  work_elems = fac_elems = out_elems = 0;
+  max_nc = max_nN = 0;
+  for (int f = 0; f < nf; ++f) {
+    const HostFront& F = fr[f];
+    FrontDesc& d = fd[f];
+    d.nc = (int)F.c.size();
+    d.nN = (int)F.N.size();
+    d.P1 = F.P1;
+    d.P2 = F.P2;
+    d.ids = (int64_t)ip.size();
+    ip.insert(ip.end(), F.c.begin(), F.c.end());
+    ip.insert(ip.end(), F.pos1.begin(), F.pos1.end());
+    ip.insert(ip.end(), F.pos2.begin(), F.pos2.end());
+    d.out = out_elems;
+    out_elems += 1 + 2 * d.nc;
+    d.work = work_elems;
+    work_elems += (int64_t)d.nN * d.nc + 4 * (int64_t)d.nc * d.nc;
+    d.fac = fac_elems;
+    fac_elems += front_fac_size(d.nc);
+    max_nc = std::max(max_nc, d.nc);
+    max_nN = std::max(max_nN, d.nN);
+  }
+}
+
+template <typename T>
+T* dev_copy(const std::vector<T>& v) {
+  T* p = nullptr;
+  if (v.empty()) return nullptr;
+  CU(cudaMalloc(&p, v.size() * sizeof(T)));
+  CU(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return p;
+}
+
+std::mutex g_l0_mutex;
+std::map<std::tuple<int, int, int, int>, std::shared_ptr<Level0>> g_l0_cache;
+
+std::shared_ptr<const Level0> get_level0(const Geometry& G) {
+  int dev = 0;
+  CU(cudaGetDevice(&dev));
+  const auto key = std::make_tuple(dev, G.dim, G.n, G.leaf);
+  std::lock_guard<std::mutex> lock(g_l0_mutex);
+  auto it = g_l0_cache.find(key);
+  if (it != g_l0_cache.end()) return it->second;
+  auto L0 = std::make_shared<Level0>();
+  std::vector<int> alive(G.N);
+  for (int64_t g = 0; g < G.N; ++g) alive[g] = (int)g;
+  build_cells(G, 0, alive, L0->cells);
+  std::vector<int> cip;
+  prepare_cells(G, 0, L0->cells, nullptr, L0->cdesc, cip, L0->work_elems, L0->fac_elems, L0->max_nI);
+  std::vector<ApplyDesc> ad;
+  cell_apply_descs(L0->cdesc, ad, L0->cap_max_np, L0->cap_max_nq, L0->cap_fac_elems, L0->cap_vec_rows);
+  std::vector<char> inner(G.N, 0);
+  for (const HostCell& c : L0->cells)
+    for (int g : c.I) inner[g] = 1;
+  for (int g : alive)
+    if (!inner[g]) L0->alive1.push_back(g);
+  L0->fronts = std::make_shared<std::vector<HostFront>>();
+  L0->fdesc = std::make_shared<std::vector<FrontDesc>>();
+  std::vector<int> mark;
+  build_fronts(G, 0, L0->alive1, L0->cells, *L0->fronts, mark);
+  std::vector<int> fip;
+  prepare_fronts(*L0->fronts, *L0->fdesc, fip, L0->fwork_elems, L0->ffac_elems, L0->fout_elems, L0->max_nc,
+                 L0->max_nN);
+  L0->d_cls0 = dev_copy(G.cls[0]);
+  L0->d_cdesc = dev_copy(L0->cdesc);
+  L0->d_cipool = dev_copy(cip);
+  L0->d_capply = dev_copy(ad);
+  L0->d_fdesc = dev_copy(*L0->fdesc);
+  L0->d_fip = dev_copy(fip);
+  if (g_l0_cache.size() >= 16) g_l0_cache.clear();   // handles keep their own reference
+  g_l0_cache[key] = L0;
+  return L0;
 }
 
 template <typename T>
@@ -220,10 +328,9 @@ struct Factorizer {
   hif_handle* h;
   const Geometry& G;
   cudaStream_t st;
-  DevBuf status, d_cls0;
+  DevBuf status;
   std::vector<char> dead;
   std::vector<int> mark;
-
   // pivot floor of the safeguarded Cholesky: every block in mixed precision
   // (including the FP64 root, whose entries carry FP32 rounding), none in FP64
   double tau = 0.0;
@@ -245,59 +352,87 @@ struct Factorizer {
   }
 
   void run() {
-    const int L = G.L, dim = G.dim, nchild = 1 << dim;
+    const int L = G.L, nchild = 1 << G.dim;
     status.alloc(2 * sizeof(int), st);
     CU(cudaMemsetAsync(status.p, 0, 2 * sizeof(int), st));
-    upload(d_cls0, G.cls[0], st);
     dead.assign(G.N, 0);
-    std::vector<int> alive(G.N);
-    for (int64_t g = 0; g < G.N; ++g) alive[g] = (int)g;
-
-    std::vector<HostCell> prev_cells, cells;
-    CellLevelDev prev_dev, cur_dev;
-    DevBuf prev_work, work;
-    std::vector<int> ipool;
     h->cells.resize(L);
     h->fronts.resize(L);
     const bool skel = (h->variant == HIF_VARIANT_HIFDE) && h->eps > 0.0;
+    std::shared_ptr<const Level0> L0 = get_level0(G);
+    h->level0 = L0;
 
-    for (int l = 0; l <= L; ++l) {
+    // ---- level 0: the cached structure
+    DevBuf work, prev_work;
+    {
+      SweepLevel& sw = h->cells[0];
+      work.alloc((size_t)L0->work_elems * sizeof(T), st);
+      sw.fac.alloc((size_t)L0->fac_elems * sizeof(T), st);
+      const int nc0 = (int)L0->cdesc.size();
+      launch_leaf_assemble<T>(L0->d_cdesc, nc0, L0->d_cipool, work.as<T>(), h->gi, h->a_stag.as<double>(),
+                              h->bnode.as<double>(), L0->d_cls0, G.ncell[0], st);
+      launch_cell_factor<T>(L0->d_cdesc, nc0, work.as<T>(), sw.fac.as<T>(), status.as<int>(), L0->max_nI, tau,
+                            st);
+      CU(cudaGetLastError());
+      sw.nblocks = nc0;
+      sw.desc = L0->d_capply;
+      sw.ipool = L0->d_cipool;
+      sw.max_np = L0->cap_max_np;
+      sw.max_nq = L0->cap_max_nq;
+      sw.fac_elems = L0->cap_fac_elems;
+      sw.vec_rows = L0->cap_vec_rows;
+      account_cells(L0->cdesc, sizeof(T));
+    }
+    std::vector<int> alive = L0->alive1;
+    if (skel && 0 >= h->skip_levels) {
+      run_fronts(0, L0->d_cdesc, work, alive, L0->fronts, L0->fdesc, L0->d_fdesc, L0->d_fip, L0->fwork_elems,
+                 L0->ffac_elems, L0->fout_elems, L0->max_nc, L0->max_nN);
+    }
+    const std::vector<HostCell>* prev_cells = &L0->cells;
+    const CellDesc* prev_ddesc = L0->d_cdesc;
+    std::vector<HostCell> cells_a, cells_b;
+    DevBuf ddesc_a, ddesc_b;
+    prev_work.swap(work);
+
+    // ---- levels 1 .. L (L: the root, a cell without boundary)
+    for (int l = 1; l <= L; ++l) {
       const bool is_root = (l == L);
+      std::vector<HostCell>& cells = (l & 1) ? cells_a : cells_b;
+      DevBuf& ddesc = (l & 1) ? ddesc_a : ddesc_b;
       build_cells(G, l, alive, cells);
+      std::vector<CellDesc> cdesc;
+      std::vector<int> ipool;
       int64_t work_elems = 0, fac_elems = 0;
+      int max_nI = 0;
+      prepare_cells(G, l, cells, prev_cells, cdesc, ipool, work_elems, fac_elems, max_nI);
       SweepLevel& sw = is_root ? h->root : h->cells[l];
-      prepare_cells(G, l, cells, l > 0 ? &prev_cells : nullptr, cur_dev, ipool, work_elems,
-                    fac_elems);
-      upload(cur_dev.d_desc, cur_dev.desc, st);
-      upload(sw.ipool, ipool, st);
+      upload(ddesc, cdesc, st);
+      upload(sw.ipool_own, ipool, st);
+      sw.ipool = sw.ipool_own.as<int>();
       const int ncells = (int)cells.size();
       const size_t esz = is_root ? sizeof(double) : sizeof(T);
       work.alloc((size_t)work_elems * esz, st);
       sw.fac.alloc((size_t)fac_elems * esz, st);
-      const CellDesc* dd = cur_dev.d_desc.as<CellDesc>();
+      const CellDesc* dd = ddesc.as<CellDesc>();
       if (is_root) {
-        launch_extend_add<T, double>(dd, ncells, sw.ipool.as<int>(), work.as<double>(),
-                                     prev_dev.d_desc.as<CellDesc>(), prev_work.as<T>(), nchild, st);
-        launch_cell_factor<double>(dd, ncells, work.as<double>(), sw.fac.as<double>(),
-                                   status.as<int>(), cur_dev.max_nI, tau, st);
-      } else if (l == 0) {
-        launch_leaf_assemble<T>(dd, ncells, sw.ipool.as<int>(), work.as<T>(), h->gi,
-                                h->a_stag.as<double>(), h->bnode.as<double>(), d_cls0.as<int>(),
-                                G.ncell[0], st);
-        launch_cell_factor<T>(dd, ncells, work.as<T>(), sw.fac.as<T>(), status.as<int>(),
-                              cur_dev.max_nI, tau, st);
+        launch_extend_add<T, double>(dd, ncells, sw.ipool, work.as<double>(), prev_ddesc, prev_work.as<T>(),
+                                     nchild, st);
+        launch_cell_factor<double>(dd, ncells, work.as<double>(), sw.fac.as<double>(), status.as<int>(), max_nI,
+                                   tau, st);
       } else {
-        launch_extend_add<T, T>(dd, ncells, sw.ipool.as<int>(), work.as<T>(),
-                                prev_dev.d_desc.as<CellDesc>(), prev_work.as<T>(), nchild, st);
-        launch_cell_factor<T>(dd, ncells, work.as<T>(), sw.fac.as<T>(), status.as<int>(),
-                              cur_dev.max_nI, tau, st);
+        launch_extend_add<T, T>(dd, ncells, sw.ipool, work.as<T>(), prev_ddesc, prev_work.as<T>(), nchild, st);
+        launch_cell_factor<T>(dd, ncells, work.as<T>(), sw.fac.as<T>(), status.as<int>(), max_nI, tau, st);
       }
       CU(cudaGetLastError());
-      cell_apply_descs(sw, cur_dev.desc, st);
-      account_cells(cur_dev.desc, esz);
+      std::vector<ApplyDesc> ad;
+      cell_apply_descs(cdesc, ad, sw.max_np, sw.max_nq, sw.fac_elems, sw.vec_rows);
+      sw.nblocks = (int)ad.size();
+      upload(sw.desc_own, ad, st);
+      sw.desc = sw.desc_own.as<ApplyDesc>();
+      account_cells(cdesc, esz);
       prev_work.release();           // the level l-1 updates have been consumed
       if (is_root) {
-        h->root_size = cur_dev.desc.empty() ? 0 : cur_dev.desc[0].nI;
+        h->root_size = cdesc.empty() ? 0 : cdesc[0].nI;
         if (sizeof(T) == sizeof(float) && fac_elems > 0) {
           sw.fac32.alloc((size_t)fac_elems * sizeof(float), st);
           launch_convert<double, float>(fac_elems, 1, sw.fac.as<double>(), 1, sw.fac32.as<float>(), 1, st);
@@ -305,19 +440,30 @@ struct Factorizer {
         work.release();
         break;
       }
-      // the eliminated interiors leave the active set
-      {
-        std::vector<int> next;
-        next.reserve(alive.size());
+      {   // the eliminated interiors leave the active set
         for (const HostCell& c : cells)
           for (int g : c.I) dead[g] = 1;
+        std::vector<int> next;
+        next.reserve(alive.size());
         for (int g : alive)
           if (!dead[g]) next.push_back(g);
         alive.swap(next);
       }
-      if (skel && l >= h->skip_levels) run_fronts(l, cells, cur_dev, work, alive);
-      prev_cells.swap(cells);
-      prev_dev.swap(cur_dev);
+      if (skel && l >= h->skip_levels) {
+        auto fr = std::make_shared<std::vector<HostFront>>();
+        build_fronts(G, l, alive, cells, *fr, mark);
+        auto fd = std::make_shared<std::vector<FrontDesc>>();
+        std::vector<int> ip;
+        int64_t fw = 0, ff = 0, fo = 0;
+        int mnc = 0, mnN = 0;
+        prepare_fronts(*fr, *fd, ip, fw, ff, fo, mnc, mnN);
+        DevBuf d_fd, d_ip;
+        upload(d_fd, *fd, st);
+        upload(d_ip, ip, st);
+        run_fronts(l, dd, work, alive, fr, fd, d_fd.as<FrontDesc>(), d_ip.as<int>(), fw, ff, fo, mnc, mnN);
+      }
+      prev_cells = &cells;
+      prev_ddesc = dd;
       prev_work.swap(work);
     }
     int hs2[2] = {0, 0};
@@ -328,48 +474,29 @@ struct Factorizer {
     if (hs & 1) throw HifError(HIF_ERR_NOT_SPD, "non-positive pivot in a diagonal-block Cholesky");
   }
 
-  void run_fronts(int l, const std::vector<HostCell>& cells, CellLevelDev& cdev, DevBuf& cwork,
-                  std::vector<int>& alive) {
-    std::vector<HostFront> fr;
-    build_fronts(G, l, alive, cells, fr, mark);
+  // One launch for every front of level l + 1/2, then read back ranks and
+  // skeletons, build the apply descriptors and drop the redundant DOFs.
+  void run_fronts(int l, const CellDesc* d_cdesc, DevBuf& cwork, std::vector<int>& alive,
+                  std::shared_ptr<const std::vector<HostFront>> fr, std::shared_ptr<const std::vector<FrontDesc>> fdp,
+                  const FrontDesc* d_fd, const int* d_ip, int64_t work_elems, int64_t fac_elems,
+                  int64_t out_elems, int max_nc, int max_nN) {
+    const std::vector<FrontDesc>& fd = *fdp;
+    const int nf = (int)fd.size();
     SweepLevel& sw = h->fronts[l];
-    if (fr.empty()) return;
-    const int nf = (int)fr.size();
-    std::vector<FrontDesc> fd(nf);
-    std::vector<int> ip;
-    int64_t work_elems = 0, fac_elems = 0;
-    int max_nc = 0, max_nN = 0;
-    for (int f = 0; f < nf; ++f) {
-      const HostFront& F = fr[f];
-      FrontDesc& d = fd[f];
-      d.nc = (int)F.c.size();
-      d.nN = (int)F.N.size();
-      d.P1 = F.P1;
-      d.P2 = F.P2;
-      d.ids = (int64_t)ip.size();
-      ip.insert(ip.end(), F.c.begin(), F.c.end());
-      ip.insert(ip.end(), F.pos1.begin(), F.pos1.end());
-      ip.insert(ip.end(), F.pos2.begin(), F.pos2.end());
-      d.out = (int64_t)ip.size();
-      ip.insert(ip.end(), 1 + 2 * d.nc, 0);
-      d.work = work_elems;
-      work_elems += (int64_t)d.nN * d.nc + 4 * (int64_t)d.nc * d.nc;
-      d.fac = fac_elems;
-      fac_elems += 4 * (int64_t)d.nc * d.nc;
-      max_nc = std::max(max_nc, d.nc);
-      max_nN = std::max(max_nN, d.nN);
-    }
-    DevBuf d_fd, d_ip, fwork;
-    upload(d_fd, fd, st);
-    upload(d_ip, ip, st);
+    if (nf == 0) return;
+    DevBuf fwork, obuf;
     fwork.alloc((size_t)work_elems * sizeof(T), st);
+    obuf.alloc((size_t)out_elems * sizeof(int), st);
     sw.fac.alloc((size_t)fac_elems * sizeof(T), st);
-    launch_front<T>(d_fd.as<FrontDesc>(), nf, cdev.d_desc.as<CellDesc>(), d_ip.as<int>(),
-                    fwork.as<T>(), sw.fac.as<T>(), cwork.as<T>(), h->eps, status.as<int>(), max_nc,
-                    max_nN, tau, st);
+    launch_front<T>(d_fd, nf, d_cdesc, d_ip, obuf.as<int>(), fwork.as<T>(), sw.fac.as<T>(), cwork.as<T>(), h->eps,
+                    status.as<int>(), max_nc, max_nN, tau, st);
     CU(cudaGetLastError());
-    std::vector<int> hip(ip.size());
-    CU(cudaMemcpyAsync(hip.data(), d_ip.p, ip.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
+    LevelFronts info;
+    info.level = l;
+    info.fr = fr;
+    info.fd = fdp;
+    info.out.resize(out_elems);
+    CU(cudaMemcpyAsync(info.out.data(), obuf.p, out_elems * sizeof(int), cudaMemcpyDeviceToHost, st));
     int hstat = 0;
     CU(cudaMemcpyAsync(&hstat, status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
@@ -380,14 +507,16 @@ struct Factorizer {
       CU(cudaStreamSynchronize(st));
     }
     fwork.release();
+    obuf.release();
     // apply descriptors: p = redundant (ascending), q = skeletons (pivot order)
     std::vector<ApplyDesc> ad(nf);
     std::vector<int> aip;
     sw.max_np = sw.max_nq = 0;
+    sw.fac_elems = sw.vec_rows = 0.0;
     const double esz = (double)sizeof(T);
     for (int f = 0; f < nf; ++f) {
       const FrontDesc& d = fd[f];
-      const int* out = hip.data() + d.out;
+      const int* out = info.out.data() + d.out;
       const int k = out[0];
       const int nR = d.nc - k;
       const int* ids_sr = out + 1 + d.nc;
@@ -397,10 +526,10 @@ struct Factorizer {
       a.ids = (int64_t)aip.size();
       aip.insert(aip.end(), ids_sr + k, ids_sr + d.nc);
       aip.insert(aip.end(), ids_sr, ids_sr + k);
-      a.T = d.fac;
-      a.Linv = d.fac + (int64_t)d.nc * d.nc;
-      a.L = d.fac + 2 * (int64_t)d.nc * d.nc;
-      a.G = d.fac + 3 * (int64_t)d.nc * d.nc;
+      a.Linv = d.fac;
+      a.G = d.fac + front_fac_G(d.nc);
+      a.T = d.fac + front_fac_T(d.nc);
+      a.L = d.fac + front_fac_L(d.nc);
       sw.max_np = std::max(sw.max_np, nR);
       sw.max_nq = std::max(sw.max_nq, k);
       if (nR > 0) {
@@ -408,24 +537,22 @@ struct Factorizer {
         sw.vec_rows += nR + k;
       }
       for (int t = k; t < d.nc; ++t) dead[ids_sr[t]] = 1;
-      FrontInfo fi;
-      fi.level = l;
-      fi.c = fr[f].c;
-      fi.sk.assign(ids_sr, ids_sr + k);
-      h->finfo.push_back(std::move(fi));
       h->n_fronts += 1;
       h->max_rank = std::max(h->max_rank, k);
       const double nc = d.nc, nN = d.nN, kk = k, nr = nR;
       // QR (recomputed norms and reflections: ~4 nN nc per step), T, B_rr/B_sr, Cholesky,
       // inverse, G and B_ss
-      h->factor_flops += 4.0 * nN * nc * (kk + 1) + kk * kk * nr + 2.0 * kk * kk * nr +
-                         2.0 * kk * nr * nr + 2.0 * nr * nr * nr / 3.0 + kk * nr * nr + kk * kk * nr;
+      h->factor_flops += 4.0 * nN * nc * (kk + 1) + kk * kk * nr + 2.0 * kk * kk * nr + 2.0 * kk * nr * nr +
+                         2.0 * nr * nr * nr / 3.0 + kk * nr * nr + kk * kk * nr;
       h->apply_bytes += 2.0 * esz * (2 * kk * nr + nr * (nr + 1) / 2);
       h->factor_bytes += (long long)(esz * (2 * kk * nr + nr * (nr + 1) / 2));
     }
+    h->finfo.push_back(std::move(info));
     sw.nblocks = nf;
-    upload(sw.desc, ad, st);
-    upload(sw.ipool, aip, st);
+    upload(sw.desc_own, ad, st);
+    upload(sw.ipool_own, aip, st);
+    sw.desc = sw.desc_own.as<ApplyDesc>();
+    sw.ipool = sw.ipool_own.as<int>();
     std::vector<int> next;
     next.reserve(alive.size());
     for (int g : alive)
@@ -477,8 +604,7 @@ void run_apply(hif_handle* h, int mode, T* x, int nrhs) {
       }
       CU(cudaEventRecord(h->ev_pool[h->ev_used], st));
     }
-    launch_sweep<T>(op, S.desc.as<ApplyDesc>(), S.nblocks, S.ipool.as<int>(), fac, x, nrhs, nrhs,
-                    is_front, S.max_np, S.max_nq, st);
+    launch_sweep<T>(op, S.desc, S.nblocks, S.ipool, fac, x, nrhs, nrhs, is_front, S.max_np, S.max_nq, st);
     if (prof) {
       CU(cudaEventRecord(h->ev_pool[h->ev_used + 1], st));
       h->ev_used += 2;
@@ -506,22 +632,10 @@ void run_apply(hif_handle* h, int mode, T* x, int nrhs) {
 void resolve_profile(hif_handle* h) {
   for (size_t k = 0; k + 1 < h->ev_used; k += 2) {
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, h->ev_pool[k], h->ev_pool[k + 1]) == cudaSuccess) h->prof_ms += ms;
+    CU(cudaEventElapsedTime(&ms, h->ev_pool[k], h->ev_pool[k + 1]));
+    h->prof_ms += ms;
   }
   h->ev_used = 0;
-}
-
-// z (double, packed N x nr) = F^-1 r (double, packed), via the factor's type
-void precondition(hif_handle* h, const double* r, double* z, float* wf, int nr) {
-  const int64_t N = h->G.N;
-  if (h->precision != HIF_PREC_FP64) {
-    launch_convert<double, float>(N, nr, r, nr, wf, nr, h->st);
-    run_apply<float>(h, HIF_APPLY_FINV, wf, nr);
-    launch_convert<float, double>(N, nr, wf, nr, z, nr, h->st);
-  } else {
-    CU(cudaMemcpyAsync(z, r, sizeof(double) * N * nr, cudaMemcpyDeviceToDevice, h->st));
-    run_apply<double>(h, HIF_APPLY_FINV, z, nr);
-  }
 }
 
 // Stage a user vector (host or device, strided) into a packed device array.
@@ -560,107 +674,233 @@ void stage_out(const double* packed, int nr, int ld, int64_t N, double* user, cu
   }
 }
 
-// Solver workspace for one chunk of right-hand sides (N x nr, packed).
+// Solver workspace for one chunk of right-hand sides.  Vectors are N x R,
+// R = the chunk's column count rounded up to a power of two (padding columns
+// carry a zero right-hand side and stay inactive).
 struct SolveWork {
   int64_t N = 0;
-  int nr = 0;
-  DevBuf b, xh, xl, D, R, Z, P, Q, WF, part, scal, cnt;
-  double *rz, *pq, *rr, *rzzq, *alpha, *thr2, *bn2, *rn2;
+  int R = 0;
+  bool f32 = false;
+  DevBuf f, bin, xh, xl, D, Rv, P, Q, WP, part, scal, cnt;
+  double *rzzq[2], *pq, *rr, *alpha, *thr2, *bn2, *rn2;
   int* active;
-  void init(int64_t N_, int nr_, bool mixed, cudaStream_t st) {
+  void init(int64_t N_, int R_, bool f32_, cudaStream_t st) {
     N = N_;
-    nr = nr_;
-    const size_t vb = sizeof(double) * N * nr;
-    b.alloc(vb, st); xh.alloc(vb, st); xl.alloc(vb, st); D.alloc(vb, st);
-    R.alloc(vb, st); Z.alloc(vb, st); P.alloc(vb, st); Q.alloc(vb, st);
-    if (mixed) WF.alloc(sizeof(float) * N * nr, st);
-    const int nblocks = (int)((N + 255) / 256);
-    part.alloc(sizeof(double) * nblocks * 2 * nr, st);
-    scal.alloc(sizeof(double) * 10 * nr + sizeof(int) * nr, st);
+    R = R_;
+    f32 = f32_;
+    const size_t vb = sizeof(double) * N * R;
+    f.alloc(vb, st); bin.alloc(vb, st); xh.alloc(vb, st); xl.alloc(vb, st); D.alloc(vb, st);
+    Rv.alloc(vb, st); P.alloc(vb, st); Q.alloc(vb, st);
+    WP.alloc((f32 ? sizeof(float) : sizeof(double)) * N * R, st);
+    part.alloc(sizeof(double) * 4 * 304 * R, st);
+    scal.alloc(sizeof(double) * 12 * R + sizeof(int) * R, st);
     cnt.alloc(sizeof(unsigned), st);
     CU(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned), st));
+    CU(cudaMemsetAsync(scal.p, 0, sizeof(double) * 12 * R, st));
     double* s = scal.as<double>();
-    rz = s; pq = s + nr; rr = s + 2 * nr; rzzq = s + 3 * nr; alpha = s + 5 * nr;
-    thr2 = s + 6 * nr; bn2 = s + 7 * nr; rn2 = s + 8 * nr;
-    active = reinterpret_cast<int*>(s + 10 * nr);
+    rzzq[0] = s; rzzq[1] = s + 2 * R; pq = s + 4 * R; rr = s + 5 * R; alpha = s + 6 * R;
+    thr2 = s + 7 * R; bn2 = s + 8 * R; rn2 = s + 9 * R;
+    active = reinterpret_cast<int*>(s + 12 * R);
   }
 };
 
-// Inner PCG on A d = R (FP64, preconditioner F^-1), columns whose squared
-// residual is above thr2 are active.  Stops when every recursive residual is
-// below its threshold and the FP64 true residual confirms it (or after maxit).
-int inner_pcg(hif_handle* h, SolveWork& W, const std::vector<double>& hthr, int maxit) {
+// Preconditioner z = F^-1 r applied in place on W.WP, replayed from a CUDA
+// graph after the first (eager) application.
+struct Precond {
+  hif_handle* h;
+  SolveWork& W;
+  cudaGraphExec_t exec = nullptr;
+  int calls = 0;
+  bool use_graph;
+  Precond(hif_handle* h_, SolveWork& W_) : h(h_), W(W_) {
+    const char* e = getenv("HIF_NO_GRAPH");
+    use_graph = !(e && e[0] == '1');
+  }
+  ~Precond() {
+    if (exec) cudaGraphExecDestroy(exec);
+  }
+  void eager() {
+    if (W.f32) run_apply<float>(h, HIF_APPLY_FINV, W.WP.as<float>(), W.R);
+    else run_apply<double>(h, HIF_APPLY_FINV, W.WP.as<double>(), W.R);
+  }
+  void apply() {
+    ++calls;
+    if (!use_graph || calls == 1) {
+      eager();
+      return;
+    }
+    if (!exec) {
+      // capture without sweep events: a replay is timed as one unit
+      if (h->profile) resolve_profile(h);
+      const int prof = h->profile;
+      const double b0 = h->prof_bytes;
+      const long long l0 = h->prof_launches;
+      h->profile = 0;
+      cudaGraph_t g = nullptr;
+      CU(cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal));
+      eager();
+      CU(cudaStreamEndCapture(h->st, &g));
+      h->profile = prof;
+      const cudaError_t e = cudaGraphInstantiate(&exec, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        exec = nullptr;
+        use_graph = false;
+        eager();
+        return;
+      }
+      // bytes and launches of one replay (what the eager sweeps would record)
+      h->graph_bytes = 0.0;
+      h->graph_launches = 0;
+      const double esz = W.f32 ? sizeof(float) : sizeof(double);
+      auto add = [&](const SweepLevel& S) {
+        if (S.nblocks == 0) return;
+        h->graph_bytes += 2.0 * esz * (S.fac_elems + 2.0 * S.vec_rows * W.R);
+        h->graph_launches += 2;
+      };
+      for (const auto& S : h->cells) add(S);
+      for (const auto& S : h->fronts) add(S);
+      add(h->root);
+      h->prof_bytes = b0;
+      h->prof_launches = l0;
+      if (h->profile) {
+        while (h->ev_pool.size() < 2) {
+          cudaEvent_t ev;
+          CU(cudaEventCreate(&ev));
+          h->ev_pool.push_back(ev);
+        }
+      }
+    }
+    if (h->profile) CU(cudaEventRecord(h->ev_pool[0], h->st));
+    CU(cudaGraphLaunch(exec, h->st));
+    if (h->profile) {
+      CU(cudaEventRecord(h->ev_pool[1], h->st));
+      pending_graph = true;
+    }
+    CU(cudaGetLastError());
+  }
+  bool pending_graph = false;
+  // after the stream is synchronized
+  void settle() {
+    if (!h->profile) return;
+    if (pending_graph) {
+      float ms = 0.f;
+      CU(cudaEventElapsedTime(&ms, h->ev_pool[0], h->ev_pool[1]));
+      h->prof_ms += ms;
+      h->prof_bytes += h->graph_bytes;
+      h->prof_launches += h->graph_launches;
+      pending_graph = false;
+    } else {
+      resolve_profile(h);
+    }
+  }
+};
+
+template <typename TZ>
+void cg_step_kernels(hif_handle* h, SolveWork& W, TZ* wp, int par, int restart, int phase,
+                     double* partials, unsigned* counter) {
   const int64_t N = W.N;
-  const int nr = W.nr;
+  const int R = W.R;
+  cudaStream_t st = h->st;
+  if (phase == 0) {
+    launch_dot2_e<TZ>(N, R, W.Rv.as<double>(), wp, W.Q.as<double>(), partials, counter, W.rzzq[par], st);
+    launch_update_p_e<TZ>(N, R, W.P.as<double>(), wp, W.alpha, W.rzzq[par ^ 1], W.rzzq[par], W.active,
+                          restart, st);
+  } else {
+    launch_mv_dot_e(h->gi, h->a_stag.as<double>(), h->bnode.as<double>(), W.P.as<double>(), W.Q.as<double>(),
+                    R, partials, counter, W.pq, st);
+    launch_axpy2_e<TZ>(N, R, W.D.as<double>(), W.Rv.as<double>(), W.P.as<double>(), W.Q.as<double>(),
+                       W.rzzq[par], W.pq, W.active, W.alpha, partials, counter, W.rr, wp, st);
+    launch_set_active(R, W.rr, W.thr2, W.active, st);
+  }
+}
+
+// Inner PCG on A D = Rv (FP64 recurrences, preconditioner F^-1).  Columns whose
+// squared residual is above thr2 are active.  Stops when every recursive
+// residual is below its threshold and the FP64 true residual confirms it.
+int inner_pcg(hif_handle* h, SolveWork& W, Precond& M, const std::vector<double>& hthr, int maxit) {
+  const int64_t N = W.N;
+  const int R = W.R;
   cudaStream_t st = h->st;
   double* partials = W.part.as<double>();
   unsigned* counter = W.cnt.as<unsigned>();
-  const size_t vb = sizeof(double) * N * nr;
-  CU(cudaMemcpyAsync(W.thr2, hthr.data(), sizeof(double) * nr, cudaMemcpyHostToDevice, st));
-  CU(cudaMemcpyAsync(W.b.p, W.R.p, vb, cudaMemcpyDeviceToDevice, st));   // inner right-hand side
+  const size_t vb = sizeof(double) * N * R;
+  CU(cudaMemcpyAsync(W.thr2, hthr.data(), sizeof(double) * R, cudaMemcpyHostToDevice, st));
+  CU(cudaMemcpyAsync(W.bin.p, W.Rv.p, vb, cudaMemcpyDeviceToDevice, st));
   CU(cudaMemsetAsync(W.D.p, 0, vb, st));
-  launch_sqnorm(N, nr, W.R.as<double>(), partials, counter, W.rr, st);
-  launch_set_active(nr, W.rr, W.thr2, W.active, st);
-  std::vector<double> hr(nr);
-  int it = 0, restarts = 0;
-  bool restart = true;
+  launch_sqnorm(N, R, W.Rv.as<double>(), partials, counter, W.rr, st);
+  launch_set_active(R, W.rr, W.thr2, W.active, st);
+  auto to_wp = [&]() {
+    if (W.f32) launch_convert<double, float>(N, R, W.Rv.as<double>(), R, W.WP.as<float>(), R, st);
+    else CU(cudaMemcpyAsync(W.WP.p, W.Rv.p, vb, cudaMemcpyDeviceToDevice, st));
+  };
+  to_wp();
+  std::vector<double> hr(R);
+  int it = 0, restarts = 0, par = 0;
+  int restart = 1;
   while (true) {
-    precondition(h, W.R.as<double>(), W.Z.as<double>(), W.WF.as<float>(), nr);
-    launch_dot2(N, nr, W.R.as<double>(), W.Z.as<double>(), W.Q.as<double>(), partials, counter, W.rzzq, st);
-    launch_update_p(N, nr, W.P.as<double>(), W.Z.as<double>(), W.alpha, W.rz, W.rzzq, W.active,
-                    restart ? 1 : 0, st);
-    CU(cudaMemcpyAsync(W.rz, W.rzzq, sizeof(double) * nr, cudaMemcpyDeviceToDevice, st));
-    restart = false;
+    M.apply();
+    if (W.f32) cg_step_kernels<float>(h, W, W.WP.as<float>(), par, restart, 0, partials, counter);
+    else cg_step_kernels<double>(h, W, W.WP.as<double>(), par, restart, 0, partials, counter);
+    restart = 0;
     if (it >= maxit) break;
-    launch_mv_dot(h->gi, h->a_stag.as<double>(), h->bnode.as<double>(), W.P.as<double>(),
-                  W.Q.as<double>(), nr, partials, counter, W.pq, st);
-    launch_axpy2(N, nr, W.D.as<double>(), W.R.as<double>(), W.P.as<double>(), W.Q.as<double>(), W.rz,
-                 W.pq, W.active, W.alpha, partials, counter, W.rr, st);
-    launch_set_active(nr, W.rr, W.thr2, W.active, st);
+    if (W.f32) cg_step_kernels<float>(h, W, W.WP.as<float>(), par, 0, 1, partials, counter);
+    else cg_step_kernels<double>(h, W, W.WP.as<double>(), par, 0, 1, partials, counter);
     ++it;
-    CU(cudaMemcpyAsync(hr.data(), W.rr, sizeof(double) * nr, cudaMemcpyDeviceToHost, st));
+    par ^= 1;
+    CU(cudaGetLastError());
+    CU(cudaMemcpyAsync(hr.data(), W.rr, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
-    if (h->profile) resolve_profile(h);
+    M.settle();
     bool all = true;
-    for (int c = 0; c < nr; ++c)
+    for (int c = 0; c < R; ++c)
       if (hr[c] > hthr[c]) all = false;
     if (!all) continue;
     // confirm with the FP64 true residual of the inner system
-    launch_residual(h->gi, h->a_stag.as<double>(), h->bnode.as<double>(), W.b.as<double>(),
-                    W.D.as<double>(), W.R.as<double>(), nr, partials, counter, W.rr, st);
-    CU(cudaMemcpyAsync(hr.data(), W.rr, sizeof(double) * nr, cudaMemcpyDeviceToHost, st));
+    launch_residual(h->gi, h->a_stag.as<double>(), h->bnode.as<double>(), W.bin.as<double>(), W.D.as<double>(),
+                    W.Rv.as<double>(), R, partials, counter, W.rr, st);
+    CU(cudaMemcpyAsync(hr.data(), W.rr, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
     bool ok = true;
-    for (int c = 0; c < nr; ++c)
+    for (int c = 0; c < R; ++c)
       if (hr[c] > hthr[c]) ok = false;
     if (ok || ++restarts > 3) break;
-    launch_set_active(nr, W.rr, W.thr2, W.active, st);
-    restart = true;
+    launch_set_active(R, W.rr, W.thr2, W.active, st);
+    to_wp();
+    restart = 1;
   }
+  CU(cudaStreamSynchronize(st));
+  M.settle();
   return it;
 }
 
 // Outer refinement: x = xh + xl (double-double), r = f - A x evaluated in
 // double-double; each step solves A d = r by inner_pcg to a relative
 // tolerance tau = max(tol ||f|| / (2 ||r||), 1e-9) and adds d to x.
+// rhs, x, xlo: packed N x nr device arrays.
 int solve_chunk(hif_handle* h, const double* rhs, double* x, double* xlo, int nr, double tol,
                 int maxit, hif_solve_info* info) {
   const int64_t N = h->G.N;
   cudaStream_t st = h->st;
-  const size_t vb = sizeof(double) * N * nr;
+  int R = 1;
+  while (R < nr) R <<= 1;
+  const size_t vb = sizeof(double) * N * R;
   SolveWork W;
-  W.init(N, nr, h->precision != HIF_PREC_FP64, st);
+  W.init(N, R, h->precision != HIF_PREC_FP64, st);
+  Precond M(h, W);
   double* partials = W.part.as<double>();
   unsigned* counter = W.cnt.as<unsigned>();
-  DevBuf f;
-  f.alloc(vb, st);
-  CU(cudaMemcpyAsync(f.p, rhs, vb, cudaMemcpyDeviceToDevice, st));
-  launch_sqnorm(N, nr, f.as<double>(), partials, counter, W.bn2, st);
-  std::vector<double> hb(nr), hr(nr), hthr(nr);
-  CU(cudaMemcpyAsync(hb.data(), W.bn2, sizeof(double) * nr, cudaMemcpyDeviceToHost, st));
+  CU(cudaMemsetAsync(W.f.p, 0, vb, st));
+  launch_convert<double, double>(N, nr, rhs, nr, W.f.as<double>(), R, st);
+  launch_sqnorm(N, R, W.f.as<double>(), partials, counter, W.bn2, st);
+  std::vector<double> hb(R), hr(R), hthr(R);
+  CU(cudaMemcpyAsync(hb.data(), W.bn2, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
   CU(cudaMemsetAsync(W.xh.p, 0, vb, st));
   CU(cudaMemsetAsync(W.xl.p, 0, vb, st));
-  CU(cudaMemcpyAsync(W.R.p, f.p, vb, cudaMemcpyDeviceToDevice, st));
+  CU(cudaMemsetAsync(W.P.p, 0, vb, st));
+  CU(cudaMemsetAsync(W.Q.p, 0, vb, st));
+  CU(cudaMemcpyAsync(W.Rv.p, W.f.p, vb, cudaMemcpyDeviceToDevice, st));
   CU(cudaStreamSynchronize(st));
   hr = hb;
   int iters = 0, outer = 0;
@@ -676,29 +916,28 @@ int solve_chunk(hif_handle* h, const double* rhs, double* x, double* xlo, int nr
     }
     if (all) { converged = true; break; }
     if (iters >= maxit || outer >= 8) break;
-    for (int c = 0; c < nr; ++c) {
-      if (hr[c] <= tol * tol * hb[c]) { hthr[c] = 1e300; continue; }   // column done
+    for (int c = 0; c < R; ++c) {
+      if (c >= nr || hr[c] <= tol * tol * hb[c]) { hthr[c] = 1e300; continue; }   // column done
       const double tau = std::max(0.5 * tol * std::sqrt(hb[c] / hr[c]), 1e-9);
       hthr[c] = tau * tau * hr[c];
     }
-    iters += inner_pcg(h, W, hthr, maxit - iters);
-    launch_dd_add(N, nr, W.xh.as<double>(), W.xl.as<double>(), W.D.as<double>(), st);
-    launch_dd_residual(h->gi, h->a_stag.as<double>(), h->bnode.as<double>(), f.as<double>(),
-                       W.xh.as<double>(), W.xl.as<double>(), W.R.as<double>(), nr, partials, counter,
-                       W.rn2, st);
-    CU(cudaMemcpyAsync(hr.data(), W.rn2, sizeof(double) * nr, cudaMemcpyDeviceToHost, st));
+    iters += inner_pcg(h, W, M, hthr, maxit - iters);
+    CU(cudaGetLastError());
+    launch_dd_add(N, R, W.xh.as<double>(), W.xl.as<double>(), W.D.as<double>(), st);
+    launch_dd_residual(h->gi, h->a_stag.as<double>(), h->bnode.as<double>(), W.f.as<double>(),
+                       W.xh.as<double>(), W.xl.as<double>(), W.Rv.as<double>(), R, partials, counter, W.rn2, st);
+    CU(cudaMemcpyAsync(hr.data(), W.rn2, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
     ++outer;
   }
   // residual of the FP64-rounded iterate (x_lo dropped)
   CU(cudaMemsetAsync(W.D.p, 0, vb, st));
-  launch_dd_residual(h->gi, h->a_stag.as<double>(), h->bnode.as<double>(), f.as<double>(),
-                     W.xh.as<double>(), W.D.as<double>(), W.Q.as<double>(), nr, partials, counter,
-                     W.rn2, st);
-  std::vector<double> h64(nr);
-  CU(cudaMemcpyAsync(h64.data(), W.rn2, sizeof(double) * nr, cudaMemcpyDeviceToHost, st));
-  CU(cudaMemcpyAsync(x, W.xh.p, vb, cudaMemcpyDeviceToDevice, st));
-  if (xlo) CU(cudaMemcpyAsync(xlo, W.xl.p, vb, cudaMemcpyDeviceToDevice, st));
+  launch_dd_residual(h->gi, h->a_stag.as<double>(), h->bnode.as<double>(), W.f.as<double>(),
+                     W.xh.as<double>(), W.D.as<double>(), W.Q.as<double>(), R, partials, counter, W.rn2, st);
+  std::vector<double> h64(R);
+  CU(cudaMemcpyAsync(h64.data(), W.rn2, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+  launch_convert<double, double>(N, nr, W.xh.as<double>(), R, x, nr, st);
+  if (xlo) launch_convert<double, double>(N, nr, W.xl.as<double>(), R, xlo, nr, st);
   CU(cudaStreamSynchronize(st));
   double rel64 = 0.0;
   for (int c = 0; c < nr; ++c) rel64 = std::max(rel64, hb[c] > 0 ? std::sqrt(h64[c] / hb[c]) : 0.0);
@@ -758,6 +997,12 @@ int hif_factor(const hif_grid* grid, const double* a_stag, const double* b, cons
     h->eps = grid->variant == HIF_VARIANT_HIFDE ? eps : 0.0;
     h->skip_levels = opts ? std::max(0, opts->skip_levels) : 0;
     h->st = opts ? (cudaStream_t)opts->stream : nullptr;
+    if (!h->st) {
+      // a blocking stream: ordered with the legacy default stream like NULL,
+      // but capturable into CUDA graphs
+      CU(cudaStreamCreate(&h->own_stream));
+      h->st = h->own_stream;
+    }
     const int64_t na = (int64_t)grid->n * h->G.N / (grid->n - 1) * grid->dim;
     h->a_stag.alloc(sizeof(double) * na, h->st);
     h->bnode.alloc(sizeof(double) * h->G.N, h->st);
@@ -897,17 +1142,25 @@ int hif_stats(const hif_handle* h, hif_stats_t* s) {
 int hif_structure(const hif_handle* h, int32_t* buf, long long cap, long long* needed) {
   if (!h) return set_error(HIF_ERR_ARG, "NULL handle");
   long long need = 2;
-  for (const FrontInfo& f : h->finfo) need += 3 + (long long)f.c.size() + (long long)f.sk.size();
+  for (const LevelFronts& lf : h->finfo)
+    for (size_t f = 0; f < lf.fd->size(); ++f) {
+      const FrontDesc& d = (*lf.fd)[f];
+      need += 3 + d.nc + lf.out[d.out];
+    }
   if (needed) *needed = need;
   if (!buf || cap < need) return HIF_OK;
   long long p = 0;
-  for (const FrontInfo& f : h->finfo) {
-    buf[p++] = f.level;
-    buf[p++] = (int32_t)f.c.size();
-    buf[p++] = (int32_t)f.sk.size();
-    for (int g : f.c) buf[p++] = g;
-    for (int g : f.sk) buf[p++] = g;
-  }
+  for (const LevelFronts& lf : h->finfo)
+    for (size_t f = 0; f < lf.fd->size(); ++f) {
+      const FrontDesc& d = (*lf.fd)[f];
+      const int* out = lf.out.data() + d.out;
+      const int k = out[0];
+      buf[p++] = lf.level;
+      buf[p++] = d.nc;
+      buf[p++] = k;
+      for (int g : (*lf.fr)[f].c) buf[p++] = g;
+      for (int t = 0; t < k; ++t) buf[p++] = out[1 + d.nc + t];
+    }
   buf[p++] = -1;
   buf[p++] = h->root_size;
   return HIF_OK;
@@ -932,8 +1185,10 @@ long long hif_kernel_launches(void) { return g_launches.load(); }
 void hif_free(hif_handle* h) {
   if (!h) return;
   cudaStream_t st = h->st;
+  cudaStream_t own = h->own_stream;
   delete h;
   cudaStreamSynchronize(st);
+  if (own) cudaStreamDestroy(own);
 }
 
 }  // extern "C"

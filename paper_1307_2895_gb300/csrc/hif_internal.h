@@ -22,8 +22,8 @@ constexpr int kMaxChild = 8;   // 2^dim children per cell
 struct CellDesc {
   int nI, nB;          // interior (eliminated) and boundary (c^N) sizes
   int64_t ids;         // int pool: ids_I[nI] then ids_B[nB] (global DOF ids, ascending)
-  int64_t F;           // work pool: F_II[nI*nI] | F_BI[nB*nI] | F_BB[nB*nB]   (row-major)
-  int64_t fac;         // factor pool: Linv[nI*nI] | L[nI*nI] | G[nB*nI]      (row-major)
+  int64_t F;           // work pool: F_II[nI*nI] | F_BI[nB*nI] | F_BB[nB*nB] | X[nI*nI] (row-major)
+  int64_t fac;         // factor pool: Linv (packed) | G[nB*nI] | L (packed), see fac_layout
   int64_t cmap;        // int pool: (nI+nB) x kMaxChild positions in each child's B (-1 absent)
   int child[kMaxChild];// child cell index at the previous level (-1 absent)
   int cell_lin;        // linear cell index (x fastest) at this level
@@ -35,13 +35,15 @@ struct FrontDesc {
   int P1, P2;          // adjacent cells (indices into the level's cell array)
   int64_t ids;         // int pool: ids_c[nc] | pos1[nc+nN] | pos2[nc+nN]  (c first, then N)
   int64_t work;        // work pool: M[nN*nc] (column-major) | A_cc[nc*nc] | 3 scratch nc*nc
-  int64_t fac;         // factor pool: T[nc*nc] | Linv[nc*nc] | L[nc*nc] | G[nc*nc]
-  int64_t out;         // int pool (outputs): k | perm[nc] | ids_sr[nc]
+  int64_t fac;         // factor pool (capacity for nc): Linv (packed) | G | T | L (packed)
+  int64_t out;         // output buffer: k | perm[nc] | ids_sr[nc]
 };
 
 // Block of the factor as the apply sweeps see it.  Cell: p = I, q = B.
 // Front: p = redundant set r, q = skeleton set s, with T (nq x np).
-// All matrices row-major: Linv, L (np x np), G (nq x np), T (nq x np).
+// Linv and L are lower triangular, packed by rows (entry (i, t), t <= i, at
+// i (i + 1) / 2 + t); G and T are row-major nq x np.  Every region starts on
+// a 16-byte boundary (sizes rounded up to 4 elements).
 struct ApplyDesc {
   int np, nq;
   int64_t ids;         // int pool: ids_p[np] then ids_q[nq]
@@ -53,6 +55,19 @@ void note_launches(long long n);
 
 // Message returned by hif_last_error() on the calling thread.
 void set_last_error(const char* msg);
+
+// Factor-pool sizes (elements, rounded up to 4 so every region is 16-byte aligned).
+__host__ __device__ inline int64_t pad4(int64_t x) { return (x + 3) & ~int64_t(3); }
+__host__ __device__ inline int64_t packed_size(int64_t n) { return pad4(n * (n + 1) / 2); }
+// cell: Linv | G | L
+__host__ __device__ inline int64_t cell_fac_G(int nI) { return packed_size(nI); }
+__host__ __device__ inline int64_t cell_fac_L(int nI, int nB) { return packed_size(nI) + pad4((int64_t)nB * nI); }
+__host__ __device__ inline int64_t cell_fac_size(int nI, int nB) { return 2 * packed_size(nI) + pad4((int64_t)nB * nI); }
+// front with capacity nc: Linv | G | T | L
+__host__ __device__ inline int64_t front_fac_G(int nc) { return packed_size(nc); }
+__host__ __device__ inline int64_t front_fac_T(int nc) { return packed_size(nc) + pad4((int64_t)nc * nc); }
+__host__ __device__ inline int64_t front_fac_L(int nc) { return packed_size(nc) + 2 * pad4((int64_t)nc * nc); }
+__host__ __device__ inline int64_t front_fac_size(int nc) { return 2 * packed_size(nc) + 2 * pad4((int64_t)nc * nc); }
 
 struct GridInfo {
   int dim, n, m;       // m = n - 1 nodes per axis

@@ -16,7 +16,8 @@ template <typename T>
 void launch_cell_factor(const CellDesc* cells, int ncells, T* work, T* fac, int* status, int max_nI,
                         double tau, cudaStream_t st);
 template <typename T>
-void launch_front(const FrontDesc* fronts, int nfronts, const CellDesc* cells, int* ipool, T* fwork,
+void launch_front(const FrontDesc* fronts, int nfronts, const CellDesc* cells, const int* ipool, int* obuf,
+                  T* fwork,
                   T* fac, T* cwork, double eps, int* status, int max_nc, int max_nN, double tau,
                   cudaStream_t st);
 
@@ -47,6 +48,19 @@ void launch_dd_residual(GridInfo g, const double* a_stag, const double* bn, cons
                         const double* xh, const double* xl, double* r, int nr, double* partials,
                         unsigned* counter, double* nrm2, cudaStream_t st);
 void launch_dd_add(int64_t N, int nr, double* xh, double* xl, const double* d, cudaStream_t st);
+// element-parallel CG kernels on N x R vectors, R in {1, 2, 4, 8, 16}
+void launch_mv_dot_e(GridInfo g, const double* a_stag, const double* b, const double* p, double* q,
+                     int R, double* partials, unsigned* counter, double* pq, cudaStream_t st);
+template <typename TZ>
+void launch_axpy2_e(int64_t N, int R, double* x, double* r, const double* p, const double* q,
+                    const double* rz, const double* pq, const int* active, double* alpha, double* partials,
+                    unsigned* counter, double* rr, TZ* zin, cudaStream_t st);
+template <typename TZ>
+void launch_dot2_e(int64_t N, int R, const double* r, const TZ* z, const double* q, double* partials,
+                   unsigned* counter, double* out, cudaStream_t st);
+template <typename TZ>
+void launch_update_p_e(int64_t N, int R, double* p, const TZ* z, const double* alpha, const double* rz_old,
+                       const double* rzzq, const int* active, int restart, cudaStream_t st);
 void launch_set_active(int nr, const double* rr, const double* thr2, int* active, cudaStream_t st);
 template <typename TI, typename TO>
 void launch_convert(int64_t N, int nr, const TI* in, int ldi, TO* out, int ldo, cudaStream_t st);

@@ -11,6 +11,12 @@
 //   fwd_down (V^-T):  x_q += G x_p;  x_p = L x_p;  [front] x_p += T^T x_q
 // Cells of one level share boundary DOFs, so their x_q updates use atomics;
 // the DOFs of a front belong to it alone.
+//
+// The F^-1 sweeps read each block of the factor once: when the launch's
+// largest block fits, the block's Linv (packed), G and T are first copied to
+// shared memory with 16-byte loads (all threads, fully coalesced), then every
+// product is a serial dot per (output row, right-hand side) pair, one thread
+// per pair, with no cross-lane reductions.
 #include "hif_internal.h"
 #include "blockops.cuh"
 #include "kernels.h"
@@ -25,30 +31,74 @@ __device__ __forceinline__ void gather(T* dst, const T* x, const int* ids, int n
   }
 }
 
-// Every product below is a serial dot per (output row, right-hand side)
-// pair: one thread per pair, no cross-lane reductions (FP64 additions are
-// scarce on this GPU, so they are spent only on the products themselves).
+// Copy n elements (16-byte aligned source and destination) with uint4 loads.
+template <typename T>
+__device__ __forceinline__ void stage(T* __restrict__ dst, const T* __restrict__ src, int64_t n) {
+  const int64_t nb = n * (int64_t)sizeof(T);
+  const int64_t nv = nb >> 4;
+  const uint4* s4 = reinterpret_cast<const uint4*>(src);
+  uint4* d4 = reinterpret_cast<uint4*>(dst);
+  for (int64_t e = threadIdx.x; e < nv; e += blockDim.x) d4[e] = __ldg(s4 + e);
+  for (int64_t e = (nv << 4) / (int64_t)sizeof(T) + threadIdx.x; e < n; e += blockDim.x) dst[e] = src[e];
+}
+
+__device__ __forceinline__ int64_t tri(int i) { return (int64_t)i * (i + 1) / 2; }
+
+// Shared-memory plan of one F^-1 sweep block: [Linv | G | T | xp | yp | xq]
+// (each region 16-byte aligned); `staged` is decided per launch.
+template <typename T, int R>
+struct SweepSmem {
+  T *Ls, *Gs, *Ts, *xp, *yp, *xq;
+  __device__ SweepSmem(unsigned char* raw, int np, int nq, bool staged, bool front) {
+    T* p = reinterpret_cast<T*>(raw);
+    Ls = Gs = Ts = nullptr;
+    if (staged) {
+      Ls = p;
+      p += packed_size(np);
+      Gs = p;
+      p += pad4((int64_t)nq * np);
+      if (front) {
+        Ts = p;
+        p += pad4((int64_t)nq * np);
+      }
+    }
+    xp = p;
+    p += pad4((int64_t)np * R);
+    yp = p;
+    p += pad4((int64_t)np * R);
+    xq = p;
+  }
+};
 
 template <typename T, int R>
 __global__ void k_apply_up(const ApplyDesc* __restrict__ blocks, const int* __restrict__ ipool,
                            const T* __restrict__ fac, T* __restrict__ x, int nr, int ldx,
-                           int is_front) {
+                           int is_front, int staged) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const ApplyDesc bd = blocks[blockIdx.x];
   const int np = bd.np, nq = bd.nq;
   if (np == 0) return;
   const int* idp = ipool + bd.ids;
   const int* idq = idp + np;
-  T* xp = reinterpret_cast<T*>(smem_raw);
-  T* yp = xp + np * R;
-  T* xq = yp + np * R;
+  SweepSmem<T, R> sm(smem_raw, np, nq, staged, is_front);
   const T* Linv = fac + bd.Linv;
   const T* G = fac + bd.G;
+  const T* Tm = is_front ? fac + bd.T : nullptr;
+  if (staged) {
+    stage(sm.Ls, Linv, tri(np));
+    stage(sm.Gs, G, (int64_t)nq * np);
+    if (is_front) stage(sm.Ts, Tm, (int64_t)nq * np);
+    Linv = sm.Ls;
+    G = sm.Gs;
+    Tm = sm.Ts;
+  }
+  T* xp = sm.xp;
+  T* yp = sm.yp;
+  T* xq = sm.xq;
   gather<T, R>(xp, x, idp, np, nr, ldx);
   if (is_front) gather<T, R>(xq, x, idq, nq, nr, ldx);
   __syncthreads();
   if (is_front && nq > 0) {                      // x_p -= T^T x_q
-    const T* Tm = fac + bd.T;                    // nq x np
     for (int e = threadIdx.x; e < np * R; e += blockDim.x) {
       const int i = e / R, r = e % R;
       T acc = T(0);
@@ -59,7 +109,7 @@ __global__ void k_apply_up(const ApplyDesc* __restrict__ blocks, const int* __re
   }
   for (int e = threadIdx.x; e < np * R; e += blockDim.x) {   // y_p = Linv x_p
     const int i = e / R, r = e % R;
-    const T* l = Linv + (int64_t)i * np;
+    const T* l = Linv + tri(i);
     T acc = T(0);
     for (int t = 0; t <= i; ++t) acc += l[t] * xp[t * R + r];
     yp[e] = acc;
@@ -82,18 +132,28 @@ __global__ void k_apply_up(const ApplyDesc* __restrict__ blocks, const int* __re
 template <typename T, int R>
 __global__ void k_apply_down(const ApplyDesc* __restrict__ blocks, const int* __restrict__ ipool,
                              const T* __restrict__ fac, T* __restrict__ x, int nr, int ldx,
-                             int is_front) {
+                             int is_front, int staged) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const ApplyDesc bd = blocks[blockIdx.x];
   const int np = bd.np, nq = bd.nq;
   if (np == 0) return;
   const int* idp = ipool + bd.ids;
   const int* idq = idp + np;
-  T* xp = reinterpret_cast<T*>(smem_raw);
-  T* zp = xp + np * R;
-  T* xq = zp + np * R;
+  SweepSmem<T, R> sm(smem_raw, np, nq, staged, is_front);
   const T* Linv = fac + bd.Linv;
   const T* G = fac + bd.G;
+  const T* Tm = is_front ? fac + bd.T : nullptr;
+  if (staged) {
+    stage(sm.Ls, Linv, tri(np));
+    stage(sm.Gs, G, (int64_t)nq * np);
+    if (is_front) stage(sm.Ts, Tm, (int64_t)nq * np);
+    Linv = sm.Ls;
+    G = sm.Gs;
+    Tm = sm.Ts;
+  }
+  T* xp = sm.xp;
+  T* zp = sm.yp;
+  T* xq = sm.xq;
   gather<T, R>(xp, x, idp, np, nr, ldx);
   gather<T, R>(xq, x, idq, nq, nr, ldx);
   __syncthreads();
@@ -109,13 +169,12 @@ __global__ void k_apply_down(const ApplyDesc* __restrict__ blocks, const int* __
   for (int e = threadIdx.x; e < np * R; e += blockDim.x) {   // z = Linv^T w
     const int i = e / R, r = e % R;
     T acc = T(0);
-    for (int t = i; t < np; ++t) acc += Linv[(int64_t)t * np + i] * xp[t * R + r];
+    for (int t = i; t < np; ++t) acc += Linv[tri(t) + i] * xp[t * R + r];
     zp[e] = acc;
     if (r < nr) x[(int64_t)idp[i] * ldx + r] = acc;
   }
   if (is_front && nq > 0) {                      // x_q -= T z
     __syncthreads();
-    const T* Tm = fac + bd.T;
     for (int e = threadIdx.x; e < nq * R; e += blockDim.x) {
       const int s2 = e / R, r = e % R;
       const T* t = Tm + (int64_t)s2 * np;
@@ -126,26 +185,28 @@ __global__ void k_apply_down(const ApplyDesc* __restrict__ blocks, const int* __
   }
 }
 
-// ---- forward operator F (used by the error estimates) ----------------------
+// ---- forward operator F (used by the error estimates; not staged) ----------
 template <typename T, int R>
 __global__ void k_fwd_up(const ApplyDesc* __restrict__ blocks, const int* __restrict__ ipool,
-                         const T* __restrict__ fac, T* __restrict__ x, int nr, int ldx, int is_front) {
+                         const T* __restrict__ fac, T* __restrict__ x, int nr, int ldx, int is_front,
+                         int staged) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  (void)staged;
   const ApplyDesc bd = blocks[blockIdx.x];
   const int np = bd.np, nq = bd.nq;
   if (np == 0) return;
   const int* idp = ipool + bd.ids;
   const int* idq = idp + np;
   T* xp = reinterpret_cast<T*>(smem_raw);
-  T* xq = xp + np * R;
-  const T* Lf = fac + bd.L;
+  T* xq = xp + pad4((int64_t)np * R);
+  T* tq = xq + pad4((int64_t)nq * R);
+  const T* Lp = fac + bd.L;
   const T* G = fac + bd.G;
   gather<T, R>(xp, x, idp, np, nr, ldx);
   gather<T, R>(xq, x, idq, nq, nr, ldx);
   __syncthreads();
   if (is_front && nq > 0) {       // x_q += T x_p
     const T* Tm = fac + bd.T;
-    T* tq = xq + nq * R;          // scratch: the launch reserves (2 np + 2 nq) R
     for (int e = threadIdx.x; e < nq * R; e += blockDim.x) {
       const int s2 = e / R, r = e % R;
       T acc = T(0);
@@ -160,7 +221,7 @@ __global__ void k_fwd_up(const ApplyDesc* __restrict__ blocks, const int* __rest
   for (int e = threadIdx.x; e < np * R; e += blockDim.x) {   // x_p = L^T x_p + G^T x_q
     const int i = e / R, r = e % R;
     T acc = T(0);
-    for (int t = i; t < np; ++t) acc += Lf[(int64_t)t * np + i] * xp[t * R + r];
+    for (int t = i; t < np; ++t) acc += Lp[tri(t) + i] * xp[t * R + r];
     for (int s2 = 0; s2 < nq; ++s2) acc += G[(int64_t)s2 * np + i] * xq[s2 * R + r];
     if (r < nr) x[(int64_t)idp[i] * ldx + r] = acc;
   }
@@ -168,16 +229,18 @@ __global__ void k_fwd_up(const ApplyDesc* __restrict__ blocks, const int* __rest
 
 template <typename T, int R>
 __global__ void k_fwd_down(const ApplyDesc* __restrict__ blocks, const int* __restrict__ ipool,
-                           const T* __restrict__ fac, T* __restrict__ x, int nr, int ldx, int is_front) {
+                           const T* __restrict__ fac, T* __restrict__ x, int nr, int ldx, int is_front,
+                           int staged) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  (void)staged;
   const ApplyDesc bd = blocks[blockIdx.x];
   const int np = bd.np, nq = bd.nq;
   if (np == 0) return;
   const int* idp = ipool + bd.ids;
   const int* idq = idp + np;
   T* xp = reinterpret_cast<T*>(smem_raw);
-  T* xq = xp + np * R;
-  const T* Lf = fac + bd.L;
+  T* xq = xp + pad4((int64_t)np * R);
+  const T* Lp = fac + bd.L;
   const T* G = fac + bd.G;
   gather<T, R>(xp, x, idp, np, nr, ldx);
   if (is_front) gather<T, R>(xq, x, idq, nq, nr, ldx);
@@ -197,7 +260,7 @@ __global__ void k_fwd_down(const ApplyDesc* __restrict__ blocks, const int* __re
   __syncthreads();
   for (int e = threadIdx.x; e < np * R; e += blockDim.x) {   // x_p = L x_p [+ T^T x_q]
     const int i = e / R, r = e % R;
-    const T* l = Lf + (int64_t)i * np;
+    const T* l = Lp + tri(i);
     T acc = T(0);
     for (int t = 0; t <= i; ++t) acc += l[t] * xp[t * R + r];
     if (is_front) {
@@ -209,28 +272,49 @@ __global__ void k_fwd_down(const ApplyDesc* __restrict__ blocks, const int* __re
 }
 
 // ---------------------------------------------------------------------------
+constexpr size_t kSweepSmemCap = 200 * 1024;
+constexpr size_t kStageCap = 96 * 1024;   // stage only when two blocks still fit an SM
+
+template <typename T>
+static size_t vec_smem(int R, int max_np, int max_nq) {
+  return sizeof(T) * (size_t)(2 * pad4((int64_t)max_np * R) + 2 * pad4((int64_t)max_nq * R));
+}
+
+template <typename T>
+static size_t stage_smem(int max_np, int max_nq, int is_front) {
+  return sizeof(T) * (size_t)(packed_size(max_np) + (is_front ? 2 : 1) * pad4((int64_t)max_nq * max_np));
+}
+
 template <typename T, int R>
 static void launch_sweep_R(int op, const ApplyDesc* blocks, int nblocks, const int* ipool,
                            const T* fac, T* x, int nr, int ldx, int is_front, int max_np,
                            int max_nq, cudaStream_t st) {
-  const size_t smem = sizeof(T) * R * (size_t)(2 * max_np + 2 * max_nq);
-  void (*fn)(const ApplyDesc*, const int*, const T*, T*, int, int, int) = nullptr;
+  const size_t vsm = vec_smem<T>(R, max_np, max_nq);
+  const size_t ssm = stage_smem<T>(max_np, max_nq, is_front);
+  const int staged = (op <= 1) && (vsm + ssm <= kStageCap);
+  const size_t smem = vsm + (staged ? ssm : 0);
+  void (*fn)(const ApplyDesc*, const int*, const T*, T*, int, int, int, int) = nullptr;
   switch (op) {
     case 0: fn = k_apply_up<T, R>; break;
     case 1: fn = k_apply_down<T, R>; break;
     case 2: fn = k_fwd_up<T, R>; break;
     default: fn = k_fwd_down<T, R>; break;
   }
-  if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // raise the dynamic shared-memory limit once per kernel (not again while a
+  // stream capture records the launch)
+  static size_t smem_set[4] = {48 * 1024, 48 * 1024, 48 * 1024, 48 * 1024};
+  if (smem > smem_set[op]) {
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSweepSmemCap);
+    smem_set[op] = kSweepSmemCap;
+  }
   note_launches(1);
-  fn<<<nblocks, 256, smem, st>>>(blocks, ipool, fac, x, nr, ldx, is_front);
+  fn<<<nblocks, 256, smem, st>>>(blocks, ipool, fac, x, nr, ldx, is_front, staged);
 }
 
 template <typename T>
 int sweep_chunk(int max_np, int max_nq, int nrhs) {
-  const size_t cap = 200 * 1024;
   int R = 32;
-  while (R > 1 && (R / 2 >= nrhs || sizeof(T) * R * (size_t)(2 * max_np + 2 * max_nq) > cap)) R /= 2;
+  while (R > 1 && (R / 2 >= nrhs || vec_smem<T>(R, max_np, max_nq) > kSweepSmemCap)) R /= 2;
   return R;
 }
 

@@ -165,12 +165,13 @@ __global__ void k_cell_factor(const CellDesc* __restrict__ cells, T* __restrict_
   T* FII = work + cd.F;
   T* FBI = FII + (int64_t)nI * nI;
   T* FBB = FBI + (int64_t)nB * nI;
+  T* Xg = FBB + (int64_t)nB * nB;           // global room for Linv when smem is short
   T* Linv = fac + cd.fac;
-  T* Lf = Linv + (int64_t)nI * nI;
-  T* G = Lf + (int64_t)nI * nI;
+  T* G = fac + cd.fac + cell_fac_G(nI);
+  T* Lp = fac + cd.fac + cell_fac_L(nI, nB);
   const int64_t n2 = (int64_t)nI * nI;
   T* A = FII;
-  T* X = Linv;
+  T* X = Xg;
   if (2 * n2 <= smem_elems) {
     A = sm;
     X = sm + n2;
@@ -179,9 +180,9 @@ __global__ void k_cell_factor(const CellDesc* __restrict__ cells, T* __restrict_
   }
   if (A != FII) blk_copy(FII, nI, A, nI, nI, nI);
   blk_cholesky(A, nI, nI, status, tau);
-  blk_copy_lower(A, nI, Lf, nI, nI);
-  blk_tri_inverse(Lf, nI, nI, X, nI);
-  if (X != Linv) blk_copy(X, nI, Linv, nI, nI, nI);
+  blk_tri_inverse(A, nI, nI, X, nI);
+  blk_pack_lower(A, nI, Lp, nI);
+  blk_pack_lower(X, nI, Linv, nI);
   if (nB > 0) {
     blk_mul_linvT(FBI, nI, X, nI, nB, nI, G, nI);
     blk_syrk_sub(FBB, nB, G, nI, nB, nI);
@@ -206,7 +207,8 @@ __device__ __forceinline__ T front_entry(const T* U1, int ld1, const T* U2, int 
 
 template <typename T>
 __global__ void k_front(const FrontDesc* __restrict__ fronts, const CellDesc* __restrict__ cells,
-                        int* __restrict__ ipool, T* __restrict__ fwork, T* __restrict__ fac,
+                        const int* __restrict__ ipool, int* __restrict__ obuf, T* __restrict__ fwork,
+                        T* __restrict__ fac,
                         T* __restrict__ cwork, double eps, int* status, T tau) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const FrontDesc fd = fronts[blockIdx.x];
@@ -214,7 +216,7 @@ __global__ void k_front(const FrontDesc* __restrict__ fronts, const CellDesc* __
   const int* idc = ipool + fd.ids;
   const int* pos1 = idc + nc;
   const int* pos2 = pos1 + nc + nN;
-  int* out = ipool + fd.out;
+  int* out = obuf + fd.out;
   const CellDesc P1 = cells[fd.P1], P2 = cells[fd.P2];
   T* U1 = cwork + P1.F + (int64_t)P1.nI * P1.nI + (int64_t)P1.nB * P1.nI;
   T* U2 = cwork + P2.F + (int64_t)P2.nI * P2.nI + (int64_t)P2.nB * P2.nI;
@@ -323,10 +325,10 @@ __global__ void k_front(const FrontDesc* __restrict__ fronts, const CellDesc* __
   }
   __syncthreads();
 
-  T* Tm = fac + fd.fac;                    // k x nR
-  T* Linv = Tm + (int64_t)nc * nc;         // nR x nR
-  T* Lf = Linv + (int64_t)nc * nc;         // nR x nR
-  T* G = Lf + (int64_t)nc * nc;            // k x nR
+  T* Linvp = fac + fd.fac;                 // packed nR x nR
+  T* G = fac + fd.fac + front_fac_G(nc);   // k x nR
+  T* Tm = fac + fd.fac + front_fac_T(nc);  // k x nR
+  T* Lp = fac + fd.fac + front_fac_L(nc);  // packed nR x nR
 
   // ---- T = R11^{-1} R12 (back substitution, one thread per column)
   for (int c = threadIdx.x; c < nR; c += blockDim.x) {
@@ -367,10 +369,12 @@ __global__ void k_front(const FrontDesc* __restrict__ fronts, const CellDesc* __
   __syncthreads();
   if (nR > 0) {
     blk_cholesky(S3, nR, nR, status, tau);
-    blk_copy_lower(S3, nR, Lf, nR, nR);
-    blk_tri_inverse(Lf, nR, nR, Linv, nR);
+    T* X = S1;                             // W is no longer needed
+    blk_tri_inverse(S3, nR, nR, X, nR);
+    blk_pack_lower(S3, nR, Lp, nR);
+    blk_pack_lower(X, nR, Linvp, nR);
     if (k > 0) {
-      blk_mul_linvT(S2, nR, Linv, nR, k, nR, G, nR);
+      blk_mul_linvT(S2, nR, X, nR, k, nR, G, nR);
       // B_ss = A_ss - G G^T -> P1's update (skeleton block), zero in P2's
       for (int64_t e = threadIdx.x; e < (int64_t)k * k; e += blockDim.x) {
         const int i = (int)(e / k), j = (int)(e % k);
@@ -427,14 +431,15 @@ void launch_cell_factor(const CellDesc* cells, int ncells, T* work, T* fac, int*
 }
 
 template <typename T>
-void launch_front(const FrontDesc* fronts, int nfronts, const CellDesc* cells, int* ipool, T* fwork,
+void launch_front(const FrontDesc* fronts, int nfronts, const CellDesc* cells, const int* ipool, int* obuf,
+                  T* fwork,
                   T* fac, T* cwork, double eps, int* status, int max_nc, int max_nN, double tau,
                   cudaStream_t st) {
   const int smem = (int)(sizeof(double) * (max_nc + max_nN) + sizeof(int) * 2 * max_nc + 64);
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(k_front<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   note_launches(1);
-  k_front<T><<<nfronts, 256, smem, st>>>(fronts, cells, ipool, fwork, fac, cwork, eps, status, (T)tau);
+  k_front<T><<<nfronts, 256, smem, st>>>(fronts, cells, ipool, obuf, fwork, fac, cwork, eps, status, (T)tau);
 }
 
 template void launch_leaf_assemble<double>(const CellDesc*, int, const int*, double*, GridInfo,
@@ -449,9 +454,9 @@ template void launch_extend_add<float, double>(const CellDesc*, int, const int*,
                                                const CellDesc*, const float*, int, cudaStream_t);
 template void launch_cell_factor<double>(const CellDesc*, int, double*, double*, int*, int, double, cudaStream_t);
 template void launch_cell_factor<float>(const CellDesc*, int, float*, float*, int*, int, double, cudaStream_t);
-template void launch_front<double>(const FrontDesc*, int, const CellDesc*, int*, double*, double*,
+template void launch_front<double>(const FrontDesc*, int, const CellDesc*, const int*, int*, double*, double*,
                                    double*, double, int*, int, int, double, cudaStream_t);
-template void launch_front<float>(const FrontDesc*, int, const CellDesc*, int*, float*, float*,
+template void launch_front<float>(const FrontDesc*, int, const CellDesc*, const int*, int*, float*, float*,
                                   float*, double, int*, int, int, double, cudaStream_t);
 
 }  // namespace hif

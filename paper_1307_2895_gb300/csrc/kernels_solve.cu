@@ -258,6 +258,125 @@ __global__ void k_sqnorm(int64_t N, int nr, const double* __restrict__ v, double
   grid_reduce<R>(acc, nr, partials, counter, out);
 }
 
+// ---- element-parallel CG kernels ------------------------------------------
+// One thread per (unknown, column) element e = i * R + c of an N x R vector
+// (R a power of two, so a grid-stride thread keeps one column); reductions
+// sum threads of equal column in a shared-memory tree, then across blocks.
+template <int R, int NG>
+__device__ void grid_reduce_cols(const double (&acc)[NG], double* partials, unsigned* counter,
+                                 double* out) {
+  __shared__ double shr[NG][kVecThreads];
+  __shared__ bool last;
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int g = 0; g < NG; ++g) shr[g][tid] = acc[g];
+  __syncthreads();
+  for (int s = blockDim.x >> 1; s >= R; s >>= 1) {
+    if (tid < s)
+#pragma unroll
+      for (int g = 0; g < NG; ++g) shr[g][tid] += shr[g][tid + s];
+    __syncthreads();
+  }
+  if (tid < R)
+#pragma unroll
+    for (int g = 0; g < NG; ++g) partials[((int64_t)blockIdx.x * NG + g) * R + tid] = shr[g][tid];
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int v = tid; v < NG * R; v += blockDim.x) {
+    const int g = v / R, c = v % R;
+    double s = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) s += partials[((int64_t)b * NG + g) * R + c];
+    out[v] = s;
+  }
+  if (tid == 0) *counter = 0u;
+}
+
+// (A x)[e] for element e = gid * R + c
+template <int R>
+__device__ __forceinline__ double stencil_elem(const Stencil& S, int64_t gid, int c, const double* x) {
+  const int m = S.g.m, dim = S.g.dim;
+  const int jj[3] = {(int)(gid % m) + 1, (int)((gid / m) % m) + 1,
+                     dim == 3 ? (int)(gid / ((int64_t)m * m)) + 1 : 1};
+  const int64_t stride[3] = {1, m, (int64_t)m * m};
+  const double h2 = S.g.inv_h2;
+  double diag = S.bnode[gid];
+  double y = 0.0;
+  for (int ax = 0; ax < dim; ++ax) {
+    int lo[3] = {jj[0], jj[1], jj[2]};
+    lo[ax] -= 1;
+    const double alo = sbond(S, ax, lo[0], lo[1], lo[2]) * h2;
+    const double ahi = sbond(S, ax, jj[0], jj[1], jj[2]) * h2;
+    diag += alo + ahi;
+    if (jj[ax] > 1) y -= alo * x[(gid - stride[ax]) * R + c];
+    if (jj[ax] < m) y -= ahi * x[(gid + stride[ax]) * R + c];
+  }
+  return y + diag * x[gid * R + c];
+}
+
+template <int R>
+__global__ void k_mv_dot_e(Stencil S, int64_t N, const double* __restrict__ p, double* __restrict__ q,
+                           double* partials, unsigned* counter, double* pq) {
+  double acc[1] = {0.0};
+  GRID_LOOP(e, N * R) {
+    const double v = stencil_elem<R>(S, e / R, (int)(e % R), p);
+    q[e] = v;
+    acc[0] = fma(v, p[e], acc[0]);
+  }
+  grid_reduce_cols<R, 1>(acc, partials, counter, pq);
+}
+
+// alpha = rz/pq (active columns); x += alpha p; r -= alpha q; rr = r.r; zin = (TZ) r
+template <int R, typename TZ>
+__global__ void k_axpy2_e(int64_t N, double* __restrict__ x, double* __restrict__ r,
+                          const double* __restrict__ p, const double* __restrict__ q,
+                          const double* rz, const double* pq, const int* active, double* alpha_out,
+                          double* partials, unsigned* counter, double* rr, TZ* __restrict__ zin) {
+  const int c = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) % R);
+  const double a = (active[c] && pq[c] != 0.0) ? rz[c] / pq[c] : 0.0;
+  if (blockIdx.x == 0 && threadIdx.x < R) alpha_out[threadIdx.x] = a;
+  double acc[1] = {0.0};
+  GRID_LOOP(e, N * R) {
+    x[e] = fma(a, p[e], x[e]);
+    const double rv = fma(-a, q[e], r[e]);
+    r[e] = rv;
+    zin[e] = (TZ)rv;
+    acc[0] = fma(rv, rv, acc[0]);
+  }
+  grid_reduce_cols<R, 1>(acc, partials, counter, rr);
+}
+
+// out = [r.z | z.q]
+template <int R, typename TZ>
+__global__ void k_dot2_e(int64_t N, const double* __restrict__ r, const TZ* __restrict__ z,
+                         const double* __restrict__ q, double* partials, unsigned* counter, double* out) {
+  double acc[2] = {0.0, 0.0};
+  GRID_LOOP(e, N * R) {
+    const double zv = (double)z[e];
+    acc[0] = fma(r[e], zv, acc[0]);
+    acc[1] = fma(zv, q[e], acc[1]);
+  }
+  grid_reduce_cols<R, 2>(acc, partials, counter, out);
+}
+
+// beta = -alpha zq / rz_old (flexible / Polak-Ribiere form); p = z + beta p
+template <int R, typename TZ>
+__global__ void k_update_p_e(int64_t N, double* __restrict__ p, const TZ* __restrict__ z,
+                             const double* alpha, const double* rz_old, const double* rzzq,
+                             const int* active, int restart) {
+  const int c = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) % R);
+  if (!active[c]) return;
+  const bool rs = restart || rz_old[c] == 0.0;
+  const double beta = rs ? 0.0 : -alpha[c] * rzzq[R + c] / rz_old[c];
+  GRID_LOOP(e, N * R) {
+    const double zv = (double)z[e];
+    p[e] = rs ? zv : fma(beta, p[e], zv);
+  }
+}
+
 // ---- double-double outer iterate -------------------------------------------
 // Error-free transformations (Knuth TwoSum, FMA TwoProd) with explicit
 // round-to-nearest intrinsics so that no contraction changes them.
@@ -467,6 +586,70 @@ void launch_dd_add(int64_t N, int nr, double* xh, double* xl, const double* d, c
   note_launches(1);
   k_dd_add<<<vec_blocks(N * nr), kVecThreads, 0, st>>>(N, nr, xh, xl, d);
 }
+
+#define DISPATCH_POW2(R_, ...)                                  \
+  do {                                                          \
+    switch (R_) {                                               \
+      case 1: { constexpr int R = 1; __VA_ARGS__; } break;      \
+      case 2: { constexpr int R = 2; __VA_ARGS__; } break;      \
+      case 4: { constexpr int R = 4; __VA_ARGS__; } break;      \
+      case 8: { constexpr int R = 8; __VA_ARGS__; } break;      \
+      default: { constexpr int R = 16; __VA_ARGS__; } break;    \
+    }                                                           \
+  } while (0)
+
+static inline int elem_blocks(int64_t n) {
+  // grid-stride threads; a multiple of every R in {1,..,16} by construction (256 per block)
+  return vec_blocks(n);
+}
+
+void launch_mv_dot_e(GridInfo g, const double* a_stag, const double* b, const double* p, double* q,
+                     int R_, double* partials, unsigned* counter, double* pq, cudaStream_t st) {
+  const int64_t N = grid_n(g);
+  Stencil S{g, a_stag, b};
+  note_launches(1);
+  DISPATCH_POW2(R_, k_mv_dot_e<R><<<elem_blocks(N * R), kVecThreads, 0, st>>>(S, N, p, q, partials, counter, pq));
+}
+
+template <typename TZ>
+void launch_axpy2_e(int64_t N, int R_, double* x, double* r, const double* p, const double* q,
+                    const double* rz, const double* pq, const int* active, double* alpha, double* partials,
+                    unsigned* counter, double* rr, TZ* zin, cudaStream_t st) {
+  note_launches(1);
+  DISPATCH_POW2(R_, k_axpy2_e<R, TZ><<<elem_blocks(N * R), kVecThreads, 0, st>>>(
+      N, x, r, p, q, rz, pq, active, alpha, partials, counter, rr, zin));
+}
+
+template <typename TZ>
+void launch_dot2_e(int64_t N, int R_, const double* r, const TZ* z, const double* q, double* partials,
+                   unsigned* counter, double* out, cudaStream_t st) {
+  note_launches(1);
+  DISPATCH_POW2(R_, k_dot2_e<R, TZ><<<elem_blocks(N * R), kVecThreads, 0, st>>>(N, r, z, q, partials, counter,
+                                                                                 out));
+}
+
+template <typename TZ>
+void launch_update_p_e(int64_t N, int R_, double* p, const TZ* z, const double* alpha, const double* rz_old,
+                       const double* rzzq, const int* active, int restart, cudaStream_t st) {
+  note_launches(1);
+  DISPATCH_POW2(R_, k_update_p_e<R, TZ><<<elem_blocks(N * R), kVecThreads, 0, st>>>(N, p, z, alpha, rz_old,
+                                                                                      rzzq, active, restart));
+}
+
+template void launch_axpy2_e<double>(int64_t, int, double*, double*, const double*, const double*,
+                                     const double*, const double*, const int*, double*, double*,
+                                     unsigned*, double*, double*, cudaStream_t);
+template void launch_axpy2_e<float>(int64_t, int, double*, double*, const double*, const double*,
+                                    const double*, const double*, const int*, double*, double*,
+                                    unsigned*, double*, float*, cudaStream_t);
+template void launch_dot2_e<double>(int64_t, int, const double*, const double*, const double*, double*,
+                                    unsigned*, double*, cudaStream_t);
+template void launch_dot2_e<float>(int64_t, int, const double*, const float*, const double*, double*,
+                                   unsigned*, double*, cudaStream_t);
+template void launch_update_p_e<double>(int64_t, int, double*, const double*, const double*, const double*,
+                                        const double*, const int*, int, cudaStream_t);
+template void launch_update_p_e<float>(int64_t, int, double*, const float*, const double*, const double*,
+                                       const double*, const int*, int, cudaStream_t);
 
 void launch_set_active(int nr, const double* rr, const double* thr2, int* active, cudaStream_t st) {
   note_launches(1);
