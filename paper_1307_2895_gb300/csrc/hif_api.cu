@@ -162,6 +162,8 @@ struct hif_handle {
   cudaStream_t st = nullptr;
   cudaStream_t own_stream = nullptr;   // created when the caller passes no stream
   DevBuf a_stag, bnode;
+  DevBuf dev_err;   // device status of the apply kernels (bit 3: a bounded wait ran out)
+  DevBuf stencil_w; // per-node stencil weights (diagonal and neighbour couplings)
   std::shared_ptr<const Level0> level0;
   std::vector<SweepLevel> cells, fronts;   // levels 0..L-1
   SweepLevel root;                         // level L
@@ -604,7 +606,8 @@ void run_apply(hif_handle* h, int mode, T* x, int nrhs) {
       }
       CU(cudaEventRecord(h->ev_pool[h->ev_used], st));
     }
-    launch_sweep<T>(op, S.desc, S.nblocks, S.ipool, fac, x, nrhs, nrhs, is_front, S.max_np, S.max_nq, st);
+    launch_sweep<T>(op, S.desc, S.nblocks, S.ipool, fac, x, nrhs, nrhs, is_front, S.max_np, S.max_nq,
+                    h->dev_err.as<int>(), st);
     if (prof) {
       CU(cudaEventRecord(h->ev_pool[h->ev_used + 1], st));
       h->ev_used += 2;
@@ -808,8 +811,8 @@ void cg_step_kernels(hif_handle* h, SolveWork& W, TZ* wp, int par, int restart, 
     launch_update_p_e<TZ>(N, R, W.P.as<double>(), wp, W.alpha, W.rzzq[par ^ 1], W.rzzq[par], W.active,
                           restart, st);
   } else {
-    launch_mv_dot_e(h->gi, h->a_stag.as<double>(), h->bnode.as<double>(), W.P.as<double>(), W.Q.as<double>(),
-                    R, partials, counter, W.pq, st);
+    launch_mv_dot_e(h->gi, h->stencil_w.as<double>(), W.P.as<double>(), W.Q.as<double>(), R, partials, counter,
+                    W.pq, st);
     launch_axpy2_e<TZ>(N, R, W.D.as<double>(), W.Rv.as<double>(), W.P.as<double>(), W.Q.as<double>(),
                        W.rzzq[par], W.pq, W.active, W.alpha, partials, counter, W.rr, wp, st);
     launch_set_active(R, W.rr, W.thr2, W.active, st);
@@ -955,6 +958,20 @@ int solve_chunk(hif_handle* h, const double* rhs, double* x, double* xlo, int nr
 
 void hif::set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
 
+namespace {
+// Reads and clears the apply kernels' device status (stream synchronized).
+int check_dev_err(hif_handle* h) {
+  int e = 0;
+  CU(cudaMemcpyAsync(&e, h->dev_err.p, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  CU(cudaStreamSynchronize(h->st));
+  if (e) {
+    CU(cudaMemsetAsync(h->dev_err.p, 0, sizeof(int), h->st));
+    throw HifError(HIF_ERR_TIMEOUT, "a bounded wait for a bulk copy into shared memory ran out");
+  }
+  return HIF_OK;
+}
+}  // namespace
+
 // ===========================================================================
 // C ABI
 // ===========================================================================
@@ -1004,10 +1021,14 @@ int hif_factor(const hif_grid* grid, const double* a_stag, const double* b, cons
       h->st = h->own_stream;
     }
     const int64_t na = (int64_t)grid->n * h->G.N / (grid->n - 1) * grid->dim;
+    h->dev_err.alloc(sizeof(int), h->st);
+    CU(cudaMemsetAsync(h->dev_err.p, 0, sizeof(int), h->st));
     h->a_stag.alloc(sizeof(double) * na, h->st);
     h->bnode.alloc(sizeof(double) * h->G.N, h->st);
     CU(cudaMemcpyAsync(h->a_stag.p, a_stag, sizeof(double) * na, cudaMemcpyDefault, h->st));
     CU(cudaMemcpyAsync(h->bnode.p, b, sizeof(double) * h->G.N, cudaMemcpyDefault, h->st));
+    h->stencil_w.alloc(sizeof(double) * h->G.N * (2 * grid->dim + 1), h->st);
+    launch_stencil_weights(h->gi, h->a_stag.as<double>(), h->bnode.as<double>(), h->stencil_w.as<double>(), h->st);
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
@@ -1061,6 +1082,7 @@ int hif_apply(hif_handle* h, int mode, const double* x, double* y, int nrhs, int
     CU(cudaGetLastError());
     CU(cudaStreamSynchronize(st));
     if (h->profile) resolve_profile(h);
+    check_dev_err(h);
   } catch (const HifError& e) {
     return set_error(e.code, e.msg);
   }
@@ -1113,6 +1135,7 @@ int hif_solve(hif_handle* h, const double* rhs, double* x, double* x_lo, int nrh
     }
     CU(cudaStreamSynchronize(st));
     if (h->profile) resolve_profile(h);
+    check_dev_err(h);
   } catch (const HifError& e) {
     return set_error(e.code, e.msg);
   }

@@ -24,7 +24,7 @@ void launch_front(const FrontDesc* fronts, int nfronts, const CellDesc* cells, c
 // apply sweeps (kernels_apply.cu); op: 0 up, 1 down, 2 fwd_up, 3 fwd_down
 template <typename T>
 void launch_sweep(int op, const ApplyDesc* blocks, int nblocks, const int* ipool, const T* fac, T* x,
-                  int nrhs, int ldx, int is_front, int max_np, int max_nq, cudaStream_t st);
+                  int nrhs, int ldx, int is_front, int max_np, int max_nq, int* err, cudaStream_t st);
 
 // stencil operator and CG vector operations (kernels_solve.cu)
 void launch_matvec(GridInfo g, const double* a_stag, const double* b, const double* x, int ldx,
@@ -49,8 +49,9 @@ void launch_dd_residual(GridInfo g, const double* a_stag, const double* bn, cons
                         unsigned* counter, double* nrm2, cudaStream_t st);
 void launch_dd_add(int64_t N, int nr, double* xh, double* xl, const double* d, cudaStream_t st);
 // element-parallel CG kernels on N x R vectors, R in {1, 2, 4, 8, 16}
-void launch_mv_dot_e(GridInfo g, const double* a_stag, const double* b, const double* p, double* q,
-                     int R, double* partials, unsigned* counter, double* pq, cudaStream_t st);
+void launch_stencil_weights(GridInfo g, const double* a_stag, const double* b, double* W, cudaStream_t st);
+void launch_mv_dot_e(GridInfo g, const double* W, const double* p, double* q, int R, double* partials,
+                     unsigned* counter, double* pq, cudaStream_t st);
 template <typename TZ>
 void launch_axpy2_e(int64_t N, int R, double* x, double* r, const double* p, const double* q,
                     const double* rz, const double* pq, const int* active, double* alpha, double* partials,

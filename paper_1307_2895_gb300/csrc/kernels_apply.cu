@@ -31,26 +31,65 @@ __device__ __forceinline__ void gather(T* dst, const T* x, const int* ids, int n
   }
 }
 
-// Copy n elements (16-byte aligned source and destination) with uint4 loads.
-template <typename T>
-__device__ __forceinline__ void stage(T* __restrict__ dst, const T* __restrict__ src, int64_t n) {
-  const int64_t nb = n * (int64_t)sizeof(T);
-  const int64_t nv = nb >> 4;
-  const uint4* s4 = reinterpret_cast<const uint4*>(src);
-  uint4* d4 = reinterpret_cast<uint4*>(dst);
-  for (int64_t e = threadIdx.x; e < nv; e += blockDim.x) d4[e] = __ldg(s4 + e);
-  for (int64_t e = (nv << 4) / (int64_t)sizeof(T) + threadIdx.x; e < n; e += blockDim.x) dst[e] = src[e];
+// ---- TMA bulk staging -------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
 }
+
+// One thread starts bulk copies (global -> this CTA's shared memory) of the
+// listed regions, all completing on one mbarrier; every thread then waits
+// with a bounded spin.  Regions are 16-byte aligned with sizes that are
+// multiples of 16 bytes.  Returns false (and sets bit 3 of *err) if the wait
+// ran out; the block then waits once more, bounded, for its copies to land.
+struct BulkStage {
+  uint64_t* mbar;
+  __device__ void start(int nreg, void* const* dst, const void* const* src, const uint32_t* bytes) {
+    if (threadIdx.x == 0) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)) : "memory");
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      uint32_t total = 0;
+      for (int k = 0; k < nreg; ++k) total += bytes[k];
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(total)
+                   : "memory");
+      for (int k = 0; k < nreg; ++k)
+        if (bytes[k] > 0)
+          asm volatile(
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                  smem_u32(dst[k])),
+              "l"(src[k]), "r"(bytes[k]), "r"(smem_u32(mbar))
+              : "memory");
+    }
+  }
+  __device__ bool try_wait() const {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(mbar))
+        : "memory");
+    return ok != 0;
+  }
+  __device__ bool wait(int* err) const {
+    for (long it = 0; it < (1L << 26); ++it)
+      if (try_wait()) return true;
+    if (err) atomicOr(err, 8);
+    for (long it = 0; it < (1L << 26); ++it)
+      if (try_wait()) break;
+    return false;
+  }
+};
 
 __device__ __forceinline__ int64_t tri(int i) { return (int64_t)i * (i + 1) / 2; }
 
-// Shared-memory plan of one F^-1 sweep block: [Linv | G | T | xp | yp | xq]
-// (each region 16-byte aligned); `staged` is decided per launch.
+// Shared-memory plan of one F^-1 sweep block:
+// [mbarrier | Linv | G | T | xp | yp | xq] (each region 16-byte aligned).
 template <typename T, int R>
 struct SweepSmem {
+  uint64_t* mbar;
   T *Ls, *Gs, *Ts, *xp, *yp, *xq;
   __device__ SweepSmem(unsigned char* raw, int np, int nq, bool staged, bool front) {
-    T* p = reinterpret_cast<T*>(raw);
+    mbar = reinterpret_cast<uint64_t*>(raw);
+    T* p = reinterpret_cast<T*>(raw + 16);
     Ls = Gs = Ts = nullptr;
     if (staged) {
       Ls = p;
@@ -70,10 +109,28 @@ struct SweepSmem {
   }
 };
 
+// Columns per thread in the products: each thread owns one output row and a
+// group of CG consecutive right-hand sides (register accumulators).
+template <int R> struct ColGroup { static constexpr int CG = R < 4 ? R : 4; static constexpr int NG = R / CG; };
+
+template <typename T, int R>
+__device__ __forceinline__ void stage_factor(SweepSmem<T, R>& sm, BulkStage& bs, const T*& Linv, const T*& G,
+                                             const T*& Tm, int np, int nq, bool front) {
+  void* dst[3] = {sm.Ls, sm.Gs, sm.Ts};
+  const void* src[3] = {Linv, G, Tm};
+  uint32_t bytes[3] = {(uint32_t)(sizeof(T) * packed_size(np)), (uint32_t)(sizeof(T) * pad4((int64_t)nq * np)),
+                       front ? (uint32_t)(sizeof(T) * pad4((int64_t)nq * np)) : 0u};
+  bs.start(front ? 3 : 2, dst, src, bytes);
+  Linv = sm.Ls;
+  G = sm.Gs;
+  Tm = sm.Ts;
+}
+
 template <typename T, int R>
 __global__ void k_apply_up(const ApplyDesc* __restrict__ blocks, const int* __restrict__ ipool,
                            const T* __restrict__ fac, T* __restrict__ x, int nr, int ldx,
-                           int is_front, int staged) {
+                           int is_front, int staged, int* err) {
+  constexpr int CG = ColGroup<R>::CG, NG = ColGroup<R>::NG;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const ApplyDesc bd = blocks[blockIdx.x];
   const int np = bd.np, nq = bd.nq;
@@ -81,50 +138,63 @@ __global__ void k_apply_up(const ApplyDesc* __restrict__ blocks, const int* __re
   const int* idp = ipool + bd.ids;
   const int* idq = idp + np;
   SweepSmem<T, R> sm(smem_raw, np, nq, staged, is_front);
+  BulkStage bs{sm.mbar};
   const T* Linv = fac + bd.Linv;
   const T* G = fac + bd.G;
   const T* Tm = is_front ? fac + bd.T : nullptr;
-  if (staged) {
-    stage(sm.Ls, Linv, tri(np));
-    stage(sm.Gs, G, (int64_t)nq * np);
-    if (is_front) stage(sm.Ts, Tm, (int64_t)nq * np);
-    Linv = sm.Ls;
-    G = sm.Gs;
-    Tm = sm.Ts;
-  }
+  if (staged) stage_factor<T, R>(sm, bs, Linv, G, Tm, np, nq, is_front);
   T* xp = sm.xp;
   T* yp = sm.yp;
   T* xq = sm.xq;
   gather<T, R>(xp, x, idp, np, nr, ldx);
   if (is_front) gather<T, R>(xq, x, idq, nq, nr, ldx);
   __syncthreads();
+  if (staged && !bs.wait(err)) return;
   if (is_front && nq > 0) {                      // x_p -= T^T x_q
-    for (int e = threadIdx.x; e < np * R; e += blockDim.x) {
-      const int i = e / R, r = e % R;
-      T acc = T(0);
-      for (int s2 = 0; s2 < nq; ++s2) acc += Tm[(int64_t)s2 * np + i] * xq[s2 * R + r];
-      xp[e] -= acc;
+    for (int e = threadIdx.x; e < np * NG; e += blockDim.x) {
+      const int i = e / NG, c0 = (e % NG) * CG;
+      T acc[CG] = {};
+      for (int s2 = 0; s2 < nq; ++s2) {
+        const T t = Tm[(int64_t)s2 * np + i];
+#pragma unroll
+        for (int c = 0; c < CG; ++c) acc[c] += t * xq[s2 * R + c0 + c];
+      }
+#pragma unroll
+      for (int c = 0; c < CG; ++c) xp[i * R + c0 + c] -= acc[c];
     }
     __syncthreads();
   }
-  for (int e = threadIdx.x; e < np * R; e += blockDim.x) {   // y_p = Linv x_p
-    const int i = e / R, r = e % R;
+  for (int e = threadIdx.x; e < np * NG; e += blockDim.x) {   // y_p = Linv x_p
+    const int i = e / NG, c0 = (e % NG) * CG;
     const T* l = Linv + tri(i);
-    T acc = T(0);
-    for (int t = 0; t <= i; ++t) acc += l[t] * xp[t * R + r];
-    yp[e] = acc;
-    if (r < nr) x[(int64_t)idp[i] * ldx + r] = acc;
+    T acc[CG] = {};
+    for (int t = 0; t <= i; ++t) {
+      const T lv = l[t];
+#pragma unroll
+      for (int c = 0; c < CG; ++c) acc[c] += lv * xp[t * R + c0 + c];
+    }
+#pragma unroll
+    for (int c = 0; c < CG; ++c) {
+      yp[i * R + c0 + c] = acc[c];
+      if (c0 + c < nr) x[(int64_t)idp[i] * ldx + c0 + c] = acc[c];
+    }
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < nq * R; e += blockDim.x) {   // x_q -= G y_p
-    const int s2 = e / R, r = e % R;
+  for (int e = threadIdx.x; e < nq * NG; e += blockDim.x) {   // x_q -= G y_p
+    const int s2 = e / NG, c0 = (e % NG) * CG;
     const T* g = G + (int64_t)s2 * np;
-    T acc = T(0);
-    for (int t = 0; t < np; ++t) acc += g[t] * yp[t * R + r];
-    if (r < nr) {
-      T* dst = x + (int64_t)idq[s2] * ldx + r;
-      if (is_front) *dst = xq[e] - acc;
-      else atomicAdd(dst, -acc);
+    T acc[CG] = {};
+    for (int t = 0; t < np; ++t) {
+      const T gv = g[t];
+#pragma unroll
+      for (int c = 0; c < CG; ++c) acc[c] += gv * yp[t * R + c0 + c];
+    }
+#pragma unroll
+    for (int c = 0; c < CG; ++c) {
+      if (c0 + c >= nr) continue;
+      T* dst = x + (int64_t)idq[s2] * ldx + c0 + c;
+      if (is_front) *dst = xq[s2 * R + c0 + c] - acc[c];
+      else atomicAdd(dst, -acc[c]);
     }
   }
 }
@@ -132,7 +202,8 @@ __global__ void k_apply_up(const ApplyDesc* __restrict__ blocks, const int* __re
 template <typename T, int R>
 __global__ void k_apply_down(const ApplyDesc* __restrict__ blocks, const int* __restrict__ ipool,
                              const T* __restrict__ fac, T* __restrict__ x, int nr, int ldx,
-                             int is_front, int staged) {
+                             int is_front, int staged, int* err) {
+  constexpr int CG = ColGroup<R>::CG, NG = ColGroup<R>::NG;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const ApplyDesc bd = blocks[blockIdx.x];
   const int np = bd.np, nq = bd.nq;
@@ -140,47 +211,60 @@ __global__ void k_apply_down(const ApplyDesc* __restrict__ blocks, const int* __
   const int* idp = ipool + bd.ids;
   const int* idq = idp + np;
   SweepSmem<T, R> sm(smem_raw, np, nq, staged, is_front);
+  BulkStage bs{sm.mbar};
   const T* Linv = fac + bd.Linv;
   const T* G = fac + bd.G;
   const T* Tm = is_front ? fac + bd.T : nullptr;
-  if (staged) {
-    stage(sm.Ls, Linv, tri(np));
-    stage(sm.Gs, G, (int64_t)nq * np);
-    if (is_front) stage(sm.Ts, Tm, (int64_t)nq * np);
-    Linv = sm.Ls;
-    G = sm.Gs;
-    Tm = sm.Ts;
-  }
+  if (staged) stage_factor<T, R>(sm, bs, Linv, G, Tm, np, nq, is_front);
   T* xp = sm.xp;
   T* zp = sm.yp;
   T* xq = sm.xq;
   gather<T, R>(xp, x, idp, np, nr, ldx);
   gather<T, R>(xq, x, idq, nq, nr, ldx);
   __syncthreads();
+  if (staged && !bs.wait(err)) return;
   if (nq > 0) {                                  // w = x_p - G^T x_q (in place)
-    for (int e = threadIdx.x; e < np * R; e += blockDim.x) {
-      const int i = e / R, r = e % R;
-      T acc = T(0);
-      for (int s2 = 0; s2 < nq; ++s2) acc += G[(int64_t)s2 * np + i] * xq[s2 * R + r];
-      xp[e] -= acc;
+    for (int e = threadIdx.x; e < np * NG; e += blockDim.x) {
+      const int i = e / NG, c0 = (e % NG) * CG;
+      T acc[CG] = {};
+      for (int s2 = 0; s2 < nq; ++s2) {
+        const T gv = G[(int64_t)s2 * np + i];
+#pragma unroll
+        for (int c = 0; c < CG; ++c) acc[c] += gv * xq[s2 * R + c0 + c];
+      }
+#pragma unroll
+      for (int c = 0; c < CG; ++c) xp[i * R + c0 + c] -= acc[c];
     }
     __syncthreads();
   }
-  for (int e = threadIdx.x; e < np * R; e += blockDim.x) {   // z = Linv^T w
-    const int i = e / R, r = e % R;
-    T acc = T(0);
-    for (int t = i; t < np; ++t) acc += Linv[tri(t) + i] * xp[t * R + r];
-    zp[e] = acc;
-    if (r < nr) x[(int64_t)idp[i] * ldx + r] = acc;
+  for (int e = threadIdx.x; e < np * NG; e += blockDim.x) {   // z = Linv^T w
+    const int i = e / NG, c0 = (e % NG) * CG;
+    T acc[CG] = {};
+    for (int t = i; t < np; ++t) {
+      const T lv = Linv[tri(t) + i];
+#pragma unroll
+      for (int c = 0; c < CG; ++c) acc[c] += lv * xp[t * R + c0 + c];
+    }
+#pragma unroll
+    for (int c = 0; c < CG; ++c) {
+      zp[i * R + c0 + c] = acc[c];
+      if (c0 + c < nr) x[(int64_t)idp[i] * ldx + c0 + c] = acc[c];
+    }
   }
   if (is_front && nq > 0) {                      // x_q -= T z
     __syncthreads();
-    for (int e = threadIdx.x; e < nq * R; e += blockDim.x) {
-      const int s2 = e / R, r = e % R;
+    for (int e = threadIdx.x; e < nq * NG; e += blockDim.x) {
+      const int s2 = e / NG, c0 = (e % NG) * CG;
       const T* t = Tm + (int64_t)s2 * np;
-      T acc = T(0);
-      for (int c = 0; c < np; ++c) acc += t[c] * zp[c * R + r];
-      if (r < nr) x[(int64_t)idq[s2] * ldx + r] = xq[e] - acc;
+      T acc[CG] = {};
+      for (int c1 = 0; c1 < np; ++c1) {
+        const T tv = t[c1];
+#pragma unroll
+        for (int c = 0; c < CG; ++c) acc[c] += tv * zp[c1 * R + c0 + c];
+      }
+#pragma unroll
+      for (int c = 0; c < CG; ++c)
+        if (c0 + c < nr) x[(int64_t)idq[s2] * ldx + c0 + c] = xq[s2 * R + c0 + c] - acc[c];
     }
   }
 }
@@ -189,7 +273,8 @@ __global__ void k_apply_down(const ApplyDesc* __restrict__ blocks, const int* __
 template <typename T, int R>
 __global__ void k_fwd_up(const ApplyDesc* __restrict__ blocks, const int* __restrict__ ipool,
                          const T* __restrict__ fac, T* __restrict__ x, int nr, int ldx, int is_front,
-                         int staged) {
+                         int staged, int* err) {
+  (void)err;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   (void)staged;
   const ApplyDesc bd = blocks[blockIdx.x];
@@ -230,7 +315,8 @@ __global__ void k_fwd_up(const ApplyDesc* __restrict__ blocks, const int* __rest
 template <typename T, int R>
 __global__ void k_fwd_down(const ApplyDesc* __restrict__ blocks, const int* __restrict__ ipool,
                            const T* __restrict__ fac, T* __restrict__ x, int nr, int ldx, int is_front,
-                           int staged) {
+                           int staged, int* err) {
+  (void)err;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   (void)staged;
   const ApplyDesc bd = blocks[blockIdx.x];
@@ -277,7 +363,7 @@ constexpr size_t kStageCap = 96 * 1024;   // stage only when two blocks still fi
 
 template <typename T>
 static size_t vec_smem(int R, int max_np, int max_nq) {
-  return sizeof(T) * (size_t)(2 * pad4((int64_t)max_np * R) + 2 * pad4((int64_t)max_nq * R));
+  return 16 + sizeof(T) * (size_t)(2 * pad4((int64_t)max_np * R) + 2 * pad4((int64_t)max_nq * R));
 }
 
 template <typename T>
@@ -288,12 +374,12 @@ static size_t stage_smem(int max_np, int max_nq, int is_front) {
 template <typename T, int R>
 static void launch_sweep_R(int op, const ApplyDesc* blocks, int nblocks, const int* ipool,
                            const T* fac, T* x, int nr, int ldx, int is_front, int max_np,
-                           int max_nq, cudaStream_t st) {
+                           int max_nq, int* err, cudaStream_t st) {
   const size_t vsm = vec_smem<T>(R, max_np, max_nq);
   const size_t ssm = stage_smem<T>(max_np, max_nq, is_front);
   const int staged = (op <= 1) && (vsm + ssm <= kStageCap);
   const size_t smem = vsm + (staged ? ssm : 0);
-  void (*fn)(const ApplyDesc*, const int*, const T*, T*, int, int, int, int) = nullptr;
+  void (*fn)(const ApplyDesc*, const int*, const T*, T*, int, int, int, int, int*) = nullptr;
   switch (op) {
     case 0: fn = k_apply_up<T, R>; break;
     case 1: fn = k_apply_down<T, R>; break;
@@ -308,7 +394,7 @@ static void launch_sweep_R(int op, const ApplyDesc* blocks, int nblocks, const i
     smem_set[op] = kSweepSmemCap;
   }
   note_launches(1);
-  fn<<<nblocks, 256, smem, st>>>(blocks, ipool, fac, x, nr, ldx, is_front, staged);
+  fn<<<nblocks, 256, smem, st>>>(blocks, ipool, fac, x, nr, ldx, is_front, staged, err);
 }
 
 template <typename T>
@@ -320,26 +406,26 @@ int sweep_chunk(int max_np, int max_nq, int nrhs) {
 
 template <typename T>
 void launch_sweep(int op, const ApplyDesc* blocks, int nblocks, const int* ipool, const T* fac,
-                  T* x, int nrhs, int ldx, int is_front, int max_np, int max_nq, cudaStream_t st) {
+                  T* x, int nrhs, int ldx, int is_front, int max_np, int max_nq, int* err, cudaStream_t st) {
   if (nblocks == 0) return;
   const int R = sweep_chunk<T>(max_np, max_nq, nrhs);
   for (int r0 = 0; r0 < nrhs; r0 += R) {
     const int nr = (nrhs - r0) < R ? (nrhs - r0) : R;
     T* xr = x + r0;
     switch (R) {
-      case 32: launch_sweep_R<T, 32>(op, blocks, nblocks, ipool, fac, xr, nr, ldx, is_front, max_np, max_nq, st); break;
-      case 16: launch_sweep_R<T, 16>(op, blocks, nblocks, ipool, fac, xr, nr, ldx, is_front, max_np, max_nq, st); break;
-      case 8: launch_sweep_R<T, 8>(op, blocks, nblocks, ipool, fac, xr, nr, ldx, is_front, max_np, max_nq, st); break;
-      case 4: launch_sweep_R<T, 4>(op, blocks, nblocks, ipool, fac, xr, nr, ldx, is_front, max_np, max_nq, st); break;
-      case 2: launch_sweep_R<T, 2>(op, blocks, nblocks, ipool, fac, xr, nr, ldx, is_front, max_np, max_nq, st); break;
-      default: launch_sweep_R<T, 1>(op, blocks, nblocks, ipool, fac, xr, nr, ldx, is_front, max_np, max_nq, st); break;
+      case 32: launch_sweep_R<T, 32>(op, blocks, nblocks, ipool, fac, xr, nr, ldx, is_front, max_np, max_nq, err, st); break;
+      case 16: launch_sweep_R<T, 16>(op, blocks, nblocks, ipool, fac, xr, nr, ldx, is_front, max_np, max_nq, err, st); break;
+      case 8: launch_sweep_R<T, 8>(op, blocks, nblocks, ipool, fac, xr, nr, ldx, is_front, max_np, max_nq, err, st); break;
+      case 4: launch_sweep_R<T, 4>(op, blocks, nblocks, ipool, fac, xr, nr, ldx, is_front, max_np, max_nq, err, st); break;
+      case 2: launch_sweep_R<T, 2>(op, blocks, nblocks, ipool, fac, xr, nr, ldx, is_front, max_np, max_nq, err, st); break;
+      default: launch_sweep_R<T, 1>(op, blocks, nblocks, ipool, fac, xr, nr, ldx, is_front, max_np, max_nq, err, st); break;
     }
   }
 }
 
 template void launch_sweep<double>(int, const ApplyDesc*, int, const int*, const double*, double*,
-                                   int, int, int, int, int, cudaStream_t);
+                                   int, int, int, int, int, int*, cudaStream_t);
 template void launch_sweep<float>(int, const ApplyDesc*, int, const int*, const float*, float*,
-                                  int, int, int, int, int, cudaStream_t);
+                                  int, int, int, int, int, int*, cudaStream_t);
 
 }  // namespace hif

@@ -20,6 +20,28 @@ static inline int vec_blocks(int64_t n) {
   return (int)(b < kVecBlocksMax ? (b > 0 ? b : 1) : kVecBlocksMax);
 }
 
+// In the last block: out[v] = sum over blocks b (in block order within each
+// thread's stride, then a fixed tree) of partials[b * nv + v].  Every thread
+// takes value v = tid % nv and the blocks b = tid / nv + k * (blockDim / nv),
+// so the partials are read with many loads in flight.  nv <= blockDim.x.
+__device__ void last_block_sum(const double* partials, int nv, double* shr, double* out) {
+  const int tid = threadIdx.x;
+  const int lanes = blockDim.x / nv;           // threads per value
+  double s = 0.0;
+  if (tid < lanes * nv) {
+    const int v = tid % nv;
+    for (int b = tid / nv; b < (int)gridDim.x; b += lanes) s += partials[(int64_t)b * nv + v];
+  }
+  __syncthreads();
+  shr[tid] = s;
+  __syncthreads();
+  for (int step = lanes >> 1; step > 0; step >>= 1) {
+    if (tid < step * nv) shr[tid] += shr[tid + step * nv];
+    __syncthreads();
+  }
+  if (tid < nv) out[tid] = shr[tid];
+}
+
 // Sum acc[0..nv) over the grid into out[0..nv).  Needs nv*blockDim.x doubles
 // of dynamic shared memory.
 template <int NV>
@@ -42,11 +64,7 @@ __device__ void grid_reduce(const double (&acc)[NV], int nv, double* partials, u
   __syncthreads();
   if (!last) return;
   __threadfence();
-  for (int v = tid; v < nv; v += blockDim.x) {
-    double s = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) s += partials[(int64_t)b * nv + v];
-    out[v] = s;
-  }
+  last_block_sum(partials, nv, shr, out);
   if (tid == 0) *counter = 0u;
 }
 
@@ -286,43 +304,74 @@ __device__ void grid_reduce_cols(const double (&acc)[NG], double* partials, unsi
   __syncthreads();
   if (!last) return;
   __threadfence();
-  for (int v = tid; v < NG * R; v += blockDim.x) {
-    const int g = v / R, c = v % R;
-    double s = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) s += partials[((int64_t)b * NG + g) * R + c];
-    out[v] = s;
-  }
+  last_block_sum(partials, NG * R, &shr[0][0], out);
   if (tid == 0) *counter = 0u;
 }
 
-// (A x)[e] for element e = gid * R + c
-template <int R>
-__device__ __forceinline__ double stencil_elem(const Stencil& S, int64_t gid, int c, const double* x) {
-  const int m = S.g.m, dim = S.g.dim;
-  const int jj[3] = {(int)(gid % m) + 1, (int)((gid / m) % m) + 1,
-                     dim == 3 ? (int)(gid / ((int64_t)m * m)) + 1 : 1};
-  const int64_t stride[3] = {1, m, (int64_t)m * m};
+// Stencil weights, computed once per problem: W[i*S + 0] = diagonal,
+// W[i*S + 1 + 2*axis + side] = coupling to the neighbour below (side 0) or
+// above (side 1) along axis (0 when that neighbour is a boundary node),
+// S = 2 dim + 1.
+__global__ void k_stencil_weights(Stencil S, int64_t N, double* __restrict__ W) {
+  const int m = S.g.m, dim = S.g.dim, ns = 2 * dim + 1;
   const double h2 = S.g.inv_h2;
-  double diag = S.bnode[gid];
-  double y = 0.0;
-  for (int ax = 0; ax < dim; ++ax) {
-    int lo[3] = {jj[0], jj[1], jj[2]};
-    lo[ax] -= 1;
-    const double alo = sbond(S, ax, lo[0], lo[1], lo[2]) * h2;
-    const double ahi = sbond(S, ax, jj[0], jj[1], jj[2]) * h2;
-    diag += alo + ahi;
-    if (jj[ax] > 1) y -= alo * x[(gid - stride[ax]) * R + c];
-    if (jj[ax] < m) y -= ahi * x[(gid + stride[ax]) * R + c];
+  GRID_LOOP(gid, N) {
+    const int jj[3] = {(int)(gid % m) + 1, (int)((gid / m) % m) + 1,
+                       dim == 3 ? (int)(gid / ((int64_t)m * m)) + 1 : 1};
+    double diag = S.bnode[gid];
+    for (int ax = 0; ax < dim; ++ax) {
+      int lo[3] = {jj[0], jj[1], jj[2]};
+      lo[ax] -= 1;
+      const double alo = sbond(S, ax, lo[0], lo[1], lo[2]) * h2;
+      const double ahi = sbond(S, ax, jj[0], jj[1], jj[2]) * h2;
+      diag += alo + ahi;
+      W[gid * ns + 1 + 2 * ax] = jj[ax] > 1 ? -alo : 0.0;
+      W[gid * ns + 2 + 2 * ax] = jj[ax] < m ? -ahi : 0.0;
+    }
+    W[gid * ns] = diag;
   }
-  return y + diag * x[gid * R + c];
 }
 
-template <int R>
-__global__ void k_mv_dot_e(Stencil S, int64_t N, const double* __restrict__ p, double* __restrict__ q,
-                           double* partials, unsigned* counter, double* pq) {
+// (A x)[e] for element e = gid * R + c from the weights (boundary neighbours
+// have weight 0 and are read at the node itself)
+template <int R, int DIM>
+__device__ __forceinline__ double stencil_w(const double* __restrict__ W, int m, int64_t gid, int c,
+                                            const double* __restrict__ x) {
+  constexpr int ns = 2 * DIM + 1;
+  const double* w = W + gid * ns;
+  const int64_t stride[3] = {1, m, (int64_t)m * m};
+  double y = w[0] * x[gid * R + c];
+#pragma unroll
+  for (int ax = 0; ax < DIM; ++ax) {
+    const int64_t lo = w[1 + 2 * ax] != 0.0 ? gid - stride[ax] : gid;
+    const int64_t hi = w[2 + 2 * ax] != 0.0 ? gid + stride[ax] : gid;
+    y = fma(w[1 + 2 * ax], x[lo * R + c], y);
+    y = fma(w[2 + 2 * ax], x[hi * R + c], y);
+  }
+  return y;
+}
+
+template <int R, int DIM>
+__global__ void k_mv_dot_e(const double* __restrict__ W, int m, int64_t N, const double* __restrict__ p,
+                           double* __restrict__ q, double* partials, unsigned* counter, double* pq) {
   double acc[1] = {0.0};
-  GRID_LOOP(e, N * R) {
-    const double v = stencil_elem<R>(S, e / R, (int)(e % R), p);
+  const int64_t n = N * R, stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; e + 3 * stride < n; e += 4 * stride) {
+    double v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t eu = e + u * stride;
+      v[u] = stencil_w<R, DIM>(W, m, eu / R, (int)(eu % R), p);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      q[e + u * stride] = v[u];
+      acc[0] = fma(v[u], p[e + u * stride], acc[0]);
+    }
+  }
+  for (; e < n; e += stride) {
+    const double v = stencil_w<R, DIM>(W, m, e / R, (int)(e % R), p);
     q[e] = v;
     acc[0] = fma(v, p[e], acc[0]);
   }
@@ -339,7 +388,27 @@ __global__ void k_axpy2_e(int64_t N, double* __restrict__ x, double* __restrict_
   const double a = (active[c] && pq[c] != 0.0) ? rz[c] / pq[c] : 0.0;
   if (blockIdx.x == 0 && threadIdx.x < R) alpha_out[threadIdx.x] = a;
   double acc[1] = {0.0};
-  GRID_LOOP(e, N * R) {
+  const int64_t n = N * R, stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; e + 3 * stride < n; e += 4 * stride) {
+    double xv[4], pv[4], qv[4], rv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      xv[u] = x[e + u * stride];
+      pv[u] = p[e + u * stride];
+      qv[u] = q[e + u * stride];
+      rv[u] = r[e + u * stride];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      x[e + u * stride] = fma(a, pv[u], xv[u]);
+      const double rn = fma(-a, qv[u], rv[u]);
+      r[e + u * stride] = rn;
+      zin[e + u * stride] = (TZ)rn;
+      acc[0] = fma(rn, rn, acc[0]);
+    }
+  }
+  for (; e < n; e += stride) {
     x[e] = fma(a, p[e], x[e]);
     const double rv = fma(-a, q[e], r[e]);
     r[e] = rv;
@@ -354,7 +423,23 @@ template <int R, typename TZ>
 __global__ void k_dot2_e(int64_t N, const double* __restrict__ r, const TZ* __restrict__ z,
                          const double* __restrict__ q, double* partials, unsigned* counter, double* out) {
   double acc[2] = {0.0, 0.0};
-  GRID_LOOP(e, N * R) {
+  const int64_t n = N * R, stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; e + 3 * stride < n; e += 4 * stride) {
+    double rv[4], zv[4], qv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      rv[u] = r[e + u * stride];
+      zv[u] = (double)z[e + u * stride];
+      qv[u] = q[e + u * stride];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      acc[0] = fma(rv[u], zv[u], acc[0]);
+      acc[1] = fma(zv[u], qv[u], acc[1]);
+    }
+  }
+  for (; e < n; e += stride) {
     const double zv = (double)z[e];
     acc[0] = fma(r[e], zv, acc[0]);
     acc[1] = fma(zv, q[e], acc[1]);
@@ -371,7 +456,19 @@ __global__ void k_update_p_e(int64_t N, double* __restrict__ p, const TZ* __rest
   if (!active[c]) return;
   const bool rs = restart || rz_old[c] == 0.0;
   const double beta = rs ? 0.0 : -alpha[c] * rzzq[R + c] / rz_old[c];
-  GRID_LOOP(e, N * R) {
+  const int64_t n = N * R, stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; e + 3 * stride < n; e += 4 * stride) {
+    double zv[4], pv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      zv[u] = (double)z[e + u * stride];
+      pv[u] = p[e + u * stride];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) p[e + u * stride] = rs ? zv[u] : fma(beta, pv[u], zv[u]);
+  }
+  for (; e < n; e += stride) {
     const double zv = (double)z[e];
     p[e] = rs ? zv : fma(beta, p[e], zv);
   }
@@ -603,12 +700,23 @@ static inline int elem_blocks(int64_t n) {
   return vec_blocks(n);
 }
 
-void launch_mv_dot_e(GridInfo g, const double* a_stag, const double* b, const double* p, double* q,
-                     int R_, double* partials, unsigned* counter, double* pq, cudaStream_t st) {
+void launch_stencil_weights(GridInfo g, const double* a_stag, const double* b, double* W, cudaStream_t st) {
   const int64_t N = grid_n(g);
   Stencil S{g, a_stag, b};
   note_launches(1);
-  DISPATCH_POW2(R_, k_mv_dot_e<R><<<elem_blocks(N * R), kVecThreads, 0, st>>>(S, N, p, q, partials, counter, pq));
+  k_stencil_weights<<<vec_blocks(N), kVecThreads, 0, st>>>(S, N, W);
+}
+
+void launch_mv_dot_e(GridInfo g, const double* W, const double* p, double* q, int R_, double* partials,
+                     unsigned* counter, double* pq, cudaStream_t st) {
+  const int64_t N = grid_n(g);
+  note_launches(1);
+  if (g.dim == 2)
+    DISPATCH_POW2(R_, (k_mv_dot_e<R, 2><<<elem_blocks(N * R), kVecThreads, 0, st>>>(W, g.m, N, p, q, partials,
+                                                                                    counter, pq)));
+  else
+    DISPATCH_POW2(R_, (k_mv_dot_e<R, 3><<<elem_blocks(N * R), kVecThreads, 0, st>>>(W, g.m, N, p, q, partials,
+                                                                                    counter, pq)));
 }
 
 template <typename TZ>
