@@ -327,6 +327,29 @@ def run_gpu(args, rank, world, local_rank):
     return 0
 
 
+def run_apply_only(args):
+    """Factor the workload once and run a number of F^-1 applies (8 RHS):
+    the command ncu captures the sweep kernels of."""
+    import torch
+    from paper_1307_2895_gb300 import hif
+    hif.load()
+    w, f_np = _workload_arrays()
+    dev = torch.device("cuda", 0)
+    st = torch.cuda.Stream(device=dev)
+    a = torch.from_numpy(w["a_stag"]).to(dev)
+    b = torch.from_numpy(w["b"]).to(dev)
+    f = torch.from_numpy(f_np).to(dev)
+    G = hif.factor(w["dim"], w["n"], a, b, w["eps"], precision=args.precision, stream=st)
+    try:
+        for _ in range(args.ncu_apply):
+            G.apply(f)
+        torch.cuda.synchronize()
+        print(json.dumps({"applies": args.ncu_apply, "stats": G.stats()}))
+    finally:
+        G.free()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -337,7 +360,11 @@ def main():
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--ncu-apply", type=int, default=0,
+                    help="profiling helper: factor the workload, then run this many F^-1 applies and exit")
     args = ap.parse_args()
+    if args.ncu_apply:
+        return run_apply_only(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

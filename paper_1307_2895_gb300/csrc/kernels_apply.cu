@@ -386,15 +386,22 @@ static void launch_sweep_R(int op, const ApplyDesc* blocks, int nblocks, const i
     case 2: fn = k_fwd_up<T, R>; break;
     default: fn = k_fwd_down<T, R>; break;
   }
-  // raise the dynamic shared-memory limit once per kernel (not again while a
-  // stream capture records the launch)
-  static size_t smem_set[4] = {48 * 1024, 48 * 1024, 48 * 1024, 48 * 1024};
-  if (smem > smem_set[op]) {
+  // raise the dynamic shared-memory limit and prefer the largest shared
+  // carveout once per kernel (not again while a stream capture records it)
+  static bool attr_set[4] = {false, false, false, false};
+  if (!attr_set[op]) {
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSweepSmemCap);
-    smem_set[op] = kSweepSmemCap;
+    cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    attr_set[op] = true;
   }
+  // one thread per (row, column group) of the largest product, in warps,
+  // so that small blocks leave room for more resident blocks per SM
+  constexpr int NG = ColGroup<R>::NG;
+  int work = (max_np > max_nq ? max_np : max_nq) * NG;
+  int threads = ((work + 31) / 32) * 32;
+  threads = threads < 32 ? 32 : (threads > 256 ? 256 : threads);
   note_launches(1);
-  fn<<<nblocks, 256, smem, st>>>(blocks, ipool, fac, x, nr, ldx, is_front, staged, err);
+  fn<<<nblocks, threads, smem, st>>>(blocks, ipool, fac, x, nr, ldx, is_front, staged, err);
 }
 
 template <typename T>
