@@ -75,13 +75,23 @@ typedef struct hif_grid {
   int variant;  /* HIF_VARIANT_*                                                */
 } hif_grid;
 
+/* ID modes (Section 4.3): the pivoted-QR ID of A_{N,c}; or an ID of the
+ * Gaussian sketch Phi A_{N,c} with ell = k_hat + oversample rows, accepted only
+ * if ||A_r - A_s T||_F <= eps ||A||_F and k < ell (else the pivoted-QR ID of
+ * A_{N,c}), with k_hat = ceil(|c|/2) (RAND) or predicted per front by the
+ * rank MLP (LEARNED, opts.rank_model required). */
+enum { HIF_ID_QR = 0, HIF_ID_RAND = 1, HIF_ID_LEARNED = 2 };
+
 typedef struct hif_opts {
   int precision;        /* HIF_PREC_*                                           */
   int skip_levels;      /* fractional levels l + 1/2 skipped for l < skip_levels
                            (Section 5: "the first few fractional levels ...")    */
-  int reserved0;
-  int reserved1;
+  int id_mode;          /* HIF_ID_*                                             */
+  int oversample;       /* sketch rows beyond k_hat (0 -> 10)                    */
   void* stream;         /* cudaStream_t for all device work                     */
+  const float* rank_model; /* HIF_ID_LEARNED: HIF_MLP_PARAMS floats (see
+                              hif_mlp_train), host or device memory            */
+  unsigned long long seed; /* counter-based sketch RNG seed                     */
 } hif_opts;
 
 typedef struct hif_handle hif_handle;
@@ -102,6 +112,9 @@ typedef struct hif_stats_t {
   int max_front_rank;          /* largest skeleton size k                        */
   int near_threshold_fronts;   /* fronts with a pivot ratio within 1e-8 of eps   */
   int clamped_pivots;          /* MIXED: Cholesky pivots raised to the floor     */
+  int sketched_fronts;         /* fronts whose sketched ID passed the check      */
+  int fallback_fronts;         /* fronts that fell back to the pivoted-QR ID     */
+  double t_fronts_ms;          /* device time of the front (ID) launches         */
   long long factor_bytes;      /* m_f: bytes of the stored factor                */
   double factor_flops;         /* algorithmic flops of the factorization         */
   double apply_bytes;          /* factor bytes read by one apply of F^-1         */
@@ -199,6 +212,39 @@ long long hif_kernel_launches(void);
 int hif_residual_norms_noalloc(int dim, int n, const double* a_stag, const double* b,
                                const double* f, const double* x, int nrhs, int ld,
                                double* rnorm2, void* stream);
+
+/*
+ * Rank-prediction MLP (no counterpart in the paper; it sizes the sketch of
+ * HIF_ID_LEARNED).  Input: HIF_MLP_FEATURES features per front (level,
+ * log2 |c|, log2 |N|, log10 eps, min / max / mean / std / spread of log10 a
+ * over the front DOFs' stencil couplings, dim); output: a prediction of
+ * log(1 + k).  Three layers of width 64 with ReLU; parameters flat float:
+ * W1 (64 x 10) | b1 | W2 (64 x 64) | b2 | W3 (1 x 64) | b3, HIF_MLP_PARAMS
+ * floats.  Loss: mean Huber loss (delta 1).  All pointers of these three
+ * calls are device pointers; stream may be NULL.
+ */
+#define HIF_MLP_FEATURES 10
+#define HIF_MLP_PARAMS 4929
+
+/* hif_front_log -- features (count x 10 floats), ranks k and sizes |c| of every
+ * front of a factorization (the training data of the rank MLP).  Host
+ * pointers; nothing is written if cap < count; *count receives the count. */
+int hif_front_log(const hif_handle* h, float* feats, int32_t* ranks, int32_t* sizes, long long cap,
+                  long long* count);
+
+/* hif_mlp_grad -- loss and gradient (mean over the n samples) at params (FP32). */
+int hif_mlp_grad(const float* X, const float* target, int n, const float* params, float* grad,
+                 float* loss, void* stream);
+
+/* hif_mlp_train -- steps of Adam (lr) on minibatches of `batch` samples taken
+ * in a seeded shuffled order; params updated in place; loss_hist (may be
+ * NULL) receives the minibatch loss of every step. */
+int hif_mlp_train(const float* X, const float* target, int n, float* params, int steps, int batch,
+                  float lr, unsigned long long seed, float* loss_hist, void* stream);
+
+/* hif_mlp_predict -- y = MLP(X) with the parameters rounded to BF16, FP32
+ * accumulation (the inference used inside hif_factor). */
+int hif_mlp_predict(const float* X, int n, const float* params, float* y, void* stream);
 
 /* hif_free -- release the factor (stream-ordered on the handle's stream). */
 void hif_free(hif_handle* h);

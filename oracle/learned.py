@@ -1,0 +1,90 @@
+"""Randomized ID and the rank-prediction MLP, in plain FP64 numpy.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+* :func:`randomized_id` -- the randomized ID mentioned in Section 4.3 (and
+  again at the end of Section 4.5): compress ``Phi M`` instead of ``M``, with
+  ``Phi`` a Gaussian sampling matrix of ``ell`` rows (passed in as an input),
+  then accept the result only if the interpolation residual of ``M`` itself
+  passes the check ``||M_r - M_s T||_F <= eps ||M||_F``; otherwise the caller
+  falls back to the pivoted-QR ID of ``M`` (Lemma 2.2).  The skeleton choice
+  is not comparable with the GPU's (different random numbers): parity is
+  pinned by the residual check and by the end-to-end residual only.
+* :class:`MLP` -- the rank predictor: three layers of width 64 with ReLU,
+  target log(1 + k), Huber loss (delta 1), mean over samples.  Forward and
+  backward written out; gradients are pinned by central finite differences
+  in ``tests/test_oracle_learned.py``.
+
+Parity status: the MLP gradients are pinned (finite differences); the
+randomized ID is pinned by exact low-rank cases (it must recover the rank and
+interpolate to rounding) and by its fallback on an undersized sketch.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .hifde import interp_decomp
+
+HUBER_DELTA = 1.0
+
+
+def randomized_id(M: np.ndarray, eps: float, Phi: np.ndarray):
+    """ID of M from the sketch Y = Phi M.  Returns (IDResult, ok) where ok says
+    the residual check passed and the sketch was not saturated (k < ell)."""
+    Y = Phi @ M
+    idr = interp_decomp(Y, eps)
+    k, ell = len(idr.sk), Phi.shape[0]
+    E = M[:, idr.rd] - M[:, idr.sk] @ idr.T
+    ok = bool(k < ell and np.linalg.norm(E) <= eps * np.linalg.norm(M))
+    return idr, ok
+
+
+class MLP:
+    """y = W3 relu(W2 relu(W1 x + b1) + b2) + b3, hidden width H."""
+
+    def __init__(self, params):
+        self.W1, self.b1, self.W2, self.b2, self.W3, self.b3 = [np.asarray(p, dtype=np.float64) for p in params]
+
+    @staticmethod
+    def unpack(flat: np.ndarray, nin: int, H: int = 64):
+        """Split the flat parameter vector (layout: W1 (H x nin) row-major, b1,
+        W2 (H x H), b2, W3 (1 x H), b3)."""
+        sizes = [H * nin, H, H * H, H, H, 1]
+        out, off = [], 0
+        for s in sizes:
+            out.append(np.asarray(flat[off:off + s], dtype=np.float64))
+            off += s
+        W1, b1, W2, b2, W3, b3 = out
+        return MLP([W1.reshape(H, nin), b1, W2.reshape(H, H), b2, W3.reshape(1, H), b3])
+
+    def flat(self) -> np.ndarray:
+        return np.concatenate([self.W1.ravel(), self.b1, self.W2.ravel(), self.b2, self.W3.ravel(), self.b3])
+
+    def forward(self, X: np.ndarray):
+        Z1 = X @ self.W1.T + self.b1
+        H1 = np.maximum(Z1, 0.0)
+        Z2 = H1 @ self.W2.T + self.b2
+        H2 = np.maximum(Z2, 0.0)
+        y = (H2 @ self.W3.T + self.b3)[:, 0]
+        return y, (X, Z1, H1, Z2, H2)
+
+    def loss_and_grad(self, X: np.ndarray, t: np.ndarray):
+        """Mean Huber loss of (y - t) and its gradient (flat, same layout)."""
+        y, (X, Z1, H1, Z2, H2) = self.forward(X)
+        d = y - t
+        n = len(t)
+        loss = np.where(np.abs(d) <= HUBER_DELTA, 0.5 * d * d,
+                        HUBER_DELTA * (np.abs(d) - 0.5 * HUBER_DELTA)).mean()
+        g = np.clip(d, -HUBER_DELTA, HUBER_DELTA) / n          # dL/dy
+        gW3 = g[None, :] @ H2                                   # 1 x H
+        gb3 = np.array([g.sum()])
+        gH2 = g[:, None] * self.W3                              # n x H
+        gZ2 = gH2 * (Z2 > 0)
+        gW2 = gZ2.T @ H1
+        gb2 = gZ2.sum(axis=0)
+        gH1 = gZ2 @ self.W2
+        gZ1 = gH1 * (Z1 > 0)
+        gW1 = gZ1.T @ X
+        gb1 = gZ1.sum(axis=0)
+        grad = np.concatenate([gW1.ravel(), gb1, gW2.ravel(), gb2, gW3.ravel(), gb3])
+        return loss, grad

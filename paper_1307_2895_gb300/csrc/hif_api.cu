@@ -124,6 +124,7 @@ struct LevelFronts {
   std::shared_ptr<const std::vector<HostFront>> fr;
   std::shared_ptr<const std::vector<FrontDesc>> fd;
   std::vector<int> out;     // host copy of the front kernel's outputs
+  DevBuf feats;             // rank-predictor features, nf x kFeat floats
 };
 
 // Rank-independent structure of level 0 of one grid (cells and the fronts of
@@ -158,17 +159,23 @@ struct hif_handle {
   int precision = HIF_PREC_FP64;
   int variant = HIF_VARIANT_HIFDE;
   int skip_levels = 0;
+  int id_mode = HIF_ID_QR;
+  int oversample = 10;
+  unsigned long long seed = 0;
   double eps = 0.0;
   cudaStream_t st = nullptr;
   cudaStream_t own_stream = nullptr;   // created when the caller passes no stream
   DevBuf a_stag, bnode;
   DevBuf dev_err;   // device status of the apply kernels (bit 3: a bounded wait ran out)
   DevBuf stencil_w; // per-node stencil weights (diagonal and neighbour couplings)
+  DevBuf model_bf16; // rank-predictor parameters in BF16 (HIF_ID_LEARNED)
   std::shared_ptr<const Level0> level0;
   std::vector<SweepLevel> cells, fronts;   // levels 0..L-1
   SweepLevel root;                         // level L
   std::vector<LevelFronts> finfo;
   int root_size = 0, n_cells = 0, n_fronts = 0, max_rank = 0, near = 0, clamped = 0;
+  int sketched = 0, fallback = 0;
+  double t_fronts_ms = 0.0;
   long long factor_bytes = 0;
   double factor_flops = 0.0, apply_bytes = 0.0, t_factor_ms = 0.0;
   // optional event timing of the F^-1 sweep launches
@@ -267,7 +274,7 @@ void prepare_fronts(const std::vector<HostFront>& fr, std::vector<FrontDesc>& fd
     d.out = out_elems;
     out_elems += 1 + 2 * d.nc;
     d.work = work_elems;
-    work_elems += (int64_t)d.nN * d.nc + 4 * (int64_t)d.nc * d.nc;
+    work_elems += 2 * (int64_t)d.nN * d.nc + 4 * (int64_t)d.nc * d.nc;
     d.fac = fac_elems;
     fac_elems += front_fac_size(d.nc);
     max_nc = std::max(max_nc, d.nc);
@@ -355,8 +362,8 @@ struct Factorizer {
 
   void run() {
     const int L = G.L, nchild = 1 << G.dim;
-    status.alloc(2 * sizeof(int), st);
-    CU(cudaMemsetAsync(status.p, 0, 2 * sizeof(int), st));
+    status.alloc(4 * sizeof(int), st);
+    CU(cudaMemsetAsync(status.p, 0, 4 * sizeof(int), st));
     dead.assign(G.N, 0);
     h->cells.resize(L);
     h->fronts.resize(L);
@@ -468,11 +475,13 @@ struct Factorizer {
       prev_ddesc = dd;
       prev_work.swap(work);
     }
-    int hs2[2] = {0, 0};
-    CU(cudaMemcpyAsync(hs2, status.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    int hs2[4] = {0, 0, 0, 0};
+    CU(cudaMemcpyAsync(hs2, status.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
     const int hs = hs2[0];
     h->clamped = hs2[1];
+    h->sketched = hs2[2];
+    h->fallback = hs2[3];
     if (hs & 1) throw HifError(HIF_ERR_NOT_SPD, "non-positive pivot in a diagonal-block Cholesky");
   }
 
@@ -486,15 +495,32 @@ struct Factorizer {
     const int nf = (int)fd.size();
     SweepLevel& sw = h->fronts[l];
     if (nf == 0) return;
-    DevBuf fwork, obuf;
+    DevBuf fwork, obuf, pred, sketch;
     fwork.alloc((size_t)work_elems * sizeof(T), st);
     obuf.alloc((size_t)out_elems * sizeof(int), st);
     sw.fac.alloc((size_t)fac_elems * sizeof(T), st);
-    launch_front<T>(d_fd, nf, d_cdesc, d_ip, obuf.as<int>(), fwork.as<T>(), sw.fac.as<T>(), cwork.as<T>(), h->eps,
-                    status.as<int>(), max_nc, max_nN, tau, st);
-    CU(cudaGetLastError());
     LevelFronts info;
     info.level = l;
+    info.feats.alloc((size_t)nf * kFeat * sizeof(float), st);
+    launch_front_features(d_fd, nf, d_ip, h->stencil_w.as<double>(), G.dim, G.n, l, h->eps, info.feats.as<float>(),
+                          st);
+    if (h->id_mode != HIF_ID_QR) {
+      sketch.alloc((size_t)nf * sizeof(int), st);
+      if (h->id_mode == HIF_ID_LEARNED) {
+        pred.alloc((size_t)nf * sizeof(float), st);
+        mlp_predict(info.feats.as<float>(), nf, h->model_bf16.p, pred.as<float>(), st);
+      }
+      launch_sketch_sizes(d_fd, nf, pred.as<float>(), h->id_mode, h->oversample, sketch.as<int>(), st);
+    }
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    CU(cudaEventRecord(e0, st));
+    launch_front<T>(d_fd, nf, d_cdesc, d_ip, obuf.as<int>(), fwork.as<T>(), sw.fac.as<T>(), cwork.as<T>(), h->eps,
+                    status.as<int>(), max_nc, max_nN, tau, sketch.as<int>(),
+                    h->seed * 0x9E3779B97F4A7C15ull + (uint64_t)l, st);
+    CU(cudaEventRecord(e1, st));
+    CU(cudaGetLastError());
     info.fr = fr;
     info.fd = fdp;
     info.out.resize(out_elems);
@@ -502,6 +528,13 @@ struct Factorizer {
     int hstat = 0;
     CU(cudaMemcpyAsync(&hstat, status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
+    {
+      float ms = 0.f;
+      CU(cudaEventElapsedTime(&ms, e0, e1));
+      h->t_fronts_ms += ms;
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+    }
     if (hstat & 2) {
       h->near += 1;
       const int keep = hstat & 1;
@@ -1013,6 +1046,12 @@ int hif_factor(const hif_grid* grid, const double* a_stag, const double* b, cons
     h->variant = grid->variant;
     h->eps = grid->variant == HIF_VARIANT_HIFDE ? eps : 0.0;
     h->skip_levels = opts ? std::max(0, opts->skip_levels) : 0;
+    h->id_mode = opts ? opts->id_mode : HIF_ID_QR;
+    if (h->id_mode < HIF_ID_QR || h->id_mode > HIF_ID_LEARNED) throw HifError(HIF_ERR_ARG, "unknown id_mode");
+    h->oversample = (opts && opts->oversample > 0) ? opts->oversample : 10;
+    h->seed = opts ? opts->seed : 0;
+    if (h->id_mode == HIF_ID_LEARNED && !(opts && opts->rank_model))
+      throw HifError(HIF_ERR_ARG, "HIF_ID_LEARNED needs opts.rank_model");
     h->st = opts ? (cudaStream_t)opts->stream : nullptr;
     if (!h->st) {
       // a blocking stream: ordered with the legacy default stream like NULL,
@@ -1027,6 +1066,13 @@ int hif_factor(const hif_grid* grid, const double* a_stag, const double* b, cons
     h->bnode.alloc(sizeof(double) * h->G.N, h->st);
     CU(cudaMemcpyAsync(h->a_stag.p, a_stag, sizeof(double) * na, cudaMemcpyDefault, h->st));
     CU(cudaMemcpyAsync(h->bnode.p, b, sizeof(double) * h->G.N, cudaMemcpyDefault, h->st));
+    if (h->id_mode == HIF_ID_LEARNED) {
+      DevBuf m32;
+      m32.alloc(sizeof(float) * kMlpParams, h->st);
+      CU(cudaMemcpyAsync(m32.p, opts->rank_model, sizeof(float) * kMlpParams, cudaMemcpyDefault, h->st));
+      h->model_bf16.alloc(2 * kMlpParams, h->st);
+      mlp_to_bf16(m32.as<float>(), h->model_bf16.p, h->st);
+    }
     h->stencil_w.alloc(sizeof(double) * h->G.N * (2 * grid->dim + 1), h->st);
     launch_stencil_weights(h->gi, h->a_stag.as<double>(), h->bnode.as<double>(), h->stencil_w.as<double>(), h->st);
     cudaEvent_t e0, e1;
@@ -1155,6 +1201,9 @@ int hif_stats(const hif_handle* h, hif_stats_t* s) {
   s->max_front_rank = h->max_rank;
   s->near_threshold_fronts = h->near;
   s->clamped_pivots = h->clamped;
+  s->sketched_fronts = h->sketched;
+  s->fallback_fronts = h->fallback;
+  s->t_fronts_ms = h->t_fronts_ms;
   s->factor_bytes = h->factor_bytes;
   s->factor_flops = h->factor_flops;
   s->apply_bytes = h->apply_bytes;
@@ -1204,6 +1253,116 @@ int hif_profile(hif_handle* h, int enable, hif_profile_t* out) {
 }
 
 long long hif_kernel_launches(void) { return g_launches.load(); }
+
+int hif_front_log(const hif_handle* h, float* feats, int32_t* ranks, int32_t* sizes, long long cap,
+                  long long* count) {
+  if (!h) return set_error(HIF_ERR_ARG, "NULL handle");
+  long long nf = 0;
+  for (const LevelFronts& lf : h->finfo) nf += (long long)lf.fd->size();
+  if (count) *count = nf;
+  if (cap < nf || !feats || !ranks || !sizes) return HIF_OK;
+  try {
+    long long p = 0;
+    for (const LevelFronts& lf : h->finfo) {
+      const size_t m = lf.fd->size();
+      CU(cudaMemcpyAsync(feats + p * kFeat, lf.feats.p, m * kFeat * sizeof(float), cudaMemcpyDeviceToHost, h->st));
+      for (size_t f = 0; f < m; ++f) {
+        const FrontDesc& d = (*lf.fd)[f];
+        ranks[p + f] = lf.out[d.out];
+        sizes[p + f] = d.nc;
+      }
+      p += (long long)m;
+    }
+    CU(cudaStreamSynchronize(h->st));
+  } catch (const HifError& e) {
+    return set_error(e.code, e.msg);
+  }
+  return HIF_OK;
+}
+
+int hif_mlp_grad(const float* X, const float* target, int n, const float* params, float* grad, float* loss,
+                 void* stream) {
+  if (!X || !target || !params || !grad || n < 1) return set_error(HIF_ERR_ARG, "bad arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  try {
+    DevBuf partial, ploss;
+    const int nblk = mlp_chunks(n);
+    partial.alloc(sizeof(float) * (size_t)nblk * kMlpParams, st);
+    ploss.alloc(sizeof(float) * nblk, st);
+    mlp_grad(X, target, nullptr, n, 1.0f / n, params, partial.as<float>(), ploss.as<float>(), grad, loss, st);
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(st));
+  } catch (const HifError& e) {
+    return set_error(e.code, e.msg);
+  }
+  return HIF_OK;
+}
+
+int hif_mlp_train(const float* X, const float* target, int n, float* params, int steps, int batch, float lr,
+                  unsigned long long seed, float* loss_hist, void* stream) {
+  if (!X || !target || !params || n < 1 || steps < 0 || batch < 1 || !(lr > 0.f))
+    return set_error(HIF_ERR_ARG, "bad arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  try {
+    batch = std::min(batch, n);
+    const int nblk = mlp_chunks(batch);
+    DevBuf idx, m, v, grad, partial, ploss, lossd;
+    idx.alloc(sizeof(int) * (size_t)n, st);
+    m.alloc(sizeof(float) * kMlpParams, st);
+    v.alloc(sizeof(float) * kMlpParams, st);
+    grad.alloc(sizeof(float) * kMlpParams, st);
+    partial.alloc(sizeof(float) * (size_t)nblk * kMlpParams, st);
+    ploss.alloc(sizeof(float) * nblk, st);
+    lossd.alloc(sizeof(float) * std::max(steps, 1), st);
+    CU(cudaMemsetAsync(m.p, 0, sizeof(float) * kMlpParams, st));
+    CU(cudaMemsetAsync(v.p, 0, sizeof(float) * kMlpParams, st));
+    std::vector<int> perm(n);
+    uint64_t state = seed;
+    auto next = [&]() {   // splitmix64
+      uint64_t z = (state += 0x9E3779B97F4A7C15ull);
+      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+      return z ^ (z >> 31);
+    };
+    int pos = n;   // forces a shuffle on the first step
+    for (int t = 1; t <= steps; ++t) {
+      if (pos + batch > n) {
+        for (int i = 0; i < n; ++i) perm[i] = i;
+        for (int i = n - 1; i > 0; --i) std::swap(perm[i], perm[(int)(next() % (uint64_t)(i + 1))]);
+        CU(cudaStreamSynchronize(st));   // the previous upload may still be read
+        CU(cudaMemcpyAsync(idx.p, perm.data(), sizeof(int) * (size_t)n, cudaMemcpyHostToDevice, st));
+        pos = 0;
+      }
+      mlp_grad(X, target, idx.as<int>() + pos, batch, 1.0f / batch, params, partial.as<float>(), ploss.as<float>(),
+               grad.as<float>(), lossd.as<float>() + (t - 1), st);
+      mlp_adam(params, grad.as<float>(), m.as<float>(), v.as<float>(), lr, t, st);
+      pos += batch;
+    }
+    if (loss_hist && steps > 0)
+      CU(cudaMemcpyAsync(loss_hist, lossd.p, sizeof(float) * steps, cudaMemcpyDeviceToDevice, st));
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(st));
+  } catch (const HifError& e) {
+    return set_error(e.code, e.msg);
+  }
+  return HIF_OK;
+}
+
+int hif_mlp_predict(const float* X, int n, const float* params, float* y, void* stream) {
+  if (!X || !params || !y || n < 0) return set_error(HIF_ERR_ARG, "bad arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  try {
+    DevBuf w;
+    w.alloc(2 * kMlpParams, st);
+    mlp_to_bf16(params, w.p, st);
+    mlp_predict(X, n, w.p, y, st);
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(st));
+  } catch (const HifError& e) {
+    return set_error(e.code, e.msg);
+  }
+  return HIF_OK;
+}
 
 void hif_free(hif_handle* h) {
   if (!h) return;

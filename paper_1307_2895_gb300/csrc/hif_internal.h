@@ -50,6 +50,11 @@ struct ApplyDesc {
   int64_t Linv, L, G, T;   // factor pool offsets (T = -1 for cells)
 };
 
+// Rank-prediction MLP: kFeat input features per front, hidden width kHid.
+constexpr int kFeat = 10;
+constexpr int kHid = 64;
+constexpr int kMlpParams = kHid * kFeat + kHid + kHid * kHid + kHid + kHid + 1;
+
 // Process-wide count of kernel launches issued by the library.
 void note_launches(long long n);
 

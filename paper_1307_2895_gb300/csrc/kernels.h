@@ -19,7 +19,21 @@ template <typename T>
 void launch_front(const FrontDesc* fronts, int nfronts, const CellDesc* cells, const int* ipool, int* obuf,
                   T* fwork,
                   T* fac, T* cwork, double eps, int* status, int max_nc, int max_nN, double tau,
-                  cudaStream_t st);
+                  const int* sketch, uint64_t seed, cudaStream_t st);
+
+// rank-prediction MLP (kernels_mlp.cu); idx may be NULL (samples 0..nb-1)
+void mlp_grad(const float* X, const float* t, const int* idx, int nb, float inv_n, const float* prm,
+              float* partial, float* ploss, float* grad, float* loss, cudaStream_t st);
+void mlp_adam(float* prm, const float* grad, float* m, float* v, float lr, int t, cudaStream_t st);
+void mlp_to_bf16(const float* prm, void* wbf16, cudaStream_t st);
+void mlp_predict(const float* X, int n, const void* wbf16, float* y, cudaStream_t st);
+int mlp_chunks(int nb);
+
+// front features and sketch sizes (kernels_factor.cu)
+void launch_front_features(const FrontDesc* fronts, int nfronts, const int* ipool, const double* stencil_w,
+                           int dim, int n, int level, double eps, float* feats, cudaStream_t st);
+void launch_sketch_sizes(const FrontDesc* fronts, int nfronts, const float* pred, int mode, int oversample,
+                         int* sketch, cudaStream_t st);
 
 // apply sweeps (kernels_apply.cu); op: 0 up, 1 down, 2 fwd_up, 3 fwd_down
 template <typename T>

@@ -205,11 +205,126 @@ __device__ __forceinline__ T front_entry(const T* U1, int ld1, const T* U2, int 
   return v;
 }
 
+// Column-pivoted Householder QR of A (m x nc, column-major, ld m), in place,
+// with residual norms recomputed every step (FP64 accumulation), the pivot
+// tie rule (smallest position within a factor 1 - 1e-10 of the largest
+// squared norm) and the rank rule (stop when |R_ii| <= eps |R_11|).
+// perm[0..k) = skeleton columns in pivot order, perm[k..nc) = the others in
+// ascending order.  Returns k.  flag_near marks pivot ratios within 1e-8 of
+// eps in bit 1 of *status.
+template <typename T>
+__device__ int blk_pivoted_qr(T* A, int m, int nc, double eps, int* status, bool flag_near, double* sq,
+                              double* v, int* perm, int* chosen) {
+  __shared__ double s_mx, s_vv, s_alpha;
+  __shared__ int s_piv, s_stop, s_k;
+  for (int j = threadIdx.x; j < nc; j += blockDim.x) chosen[j] = 0;
+  if (threadIdx.x == 0) { s_k = 0; s_stop = 0; }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  const int kmax = m < nc ? m : nc;
+  for (int i = 0; i < kmax; ++i) {
+    for (int j = warp; j < nc; j += nwarps) {
+      if (chosen[j]) continue;
+      const T* col = A + (int64_t)j * m;
+      double acc = 0.0;
+      for (int r = i + lane; r < m; r += 32) { const double x = (double)col[r]; acc += x * x; }
+      acc = warp_sum(acc);
+      if (lane == 0) sq[j] = acc;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      double mx = -1.0;
+      for (int j = lane; j < nc; j += 32) if (!chosen[j] && sq[j] > mx) mx = sq[j];
+      for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      int piv = 0x7fffffff;
+      for (int j = lane; j < nc; j += 32)
+        if (!chosen[j] && sq[j] >= (1.0 - 1e-10) * mx) { piv = j; break; }
+      for (int o = 16; o > 0; o >>= 1) piv = min(piv, __shfl_xor_sync(0xffffffffu, piv, o));
+      if (lane == 0) {
+        if (i == 0) s_mx = mx;  // |R_11|^2
+        const double nu = (i == 0) ? mx : s_mx;
+        const double ratio = (nu > 0.0) ? sqrt(mx / nu) : 0.0;
+        if (flag_near && fabs(ratio - eps) <= 1e-8 * eps) atomicOr(status, 2);
+        const int stop = (mx <= 0.0) || (i > 0 && mx <= eps * eps * nu);
+        s_stop = stop;
+        if (!stop) {
+          s_piv = piv;
+          const double x0 = (double)A[(int64_t)piv * m + i];
+          const double sp = sq[piv];      // the pivot's own squared norm builds the reflector
+          const double a2 = (x0 >= 0.0) ? -sqrt(sp) : sqrt(sp);
+          s_alpha = a2;
+          s_vv = sp - x0 * x0 + (x0 - a2) * (x0 - a2);
+          perm[s_k] = piv;
+          chosen[piv] = 1;
+          s_k = s_k + 1;
+        }
+      }
+    }
+    __syncthreads();
+    if (s_stop) break;
+    const int piv = s_piv;
+    const double alpha = s_alpha, vv = s_vv;
+    T* pc = A + (int64_t)piv * m;
+    for (int r = i + threadIdx.x; r < m; r += blockDim.x) v[r] = (double)pc[r] - (r == i ? alpha : 0.0);
+    __syncthreads();
+    if (vv > 0.0) {
+      for (int j = warp; j < nc; j += nwarps) {
+        if (chosen[j]) continue;
+        T* col = A + (int64_t)j * m;
+        double s = 0.0;
+        for (int r = i + lane; r < m; r += 32) s += v[r] * (double)col[r];
+        s = warp_sum(s);
+        const double f = 2.0 * s / vv;
+        for (int r = i + lane; r < m; r += 32) col[r] = (T)((double)col[r] - f * v[r]);
+      }
+    }
+    for (int r = i + threadIdx.x; r < m; r += blockDim.x) pc[r] = (r == i) ? (T)alpha : T(0);
+    __syncthreads();
+  }
+  const int k = s_k;
+  if (threadIdx.x == 0) {
+    int t = k;
+    for (int j = 0; j < nc; ++j) if (!chosen[j]) perm[t++] = j;
+  }
+  __syncthreads();
+  return k;
+}
+
+// T = R11^{-1} R12 from the factored A of blk_pivoted_qr (back substitution,
+// one thread per redundant column); T is k x (nc - k), row-major.
+template <typename T>
+__device__ void blk_id_T(const T* A, int m, const int* perm, int k, int nc, T* Tm) {
+  const int nR = nc - k;
+  for (int c = threadIdx.x; c < nR; c += blockDim.x) {
+    const T* r12 = A + (int64_t)perm[k + c] * m;
+    for (int t = k - 1; t >= 0; --t) {
+      T s = r12[t];
+      for (int u = t + 1; u < k; ++u) s -= A[(int64_t)perm[u] * m + t] * Tm[(int64_t)u * nR + c];
+      Tm[(int64_t)t * nR + c] = s / A[(int64_t)perm[t] * m + t];
+    }
+  }
+  __syncthreads();
+}
+
+// Standard normal from two splitmix64 outputs of a counter (Box-Muller).
+__device__ __forceinline__ uint64_t smix64(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__device__ __forceinline__ float gauss01(uint64_t key) {
+  const uint64_t a = smix64(key * 2), b = smix64(key * 2 + 1);
+  const float u1 = ((float)(a >> 40) + 0.5f) * (1.0f / 16777216.0f);
+  const float u2 = (float)(b >> 40) * (1.0f / 16777216.0f);
+  return sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+}
+
 template <typename T>
 __global__ void k_front(const FrontDesc* __restrict__ fronts, const CellDesc* __restrict__ cells,
                         const int* __restrict__ ipool, int* __restrict__ obuf, T* __restrict__ fwork,
-                        T* __restrict__ fac,
-                        T* __restrict__ cwork, double eps, int* status, T tau) {
+                        T* __restrict__ fac, T* __restrict__ cwork, double eps, int* status, T tau,
+                        const int* __restrict__ sketch, uint64_t seed) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const FrontDesc fd = fronts[blockIdx.x];
   const int nc = fd.nc, nN = fd.nN;
@@ -226,14 +341,14 @@ __global__ void k_front(const FrontDesc* __restrict__ fronts, const CellDesc* __
   double* v = sq + nc;                                        // nN
   int* perm = reinterpret_cast<int*>(v + nN);                 // nc
   int* chosen = perm + nc;                                    // nc
-  __shared__ double s_mx, s_vv, s_alpha;
-  __shared__ int s_piv, s_stop, s_k;
+  __shared__ double s_e2[32], s_m2[32];
 
   T* M = fwork + fd.work;                 // nN x nc, column-major
   T* Acc = M + (int64_t)nN * nc;          // nc x nc
   T* S1 = Acc + (int64_t)nc * nc;
   T* S2 = S1 + (int64_t)nc * nc;
   T* S3 = S2 + (int64_t)nc * nc;
+  T* PH = S3 + (int64_t)nc * nc;          // sketch matrix (ell x nN), ell < nc
 
   // ---- assemble A_{N,c} and A_cc
   for (int64_t e = threadIdx.x; e < (int64_t)nN * nc; e += blockDim.x) {
@@ -244,85 +359,6 @@ __global__ void k_front(const FrontDesc* __restrict__ fronts, const CellDesc* __
     const int i = (int)(e / nc), j = (int)(e % nc);
     Acc[e] = front_entry(U1, ld1, U2, ld2, pos1, pos2, i, j);
   }
-  for (int j = threadIdx.x; j < nc; j += blockDim.x) chosen[j] = 0;
-  if (threadIdx.x == 0) { s_k = 0; s_stop = 0; }
-  __syncthreads();
-
-  // ---- column-pivoted Householder QR with recomputed norms
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-  double nu1sq = 0.0;
-  const int kmax = nN < nc ? nN : nc;
-  for (int i = 0; i < kmax; ++i) {
-    for (int j = warp; j < nc; j += nwarps) {
-      if (chosen[j]) continue;
-      const T* col = M + (int64_t)j * nN;
-      double acc = 0.0;
-      for (int r = i + lane; r < nN; r += 32) { const double x = (double)col[r]; acc += x * x; }
-      acc = warp_sum(acc);
-      if (lane == 0) sq[j] = acc;
-    }
-    __syncthreads();
-    if (warp == 0) {
-      double mx = -1.0;
-      for (int j = lane; j < nc; j += 32) if (!chosen[j] && sq[j] > mx) mx = sq[j];
-      for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      int piv = 0x7fffffff;
-      for (int j = lane; j < nc; j += 32)
-        if (!chosen[j] && sq[j] >= (1.0 - 1e-10) * mx) { piv = j; break; }
-      for (int o = 16; o > 0; o >>= 1) piv = min(piv, __shfl_xor_sync(0xffffffffu, piv, o));
-      if (lane == 0) {
-        if (i == 0) s_mx = mx; // nu1^2
-        const double nu = (i == 0) ? mx : s_mx;
-        const double ratio = (nu > 0.0) ? sqrt(mx / nu) : 0.0;
-        if (fabs(ratio - eps) <= 1e-8 * eps) atomicOr(status, 2);
-        int stop = (mx <= 0.0) || (i > 0 && mx <= eps * eps * nu);
-        s_stop = stop;
-        if (!stop) {
-          s_piv = piv;
-          const double x0 = (double)M[(int64_t)piv * nN + i];
-          const double alpha = (x0 >= 0.0) ? -sqrt(mx) : sqrt(mx);
-          // use the pivot's own squared norm for the reflector
-          const double sp = sq[piv];
-          const double a2 = (x0 >= 0.0) ? -sqrt(sp) : sqrt(sp);
-          s_alpha = a2;
-          s_vv = sp - x0 * x0 + (x0 - a2) * (x0 - a2);
-          (void)alpha;
-          perm[s_k] = piv;
-          chosen[piv] = 1;
-          s_k = s_k + 1;
-        }
-      }
-    }
-    __syncthreads();
-    if (i == 0) nu1sq = s_mx;
-    if (s_stop) break;
-    const int piv = s_piv;
-    const double alpha = s_alpha, vv = s_vv;
-    T* pc = M + (int64_t)piv * nN;
-    for (int r = i + threadIdx.x; r < nN; r += blockDim.x) v[r] = (double)pc[r] - (r == i ? alpha : 0.0);
-    __syncthreads();
-    if (vv > 0.0) {
-      for (int j = warp; j < nc; j += nwarps) {
-        if (chosen[j]) continue;
-        T* col = M + (int64_t)j * nN;
-        double s = 0.0;
-        for (int r = i + lane; r < nN; r += 32) s += v[r] * (double)col[r];
-        s = warp_sum(s);
-        const double f = 2.0 * s / vv;
-        for (int r = i + lane; r < nN; r += 32) col[r] = (T)((double)col[r] - f * v[r]);
-      }
-    }
-    for (int r = i + threadIdx.x; r < nN; r += blockDim.x) pc[r] = (r == i) ? (T)alpha : T(0);
-    __syncthreads();
-  }
-  (void)nu1sq;
-  const int k = s_k;
-  const int nR = nc - k;
-  // redundant columns in ascending order after the skeletons
-  if (threadIdx.x == 0) {
-    int t = k;
-    for (int j = 0; j < nc; ++j) if (!chosen[j]) perm[t++] = j;
-  }
   __syncthreads();
 
   T* Linvp = fac + fd.fac;                 // packed nR x nR
@@ -330,16 +366,65 @@ __global__ void k_front(const FrontDesc* __restrict__ fronts, const CellDesc* __
   T* Tm = fac + fd.fac + front_fac_T(nc);  // k x nR
   T* Lp = fac + fd.fac + front_fac_L(nc);  // packed nR x nR
 
-  // ---- T = R11^{-1} R12 (back substitution, one thread per column)
-  for (int c = threadIdx.x; c < nR; c += blockDim.x) {
-    const T* r12 = M + (int64_t)perm[k + c] * nN;
-    for (int t = k - 1; t >= 0; --t) {
-      T s = r12[t];
-      for (int u = t + 1; u < k; ++u) s -= M[(int64_t)perm[u] * nN + t] * Tm[(int64_t)u * nR + c];
-      Tm[(int64_t)t * nR + c] = s / M[(int64_t)perm[t] * nN + t];
+  // ---- ID: from a Gaussian sketch Y = Phi A_{N,c} (Section 4.3) when a
+  // sketch size is given, accepted only if ||A_r - A_s T||_F <= eps ||A||_F;
+  // otherwise (or without a sketch) the pivoted QR of A_{N,c} itself.
+  const int ell = sketch ? sketch[blockIdx.x] : 0;
+  int k = -1;
+  if (ell > 0 && ell < nc && ell < nN) {
+    const uint64_t key0 = smix64(seed ^ ((uint64_t)blockIdx.x << 32)) ;
+    for (int64_t e = threadIdx.x; e < (int64_t)ell * nN; e += blockDim.x) PH[e] = (T)gauss01(key0 + (uint64_t)e);
+    __syncthreads();
+    T* Y = S3;                             // ell x nc, column-major (ld ell)
+    for (int64_t e = threadIdx.x; e < (int64_t)ell * nc; e += blockDim.x) {
+      const int j = (int)(e / ell), r = (int)(e % ell);
+      const T* ph = PH + (int64_t)r * nN;
+      const T* mc = M + (int64_t)j * nN;
+      T a = T(0);
+      for (int i = 0; i < nN; ++i) a += ph[i] * mc[i];
+      Y[e] = a;
+    }
+    __syncthreads();
+    int ks = blk_pivoted_qr(Y, ell, nc, eps, status, false, sq, v, perm, chosen);
+    bool ok = false;
+    if (ks < ell) {
+      blk_id_T(Y, ell, perm, ks, nc, Tm);
+      const int nRs = nc - ks;
+      double e2 = 0.0, m2 = 0.0;
+      for (int64_t e = threadIdx.x; e < (int64_t)nN * nRs; e += blockDim.x) {
+        const int c = (int)(e / nN), i = (int)(e % nN);
+        double r = (double)M[(int64_t)perm[ks + c] * nN + i];
+        for (int t = 0; t < ks; ++t) r -= (double)M[(int64_t)perm[t] * nN + i] * (double)Tm[(int64_t)t * nRs + c];
+        e2 += r * r;
+      }
+      for (int64_t e = threadIdx.x; e < (int64_t)nN * nc; e += blockDim.x) m2 += (double)M[e] * (double)M[e];
+      e2 = warp_sum(e2);
+      m2 = warp_sum(m2);
+      const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+      if (lane == 0) { s_e2[warp] = e2; s_m2[warp] = m2; }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += s_e2[w]; b += s_m2[w]; }
+        s_e2[0] = a;
+        s_m2[0] = b;
+      }
+      __syncthreads();
+      ok = s_e2[0] <= eps * eps * s_m2[0];
+      __syncthreads();
+    }
+    if (ok) {
+      k = ks;
+      if (threadIdx.x == 0) atomicAdd(status + 2, 1);
+    } else if (threadIdx.x == 0) {
+      atomicAdd(status + 3, 1);
     }
   }
-  __syncthreads();
+  if (k < 0) {
+    k = blk_pivoted_qr(M, nN, nc, eps, status, true, sq, v, perm, chosen);
+    blk_id_T(M, nN, perm, k, nc, Tm);
+  }
+  const int nR = nc - k;
 
   // ---- Lemma 2.4: W = A_ss T (S1), B_sr = A_sr - W (S2), B_rr (S3)
   for (int64_t e = threadIdx.x; e < (int64_t)k * nR; e += blockDim.x) {
@@ -434,12 +519,13 @@ template <typename T>
 void launch_front(const FrontDesc* fronts, int nfronts, const CellDesc* cells, const int* ipool, int* obuf,
                   T* fwork,
                   T* fac, T* cwork, double eps, int* status, int max_nc, int max_nN, double tau,
-                  cudaStream_t st) {
+                  const int* sketch, uint64_t seed, cudaStream_t st) {
   const int smem = (int)(sizeof(double) * (max_nc + max_nN) + sizeof(int) * 2 * max_nc + 64);
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(k_front<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   note_launches(1);
-  k_front<T><<<nfronts, 256, smem, st>>>(fronts, cells, ipool, obuf, fwork, fac, cwork, eps, status, (T)tau);
+  k_front<T><<<nfronts, 256, smem, st>>>(fronts, cells, ipool, obuf, fwork, fac, cwork, eps, status, (T)tau,
+                                         sketch, seed);
 }
 
 template void launch_leaf_assemble<double>(const CellDesc*, int, const int*, double*, GridInfo,
@@ -455,8 +541,101 @@ template void launch_extend_add<float, double>(const CellDesc*, int, const int*,
 template void launch_cell_factor<double>(const CellDesc*, int, double*, double*, int*, int, double, cudaStream_t);
 template void launch_cell_factor<float>(const CellDesc*, int, float*, float*, int*, int, double, cudaStream_t);
 template void launch_front<double>(const FrontDesc*, int, const CellDesc*, const int*, int*, double*, double*,
-                                   double*, double, int*, int, int, double, cudaStream_t);
+                                   double*, double, int*, int, int, double, const int*, uint64_t, cudaStream_t);
 template void launch_front<float>(const FrontDesc*, int, const CellDesc*, const int*, int*, float*, float*,
-                                  float*, double, int*, int, int, double, cudaStream_t);
+                                  float*, double, int*, int, int, double, const int*, uint64_t, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Features of each front for the rank predictor: level, log2 |c|, log2 |N|,
+// log10 eps, and min / max / mean / std / spread of log10 a over the stencil
+// couplings of the front's DOFs, and the dimension.
+// ---------------------------------------------------------------------------
+__global__ void k_front_features(const FrontDesc* __restrict__ fronts, const int* __restrict__ ipool,
+                                 const double* __restrict__ W, int dim, int n, int level, double eps,
+                                 float* __restrict__ feats) {
+  const FrontDesc fd = fronts[blockIdx.x];
+  const int* idc = ipool + fd.ids;
+  const int ns = 2 * dim + 1;
+  const double h2 = 1.0 / ((double)n * (double)n);
+  double mn = 1e300, mx = -1e300, sm = 0.0, s2 = 0.0, cnt = 0.0;
+  for (int e = threadIdx.x; e < fd.nc * 2 * dim; e += blockDim.x) {
+    const int i = e / (2 * dim), kk = e % (2 * dim);
+    const double w = W[(int64_t)idc[i] * ns + 1 + kk];
+    if (w < 0.0) {
+      const double la = log10(-w * h2);
+      mn = fmin(mn, la);
+      mx = fmax(mx, la);
+      sm += la;
+      s2 += la * la;
+      cnt += 1.0;
+    }
+  }
+  __shared__ double r[5][32];
+  for (int o = 16; o > 0; o >>= 1) {
+    mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    sm += __shfl_xor_sync(0xffffffffu, sm, o);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  if (lane == 0) { r[0][warp] = mn; r[1][warp] = mx; r[2][warp] = sm; r[3][warp] = s2; r[4][warp] = cnt; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < nw; ++w) {
+      mn = fmin(mn, r[0][w]); mx = fmax(mx, r[1][w]); sm += r[2][w]; s2 += r[3][w]; cnt += r[4][w];
+    }
+    mn = r[0][0] < mn ? r[0][0] : mn;
+    float* f = feats + (int64_t)blockIdx.x * kFeat;
+    const double mean = cnt > 0 ? sm / cnt : 0.0;
+    const double var = cnt > 0 ? fmax(s2 / cnt - mean * mean, 0.0) : 0.0;
+    if (cnt == 0) { mn = 0.0; mx = 0.0; }
+    f[0] = (float)level;
+    f[1] = (float)log2((double)fd.nc);
+    f[2] = (float)log2((double)(fd.nN > 0 ? fd.nN : 1));
+    f[3] = (float)log10(eps);
+    f[4] = (float)mn;
+    f[5] = (float)mx;
+    f[6] = (float)mean;
+    f[7] = (float)sqrt(var);
+    f[8] = (float)(mx - mn);
+    f[9] = (float)dim;
+  }
+}
+
+// Sketch rows per front: learned (mode 2) k_hat = ceil(exp(pred) - 1), or the
+// model-free guess k_hat = ceil(|c| / 2) (mode 1); ell = k_hat + oversample,
+// 0 (pivoted QR directly) when ell would not be smaller than the block.
+__global__ void k_sketch_sizes(const FrontDesc* __restrict__ fronts, int nf, const float* __restrict__ pred,
+                               int mode, int oversample, int* __restrict__ sketch) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= nf) return;
+  const FrontDesc fd = fronts[f];
+  int kh;
+  if (mode == 2 && pred) {
+    const float p = fminf(fmaxf(pred[f], 0.f), 12.f);
+    kh = (int)ceilf(expm1f(p));
+  } else {
+    kh = (fd.nc + 1) / 2;
+  }
+  kh = kh < 1 ? 1 : kh;
+  int ell = kh + oversample;
+  const int lim = fd.nc < fd.nN ? fd.nc : fd.nN;
+  sketch[f] = ell < lim ? ell : 0;
+}
+
+void launch_front_features(const FrontDesc* fronts, int nfronts, const int* ipool, const double* stencil_w,
+                           int dim, int n, int level, double eps, float* feats, cudaStream_t st) {
+  if (nfronts == 0) return;
+  note_launches(1);
+  k_front_features<<<nfronts, 64, 0, st>>>(fronts, ipool, stencil_w, dim, n, level, eps, feats);
+}
+
+void launch_sketch_sizes(const FrontDesc* fronts, int nfronts, const float* pred, int mode, int oversample,
+                         int* sketch, cudaStream_t st) {
+  if (nfronts == 0) return;
+  note_launches(1);
+  k_sketch_sizes<<<(nfronts + 127) / 128, 128, 0, st>>>(fronts, nfronts, pred, mode, oversample, sketch);
+}
 
 }  // namespace hif

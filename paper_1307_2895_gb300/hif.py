@@ -18,6 +18,8 @@ from . import build as _build
 
 HIF_OK, HIF_ERR_ARG, HIF_ERR_NOT_SPD, HIF_ERR_NOCONV, HIF_ERR_TIMEOUT, HIF_ERR_CUDA, HIF_ERR_OOM = range(7)
 VARIANTS = {"mf": 0, "hifde": 1}
+ID_MODES = {"qr": 0, "rand": 1, "learned": 2}
+MLP_FEATURES, MLP_PARAMS = 10, 4929
 PRECISIONS = {"fp64": 0, "mixed": 1, "fp32_apply": 2}
 APPLY_F, APPLY_FINV = 0, 1
 
@@ -33,8 +35,9 @@ class _Grid(ctypes.Structure):
 
 
 class _Opts(ctypes.Structure):
-    _fields_ = [("precision", ctypes.c_int), ("skip_levels", ctypes.c_int), ("reserved0", ctypes.c_int),
-                ("reserved1", ctypes.c_int), ("stream", ctypes.c_void_p)]
+    _fields_ = [("precision", ctypes.c_int), ("skip_levels", ctypes.c_int), ("id_mode", ctypes.c_int),
+                ("oversample", ctypes.c_int), ("stream", ctypes.c_void_p), ("rank_model", ctypes.c_void_p),
+                ("seed", ctypes.c_ulonglong)]
 
 
 class _SolveInfo(ctypes.Structure):
@@ -46,7 +49,8 @@ class _Stats(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int), ("levels", ctypes.c_int),
                 ("root_size", ctypes.c_int), ("n_cells", ctypes.c_int), ("n_fronts", ctypes.c_int),
                 ("max_front_rank", ctypes.c_int), ("near_threshold_fronts", ctypes.c_int),
-                ("clamped_pivots", ctypes.c_int),
+                ("clamped_pivots", ctypes.c_int), ("sketched_fronts", ctypes.c_int),
+                ("fallback_fronts", ctypes.c_int), ("t_fronts_ms", ctypes.c_double),
                 ("factor_bytes", ctypes.c_longlong), ("factor_flops", ctypes.c_double),
                 ("apply_bytes", ctypes.c_double), ("t_factor_ms", ctypes.c_double)]
 
@@ -58,7 +62,8 @@ class _Profile(ctypes.Structure):
 
 _LIB = None
 EXPORTS = ["hif_factor", "hif_apply", "hif_solve", "hif_matvec", "hif_stats", "hif_structure",
-           "hif_profile", "hif_kernel_launches", "hif_residual_norms_noalloc", "hif_free", "hif_last_error"]
+           "hif_profile", "hif_kernel_launches", "hif_residual_norms_noalloc", "hif_front_log", "hif_mlp_grad",
+           "hif_mlp_train", "hif_mlp_predict", "hif_free", "hif_last_error"]
 
 
 def library_path() -> str:
@@ -95,6 +100,14 @@ def load(build_if_missing: bool = False):
     lib.hif_kernel_launches.restype = ctypes.c_longlong
     lib.hif_residual_norms_noalloc.argtypes = [i, i, vp, vp, vp, vp, i, i, vp, vp]
     lib.hif_residual_norms_noalloc.restype = i
+    lib.hif_front_log.argtypes = [vp, vp, vp, vp, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)]
+    lib.hif_front_log.restype = i
+    lib.hif_mlp_grad.argtypes = [vp, vp, i, vp, vp, vp, vp]
+    lib.hif_mlp_grad.restype = i
+    lib.hif_mlp_train.argtypes = [vp, vp, i, vp, i, i, ctypes.c_float, ctypes.c_ulonglong, vp, vp]
+    lib.hif_mlp_train.restype = i
+    lib.hif_mlp_predict.argtypes = [vp, i, vp, vp, vp]
+    lib.hif_mlp_predict.restype = i
     lib.hif_free.argtypes = [vp]
     lib.hif_free.restype = None
     lib.hif_last_error.argtypes = []
@@ -112,17 +125,17 @@ def _is_torch(x) -> bool:
     return type(x).__module__.startswith("torch")
 
 
-def _ptr(x):
-    """Raw address of a contiguous float64 numpy array or torch tensor."""
+def _ptr(x, dtype: str = "float64"):
+    """Raw address of a contiguous numpy array or torch tensor of the given dtype."""
     if x is None:
         return None
     if _is_torch(x):
         import torch
-        if x.dtype != torch.float64 or not x.is_contiguous():
-            raise TypeError("tensors must be contiguous float64")
+        if x.dtype != getattr(torch, dtype) or not x.is_contiguous():
+            raise TypeError(f"tensors must be contiguous {dtype}")
         return x.data_ptr()
-    if x.dtype != np.float64 or not x.flags["C_CONTIGUOUS"]:
-        raise TypeError("arrays must be C-contiguous float64")
+    if x.dtype != np.dtype(dtype) or not x.flags["C_CONTIGUOUS"]:
+        raise TypeError(f"arrays must be C-contiguous {dtype}")
     return x.ctypes.data
 
 
@@ -198,6 +211,18 @@ class Factorization:
         _check(self._lib.hif_profile(self._live(), 1 if enable else 0, ctypes.byref(p)), self._lib)
         return dict(sweep_ms=p.sweep_ms, sweep_launches=p.sweep_launches, sweep_bytes=p.sweep_bytes)
 
+    def front_log(self):
+        """(features n x 10, ranks, sizes) of every front: rank-MLP training data."""
+        cnt = ctypes.c_longlong(0)
+        _check(self._lib.hif_front_log(self._live(), None, None, None, 0, ctypes.byref(cnt)), self._lib)
+        n = cnt.value
+        feats = np.zeros((n, MLP_FEATURES), dtype=np.float32)
+        ranks = np.zeros(n, dtype=np.int32)
+        sizes = np.zeros(n, dtype=np.int32)
+        _check(self._lib.hif_front_log(self._live(), feats.ctypes.data, ranks.ctypes.data, sizes.ctypes.data, n,
+                                       ctypes.byref(cnt)), self._lib)
+        return feats, ranks, sizes
+
     def stats(self) -> dict:
         s = _Stats()
         _check(self._lib.hif_stats(self._live(), ctypes.byref(s)), self._lib)
@@ -248,12 +273,48 @@ def kernel_launches() -> int:
     return int(load().hif_kernel_launches())
 
 
+def mlp_grad(X, target, params, stream=None):
+    """(loss, grad) of the rank MLP on CUDA float32 tensors."""
+    import torch
+    lib = load()
+    grad = torch.empty_like(params)
+    loss = torch.empty(1, dtype=torch.float32, device=params.device)
+    rc = lib.hif_mlp_grad(_ptr(X, "float32"), _ptr(target, "float32"), X.shape[0], _ptr(params, "float32"),
+                          _ptr(grad, "float32"), _ptr(loss, "float32"), _stream_ptr(stream))
+    _check(rc, lib)
+    return float(loss.item()), grad
+
+
+def mlp_train(X, target, params, steps: int = 2000, batch: int = 1024, lr: float = 1e-3, seed: int = 0,
+              stream=None):
+    """Train the rank MLP in place (CUDA float32 tensors); returns the loss history."""
+    import torch
+    lib = load()
+    hist = torch.empty(max(steps, 1), dtype=torch.float32, device=params.device)
+    rc = lib.hif_mlp_train(_ptr(X, "float32"), _ptr(target, "float32"), X.shape[0], _ptr(params, "float32"),
+                           steps, batch, lr, seed, _ptr(hist, "float32"), _stream_ptr(stream))
+    _check(rc, lib)
+    return hist[:steps].cpu().numpy()
+
+
+def mlp_predict(X, params, stream=None):
+    """BF16-weight inference of the rank MLP (CUDA float32 tensors)."""
+    import torch
+    lib = load()
+    y = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
+    _check(lib.hif_mlp_predict(_ptr(X, "float32"), X.shape[0], _ptr(params, "float32"), _ptr(y, "float32"),
+                               _stream_ptr(stream)), lib)
+    return y
+
+
 def factor(dim: int, n: int, a_stag, b, eps: float, variant: str = "hifde", precision: str = "fp64",
-           leaf: int = 8, skip_levels: int = 0, stream=None) -> Factorization:
+           leaf: int = 8, skip_levels: int = 0, stream=None, id_mode: str = "qr", rank_model=None,
+           oversample: int = 10, seed: int = 0) -> Factorization:
     """hif_factor: MF or HIF-DE of the stencil operator defined by (a_stag, b)."""
     lib = load()
     grid = _Grid(dim, n, leaf, VARIANTS[variant])
-    opts = _Opts(PRECISIONS[precision], skip_levels, 0, 0, _stream_ptr(stream))
+    opts = _Opts(PRECISIONS[precision], skip_levels, ID_MODES[id_mode], oversample, _stream_ptr(stream),
+                 _ptr(rank_model, "float32"), seed)
     h = ctypes.c_void_p()
     rc = lib.hif_factor(ctypes.byref(grid), _ptr(a_stag), _ptr(b), None, float(eps), ctypes.byref(opts),
                         ctypes.byref(h))

@@ -1,0 +1,57 @@
+"""Pins of the oracle's randomized ID and rank-prediction MLP (CPU)."""
+import numpy as np
+
+from oracle import learned
+from paper_1307_2895_gb300 import inputs
+
+
+def test_mlp_gradient_matches_finite_differences():
+    rng = np.random.default_rng(0)
+    nin, H, n = 10, 64, 37
+    flat = rng.standard_normal(H * nin + H + H * H + H + H + 1) * 0.2
+    X = rng.standard_normal((n, nin))
+    t = rng.standard_normal(n) * 2
+    net = learned.MLP.unpack(flat, nin, H)
+    loss, g = net.loss_and_grad(X, t)
+    idx = rng.choice(len(flat), 60, replace=False)
+    for i in idx:
+        h = 1e-6
+        fp, fm = flat.copy(), flat.copy()
+        fp[i] += h
+        fm[i] -= h
+        lp, _ = learned.MLP.unpack(fp, nin, H).loss_and_grad(X, t)
+        lm, _ = learned.MLP.unpack(fm, nin, H).loss_and_grad(X, t)
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, g[i])
+
+
+def test_mlp_huber_regions():
+    """Residuals beyond delta contribute a clipped gradient (Huber loss)."""
+    nin, H = 3, 64
+    net = learned.MLP.unpack(np.zeros(H * nin + H + H * H + H + H + 1), nin, H)
+    X = np.zeros((2, nin))
+    loss, g = net.loss_and_grad(X, np.array([0.5, 5.0]))
+    assert np.isclose(loss, (0.5 * 0.25 + (5.0 - 0.5)) / 2)
+    assert np.isclose(g[-1], (-0.5 - 1.0) / 2)          # d/db3
+
+
+def test_randomized_id_exact_low_rank():
+    rng = np.random.default_rng(1)
+    m, n, k = 60, 25, 6
+    M = rng.standard_normal((m, k)) @ rng.standard_normal((k, n))
+    ell = k + 10
+    Phi = inputs.standard_normal(3, ell * m).reshape(ell, m)
+    idr, ok = learned.randomized_id(M, 1e-10, Phi)
+    assert ok and len(idr.sk) == k
+    E = M[:, idr.rd] - M[:, idr.sk] @ idr.T
+    assert np.linalg.norm(E) <= 1e-10 * np.linalg.norm(M)
+
+
+def test_randomized_id_undersized_sketch_is_rejected():
+    rng = np.random.default_rng(2)
+    m, n = 50, 20
+    U, _ = np.linalg.qr(rng.standard_normal((m, n)))
+    M = U * (10.0 ** -np.arange(n) * 0.5)     # numerical rank ~ 12 at eps 1e-6
+    Phi = inputs.standard_normal(4, 4 * m).reshape(4, m)
+    idr, ok = learned.randomized_id(M, 1e-6, Phi)
+    assert not ok
