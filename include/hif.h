@@ -92,6 +92,10 @@ typedef struct hif_opts {
   const float* rank_model; /* HIF_ID_LEARNED: HIF_MLP_PARAMS floats (see
                               hif_mlp_train), host or device memory            */
   unsigned long long seed; /* counter-based sketch RNG seed                     */
+  int big_cell;         /* cells with at least this many interior DOFs are
+                           eliminated by the tiled multi-block kernels (64 x 64
+                           tiles, blocked Cholesky, Lemma 2.1); 0 -> 192,
+                           < 0 -> never.  Same result up to rounding order.      */
 } hif_opts;
 
 typedef struct hif_handle hif_handle;

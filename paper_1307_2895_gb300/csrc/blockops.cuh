@@ -20,17 +20,21 @@ template <> __device__ __forceinline__ float dsqrt<float>(float x) { return sqrt
 // the column below it (|l_ij| <= sqrt(d0_i / sqrt(tau))), and counted in
 // status[1].  d0 is the pivot's original diagonal entry (or the block's
 // largest original diagonal entry when that is not positive); only a block
-// without a positive finite diagonal sets bit 0.
+// without a positive finite diagonal sets bit 0.  d0v, when given, holds the
+// original diagonal entries (a diagonal tile of a larger matrix whose
+// earlier panels have already been eliminated); the upper triangle is then
+// left untouched.
 template <typename T>
-__device__ void blk_cholesky(T* A, int n, int ld, int* status, T tau = T(0)) {
+__device__ void blk_cholesky(T* A, int n, int ld, int* status, T tau = T(0), const T* d0v = nullptr) {
   __shared__ T s_piv, s_dmax;
   if (tau > T(0)) {
-    for (int j = 1 + threadIdx.x; j < n; j += blockDim.x)
-      A[(int64_t)(j - 1) * ld + j] = A[(int64_t)j * ld + j];
+    if (!d0v)
+      for (int j = 1 + threadIdx.x; j < n; j += blockDim.x)
+        A[(int64_t)(j - 1) * ld + j] = A[(int64_t)j * ld + j];
     if (threadIdx.x == 0) {
       T dm = T(0);
       for (int j = 0; j < n; ++j) {
-        const T d = A[(int64_t)j * ld + j];
+        const T d = d0v ? d0v[j] : A[(int64_t)j * ld + j];
         if (d > dm && isfinite((double)d)) dm = d;
       }
       s_dmax = dm;
@@ -41,7 +45,7 @@ __device__ void blk_cholesky(T* A, int n, int ld, int* status, T tau = T(0)) {
     if (threadIdx.x == 0) {
       T d = A[(int64_t)j * ld + j];
       if (tau > T(0)) {
-        T d0 = (j == 0) ? d : A[(int64_t)(j - 1) * ld + j];
+        T d0 = d0v ? d0v[j] : (j == 0) ? d : A[(int64_t)(j - 1) * ld + j];
         if (!(d0 > T(0)) || !isfinite((double)d0)) d0 = s_dmax;
         if (!(d0 > T(0))) {
           atomicOr(status, 1);

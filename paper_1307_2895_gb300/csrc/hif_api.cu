@@ -159,6 +159,7 @@ struct hif_handle {
   int precision = HIF_PREC_FP64;
   int variant = HIF_VARIANT_HIFDE;
   int skip_levels = 0;
+  int big_cell = 192;   // cells with at least this many interior DOFs use the tiled elimination
   int id_mode = HIF_ID_QR;
   int oversample = 10;
   unsigned long long seed = 0;
@@ -212,7 +213,7 @@ void prepare_cells(const Geometry& G, int l, const std::vector<HostCell>& cells,
     ipool.insert(ipool.end(), c.I.begin(), c.I.end());
     ipool.insert(ipool.end(), c.B.begin(), c.B.end());
     d.F = work_elems;
-    work_elems += 2 * (int64_t)d.nI * d.nI + (int64_t)d.nB * d.nI + (int64_t)d.nB * d.nB;
+    work_elems += (int64_t)d.nI * d.nI + (int64_t)d.nB * d.nI + (int64_t)d.nB * d.nB + cell_x_elems(d.nI);
     d.fac = fac_elems;
     fac_elems += cell_fac_size(d.nI, d.nB);
     for (int s = 0; s < kMaxChild; ++s) d.child[s] = -1;
@@ -348,6 +349,42 @@ struct Factorizer {
     tau = (h_->precision == HIF_PREC_MIXED) ? 4e-6 : 0.0;
   }
 
+  // Interior elimination of one level: cells with at least h->big_cell
+  // interior DOFs go through the tiled multi-block kernels, the others
+  // through the one-block-per-cell kernel.
+  template <typename U>
+  void factor_cells(const std::vector<CellDesc>& cd, const CellDesc* d_cd, U* work, U* fac, DevBuf& selbuf) {
+    std::vector<int> small, big;
+    int max_small = 0, max_bI = 0, max_bB = 0;
+    for (int i = 0; i < (int)cd.size(); ++i) {
+      if (cd[i].nI >= h->big_cell && cd[i].nI > 0) {
+        big.push_back(i);
+        max_bI = std::max(max_bI, cd[i].nI);
+        max_bB = std::max(max_bB, cd[i].nB);
+      } else {
+        small.push_back(i);
+        max_small = std::max(max_small, cd[i].nI);
+      }
+    }
+    if (big.empty()) {
+      launch_cell_factor<U>(d_cd, nullptr, (int)cd.size(), work, fac, status.as<int>(), max_small, tau, st);
+      return;
+    }
+    std::vector<int> sel(small);
+    sel.insert(sel.end(), big.begin(), big.end());
+    upload(selbuf, sel, st);
+    const int* d_sel = selbuf.as<int>();
+    launch_cell_factor<U>(d_cd, d_sel, (int)small.size(), work, fac, status.as<int>(), max_small, tau, st);
+    launch_cell_factor_tiled<U>(d_cd, d_sel + small.size(), (int)big.size(), max_bI, max_bB, work, fac,
+                                status.as<int>(), tau, st);
+  }
+
+  static int max_front_size(const std::vector<CellDesc>& cd) {
+    int m = 0;
+    for (const CellDesc& c : cd) m = std::max(m, c.nI + c.nB);
+    return m;
+  }
+
   void account_cells(const std::vector<CellDesc>& cd, size_t esz) {
     for (const CellDesc& c : cd) {
       const double nI = c.nI, nB = c.nB;
@@ -380,8 +417,8 @@ struct Factorizer {
       const int nc0 = (int)L0->cdesc.size();
       launch_leaf_assemble<T>(L0->d_cdesc, nc0, L0->d_cipool, work.as<T>(), h->gi, h->a_stag.as<double>(),
                               h->bnode.as<double>(), L0->d_cls0, G.ncell[0], st);
-      launch_cell_factor<T>(L0->d_cdesc, nc0, work.as<T>(), sw.fac.as<T>(), status.as<int>(), L0->max_nI, tau,
-                            st);
+      DevBuf sel0;
+      factor_cells<T>(L0->cdesc, L0->d_cdesc, work.as<T>(), sw.fac.as<T>(), sel0);
       CU(cudaGetLastError());
       sw.nblocks = nc0;
       sw.desc = L0->d_capply;
@@ -423,14 +460,16 @@ struct Factorizer {
       work.alloc((size_t)work_elems * esz, st);
       sw.fac.alloc((size_t)fac_elems * esz, st);
       const CellDesc* dd = ddesc.as<CellDesc>();
+      const int max_nF = max_front_size(cdesc);
+      DevBuf selbuf;
       if (is_root) {
         launch_extend_add<T, double>(dd, ncells, sw.ipool, work.as<double>(), prev_ddesc, prev_work.as<T>(),
-                                     nchild, st);
-        launch_cell_factor<double>(dd, ncells, work.as<double>(), sw.fac.as<double>(), status.as<int>(), max_nI,
-                                   tau, st);
+                                     nchild, max_nF, st);
+        factor_cells<double>(cdesc, dd, work.as<double>(), sw.fac.as<double>(), selbuf);
       } else {
-        launch_extend_add<T, T>(dd, ncells, sw.ipool, work.as<T>(), prev_ddesc, prev_work.as<T>(), nchild, st);
-        launch_cell_factor<T>(dd, ncells, work.as<T>(), sw.fac.as<T>(), status.as<int>(), max_nI, tau, st);
+        launch_extend_add<T, T>(dd, ncells, sw.ipool, work.as<T>(), prev_ddesc, prev_work.as<T>(), nchild, max_nF,
+                                st);
+        factor_cells<T>(cdesc, dd, work.as<T>(), sw.fac.as<T>(), selbuf);
       }
       CU(cudaGetLastError());
       std::vector<ApplyDesc> ad;
@@ -1050,6 +1089,7 @@ int hif_factor(const hif_grid* grid, const double* a_stag, const double* b, cons
     if (h->id_mode < HIF_ID_QR || h->id_mode > HIF_ID_LEARNED) throw HifError(HIF_ERR_ARG, "unknown id_mode");
     h->oversample = (opts && opts->oversample > 0) ? opts->oversample : 10;
     h->seed = opts ? opts->seed : 0;
+    if (opts && opts->big_cell != 0) h->big_cell = opts->big_cell < 0 ? 0x7fffffff : opts->big_cell;
     if (h->id_mode == HIF_ID_LEARNED && !(opts && opts->rank_model))
       throw HifError(HIF_ERR_ARG, "HIF_ID_LEARNED needs opts.rank_model");
     h->st = opts ? (cudaStream_t)opts->stream : nullptr;

@@ -68,6 +68,15 @@ __host__ __device__ inline int64_t packed_size(int64_t n) { return pad4(n * (n +
 __host__ __device__ inline int64_t cell_fac_G(int nI) { return packed_size(nI); }
 __host__ __device__ inline int64_t cell_fac_L(int nI, int nB) { return packed_size(nI) + pad4((int64_t)nB * nI); }
 __host__ __device__ inline int64_t cell_fac_size(int nI, int nB) { return 2 * packed_size(nI) + pad4((int64_t)nB * nI); }
+// Tile edge of the multi-block elimination of large cells, and the size of a
+// cell's X region of the work pool: room for Linv in the single-block kernel,
+// or for the diagonal-tile inverses plus the original diagonal in the tiled one.
+constexpr int kTile = 64;
+__host__ __device__ inline int64_t cell_x_elems(int nI) {
+  const int64_t t = (int64_t)((nI + kTile - 1) / kTile) * kTile * kTile + nI;
+  const int64_t s = (int64_t)nI * nI;
+  return pad4(s > t ? s : t);
+}
 // front with capacity nc: Linv | G | T | L
 __host__ __device__ inline int64_t front_fac_G(int nc) { return packed_size(nc); }
 __host__ __device__ inline int64_t front_fac_T(int nc) { return packed_size(nc) + pad4((int64_t)nc * nc); }

@@ -11,10 +11,15 @@ void launch_leaf_assemble(const CellDesc* cells, int ncells, const int* ipool, T
                           cudaStream_t st);
 template <typename TU, typename TF>
 void launch_extend_add(const CellDesc* cells, int ncells, const int* ipool, TF* work,
-                       const CellDesc* pcells, const TU* pwork, int nchild, cudaStream_t st);
+                       const CellDesc* pcells, const TU* pwork, int nchild, int max_nF, cudaStream_t st);
+// sel (may be NULL: cells 0..ncells-1) lists the cells to factor
 template <typename T>
-void launch_cell_factor(const CellDesc* cells, int ncells, T* work, T* fac, int* status, int max_nI,
-                        double tau, cudaStream_t st);
+void launch_cell_factor(const CellDesc* cells, const int* sel, int ncells, T* work, T* fac, int* status,
+                        int max_nI, double tau, cudaStream_t st);
+// tiled multi-block elimination of the cells sel[0..nsel) (kernels_tiled.cu)
+template <typename T>
+void launch_cell_factor_tiled(const CellDesc* cells, const int* sel, int nsel, int max_nI, int max_nB, T* work,
+                              T* fac, int* status, double tau, cudaStream_t st);
 template <typename T>
 void launch_front(const FrontDesc* fronts, int nfronts, const CellDesc* cells, const int* ipool, int* obuf,
                   T* fwork,

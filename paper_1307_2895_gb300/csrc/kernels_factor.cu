@@ -1,6 +1,8 @@
 // Factorization kernels: frontal assembly, interior elimination (Lemma 2.1)
 // and front skeletonization (Lemma 2.2 ID + Lemma 2.4).  One thread block
 // per cell or front; every block of one level goes in one launch.
+#include <algorithm>
+
 #include "hif_internal.h"
 #include "blockops.cuh"
 #include "kernels.h"
@@ -113,6 +115,9 @@ __global__ void k_extend_add(const CellDesc* __restrict__ cells, const int* __re
                              TF* __restrict__ work, const CellDesc* __restrict__ pcells,
                              const TU* __restrict__ pwork, int nchild) {
   const CellDesc cd = cells[blockIdx.x];
+  const int64_t nF2 = (int64_t)(cd.nI + cd.nB) * (cd.nI + cd.nB);
+  const int64_t e0 = (int64_t)blockIdx.y * blockDim.x + threadIdx.x;
+  if ((int64_t)blockIdx.y * blockDim.x >= nF2) return;
   const int nI = cd.nI, nB = cd.nB, nF = nI + nB;
   const int* cmap = ipool + cd.cmap;
   TF* FII = work + cd.F;
@@ -133,7 +138,7 @@ __global__ void k_extend_add(const CellDesc* __restrict__ cells, const int* __re
     }
   }
   __syncthreads();
-  for (int64_t e = threadIdx.x; e < (int64_t)nF * nF; e += blockDim.x) {
+  for (int64_t e = e0; e < nF2; e += (int64_t)gridDim.y * blockDim.x) {
     const int a = (int)(e / nF), b = (int)(e % nF);
     if (a < nI && b >= nI) continue;
     const int* ca = cmap + (int64_t)a * kMaxChild;
@@ -156,11 +161,11 @@ __global__ void k_extend_add(const CellDesc* __restrict__ cells, const int* __re
 // G = F_BI L^{-T}, U = F_BB - G G^T (in place: U becomes the cell's update).
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void k_cell_factor(const CellDesc* __restrict__ cells, T* __restrict__ work,
-                              T* __restrict__ fac, int* status, int smem_elems, T tau) {
+__global__ void k_cell_factor(const CellDesc* __restrict__ cells, const int* __restrict__ sel,
+                              T* __restrict__ work, T* __restrict__ fac, int* status, int smem_elems, T tau) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
-  const CellDesc cd = cells[blockIdx.x];
+  const CellDesc cd = cells[sel ? sel[blockIdx.x] : blockIdx.x];
   const int nI = cd.nI, nB = cd.nB;
   T* FII = work + cd.F;
   T* FBI = FII + (int64_t)nI * nI;
@@ -496,14 +501,21 @@ void launch_leaf_assemble(const CellDesc* cells, int ncells, const int* ipool, T
 
 template <typename TU, typename TF>
 void launch_extend_add(const CellDesc* cells, int ncells, const int* ipool, TF* work,
-                       const CellDesc* pcells, const TU* pwork, int nchild, cudaStream_t st) {
+                       const CellDesc* pcells, const TU* pwork, int nchild, int max_nF, cudaStream_t st) {
+  if (ncells == 0) return;
+  // one block per cell for the small cells; large cells spread over up to
+  // 4096 blocks of 256 threads (one 256-entry chunk per block and pass)
+  const int64_t f2 = (int64_t)max_nF * max_nF;
+  int chunks = (int)std::min<int64_t>((f2 + 256 * 16 - 1) / (256 * 16), 4096);
+  if (chunks < 1) chunks = 1;
   note_launches(1);
-  k_extend_add<TU, TF><<<ncells, 256, 0, st>>>(cells, ipool, work, pcells, pwork, nchild);
+  k_extend_add<TU, TF><<<dim3(ncells, chunks), 256, 0, st>>>(cells, ipool, work, pcells, pwork, nchild);
 }
 
 template <typename T>
-void launch_cell_factor(const CellDesc* cells, int ncells, T* work, T* fac, int* status,
+void launch_cell_factor(const CellDesc* cells, const int* sel, int ncells, T* work, T* fac, int* status,
                         int max_nI, double tau, cudaStream_t st) {
+  if (ncells == 0) return;
   const int cap_bytes = 200 * 1024;
   int64_t need = 2LL * max_nI * max_nI * (int64_t)sizeof(T);
   if (need > cap_bytes) need = (int64_t)max_nI * max_nI * (int64_t)sizeof(T);
@@ -512,7 +524,7 @@ void launch_cell_factor(const CellDesc* cells, int ncells, T* work, T* fac, int*
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(k_cell_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   note_launches(1);
-  k_cell_factor<T><<<ncells, 256, smem, st>>>(cells, work, fac, status, smem / (int)sizeof(T), (T)tau);
+  k_cell_factor<T><<<ncells, 256, smem, st>>>(cells, sel, work, fac, status, smem / (int)sizeof(T), (T)tau);
 }
 
 template <typename T>
@@ -533,13 +545,15 @@ template void launch_leaf_assemble<double>(const CellDesc*, int, const int*, dou
 template void launch_leaf_assemble<float>(const CellDesc*, int, const int*, float*, GridInfo,
                                           const double*, const double*, const int*, int, cudaStream_t);
 template void launch_extend_add<double, double>(const CellDesc*, int, const int*, double*,
-                                                const CellDesc*, const double*, int, cudaStream_t);
+                                                const CellDesc*, const double*, int, int, cudaStream_t);
 template void launch_extend_add<float, float>(const CellDesc*, int, const int*, float*,
-                                              const CellDesc*, const float*, int, cudaStream_t);
+                                              const CellDesc*, const float*, int, int, cudaStream_t);
 template void launch_extend_add<float, double>(const CellDesc*, int, const int*, double*,
-                                               const CellDesc*, const float*, int, cudaStream_t);
-template void launch_cell_factor<double>(const CellDesc*, int, double*, double*, int*, int, double, cudaStream_t);
-template void launch_cell_factor<float>(const CellDesc*, int, float*, float*, int*, int, double, cudaStream_t);
+                                               const CellDesc*, const float*, int, int, cudaStream_t);
+template void launch_cell_factor<double>(const CellDesc*, const int*, int, double*, double*, int*, int, double,
+                                         cudaStream_t);
+template void launch_cell_factor<float>(const CellDesc*, const int*, int, float*, float*, int*, int, double,
+                                        cudaStream_t);
 template void launch_front<double>(const FrontDesc*, int, const CellDesc*, const int*, int*, double*, double*,
                                    double*, double, int*, int, int, double, const int*, uint64_t, cudaStream_t);
 template void launch_front<float>(const FrontDesc*, int, const CellDesc*, const int*, int*, float*, float*,

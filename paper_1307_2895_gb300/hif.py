@@ -37,7 +37,7 @@ class _Grid(ctypes.Structure):
 class _Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("skip_levels", ctypes.c_int), ("id_mode", ctypes.c_int),
                 ("oversample", ctypes.c_int), ("stream", ctypes.c_void_p), ("rank_model", ctypes.c_void_p),
-                ("seed", ctypes.c_ulonglong)]
+                ("seed", ctypes.c_ulonglong), ("big_cell", ctypes.c_int)]
 
 
 class _SolveInfo(ctypes.Structure):
@@ -309,12 +309,12 @@ def mlp_predict(X, params, stream=None):
 
 def factor(dim: int, n: int, a_stag, b, eps: float, variant: str = "hifde", precision: str = "fp64",
            leaf: int = 8, skip_levels: int = 0, stream=None, id_mode: str = "qr", rank_model=None,
-           oversample: int = 10, seed: int = 0) -> Factorization:
+           oversample: int = 10, seed: int = 0, big_cell: int = 0) -> Factorization:
     """hif_factor: MF or HIF-DE of the stencil operator defined by (a_stag, b)."""
     lib = load()
     grid = _Grid(dim, n, leaf, VARIANTS[variant])
     opts = _Opts(PRECISIONS[precision], skip_levels, ID_MODES[id_mode], oversample, _stream_ptr(stream),
-                 _ptr(rank_model, "float32"), seed)
+                 _ptr(rank_model, "float32"), seed, big_cell)
     h = ctypes.c_void_p()
     rc = lib.hif_factor(ctypes.byref(grid), _ptr(a_stag), _ptr(b), None, float(eps), ctypes.byref(opts),
                         ctypes.byref(h))

@@ -101,6 +101,69 @@ def test_apply_matches_oracle(hiflib, dim, n, field, eps):
     assert np.linalg.norm(yf - of) <= 1e-10 * np.linalg.norm(of)
 
 
+TILED_CASES = [(2, 64, "contrast", 1e-6), (2, 40, "contrast", 1e-4), (2, 128, "contrast", 1e-9),
+               (3, 16, "lap", 1e-6), (3, 20, "contrast", 1e-4)]
+
+
+@pytest.mark.parametrize("dim,n,field,eps", TILED_CASES)
+def test_tiled_elimination_matches_oracle(hiflib, dim, n, field, eps):
+    """Every cell through the tiled multi-block elimination (big_cell = 1):
+    the same skeletons, ranks and |s_L| as the oracle, and F^-1 x, F x to the
+    same bounds as the one-block path."""
+    from paper_1307_2895_gb300 import hif
+    a, b, A, F = _oracle(dim, n, field, eps)
+    x = inputs.rhs(dim, n, 3, seed=5)
+    G = hif.factor(dim, n, a, b, eps, precision="fp64", big_cell=1)
+    try:
+        fronts, root = G.structure()
+        yi = G.apply(x, inverse=True)
+        yf = G.apply(x, inverse=False)
+    finally:
+        G.free()
+    ostruct, oroot = F.skeleton_structure()
+    assert root == oroot
+    got = {(lev, tuple(c)): sk for lev, c, sk in fronts}
+    for lev, d in enumerate(ostruct):
+        for key, (c, sk, k) in d.items():
+            assert got.get((lev, tuple(c))) == sk, f"level {lev} front {c[:4]}...: skeletons differ"
+    oi, of = F.apply_inverse(x), F.apply(x)
+    assert np.linalg.norm(yi - oi) <= max(1e-10, 10 * 2.2e-16 * _kappa(A, dim, n, field)) * np.linalg.norm(oi)
+    assert np.linalg.norm(yf - of) <= 1e-10 * np.linalg.norm(of)
+
+
+@pytest.mark.parametrize("dim,n,field", [(2, 27, "contrast"), (3, 12, "contrast"), (3, 8, "lap")])
+def test_tiled_mf_matches_dense_lu(hiflib, dim, n, field):
+    """MF through the tiled elimination, ragged tiles (|I| not a multiple of 64)."""
+    from paper_1307_2895_gb300 import hif
+    a, b = _fields(dim, n, field)
+    A = stencil.assemble(dim, n, a, b)
+    f = inputs.rhs(dim, n, 2)
+    G = hif.factor(dim, n, a, b, 0.0, variant="mf", big_cell=1)
+    try:
+        x = G.apply(f)
+    finally:
+        G.free()
+    xd = np.linalg.solve(A.toarray(), f)
+    tol = 1e-12 if field == "lap" else 1e-10
+    assert np.linalg.norm(x - xd) <= tol * np.linalg.norm(xd)
+
+
+def test_tiled_mixed_pcg(hiflib):
+    """Mixed precision (FP32 tiles, safeguarded pivots) through the tiled path."""
+    from paper_1307_2895_gb300 import hif
+    dim, n, eps = 3, 20, 1e-4
+    a, b = _fields(dim, n, "contrast")
+    f = inputs.rhs(dim, n, 2)
+    G = hif.factor(dim, n, a, b, eps, precision="mixed", big_cell=1)
+    try:
+        xh, xl, info = G.solve(f, tol=1e-12, maxit=100, want_lo=True)
+    finally:
+        G.free()
+    A = stencil.assemble(dim, n, a, b)
+    assert info["converged"] and info["relres_max"] <= 1e-12
+    assert _relres_ext(A, f, xh, xl) <= 2e-12
+
+
 @pytest.mark.parametrize("dim,n,field", [(2, 16, "lap"), (2, 32, "contrast"), (2, 27, "contrast"),
                                          (3, 8, "lap"), (3, 12, "contrast")])
 def test_mf_matches_dense_lu(hiflib, dim, n, field):
