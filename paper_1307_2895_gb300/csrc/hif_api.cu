@@ -188,8 +188,15 @@ struct hif_handle {
   // sweep bytes and launches of one replay of the preconditioner graph
   double graph_bytes = 0.0;
   long long graph_launches = 0;
+  // pinned ring of per-iteration squared residual norms (inner CG), so that
+  // iterations can run in batches between host checks
+  double* rr_ring = nullptr;
+  cudaEvent_t it_ev[2] = {nullptr, nullptr};
   ~hif_handle() {
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+    for (cudaEvent_t e : it_ev)
+      if (e) cudaEventDestroy(e);
+    if (rr_ring) cudaFreeHost(rr_ring);
   }
 };
 
@@ -767,7 +774,7 @@ struct SolveWork {
     f.alloc(vb, st); bin.alloc(vb, st); xh.alloc(vb, st); xl.alloc(vb, st); D.alloc(vb, st);
     Rv.alloc(vb, st); P.alloc(vb, st); Q.alloc(vb, st);
     WP.alloc((f32 ? sizeof(float) : sizeof(double)) * N * R, st);
-    part.alloc(sizeof(double) * 4 * 304 * R, st);
+    part.alloc(sizeof(double) * 4 * kVecBlocksMax * R, st);
     scal.alloc(sizeof(double) * 12 * R + sizeof(int) * R, st);
     cnt.alloc(sizeof(unsigned), st);
     CU(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned), st));
@@ -806,7 +813,10 @@ struct Precond {
     }
     if (!exec) {
       // capture without sweep events: a replay is timed as one unit
-      if (h->profile) resolve_profile(h);
+      if (h->profile) {
+        CU(cudaStreamSynchronize(h->st));
+        resolve_profile(h);
+      }
       const int prof = h->profile;
       const double b0 = h->prof_bytes;
       const long long l0 = h->prof_launches;
@@ -814,11 +824,14 @@ struct Precond {
       cudaGraph_t g = nullptr;
       CU(cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal));
       eager();
-      CU(cudaStreamEndCapture(h->st, &g));
+      const cudaError_t ce = cudaStreamEndCapture(h->st, &g);
       h->profile = prof;
-      const cudaError_t e = cudaGraphInstantiate(&exec, g, 0);
-      cudaGraphDestroy(g);
-      if (e != cudaSuccess) {
+      cudaError_t e = ce;
+      if (ce == cudaSuccess && g) {
+        e = cudaGraphInstantiate(&exec, g, 0);
+        cudaGraphDestroy(g);
+      }
+      if (e != cudaSuccess || !exec) {
         cudaGetLastError();
         exec = nullptr;
         use_graph = false;
@@ -839,36 +852,31 @@ struct Precond {
       add(h->root);
       h->prof_bytes = b0;
       h->prof_launches = l0;
-      if (h->profile) {
-        while (h->ev_pool.size() < 2) {
-          cudaEvent_t ev;
-          CU(cudaEventCreate(&ev));
-          h->ev_pool.push_back(ev);
-        }
-      }
     }
-    if (h->profile) CU(cudaEventRecord(h->ev_pool[0], h->st));
+    if (h->profile) {
+      while (h->ev_used + 2 > h->ev_pool.size()) {
+        cudaEvent_t ev;
+        CU(cudaEventCreate(&ev));
+        h->ev_pool.push_back(ev);
+      }
+      CU(cudaEventRecord(h->ev_pool[h->ev_used], h->st));
+    }
     CU(cudaGraphLaunch(exec, h->st));
     if (h->profile) {
-      CU(cudaEventRecord(h->ev_pool[1], h->st));
-      pending_graph = true;
+      CU(cudaEventRecord(h->ev_pool[h->ev_used + 1], h->st));
+      h->ev_used += 2;
+      ++pending_graphs;
     }
     CU(cudaGetLastError());
   }
-  bool pending_graph = false;
-  // after the stream is synchronized
+  int pending_graphs = 0;
+  // after the stream is synchronized: every recorded replay (and eager sweep)
   void settle() {
     if (!h->profile) return;
-    if (pending_graph) {
-      float ms = 0.f;
-      CU(cudaEventElapsedTime(&ms, h->ev_pool[0], h->ev_pool[1]));
-      h->prof_ms += ms;
-      h->prof_bytes += h->graph_bytes;
-      h->prof_launches += h->graph_launches;
-      pending_graph = false;
-    } else {
-      resolve_profile(h);
-    }
+    resolve_profile(h);
+    h->prof_bytes += pending_graphs * h->graph_bytes;
+    h->prof_launches += pending_graphs * h->graph_launches;
+    pending_graphs = 0;
   }
 };
 
@@ -892,8 +900,15 @@ void cg_step_kernels(hif_handle* h, SolveWork& W, TZ* wp, int par, int restart, 
 }
 
 // Inner PCG on A D = Rv (FP64 recurrences, preconditioner F^-1).  Columns whose
-// squared residual is above thr2 are active.  Stops when every recursive
-// residual is below its threshold and the FP64 true residual confirms it.
+// squared residual is above thr2 are active; a column that drops below it is
+// frozen on the device (its updates stop).  The host checks iteration k's
+// residuals (copied to a pinned ring, waited for by an event) while
+// iteration k + 1 is already queued, so the GPU does not idle on the host;
+// when iteration k converged every column, the queued iteration changed
+// nothing.  Stops when the FP64 true residual confirms the recursive one.
+constexpr int kRingRows = 4;
+constexpr int kRingCols = 16;
+
 int inner_pcg(hif_handle* h, SolveWork& W, Precond& M, const std::vector<double>& hthr, int maxit) {
   const int64_t N = W.N;
   const int R = W.R;
@@ -901,6 +916,11 @@ int inner_pcg(hif_handle* h, SolveWork& W, Precond& M, const std::vector<double>
   double* partials = W.part.as<double>();
   unsigned* counter = W.cnt.as<unsigned>();
   const size_t vb = sizeof(double) * N * R;
+  if (!h->rr_ring) CU(cudaHostAlloc(&h->rr_ring, sizeof(double) * kRingRows * kRingCols, cudaHostAllocDefault));
+  if (!h->it_ev[0]) {
+    CU(cudaEventCreateWithFlags(&h->it_ev[0], cudaEventDisableTiming));
+    CU(cudaEventCreateWithFlags(&h->it_ev[1], cudaEventDisableTiming));
+  }
   CU(cudaMemcpyAsync(W.thr2, hthr.data(), sizeof(double) * R, cudaMemcpyHostToDevice, st));
   CU(cudaMemcpyAsync(W.bin.p, W.Rv.p, vb, cudaMemcpyDeviceToDevice, st));
   CU(cudaMemsetAsync(W.D.p, 0, vb, st));
@@ -912,38 +932,54 @@ int inner_pcg(hif_handle* h, SolveWork& W, Precond& M, const std::vector<double>
   };
   to_wp();
   std::vector<double> hr(R);
-  int it = 0, restarts = 0, par = 0;
+  int it = 0, issued = 0, restarts = 0, par = 0;
   int restart = 1;
-  while (true) {
+  auto converged_row = [&](const double* row) {
+    for (int c = 0; c < R; ++c)
+      if (row[c] > hthr[c]) return false;
+    return true;
+  };
+  // queue one iteration; false when maxit stops it after the preconditioner
+  auto issue = [&]() -> bool {
     M.apply();
     if (W.f32) cg_step_kernels<float>(h, W, W.WP.as<float>(), par, restart, 0, partials, counter);
     else cg_step_kernels<double>(h, W, W.WP.as<double>(), par, restart, 0, partials, counter);
     restart = 0;
-    if (it >= maxit) break;
+    if (issued >= maxit) return false;
     if (W.f32) cg_step_kernels<float>(h, W, W.WP.as<float>(), par, 0, 1, partials, counter);
     else cg_step_kernels<double>(h, W, W.WP.as<double>(), par, 0, 1, partials, counter);
-    ++it;
+    CU(cudaMemcpyAsync(h->rr_ring + (size_t)(issued % kRingRows) * kRingCols, W.rr, sizeof(double) * R,
+                       cudaMemcpyDeviceToHost, st));
+    CU(cudaEventRecord(h->it_ev[issued & 1], st));
+    ++issued;
     par ^= 1;
+    return true;
+  };
+  bool head = issue();                 // iteration `it` queued
+  while (true) {
+    if (!head) break;                  // maxit
+    const bool ahead = issue();        // iteration it + 1 queued behind it
     CU(cudaGetLastError());
-    CU(cudaMemcpyAsync(hr.data(), W.rr, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
-    CU(cudaStreamSynchronize(st));
-    M.settle();
-    bool all = true;
-    for (int c = 0; c < R; ++c)
-      if (hr[c] > hthr[c]) all = false;
-    if (!all) continue;
-    // confirm with the FP64 true residual of the inner system
+    CU(cudaEventSynchronize(h->it_ev[it & 1]));
+    const double* row = h->rr_ring + (size_t)(it % kRingRows) * kRingCols;
+    ++it;
+    if (!converged_row(row)) {
+      head = ahead;
+      continue;
+    }
+    // every column below its threshold after iteration `it`; the queued
+    // iteration (if any) left them unchanged
     launch_residual(h->gi, h->a_stag.as<double>(), h->bnode.as<double>(), W.bin.as<double>(), W.D.as<double>(),
                     W.Rv.as<double>(), R, partials, counter, W.rr, st);
     CU(cudaMemcpyAsync(hr.data(), W.rr, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
-    bool ok = true;
-    for (int c = 0; c < R; ++c)
-      if (hr[c] > hthr[c]) ok = false;
-    if (ok || ++restarts > 3) break;
+    M.settle();
+    if (converged_row(hr.data()) || ++restarts > 3) break;
     launch_set_active(R, W.rr, W.thr2, W.active, st);
     to_wp();
     restart = 1;
+    issued = it;
+    head = issue();
   }
   CU(cudaStreamSynchronize(st));
   M.settle();

@@ -68,6 +68,11 @@ __host__ __device__ inline int64_t packed_size(int64_t n) { return pad4(n * (n +
 __host__ __device__ inline int64_t cell_fac_G(int nI) { return packed_size(nI); }
 __host__ __device__ inline int64_t cell_fac_L(int nI, int nB) { return packed_size(nI) + pad4((int64_t)nB * nI); }
 __host__ __device__ inline int64_t cell_fac_size(int nI, int nB) { return 2 * packed_size(nI) + pad4((int64_t)nB * nI); }
+// Largest grid of the reducing vector kernels (8 blocks of 256 threads per
+// SM of a 152-SM GB300: enough loads in flight to stream HBM); the solver's
+// partial-sum buffer holds 4 values per block and right-hand side.
+constexpr int kVecBlocksMax = 1216;
+
 // Tile edge of the multi-block elimination of large cells, and the size of a
 // cell's X region of the work pool: room for Linv in the single-block kernel,
 // or for the diagonal-tile inverses plus the original diagonal in the tiled one.

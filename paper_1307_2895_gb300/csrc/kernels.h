@@ -1,5 +1,7 @@
 // Host-side launchers of the device kernels.
 #pragma once
+#include <vector>
+
 #include "hif_internal.h"
 
 namespace hif {

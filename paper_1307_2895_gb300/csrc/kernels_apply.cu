@@ -111,7 +111,7 @@ struct SweepSmem {
 
 // Columns per thread in the products: each thread owns one output row and a
 // group of CG consecutive right-hand sides (register accumulators).
-template <int R> struct ColGroup { static constexpr int CG = R < 4 ? R : 4; static constexpr int NG = R / CG; };
+template <int R> struct ColGroup { static constexpr int CG = R < 2 ? R : 2; static constexpr int NG = R / CG; };
 
 template <typename T, int R>
 __device__ __forceinline__ void stage_factor(SweepSmem<T, R>& sm, BulkStage& bs, const T*& Linv, const T*& G,
@@ -126,6 +126,11 @@ __device__ __forceinline__ void stage_factor(SweepSmem<T, R>& sm, BulkStage& bs,
   Tm = sm.Ts;
 }
 
+__device__ __forceinline__ void pdl_wait_then_release() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 template <typename T, int R>
 __global__ void k_apply_up(const ApplyDesc* __restrict__ blocks, const int* __restrict__ ipool,
                            const T* __restrict__ fac, T* __restrict__ x, int nr, int ldx,
@@ -134,7 +139,10 @@ __global__ void k_apply_up(const ApplyDesc* __restrict__ blocks, const int* __re
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const ApplyDesc bd = blocks[blockIdx.x];
   const int np = bd.np, nq = bd.nq;
-  if (np == 0) return;
+  if (np == 0) {
+    pdl_wait_then_release();
+    return;
+  }
   const int* idp = ipool + bd.ids;
   const int* idq = idp + np;
   SweepSmem<T, R> sm(smem_raw, np, nq, staged, is_front);
@@ -143,6 +151,7 @@ __global__ void k_apply_up(const ApplyDesc* __restrict__ blocks, const int* __re
   const T* G = fac + bd.G;
   const T* Tm = is_front ? fac + bd.T : nullptr;
   if (staged) stage_factor<T, R>(sm, bs, Linv, G, Tm, np, nq, is_front);
+  pdl_wait_then_release();
   T* xp = sm.xp;
   T* yp = sm.yp;
   T* xq = sm.xq;
@@ -207,7 +216,10 @@ __global__ void k_apply_down(const ApplyDesc* __restrict__ blocks, const int* __
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const ApplyDesc bd = blocks[blockIdx.x];
   const int np = bd.np, nq = bd.nq;
-  if (np == 0) return;
+  if (np == 0) {
+    pdl_wait_then_release();
+    return;
+  }
   const int* idp = ipool + bd.ids;
   const int* idq = idp + np;
   SweepSmem<T, R> sm(smem_raw, np, nq, staged, is_front);
@@ -216,6 +228,7 @@ __global__ void k_apply_down(const ApplyDesc* __restrict__ blocks, const int* __
   const T* G = fac + bd.G;
   const T* Tm = is_front ? fac + bd.T : nullptr;
   if (staged) stage_factor<T, R>(sm, bs, Linv, G, Tm, np, nq, is_front);
+  pdl_wait_then_release();
   T* xp = sm.xp;
   T* zp = sm.yp;
   T* xq = sm.xq;
@@ -401,6 +414,20 @@ static void launch_sweep_R(int op, const ApplyDesc* blocks, int nblocks, const i
   int threads = ((work + 31) / 32) * 32;
   threads = threads < 32 ? 32 : (threads > 256 ? 256 : threads);
   note_launches(1);
+  if (op <= 1) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nblocks);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, fn, blocks, ipool, fac, x, nr, ldx, is_front, staged, err);
+    return;
+  }
   fn<<<nblocks, threads, smem, st>>>(blocks, ipool, fac, x, nr, ldx, is_front, staged, err);
 }
 

@@ -13,7 +13,6 @@
 namespace hif {
 
 constexpr int kVecThreads = 256;
-constexpr int kVecBlocksMax = 304;   // 2 blocks per SM
 
 static inline int vec_blocks(int64_t n) {
   const int64_t b = (n + kVecThreads - 1) / kVecThreads;
@@ -332,8 +331,29 @@ __global__ void k_stencil_weights(Stencil S, int64_t N, double* __restrict__ W) 
   }
 }
 
+// Widening float -> double on the integer pipes (exact for normal numbers,
+// zeros, infinities and NaNs; subnormals take the hardware conversion).  On
+// this GPU the FP64 pipe is the narrow one, and the CG vector kernels spend
+// most of their time on it.
+template <typename TZ>
+__device__ __forceinline__ double widen(TZ v) { return (double)v; }
+template <>
+__device__ __forceinline__ double widen<float>(float v) {
+  const unsigned u = __float_as_uint(v);
+  const unsigned e = (u >> 23) & 0xffu;
+  if (e == 0u && (u & 0x7fffffu)) return (double)v;
+  const unsigned long long sgn = (unsigned long long)(u >> 31) << 63;
+  const unsigned long long man = (unsigned long long)(u & 0x7fffffu) << 29;
+  unsigned long long ex;
+  if (e == 0u) ex = 0ull;
+  else if (e == 0xffu) ex = 0x7ffull;
+  else ex = (unsigned long long)(e + 896u);
+  return __longlong_as_double((long long)(sgn | (ex << 52) | man));
+}
+
 // (A x)[e] for element e = gid * R + c from the weights (boundary neighbours
-// have weight 0 and are read at the node itself)
+// have weight +0.0 exactly and are read at the node itself; the test is on
+// the bits, off the FP64 pipe)
 template <int R, int DIM>
 __device__ __forceinline__ double stencil_w(const double* __restrict__ W, int m, int64_t gid, int c,
                                             const double* __restrict__ x) {
@@ -343,8 +363,8 @@ __device__ __forceinline__ double stencil_w(const double* __restrict__ W, int m,
   double y = w[0] * x[gid * R + c];
 #pragma unroll
   for (int ax = 0; ax < DIM; ++ax) {
-    const int64_t lo = w[1 + 2 * ax] != 0.0 ? gid - stride[ax] : gid;
-    const int64_t hi = w[2 + 2 * ax] != 0.0 ? gid + stride[ax] : gid;
+    const int64_t lo = __double_as_longlong(w[1 + 2 * ax]) != 0 ? gid - stride[ax] : gid;
+    const int64_t hi = __double_as_longlong(w[2 + 2 * ax]) != 0 ? gid + stride[ax] : gid;
     y = fma(w[1 + 2 * ax], x[lo * R + c], y);
     y = fma(w[2 + 2 * ax], x[hi * R + c], y);
   }
@@ -430,7 +450,7 @@ __global__ void k_dot2_e(int64_t N, const double* __restrict__ r, const TZ* __re
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       rv[u] = r[e + u * stride];
-      zv[u] = (double)z[e + u * stride];
+      zv[u] = widen<TZ>(z[e + u * stride]);
       qv[u] = q[e + u * stride];
     }
 #pragma unroll
@@ -440,7 +460,7 @@ __global__ void k_dot2_e(int64_t N, const double* __restrict__ r, const TZ* __re
     }
   }
   for (; e < n; e += stride) {
-    const double zv = (double)z[e];
+    const double zv = widen<TZ>(z[e]);
     acc[0] = fma(r[e], zv, acc[0]);
     acc[1] = fma(zv, q[e], acc[1]);
   }
@@ -462,14 +482,14 @@ __global__ void k_update_p_e(int64_t N, double* __restrict__ p, const TZ* __rest
     double zv[4], pv[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      zv[u] = (double)z[e + u * stride];
+      zv[u] = widen<TZ>(z[e + u * stride]);
       pv[u] = p[e + u * stride];
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) p[e + u * stride] = rs ? zv[u] : fma(beta, pv[u], zv[u]);
   }
   for (; e < n; e += stride) {
-    const double zv = (double)z[e];
+    const double zv = widen<TZ>(z[e]);
     p[e] = rs ? zv : fma(beta, p[e], zv);
   }
 }
