@@ -10,8 +10,16 @@ with ``a`` sampled on the staggered grid, ``b`` at the nodes, ``h = 1/n`` and ze
 Dirichlet values at the boundary nodes (a neighbour on the boundary contributes
 only to the diagonal).  Unknowns are ordered lexicographically with x fastest.
 
+``residual_ext`` evaluates f - A x in that bond form with every product and
+sum in numpy longdouble, from the FP64 coefficients themselves: the CSR
+matrix of ``assemble`` rounds each diagonal entry (a sum of 2 dim bond terms
+and b) to FP64, which on an ill-conditioned problem alone moves the relative
+residual of an accurate solution far above 1e-12.
+
 Pinned by: the closed-form eigenpairs of the constant-coefficient Laplacian
-(``tests/test_oracle_stencil.py``) and symmetry / row-sum identities.
+(``tests/test_oracle_stencil.py``) and symmetry / row-sum identities; the
+bond-form residual by agreement with the CSR product where the diagonal is
+exact in FP64, and by exact solutions of small systems refined in longdouble.
 """
 from __future__ import annotations
 
@@ -80,3 +88,46 @@ def coords(dim: int, n: int) -> np.ndarray:
     # meshgrid 'ij' gives axis0 = first coordinate; our order is x fastest
     out = np.stack([gi.transpose(*reversed(range(dim))).ravel() for gi in g], axis=1)
     return out.astype(np.int64)
+
+
+def apply_ext(dim: int, n: int, a_stag, b, x) -> np.ndarray:
+    """A x in the bond form of Section 3.1 / 3.2, in numpy longdouble.
+    x: (N, nrhs) (any float dtype); returns (N, nrhs) longdouble."""
+    m = n - 1
+    L = np.longdouble
+    x = np.asarray(x).astype(L)
+    nr = x.shape[1]
+    xg = x.reshape((m,) * dim + (nr,))             # axis order (.., j2, j1, rhs)
+    n2 = L(n) * L(n)
+    Ax = np.asarray(b, dtype=np.float64).astype(L).reshape((m,) * dim)[..., None] * xg
+    for axis, blk in enumerate(_stag_blocks(dim, n, a_stag)):
+        arr_axis = dim - 1 - axis
+        a = blk.astype(L)[..., None] * n2          # bond values, n along arr_axis
+        pad = [(0, 0)] * (dim + 1)
+        pad[arr_axis] = (1, 1)
+        xp = np.pad(xg, pad)                       # zero Dirichlet values
+        lo = [slice(None)] * (dim + 1)
+        hi = [slice(None)] * (dim + 1)
+        lo[arr_axis] = slice(0, m)
+        hi[arr_axis] = slice(2, m + 2)
+        alo = [slice(None)] * (dim + 1)
+        ahi = [slice(None)] * (dim + 1)
+        alo[arr_axis] = slice(0, m)
+        ahi[arr_axis] = slice(1, n)
+        Ax = Ax + a[tuple(alo)] * (xg - xp[tuple(lo)]) + a[tuple(ahi)] * (xg - xp[tuple(hi)])
+    return Ax.reshape(x.shape)
+
+
+def residual_ext(dim: int, n: int, a_stag, b, f, x_hi, x_lo=None) -> np.ndarray:
+    """Per-column relative residual ||f - A (x_hi + x_lo)||_2 / ||f||_2 with A
+    applied in the bond form (``apply_ext``) in numpy longdouble.
+    f, x_hi, x_lo: (N,) or (N, nrhs) in the lexicographic order (x fastest)."""
+    f2 = np.asarray(f, dtype=np.float64)
+    if f2.ndim == 1:
+        f2 = f2[:, None]
+    L = np.longdouble
+    x = np.asarray(x_hi, dtype=np.float64).reshape(f2.shape).astype(L)
+    if x_lo is not None:
+        x = x + np.asarray(x_lo, dtype=np.float64).reshape(f2.shape).astype(L)
+    r = f2.astype(L) - apply_ext(dim, n, a_stag, b, x)
+    return np.linalg.norm(r.astype(np.float64), axis=0) / np.linalg.norm(f2, axis=0)

@@ -78,3 +78,47 @@ def test_generators_deterministic_and_shaped():
     assert abs(z.mean()) < 0.01 and abs(z.std() - 1) < 0.01
     r = inputs.rhs(2, 16, 3)
     assert r.shape == (225, 3) and r.flags["C_CONTIGUOUS"]
+
+
+@pytest.mark.parametrize("dim,n", [(2, 12), (3, 7)])
+def test_residual_ext_matches_csr_where_exact(dim, n):
+    """a = 1 (all diagonal entries exact in FP64): the longdouble bond-form
+    residual equals f - A x with the CSR product carried out in longdouble."""
+    a, b = inputs.constant_coefficients(dim, n)
+    b = b + 0.5                                  # exact in FP64 as well
+    A = stencil.assemble(dim, n, a, b)
+    rng = np.random.default_rng(4)
+    x = rng.standard_normal((A.shape[0], 2))
+    f = rng.standard_normal((A.shape[0], 2))
+    L = np.longdouble
+    prod = A.data.astype(L)[:, None] * x.astype(L)[A.indices]
+    rows = np.repeat(np.arange(A.shape[0]), np.diff(A.indptr))
+    Ax = np.zeros(x.shape, dtype=L)
+    np.add.at(Ax, rows, prod)
+    ref = np.linalg.norm((f.astype(L) - Ax).astype(np.float64), axis=0) / np.linalg.norm(f, axis=0)
+    got = stencil.residual_ext(dim, n, a, b, f, x)
+    assert np.allclose(got, ref, rtol=1e-12, atol=0)
+
+
+def test_residual_ext_of_refined_solution():
+    """Contrast 1e6, b = 1e-3: a direct FP64 solve refined twice with the
+    longdouble bond-form residual reaches 1e-13 in the bond-form residual
+    (the x86 80-bit longdouble, u ~ 1e-19, limits it to a few 1e-14);
+    the same iterate measured with the FP64-assembled matrix does not (its
+    rounded diagonal is a different operator at that level)."""
+    import scipy.sparse.linalg as spla
+    dim, n = 2, 32
+    a, _ = inputs.high_contrast_coefficients(dim, n, seed=2, low=1e-3, high=1e3)
+    b = np.full((n - 1) ** dim, 1e-3)
+    A = stencil.assemble(dim, n, a, b)
+    f = inputs.rhs(dim, n, 2, seed=1)
+    lu = spla.splu(A.tocsc())
+    L = np.longdouble
+    x = lu.solve(f).astype(L)
+    for _ in range(3):
+        r = (f.astype(L) - stencil.apply_ext(dim, n, a, b, x)).astype(np.float64)
+        x = x + lu.solve(r).astype(L)
+    xh = x.astype(np.float64)
+    xl = (x - xh.astype(L)).astype(np.float64)
+    assert stencil.residual_ext(dim, n, a, b, f, xh, xl).max() <= 1e-13
+    assert stencil.residual_ext(dim, n, a, b, f, xh).max() <= 1e-9
