@@ -257,7 +257,7 @@ def run_gpu(args, rank, world, local_rank):
     peak, peak_kind = _peaks()
     achieved = (sweep_bytes / sweep_launches) / (sweep_ms / sweep_launches / 1e3) / 1e9 if sweep_ms > 0 else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": (achieved / peak) if achieved else None, "traffic": None,
+            "frac": (achieved / peak) if achieved else None, "traffic": _sweep_traffic(),
             "kernel": "k_apply_up/k_apply_down (F^-1 sweeps)", "peak_kind": peak_kind,
             "avg_launch_us": 1e3 * sweep_ms / max(sweep_launches, 1),
             "bytes_per_launch": sweep_bytes / max(sweep_launches, 1),
@@ -327,6 +327,50 @@ def run_gpu(args, rank, world, local_rank):
     return 0
 
 
+def _sweep_traffic():
+    """Measured DRAM bytes per F^-1 sweep launch (dram__bytes_read + write,
+    one ncu capture of the same workload), from the committed profile summary;
+    None once the sweep kernel source differs from the one captured."""
+    import hashlib
+    prof = os.path.join(ROOT, "profiles", "dram_sweeps_contrast2d_n512.md")
+    src = os.path.join(ROOT, "paper_1307_2895_gb300", "csrc", "kernels_apply.cu")
+    try:
+        text = open(prof).read()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    val = cap_sha = None
+    for line in text.splitlines():
+        if line.startswith("traffic_per_launch_bytes:"):
+            val = float(line.split(":", 1)[1])
+        if line.startswith("kernels_apply.cu sha256:"):
+            cap_sha = line.split(":", 1)[1].strip()
+    return val if (val is not None and cap_sha == sha) else None
+
+
+def run_solve_only(args):
+    """Factor the workload and run one 8-RHS solve, this many times: the
+    command ncu captures the CG vector kernels and the factor kernels of."""
+    import torch
+    from paper_1307_2895_gb300 import hif
+    hif.load()
+    w, f_np = _workload_arrays()
+    dev = torch.device("cuda", 0)
+    st = torch.cuda.Stream(device=dev)
+    a = torch.from_numpy(w["a_stag"]).to(dev)
+    b = torch.from_numpy(w["b"]).to(dev)
+    f = torch.from_numpy(f_np).to(dev)
+    for _ in range(args.ncu_solve):
+        G = hif.factor(w["dim"], w["n"], a, b, w["eps"], precision=args.precision, stream=st)
+        try:
+            x, info = G.solve(f, tol=TOL, maxit=1000)
+        finally:
+            G.free()
+    torch.cuda.synchronize()
+    print(json.dumps({"solves": args.ncu_solve, "info": info}))
+    return 0
+
+
 def run_apply_only(args):
     """Factor the workload once and run a number of F^-1 applies (8 RHS):
     the command ncu captures the sweep kernels of."""
@@ -360,11 +404,15 @@ def main():
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--ncu-solve", type=int, default=0,
+                    help="profiling helper: this many factor + 8-RHS solves of the workload, then exit")
     ap.add_argument("--ncu-apply", type=int, default=0,
                     help="profiling helper: factor the workload, then run this many F^-1 applies and exit")
     args = ap.parse_args()
     if args.ncu_apply:
         return run_apply_only(args)
+    if args.ncu_solve:
+        return run_solve_only(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -177,10 +177,13 @@ __global__ void k_apply_up(const ApplyDesc* __restrict__ blocks, const int* __re
     const int i = e / NG, c0 = (e % NG) * CG;
     const T* l = Linv + tri(i);
     T acc[CG] = {};
+    const T* xv = xp + c0;
+#pragma unroll 4
     for (int t = 0; t <= i; ++t) {
       const T lv = l[t];
 #pragma unroll
-      for (int c = 0; c < CG; ++c) acc[c] += lv * xp[t * R + c0 + c];
+      for (int c = 0; c < CG; ++c) acc[c] += lv * xv[c];
+      xv += R;
     }
 #pragma unroll
     for (int c = 0; c < CG; ++c) {
@@ -253,10 +256,15 @@ __global__ void k_apply_down(const ApplyDesc* __restrict__ blocks, const int* __
   for (int e = threadIdx.x; e < np * NG; e += blockDim.x) {   // z = Linv^T w
     const int i = e / NG, c0 = (e % NG) * CG;
     T acc[CG] = {};
+    const T* lcol = Linv + tri(i) + i;           // Linv[t][i], row t starts at tri(t)
+    const T* xv = xp + i * R + c0;
+#pragma unroll 4
     for (int t = i; t < np; ++t) {
-      const T lv = Linv[tri(t) + i];
+      const T lv = *lcol;
+      lcol += t + 1;
 #pragma unroll
-      for (int c = 0; c < CG; ++c) acc[c] += lv * xp[t * R + c0 + c];
+      for (int c = 0; c < CG; ++c) acc[c] += lv * xv[c];
+      xv += R;
     }
 #pragma unroll
     for (int c = 0; c < CG; ++c) {
