@@ -94,8 +94,11 @@ typedef struct hif_opts {
   unsigned long long seed; /* counter-based sketch RNG seed                     */
   int big_cell;         /* cells with at least this many interior DOFs are
                            eliminated by the tiled multi-block kernels (64 x 64
-                           tiles, blocked Cholesky, Lemma 2.1); 0 -> 192,
-                           < 0 -> never.  Same result up to rounding order.      */
+                           tiles, blocked Cholesky, Lemma 2.1), and fronts with
+                           at least max(big_cell, 128) DOFs skeletonized by the
+                           multi-block front kernels (tiled sketch, residual
+                           check and Lemma 2.4 products); 0 -> 192, < 0 ->
+                           never.  Same result up to rounding order.           */
 } hif_opts;
 
 typedef struct hif_handle hif_handle;

@@ -1,0 +1,144 @@
+// Device pieces shared by the one-block front kernel and the multi-block
+// skeletonization of large fronts: the entries of a front's blocks from the
+// two adjacent cells' update matrices, the column-pivoted QR with the rank
+// rule of Section 2.2, T = R11^-1 R12 (Lemma 2.2) and the counter-based
+// Gaussian stream of the randomized ID (Section 4.3).
+#pragma once
+#include <cstdint>
+
+#include "blockops.cuh"
+#include "hif_internal.h"
+
+namespace hif {
+
+template <typename T>
+__device__ __forceinline__ T front_entry(const T* U1, int ld1, const T* U2, int ld2,
+                                         const int* pos1, const int* pos2, int x, int y) {
+  T v = T(0);
+  const int a1 = pos1[x], b1 = pos1[y];
+  if (a1 >= 0 && b1 >= 0) v += U1[(int64_t)a1 * ld1 + b1];
+  const int a2 = pos2[x], b2 = pos2[y];
+  if (a2 >= 0 && b2 >= 0) v += U2[(int64_t)a2 * ld2 + b2];
+  return v;
+}
+
+// Column-pivoted Householder QR of A (m x nc, column-major, ld m), in place,
+// with residual norms recomputed every step (FP64 accumulation), the pivot
+// tie rule (smallest position within a factor 1 - 1e-10 of the largest
+// squared norm) and the rank rule (stop when |R_ii| <= eps |R_11|).
+// perm[0..k) = skeleton columns in pivot order, perm[k..nc) = the others in
+// ascending order.  Returns k.  flag_near marks pivot ratios within 1e-8 of
+// eps in bit 1 of *status.
+template <typename T>
+__device__ int blk_pivoted_qr(T* A, int m, int nc, double eps, int* status, bool flag_near, double* sq,
+                              double* v, int* perm, int* chosen) {
+  __shared__ double s_mx, s_vv, s_alpha;
+  __shared__ int s_piv, s_stop, s_k;
+  for (int j = threadIdx.x; j < nc; j += blockDim.x) chosen[j] = 0;
+  if (threadIdx.x == 0) { s_k = 0; s_stop = 0; }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  const int kmax = m < nc ? m : nc;
+  for (int i = 0; i < kmax; ++i) {
+    for (int j = warp; j < nc; j += nwarps) {
+      if (chosen[j]) continue;
+      const T* col = A + (int64_t)j * m;
+      double acc = 0.0;
+      for (int r = i + lane; r < m; r += 32) { const double x = (double)col[r]; acc += x * x; }
+      acc = warp_sum(acc);
+      if (lane == 0) sq[j] = acc;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      double mx = -1.0;
+      for (int j = lane; j < nc; j += 32) if (!chosen[j] && sq[j] > mx) mx = sq[j];
+      for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      int piv = 0x7fffffff;
+      for (int j = lane; j < nc; j += 32)
+        if (!chosen[j] && sq[j] >= (1.0 - 1e-10) * mx) { piv = j; break; }
+      for (int o = 16; o > 0; o >>= 1) piv = min(piv, __shfl_xor_sync(0xffffffffu, piv, o));
+      if (lane == 0) {
+        if (i == 0) s_mx = mx;  // |R_11|^2
+        const double nu = (i == 0) ? mx : s_mx;
+        const double ratio = (nu > 0.0) ? sqrt(mx / nu) : 0.0;
+        if (flag_near && fabs(ratio - eps) <= 1e-8 * eps) atomicOr(status, 2);
+        const int stop = (mx <= 0.0) || (i > 0 && mx <= eps * eps * nu);
+        s_stop = stop;
+        if (!stop) {
+          s_piv = piv;
+          const double x0 = (double)A[(int64_t)piv * m + i];
+          const double sp = sq[piv];      // the pivot's own squared norm builds the reflector
+          const double a2 = (x0 >= 0.0) ? -sqrt(sp) : sqrt(sp);
+          s_alpha = a2;
+          s_vv = sp - x0 * x0 + (x0 - a2) * (x0 - a2);
+          perm[s_k] = piv;
+          chosen[piv] = 1;
+          s_k = s_k + 1;
+        }
+      }
+    }
+    __syncthreads();
+    if (s_stop) break;
+    const int piv = s_piv;
+    const double alpha = s_alpha, vv = s_vv;
+    T* pc = A + (int64_t)piv * m;
+    for (int r = i + threadIdx.x; r < m; r += blockDim.x) v[r] = (double)pc[r] - (r == i ? alpha : 0.0);
+    __syncthreads();
+    if (vv > 0.0) {
+      for (int j = warp; j < nc; j += nwarps) {
+        if (chosen[j]) continue;
+        T* col = A + (int64_t)j * m;
+        double s = 0.0;
+        for (int r = i + lane; r < m; r += 32) s += v[r] * (double)col[r];
+        s = warp_sum(s);
+        const double f = 2.0 * s / vv;
+        for (int r = i + lane; r < m; r += 32) col[r] = (T)((double)col[r] - f * v[r]);
+      }
+    }
+    for (int r = i + threadIdx.x; r < m; r += blockDim.x) pc[r] = (r == i) ? (T)alpha : T(0);
+    __syncthreads();
+  }
+  const int k = s_k;
+  if (threadIdx.x == 0) {
+    int t = k;
+    for (int j = 0; j < nc; ++j) if (!chosen[j]) perm[t++] = j;
+  }
+  __syncthreads();
+  return k;
+}
+
+// T = R11^{-1} R12 from the factored A of blk_pivoted_qr (back substitution,
+// one thread per redundant column); T is k x (nc - k), row-major.
+template <typename T>
+__device__ void blk_id_T(const T* A, int m, const int* perm, int k, int nc, T* Tm) {
+  const int nR = nc - k;
+  for (int c = threadIdx.x; c < nR; c += blockDim.x) {
+    const T* r12 = A + (int64_t)perm[k + c] * m;
+    for (int t = k - 1; t >= 0; --t) {
+      T s = r12[t];
+      for (int u = t + 1; u < k; ++u) s -= A[(int64_t)perm[u] * m + t] * Tm[(int64_t)u * nR + c];
+      Tm[(int64_t)t * nR + c] = s / A[(int64_t)perm[t] * m + t];
+    }
+  }
+  __syncthreads();
+}
+
+// Standard normal from two splitmix64 outputs of a counter (Box-Muller).
+__device__ __forceinline__ uint64_t smix64(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__device__ __forceinline__ float gauss01(uint64_t key) {
+  const uint64_t a = smix64(key * 2), b = smix64(key * 2 + 1);
+  const float u1 = ((float)(a >> 40) + 0.5f) * (1.0f / 16777216.0f);
+  const float u2 = (float)(b >> 40) * (1.0f / 16777216.0f);
+  return sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+}
+
+
+// Key of front f's Gaussian stream at one fractional level.
+__device__ __forceinline__ uint64_t sketch_key(uint64_t seed, int f) { return smix64(seed ^ ((uint64_t)f << 32)); }
+
+}  // namespace hif

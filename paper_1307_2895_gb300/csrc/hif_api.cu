@@ -360,7 +360,8 @@ struct Factorizer {
   // interior DOFs go through the tiled multi-block kernels, the others
   // through the one-block-per-cell kernel.
   template <typename U>
-  void factor_cells(const std::vector<CellDesc>& cd, const CellDesc* d_cd, U* work, U* fac, DevBuf& selbuf) {
+  void factor_cells(const std::vector<CellDesc>& cd, const CellDesc* d_cd, U* work, U* fac, DevBuf& selbuf,
+                    DevBuf& tdbuf) {
     std::vector<int> small, big;
     int max_small = 0, max_bI = 0, max_bB = 0;
     for (int i = 0; i < (int)cd.size(); ++i) {
@@ -377,13 +378,27 @@ struct Factorizer {
       launch_cell_factor<U>(d_cd, nullptr, (int)cd.size(), work, fac, status.as<int>(), max_small, tau, st);
       return;
     }
-    std::vector<int> sel(small);
-    sel.insert(sel.end(), big.begin(), big.end());
-    upload(selbuf, sel, st);
-    const int* d_sel = selbuf.as<int>();
-    launch_cell_factor<U>(d_cd, d_sel, (int)small.size(), work, fac, status.as<int>(), max_small, tau, st);
-    launch_cell_factor_tiled<U>(d_cd, d_sel + small.size(), (int)big.size(), max_bI, max_bB, work, fac,
-                                status.as<int>(), tau, st);
+    if (!small.empty()) {
+      upload(selbuf, small, st);
+      launch_cell_factor<U>(d_cd, selbuf.as<int>(), (int)small.size(), work, fac, status.as<int>(), max_small, tau,
+                            st);
+    }
+    std::vector<TDesc> td(big.size());
+    for (size_t b = 0; b < big.size(); ++b) {
+      const CellDesc& c = cd[big[b]];
+      TDesc& t = td[b];
+      t.nI = c.nI;
+      t.nB = c.nB;
+      t.FII = c.F;
+      t.FBI = c.F + (int64_t)c.nI * c.nI;
+      t.FBB = t.FBI + (int64_t)c.nB * c.nI;
+      t.X = t.FBB + (int64_t)c.nB * c.nB;
+      t.Linv = c.fac;
+      t.G = c.fac + cell_fac_G(c.nI);
+      t.Lp = c.fac + cell_fac_L(c.nI, c.nB);
+    }
+    upload(tdbuf, td, st);
+    launch_tiled_elim<U>(tdbuf.as<TDesc>(), (int)big.size(), max_bI, max_bB, work, fac, status.as<int>(), tau, st);
   }
 
   static int max_front_size(const std::vector<CellDesc>& cd) {
@@ -424,8 +439,8 @@ struct Factorizer {
       const int nc0 = (int)L0->cdesc.size();
       launch_leaf_assemble<T>(L0->d_cdesc, nc0, L0->d_cipool, work.as<T>(), h->gi, h->a_stag.as<double>(),
                               h->bnode.as<double>(), L0->d_cls0, G.ncell[0], st);
-      DevBuf sel0;
-      factor_cells<T>(L0->cdesc, L0->d_cdesc, work.as<T>(), sw.fac.as<T>(), sel0);
+      DevBuf sel0, td0;
+      factor_cells<T>(L0->cdesc, L0->d_cdesc, work.as<T>(), sw.fac.as<T>(), sel0, td0);
       CU(cudaGetLastError());
       sw.nblocks = nc0;
       sw.desc = L0->d_capply;
@@ -468,15 +483,15 @@ struct Factorizer {
       sw.fac.alloc((size_t)fac_elems * esz, st);
       const CellDesc* dd = ddesc.as<CellDesc>();
       const int max_nF = max_front_size(cdesc);
-      DevBuf selbuf;
+      DevBuf selbuf, tdbuf;
       if (is_root) {
         launch_extend_add<T, double>(dd, ncells, sw.ipool, work.as<double>(), prev_ddesc, prev_work.as<T>(),
                                      nchild, max_nF, st);
-        factor_cells<double>(cdesc, dd, work.as<double>(), sw.fac.as<double>(), selbuf);
+        factor_cells<double>(cdesc, dd, work.as<double>(), sw.fac.as<double>(), selbuf, tdbuf);
       } else {
         launch_extend_add<T, T>(dd, ncells, sw.ipool, work.as<T>(), prev_ddesc, prev_work.as<T>(), nchild, max_nF,
                                 st);
-        factor_cells<T>(cdesc, dd, work.as<T>(), sw.fac.as<T>(), selbuf);
+        factor_cells<T>(cdesc, dd, work.as<T>(), sw.fac.as<T>(), selbuf, tdbuf);
       }
       CU(cudaGetLastError());
       std::vector<ApplyDesc> ad;
@@ -562,10 +577,49 @@ struct Factorizer {
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
     CU(cudaEventRecord(e0, st));
-    launch_front<T>(d_fd, nf, d_cdesc, d_ip, obuf.as<int>(), fwork.as<T>(), sw.fac.as<T>(), cwork.as<T>(), h->eps,
-                    status.as<int>(), max_nc, max_nN, tau, sketch.as<int>(),
-                    h->seed * 0x9E3779B97F4A7C15ull + (uint64_t)l, st);
-    CU(cudaEventRecord(e1, st));
+    const uint64_t seed = h->seed * 0x9E3779B97F4A7C15ull + (uint64_t)l;
+    // fronts with at least max(big_cell, kBigFrontMin) DOFs: the multi-block
+    // skeletonization (its elimination scratch needs |c|^2 >= cell_x_elems(|c|))
+    const int big_front = std::max(h->big_cell, kBigFrontMin);
+    std::vector<int> small, big;
+    int big_nc = 0, big_nN = 0;
+    for (int f = 0; f < nf; ++f) {
+      if (fd[f].nc >= big_front) {
+        big.push_back(f);
+        big_nc = std::max(big_nc, fd[f].nc);
+        big_nN = std::max(big_nN, fd[f].nN);
+      } else {
+        small.push_back(f);
+      }
+    }
+    DevBuf d_sel, d_big, bstate, m2part, e2part, d_td;
+    const int nbig = (int)big.size();
+    const int nm = nbig ? bigfront_colmax_blocks(big_nc) : 0;
+    const int ne = nbig ? bigfront_resid_strips(big_nc) : 0;
+    if (big.empty()) {
+      launch_front<T>(d_fd, nf, d_cdesc, d_ip, obuf.as<int>(), fwork.as<T>(), sw.fac.as<T>(), cwork.as<T>(), h->eps,
+                      status.as<int>(), max_nc, max_nN, tau, sketch.as<int>(), seed, nullptr, st);
+    } else {
+      if (!small.empty()) {
+        upload(d_sel, small, st);
+        int snc = 0, snN = 0;
+        for (int f : small) {
+          snc = std::max(snc, fd[f].nc);
+          snN = std::max(snN, fd[f].nN);
+        }
+        launch_front<T>(d_fd, (int)small.size(), d_cdesc, d_ip, obuf.as<int>(), fwork.as<T>(), sw.fac.as<T>(),
+                        cwork.as<T>(), h->eps, status.as<int>(), snc, snN, tau, sketch.as<int>(), seed,
+                        d_sel.as<int>(), st);
+      }
+      upload(d_big, big, st);
+      bstate.alloc(sizeof(int) * nbig, st);
+      m2part.alloc(sizeof(double) * nbig * nm, st);
+      e2part.alloc(sizeof(double) * nbig * ne, st);
+      launch_bigfront_id<T>(d_fd, d_big.as<int>(), nbig, d_cdesc, d_ip, cwork.as<T>(), fwork.as<T>(), sw.fac.as<T>(),
+                            obuf.as<int>(), sketch.as<int>(), seed, h->eps, status.as<int>(), bstate.as<int>(),
+                            m2part.as<double>(), nm, e2part.as<double>(), ne, big_nc, big_nN,
+                            sketch.p ? big_nc : 0, st);
+    }
     CU(cudaGetLastError());
     info.fr = fr;
     info.fd = fdp;
@@ -574,6 +628,42 @@ struct Factorizer {
     int hstat = 0;
     CU(cudaMemcpyAsync(&hstat, status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
+    if (!big.empty()) {
+      // ranks known: B_sr, B_rr, A_ss, the tiled elimination, B_ss back
+      std::vector<TDesc> td;
+      int max_k = 0, max_nR = 0;
+      for (int f : big) {
+        const FrontDesc& d = fd[f];
+        const int k = info.out[d.out];
+        const int nR = d.nc - k;
+        max_k = std::max(max_k, k);
+        max_nR = std::max(max_nR, nR);
+        if (nR == 0) continue;
+        TDesc t;
+        t.nI = nR;
+        t.nB = k;
+        t.FII = d.work + (int64_t)d.nN * d.nc + (int64_t)d.nc * d.nc;
+        t.FBI = t.FII + (int64_t)nR * nR;
+        t.FBB = t.FBI + (int64_t)k * nR;
+        t.X = t.FII + (int64_t)d.nc * d.nc;
+        t.Linv = d.fac;
+        t.G = d.fac + front_fac_G(d.nc);
+        t.Lp = d.fac + front_fac_L(d.nc);
+        td.push_back(t);
+      }
+      launch_bigfront_form<T>(d_fd, d_big.as<int>(), nbig, obuf.as<int>(), fwork.as<T>(), sw.fac.as<T>(), max_k,
+                              max_nR, st);
+      if (!td.empty()) {
+        upload(d_td, td, st);
+        launch_tiled_elim<T>(d_td.as<TDesc>(), (int)td.size(), max_nR, max_k, fwork.as<T>(), sw.fac.as<T>(),
+                             status.as<int>(), tau, st);
+      }
+      launch_bigfront_scatter<T>(d_fd, d_big.as<int>(), nbig, d_cdesc, d_ip, obuf.as<int>(), fwork.as<T>(),
+                                 cwork.as<T>(), max_k, st);
+      CU(cudaGetLastError());
+    }
+    CU(cudaEventRecord(e1, st));
+    CU(cudaEventSynchronize(e1));
     {
       float ms = 0.f;
       CU(cudaEventElapsedTime(&ms, e0, e1));

@@ -39,6 +39,18 @@ struct FrontDesc {
   int64_t out;         // output buffer: k | perm[nc] | ids_sr[nc]
 };
 
+// A dense elimination problem for the tiled kernels (Lemma 2.1 on
+// [F_II F_BI^T; F_BI F_BB]): a large cell, or the redundant block of a large
+// front after its ID (F_II = B_rr, F_BI = B_sr, F_BB = A_ss, Lemma 2.4).
+// Offsets of the row-major blocks into the work pool (F_II: nI x nI, F_BI:
+// nB x nI, F_BB: nB x nB, X: cell_x_elems(nI) scratch) and of the outputs
+// into the factor pool (Linv and L packed by rows, G = F_BI L^-T: nB x nI).
+struct TDesc {
+  int nI, nB;
+  int64_t FII, FBI, FBB, X;
+  int64_t Linv, G, Lp;
+};
+
 // Block of the factor as the apply sweeps see it.  Cell: p = I, q = B.
 // Front: p = redundant set r, q = skeleton set s, with T (nq x np).
 // Linv and L are lower triangular, packed by rows (entry (i, t), t <= i, at
@@ -77,6 +89,10 @@ constexpr int kVecBlocksMax = 1216;
 // cell's X region of the work pool: room for Linv in the single-block kernel,
 // or for the diagonal-tile inverses plus the original diagonal in the tiled one.
 constexpr int kTile = 64;
+// Smallest front of the multi-block skeletonization: its work layout gives the
+// elimination scratch |c|^2 elements, which covers cell_x_elems(|c|) from
+// |c| = 105 on.
+constexpr int kBigFrontMin = 128;
 __host__ __device__ inline int64_t cell_x_elems(int nI) {
   const int64_t t = (int64_t)((nI + kTile - 1) / kTile) * kTile * kTile + nI;
   const int64_t s = (int64_t)nI * nI;

@@ -18,15 +18,33 @@ void launch_extend_add(const CellDesc* cells, int ncells, const int* ipool, TF* 
 template <typename T>
 void launch_cell_factor(const CellDesc* cells, const int* sel, int ncells, T* work, T* fac, int* status,
                         int max_nI, double tau, cudaStream_t st);
-// tiled multi-block elimination of the cells sel[0..nsel) (kernels_tiled.cu)
+// tiled multi-block elimination of the problems td[0..n) (kernels_tiled.cu)
 template <typename T>
-void launch_cell_factor_tiled(const CellDesc* cells, const int* sel, int nsel, int max_nI, int max_nB, T* work,
-                              T* fac, int* status, double tau, cudaStream_t st);
+void launch_tiled_elim(const TDesc* td, int n, int max_nI, int max_nB, T* work, T* fac, int* status, double tau,
+                       cudaStream_t st);
 template <typename T>
 void launch_front(const FrontDesc* fronts, int nfronts, const CellDesc* cells, const int* ipool, int* obuf,
                   T* fwork,
                   T* fac, T* cwork, double eps, int* status, int max_nc, int max_nN, double tau,
-                  const int* sketch, uint64_t seed, cudaStream_t st);
+                  const int* sketch, uint64_t seed, const int* sel, cudaStream_t st);
+
+// skeletonization of large fronts (kernels_bigfront.cu): the ID (writes T
+// and the front's outputs), then, with the ranks known on the host, the
+// Lemma 2.4 blocks, and after the tiled elimination the B_ss scatter.
+template <typename T>
+void launch_bigfront_id(const FrontDesc* fronts, const int* big, int nbig, const CellDesc* cells, const int* ipool,
+                        const T* cwork, T* fwork, T* fac, int* obuf, const int* sketch, uint64_t seed, double eps,
+                        int* status, int* state, double* m2part, int nm, double* e2part, int ne, int max_nc,
+                        int max_nN, int max_ell, cudaStream_t st);
+template <typename T>
+void launch_bigfront_form(const FrontDesc* fronts, const int* big, int nbig, const int* obuf, T* fwork,
+                          const T* fac, int max_k, int max_nR, cudaStream_t st);
+template <typename T>
+void launch_bigfront_scatter(const FrontDesc* fronts, const int* big, int nbig, const CellDesc* cells,
+                             const int* ipool, const int* obuf, const T* fwork, T* cwork, int max_k,
+                             cudaStream_t st);
+int bigfront_colmax_blocks(int max_nc);
+int bigfront_resid_strips(int max_nc);
 
 // rank-prediction MLP (kernels_mlp.cu); idx may be NULL (samples 0..nb-1)
 void mlp_grad(const float* X, const float* t, const int* idx, int nb, float inv_n, const float* prm,

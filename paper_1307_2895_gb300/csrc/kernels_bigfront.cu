@@ -1,0 +1,486 @@
+// Skeletonization of large fronts (the ID of Section 2.2 / 4.3 and the
+// elimination of Lemma 2.4) spread over many thread blocks per front.  The
+// one-block kernel (k_front) runs every step of a front on one SM, which at
+// the top levels of a 3D tree leaves the GPU nearly idle for seconds; here
+// every dense product of the fronts of a level is one launch over 64 x 64
+// tiles of all of them:
+//
+//   M = A_{N,c}, A_cc from the adjacent cells' update matrices (k_bf_assemble)
+//   ID:  Y = Phi M (k_bf_sketch, Phi generated on the fly), pivoted QR of Y
+//        and T from its R (k_bf_id), accepted when every column of
+//        M_r - M_s T has norm <= eps max_j ||M_j|| (k_bf_colmax, k_bf_resid,
+//        k_bf_check); otherwise, and in the
+//        pivoted-QR mode, the pivoted QR of M itself (k_bf_id, one block)
+//   B_sr = A_sr - A_ss T, B_rr = A_rr - A_sr^T T - T^T B_sr (k_bf_form_*)
+//   L L^T = B_rr, G = B_sr L^-T, B_ss = A_ss - G G^T by the tiled
+//   elimination of large cells (kernels_tiled.cu) on [B_rr; B_sr; A_ss]
+//   B_ss into the first cell's update matrix, zeros into the second's
+//   (k_bf_scatter).
+//
+// Work layout of a large front (from fd.work in the level's front pool):
+//   M (nN x nc, column-major) | A_cc (nc x nc) | F: B_rr (nR x nR) | B_sr
+//   (k x nR) | A_ss (k x k) (<= nc^2) | X (elimination scratch, <= nc^2) |
+//   Y (the sketch, ell x nc column-major, <= nc^2).
+#include "hif_internal.h"
+#include "blockops.cuh"
+#include "front_common.cuh"
+#include "kernels.h"
+#include "tile_mma.cuh"
+
+namespace hif {
+
+struct BfView {
+  int nc, nN;
+  int64_t M, Acc, F, X, Y;
+};
+
+__device__ __forceinline__ BfView bf_view(const FrontDesc& fd) {
+  BfView v;
+  v.nc = fd.nc;
+  v.nN = fd.nN;
+  v.M = fd.work;
+  v.Acc = v.M + (int64_t)fd.nN * fd.nc;
+  v.F = v.Acc + (int64_t)fd.nc * fd.nc;
+  v.X = v.F + (int64_t)fd.nc * fd.nc;
+  v.Y = v.X + (int64_t)fd.nc * fd.nc;
+  return v;
+}
+
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double s_part[32];
+  v = warp_sum(v);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) s_part[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_part[w];
+  __syncthreads();
+  return t;   // valid in thread 0
+}
+
+// ---- assembly: M and A_cc
+template <typename T>
+__global__ void k_bf_assemble(const FrontDesc* __restrict__ fronts, const int* __restrict__ big,
+                              const CellDesc* __restrict__ cells, const int* __restrict__ ipool,
+                              const T* __restrict__ cwork, T* __restrict__ fwork) {
+  const FrontDesc fd = fronts[big[blockIdx.y]];
+  const BfView v = bf_view(fd);
+  const int nc = fd.nc, nN = fd.nN;
+  const int* idc = ipool + fd.ids;
+  const int* pos1 = idc + nc;
+  const int* pos2 = pos1 + nc + nN;
+  const CellDesc P1 = cells[fd.P1], P2 = cells[fd.P2];
+  const T* U1 = cwork + P1.F + (int64_t)P1.nI * P1.nI + (int64_t)P1.nB * P1.nI;
+  const T* U2 = cwork + P2.F + (int64_t)P2.nI * P2.nI + (int64_t)P2.nB * P2.nI;
+  const int ld1 = P1.nB, ld2 = P2.nB;
+  T* M = fwork + v.M;
+  T* Acc = fwork + v.Acc;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)nN * nc; e += stride) {
+    const int j = (int)(e / nN), i = (int)(e % nN);
+    M[e] = front_entry(U1, ld1, U2, ld2, pos1, pos2, nc + i, j);
+  }
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)nc * nc; e += stride) {
+    const int i = (int)(e / nc), j = (int)(e % nc);
+    Acc[e] = front_entry(U1, ld1, U2, ld2, pos1, pos2, i, j);
+  }
+}
+
+// ---- largest squared column norm of M: one warp per column, block maxima
+template <typename T>
+__global__ void k_bf_colmax(const FrontDesc* __restrict__ fronts, const int* __restrict__ big,
+                            const T* __restrict__ fwork, double* __restrict__ m2part) {
+  __shared__ double s_mx[8];
+  const FrontDesc fd = fronts[big[blockIdx.y]];
+  const BfView v = bf_view(fd);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = blockIdx.x * 8 + warp;
+  double s = 0.0;
+  if (c < fd.nc) {
+    const T* col = fwork + v.M + (int64_t)c * fd.nN;
+    for (int i = lane; i < fd.nN; i += 32) s += (double)col[i] * (double)col[i];
+  }
+  s = warp_sum(s);
+  if (lane == 0) s_mx[warp] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double mx = 0.0;
+    for (int w = 0; w < 8; ++w) mx = fmax(mx, s_mx[w]);
+    m2part[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = mx;
+  }
+}
+
+// ---- sketch: Y = Phi M (ell x nc), Phi_{r,i} = gauss01(key_f + r nN + i)
+template <typename T>
+__global__ void __launch_bounds__(TT) k_bf_sketch(const FrontDesc* __restrict__ fronts, const int* __restrict__ big,
+                                                  const int* __restrict__ sketch, T* __restrict__ fwork,
+                                                  uint64_t seed) {
+  __shared__ TileSmem<T> sm;
+  const int f = big[blockIdx.y];
+  const FrontDesc fd = fronts[f];
+  const BfView v = bf_view(fd);
+  const int nc = fd.nc, nN = fd.nN;
+  const int ell = sketch ? sketch[f] : 0;
+  if (ell <= 0 || ell >= nc || ell >= nN) return;
+  const int tcn = (nc + TB - 1) / TB;
+  if ((int)blockIdx.x >= ((ell + TB - 1) / TB) * tcn) return;
+  const int r0 = (blockIdx.x / tcn) * TB, c0 = (blockIdx.x % tcn) * TB;
+  const uint64_t key0 = sketch_key(seed, f);
+  const T* M = fwork + v.M;
+  T* Y = fwork + v.Y;
+  T acc[4][4];
+  zero_acc(acc);
+  tile_mma<T, true>(
+      sm, acc, nN,
+      [&](int r, int k) {
+        return (r0 + r < ell) ? (T)gauss01(key0 + (uint64_t)(r0 + r) * (uint64_t)nN + (uint64_t)k) : T(0);
+      },
+      [&](int k, int c) { return (c0 + c < nc) ? M[(int64_t)(c0 + c) * nN + k] : T(0); });
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = r0 + ty + 16 * i, c = c0 + tx + 16 * j;
+      if (r < ell && c < nc) Y[(int64_t)c * ell + r] = acc[i][j];
+    }
+}
+
+// ---- the ID, one thread block per front.
+// pass 0: fronts with a valid sketch size take the pivoted QR of Y (state 1:
+// residual check pending; state 2 if the sketch saturated, k = ell); the
+// others the pivoted QR of M (state 0).  pass 1: fronts in state 2 take the
+// pivoted QR of M (state 0).  Writes T (k x nR) to the front's factor, and
+// k | perm | ids (pivot order) to its output slot.
+template <typename T>
+__global__ void k_bf_id(const FrontDesc* __restrict__ fronts, const int* __restrict__ big,
+                        const int* __restrict__ sketch, const int* __restrict__ ipool, T* __restrict__ fwork,
+                        T* __restrict__ fac, int* __restrict__ obuf, int* __restrict__ state, double eps,
+                        int* status, int pass) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int f = big[blockIdx.x];
+  const FrontDesc fd = fronts[f];
+  const BfView v = bf_view(fd);
+  const int nc = fd.nc, nN = fd.nN;
+  const int ell = sketch ? sketch[f] : 0;
+  const bool use_sketch = pass == 0 && ell > 0 && ell < nc && ell < nN;
+  if (pass == 1 && state[blockIdx.x] != 2) return;
+  const int m = use_sketch ? ell : nN;
+  double* sq = reinterpret_cast<double*>(smem_raw);            // nc
+  double* vv = sq + nc;                                         // m
+  int* perm = reinterpret_cast<int*>(vv + m);                   // nc
+  int* chosen = perm + nc;                                      // nc
+  T* A = fwork + (use_sketch ? v.Y : v.M);
+  T* Tm = fac + fd.fac + front_fac_T(nc);
+  const int k = blk_pivoted_qr(A, m, nc, eps, status, !use_sketch, sq, vv, perm, chosen);
+  if (use_sketch && k >= ell) {                                 // saturated: fall back
+    if (threadIdx.x == 0) state[blockIdx.x] = 2;
+    return;
+  }
+  blk_id_T(A, m, perm, k, nc, Tm);
+  int* out = obuf + fd.out;
+  const int* idc = ipool + fd.ids;
+  if (threadIdx.x == 0) {
+    out[0] = k;
+    state[blockIdx.x] = use_sketch ? 1 : 0;
+  }
+  for (int t = threadIdx.x; t < nc; t += blockDim.x) {
+    out[1 + t] = perm[t];
+    out[1 + nc + t] = idc[perm[t]];
+  }
+}
+
+// ---- residual of a sketched ID, E = M_r - M_s T: each block takes a strip of
+// 64 columns over all rows and writes the largest squared column norm.
+template <typename T>
+__global__ void __launch_bounds__(TT) k_bf_resid(const FrontDesc* __restrict__ fronts, const int* __restrict__ big,
+                                                 const int* __restrict__ obuf, const int* __restrict__ state,
+                                                 const T* __restrict__ fwork, const T* __restrict__ fac,
+                                                 double* __restrict__ e2part) {
+  __shared__ TileSmem<T> sm;
+  __shared__ double s_col[16][TB];
+  const FrontDesc fd = fronts[big[blockIdx.y]];
+  double* part = e2part + (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+  const int* out = obuf + fd.out;
+  const int k = out[0], nR = fd.nc - k;
+  const int j0 = blockIdx.x * TB;
+  if (state[blockIdx.y] != 1 || j0 >= nR) {
+    if (threadIdx.x == 0) *part = 0.0;
+    return;
+  }
+  const BfView v = bf_view(fd);
+  const int nN = fd.nN;
+  const int* perm = out + 1;
+  const T* M = fwork + v.M;
+  const T* Tm = fac + fd.fac + front_fac_T(fd.nc);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double cs[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int i0 = 0; i0 < nN; i0 += TB) {
+    T acc[4][4];
+    zero_acc(acc);
+    tile_mma<T, false>(
+        sm, acc, k, [&](int r, int t) { return (i0 + r < nN) ? M[(int64_t)perm[t] * nN + i0 + r] : T(0); },
+        [&](int t, int c) { return (j0 + c < nR) ? Tm[(int64_t)t * nR + j0 + c] : T(0); });
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int r = i0 + ty + 16 * i, c = j0 + tx + 16 * j;
+        if (r < nN && c < nR) {
+          const double e = (double)M[(int64_t)perm[k + c] * nN + r] - (double)acc[i][j];
+          cs[j] += e * e;
+        }
+      }
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) s_col[ty][tx + 16 * j] = cs[j];
+  __syncthreads();
+  if (threadIdx.x < TB) {
+    double t = 0.0;
+    for (int y = 0; y < 16; ++y) t += s_col[y][threadIdx.x];
+    s_col[0][threadIdx.x] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double mx = 0.0;
+    for (int c = 0; c < TB; ++c) mx = fmax(mx, s_col[0][c]);
+    *part = mx;
+  }
+}
+
+// ---- accept a sketched ID when the largest residual column norm is at most
+// eps times the largest column norm of M (the pivoted QR's stopping rule
+// |R_{k+1,k+1}| <= eps |R_11| applied to the sketch's skeletons)
+__global__ void k_bf_check(int nbig, int* __restrict__ state, const double* __restrict__ m2part, int nm,
+                           const double* __restrict__ e2part, int ne, double eps, int* status) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nbig || state[b] != 1) return;
+  double m2 = 0.0, e2 = 0.0;
+  for (int i = 0; i < nm; ++i) m2 = fmax(m2, m2part[(int64_t)b * nm + i]);
+  for (int i = 0; i < ne; ++i) e2 = fmax(e2, e2part[(int64_t)b * ne + i]);
+  if (e2 <= eps * eps * m2) {
+    state[b] = 0;
+    atomicAdd(status + 2, 1);
+  } else {
+    state[b] = 2;
+    atomicAdd(status + 3, 1);
+  }
+}
+
+// ---- Lemma 2.4 blocks in the elimination layout.  F_BI (k x nR) = B_sr =
+// A_sr - A_ss T; F_BB (k x k) = A_ss.
+template <typename T>
+__global__ void __launch_bounds__(TT) k_bf_form_sr(const FrontDesc* __restrict__ fronts, const int* __restrict__ big,
+                                                   const int* __restrict__ obuf, T* __restrict__ fwork,
+                                                   const T* __restrict__ fac) {
+  __shared__ TileSmem<T> sm;
+  const FrontDesc fd = fronts[big[blockIdx.y]];
+  const BfView v = bf_view(fd);
+  const int nc = fd.nc;
+  const int* out = obuf + fd.out;
+  const int k = out[0], nR = nc - k;
+  const int* perm = out + 1;
+  if (k == 0 || nR == 0) return;
+  const int tcn = (nR + TB - 1) / TB;
+  if ((int)blockIdx.x >= ((k + TB - 1) / TB) * tcn) return;
+  const int i0 = (blockIdx.x / tcn) * TB, j0 = (blockIdx.x % tcn) * TB;
+  const T* Acc = fwork + v.Acc;
+  const T* Tm = fac + fd.fac + front_fac_T(nc);
+  T* FBI = fwork + v.F + (int64_t)nR * nR;
+  T acc[4][4];
+  zero_acc(acc);
+  tile_mma<T, false>(
+      sm, acc, k,
+      [&](int r, int t) { return (i0 + r < k) ? Acc[(int64_t)perm[i0 + r] * nc + perm[t]] : T(0); },
+      [&](int t, int c) { return (j0 + c < nR) ? Tm[(int64_t)t * nR + j0 + c] : T(0); });
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = i0 + ty + 16 * i, c = j0 + tx + 16 * j;
+      if (r < k && c < nR) FBI[(int64_t)r * nR + c] = Acc[(int64_t)perm[r] * nc + perm[k + c]] - acc[i][j];
+    }
+}
+
+template <typename T>
+__global__ void k_bf_form_ss(const FrontDesc* __restrict__ fronts, const int* __restrict__ big,
+                             const int* __restrict__ obuf, T* __restrict__ fwork) {
+  const FrontDesc fd = fronts[big[blockIdx.y]];
+  const BfView v = bf_view(fd);
+  const int nc = fd.nc;
+  const int* out = obuf + fd.out;
+  const int k = out[0], nR = nc - k;
+  const int* perm = out + 1;
+  if (nR == 0) return;
+  const T* Acc = fwork + v.Acc;
+  T* FBB = fwork + v.F + (int64_t)nR * nR + (int64_t)k * nR;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)k * k;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / k), j = (int)(e % k);
+    FBB[e] = Acc[(int64_t)perm[i] * nc + perm[j]];
+  }
+}
+
+// F_II (nR x nR) = B_rr = A_rr - A_sr^T T - T^T B_sr, lower tiles only (the
+// elimination reads the lower triangle).
+template <typename T>
+__global__ void __launch_bounds__(TT) k_bf_form_rr(const FrontDesc* __restrict__ fronts, const int* __restrict__ big,
+                                                   const int* __restrict__ obuf, T* __restrict__ fwork,
+                                                   const T* __restrict__ fac) {
+  __shared__ TileSmem<T> sm;
+  const FrontDesc fd = fronts[big[blockIdx.y]];
+  const BfView v = bf_view(fd);
+  const int nc = fd.nc;
+  const int* out = obuf + fd.out;
+  const int k = out[0], nR = nc - k;
+  const int* perm = out + 1;
+  const int P = (nR + TB - 1) / TB;
+  const int64_t t = blockIdx.x;
+  if (nR == 0 || t >= (int64_t)P * (P + 1) / 2) return;
+  int a = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+  while ((int64_t)(a + 1) * (a + 2) / 2 <= t) ++a;
+  while ((int64_t)a * (a + 1) / 2 > t) --a;
+  const int b = (int)(t - (int64_t)a * (a + 1) / 2);
+  const int i0 = a * TB, j0 = b * TB;
+  const T* Acc = fwork + v.Acc;
+  const T* Tm = fac + fd.fac + front_fac_T(nc);
+  const T* Bsr = fwork + v.F + (int64_t)nR * nR;
+  T* FII = fwork + v.F;
+  T acc[4][4];
+  zero_acc(acc);
+  if (k > 0) {
+    tile_mma<T, false>(
+        sm, acc, k,
+        [&](int r, int s) { return (i0 + r < nR) ? Acc[(int64_t)perm[s] * nc + perm[k + i0 + r]] : T(0); },
+        [&](int s, int c) { return (j0 + c < nR) ? Tm[(int64_t)s * nR + j0 + c] : T(0); });
+    tile_mma<T, false>(
+        sm, acc, k, [&](int r, int s) { return (i0 + r < nR) ? Tm[(int64_t)s * nR + i0 + r] : T(0); },
+        [&](int s, int c) { return (j0 + c < nR) ? Bsr[(int64_t)s * nR + j0 + c] : T(0); });
+  }
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = i0 + ty + 16 * i, c = j0 + tx + 16 * j;
+      if (r < nR && c < nR)
+        FII[(int64_t)r * nR + c] = Acc[(int64_t)perm[k + r] * nc + perm[k + c]] - acc[i][j];
+    }
+}
+
+// ---- B_ss (F_BB after the elimination) into the first adjacent cell's
+// update matrix, zeros into the second's
+template <typename T>
+__global__ void k_bf_scatter(const FrontDesc* __restrict__ fronts, const int* __restrict__ big,
+                             const CellDesc* __restrict__ cells, const int* __restrict__ ipool,
+                             const int* __restrict__ obuf, const T* __restrict__ fwork, T* __restrict__ cwork) {
+  const FrontDesc fd = fronts[big[blockIdx.y]];
+  const BfView v = bf_view(fd);
+  const int nc = fd.nc, nN = fd.nN;
+  const int* out = obuf + fd.out;
+  const int k = out[0], nR = nc - k;
+  const int* perm = out + 1;
+  if (k == 0 || nR == 0) return;
+  const int* idc = ipool + fd.ids;
+  const int* pos1 = idc + nc;
+  const int* pos2 = pos1 + nc + nN;
+  const CellDesc P1 = cells[fd.P1], P2 = cells[fd.P2];
+  T* U1 = cwork + P1.F + (int64_t)P1.nI * P1.nI + (int64_t)P1.nB * P1.nI;
+  T* U2 = cwork + P2.F + (int64_t)P2.nI * P2.nI + (int64_t)P2.nB * P2.nI;
+  const int ld1 = P1.nB, ld2 = P2.nB;
+  const T* FBB = fwork + v.F + (int64_t)nR * nR + (int64_t)k * nR;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)k * k;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / k), j = (int)(e % k);
+    const int ci = perm[i], cj = perm[j];
+    U1[(int64_t)pos1[ci] * ld1 + pos1[cj]] = FBB[e];
+    U2[(int64_t)pos2[ci] * ld2 + pos2[cj]] = T(0);
+  }
+}
+
+// ---------------------------------------------------------------------------
+static int chunk_blocks(int64_t n, int cap) {
+  const int64_t b = (n + 256 * 8 - 1) / (256 * 8);
+  return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+template <typename T>
+void launch_bigfront_id(const FrontDesc* fronts, const int* big, int nbig, const CellDesc* cells, const int* ipool,
+                        const T* cwork, T* fwork, T* fac, int* obuf, const int* sketch, uint64_t seed, double eps,
+                        int* status, int* state, double* m2part, int nm, double* e2part, int ne, int max_nc,
+                        int max_nN, int max_ell, cudaStream_t st) {
+  if (nbig == 0) return;
+  long long nl = 0;
+  k_bf_assemble<T><<<dim3(chunk_blocks((int64_t)max_nc * (max_nN + max_nc), 2048), nbig), 256, 0, st>>>(
+      fronts, big, cells, ipool, cwork, fwork);
+  ++nl;
+  const bool sk = sketch && max_ell > 0;
+  if (sk) {
+    k_bf_colmax<T><<<dim3(nm, nbig), 256, 0, st>>>(fronts, big, fwork, m2part);
+    ++nl;
+    const int tiles = ((max_ell + TB - 1) / TB) * ((max_nc + TB - 1) / TB);
+    k_bf_sketch<T><<<dim3(tiles, nbig), TT, 0, st>>>(fronts, big, sketch, fwork, seed);
+    ++nl;
+  }
+  const int smem = (int)(sizeof(double) * (max_nc + max_nN) + sizeof(int) * 2 * max_nc + 64);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_bf_id<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  k_bf_id<T><<<nbig, 256, smem, st>>>(fronts, big, sketch, ipool, fwork, fac, obuf, state, eps, status, 0);
+  ++nl;
+  if (sk) {
+    k_bf_resid<T><<<dim3(ne, nbig), TT, 0, st>>>(fronts, big, obuf, state, fwork, fac, e2part);
+    k_bf_check<<<(nbig + 127) / 128, 128, 0, st>>>(nbig, state, m2part, nm, e2part, ne, eps, status);
+    k_bf_id<T><<<nbig, 256, smem, st>>>(fronts, big, sketch, ipool, fwork, fac, obuf, state, eps, status, 1);
+    nl += 3;
+  }
+  note_launches(nl);
+}
+
+template <typename T>
+void launch_bigfront_form(const FrontDesc* fronts, const int* big, int nbig, const int* obuf, T* fwork,
+                          const T* fac, int max_k, int max_nR, cudaStream_t st) {
+  if (nbig == 0) return;
+  long long nl = 0;
+  if (max_k > 0 && max_nR > 0) {
+    const int tiles = ((max_k + TB - 1) / TB) * ((max_nR + TB - 1) / TB);
+    k_bf_form_sr<T><<<dim3(tiles, nbig), TT, 0, st>>>(fronts, big, obuf, fwork, fac);
+    k_bf_form_ss<T><<<dim3(chunk_blocks((int64_t)max_k * max_k, 1024), nbig), 256, 0, st>>>(fronts, big, obuf,
+                                                                                           fwork);
+    nl += 2;
+  }
+  if (max_nR > 0) {
+    const int P = (max_nR + TB - 1) / TB;
+    k_bf_form_rr<T><<<dim3(P * (P + 1) / 2, nbig), TT, 0, st>>>(fronts, big, obuf, fwork, fac);
+    ++nl;
+  }
+  note_launches(nl);
+}
+
+template <typename T>
+void launch_bigfront_scatter(const FrontDesc* fronts, const int* big, int nbig, const CellDesc* cells,
+                             const int* ipool, const int* obuf, const T* fwork, T* cwork, int max_k,
+                             cudaStream_t st) {
+  if (nbig == 0 || max_k == 0) return;
+  note_launches(1);
+  k_bf_scatter<T><<<dim3(chunk_blocks((int64_t)max_k * max_k, 1024), nbig), 256, 0, st>>>(fronts, big, cells, ipool,
+                                                                                        obuf, fwork, cwork);
+}
+
+int bigfront_colmax_blocks(int max_nc) { return (max_nc + 7) / 8; }
+int bigfront_resid_strips(int max_nc) { return (max_nc + TB - 1) / TB; }
+
+#define HIF_BF_INST(T)                                                                                          \
+  template void launch_bigfront_id<T>(const FrontDesc*, const int*, int, const CellDesc*, const int*, const T*, \
+                                      T*, T*, int*, const int*, uint64_t, double, int*, int*, double*, int,     \
+                                      double*, int, int, int, int, cudaStream_t);                                \
+  template void launch_bigfront_form<T>(const FrontDesc*, const int*, int, const int*, T*, const T*, int, int,  \
+                                        cudaStream_t);                                                           \
+  template void launch_bigfront_scatter<T>(const FrontDesc*, const int*, int, const CellDesc*, const int*,      \
+                                           const int*, const T*, T*, int, cudaStream_t);
+HIF_BF_INST(double)
+HIF_BF_INST(float)
+#undef HIF_BF_INST
+
+}  // namespace hif

@@ -6,6 +6,7 @@
 #include "hif_internal.h"
 #include "blockops.cuh"
 #include "kernels.h"
+#include "front_common.cuh"
 
 namespace hif {
 
@@ -200,138 +201,13 @@ __global__ void k_cell_factor(const CellDesc* __restrict__ cells, const int* __r
 // redundant DOFs.
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ __forceinline__ T front_entry(const T* U1, int ld1, const T* U2, int ld2,
-                                         const int* pos1, const int* pos2, int x, int y) {
-  T v = T(0);
-  const int a1 = pos1[x], b1 = pos1[y];
-  if (a1 >= 0 && b1 >= 0) v += U1[(int64_t)a1 * ld1 + b1];
-  const int a2 = pos2[x], b2 = pos2[y];
-  if (a2 >= 0 && b2 >= 0) v += U2[(int64_t)a2 * ld2 + b2];
-  return v;
-}
-
-// Column-pivoted Householder QR of A (m x nc, column-major, ld m), in place,
-// with residual norms recomputed every step (FP64 accumulation), the pivot
-// tie rule (smallest position within a factor 1 - 1e-10 of the largest
-// squared norm) and the rank rule (stop when |R_ii| <= eps |R_11|).
-// perm[0..k) = skeleton columns in pivot order, perm[k..nc) = the others in
-// ascending order.  Returns k.  flag_near marks pivot ratios within 1e-8 of
-// eps in bit 1 of *status.
-template <typename T>
-__device__ int blk_pivoted_qr(T* A, int m, int nc, double eps, int* status, bool flag_near, double* sq,
-                              double* v, int* perm, int* chosen) {
-  __shared__ double s_mx, s_vv, s_alpha;
-  __shared__ int s_piv, s_stop, s_k;
-  for (int j = threadIdx.x; j < nc; j += blockDim.x) chosen[j] = 0;
-  if (threadIdx.x == 0) { s_k = 0; s_stop = 0; }
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-  const int kmax = m < nc ? m : nc;
-  for (int i = 0; i < kmax; ++i) {
-    for (int j = warp; j < nc; j += nwarps) {
-      if (chosen[j]) continue;
-      const T* col = A + (int64_t)j * m;
-      double acc = 0.0;
-      for (int r = i + lane; r < m; r += 32) { const double x = (double)col[r]; acc += x * x; }
-      acc = warp_sum(acc);
-      if (lane == 0) sq[j] = acc;
-    }
-    __syncthreads();
-    if (warp == 0) {
-      double mx = -1.0;
-      for (int j = lane; j < nc; j += 32) if (!chosen[j] && sq[j] > mx) mx = sq[j];
-      for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      int piv = 0x7fffffff;
-      for (int j = lane; j < nc; j += 32)
-        if (!chosen[j] && sq[j] >= (1.0 - 1e-10) * mx) { piv = j; break; }
-      for (int o = 16; o > 0; o >>= 1) piv = min(piv, __shfl_xor_sync(0xffffffffu, piv, o));
-      if (lane == 0) {
-        if (i == 0) s_mx = mx;  // |R_11|^2
-        const double nu = (i == 0) ? mx : s_mx;
-        const double ratio = (nu > 0.0) ? sqrt(mx / nu) : 0.0;
-        if (flag_near && fabs(ratio - eps) <= 1e-8 * eps) atomicOr(status, 2);
-        const int stop = (mx <= 0.0) || (i > 0 && mx <= eps * eps * nu);
-        s_stop = stop;
-        if (!stop) {
-          s_piv = piv;
-          const double x0 = (double)A[(int64_t)piv * m + i];
-          const double sp = sq[piv];      // the pivot's own squared norm builds the reflector
-          const double a2 = (x0 >= 0.0) ? -sqrt(sp) : sqrt(sp);
-          s_alpha = a2;
-          s_vv = sp - x0 * x0 + (x0 - a2) * (x0 - a2);
-          perm[s_k] = piv;
-          chosen[piv] = 1;
-          s_k = s_k + 1;
-        }
-      }
-    }
-    __syncthreads();
-    if (s_stop) break;
-    const int piv = s_piv;
-    const double alpha = s_alpha, vv = s_vv;
-    T* pc = A + (int64_t)piv * m;
-    for (int r = i + threadIdx.x; r < m; r += blockDim.x) v[r] = (double)pc[r] - (r == i ? alpha : 0.0);
-    __syncthreads();
-    if (vv > 0.0) {
-      for (int j = warp; j < nc; j += nwarps) {
-        if (chosen[j]) continue;
-        T* col = A + (int64_t)j * m;
-        double s = 0.0;
-        for (int r = i + lane; r < m; r += 32) s += v[r] * (double)col[r];
-        s = warp_sum(s);
-        const double f = 2.0 * s / vv;
-        for (int r = i + lane; r < m; r += 32) col[r] = (T)((double)col[r] - f * v[r]);
-      }
-    }
-    for (int r = i + threadIdx.x; r < m; r += blockDim.x) pc[r] = (r == i) ? (T)alpha : T(0);
-    __syncthreads();
-  }
-  const int k = s_k;
-  if (threadIdx.x == 0) {
-    int t = k;
-    for (int j = 0; j < nc; ++j) if (!chosen[j]) perm[t++] = j;
-  }
-  __syncthreads();
-  return k;
-}
-
-// T = R11^{-1} R12 from the factored A of blk_pivoted_qr (back substitution,
-// one thread per redundant column); T is k x (nc - k), row-major.
-template <typename T>
-__device__ void blk_id_T(const T* A, int m, const int* perm, int k, int nc, T* Tm) {
-  const int nR = nc - k;
-  for (int c = threadIdx.x; c < nR; c += blockDim.x) {
-    const T* r12 = A + (int64_t)perm[k + c] * m;
-    for (int t = k - 1; t >= 0; --t) {
-      T s = r12[t];
-      for (int u = t + 1; u < k; ++u) s -= A[(int64_t)perm[u] * m + t] * Tm[(int64_t)u * nR + c];
-      Tm[(int64_t)t * nR + c] = s / A[(int64_t)perm[t] * m + t];
-    }
-  }
-  __syncthreads();
-}
-
-// Standard normal from two splitmix64 outputs of a counter (Box-Muller).
-__device__ __forceinline__ uint64_t smix64(uint64_t z) {
-  z += 0x9E3779B97F4A7C15ull;
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
-}
-__device__ __forceinline__ float gauss01(uint64_t key) {
-  const uint64_t a = smix64(key * 2), b = smix64(key * 2 + 1);
-  const float u1 = ((float)(a >> 40) + 0.5f) * (1.0f / 16777216.0f);
-  const float u2 = (float)(b >> 40) * (1.0f / 16777216.0f);
-  return sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
-}
-
-template <typename T>
 __global__ void k_front(const FrontDesc* __restrict__ fronts, const CellDesc* __restrict__ cells,
                         const int* __restrict__ ipool, int* __restrict__ obuf, T* __restrict__ fwork,
                         T* __restrict__ fac, T* __restrict__ cwork, double eps, int* status, T tau,
-                        const int* __restrict__ sketch, uint64_t seed) {
+                        const int* __restrict__ sketch, uint64_t seed, const int* __restrict__ sel) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const FrontDesc fd = fronts[blockIdx.x];
+  const int fi = sel ? sel[blockIdx.x] : (int)blockIdx.x;
+  const FrontDesc fd = fronts[fi];
   const int nc = fd.nc, nN = fd.nN;
   const int* idc = ipool + fd.ids;
   const int* pos1 = idc + nc;
@@ -372,12 +248,13 @@ __global__ void k_front(const FrontDesc* __restrict__ fronts, const CellDesc* __
   T* Lp = fac + fd.fac + front_fac_L(nc);  // packed nR x nR
 
   // ---- ID: from a Gaussian sketch Y = Phi A_{N,c} (Section 4.3) when a
-  // sketch size is given, accepted only if ||A_r - A_s T||_F <= eps ||A||_F;
+  // sketch size is given, accepted only if every column of A_r - A_s T has
+  // norm <= eps max_j ||A_j||;
   // otherwise (or without a sketch) the pivoted QR of A_{N,c} itself.
-  const int ell = sketch ? sketch[blockIdx.x] : 0;
+  const int ell = sketch ? sketch[fi] : 0;
   int k = -1;
   if (ell > 0 && ell < nc && ell < nN) {
-    const uint64_t key0 = smix64(seed ^ ((uint64_t)blockIdx.x << 32)) ;
+    const uint64_t key0 = sketch_key(seed, fi);
     for (int64_t e = threadIdx.x; e < (int64_t)ell * nN; e += blockDim.x) PH[e] = (T)gauss01(key0 + (uint64_t)e);
     __syncthreads();
     T* Y = S3;                             // ell x nc, column-major (ld ell)
@@ -394,23 +271,36 @@ __global__ void k_front(const FrontDesc* __restrict__ fronts, const CellDesc* __
     bool ok = false;
     if (ks < ell) {
       blk_id_T(Y, ell, perm, ks, nc, Tm);
+      // accept when every residual column |M_r - M_s T|_j <= eps max_j |M_j|
+      // (the pivoted QR's stopping rule for the sketch's skeletons)
       const int nRs = nc - ks;
       double e2 = 0.0, m2 = 0.0;
-      for (int64_t e = threadIdx.x; e < (int64_t)nN * nRs; e += blockDim.x) {
-        const int c = (int)(e / nN), i = (int)(e % nN);
-        double r = (double)M[(int64_t)perm[ks + c] * nN + i];
-        for (int t = 0; t < ks; ++t) r -= (double)M[(int64_t)perm[t] * nN + i] * (double)Tm[(int64_t)t * nRs + c];
-        e2 += r * r;
+      for (int c = threadIdx.x; c < nRs; c += blockDim.x) {
+        const T* mr = M + (int64_t)perm[ks + c] * nN;
+        double cs = 0.0;
+        for (int i = 0; i < nN; ++i) {
+          double r = (double)mr[i];
+          for (int t = 0; t < ks; ++t) r -= (double)M[(int64_t)perm[t] * nN + i] * (double)Tm[(int64_t)t * nRs + c];
+          cs += r * r;
+        }
+        e2 = fmax(e2, cs);
       }
-      for (int64_t e = threadIdx.x; e < (int64_t)nN * nc; e += blockDim.x) m2 += (double)M[e] * (double)M[e];
-      e2 = warp_sum(e2);
-      m2 = warp_sum(m2);
+      for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+        const T* mc = M + (int64_t)c * nN;
+        double cs = 0.0;
+        for (int i = 0; i < nN; ++i) cs += (double)mc[i] * (double)mc[i];
+        m2 = fmax(m2, cs);
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        e2 = fmax(e2, __shfl_xor_sync(0xffffffffu, e2, o));
+        m2 = fmax(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+      }
       const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
       if (lane == 0) { s_e2[warp] = e2; s_m2[warp] = m2; }
       __syncthreads();
       if (threadIdx.x == 0) {
         double a = 0.0, b = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += s_e2[w]; b += s_m2[w]; }
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a = fmax(a, s_e2[w]); b = fmax(b, s_m2[w]); }
         s_e2[0] = a;
         s_m2[0] = b;
       }
@@ -531,13 +421,14 @@ template <typename T>
 void launch_front(const FrontDesc* fronts, int nfronts, const CellDesc* cells, const int* ipool, int* obuf,
                   T* fwork,
                   T* fac, T* cwork, double eps, int* status, int max_nc, int max_nN, double tau,
-                  const int* sketch, uint64_t seed, cudaStream_t st) {
+                  const int* sketch, uint64_t seed, const int* sel, cudaStream_t st) {
+  if (nfronts == 0) return;
   const int smem = (int)(sizeof(double) * (max_nc + max_nN) + sizeof(int) * 2 * max_nc + 64);
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(k_front<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   note_launches(1);
   k_front<T><<<nfronts, 256, smem, st>>>(fronts, cells, ipool, obuf, fwork, fac, cwork, eps, status, (T)tau,
-                                         sketch, seed);
+                                         sketch, seed, sel);
 }
 
 template void launch_leaf_assemble<double>(const CellDesc*, int, const int*, double*, GridInfo,
@@ -555,9 +446,11 @@ template void launch_cell_factor<double>(const CellDesc*, const int*, int, doubl
 template void launch_cell_factor<float>(const CellDesc*, const int*, int, float*, float*, int*, int, double,
                                         cudaStream_t);
 template void launch_front<double>(const FrontDesc*, int, const CellDesc*, const int*, int*, double*, double*,
-                                   double*, double, int*, int, int, double, const int*, uint64_t, cudaStream_t);
+                                   double*, double, int*, int, int, double, const int*, uint64_t, const int*,
+                                   cudaStream_t);
 template void launch_front<float>(const FrontDesc*, int, const CellDesc*, const int*, int*, float*, float*,
-                                  float*, double, int*, int, int, double, const int*, uint64_t, cudaStream_t);
+                                  float*, double, int*, int, int, double, const int*, uint64_t, const int*,
+                                  cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // Features of each front for the rank predictor: level, log2 |c|, log2 |N|,

@@ -14,100 +14,42 @@
 //
 // Results are those of k_cell_factor up to rounding order: the same L, Linv,
 // G and Schur complement.  Scratch (the D_p tiles and the original diagonal
-// for the pivot safeguard) lives in the cell's X region of the work pool.
+// for the pivot safeguard) lives in the problem's X region of the work pool.
+// Each problem is described by a TDesc (a large cell, or the redundant block
+// of a large front).
 #include "hif_internal.h"
 #include "blockops.cuh"
 #include "kernels.h"
+#include "tile_mma.cuh"
 
 namespace hif {
 
-constexpr int TB = kTile;   // tile edge
-constexpr int TK = 32;      // k-chunk staged in shared memory
-constexpr int TT = 256;     // threads per block (16 x 16, 4 x 4 outputs each)
 
 struct TCell {
   int nI, nB, P, RB;
   int64_t FII, FBI, FBB, X, Linv, G, Lp;
 };
 
-template <typename T>
-__device__ __forceinline__ TCell tcell(const CellDesc& cd) {
+__device__ __forceinline__ TCell tcell(const TDesc& d) {
   TCell c;
-  c.nI = cd.nI;
-  c.nB = cd.nB;
-  c.P = (cd.nI + TB - 1) / TB;
-  c.RB = (cd.nB + TB - 1) / TB;
-  c.FII = cd.F;
-  c.FBI = c.FII + (int64_t)cd.nI * cd.nI;
-  c.FBB = c.FBI + (int64_t)cd.nB * cd.nI;
-  c.X = c.FBB + (int64_t)cd.nB * cd.nB;
-  c.Linv = cd.fac;
-  c.G = cd.fac + cell_fac_G(cd.nI);
-  c.Lp = cd.fac + cell_fac_L(cd.nI, cd.nB);
+  c.nI = d.nI;
+  c.nB = d.nB;
+  c.P = (d.nI + TB - 1) / TB;
+  c.RB = (d.nB + TB - 1) / TB;
+  c.FII = d.FII;
+  c.FBI = d.FBI;
+  c.FBB = d.FBB;
+  c.X = d.X;
+  c.Linv = d.Linv;
+  c.G = d.G;
+  c.Lp = d.Lp;
   return c;
-}
-
-__device__ __forceinline__ int64_t tri(int64_t r) { return r * (r + 1) / 2; }
-
-// acc[i][j] += sum_{k < K} fa(ty + 16 i, k) * fb(k, tx + 16 j).
-// fa(r, k) / fb(k, c) return 0 outside their operands.  BKC: the right
-// operand is stored with k contiguous (load it k-fastest for coalescing).
-template <typename T>
-struct TileSmem {
-  T a[TB][TK + 1];
-  T b[TK][TB + 1];
-};
-
-template <typename T, bool BKC, typename FA, typename FB>
-__device__ __forceinline__ void tile_mma(TileSmem<T>& sm, T (&acc)[4][4], int K, FA fa, FB fb) {
-  T (*sA)[TK + 1] = sm.a;
-  T (*sB)[TB + 1] = sm.b;
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  for (int k0 = 0; k0 < K; k0 += TK) {
-    for (int e = threadIdx.x; e < TB * TK; e += TT) {
-      const int r = e / TK, kk = e % TK;
-      sA[r][kk] = (k0 + kk < K) ? fa(r, k0 + kk) : T(0);
-    }
-    if (BKC) {
-      for (int e = threadIdx.x; e < TB * TK; e += TT) {
-        const int c = e / TK, kk = e % TK;
-        sB[kk][c] = (k0 + kk < K) ? fb(k0 + kk, c) : T(0);
-      }
-    } else {
-      for (int e = threadIdx.x; e < TK * TB; e += TT) {
-        const int kk = e / TB, c = e % TB;
-        sB[kk][c] = (k0 + kk < K) ? fb(k0 + kk, c) : T(0);
-      }
-    }
-    __syncthreads();
-#pragma unroll 8
-    for (int kk = 0; kk < TK; ++kk) {
-      T a[4], b[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = sA[ty + 16 * i][kk];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = sB[kk][tx + 16 * j];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
-    }
-    __syncthreads();
-  }
-}
-
-template <typename T>
-__device__ __forceinline__ void zero_acc(T (&acc)[4][4]) {
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
 }
 
 // original diagonal of F_II (pivot safeguard of the mixed mode)
 template <typename T>
-__global__ void k_tl_init(const CellDesc* __restrict__ cells, const int* __restrict__ sel, T* __restrict__ work) {
-  const TCell c = tcell<T>(cells[sel[blockIdx.y]]);
+__global__ void k_tl_init(const TDesc* __restrict__ td, T* __restrict__ work) {
+  const TCell c = tcell(td[blockIdx.y]);
   T* d0 = work + c.X + (int64_t)c.P * TB * TB;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < c.nI; i += gridDim.x * blockDim.x)
     d0[i] = work[c.FII + (int64_t)i * c.nI + i];
@@ -116,12 +58,12 @@ __global__ void k_tl_init(const CellDesc* __restrict__ cells, const int* __restr
 // Panel p: Cholesky of the diagonal tile and its inverse D_p (written to the
 // scratch tile, zero-padded to 64 x 64, and to Linv's diagonal tile).
 template <typename T>
-__global__ void k_tl_potrf(const CellDesc* __restrict__ cells, const int* __restrict__ sel, int p,
+__global__ void k_tl_potrf(const TDesc* __restrict__ td, int p,
                            T* __restrict__ work, T* __restrict__ fac, int* status, T tau) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* A = reinterpret_cast<T*>(smem_raw);   // TB x TB
   T* X = A + TB * TB;                      // TB x TB
-  const TCell c = tcell<T>(cells[sel[blockIdx.x]]);
+  const TCell c = tcell(td[blockIdx.x]);
   if (p >= c.P) return;
   const int o = p * TB, w = min(TB, c.nI - o);
   T* FII = work + c.FII;
@@ -141,17 +83,17 @@ __global__ void k_tl_potrf(const CellDesc* __restrict__ cells, const int* __rest
     D[e] = in ? X[r * TB + q] : T(0);
     if (in && q <= r) {
       FII[(int64_t)(o + r) * c.nI + o + q] = A[r * TB + q];
-      Linv[tri(o + r) + o + q] = X[r * TB + q];
+      Linv[tri64(o + r) + o + q] = X[r * TB + q];
     }
   }
 }
 
 // Panel p: row tiles below the diagonal (F_II rows, then F_BI rows) times D_p^T.
 template <typename T>
-__global__ void __launch_bounds__(TT) k_tl_trsm(const CellDesc* __restrict__ cells, const int* __restrict__ sel,
+__global__ void __launch_bounds__(TT) k_tl_trsm(const TDesc* __restrict__ td,
                                                 int p, T* __restrict__ work) {
   __shared__ TileSmem<T> sm;
-  const TCell c = tcell<T>(cells[sel[blockIdx.y]]);
+  const TCell c = tcell(td[blockIdx.y]);
   if (p >= c.P) return;
   const int below = c.P - p - 1;
   const int t = blockIdx.x;
@@ -188,10 +130,10 @@ __global__ void __launch_bounds__(TT) k_tl_trsm(const CellDesc* __restrict__ cel
 // Panel p: trailing update of column tiles j > p: lower tiles of F_II, then
 // all row tiles of F_BI.
 template <typename T>
-__global__ void __launch_bounds__(TT) k_tl_update(const CellDesc* __restrict__ cells, const int* __restrict__ sel,
+__global__ void __launch_bounds__(TT) k_tl_update(const TDesc* __restrict__ td,
                                                   int p, T* __restrict__ work) {
   __shared__ TileSmem<T> sm;
-  const TCell c = tcell<T>(cells[sel[blockIdx.y]]);
+  const TCell c = tcell(td[blockIdx.y]);
   if (p >= c.P) return;
   const int m = c.P - p - 1;
   const int64_t nlow = (int64_t)m * (m + 1) / 2;
@@ -241,10 +183,10 @@ __global__ void __launch_bounds__(TT) k_tl_update(const CellDesc* __restrict__ c
 // U = F_BB - G G^T (G = F_BI after the panels), tile (i, j >= ... ) with
 // i >= j, mirrored into (j, i).
 template <typename T>
-__global__ void __launch_bounds__(TT) k_tl_syrk(const CellDesc* __restrict__ cells, const int* __restrict__ sel,
+__global__ void __launch_bounds__(TT) k_tl_syrk(const TDesc* __restrict__ td,
                                                 T* __restrict__ work) {
   __shared__ TileSmem<T> sm;
-  const TCell c = tcell<T>(cells[sel[blockIdx.y]]);
+  const TCell c = tcell(td[blockIdx.y]);
   const int64_t t = blockIdx.x;
   if (t >= (int64_t)c.RB * (c.RB + 1) / 2) return;
   int a = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
@@ -278,10 +220,10 @@ __global__ void __launch_bounds__(TT) k_tl_syrk(const CellDesc* __restrict__ cel
 
 // Row block i of Linv: tiles (i, j), j < i.
 template <typename T>
-__global__ void __launch_bounds__(TT) k_tl_linv(const CellDesc* __restrict__ cells, const int* __restrict__ sel,
+__global__ void __launch_bounds__(TT) k_tl_linv(const TDesc* __restrict__ td,
                                                 int i, const T* __restrict__ work, T* __restrict__ fac) {
   __shared__ TileSmem<T> sm;
-  const TCell c = tcell<T>(cells[sel[blockIdx.y]]);
+  const TCell c = tcell(td[blockIdx.y]);
   const int j = blockIdx.x;
   if (i >= c.P || j >= i) return;
   const int ld = c.nI;
@@ -296,7 +238,7 @@ __global__ void __launch_bounds__(TT) k_tl_linv(const CellDesc* __restrict__ cel
       sm, acc, r0 - c0, [&](int r, int k) { return r < rows ? Lr[(int64_t)r * ld + c0 + k] : T(0); },
       [&](int k, int q) {
         const int64_t R = c0 + k, Q = c0 + q;
-        return Q <= R ? Linv[tri(R) + Q] : T(0);
+        return Q <= R ? Linv[tri64(R) + Q] : T(0);
       });
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll
@@ -304,7 +246,7 @@ __global__ void __launch_bounds__(TT) k_tl_linv(const CellDesc* __restrict__ cel
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       const int r = ty + 16 * a, q = tx + 16 * b;
-      if (r < rows) Linv[tri(r0 + r) + c0 + q] = acc[a][b];
+      if (r < rows) Linv[tri64(r0 + r) + c0 + q] = acc[a][b];
     }
   __syncthreads();
   const T* D = work + c.X + (int64_t)i * TB * TB;
@@ -312,26 +254,26 @@ __global__ void __launch_bounds__(TT) k_tl_linv(const CellDesc* __restrict__ cel
   zero_acc(acc2);
   tile_mma<T, false>(
       sm, acc2, rows, [&](int r, int k) { return D[r * TB + k]; },
-      [&](int k, int q) { return Linv[tri(r0 + k) + c0 + q]; });
+      [&](int k, int q) { return Linv[tri64(r0 + k) + c0 + q]; });
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
       const int r = ty + 16 * a, q = tx + 16 * b;
-      if (r < rows) Linv[tri(r0 + r) + c0 + q] = -acc2[a][b];
+      if (r < rows) Linv[tri64(r0 + r) + c0 + q] = -acc2[a][b];
     }
 }
 
 // L (lower F_II, packed by rows) and G (= F_BI) into the factor.
 template <typename T>
-__global__ void k_tl_pack(const CellDesc* __restrict__ cells, const int* __restrict__ sel,
+__global__ void k_tl_pack(const TDesc* __restrict__ td,
                           const T* __restrict__ work, T* __restrict__ fac) {
-  const TCell c = tcell<T>(cells[sel[blockIdx.y]]);
+  const TCell c = tcell(td[blockIdx.y]);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int r = blockIdx.x * (blockDim.x >> 5) + warp; r < c.nI + c.nB; r += gridDim.x * (blockDim.x >> 5)) {
     if (r < c.nI) {
       const T* src = work + c.FII + (int64_t)r * c.nI;
-      T* dst = fac + c.Lp + tri(r);
+      T* dst = fac + c.Lp + tri64(r);
       for (int q = lane; q <= r; q += 32) dst[q] = src[q];
     } else {
       const T* src = work + c.FBI + (int64_t)(r - c.nI) * c.nI;
@@ -342,8 +284,8 @@ __global__ void k_tl_pack(const CellDesc* __restrict__ cells, const int* __restr
 }
 
 template <typename T>
-void launch_cell_factor_tiled(const CellDesc* cells, const int* sel, int nsel, int max_nI, int max_nB, T* work,
-                              T* fac, int* status, double tau, cudaStream_t st) {
+void launch_tiled_elim(const TDesc* td, int nsel, int max_nI, int max_nB, T* work, T* fac, int* status,
+                       double tau, cudaStream_t st) {
   if (nsel == 0 || max_nI == 0) return;
   const int P = (max_nI + TB - 1) / TB, RB = (max_nB + TB - 1) / TB;
   const int psmem = 2 * TB * TB * (int)sizeof(T);
@@ -355,34 +297,32 @@ void launch_cell_factor_tiled(const CellDesc* cells, const int* sel, int nsel, i
   }
   long long nl = 0;
   if (tau > 0.0) {
-    k_tl_init<T><<<dim3((max_nI + 255) / 256, nsel), 256, 0, st>>>(cells, sel, work);
+    k_tl_init<T><<<dim3((max_nI + 255) / 256, nsel), 256, 0, st>>>(td, work);
     ++nl;
   }
   for (int p = 0; p < P; ++p) {
-    k_tl_potrf<T><<<nsel, TT, psmem, st>>>(cells, sel, p, work, fac, status, (T)tau);
+    k_tl_potrf<T><<<nsel, TT, psmem, st>>>(td, p, work, fac, status, (T)tau);
     const int below = P - p - 1;
-    if (below + RB > 0) k_tl_trsm<T><<<dim3(below + RB, nsel), TT, 0, st>>>(cells, sel, p, work);
+    if (below + RB > 0) k_tl_trsm<T><<<dim3(below + RB, nsel), TT, 0, st>>>(td, p, work);
     const int64_t nup = (int64_t)below * (below + 1) / 2 + (int64_t)RB * below;
-    if (nup > 0) k_tl_update<T><<<dim3((unsigned)nup, nsel), TT, 0, st>>>(cells, sel, p, work);
+    if (nup > 0) k_tl_update<T><<<dim3((unsigned)nup, nsel), TT, 0, st>>>(td, p, work);
     nl += 1 + (below + RB > 0) + (nup > 0);
   }
   if (RB > 0) {
-    k_tl_syrk<T><<<dim3((unsigned)((int64_t)RB * (RB + 1) / 2), nsel), TT, 0, st>>>(cells, sel, work);
+    k_tl_syrk<T><<<dim3((unsigned)((int64_t)RB * (RB + 1) / 2), nsel), TT, 0, st>>>(td, work);
     ++nl;
   }
   for (int i = 1; i < P; ++i) {
-    k_tl_linv<T><<<dim3(i, nsel), TT, 0, st>>>(cells, sel, i, work, fac);
+    k_tl_linv<T><<<dim3(i, nsel), TT, 0, st>>>(td, i, work, fac);
     ++nl;
   }
   const int rows = max_nI + max_nB;
-  k_tl_pack<T><<<dim3((rows + 7) / 8 < 4096 ? (rows + 7) / 8 : 4096, nsel), 256, 0, st>>>(cells, sel, work, fac);
+  k_tl_pack<T><<<dim3((rows + 7) / 8 < 4096 ? (rows + 7) / 8 : 4096, nsel), 256, 0, st>>>(td, work, fac);
   ++nl;
   note_launches(nl);
 }
 
-template void launch_cell_factor_tiled<double>(const CellDesc*, const int*, int, int, int, double*, double*, int*,
-                                               double, cudaStream_t);
-template void launch_cell_factor_tiled<float>(const CellDesc*, const int*, int, int, int, float*, float*, int*,
-                                              double, cudaStream_t);
+template void launch_tiled_elim<double>(const TDesc*, int, int, int, double*, double*, int*, double, cudaStream_t);
+template void launch_tiled_elim<float>(const TDesc*, int, int, int, float*, float*, int*, double, cudaStream_t);
 
 }  // namespace hif

@@ -131,6 +131,59 @@ def test_tiled_elimination_matches_oracle(hiflib, dim, n, field, eps):
     assert np.linalg.norm(yf - of) <= 1e-10 * np.linalg.norm(of)
 
 
+@pytest.mark.parametrize("eps", [1e-3, 1e-6])
+def test_large_front_path_matches_oracle(hiflib, eps):
+    """3D 31^3 Laplacian (two levels; the level-1 faces hold 128+ DOFs) with
+    every cell of 128+ interior DOFs through the tiled elimination and every
+    front of 128+ DOFs through the multi-block skeletonization: skeletons,
+    ranks and |s_L| identical to the oracle's, F^-1 x and F x to 1e-10."""
+    from paper_1307_2895_gb300 import hif
+    dim, n = 3, 32
+    a, b, A, F = _oracle(dim, n, "lap", eps)
+    x = inputs.rhs(dim, n, 2, seed=5)
+    G = hif.factor(dim, n, a, b, eps, precision="fp64", big_cell=128)
+    try:
+        fronts, root = G.structure()
+        yi = G.apply(x, inverse=True)
+        yf = G.apply(x, inverse=False)
+        st = G.stats()
+    finally:
+        G.free()
+    assert st["max_front_rank"] > 0
+    ostruct, oroot = F.skeleton_structure()
+    assert root == oroot
+    got = {(lev, tuple(c)): sk for lev, c, sk in fronts}
+    nbig = 0
+    for lev, d in enumerate(ostruct):
+        for key, (c, sk, k) in d.items():
+            nbig += len(c) >= 128
+            assert got.get((lev, tuple(c))) == sk, f"level {lev} front {c[:4]}...: skeletons differ"
+    assert nbig > 0
+    oi, of = F.apply_inverse(x), F.apply(x)
+    assert np.linalg.norm(yi - oi) <= 1e-10 * np.linalg.norm(oi)
+    assert np.linalg.norm(yf - of) <= 1e-10 * np.linalg.norm(of)
+
+
+@pytest.mark.parametrize("mode", ["rand", "rand_os40"])
+def test_large_front_sketch_keeps_solver_target(hiflib, mode):
+    """The multi-block randomized ID (tiled Gaussian sketch, tiled residual
+    check, fallback) on 3D 31^3 contrast 1e4: PCG still reaches 1e-12."""
+    from paper_1307_2895_gb300 import hif
+    dim, n, eps = 3, 32, 1e-6
+    a, b = _fields(dim, n, "contrast")
+    f = inputs.rhs(dim, n, 2)
+    kw = {"id_mode": "rand", "oversample": 10 if mode == "rand" else 40}
+    G = hif.factor(dim, n, a, b, eps, precision="fp64", big_cell=128, seed=3, **kw)
+    try:
+        st = G.stats()
+        xh, xl, info = G.solve(f, tol=1e-12, maxit=100, want_lo=True)
+    finally:
+        G.free()
+    assert st["sketched_fronts"] + st["fallback_fronts"] > 0
+    assert info["converged"] and info["relres_max"] <= 1e-12
+    assert stencil.residual_ext(dim, n, a, b, f, xh, xl).max() <= 2e-12
+
+
 @pytest.mark.parametrize("dim,n,field", [(2, 27, "contrast"), (3, 12, "contrast"), (3, 8, "lap")])
 def test_tiled_mf_matches_dense_lu(hiflib, dim, n, field):
     """MF through the tiled elimination, ragged tiles (|I| not a multiple of 64)."""

@@ -47,6 +47,25 @@ def test_randomized_id_exact_low_rank():
     assert np.linalg.norm(E) <= 1e-10 * np.linalg.norm(M)
 
 
+def test_randomized_id_check_is_the_qr_stopping_rule():
+    """On a matrix whose pivoted QR stops at rank k (|R_kk| > eps |R_11| >=
+    |R_{k+1,k+1}|), a sketch that finds the same skeletons passes the column
+    check, while the Frobenius test ||E||_F <= eps ||M||_F, stricter by up
+    to sqrt(#columns), rejects it."""
+    rng = np.random.default_rng(7)
+    m, n, k, eps = 200, 60, 10, 1e-6
+    U, _ = np.linalg.qr(rng.standard_normal((m, n)))
+    V, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    s = np.concatenate([np.logspace(0, -3, k), np.full(n - k, 0.1 * eps)])
+    M = (U * s) @ V.T
+    Phi = inputs.standard_normal(8, (k + 30) * m).reshape(k + 30, m)
+    idr, ok = learned.randomized_id(M, eps, Phi)
+    E = M[:, idr.rd] - M[:, idr.sk] @ idr.T
+    assert ok and len(idr.sk) == k
+    assert np.linalg.norm(E, axis=0).max() <= eps * np.linalg.norm(M, axis=0).max()
+    assert np.linalg.norm(E) > eps * np.linalg.norm(M)
+
+
 def test_randomized_id_undersized_sketch_is_rejected():
     rng = np.random.default_rng(2)
     m, n = 50, 20
