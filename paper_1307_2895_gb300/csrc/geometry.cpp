@@ -57,36 +57,72 @@ static inline int lin_index(const int iv[3], int dim, int nc) {
   return lin;
 }
 
+// Cells touched by the alive DOF g at level l: interior DOFs belong to one
+// cell (I), separator DOFs to the 2^(#separator coordinates) adjacent cells (B).
+struct CellSpan {
+  int lo[3], hi[3];
+  bool interior;
+};
+
+static inline CellSpan cell_span(const Geometry& G, const std::vector<int>& cl, int g) {
+  int x[3];
+  G.coords(g, x);
+  CellSpan s;
+  s.interior = true;
+  for (int a = 0; a < 3; ++a) {
+    if (a >= G.dim) { s.lo[a] = s.hi[a] = 0; continue; }
+    const int c = cl[x[a]];
+    if (c >= 0) { s.lo[a] = s.hi[a] = c; }
+    else { s.lo[a] = -c - 1; s.hi[a] = -c; s.interior = false; }
+  }
+  return s;
+}
+
 void build_cells(const Geometry& G, int l, const std::vector<int>& alive, std::vector<HostCell>& cells) {
   const int nc = G.ncell[l];
   const int ncells = G.ncells(l);
-  cells.assign(ncells, HostCell{});
+  cells.resize(ncells);
   const std::vector<int>& cl = G.cls[l];
+  // count, size every list once, then fill (alive is ascending, so are I and B)
+  std::vector<int> nI(ncells, 0), nB(ncells, 0);
   for (int g : alive) {
-    int x[3];
-    G.coords(g, x);
-    int lo[3], hi[3];
-    bool interior = true;
-    for (int a = 0; a < 3; ++a) {
-      if (a >= G.dim) { lo[a] = hi[a] = 0; continue; }
-      const int c = cl[x[a]];
-      if (c >= 0) { lo[a] = hi[a] = c; }
-      else { lo[a] = -c - 1; hi[a] = -c; interior = false; }
-    }
-    if (interior) {
-      cells[lin_index(lo, G.dim, nc)].I.push_back(g);
+    const CellSpan sp = cell_span(G, cl, g);
+    if (sp.interior) { ++nI[lin_index(sp.lo, G.dim, nc)]; continue; }
+    int iv[3];
+    for (iv[2] = sp.lo[2]; iv[2] <= sp.hi[2]; ++iv[2])
+      for (iv[1] = sp.lo[1]; iv[1] <= sp.hi[1]; ++iv[1])
+        for (iv[0] = sp.lo[0]; iv[0] <= sp.hi[0]; ++iv[0]) ++nB[lin_index(iv, G.dim, nc)];
+  }
+  for (int c = 0; c < ncells; ++c) {
+    cells[c].I.resize(nI[c]);
+    cells[c].B.resize(nB[c]);
+    nI[c] = nB[c] = 0;
+  }
+  for (int g : alive) {
+    const CellSpan sp = cell_span(G, cl, g);
+    if (sp.interior) {
+      const int c = lin_index(sp.lo, G.dim, nc);
+      cells[c].I[nI[c]++] = g;
       continue;
     }
     int iv[3];
-    for (iv[2] = lo[2]; iv[2] <= hi[2]; ++iv[2])
-      for (iv[1] = lo[1]; iv[1] <= hi[1]; ++iv[1])
-        for (iv[0] = lo[0]; iv[0] <= hi[0]; ++iv[0])
-          cells[lin_index(iv, G.dim, nc)].B.push_back(g);
+    for (iv[2] = sp.lo[2]; iv[2] <= sp.hi[2]; ++iv[2])
+      for (iv[1] = sp.lo[1]; iv[1] <= sp.hi[1]; ++iv[1])
+        for (iv[0] = sp.lo[0]; iv[0] <= sp.hi[0]; ++iv[0]) {
+          const int c = lin_index(iv, G.dim, nc);
+          cells[c].B[nB[c]++] = g;
+        }
   }
 }
 
 void build_child_map(const Geometry& G, int l, const HostCell& P, int cell_lin,
                      const std::vector<HostCell>& prev, std::vector<int>& out, int child[8]) {
+  out.resize((P.I.size() + P.B.size()) * 8);
+  build_child_map(G, l, P, cell_lin, prev, out.data(), child);
+}
+
+void build_child_map(const Geometry& G, int l, const HostCell& P, int cell_lin,
+                     const std::vector<HostCell>& prev, int* out, int child[8]) {
   const int nc = G.ncell[l], ncp = G.ncell[l - 1];
   const int nchild = 1 << G.dim;
   int iv[3] = {0, 0, 0};
@@ -101,7 +137,7 @@ void build_child_map(const Geometry& G, int l, const HostCell& P, int cell_lin,
     child[s] = lin_index(civ, G.dim, ncp);
   }
   const int nF = (int)(P.I.size() + P.B.size());
-  out.assign((size_t)nF * 8, -1);
+  std::fill(out, out + (size_t)nF * 8, -1);
   for (int s = 0; s < nchild; ++s) {
     const std::vector<int>& cb = prev[child[s]].B;
     // both lists ascending: merge-walk I and B separately
@@ -125,20 +161,43 @@ void build_fronts(const Geometry& G, int l, const std::vector<int>& alive,
   const std::vector<int>& cl = G.cls[l];
   int per_axis = nsep;
   for (int a = 1; a < G.dim; ++a) per_axis *= nc;
-  fronts.assign((size_t)per_axis * G.dim, HostFront{});
-  for (int g : alive) {
-    int x[3];
+  const int nslot = per_axis * G.dim;
+  // slot of an alive DOF with exactly one separator coordinate, else -1
+  auto slot_of = [&](int g, int& axis, int& ord, int x[3]) {
     G.coords(g, x);
-    int non = 0, axis = -1;
+    int non = 0;
+    axis = -1;
     for (int a = 0; a < G.dim; ++a)
       if (cl[x[a]] < 0) { ++non; axis = a; }
-    if (non != 1) continue;
-    const int ord = -cl[x[axis]] - 1;
+    if (non != 1) return -1;
+    ord = -cl[x[axis]] - 1;
     int other = 0;
     for (int a = G.dim - 1; a >= 0; --a)
       if (a != axis) other = other * nc + cl[x[a]];
-    const int f = axis * per_axis + ord + nsep * other;
-    HostFront& F = fronts[f];
+    return axis * per_axis + ord + nsep * other;
+  };
+  // count per slot; the non-empty slots become the fronts (in slot order)
+  std::vector<int> cnt(nslot, 0);
+  for (int g : alive) {
+    int axis, ord, x[3];
+    const int f = slot_of(g, axis, ord, x);
+    if (f >= 0) ++cnt[f];
+  }
+  std::vector<int> fid(nslot, -1);
+  int nf = 0;
+  for (int f = 0; f < nslot; ++f)
+    if (cnt[f] > 0) fid[f] = nf++;
+  fronts.assign(nf, HostFront{});
+  for (int f = 0; f < nslot; ++f)
+    if (fid[f] >= 0) {
+      fronts[fid[f]].c.reserve(cnt[f]);
+      cnt[f] = 0;
+    }
+  for (int g : alive) {
+    int axis, ord, x[3];
+    const int f = slot_of(g, axis, ord, x);
+    if (f < 0) continue;
+    HostFront& F = fronts[fid[f]];
     if (F.c.empty()) {
       F.axis = axis;
       int iv[3] = {0, 0, 0};
@@ -149,41 +208,37 @@ void build_fronts(const Geometry& G, int l, const std::vector<int>& alive,
     }
     F.c.push_back(g);
   }
-  // drop empty fronts
-  std::vector<HostFront> kept;
-  kept.reserve(fronts.size());
-  for (auto& F : fronts)
-    if (!F.c.empty()) kept.push_back(std::move(F));
-  fronts.swap(kept);
   if ((int64_t)mark.size() < G.N) mark.assign(G.N, -1);
   for (size_t f = 0; f < fronts.size(); ++f) {
     HostFront& F = fronts[f];
     for (int g : F.c) mark[g] = (int)f;
     const std::vector<int>& b1 = cells[F.P1].B;
     const std::vector<int>& b2 = cells[F.P2].B;
-    std::vector<int> c1(F.c.size(), -1), c2(F.c.size(), -1);
-    std::vector<int> n1, n2;
-    size_t i = 0, j = 0, ci = 0;
+    const size_t ncf = F.c.size(), bound = b1.size() + b2.size();
+    F.pos1.assign(ncf + bound, -1);
+    F.pos2.assign(ncf + bound, -1);
+    F.N.resize(bound);
+    size_t i = 0, j = 0, ci = 0, ni = 0;
     while (i < b1.size() || j < b2.size()) {
       int g;
       int p1 = -1, p2 = -1;
       if (j >= b2.size() || (i < b1.size() && b1[i] < b2[j])) { g = b1[i]; p1 = (int)i++; }
       else if (i >= b1.size() || b2[j] < b1[i]) { g = b2[j]; p2 = (int)j++; }
       else { g = b1[i]; p1 = (int)i++; p2 = (int)j++; }
-      if (mark[g] == (int)f) {
-        c1[ci] = p1;
-        c2[ci] = p2;
+      if (mark[g] == (int)f) {            // c in ascending order, as F.c
+        F.pos1[ci] = p1;
+        F.pos2[ci] = p2;
         ++ci;
       } else {
-        F.N.push_back(g);
-        n1.push_back(p1);
-        n2.push_back(p2);
+        F.N[ni] = g;
+        F.pos1[ncf + ni] = p1;
+        F.pos2[ncf + ni] = p2;
+        ++ni;
       }
     }
-    F.pos1 = c1;
-    F.pos1.insert(F.pos1.end(), n1.begin(), n1.end());
-    F.pos2 = c2;
-    F.pos2.insert(F.pos2.end(), n2.begin(), n2.end());
+    F.N.resize(ni);
+    F.pos1.resize(ncf + ni);
+    F.pos2.resize(ncf + ni);
     for (int g : F.c) mark[g] = -1;
   }
 }

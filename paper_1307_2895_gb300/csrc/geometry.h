@@ -48,6 +48,8 @@ void build_cells(const Geometry& G, int l, const std::vector<int>& alive, std::v
 // out[(a) * 8 + s] for the frontal index a of cell P (I then B) and child slot s.
 void build_child_map(const Geometry& G, int l, const HostCell& P, int cell_lin,
                      const std::vector<HostCell>& prev, std::vector<int>& out, int child[8]);
+void build_child_map(const Geometry& G, int l, const HostCell& P, int cell_lin,
+                     const std::vector<HostCell>& prev, int* out, int child[8]);
 
 // Fronts of level l + 1/2 from the DOFs alive after the level-l elimination.
 void build_fronts(const Geometry& G, int l, const std::vector<int>& alive,

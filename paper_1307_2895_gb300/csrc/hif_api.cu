@@ -206,29 +206,34 @@ void prepare_cells(const Geometry& G, int l, const std::vector<HostCell>& cells,
                    const std::vector<HostCell>* prev, std::vector<CellDesc>& desc, std::vector<int>& ipool,
                    int64_t& work_elems, int64_t& fac_elems, int& max_nI) {
   desc.resize(cells.size());
-  ipool.clear();
   work_elems = fac_elems = 0;
   max_nI = 0;
-  std::vector<int> cmap;
+  const bool maps = l > 0 && prev;
+  int64_t total = 0;
+  for (const HostCell& c : cells) total += (int64_t)(c.I.size() + c.B.size()) * (maps ? 9 : 1);
+  ipool.resize(total);
+  int64_t p = 0;
   for (size_t i = 0; i < cells.size(); ++i) {
     const HostCell& c = cells[i];
     CellDesc& d = desc[i];
     d.nI = (int)c.I.size();
     d.nB = (int)c.B.size();
     d.cell_lin = (int)i;
-    d.ids = (int64_t)ipool.size();
-    ipool.insert(ipool.end(), c.I.begin(), c.I.end());
-    ipool.insert(ipool.end(), c.B.begin(), c.B.end());
+    d.ids = p;
+    std::copy(c.I.begin(), c.I.end(), ipool.begin() + p);
+    p += d.nI;
+    std::copy(c.B.begin(), c.B.end(), ipool.begin() + p);
+    p += d.nB;
     d.F = work_elems;
     work_elems += (int64_t)d.nI * d.nI + (int64_t)d.nB * d.nI + (int64_t)d.nB * d.nB + cell_x_elems(d.nI);
     d.fac = fac_elems;
     fac_elems += cell_fac_size(d.nI, d.nB);
     for (int s = 0; s < kMaxChild; ++s) d.child[s] = -1;
     d.cmap = -1;
-    if (l > 0 && prev) {
-      build_child_map(G, l, c, (int)i, *prev, cmap, d.child);
-      d.cmap = (int64_t)ipool.size();
-      ipool.insert(ipool.end(), cmap.begin(), cmap.end());
+    if (maps) {
+      d.cmap = p;
+      build_child_map(G, l, c, (int)i, *prev, ipool.data() + p, d.child);
+      p += (int64_t)(d.nI + d.nB) * 8;
     }
     max_nI = std::max(max_nI, d.nI);
   }
