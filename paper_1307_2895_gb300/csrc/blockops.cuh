@@ -7,6 +7,17 @@
 
 namespace hif {
 
+// (i, j), j <= i, of the e-th entry of a lower triangle enumerated by rows.
+// The square root is taken in FP32 (exact enough up to e ~ 2^24, corrected
+// by the integer steps beyond): on this GPU the FP64 pipe is the scarce one.
+__device__ __forceinline__ void tri_decode(int64_t e, int& i, int& j) {
+  int r = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+  while ((int64_t)(r + 1) * (r + 2) / 2 <= e) ++r;
+  while ((int64_t)r * (r + 1) / 2 > e) --r;
+  i = r;
+  j = (int)(e - (int64_t)r * (r + 1) / 2);
+}
+
 template <typename T> __device__ __forceinline__ T dsqrt(T x);
 template <> __device__ __forceinline__ double dsqrt<double>(double x) { return sqrt(x); }
 template <> __device__ __forceinline__ float dsqrt<float>(float x) { return sqrtf(x); }
@@ -68,11 +79,12 @@ __device__ void blk_cholesky(T* A, int n, int ld, int* status, T tau = T(0), con
     for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[(int64_t)i * ld + j] *= r;
     __syncthreads();
     const int m = n - j - 1;
-    const int64_t tot = (int64_t)m * m;
+    const int64_t tot = (int64_t)m * (m + 1) / 2;   // lower triangle of the trailing block only
     for (int64_t e = threadIdx.x; e < tot; e += blockDim.x) {
-      const int i = j + 1 + (int)(e / m);
-      const int k = j + 1 + (int)(e % m);
-      if (k <= i) A[(int64_t)i * ld + k] -= A[(int64_t)i * ld + j] * A[(int64_t)k * ld + j];
+      int a, b;
+      tri_decode(e, a, b);
+      const int i = j + 1 + a, k = j + 1 + b;
+      A[(int64_t)i * ld + k] -= A[(int64_t)i * ld + j] * A[(int64_t)k * ld + j];
     }
     __syncthreads();
   }
@@ -121,11 +133,8 @@ template <typename T>
 __device__ void blk_syrk_sub(T* C, int ldc, const T* G, int ldg, int m, int kk) {
   const int64_t tot = (int64_t)m * (m + 1) / 2;
   for (int64_t e = threadIdx.x; e < tot; e += blockDim.x) {
-    // map e -> (i, j) with j <= i
-    int i = (int)((sqrt(8.0 * (double)e + 1.0) - 1.0) * 0.5);
-    while ((int64_t)(i + 1) * (i + 2) / 2 <= e) ++i;
-    while ((int64_t)i * (i + 1) / 2 > e) --i;
-    const int j = (int)(e - (int64_t)i * (i + 1) / 2);
+    int i, j;
+    tri_decode(e, i, j);
     const T* gi = G + (int64_t)i * ldg;
     const T* gj = G + (int64_t)j * ldg;
     T s = T(0);
@@ -142,10 +151,8 @@ template <typename T>
 __device__ void blk_pack_lower(const T* A, int lda, T* P, int n) {
   const int64_t tot = (int64_t)n * (n + 1) / 2;
   for (int64_t e = threadIdx.x; e < tot; e += blockDim.x) {
-    int i = (int)((sqrt(8.0 * (double)e + 1.0) - 1.0) * 0.5);
-    while ((int64_t)(i + 1) * (i + 2) / 2 <= e) ++i;
-    while ((int64_t)i * (i + 1) / 2 > e) --i;
-    const int t = (int)(e - (int64_t)i * (i + 1) / 2);
+    int i, t;
+    tri_decode(e, i, t);
     P[e] = A[(int64_t)i * lda + t];
   }
   __syncthreads();

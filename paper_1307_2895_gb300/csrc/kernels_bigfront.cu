@@ -339,10 +339,8 @@ __global__ void __launch_bounds__(TT) k_bf_form_rr(const FrontDesc* __restrict__
   const int P = (nR + TB - 1) / TB;
   const int64_t t = blockIdx.x;
   if (nR == 0 || t >= (int64_t)P * (P + 1) / 2) return;
-  int a = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-  while ((int64_t)(a + 1) * (a + 2) / 2 <= t) ++a;
-  while ((int64_t)a * (a + 1) / 2 > t) --a;
-  const int b = (int)(t - (int64_t)a * (a + 1) / 2);
+  int a, b;
+  tri_decode(t, a, b);
   const int i0 = a * TB, j0 = b * TB;
   const T* Acc = fwork + v.Acc;
   const T* Tm = fac + fd.fac + front_fac_T(nc);

@@ -331,9 +331,9 @@ __global__ void k_front(const FrontDesc* __restrict__ fronts, const CellDesc* __
     S2[e] = arow[perm[k + j]] - s;
   }
   __syncthreads();
-  for (int64_t e = threadIdx.x; e < (int64_t)nR * nR; e += blockDim.x) {
-    const int i = (int)(e / nR), j = (int)(e % nR);
-    if (j > i) continue;
+  for (int64_t e = threadIdx.x; e < (int64_t)nR * (nR + 1) / 2; e += blockDim.x) {
+    int i, j;
+    tri_decode(e, i, j);                   // j <= i
     T x1 = T(0), x2 = T(0), y = T(0);
     for (int t = 0; t < k; ++t) {
       const T* at = Acc + (int64_t)perm[t] * nc;
@@ -356,8 +356,9 @@ __global__ void k_front(const FrontDesc* __restrict__ fronts, const CellDesc* __
     if (k > 0) {
       blk_mul_linvT(S2, nR, X, nR, k, nR, G, nR);
       // B_ss = A_ss - G G^T -> P1's update (skeleton block), zero in P2's
-      for (int64_t e = threadIdx.x; e < (int64_t)k * k; e += blockDim.x) {
-        const int i = (int)(e / k), j = (int)(e % k);
+      for (int64_t e = threadIdx.x; e < (int64_t)k * (k + 1) / 2; e += blockDim.x) {
+        int i, j;
+        tri_decode(e, i, j);               // j <= i; B_ss is symmetric
         const T* gi = G + (int64_t)i * nR;
         const T* gj = G + (int64_t)j * nR;
         T s = T(0);
@@ -365,7 +366,9 @@ __global__ void k_front(const FrontDesc* __restrict__ fronts, const CellDesc* __
         const int ci = perm[i], cj = perm[j];
         const T b = Acc[(int64_t)ci * nc + cj] - s;
         U1[(int64_t)pos1[ci] * ld1 + pos1[cj]] = b;
+        U1[(int64_t)pos1[cj] * ld1 + pos1[ci]] = b;
         U2[(int64_t)pos2[ci] * ld2 + pos2[cj]] = T(0);
+        U2[(int64_t)pos2[cj] * ld2 + pos2[ci]] = T(0);
       }
     }
   }

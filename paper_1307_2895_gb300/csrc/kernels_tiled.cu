@@ -145,10 +145,8 @@ __global__ void __launch_bounds__(TT) k_tl_update(const TDesc* __restrict__ td,
   T* Out;
   int rows, j;
   if (t < nlow) {
-    int a = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-    while ((int64_t)(a + 1) * (a + 2) / 2 <= t) ++a;
-    while ((int64_t)a * (a + 1) / 2 > t) --a;
-    const int b = (int)(t - (int64_t)a * (a + 1) / 2);
+    int a, b;
+    tri_decode(t, a, b);
     const int i = p + 1 + a;
     j = p + 1 + b;
     Lrow = work + c.FII + (int64_t)i * TB * ld;
@@ -189,10 +187,8 @@ __global__ void __launch_bounds__(TT) k_tl_syrk(const TDesc* __restrict__ td,
   const TCell c = tcell(td[blockIdx.y]);
   const int64_t t = blockIdx.x;
   if (t >= (int64_t)c.RB * (c.RB + 1) / 2) return;
-  int a = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-  while ((int64_t)(a + 1) * (a + 2) / 2 <= t) ++a;
-  while ((int64_t)a * (a + 1) / 2 > t) --a;
-  const int b = (int)(t - (int64_t)a * (a + 1) / 2);
+  int a, b;
+  tri_decode(t, a, b);
   const int ld = c.nI;
   const T* Gi = work + c.FBI + (int64_t)a * TB * ld;
   const T* Gj = work + c.FBI + (int64_t)b * TB * ld;
