@@ -94,13 +94,18 @@ __device__ void blk_cholesky(T* A, int n, int ld, int* status, T tau = T(0), con
 // above the diagonal).  Column-oriented forward substitution on the identity.
 template <typename T>
 __device__ void blk_tri_inverse(const T* L, int n, int ldl, T* X, int ldx) {
+  // reciprocals of the diagonal, each taken once (a division is many FP64
+  // instructions, and every lane of a warp pays for it)
+  constexpr int kRecip = 256;
+  __shared__ T s_rinv[kRecip];
+  for (int k = threadIdx.x; k < n && k < kRecip; k += blockDim.x) s_rinv[k] = T(1) / L[(int64_t)k * ldl + k];
   for (int64_t e = threadIdx.x; e < (int64_t)n * n; e += blockDim.x) {
     const int i = (int)(e / n), c = (int)(e % n);
     X[(int64_t)i * ldx + c] = (i == c) ? T(1) : T(0);
   }
   __syncthreads();
   for (int k = 0; k < n; ++k) {
-    const T r = T(1) / L[(int64_t)k * ldl + k];
+    const T r = k < kRecip ? s_rinv[k] : T(1) / L[(int64_t)k * ldl + k];
     for (int c = threadIdx.x; c <= k; c += blockDim.x) X[(int64_t)k * ldx + c] *= r;
     __syncthreads();
     const int m = n - k - 1;
