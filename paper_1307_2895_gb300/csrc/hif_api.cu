@@ -160,6 +160,7 @@ struct hif_handle {
   int variant = HIF_VARIANT_HIFDE;
   int skip_levels = 0;
   int big_cell = 192;   // cells with at least this many interior DOFs use the tiled elimination
+  bool coop_qr = true;  // large fronts: pivoted QR by co-resident block groups
   int id_mode = HIF_ID_QR;
   int oversample = 10;
   unsigned long long seed = 0;
@@ -549,6 +550,7 @@ struct Factorizer {
     h->sketched = hs2[2];
     h->fallback = hs2[3];
     if (hs & 1) throw HifError(HIF_ERR_NOT_SPD, "non-positive pivot in a diagonal-block Cholesky");
+    if (hs & 16) throw HifError(HIF_ERR_TIMEOUT, "a bounded group-barrier wait of the multi-block pivoted QR ran out");
   }
 
   // One launch for every front of level l + 1/2, then read back ranks and
@@ -620,10 +622,15 @@ struct Factorizer {
       bstate.alloc(sizeof(int) * nbig, st);
       m2part.alloc(sizeof(double) * nbig * nm, st);
       e2part.alloc(sizeof(double) * nbig * ne, st);
+      std::vector<int> bnc(nbig), bnN(nbig);
+      for (int b = 0; b < nbig; ++b) {
+        bnc[b] = fd[big[b]].nc;
+        bnN[b] = fd[big[b]].nN;
+      }
       launch_bigfront_id<T>(d_fd, d_big.as<int>(), nbig, d_cdesc, d_ip, cwork.as<T>(), fwork.as<T>(), sw.fac.as<T>(),
                             obuf.as<int>(), sketch.as<int>(), seed, h->eps, status.as<int>(), bstate.as<int>(),
                             m2part.as<double>(), nm, e2part.as<double>(), ne, big_nc, big_nN,
-                            sketch.p ? big_nc : 0, st);
+                            sketch.p ? big_nc : 0, bnc.data(), bnN.data(), h->coop_qr, st);
     }
     CU(cudaGetLastError());
     info.fr = fr;

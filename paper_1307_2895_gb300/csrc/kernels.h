@@ -29,13 +29,15 @@ void launch_front(const FrontDesc* fronts, int nfronts, const CellDesc* cells, c
                   const int* sketch, uint64_t seed, const int* sel, cudaStream_t st);
 
 // skeletonization of large fronts (kernels_bigfront.cu): the ID (writes T
-// and the front's outputs), then, with the ranks known on the host, the
-// Lemma 2.4 blocks, and after the tiled elimination the B_ss scatter.
+// and the front's outputs; h_nc / h_nN: host copies of the fronts' sizes, for
+// the block groups of the multi-block pivoted QR, used when coop_ok), then,
+// with the ranks known on the host, the Lemma 2.4 blocks, and after the
+// tiled elimination the B_ss scatter.
 template <typename T>
 void launch_bigfront_id(const FrontDesc* fronts, const int* big, int nbig, const CellDesc* cells, const int* ipool,
                         const T* cwork, T* fwork, T* fac, int* obuf, const int* sketch, uint64_t seed, double eps,
                         int* status, int* state, double* m2part, int nm, double* e2part, int ne, int max_nc,
-                        int max_nN, int max_ell, cudaStream_t st);
+                        int max_nN, int max_ell, const int* h_nc, const int* h_nN, bool coop_ok, cudaStream_t st);
 template <typename T>
 void launch_bigfront_form(const FrontDesc* fronts, const int* big, int nbig, const int* obuf, T* fwork,
                           const T* fac, int max_k, int max_nR, cudaStream_t st);

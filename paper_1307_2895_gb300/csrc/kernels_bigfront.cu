@@ -21,6 +21,9 @@
 //   M (nN x nc, column-major) | A_cc (nc x nc) | F: B_rr (nR x nR) | B_sr
 //   (k x nR) | A_ss (k x k) (<= nc^2) | X (elimination scratch, <= nc^2) |
 //   Y (the sketch, ell x nc column-major, <= nc^2).
+#include <algorithm>
+#include <vector>
+
 #include "hif_internal.h"
 #include "blockops.cuh"
 #include "front_common.cuh"
@@ -150,14 +153,15 @@ __global__ void __launch_bounds__(TT) k_bf_sketch(const FrontDesc* __restrict__ 
 // ---- the ID, one thread block per front.
 // pass 0: fronts with a valid sketch size take the pivoted QR of Y (state 1:
 // residual check pending; state 2 if the sketch saturated, k = ell); the
-// others the pivoted QR of M (state 0).  pass 1: fronts in state 2 take the
-// pivoted QR of M (state 0).  Writes T (k x nR) to the front's factor, and
+// others the pivoted QR of M (state 0), or are left in state 2 for the
+// multi-block QR (defer_qr).  pass 1: fronts in state 2 take the pivoted QR
+// of M (state 0).  Writes T (k x nR) to the front's factor, and
 // k | perm | ids (pivot order) to its output slot.
 template <typename T>
 __global__ void k_bf_id(const FrontDesc* __restrict__ fronts, const int* __restrict__ big,
                         const int* __restrict__ sketch, const int* __restrict__ ipool, T* __restrict__ fwork,
                         T* __restrict__ fac, int* __restrict__ obuf, int* __restrict__ state, double eps,
-                        int* status, int pass) {
+                        int* status, int pass, int defer_qr) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int f = big[blockIdx.x];
   const FrontDesc fd = fronts[f];
@@ -166,6 +170,10 @@ __global__ void k_bf_id(const FrontDesc* __restrict__ fronts, const int* __restr
   const int ell = sketch ? sketch[f] : 0;
   const bool use_sketch = pass == 0 && ell > 0 && ell < nc && ell < nN;
   if (pass == 1 && state[blockIdx.x] != 2) return;
+  if (!use_sketch && defer_qr) {                 // the pivoted QR of M goes to k_bf_qr_coop
+    if (threadIdx.x == 0) state[blockIdx.x] = 2;
+    return;
+  }
   const int m = use_sketch ? ell : nN;
   double* sq = reinterpret_cast<double*>(smem_raw);            // nc
   double* vv = sq + nc;                                         // m
@@ -398,6 +406,195 @@ __global__ void k_bf_scatter(const FrontDesc* __restrict__ fronts, const int* __
   }
 }
 
+// ---- pivoted QR of M by a group of co-resident thread blocks per front.
+// Block g of G owns the columns [g nc / G, (g+1) nc / G).  Every step: each
+// block writes the squared residual norms of its unchosen columns (parity
+// buffer of the front's scratch), one group barrier, then every block takes
+// the same pivot from all norms (tie rule and rank rule of blk_pivoted_qr),
+// builds the reflector from the pivot column and applies it to its own
+// columns.  The pivot column itself is never rewritten (its diagonal R_ii
+// goes to diagR), so blocks still reading it are never raced.  The norms
+// and dot products are the warp-per-column reductions of blk_pivoted_qr, so
+// pivots, R and T are those of the one-block kernel bit for bit.
+// Scratch per front: sq[2][nc] | diagR[nc] (double) | chosen[nc] (int) |
+// barrier[2] (unsigned), zeroed before the launch.
+__device__ bool group_barrier(unsigned* bar, int G, int* err) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    s_ok = 1;
+    volatile unsigned* vgen = bar + 1;
+    const unsigned gen = *vgen;
+    __threadfence();
+    if (atomicAdd(bar, 1u) == (unsigned)(G - 1)) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long it = 0;
+      while (*vgen == gen) {
+        if (++it > (1L << 22)) {   // ~0.1-1 s: a member never arrived
+          atomicOr(err, 16);
+          s_ok = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+__host__ __device__ inline int64_t coop_scratch_elems(int nc) { return 3 * (int64_t)nc + ((int64_t)nc + 4) / 2 + 2; }
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_bf_qr_coop(const FrontDesc* __restrict__ fronts, const int* __restrict__ big,
+                                                    const int4* __restrict__ ctas, double* __restrict__ scratch,
+                                                    const int64_t* __restrict__ soff, const int* __restrict__ ipool,
+                                                    T* __restrict__ fwork, T* __restrict__ fac, int* __restrict__ obuf,
+                                                    int* __restrict__ state, double eps, int* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* v = reinterpret_cast<double*>(smem_raw);   // m
+  __shared__ double s_alpha, s_vv, s_nu;
+  __shared__ int s_piv, s_stop, s_k;
+  const int4 cd = ctas[blockIdx.x];
+  const int b = cd.x, g = cd.y, G = cd.z;
+  if (state[b] != 2) return;                          // the same for the whole group
+  const FrontDesc fd = fronts[big[b]];
+  const BfView bv = bf_view(fd);
+  const int nc = fd.nc, m = fd.nN;
+  T* A = fwork + bv.M;
+  double* sq2 = scratch + soff[b];
+  double* diagR = sq2 + 2 * nc;
+  int* chosen = reinterpret_cast<int*>(diagR + nc);
+  unsigned* bar = reinterpret_cast<unsigned*>(scratch + soff[b] + coop_scratch_elems(nc) - 2);
+  int* out = obuf + fd.out;
+  const int c0 = (int)((int64_t)g * nc / G), c1 = (int)((int64_t)(g + 1) * nc / G);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  if (threadIdx.x == 0) { s_k = 0; s_stop = 0; }
+  const int kmax = m < nc ? m : nc;
+  for (int i = 0; i < kmax; ++i) {
+    double* sq = sq2 + (i & 1) * nc;
+    for (int j = c0 + warp; j < c1; j += nwarps) {
+      if (__ldcg(chosen + j)) {
+        if (lane == 0) sq[j] = -1.0;
+        continue;
+      }
+      const T* col = A + (int64_t)j * m;
+      double acc = 0.0;
+      for (int r = i + lane; r < m; r += 32) { const double x = (double)col[r]; acc += x * x; }
+      acc = warp_sum(acc);
+      if (lane == 0) sq[j] = acc;
+    }
+    if (!group_barrier(bar, G, status)) return;
+    // The pivot is taken from this step's norm snapshot alone, in which the
+    // owners marked their chosen columns -1 before the barrier: chosen[] may
+    // change during this step (the owner of this step's pivot marks it), the
+    // snapshot cannot until every block has passed the next barrier.  Data
+    // written by other blocks of the group is read through L2.
+    if (warp == 0) {
+      double mx = -1.0;
+      for (int j = lane; j < nc; j += 32) {
+        const double sj = __ldcg(sq + j);
+        if (sj > mx) mx = sj;
+      }
+      for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      int piv = 0x7fffffff;
+      for (int j = lane; j < nc; j += 32)
+        if (__ldcg(sq + j) >= (1.0 - 1e-10) * mx) { piv = j; break; }
+      for (int o = 16; o > 0; o >>= 1) piv = min(piv, __shfl_xor_sync(0xffffffffu, piv, o));
+      if (lane == 0) {
+        if (i == 0) s_nu = mx;
+        const double nu = s_nu;
+        const double ratio = (nu > 0.0) ? sqrt(mx / nu) : 0.0;
+        if (g == 0 && fabs(ratio - eps) <= 1e-8 * eps) atomicOr(status, 2);
+        const int stop = (mx <= 0.0) || (i > 0 && mx <= eps * eps * nu);
+        s_stop = stop;
+        if (!stop) {
+          s_piv = piv;
+          const double x0 = (double)__ldcg(A + (int64_t)piv * m + i);
+          const double sp = __ldcg(sq + piv);
+          const double a2 = (x0 >= 0.0) ? -sqrt(sp) : sqrt(sp);
+          s_alpha = a2;
+          s_vv = sp - x0 * x0 + (x0 - a2) * (x0 - a2);
+          s_k = i + 1;
+        }
+      }
+    }
+    __syncthreads();
+    if (s_stop) break;
+    const int piv = s_piv;
+    const double alpha = s_alpha, vv = s_vv;
+    const T* pc = A + (int64_t)piv * m;
+    for (int r = i + threadIdx.x; r < m; r += blockDim.x) v[r] = (double)__ldcg(pc + r) - (r == i ? alpha : 0.0);
+    if (threadIdx.x == 0) {
+      if (g == 0) {
+        out[1 + i] = piv;
+        diagR[i] = (double)(T)alpha;
+      }
+      if (piv >= c0 && piv < c1) chosen[piv] = 1;
+    }
+    __syncthreads();
+    if (vv > 0.0) {
+      for (int j = c0 + warp; j < c1; j += nwarps) {
+        if (j == piv || __ldcg(chosen + j)) continue;
+        T* col = A + (int64_t)j * m;
+        double s = 0.0;
+        for (int r = i + lane; r < m; r += 32) s += v[r] * (double)col[r];
+        s = warp_sum(s);
+        const double f = 2.0 * s / vv;
+        for (int r = i + lane; r < m; r += 32) col[r] = (T)((double)col[r] - f * v[r]);
+      }
+    }
+    __syncthreads();
+  }
+  const int k = s_k;
+  if (!group_barrier(bar, G, status)) return;
+  // redundant columns in ascending order: index of this block's first one
+  __shared__ int s_base, s_own;
+  if (threadIdx.x == 0) {
+    int cnt = 0, own = 0;
+    for (int j = 0; j < c0; ++j) cnt += !__ldcg(chosen + j);
+    for (int j = c0; j < c1; ++j) own += !__ldcg(chosen + j);
+    s_base = cnt;
+    s_own = own;
+  }
+  __syncthreads();
+  const int nR = nc - k;
+  T* Tm = fac + fd.fac + front_fac_T(nc);
+  const int* idc = ipool + fd.ids;
+  if (threadIdx.x == 0) {
+    int idx = s_base;
+    for (int j = c0; j < c1 && idx < nR; ++j)      // (idx < nR holds when the group agrees on k)
+      if (!__ldcg(chosen + j)) {
+        out[1 + k + idx] = j;
+        out[1 + nc + k + idx] = idc[j];
+        ++idx;
+      }
+  }
+  __syncthreads();
+  // T = R11^-1 R12 for this block's redundant columns (blk_id_T's arithmetic)
+  for (int c = s_base + threadIdx.x; c < s_base + s_own && c < nR; c += blockDim.x) {
+    const int col = out[1 + k + c];
+    const T* r12 = A + (int64_t)col * m;
+    for (int t = k - 1; t >= 0; --t) {
+      T sum = r12[t];
+      for (int u = t + 1; u < k; ++u)
+        sum -= __ldcg(A + (int64_t)__ldcg(out + 1 + u) * m + t) * Tm[(int64_t)u * nR + c];
+      Tm[(int64_t)t * nR + c] = sum / (T)__ldcg(diagR + t);
+    }
+  }
+  if (g == 0) {
+    for (int t = threadIdx.x; t < k; t += blockDim.x) out[1 + nc + t] = idc[__ldcg(out + 1 + t)];
+    if (threadIdx.x == 0) {
+      out[0] = k;
+      state[b] = 0;
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 static int chunk_blocks(int64_t n, int cap) {
   const int64_t b = (n + 256 * 8 - 1) / (256 * 8);
@@ -408,7 +605,7 @@ template <typename T>
 void launch_bigfront_id(const FrontDesc* fronts, const int* big, int nbig, const CellDesc* cells, const int* ipool,
                         const T* cwork, T* fwork, T* fac, int* obuf, const int* sketch, uint64_t seed, double eps,
                         int* status, int* state, double* m2part, int nm, double* e2part, int ne, int max_nc,
-                        int max_nN, int max_ell, cudaStream_t st) {
+                        int max_nN, int max_ell, const int* h_nc, const int* h_nN, bool coop_ok, cudaStream_t st) {
   if (nbig == 0) return;
   long long nl = 0;
   k_bf_assemble<T><<<dim3(chunk_blocks((int64_t)max_nc * (max_nN + max_nc), 2048), nbig), 256, 0, st>>>(
@@ -425,13 +622,95 @@ void launch_bigfront_id(const FrontDesc* fronts, const int* big, int nbig, const
   const int smem = (int)(sizeof(double) * (max_nc + max_nN) + sizeof(int) * 2 * max_nc + 64);
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(k_bf_id<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  k_bf_id<T><<<nbig, 256, smem, st>>>(fronts, big, sketch, ipool, fwork, fac, obuf, state, eps, status, 0);
+  // groups of the multi-block QR: blocks per front in proportion to its QR
+  // work (|N| |c|^2), at least 32 columns per block, all co-resident
+  const int csmem = (int)(sizeof(double) * max_nN + 64);
+  bool coop = coop_ok && csmem <= 200 * 1024;
+  std::vector<int4> ctas;
+  std::vector<int64_t> soff(nbig);
+  int64_t sc_elems = 0;
+  if (coop) {
+    if (csmem > 48 * 1024)
+      cudaFuncSetAttribute(k_bf_qr_coop<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, csmem);
+    int nb = 0, dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_bf_qr_coop<T>, 256, csmem) != cudaSuccess) {
+      cudaGetLastError();
+      nb = 0;
+    }
+    const int cap = nb * nsm;
+    double wsum = 0.0;
+    for (int b = 0; b < nbig; ++b) wsum += (double)h_nN[b] * h_nc[b] * h_nc[b];
+    std::vector<int> G(nbig, 1);
+    int tot = nbig;
+    if (cap >= nbig) {
+      tot = 0;
+      for (int b = 0; b < nbig; ++b) {
+        const double w = (double)h_nN[b] * h_nc[b] * h_nc[b];
+        int g = (int)((double)(cap - nbig) * w / (wsum > 0 ? wsum : 1.0)) + 1;
+        g = std::min(g, std::max(1, h_nc[b] / 32));
+        G[b] = g;
+        tot += g;
+      }
+    }
+    coop = cap >= nbig && tot <= cap;
+    if (coop) {
+      for (int b = 0; b < nbig; ++b) {
+        soff[b] = sc_elems;
+        sc_elems += (coop_scratch_elems(h_nc[b]) + 3) & ~int64_t(3);
+        for (int g = 0; g < G[b]; ++g) ctas.push_back(make_int4(b, g, G[b], 0));
+      }
+    }
+  }
+  k_bf_id<T><<<nbig, 256, smem, st>>>(fronts, big, sketch, ipool, fwork, fac, obuf, state, eps, status, 0,
+                                      coop ? 1 : 0);
   ++nl;
   if (sk) {
     k_bf_resid<T><<<dim3(ne, nbig), TT, 0, st>>>(fronts, big, obuf, state, fwork, fac, e2part);
     k_bf_check<<<(nbig + 127) / 128, 128, 0, st>>>(nbig, state, m2part, nm, e2part, ne, eps, status);
-    k_bf_id<T><<<nbig, 256, smem, st>>>(fronts, big, sketch, ipool, fwork, fac, obuf, state, eps, status, 1);
-    nl += 3;
+    nl += 2;
+  }
+  bool done = false;
+  if (coop) {
+    // descriptors and the zeroed scratch live in one stream-ordered buffer
+    const size_t cbytes = sizeof(int4) * ctas.size(), obytes = sizeof(int64_t) * soff.size();
+    const size_t off_s = (cbytes + obytes + 255) & ~size_t(255);
+    void* buf = nullptr;
+    if (cudaMallocAsync(&buf, off_s + sizeof(double) * (size_t)sc_elems, st) == cudaSuccess) {
+      char* cb = static_cast<char*>(buf);
+      cudaMemcpyAsync(cb, ctas.data(), cbytes, cudaMemcpyHostToDevice, st);
+      cudaMemcpyAsync(cb + cbytes, soff.data(), obytes, cudaMemcpyHostToDevice, st);
+      cudaMemsetAsync(cb + off_s, 0, sizeof(double) * (size_t)sc_elems, st);
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)ctas.size());
+      cfg.blockDim = dim3(256);
+      cfg.dynamicSmemBytes = csmem;
+      cfg.stream = st;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeCooperative;
+      attr[0].val.cooperative = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      const cudaError_t e = cudaLaunchKernelEx(&cfg, k_bf_qr_coop<T>, fronts, big,
+                                               reinterpret_cast<const int4*>(cb),
+                                               reinterpret_cast<double*>(cb + off_s),
+                                               reinterpret_cast<const int64_t*>(cb + cbytes), ipool, fwork, fac,
+                                               obuf, state, eps, status);
+      cudaFreeAsync(buf, st);
+      if (e == cudaSuccess) {
+        done = true;
+        ++nl;
+      } else {
+        cudaGetLastError();
+      }
+    } else {
+      cudaGetLastError();
+    }
+  }
+  if (!done && (sk || coop)) {
+    k_bf_id<T><<<nbig, 256, smem, st>>>(fronts, big, sketch, ipool, fwork, fac, obuf, state, eps, status, 1, 0);
+    ++nl;
   }
   note_launches(nl);
 }
@@ -472,7 +751,7 @@ int bigfront_resid_strips(int max_nc) { return (max_nc + TB - 1) / TB; }
 #define HIF_BF_INST(T)                                                                                          \
   template void launch_bigfront_id<T>(const FrontDesc*, const int*, int, const CellDesc*, const int*, const T*, \
                                       T*, T*, int*, const int*, uint64_t, double, int*, int*, double*, int,     \
-                                      double*, int, int, int, int, cudaStream_t);                                \
+                                      double*, int, int, int, int, const int*, const int*, bool, cudaStream_t); \
   template void launch_bigfront_form<T>(const FrontDesc*, const int*, int, const int*, T*, const T*, int, int,  \
                                         cudaStream_t);                                                           \
   template void launch_bigfront_scatter<T>(const FrontDesc*, const int*, int, const CellDesc*, const int*,      \
