@@ -7,6 +7,10 @@
   stencil in bond form (``oracle.stencil.residual_ext``).
 * 2D 511^2 contrast-1e6 workload in the launch configuration bench.py times
   (FP32 apply, 8 right-hand sides): 1e-12 reached and re-checked likewise.
+* 3D 127^3 contrast-1e4 workload with the learned rank predictor sizing the
+  randomized ID (trained on 31^3 rank logs of other fields): |s_L| within 15%
+  of the paper's Example 5 value (Table 9, hifde3 at 127^3: 6679), 1e-12
+  reached with 4 right-hand sides and re-checked likewise.
 """
 import os
 
@@ -64,3 +68,41 @@ def test_contrast2d_511_bench_configuration(hiflib):
     assert info["converged"] and info["relres_max"] <= 1e-12
     assert stencil.residual_ext(2, 512, w["a_stag"], w["b"], f, xh, xl).max() <= 2e-12
     assert st["clamped_pivots"] == 0
+
+
+def test_contrast3d_127_learned(hiflib):
+    import torch
+    from paper_1307_2895_gb300 import hif
+    H, NF = 64, 10
+    rng = np.random.default_rng(7)
+    p = np.zeros(hif.MLP_PARAMS, np.float32)
+    p[:H * NF] = rng.standard_normal(H * NF) * np.sqrt(2 / NF)
+    o = H * NF + H
+    p[o:o + H * H] = rng.standard_normal(H * H) * np.sqrt(2 / H)
+    o += H * H + H
+    p[o:o + H] = rng.standard_normal(H) * np.sqrt(1 / H)
+    Xs, ts = [], []
+    for seed in (11, 12):
+        a, b = inputs.high_contrast_coefficients(3, 32, seed=seed, low=1e-2, high=1e2)
+        G = hif.factor(3, 32, a, b, 1e-6)
+        try:
+            f_, r_, _ = G.front_log()
+        finally:
+            G.free()
+        Xs.append(f_)
+        ts.append(np.log1p(r_.astype(np.float32)))
+    params = torch.tensor(p, device="cuda")
+    hif.mlp_train(torch.tensor(np.concatenate(Xs), device="cuda"), torch.tensor(np.concatenate(ts), device="cuda"),
+                  params, steps=2000, batch=512, lr=2e-3, seed=1)
+    w = inputs.workload("contrast3d_n128")
+    f = inputs.rhs(3, 128, w["nrhs"], seed=0)
+    F = hif.factor(3, 128, w["a_stag"], w["b"], w["eps"], precision="fp32_apply", id_mode="learned",
+                   rank_model=params, seed=5)
+    try:
+        st = F.stats()
+        xh, xl, info = F.solve(f, tol=1e-12, maxit=200, want_lo=True)
+    finally:
+        F.free()
+    assert abs(st["root_size"] - 6679) <= 0.15 * 6679, st["root_size"]
+    assert info["converged"] and info["relres_max"] <= 1e-12
+    assert stencil.residual_ext(3, 128, w["a_stag"], w["b"], f, xh, xl).max() <= 2e-12
