@@ -166,6 +166,21 @@ int hif_apply(hif_handle* h, int mode, const double* x, double* y, int nrhs, int
 int hif_solve(hif_handle* h, const double* rhs, double* x, double* x_lo, int nrhs,
               int ld, double tol, int maxit, hif_solve_info* info);
 
+/*
+ * Batches of independent problems (each one a separate HIF-DE, Section 5's
+ * workloads at many sizes): hif_factor / hif_solve for problems 0..nprob-1,
+ * issued concurrently from up to nthreads host threads (<= 0 -> 8), each
+ * problem on its own stream (opts->stream is ignored), so the small launches
+ * of different problems overlap on the GPU.  Arrays are indexed by problem;
+ * out[p] receives problem p's handle (NULL on failure), infos may be NULL.
+ * Returns HIF_OK, or the status of the lowest-numbered failing problem (the
+ * other problems still run); hif_last_error() then describes that failure.
+ */
+int hif_factor_batch(int nprob, const hif_grid* grids, const double* const* a_stag, const double* const* b,
+                     const double* eps, const hif_opts* opts, int nthreads, hif_handle** out);
+int hif_solve_batch(int nprob, hif_handle* const* hs, const double* const* rhs, double* const* x,
+                    const int* nrhs, double tol, int maxit, hif_solve_info* infos, int nthreads);
+
 /* hif_matvec -- y = A x with the stencil of the factored problem (FP64). */
 int hif_matvec(hif_handle* h, const double* x, double* y, int nrhs, int ld);
 

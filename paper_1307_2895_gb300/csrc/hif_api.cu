@@ -14,6 +14,8 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <thread>
+#include <functional>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -1431,6 +1433,60 @@ int hif_profile(hif_handle* h, int enable, hif_profile_t* out) {
 }
 
 long long hif_kernel_launches(void) { return g_launches.load(); }
+
+// Batches: one problem per task, tasks pulled by a small pool of host threads
+// (each handle works on its own stream, so different problems overlap).
+static int run_batch(int nprob, int nthreads, const std::function<int(int)>& task) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  nthreads = nthreads <= 0 ? 8 : nthreads;
+  nthreads = std::max(1, std::min(nthreads, nprob));
+  std::atomic<int> next{0};
+  std::mutex mu;
+  int first = nprob, first_rc = HIF_OK;
+  std::string first_msg;
+  auto worker = [&]() {
+    cudaSetDevice(dev);
+    for (int p = next.fetch_add(1); p < nprob; p = next.fetch_add(1)) {
+      const int rc = task(p);
+      if (rc != HIF_OK) {
+        std::lock_guard<std::mutex> lock(mu);
+        if (p < first) {
+          first = p;
+          first_rc = rc;
+          first_msg = g_last_error;
+        }
+      }
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int t = 1; t < nthreads; ++t) pool.emplace_back(worker);
+  worker();
+  for (std::thread& t : pool) t.join();
+  if (first_rc != HIF_OK) return set_error(first_rc, first_msg);
+  return HIF_OK;
+}
+
+int hif_factor_batch(int nprob, const hif_grid* grids, const double* const* a_stag, const double* const* b,
+                     const double* eps, const hif_opts* opts, int nthreads, hif_handle** out) {
+  if (nprob < 0 || (nprob > 0 && (!grids || !a_stag || !b || !eps || !out)))
+    return set_error(HIF_ERR_ARG, "bad batch arguments");
+  for (int p = 0; p < nprob; ++p) out[p] = nullptr;
+  return run_batch(nprob, nthreads, [&](int p) {
+    hif_opts o{};
+    if (opts) o = *opts;
+    o.stream = nullptr;
+    return hif_factor(&grids[p], a_stag[p], b[p], nullptr, eps[p], &o, &out[p]);
+  });
+}
+
+int hif_solve_batch(int nprob, hif_handle* const* hs, const double* const* rhs, double* const* x,
+                    const int* nrhs, double tol, int maxit, hif_solve_info* infos, int nthreads) {
+  if (nprob < 0 || (nprob > 0 && (!hs || !rhs || !x || !nrhs))) return set_error(HIF_ERR_ARG, "bad batch arguments");
+  return run_batch(nprob, nthreads, [&](int p) {
+    return hif_solve(hs[p], rhs[p], x[p], nullptr, nrhs[p], nrhs[p], tol, maxit, infos ? &infos[p] : nullptr);
+  });
+}
 
 int hif_front_log(const hif_handle* h, float* feats, int32_t* ranks, int32_t* sizes, long long cap,
                   long long* count) {

@@ -17,6 +17,8 @@
 // shared memory with 16-byte loads (all threads, fully coalesced), then every
 // product is a serial dot per (output row, right-hand side) pair, one thread
 // per pair, with no cross-lane reductions.
+#include <atomic>
+
 #include "hif_internal.h"
 #include "blockops.cuh"
 #include "kernels.h"
@@ -409,7 +411,7 @@ static void launch_sweep_R(int op, const ApplyDesc* blocks, int nblocks, const i
   }
   // raise the dynamic shared-memory limit and prefer the largest shared
   // carveout once per kernel (not again while a stream capture records it)
-  static bool attr_set[4] = {false, false, false, false};
+  static std::atomic<bool> attr_set[4] = {false, false, false, false};
   if (!attr_set[op]) {
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSweepSmemCap);
     cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);

@@ -7,6 +7,8 @@
 // b2 (H) | W3 (1 x H) | b3 (1).  F = kFeat, H = kHid.
 #include <cuda_bf16.h>
 
+#include <atomic>
+
 #include "hif_internal.h"
 #include "kernels.h"
 
@@ -198,7 +200,7 @@ void mlp_grad(const float* X, const float* t, const int* idx, int nb, float inv_
               float* partial, float* ploss, float* grad, float* loss, cudaStream_t st) {
   const int nblk = (nb + kChunk - 1) / kChunk;
   const size_t smem = fwd_bwd_smem();
-  static bool attr = false;
+  static std::atomic<bool> attr{false};
   if (!attr) {
     cudaFuncSetAttribute(k_mlp_fwd_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;

@@ -17,6 +17,8 @@
 // for the pivot safeguard) lives in the problem's X region of the work pool.
 // Each problem is described by a TDesc (a large cell, or the redundant block
 // of a large front).
+#include <atomic>
+
 #include "hif_internal.h"
 #include "blockops.cuh"
 #include "kernels.h"
@@ -285,7 +287,7 @@ void launch_tiled_elim(const TDesc* td, int nsel, int max_nI, int max_nB, T* wor
   if (nsel == 0 || max_nI == 0) return;
   const int P = (max_nI + TB - 1) / TB, RB = (max_nB + TB - 1) / TB;
   const int psmem = 2 * TB * TB * (int)sizeof(T);
-  static bool attr = false;
+  static std::atomic<bool> attr{false};
   if (!attr) {
     cudaFuncSetAttribute(k_tl_potrf<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * TB * TB * 8);
     cudaFuncSetAttribute(k_tl_potrf<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * TB * TB * 4);

@@ -63,7 +63,7 @@ class _Profile(ctypes.Structure):
 _LIB = None
 EXPORTS = ["hif_factor", "hif_apply", "hif_solve", "hif_matvec", "hif_stats", "hif_structure",
            "hif_profile", "hif_kernel_launches", "hif_residual_norms_noalloc", "hif_front_log", "hif_mlp_grad",
-           "hif_mlp_train", "hif_mlp_predict", "hif_free", "hif_last_error"]
+           "hif_mlp_train", "hif_mlp_predict", "hif_factor_batch", "hif_solve_batch", "hif_free", "hif_last_error"]
 
 
 def library_path() -> str:
@@ -108,6 +108,10 @@ def load(build_if_missing: bool = False):
     lib.hif_mlp_train.restype = i
     lib.hif_mlp_predict.argtypes = [vp, i, vp, vp, vp]
     lib.hif_mlp_predict.restype = i
+    lib.hif_factor_batch.argtypes = [i, ctypes.POINTER(_Grid), vp, vp, vp, ctypes.POINTER(_Opts), i, vp]
+    lib.hif_factor_batch.restype = i
+    lib.hif_solve_batch.argtypes = [i, vp, vp, vp, vp, d, i, ctypes.POINTER(_SolveInfo), i]
+    lib.hif_solve_batch.restype = i
     lib.hif_free.argtypes = [vp]
     lib.hif_free.restype = None
     lib.hif_last_error.argtypes = []
@@ -320,3 +324,50 @@ def factor(dim: int, n: int, a_stag, b, eps: float, variant: str = "hifde", prec
                         ctypes.byref(h))
     _check(rc, lib)
     return Factorization(h, lib, (n - 1) ** dim)
+
+
+def factor_batch(problems, eps: float, variant: str = "hifde", precision: str = "fp64", leaf: int = 8,
+                 nthreads: int = 8, big_cell: int = 0):
+    """hif_factor_batch: problems = [(dim, n, a_stag, b), ...], factored
+    concurrently (one stream each); returns one Factorization per problem."""
+    lib = load()
+    m = len(problems)
+    grids = (_Grid * m)(*[_Grid(d, n, leaf, VARIANTS[variant]) for d, n, _, _ in problems])
+    pa = (ctypes.c_void_p * m)(*[_ptr(a) for _, _, a, _ in problems])
+    pb = (ctypes.c_void_p * m)(*[_ptr(b) for _, _, _, b in problems])
+    pe = (ctypes.c_double * m)(*([float(eps)] * m))
+    opts = _Opts(PRECISIONS[precision], 0, ID_MODES["qr"], 10, None, None, 0, big_cell)
+    hs = (ctypes.c_void_p * m)()
+    rc = lib.hif_factor_batch(m, grids, pa, pb, pe, ctypes.byref(opts), nthreads, hs)
+    facts = [Factorization(ctypes.c_void_p(hs[p]), lib, (problems[p][1] - 1) ** problems[p][0]) if hs[p] else None
+             for p in range(m)]
+    if rc != 0:
+        for F in facts:
+            if F is not None:
+                F.free()
+        _check(rc, lib)
+    return facts
+
+
+def solve_batch(facts, rhs_list, tol: float = 1e-12, maxit: int = 1000, nthreads: int = 8):
+    """hif_solve_batch: one (N, nrhs) float64 right-hand side array per
+    factorization, solved concurrently; returns [(x, info dict), ...]."""
+    lib = load()
+    m = len(facts)
+    r2 = [_as_2d(r) for r in rhs_list]
+    xs = [_empty_like(r, q.shape) for r, q in zip(rhs_list, r2)]
+    hs = (ctypes.c_void_p * m)(*[F._live() for F in facts])
+    pr = (ctypes.c_void_p * m)(*[_ptr(q) for q in r2])
+    px = (ctypes.c_void_p * m)(*[_ptr(x) for x in xs])
+    pn = (ctypes.c_int * m)(*[q.shape[1] for q in r2])
+    infos = (_SolveInfo * m)()
+    rc = lib.hif_solve_batch(m, hs, pr, px, pn, tol, maxit, infos, nthreads)
+    if rc != HIF_ERR_NOCONV:
+        _check(rc, lib)
+    out = []
+    for p in range(m):
+        i = infos[p]
+        out.append((xs[p].reshape(rhs_list[p].shape),
+                    dict(iters=i.iters, outer=i.outer, converged=bool(i.converged), relres_max=i.relres_max,
+                         relres_fp64_max=i.relres_fp64_max)))
+    return out

@@ -182,3 +182,20 @@ def workload(name: str):
         a, b = high_contrast_coefficients(3, 128, seed=5, low=1e-2, high=1e2)
         return dict(dim=3, n=128, a_stag=a, b=b, eps=1e-6, nrhs=4)
     raise KeyError(name)
+
+
+def batched_problems(nprob: int = 64, seed: int = 0, nmin: int = 127, nmax: int = 1023, nrhs: int = 32):
+    """Independent 2D problems of the batched workload: interior edge sizes
+    n - 1 = round(exp(U[ln nmin, ln nmax])) (log-uniform), each with its own
+    quantized high-contrast field of contrast 10^k, k uniform in {2, 4, 6}
+    (values 10^(-k/2) and 10^(k/2), the recipe of the 511^2 workload), b = 0.
+    Returns a list of dicts with ``dim, n, a_stag, b, nrhs, seed``."""
+    u = uniform01(seed, 2 * nprob)
+    out = []
+    for p in range(nprob):
+        m = int(round(float(np.exp(np.log(nmin) + u[2 * p] * (np.log(nmax) - np.log(nmin))))))
+        k = 2 * (1 + min(int(u[2 * p + 1] * 3), 2))
+        n = m + 1
+        a, b = high_contrast_coefficients(2, n, seed=1000 + p, low=10.0 ** (-k / 2), high=10.0 ** (k / 2))
+        out.append(dict(dim=2, n=n, a_stag=a, b=b, nrhs=nrhs, seed=1000 + p, contrast=10.0 ** k))
+    return out

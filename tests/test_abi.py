@@ -53,3 +53,12 @@ def test_product_path_does_not_import_oracle():
             if f.endswith((".py", ".cu", ".cpp", ".h", ".cuh")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(from|import)\s+oracle", txt, re.M), f
+
+
+def test_batch_argument_errors():
+    """The batch entry points reject bad arguments before touching a GPU."""
+    from paper_1307_2895_gb300 import hif
+    lib = hif.load()
+    assert lib.hif_factor_batch(-1, None, None, None, None, None, 1, None) == hif.HIF_ERR_ARG
+    assert lib.hif_solve_batch(-1, None, None, None, None, 1e-12, 10, None, 1) == hif.HIF_ERR_ARG
+    assert lib.hif_factor_batch(0, None, None, None, None, None, 1, None) == 0

@@ -11,6 +11,11 @@
   randomized ID (trained on 31^3 rank logs of other fields): |s_L| within 15%
   of the paper's Example 5 value (Table 9, hifde3 at 127^3: 6679), 1e-12
   reached with 4 right-hand sides and re-checked likewise.
+* The batched workload: 64 independent 2D problems (interior edges
+  log-uniform in 127..1023, contrast 1e2 / 1e4 / 1e6, 32 right-hand sides
+  each) factored and solved concurrently through hif_factor_batch /
+  hif_solve_batch: every column reaches 1e-12; the three smallest problems
+  are re-checked in extended precision.
 """
 import os
 
@@ -106,3 +111,24 @@ def test_contrast3d_127_learned(hiflib):
     assert abs(st["root_size"] - 6679) <= 0.15 * 6679, st["root_size"]
     assert info["converged"] and info["relres_max"] <= 1e-12
     assert stencil.residual_ext(3, 128, w["a_stag"], w["b"], f, xh, xl).max() <= 2e-12
+
+
+def test_batched_problems(hiflib):
+    from paper_1307_2895_gb300 import hif
+    probs = inputs.batched_problems(64, seed=0)
+    facts = hif.factor_batch([(p["dim"], p["n"], p["a_stag"], p["b"]) for p in probs], 1e-6,
+                             precision="fp32_apply", nthreads=8)
+    try:
+        rhs = [inputs.rhs(2, p["n"], p["nrhs"], seed=p["seed"]) for p in probs]
+        res = hif.solve_batch(facts, rhs, tol=1e-12, maxit=2000, nthreads=8)
+    finally:
+        for F in facts:
+            F.free()
+    for p, (x, info) in zip(probs, res):
+        assert info["converged"] and info["relres_max"] <= 1e-12, (p["n"], p["contrast"], info)
+    order = sorted(range(len(probs)), key=lambda i: probs[i]["n"])[:3]
+    for i in order:
+        p = probs[i]
+        r = stencil.residual_ext(2, p["n"], p["a_stag"], p["b"], rhs[i], res[i][0])
+        # x_hi alone: within the FP64 floor of the problem (contrast up to 1e6)
+        assert r.max() <= 1e-9
