@@ -25,11 +25,13 @@
 
 namespace hif {
 
-template <typename T, int R>
+// L2: read through L2 only (rows written by other blocks of the same launch).
+template <typename T, int R, bool L2 = false>
 __device__ __forceinline__ void gather(T* dst, const T* x, const int* ids, int n, int nr, int ldx) {
   for (int e = threadIdx.x; e < n * R; e += blockDim.x) {
     const int i = e / R, r = e % R;
-    dst[e] = (r < nr) ? x[(int64_t)ids[i] * ldx + r] : T(0);
+    const T* src = x + (int64_t)ids[i] * ldx + r;
+    dst[e] = (r < nr) ? (L2 ? __ldcg(src) : *src) : T(0);
   }
 }
 
@@ -133,16 +135,18 @@ __device__ __forceinline__ void pdl_wait_then_release() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
-template <typename T, int R>
-__global__ void k_apply_up(const ApplyDesc* __restrict__ blocks, const int* __restrict__ ipool,
-                           const T* __restrict__ fac, T* __restrict__ x, int nr, int ldx,
-                           int is_front, int staged, int* err) {
+// One block of the up sweep (V^T) by the whole thread block.  wait() runs
+// after the block's factor copy has started and before it reads any vector
+// row (the previous level's results); it returns false to skip the block.
+// L2: vector rows are read through L2 only.
+template <typename T, int R, bool L2, typename Wait>
+__device__ void sweep_up_block(const ApplyDesc& bd, const int* __restrict__ ipool, const T* __restrict__ fac,
+                               T* __restrict__ x, int nr, int ldx, int is_front, int staged, int* err,
+                               unsigned char* smem_raw, Wait wait) {
   constexpr int CG = ColGroup<R>::CG, NG = ColGroup<R>::NG;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const ApplyDesc bd = blocks[blockIdx.x];
   const int np = bd.np, nq = bd.nq;
   if (np == 0) {
-    pdl_wait_then_release();
+    wait();
     return;
   }
   const int* idp = ipool + bd.ids;
@@ -153,14 +157,17 @@ __global__ void k_apply_up(const ApplyDesc* __restrict__ blocks, const int* __re
   const T* G = fac + bd.G;
   const T* Tm = is_front ? fac + bd.T : nullptr;
   if (staged) stage_factor<T, R>(sm, bs, Linv, G, Tm, np, nq, is_front);
-  pdl_wait_then_release();
+  const bool go = wait();
   T* xp = sm.xp;
   T* yp = sm.yp;
   T* xq = sm.xq;
-  gather<T, R>(xp, x, idp, np, nr, ldx);
-  if (is_front) gather<T, R>(xq, x, idq, nq, nr, ldx);
+  if (go) {
+    gather<T, R, L2>(xp, x, idp, np, nr, ldx);
+    if (is_front) gather<T, R, L2>(xq, x, idq, nq, nr, ldx);
+  }
   __syncthreads();
   if (staged && !bs.wait(err)) return;
+  if (!go) return;
   if (is_front && nq > 0) {                      // x_p -= T^T x_q
     for (int e = threadIdx.x; e < np * NG; e += blockDim.x) {
       const int i = e / NG, c0 = (e % NG) * CG;
@@ -214,15 +221,26 @@ __global__ void k_apply_up(const ApplyDesc* __restrict__ blocks, const int* __re
 }
 
 template <typename T, int R>
-__global__ void k_apply_down(const ApplyDesc* __restrict__ blocks, const int* __restrict__ ipool,
-                             const T* __restrict__ fac, T* __restrict__ x, int nr, int ldx,
-                             int is_front, int staged, int* err) {
-  constexpr int CG = ColGroup<R>::CG, NG = ColGroup<R>::NG;
+__global__ void k_apply_up(const ApplyDesc* __restrict__ blocks, const int* __restrict__ ipool,
+                           const T* __restrict__ fac, T* __restrict__ x, int nr, int ldx,
+                           int is_front, int staged, int* err) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const ApplyDesc bd = blocks[blockIdx.x];
+  sweep_up_block<T, R, false>(bd, ipool, fac, x, nr, ldx, is_front, staged, err, smem_raw, [] {
+    pdl_wait_then_release();
+    return true;
+  });
+}
+
+// One block of the down sweep (V), as sweep_up_block.
+template <typename T, int R, bool L2, typename Wait>
+__device__ void sweep_down_block(const ApplyDesc& bd, const int* __restrict__ ipool, const T* __restrict__ fac,
+                                 T* __restrict__ x, int nr, int ldx, int is_front, int staged, int* err,
+                                 unsigned char* smem_raw, Wait wait) {
+  constexpr int CG = ColGroup<R>::CG, NG = ColGroup<R>::NG;
   const int np = bd.np, nq = bd.nq;
   if (np == 0) {
-    pdl_wait_then_release();
+    wait();
     return;
   }
   const int* idp = ipool + bd.ids;
@@ -233,14 +251,17 @@ __global__ void k_apply_down(const ApplyDesc* __restrict__ blocks, const int* __
   const T* G = fac + bd.G;
   const T* Tm = is_front ? fac + bd.T : nullptr;
   if (staged) stage_factor<T, R>(sm, bs, Linv, G, Tm, np, nq, is_front);
-  pdl_wait_then_release();
+  const bool go = wait();
   T* xp = sm.xp;
   T* zp = sm.yp;
   T* xq = sm.xq;
-  gather<T, R>(xp, x, idp, np, nr, ldx);
-  gather<T, R>(xq, x, idq, nq, nr, ldx);
+  if (go) {
+    gather<T, R, L2>(xp, x, idp, np, nr, ldx);
+    gather<T, R, L2>(xq, x, idq, nq, nr, ldx);
+  }
   __syncthreads();
   if (staged && !bs.wait(err)) return;
+  if (!go) return;
   if (nq > 0) {                                  // w = x_p - G^T x_q (in place)
     for (int e = threadIdx.x; e < np * NG; e += blockDim.x) {
       const int i = e / NG, c0 = (e % NG) * CG;
@@ -290,6 +311,18 @@ __global__ void k_apply_down(const ApplyDesc* __restrict__ blocks, const int* __
         if (c0 + c < nr) x[(int64_t)idq[s2] * ldx + c0 + c] = xq[s2 * R + c0 + c] - acc[c];
     }
   }
+}
+
+template <typename T, int R>
+__global__ void k_apply_down(const ApplyDesc* __restrict__ blocks, const int* __restrict__ ipool,
+                             const T* __restrict__ fac, T* __restrict__ x, int nr, int ldx,
+                             int is_front, int staged, int* err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const ApplyDesc bd = blocks[blockIdx.x];
+  sweep_down_block<T, R, false>(bd, ipool, fac, x, nr, ldx, is_front, staged, err, smem_raw, [] {
+    pdl_wait_then_release();
+    return true;
+  });
 }
 
 // ---- forward operator F (used by the error estimates; not staged) ----------
