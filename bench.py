@@ -136,9 +136,10 @@ def oracle_sample_step():
     return (n - 1) ** 2 * 1, dt, iters[0], rel[0]
 
 
-def cpu_baseline(steps: int = 1):
+def cpu_baseline(min_secs: float = 10.0):
+    """The oracle on host cores, repeated until about ``min_secs`` of CPU work."""
     dofs, secs, its, rels = 0, 0.0, [], []
-    for _ in range(steps):
+    while secs < min_secs:
         d, s, it, rel = oracle_sample_step()
         dofs += d
         secs += s
@@ -146,7 +147,7 @@ def cpu_baseline(steps: int = 1):
         rels.append(rel)
     return {"value": dofs / secs, "unit": "DOF/s", "cores": 1, "kind": "oracle",
             "sample": f"FP64 numpy oracle, same recipe on a {ORACLE_SAMPLE_N - 1}^2 grid, 1 RHS, factor + PCG "
-                      f"to {ORACLE_SAMPLE_TOL:g} (its FP64 residual floor), {steps} step(s), "
+                      f"to {ORACLE_SAMPLE_TOL:g} (its FP64 residual floor), {len(its)} step(s), "
                       f"{secs:.1f} s, iters {its}, relres {max(rels):.1e}"}
 
 
@@ -297,7 +298,7 @@ def run_gpu(args, rank, world, local_rank):
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
         try:
-            cpu = cpu_baseline(1)
+            cpu = cpu_baseline()
         except Exception as exc:  # the oracle leg must not hide the GPU result
             cpu = {"error": repr(exc)}
 
