@@ -387,6 +387,109 @@ def run_batched(args):
     return 0
 
 
+def _tf32_peak():
+    """Dense TF32 tensor peak: the measured bf16 burst GEMM rate times the
+    nominal TF32 / BF16 ratio (1.1 / 2.25 PFLOP/s dense)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["bf16_tflops"]) * 1.1 / 2.25, "measured bf16 x nominal tf32/bf16"
+    except (OSError, KeyError, ValueError):
+        return 1900.0 * 1.1 / 2.25, "fallback bf16 x nominal tf32/bf16"
+
+
+def tc_roofline(split: int = 3, nb: int = 16, m: int = 1024, k: int = 2048, reps: int = 5):
+    """The tensor-core Schur update (hif_schur_update_f32) timed alone with CUDA
+    events on its stream: nb blocks U -= G G^T, G m x k (inputs 192 MB, beyond
+    L2).  Useful work m (m + 1) k flops per block (the lower triangle and the
+    diagonal; the mirror is a copy); the tensor pipe issues 1, 3 or 6 TF32
+    products for each (split = 1, 2, 3 parts per operand value), over the
+    128 x 64 output blocks on and below the diagonal."""
+    import torch
+    from paper_1307_2895_gb300 import hif
+    dev = torch.device("cuda", 0)
+    st = torch.cuda.Stream(device=dev)
+    gen = torch.Generator(device=dev).manual_seed(0)
+    G = torch.randn((nb, m, k), device=dev, generator=gen, dtype=torch.float32)
+    U0 = torch.randn((nb, m, m), device=dev, generator=gen, dtype=torch.float32)
+    U = U0.clone()
+    with torch.cuda.stream(st):
+        hif.schur_update(G, U, split=split, stream=st)        # warm-up
+        ms = []
+        for _ in range(reps):
+            U.copy_(U0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            hif.schur_update(G, U, split=split, stream=st)
+            e1.record(st)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+    t = sorted(ms)[len(ms) // 2] / 1e3
+    rb = (m + 63) // 64
+    issued_blocks = sum(min(2 * a + 2, rb) for a in range((rb + 1) // 2))   # (128-row, 64-col) blocks run
+    useful = nb * m * (m + 1) * k
+    issued = nb * issued_blocks * 128 * 64 * 2 * k * {1: 1, 2: 3, 3: 6}[split]
+    peak, how = _tf32_peak()
+    achieved = issued / t / 1e12
+    return {"kernel": "k_tc_syrk_flat", "shape": f"{nb} x (U {m}x{m} -= G G^T, G {m}x{k})", "split": split,
+            "ms": t * 1e3, "useful_fp32_tflops": useful / t / 1e12,
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "peak_source": how, "traffic": None}}
+
+
+def run_3d(args):
+    """A 3D workload: factor + 4-RHS PCG to 1e-12 per step, wall clock with a
+    device synchronize on both sides (the factorization's host work included);
+    one JSON line with the factor and solve times, iterations and |s_L|, and
+    in the mixed mode the tensor-core Schur update timed alone."""
+    import torch
+    from paper_1307_2895_gb300 import hif, inputs
+    hif.load()
+    w = inputs.workload(args.workload3d)
+    n, nrhs = w["n"], w["nrhs"]
+    eps = args.eps if args.eps > 0 else w["eps"]
+    dev = torch.device("cuda", 0)
+    st = torch.cuda.Stream(device=dev)
+    a = torch.from_numpy(w["a_stag"]).to(dev)
+    b = torch.from_numpy(w["b"]).to(dev)
+    f = torch.from_numpy(inputs.rhs(3, n, nrhs, seed=0)).to(dev)
+    fac, sol, infos, stats = [], [], [], []
+    for step in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        G = hif.factor(3, n, a, b, eps, precision=args.precision, stream=st, tensor_cores=args.tensor_cores)
+        try:
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            x, info = G.solve(f, tol=TOL, maxit=500)
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            s = G.stats()
+        finally:
+            G.free()
+        if step >= args.warmup:
+            fac.append(t1 - t0)
+            sol.append(t2 - t1)
+            infos.append(info)
+            stats.append(s)
+    t = sum(fac) + sum(sol)
+    N = (n - 1) ** 3
+    line = {"metric": "factor+solve DOF x RHS/s at rel. residual 1e-12 (3D)",
+            "value": N * nrhs * args.steps / t, "unit": "DOF*RHS/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+            "dtype": {"fp64": "f64", "mixed": "f32+f64", "fp32_apply": "f64+f32"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": f"{args.workload3d}: {n - 1}^3, eps={eps:g}, {nrhs} RHS",
+                       "precision": args.precision, "tensor_cores": args.tensor_cores},
+            "factor_ms": 1e3 * sum(fac) / len(fac), "solve_ms": 1e3 * sum(sol) / len(sol),
+            "t_fronts_ms": stats[-1]["t_fronts_ms"], "root_size": stats[-1]["root_size"],
+            "cg_iters": infos[-1]["iters"], "relres_max": max(i["relres_max"] for i in infos),
+            "converged": all(i["converged"] for i in infos)}
+    if args.precision == "mixed" and args.tensor_cores >= 0:
+        line["tensor_core_kernel"] = tc_roofline(split=args.tensor_cores or 3)
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_solve_only(args):
     """Factor the workload and run one 8-RHS solve, this many times: the
     command ncu captures the CG vector kernels and the factor kernels of."""
@@ -445,6 +548,13 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--batched", action="store_true",
                     help="time the batched workload (64 independent problems) instead of the headline one")
+    ap.add_argument("--workload3d", default="", choices=["", "laplace3d_n64", "contrast3d_n128"],
+                    help="time a 3D workload (factor + PCG) instead of the headline one")
+    ap.add_argument("--eps", type=float, default=0.0, help="3D workloads: eps (default: the workload's)")
+    ap.add_argument("--tensor-cores", type=int, default=0, choices=[0, 1, 2, 3, -1],
+                    help="mixed precision: 0 or 3 three-part TF32 split, 2 two-part, 1 plain TF32, -1 SIMT FP32")
+    ap.add_argument("--tc-roofline", action="store_true",
+                    help="time the tensor-core Schur update alone (one JSON line) and exit")
     ap.add_argument("--ncu-solve", type=int, default=0,
                     help="profiling helper: this many factor + 8-RHS solves of the workload, then exit")
     ap.add_argument("--ncu-apply", type=int, default=0,
@@ -456,6 +566,13 @@ def main():
         return run_solve_only(args)
     if args.batched:
         return run_batched(args)
+    if args.workload3d:
+        return run_3d(args)
+    if args.tc_roofline:
+        from paper_1307_2895_gb300 import hif
+        hif.load()
+        print(json.dumps(tc_roofline(split=args.tensor_cores if args.tensor_cores > 0 else 3)), flush=True)
+        return 0
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

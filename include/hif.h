@@ -99,6 +99,13 @@ typedef struct hif_opts {
                            multi-block front kernels (tiled sketch, residual
                            check and Lemma 2.4 products); 0 -> 192, < 0 ->
                            never.  Same result up to rounding order.           */
+  int tensor_cores;     /* HIF_PREC_MIXED: products of the tiled elimination
+                           (panel solves, trailing updates, Schur complement)
+                           on the tensor cores in TF32 with FP32 accumulation,
+                           each operand split into TF32 parts: 0 -> three
+                           parts (exact split, about FP32 accuracy), 2 -> two
+                           parts (about 2^-21), 1 -> plain TF32, < 0 -> FP32 on
+                           the SIMT pipes.  Ignored in the FP64 modes.          */
 } hif_opts;
 
 typedef struct hif_handle hif_handle;
@@ -253,6 +260,21 @@ int hif_residual_norms_noalloc(int dim, int n, const double* a_stag, const doubl
  * pointers; nothing is written if cap < count; *count receives the count. */
 int hif_front_log(const hif_handle* h, float* feats, int32_t* ranks, int32_t* sizes, long long cap,
                   long long* count);
+
+/* hif_schur_update_f32 -- U_b <- U_b - G_b G_b^T for nb dense FP32 blocks:
+ * the Schur complement update of Lemma 2.1 (A_qq - A_qp A_pp^{-1} A_pq with
+ * G = A_qp L^{-T}, L L^T = A_pp), on the tensor cores (tcgen05, TF32 inputs,
+ * FP32 accumulation).  split = number of TF32 parts each operand value is
+ * cut into by repeated round-to-nearest: 3 (exact, six products, about FP32
+ * accuracy), 2 (three products, about 2^-21), 1 (plain TF32).  G: nb blocks
+ * of m x k, row-major, block b at G + b m k; U: nb blocks of m x m,
+ * row-major, block b at U + b m m, overwritten (whole block, both
+ * triangles).  Device pointers owned by the caller; work is issued on
+ * `stream` (NULL: the default stream) and the call returns after it has
+ * completed.  HIF_ERR_ARG: nb, m or k negative, nb > 65535, split not in
+ * 1..3, or a NULL pointer with nb m > 0; HIF_ERR_TIMEOUT: a bounded wait for
+ * the MMAs ran out. */
+int hif_schur_update_f32(int nb, int m, int k, const float* G, float* U, int split, void* stream);
 
 /* hif_mlp_grad -- loss and gradient (mean over the n samples) at params (FP32). */
 int hif_mlp_grad(const float* X, const float* target, int n, const float* params, float* grad,

@@ -163,6 +163,7 @@ struct hif_handle {
   int skip_levels = 0;
   int big_cell = 192;   // cells with at least this many interior DOFs use the tiled elimination
   bool coop_qr = true;  // large fronts: pivoted QR by co-resident block groups
+  int tc_split = 3;     // FP32 tiled elimination on the tensor cores: TF32 parts per value (1..3), 0 = SIMT
   int id_mode = HIF_ID_QR;
   int oversample = 10;
   unsigned long long seed = 0;
@@ -406,7 +407,8 @@ struct Factorizer {
       t.Lp = c.fac + cell_fac_L(c.nI, c.nB);
     }
     upload(tdbuf, td, st);
-    launch_tiled_elim<U>(tdbuf.as<TDesc>(), (int)big.size(), max_bI, max_bB, work, fac, status.as<int>(), tau, st);
+    launch_tiled_elim<U>(tdbuf.as<TDesc>(), (int)big.size(), max_bI, max_bB, work, fac, status.as<int>(), tau, st,
+                         h->tc_split);
   }
 
   static int max_front_size(const std::vector<CellDesc>& cd) {
@@ -553,6 +555,7 @@ struct Factorizer {
     h->fallback = hs2[3];
     if (hs & 1) throw HifError(HIF_ERR_NOT_SPD, "non-positive pivot in a diagonal-block Cholesky");
     if (hs & 16) throw HifError(HIF_ERR_TIMEOUT, "a bounded group-barrier wait of the multi-block pivoted QR ran out");
+    if (hs & 32) throw HifError(HIF_ERR_TIMEOUT, "a bounded wait for tensor-core MMAs ran out");
   }
 
   // One launch for every front of level l + 1/2, then read back ranks and
@@ -670,7 +673,7 @@ struct Factorizer {
       if (!td.empty()) {
         upload(d_td, td, st);
         launch_tiled_elim<T>(d_td.as<TDesc>(), (int)td.size(), max_nR, max_k, fwork.as<T>(), sw.fac.as<T>(),
-                             status.as<int>(), tau, st);
+                             status.as<int>(), tau, st, h->tc_split);
       }
       launch_bigfront_scatter<T>(d_fd, d_big.as<int>(), nbig, d_cdesc, d_ip, obuf.as<int>(), fwork.as<T>(),
                                  cwork.as<T>(), max_k, st);
@@ -1230,6 +1233,7 @@ int hif_factor(const hif_grid* grid, const double* a_stag, const double* b, cons
     h->oversample = (opts && opts->oversample > 0) ? opts->oversample : 10;
     h->seed = opts ? opts->seed : 0;
     if (opts && opts->big_cell != 0) h->big_cell = opts->big_cell < 0 ? 0x7fffffff : opts->big_cell;
+    if (opts) h->tc_split = opts->tensor_cores < 0 ? 0 : opts->tensor_cores == 0 ? 3 : std::min(opts->tensor_cores, 3);
     if (h->id_mode == HIF_ID_LEARNED && !(opts && opts->rank_model))
       throw HifError(HIF_ERR_ARG, "HIF_ID_LEARNED needs opts.rank_model");
     h->st = opts ? (cudaStream_t)opts->stream : nullptr;
@@ -1576,6 +1580,29 @@ int hif_mlp_train(const float* X, const float* target, int n, float* params, int
       CU(cudaMemcpyAsync(loss_hist, lossd.p, sizeof(float) * steps, cudaMemcpyDeviceToDevice, st));
     CU(cudaGetLastError());
     CU(cudaStreamSynchronize(st));
+  } catch (const HifError& e) {
+    return set_error(e.code, e.msg);
+  }
+  return HIF_OK;
+}
+
+int hif_schur_update_f32(int nb, int m, int k, const float* G, float* U, int split, void* stream) {
+  if (nb < 0 || m < 0 || k < 0 || nb > 65535 || split < 1 || split > 3)
+    return set_error(HIF_ERR_ARG, "bad sizes or split");
+  if ((int64_t)nb * m == 0) return HIF_OK;
+  if (!U || (!G && k > 0)) return set_error(HIF_ERR_ARG, "NULL pointer");
+  cudaStream_t st = (cudaStream_t)stream;
+  try {
+    DevBuf status;
+    status.alloc(sizeof(int), st);
+    CU(cudaMemsetAsync(status.p, 0, sizeof(int), st));
+    tc_syrk_flat(nb, m, k, G, U, split, status.as<int>(), st);
+    CU(cudaGetLastError());
+    note_launches(1);
+    int hs = 0;
+    CU(cudaMemcpyAsync(&hs, status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    if (hs & 32) throw HifError(HIF_ERR_TIMEOUT, "a bounded wait for tensor-core MMAs ran out");
   } catch (const HifError& e) {
     return set_error(e.code, e.msg);
   }

@@ -21,7 +21,15 @@ void launch_cell_factor(const CellDesc* cells, const int* sel, int ncells, T* wo
 // tiled multi-block elimination of the problems td[0..n) (kernels_tiled.cu)
 template <typename T>
 void launch_tiled_elim(const TDesc* td, int n, int max_nI, int max_nB, T* work, T* fac, int* status, double tau,
-                       cudaStream_t st);
+                       cudaStream_t st, int tc_split = 0);
+// tensor-core (tcgen05 TF32) panel solve + trailing update of panel p, and
+// Schur complement, of the FP32 tiled elimination; return launches made
+// (parts: TF32 parts per operand value, 1..3)
+long long tc_panel(const TDesc* td, int nsel, int p, int P, int max_nI, int max_nB, float* work, int parts,
+                   int* status, cudaStream_t st);
+long long tc_syrk(const TDesc* td, int nsel, int max_nB, float* work, int parts, int* status, cudaStream_t st);
+// U_b -= G_b G_b^T on nb contiguous blocks (G_b m x k, U_b m x m, row-major)
+void tc_syrk_flat(int nb, int m, int k, const float* G, float* U, int parts, int* status, cudaStream_t st);
 template <typename T>
 void launch_front(const FrontDesc* fronts, int nfronts, const CellDesc* cells, const int* ipool, int* obuf,
                   T* fwork,

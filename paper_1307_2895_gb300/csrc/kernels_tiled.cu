@@ -18,6 +18,7 @@
 // Each problem is described by a TDesc (a large cell, or the redundant block
 // of a large front).
 #include <atomic>
+#include <type_traits>
 
 #include "hif_internal.h"
 #include "blockops.cuh"
@@ -26,27 +27,6 @@
 
 namespace hif {
 
-
-struct TCell {
-  int nI, nB, P, RB;
-  int64_t FII, FBI, FBB, X, Linv, G, Lp;
-};
-
-__device__ __forceinline__ TCell tcell(const TDesc& d) {
-  TCell c;
-  c.nI = d.nI;
-  c.nB = d.nB;
-  c.P = (d.nI + TB - 1) / TB;
-  c.RB = (d.nB + TB - 1) / TB;
-  c.FII = d.FII;
-  c.FBI = d.FBI;
-  c.FBB = d.FBB;
-  c.X = d.X;
-  c.Linv = d.Linv;
-  c.G = d.G;
-  c.Lp = d.Lp;
-  return c;
-}
 
 // original diagonal of F_II (pivot safeguard of the mixed mode)
 template <typename T>
@@ -283,7 +263,11 @@ __global__ void k_tl_pack(const TDesc* __restrict__ td,
 
 template <typename T>
 void launch_tiled_elim(const TDesc* td, int nsel, int max_nI, int max_nB, T* work, T* fac, int* status,
-                       double tau, cudaStream_t st) {
+                       double tau, cudaStream_t st, int tc_split) {
+  // FP32 with tc_split > 0: the panel solves, trailing updates and the Schur
+  // complement run on the tensor cores (kernels_tc.cu), each operand split
+  // into tc_split TF32 parts
+  const bool tc = std::is_same<T, float>::value && tc_split > 0;
   if (nsel == 0 || max_nI == 0) return;
   const int P = (max_nI + TB - 1) / TB, RB = (max_nB + TB - 1) / TB;
   const int psmem = 2 * TB * TB * (int)sizeof(T);
@@ -300,13 +284,20 @@ void launch_tiled_elim(const TDesc* td, int nsel, int max_nI, int max_nB, T* wor
   }
   for (int p = 0; p < P; ++p) {
     k_tl_potrf<T><<<nsel, TT, psmem, st>>>(td, p, work, fac, status, (T)tau);
+    ++nl;
+    if (tc) {
+      nl += tc_panel(td, nsel, p, P, max_nI, max_nB, reinterpret_cast<float*>(work), tc_split, status, st);
+      continue;
+    }
     const int below = P - p - 1;
     if (below + RB > 0) k_tl_trsm<T><<<dim3(below + RB, nsel), TT, 0, st>>>(td, p, work);
     const int64_t nup = (int64_t)below * (below + 1) / 2 + (int64_t)RB * below;
     if (nup > 0) k_tl_update<T><<<dim3((unsigned)nup, nsel), TT, 0, st>>>(td, p, work);
-    nl += 1 + (below + RB > 0) + (nup > 0);
+    nl += (below + RB > 0) + (nup > 0);
   }
-  if (RB > 0) {
+  if (tc) {
+    nl += tc_syrk(td, nsel, max_nB, reinterpret_cast<float*>(work), tc_split, status, st);
+  } else if (RB > 0) {
     k_tl_syrk<T><<<dim3((unsigned)((int64_t)RB * (RB + 1) / 2), nsel), TT, 0, st>>>(td, work);
     ++nl;
   }
@@ -320,7 +311,8 @@ void launch_tiled_elim(const TDesc* td, int nsel, int max_nI, int max_nB, T* wor
   note_launches(nl);
 }
 
-template void launch_tiled_elim<double>(const TDesc*, int, int, int, double*, double*, int*, double, cudaStream_t);
-template void launch_tiled_elim<float>(const TDesc*, int, int, int, float*, float*, int*, double, cudaStream_t);
+template void launch_tiled_elim<double>(const TDesc*, int, int, int, double*, double*, int*, double, cudaStream_t,
+                                        int);
+template void launch_tiled_elim<float>(const TDesc*, int, int, int, float*, float*, int*, double, cudaStream_t, int);
 
 }  // namespace hif

@@ -63,6 +63,29 @@ __device__ __forceinline__ void tile_mma(TileSmem<T>& sm, T (&acc)[4][4], int K,
   }
 }
 
+// One tiled elimination problem (a large cell, or the redundant block of a
+// large front) with its tile counts: P panels of F_II, RB row tiles of F_BI.
+struct TCell {
+  int nI, nB, P, RB;
+  int64_t FII, FBI, FBB, X, Linv, G, Lp;
+};
+
+__device__ __forceinline__ TCell tcell(const TDesc& d) {
+  TCell c;
+  c.nI = d.nI;
+  c.nB = d.nB;
+  c.P = (d.nI + TB - 1) / TB;
+  c.RB = (d.nB + TB - 1) / TB;
+  c.FII = d.FII;
+  c.FBI = d.FBI;
+  c.FBB = d.FBB;
+  c.X = d.X;
+  c.Linv = d.Linv;
+  c.G = d.G;
+  c.Lp = d.Lp;
+  return c;
+}
+
 template <typename T>
 __device__ __forceinline__ void zero_acc(T (&acc)[4][4]) {
 #pragma unroll

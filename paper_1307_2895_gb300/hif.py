@@ -37,7 +37,7 @@ class _Grid(ctypes.Structure):
 class _Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("skip_levels", ctypes.c_int), ("id_mode", ctypes.c_int),
                 ("oversample", ctypes.c_int), ("stream", ctypes.c_void_p), ("rank_model", ctypes.c_void_p),
-                ("seed", ctypes.c_ulonglong), ("big_cell", ctypes.c_int)]
+                ("seed", ctypes.c_ulonglong), ("big_cell", ctypes.c_int), ("tensor_cores", ctypes.c_int)]
 
 
 class _SolveInfo(ctypes.Structure):
@@ -63,7 +63,7 @@ class _Profile(ctypes.Structure):
 _LIB = None
 EXPORTS = ["hif_factor", "hif_apply", "hif_solve", "hif_matvec", "hif_stats", "hif_structure",
            "hif_profile", "hif_kernel_launches", "hif_residual_norms_noalloc", "hif_front_log", "hif_mlp_grad",
-           "hif_mlp_train", "hif_mlp_predict", "hif_factor_batch", "hif_solve_batch", "hif_free", "hif_last_error"]
+           "hif_mlp_train", "hif_mlp_predict", "hif_schur_update_f32", "hif_factor_batch", "hif_solve_batch", "hif_free", "hif_last_error"]
 
 
 def library_path() -> str:
@@ -108,6 +108,8 @@ def load(build_if_missing: bool = False):
     lib.hif_mlp_train.restype = i
     lib.hif_mlp_predict.argtypes = [vp, i, vp, vp, vp]
     lib.hif_mlp_predict.restype = i
+    lib.hif_schur_update_f32.argtypes = [i, i, i, vp, vp, i, vp]
+    lib.hif_schur_update_f32.restype = i
     lib.hif_factor_batch.argtypes = [i, ctypes.POINTER(_Grid), vp, vp, vp, ctypes.POINTER(_Opts), i, vp]
     lib.hif_factor_batch.restype = i
     lib.hif_solve_batch.argtypes = [i, vp, vp, vp, vp, d, i, ctypes.POINTER(_SolveInfo), i]
@@ -311,14 +313,28 @@ def mlp_predict(X, params, stream=None):
     return y
 
 
+def schur_update(G, U, split: int = 3, stream=None):
+    """hif_schur_update_f32: U_b -= G_b G_b^T in place on the tensor cores
+    (CUDA float32 tensors G of shape (nb, m, k) and U of shape (nb, m, m))."""
+    lib = load()
+    nb, m, k = G.shape
+    if tuple(U.shape) != (nb, m, m):
+        raise ValueError("U must have shape (nb, m, m)")
+    _check(lib.hif_schur_update_f32(nb, m, k, _ptr(G, "float32"), _ptr(U, "float32"), split,
+                                    _stream_ptr(stream)), lib)
+    return U
+
+
 def factor(dim: int, n: int, a_stag, b, eps: float, variant: str = "hifde", precision: str = "fp64",
            leaf: int = 8, skip_levels: int = 0, stream=None, id_mode: str = "qr", rank_model=None,
-           oversample: int = 10, seed: int = 0, big_cell: int = 0) -> Factorization:
-    """hif_factor: MF or HIF-DE of the stencil operator defined by (a_stag, b)."""
+           oversample: int = 10, seed: int = 0, big_cell: int = 0, tensor_cores: int = 0) -> Factorization:
+    """hif_factor: MF or HIF-DE of the stencil operator defined by (a_stag, b).
+    tensor_cores (mixed precision): 0 three-part TF32 split (about FP32),
+    2 two-part, 1 plain TF32, -1 FP32 on the SIMT pipes."""
     lib = load()
     grid = _Grid(dim, n, leaf, VARIANTS[variant])
     opts = _Opts(PRECISIONS[precision], skip_levels, ID_MODES[id_mode], oversample, _stream_ptr(stream),
-                 _ptr(rank_model, "float32"), seed, big_cell)
+                 _ptr(rank_model, "float32"), seed, big_cell, tensor_cores)
     h = ctypes.c_void_p()
     rc = lib.hif_factor(ctypes.byref(grid), _ptr(a_stag), _ptr(b), None, float(eps), ctypes.byref(opts),
                         ctypes.byref(h))
@@ -327,7 +343,7 @@ def factor(dim: int, n: int, a_stag, b, eps: float, variant: str = "hifde", prec
 
 
 def factor_batch(problems, eps: float, variant: str = "hifde", precision: str = "fp64", leaf: int = 8,
-                 nthreads: int = 8, big_cell: int = 0):
+                 nthreads: int = 8, big_cell: int = 0, tensor_cores: int = 0):
     """hif_factor_batch: problems = [(dim, n, a_stag, b), ...], factored
     concurrently (one stream each); returns one Factorization per problem."""
     lib = load()
@@ -336,7 +352,7 @@ def factor_batch(problems, eps: float, variant: str = "hifde", precision: str = 
     pa = (ctypes.c_void_p * m)(*[_ptr(a) for _, _, a, _ in problems])
     pb = (ctypes.c_void_p * m)(*[_ptr(b) for _, _, _, b in problems])
     pe = (ctypes.c_double * m)(*([float(eps)] * m))
-    opts = _Opts(PRECISIONS[precision], 0, ID_MODES["qr"], 10, None, None, 0, big_cell)
+    opts = _Opts(PRECISIONS[precision], 0, ID_MODES["qr"], 10, None, None, 0, big_cell, tensor_cores)
     hs = (ctypes.c_void_p * m)()
     rc = lib.hif_factor_batch(m, grids, pa, pb, pe, ctypes.byref(opts), nthreads, hs)
     facts = [Factorization(ctypes.c_void_p(hs[p]), lib, (problems[p][1] - 1) ** problems[p][0]) if hs[p] else None

@@ -62,3 +62,15 @@ def test_batch_argument_errors():
     assert lib.hif_factor_batch(-1, None, None, None, None, None, 1, None) == hif.HIF_ERR_ARG
     assert lib.hif_solve_batch(-1, None, None, None, None, 1e-12, 10, None, 1) == hif.HIF_ERR_ARG
     assert lib.hif_factor_batch(0, None, None, None, None, None, 1, None) == 0
+
+
+def test_schur_update_argument_errors_without_gpu():
+    """hif_schur_update_f32 rejects bad sizes and splits before any CUDA call."""
+    lib = hif.load()
+    assert lib.hif_schur_update_f32(1, 4, 4, None, None, 0, None) == hif.HIF_ERR_ARG
+    assert lib.hif_schur_update_f32(1, 4, 4, None, None, 4, None) == hif.HIF_ERR_ARG
+    assert lib.hif_schur_update_f32(-1, 4, 4, None, None, 3, None) == hif.HIF_ERR_ARG
+    assert lib.hif_schur_update_f32(70000, 4, 4, None, None, 3, None) == hif.HIF_ERR_ARG
+    assert lib.hif_schur_update_f32(1, 4, 4, None, None, 3, None) == hif.HIF_ERR_ARG   # NULL U
+    assert lib.hif_schur_update_f32(3, 0, 4, None, None, 3, None) == hif.HIF_OK        # nothing to do
+
