@@ -256,23 +256,33 @@ struct TcCta {
   // acc = sum_{k < K} fa(r, k) fb(q, k).  BKC: fb is read k-fastest across
   // threads (operand stored k-contiguous), else q-fastest.
   template <bool BKC, typename FA, typename FB>
+  __device__ __forceinline__ void load_chunk(int K, int k0, FA& fa, FB& fb, float (&va)[kPerThreadA],
+                                             float (&vb)[kPerThreadB]) {
+#pragma unroll
+    for (int i = 0; i < kPerThreadA; ++i) {
+      const int e = threadIdx.x + kThreads * i, r = e >> 5, k = k0 + (e & 31);
+      va[i] = k < K ? fa(r, k) : 0.f;
+    }
+#pragma unroll
+    for (int i = 0; i < kPerThreadB; ++i) {
+      const int e = threadIdx.x + kThreads * i;
+      const int q = BKC ? (e >> 5) : (e & 63), k = k0 + (BKC ? (e & 31) : (e >> 6));
+      vb[i] = k < K ? fb(q, k) : 0.f;
+    }
+  }
+
+  // acc = sum_{k < K} fa(r, k) fb(q, k).  BKC: fb is read k-fastest across
+  // threads (operand stored k-contiguous), else q-fastest.  The global loads
+  // of chunk ch + 1 are issued right after chunk ch's MMAs, so they are in
+  // flight while those MMAs run and chunk ch - 1 is drained.
+  template <bool BKC, typename FA, typename FB>
   __device__ void product(int K, FA fa, FB fb) {
     const int nch = K > 0 ? (K + kChunk - 1) / kChunk : 1;
     const uint64_t dA = sw128_desc(su32(ring)), dB = sw128_desc(su32(ring) + PARTS * kABytes);
+    float va[kPerThreadA], vb[kPerThreadB];
+    load_chunk<BKC>(K, 0, fa, fb, va, vb);
     for (int ch = 0; ch < nch; ++ch) {
-      const int s = ch & 1, k0 = ch * kChunk;
-      float va[kPerThreadA], vb[kPerThreadB];
-#pragma unroll
-      for (int i = 0; i < kPerThreadA; ++i) {
-        const int e = threadIdx.x + kThreads * i, r = e >> 5, k = k0 + (e & 31);
-        va[i] = k < K ? fa(r, k) : 0.f;
-      }
-#pragma unroll
-      for (int i = 0; i < kPerThreadB; ++i) {
-        const int e = threadIdx.x + kThreads * i;
-        const int q = BKC ? (e >> 5) : (e & 63), k = k0 + (BKC ? (e & 31) : (e >> 6));
-        vb[i] = k < K ? fb(q, k) : 0.f;
-      }
+      const int s = ch & 1;
       // stage s was last read by the MMAs of chunk ch - 2, drained (waited
       // for) by every thread in the previous iteration
       uint8_t* st = ring + s * kStage;
@@ -301,6 +311,7 @@ struct TcCta {
                      dB + so + (uint64_t)((Pairs<PARTS>::b(t) * kBBytes + 32 * j) >> 4), t > 0 ? 1u : 0u);
         mma_commit(su32(bars + s));
       }
+      if (ch + 1 < nch) load_chunk<BKC>(K, (ch + 1) * kChunk, fa, fb, va, vb);
       if (ch >= 1) drain(ch - 1);
     }
     drain(nch - 1);
