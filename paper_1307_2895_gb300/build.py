@@ -18,8 +18,10 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libhif.so")
 SOURCES = ["kernels_factor.cu", "kernels_apply.cu", "kernels_solve.cu", "hif_api.cu", "geometry.cpp",
-           "noalloc.cu", "kernels_mlp.cu", "kernels_tiled.cu", "kernels_bigfront.cu", "kernels_tc.cu"]
-HEADERS = ["hif_internal.h", "kernels.h", "blockops.cuh", "geometry.h", "tile_mma.cuh", "front_common.cuh"]
+           "noalloc.cu", "kernels_mlp.cu", "kernels_tiled.cu", "kernels_bigfront.cu", "kernels_tc.cu",
+           "host_pool.cpp"]
+HEADERS = ["hif_internal.h", "kernels.h", "blockops.cuh", "geometry.h", "tile_mma.cuh", "front_common.cuh",
+           "host_pool.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

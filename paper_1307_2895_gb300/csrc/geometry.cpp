@@ -15,6 +15,8 @@
 #include <algorithm>
 #include <cmath>
 
+#include "host_pool.h"
+
 namespace hif {
 
 void Geometry::init(int dim_, int n_, int leaf_) {
@@ -83,36 +85,48 @@ void build_cells(const Geometry& G, int l, const std::vector<int>& alive, std::v
   const int ncells = G.ncells(l);
   cells.resize(ncells);
   const std::vector<int>& cl = G.cls[l];
-  // count, size every list once, then fill (alive is ascending, so are I and B)
-  std::vector<int> nI(ncells, 0), nB(ncells, 0);
-  for (int g : alive) {
-    const CellSpan sp = cell_span(G, cl, g);
-    if (sp.interior) { ++nI[lin_index(sp.lo, G.dim, nc)]; continue; }
-    int iv[3];
-    for (iv[2] = sp.lo[2]; iv[2] <= sp.hi[2]; ++iv[2])
-      for (iv[1] = sp.lo[1]; iv[1] <= sp.hi[1]; ++iv[1])
-        for (iv[0] = sp.lo[0]; iv[0] <= sp.hi[0]; ++iv[0]) ++nB[lin_index(iv, G.dim, nc)];
-  }
-  for (int c = 0; c < ncells; ++c) {
-    cells[c].I.resize(nI[c]);
-    cells[c].B.resize(nB[c]);
-    nI[c] = nB[c] = 0;
-  }
-  for (int g : alive) {
-    const CellSpan sp = cell_span(G, cl, g);
-    if (sp.interior) {
-      const int c = lin_index(sp.lo, G.dim, nc);
-      cells[c].I[nI[c]++] = g;
-      continue;
+  // count, size every list once, then fill.  alive is ascending and cut into
+  // contiguous ranges, one per task; a task writes its DOFs of a cell after
+  // those of the tasks before it, so I and B come out ascending, exactly as
+  // one pass over alive would make them.
+  const int64_t na = (int64_t)alive.size();
+  const int T = task_count(na, 16384);
+  std::vector<std::vector<int>> nI(T, std::vector<int>(ncells, 0)), nB(T, std::vector<int>(ncells, 0));
+  auto each = [&](int t, auto&& on_interior, auto&& on_boundary) {
+    int64_t lo, hi;
+    task_range(na, T, t, lo, hi);
+    for (int64_t e = lo; e < hi; ++e) {
+      const int g = alive[e];
+      const CellSpan sp = cell_span(G, cl, g);
+      if (sp.interior) { on_interior(lin_index(sp.lo, G.dim, nc), g); continue; }
+      int iv[3];
+      for (iv[2] = sp.lo[2]; iv[2] <= sp.hi[2]; ++iv[2])
+        for (iv[1] = sp.lo[1]; iv[1] <= sp.hi[1]; ++iv[1])
+          for (iv[0] = sp.lo[0]; iv[0] <= sp.hi[0]; ++iv[0]) on_boundary(lin_index(iv, G.dim, nc), g);
     }
-    int iv[3];
-    for (iv[2] = sp.lo[2]; iv[2] <= sp.hi[2]; ++iv[2])
-      for (iv[1] = sp.lo[1]; iv[1] <= sp.hi[1]; ++iv[1])
-        for (iv[0] = sp.lo[0]; iv[0] <= sp.hi[0]; ++iv[0]) {
-          const int c = lin_index(iv, G.dim, nc);
-          cells[c].B[nB[c]++] = g;
-        }
+  };
+  parallel_tasks(T, [&](int t) {
+    std::vector<int>& ci = nI[t];
+    std::vector<int>& cb = nB[t];
+    each(t, [&](int c, int) { ++ci[c]; }, [&](int c, int) { ++cb[c]; });
+  });
+  for (int c = 0; c < ncells; ++c) {   // counts -> each task's first position
+    int si = 0, sb = 0;
+    for (int t = 0; t < T; ++t) {
+      const int a = nI[t][c], b = nB[t][c];
+      nI[t][c] = si;
+      nB[t][c] = sb;
+      si += a;
+      sb += b;
+    }
+    cells[c].I.resize(si);
+    cells[c].B.resize(sb);
   }
+  parallel_tasks(T, [&](int t) {
+    std::vector<int>& ci = nI[t];
+    std::vector<int>& cb = nB[t];
+    each(t, [&](int c, int g) { cells[c].I[ci[c]++] = g; }, [&](int c, int g) { cells[c].B[cb[c]++] = g; });
+  });
 }
 
 void build_child_map(const Geometry& G, int l, const HostCell& P, int cell_lin,
@@ -176,71 +190,100 @@ void build_fronts(const Geometry& G, int l, const std::vector<int>& alive,
       if (a != axis) other = other * nc + cl[x[a]];
     return axis * per_axis + ord + nsep * other;
   };
-  // count per slot; the non-empty slots become the fronts (in slot order)
-  std::vector<int> cnt(nslot, 0);
-  for (int g : alive) {
-    int axis, ord, x[3];
-    const int f = slot_of(g, axis, ord, x);
-    if (f >= 0) ++cnt[f];
-  }
-  std::vector<int> fid(nslot, -1);
+  // count per slot; the non-empty slots become the fronts (in slot order).
+  // As in build_cells: contiguous ranges of alive per task, positions
+  // assigned in task order, so every F.c is ascending.
+  const int64_t na = (int64_t)alive.size();
+  const int T = task_count(na, 16384);
+  std::vector<std::vector<int>> cnt(T, std::vector<int>(nslot, 0));
+  parallel_tasks(T, [&](int t) {
+    int64_t lo, hi;
+    task_range(na, T, t, lo, hi);
+    std::vector<int>& ct = cnt[t];
+    for (int64_t e = lo; e < hi; ++e) {
+      int axis, ord, x[3];
+      const int f = slot_of(alive[e], axis, ord, x);
+      if (f >= 0) ++ct[f];
+    }
+  });
+  std::vector<int> fid(nslot, -1), fsize;
   int nf = 0;
-  for (int f = 0; f < nslot; ++f)
-    if (cnt[f] > 0) fid[f] = nf++;
+  for (int f = 0; f < nslot; ++f) {   // counts -> each task's first position
+    int tot = 0;
+    for (int t = 0; t < T; ++t) {
+      const int a = cnt[t][f];
+      cnt[t][f] = tot;
+      tot += a;
+    }
+    if (tot > 0) {
+      fid[f] = nf++;
+      fsize.push_back(tot);
+    }
+  }
   fronts.assign(nf, HostFront{});
-  for (int f = 0; f < nslot; ++f)
-    if (fid[f] >= 0) {
-      fronts[fid[f]].c.reserve(cnt[f]);
-      cnt[f] = 0;
-    }
-  for (int g : alive) {
-    int axis, ord, x[3];
-    const int f = slot_of(g, axis, ord, x);
-    if (f < 0) continue;
-    HostFront& F = fronts[fid[f]];
-    if (F.c.empty()) {
-      F.axis = axis;
-      int iv[3] = {0, 0, 0};
-      for (int a = 0; a < G.dim; ++a) iv[a] = (a == axis) ? ord : cl[x[a]];
-      F.P1 = lin_index(iv, G.dim, nc);
-      iv[axis] = ord + 1;
-      F.P2 = lin_index(iv, G.dim, nc);
-    }
-    F.c.push_back(g);
-  }
-  if ((int64_t)mark.size() < G.N) mark.assign(G.N, -1);
-  for (size_t f = 0; f < fronts.size(); ++f) {
-    HostFront& F = fronts[f];
-    for (int g : F.c) mark[g] = (int)f;
-    const std::vector<int>& b1 = cells[F.P1].B;
-    const std::vector<int>& b2 = cells[F.P2].B;
-    const size_t ncf = F.c.size(), bound = b1.size() + b2.size();
-    F.pos1.assign(ncf + bound, -1);
-    F.pos2.assign(ncf + bound, -1);
-    F.N.resize(bound);
-    size_t i = 0, j = 0, ci = 0, ni = 0;
-    while (i < b1.size() || j < b2.size()) {
-      int g;
-      int p1 = -1, p2 = -1;
-      if (j >= b2.size() || (i < b1.size() && b1[i] < b2[j])) { g = b1[i]; p1 = (int)i++; }
-      else if (i >= b1.size() || b2[j] < b1[i]) { g = b2[j]; p2 = (int)j++; }
-      else { g = b1[i]; p1 = (int)i++; p2 = (int)j++; }
-      if (mark[g] == (int)f) {            // c in ascending order, as F.c
-        F.pos1[ci] = p1;
-        F.pos2[ci] = p2;
-        ++ci;
-      } else {
-        F.N[ni] = g;
-        F.pos1[ncf + ni] = p1;
-        F.pos2[ncf + ni] = p2;
-        ++ni;
+  for (int f = 0; f < nf; ++f) fronts[f].c.resize(fsize[f]);
+  parallel_tasks(T, [&](int t) {
+    int64_t lo, hi;
+    task_range(na, T, t, lo, hi);
+    std::vector<int>& ct = cnt[t];
+    for (int64_t e = lo; e < hi; ++e) {
+      const int g = alive[e];
+      int axis, ord, x[3];
+      const int f = slot_of(g, axis, ord, x);
+      if (f < 0) continue;
+      HostFront& F = fronts[fid[f]];
+      const int pos = ct[f]++;
+      if (pos == 0) {    // the front's first DOF: its axis and the two cells
+        F.axis = axis;
+        int iv[3] = {0, 0, 0};
+        for (int a = 0; a < G.dim; ++a) iv[a] = (a == axis) ? ord : cl[x[a]];
+        F.P1 = lin_index(iv, G.dim, nc);
+        iv[axis] = ord + 1;
+        F.P2 = lin_index(iv, G.dim, nc);
       }
+      F.c[pos] = g;
     }
-    F.N.resize(ni);
-    F.pos1.resize(ncf + ni);
-    F.pos2.resize(ncf + ni);
-    for (int g : F.c) mark[g] = -1;
-  }
+  });
+  if ((int64_t)mark.size() < G.N) mark.assign(G.N, -1);
+  // neighbour lists: the fronts partition the DOFs, so each front marks and
+  // unmarks its own entries of `mark`
+  const int TF = task_count(nf, 64);
+  parallel_tasks(TF, [&](int t) {
+    int64_t f0, f1;
+    task_range(nf, TF, t, f0, f1);
+    for (int64_t f = f0; f < f1; ++f) {
+      HostFront& F = fronts[f];
+      for (int g : F.c) mark[g] = (int)f;
+      const std::vector<int>& b1 = cells[F.P1].B;
+      const std::vector<int>& b2 = cells[F.P2].B;
+      const size_t ncf = F.c.size(), bound = b1.size() + b2.size();
+      F.pos1.assign(ncf + bound, -1);
+      F.pos2.assign(ncf + bound, -1);
+      F.N.resize(bound);
+      size_t i = 0, j = 0, ci = 0, ni = 0;
+      while (i < b1.size() || j < b2.size()) {
+        int g;
+        int p1 = -1, p2 = -1;
+        if (j >= b2.size() || (i < b1.size() && b1[i] < b2[j])) { g = b1[i]; p1 = (int)i++; }
+        else if (i >= b1.size() || b2[j] < b1[i]) { g = b2[j]; p2 = (int)j++; }
+        else { g = b1[i]; p1 = (int)i++; p2 = (int)j++; }
+        if (mark[g] == (int)f) {            // c in ascending order, as F.c
+          F.pos1[ci] = p1;
+          F.pos2[ci] = p2;
+          ++ci;
+        } else {
+          F.N[ni] = g;
+          F.pos1[ncf + ni] = p1;
+          F.pos2[ncf + ni] = p2;
+          ++ni;
+        }
+      }
+      F.N.resize(ni);
+      F.pos1.resize(ncf + ni);
+      F.pos2.resize(ncf + ni);
+      for (int g : F.c) mark[g] = -1;
+    }
+  });
 }
 
 }  // namespace hif

@@ -32,6 +32,7 @@
 #include "../../include/hif.h"
 #include "geometry.h"
 #include "hif_internal.h"
+#include "host_pool.h"
 #include "kernels.h"
 
 using namespace hif;
@@ -213,9 +214,8 @@ void prepare_cells(const Geometry& G, int l, const std::vector<HostCell>& cells,
   work_elems = fac_elems = 0;
   max_nI = 0;
   const bool maps = l > 0 && prev;
-  int64_t total = 0;
-  for (const HostCell& c : cells) total += (int64_t)(c.I.size() + c.B.size()) * (maps ? 9 : 1);
-  ipool.resize(total);
+  // sizes and offsets in cell order, then the id lists and child maps of the
+  // cells in parallel (each cell writes its own range of the pool)
   int64_t p = 0;
   for (size_t i = 0; i < cells.size(); ++i) {
     const HostCell& c = cells[i];
@@ -224,10 +224,7 @@ void prepare_cells(const Geometry& G, int l, const std::vector<HostCell>& cells,
     d.nB = (int)c.B.size();
     d.cell_lin = (int)i;
     d.ids = p;
-    std::copy(c.I.begin(), c.I.end(), ipool.begin() + p);
-    p += d.nI;
-    std::copy(c.B.begin(), c.B.end(), ipool.begin() + p);
-    p += d.nB;
+    p += d.nI + d.nB;
     d.F = work_elems;
     work_elems += (int64_t)d.nI * d.nI + (int64_t)d.nB * d.nI + (int64_t)d.nB * d.nB + cell_x_elems(d.nI);
     d.fac = fac_elems;
@@ -236,11 +233,24 @@ void prepare_cells(const Geometry& G, int l, const std::vector<HostCell>& cells,
     d.cmap = -1;
     if (maps) {
       d.cmap = p;
-      build_child_map(G, l, c, (int)i, *prev, ipool.data() + p, d.child);
       p += (int64_t)(d.nI + d.nB) * 8;
     }
     max_nI = std::max(max_nI, d.nI);
   }
+  ipool.resize(p);
+  const int ncell = (int)cells.size();
+  const int T = task_count(p, 32768);
+  parallel_tasks(T, [&](int t) {
+    int64_t c0, c1;
+    task_range(ncell, T, t, c0, c1);
+    for (int64_t i = c0; i < c1; ++i) {
+      const HostCell& c = cells[i];
+      CellDesc& d = desc[i];
+      std::copy(c.I.begin(), c.I.end(), ipool.begin() + d.ids);
+      std::copy(c.B.begin(), c.B.end(), ipool.begin() + d.ids + d.nI);
+      if (maps) build_child_map(G, l, c, (int)i, *prev, ipool.data() + d.cmap, d.child);
+    }
+  });
 }
 
 // Apply descriptors of the cells of a level and the sweep statistics.
