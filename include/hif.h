@@ -111,13 +111,27 @@ typedef struct hif_opts {
 typedef struct hif_handle hif_handle;
 
 typedef struct hif_solve_info {
-  int iters;            /* inner CG iterations, all refinement steps            */
+  int iters;            /* inner iterations (CG steps and GMRES Arnoldi steps),
+                           all refinement steps                                  */
   int outer;            /* refinement steps                                     */
   int converged;        /* 1 if every column reached tol                        */
   double relres_max;    /* max_r ||b_r - A x_r||_2 / ||b_r||_2 of the
                            double-double iterate x = x_hi + x_lo                 */
   double relres_fp64_max; /* the same for the FP64 iterate x_hi alone           */
+  int gmres_iters;      /* of iters, the GMRES Arnoldi steps (0: CG only)        */
 } hif_solve_info;
+
+/* Inner solver of hif_solve's refinement steps (Section 5: CG for the SPD
+ * systems, GMRES where the preconditioned operator is not SPD). */
+enum {
+  HIF_SOLVER_AUTO = 0,   /* CG; on a breakdown (r.z <= 0 on a column: F^-1 is
+                            not positive definite there, a non-finite
+                            residual, or 50 iterations without a new smallest
+                            residual) that refinement step and the following
+                            ones run flexible GMRES                              */
+  HIF_SOLVER_CG = 1,     /* CG only                                              */
+  HIF_SOLVER_GMRES = 2   /* flexible GMRES(restart) only                          */
+};
 
 typedef struct hif_stats_t {
   int dim, n, levels;          /* L                                              */
@@ -192,6 +206,18 @@ int hif_solve_batch(int nprob, hif_handle* const* hs, const double* const* rhs, 
 int hif_matvec(hif_handle* h, const double* x, double* y, int nrhs, int ld);
 
 /* hif_stats -- sizes and counts of the factorization (Section 5 columns). */
+/*
+ * hif_set_solver -- the inner solver of later hif_solve calls on h:
+ * HIF_SOLVER_* (default AUTO) and the GMRES restart length (0 -> 50,
+ * else 2..500).  Flexible GMRES (Saad, 1993) right-preconditioned by F^-1:
+ * Arnoldi with classical Gram-Schmidt applied twice, FP64 basis, the
+ * preconditioned vectors kept in the factor's apply precision; one GMRES per
+ * right-hand side; memory (restart + 1) N nr FP64 + restart N nr values of
+ * the apply precision per 16 right-hand sides.  HIF_ERR_ARG: NULL handle,
+ * unknown solver, restart out of range.
+ */
+int hif_set_solver(hif_handle* h, int solver, int restart);
+
 int hif_stats(const hif_handle* h, hif_stats_t* st);
 
 /*

@@ -22,6 +22,9 @@ What each function follows:
 * :func:`Factor.apply_inverse`, :func:`Factor.apply` -- Eq. (4.2):
   ``F^-1 = V_0 V_1/2 ... D^-1 ... V_1/2^T V_0^T`` and ``F`` itself.
 * :func:`pcg` -- preconditioned CG of Section 5 (relative residual 1e-12).
+* :func:`fgmres` -- GMRES (Saad and Schultz, 1986), which Section 5 uses with
+  the preconditioner ``F^-1`` where the system is not SPD; the right
+  preconditioned flexible form (``z_j = F^-1 v_j`` kept).
 * :func:`power_estimates` -- the a posteriori estimates ``e_a``, ``e_s`` of
   Section 5 by power iteration to 1e-2 relative precision.
 
@@ -531,6 +534,58 @@ def pcg(A_csr, F: Factor, b: np.ndarray, tol: float = 1e-12, maxit: int = 200):
         X[:, col] = x
         iters.append(it)
         relres.append(np.linalg.norm(bb - A_csr @ x) / nb)
+    return X.reshape(b.shape), iters, relres
+
+
+def fgmres(A, apply_minv, b: np.ndarray, tol: float = 1e-12, maxit: int = 200, restart: int = 50):
+    """Right-preconditioned flexible GMRES(restart) on each column of b.
+
+    One cycle from the residual r (beta = ||r||): v_0 = r / beta; for
+    j = 0, 1, ...: z_j = M^-1 v_j, w = A z_j, modified Gram-Schmidt
+    h_ij = <w, v_i>, w -= h_ij v_i (i <= j), h_{j+1,j} = ||w||,
+    v_{j+1} = w / h_{j+1,j}; y minimizes ||beta e_1 - H_j y|| (numpy lstsq)
+    and the cycle stops when that residual is at most tol ||b|| (or at a
+    breakdown h_{j+1,j} = 0, or after `restart` steps); then x += Z y and
+    the next cycle starts from the true residual b - A x.  ``A`` is anything
+    with ``A @ v``; ``apply_minv(v)`` applies M^-1.  Returns (x, iters,
+    relres) like :func:`pcg`, iters counting the steps j."""
+    b2 = b.reshape(b.shape[0], -1)
+    X = np.zeros_like(b2)
+    iters, relres = [], []
+    for col in range(b2.shape[1]):
+        bb = b2[:, col]
+        nb = np.linalg.norm(bb)
+        x = np.zeros_like(bb)
+        r = bb.copy()
+        it = 0
+        while it < maxit:
+            beta = np.linalg.norm(r)
+            if beta <= tol * nb:
+                break
+            V = [r / beta]
+            Z = []
+            H = np.zeros((restart + 1, restart))
+            y = np.zeros(0)
+            for j in range(restart):
+                Z.append(apply_minv(V[j]))
+                w = A @ Z[j]
+                for i in range(j + 1):
+                    H[i, j] = w @ V[i]
+                    w = w - H[i, j] * V[i]
+                H[j + 1, j] = np.linalg.norm(w)
+                it += 1
+                e1 = np.zeros(j + 2)
+                e1[0] = beta
+                y = np.linalg.lstsq(H[:j + 2, :j + 1], e1, rcond=None)[0]
+                res = np.linalg.norm(e1 - H[:j + 2, :j + 1] @ y)
+                if H[j + 1, j] == 0.0 or res <= tol * nb or it >= maxit:
+                    break
+                V.append(w / H[j + 1, j])
+            x = x + np.column_stack(Z) @ y
+            r = bb - A @ x
+        X[:, col] = x
+        iters.append(it)
+        relres.append(np.linalg.norm(bb - A @ x) / nb)
     return X.reshape(b.shape), iters, relres
 
 

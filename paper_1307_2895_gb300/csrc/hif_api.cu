@@ -197,6 +197,9 @@ struct hif_handle {
   // iterations can run in batches between host checks
   double* rr_ring = nullptr;
   cudaEvent_t it_ev[2] = {nullptr, nullptr};
+  // inner solver of the refinement steps (HIF_SOLVER_*) and GMRES restart length
+  int solver = HIF_SOLVER_AUTO;
+  int gmres_m = 50;
   ~hif_handle() {
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
     for (cudaEvent_t e : it_ev)
@@ -1024,9 +1027,10 @@ void cg_step_kernels(hif_handle* h, SolveWork& W, TZ* wp, int par, int restart, 
 // when iteration k converged every column, the queued iteration changed
 // nothing.  Stops when the FP64 true residual confirms the recursive one.
 constexpr int kRingRows = 4;
-constexpr int kRingCols = 16;
+constexpr int kRingCols = 32;   // rr (R <= 16 values), then r.z of the same iteration
 
-int inner_pcg(hif_handle* h, SolveWork& W, Precond& M, const std::vector<double>& hthr, int maxit) {
+int inner_pcg(hif_handle* h, SolveWork& W, Precond& M, const std::vector<double>& hthr, int maxit,
+              bool* broke) {
   const int64_t N = W.N;
   const int R = W.R;
   cudaStream_t st = h->st;
@@ -1067,10 +1071,33 @@ int inner_pcg(hif_handle* h, SolveWork& W, Precond& M, const std::vector<double>
     else cg_step_kernels<double>(h, W, W.WP.as<double>(), par, 0, 1, partials, counter);
     CU(cudaMemcpyAsync(h->rr_ring + (size_t)(issued % kRingRows) * kRingCols, W.rr, sizeof(double) * R,
                        cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(h->rr_ring + (size_t)(issued % kRingRows) * kRingCols + R, W.rzzq[par], sizeof(double) * R,
+                       cudaMemcpyDeviceToHost, st));
     CU(cudaEventRecord(h->it_ev[issued & 1], st));
     ++issued;
     par ^= 1;
     return true;
+  };
+  // breakdown (the caller may switch to GMRES): r.z <= 0 on a live column
+  // (F^-1 not positive definite there), a non-finite residual, or no new
+  // smallest residual for kStall iterations
+  constexpr int kStall = 50;
+  std::vector<double> best(R, 1e300);
+  std::vector<int> since(R, 0);
+  if (broke) *broke = false;
+  auto breakdown = [&](const double* row) {
+    for (int c = 0; c < R; ++c) {
+      if (hthr[c] >= 1e299) continue;
+      const double rr = row[c], rz = row[R + c];
+      if (!std::isfinite(rr) || !std::isfinite(rz) || (rz <= 0.0 && rr > hthr[c])) return true;
+      if (rr < best[c]) {
+        best[c] = rr;
+        since[c] = 0;
+      } else if (++since[c] >= kStall) {
+        return true;
+      }
+    }
+    return false;
   };
   bool head = issue();                 // iteration `it` queued
   while (true) {
@@ -1080,6 +1107,10 @@ int inner_pcg(hif_handle* h, SolveWork& W, Precond& M, const std::vector<double>
     CU(cudaEventSynchronize(h->it_ev[it & 1]));
     const double* row = h->rr_ring + (size_t)(it % kRingRows) * kRingCols;
     ++it;
+    if (broke && breakdown(row)) {
+      *broke = true;
+      break;
+    }
     if (!converged_row(row)) {
       head = ahead;
       continue;
@@ -1099,6 +1130,128 @@ int inner_pcg(hif_handle* h, SolveWork& W, Precond& M, const std::vector<double>
     head = issue();
   }
   CU(cudaStreamSynchronize(st));
+  M.settle();
+  return it;
+}
+
+// Inner flexible GMRES(m) on A D = W.bin (right-preconditioned by F^-1, each
+// column its own Krylov space), to the squared residual thresholds hthr;
+// returns the Arnoldi steps taken.  Arnoldi: z_j = F^-1 v_j (kept, in the
+// preconditioner's precision), w = A z_j in FP64, classical Gram-Schmidt
+// twice against v_0..v_j, v_{j+1} = w / ||w||.  The small Hessenberg least
+// squares problem is reduced by Givens rotations on the host; at the end of a
+// cycle D += Z y and the true residual W.bin - A D starts the next cycle.
+int inner_gmres(hif_handle* h, SolveWork& W, Precond& M, const std::vector<double>& hthr, int maxit) {
+  const int64_t N = W.N;
+  const int R = W.R;
+  const int m = std::max(2, std::min(h->gmres_m, 500));
+  cudaStream_t st = h->st;
+  const size_t vb = sizeof(double) * N * R, zsz = W.f32 ? sizeof(float) : sizeof(double);
+  const int64_t slab = N * R;
+  double* partials = W.part.as<double>();
+  unsigned* counter = W.cnt.as<unsigned>();
+  DevBuf V, Z, hd, mpart, mcnt, tmp, yb;
+  V.alloc(vb * (m + 1), st);
+  Z.alloc(zsz * slab * m, st);
+  hd.alloc(sizeof(double) * (2 * (m + 1) + 1) * R, st);
+  mpart.alloc(sizeof(double) * (m + 1) * 304 * R, st);
+  mcnt.alloc(sizeof(unsigned) * (m + 1), st);
+  CU(cudaMemsetAsync(mcnt.p, 0, sizeof(unsigned) * (m + 1), st));
+  if (W.f32) tmp.alloc(vb, st);
+  yb.alloc(sizeof(double) * m * R, st);
+  double* Vd = V.as<double>();
+  double* h1 = hd.as<double>();
+  double* h2 = h1 + (m + 1) * R;
+  double* hn = h2 + (m + 1) * R;
+  CU(cudaMemsetAsync(W.D.p, 0, vb, st));
+  CU(cudaMemcpyAsync(W.Rv.p, W.bin.p, vb, cudaMemcpyDeviceToDevice, st));
+  launch_sqnorm(N, R, W.Rv.as<double>(), partials, counter, W.rr, st);
+  std::vector<double> hr(R), hh(sizeof(double) * (2 * (m + 1) + 1) * R / sizeof(double));
+  std::vector<double> H((size_t)R * (m + 1) * m), cs((size_t)R * m), sn((size_t)R * m), g((size_t)R * (m + 1));
+  std::vector<double> y((size_t)m * R);
+  int it = 0;
+  while (true) {
+    CU(cudaMemcpyAsync(hr.data(), W.rr, sizeof(double) * R, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    bool all = true;
+    for (int c = 0; c < R; ++c)
+      if (hthr[c] < 1e299 && !(hr[c] <= hthr[c])) all = false;
+    if (all || it >= maxit) break;
+    launch_normalize(N, R, W.Rv.as<double>(), W.rr, Vd, nullptr, st);
+    for (int c = 0; c < R; ++c) {
+      std::fill(g.begin() + (size_t)c * (m + 1), g.begin() + (size_t)(c + 1) * (m + 1), 0.0);
+      g[(size_t)c * (m + 1)] = hthr[c] < 1e299 ? std::sqrt(hr[c]) : 0.0;
+    }
+    int j = 0;
+    for (; j < m && it < maxit;) {
+      ++it;
+      double* vj = Vd + (int64_t)j * slab;
+      double* w = Vd + (int64_t)(j + 1) * slab;
+      if (W.f32) launch_convert<double, float>(N, R, vj, R, W.WP.as<float>(), R, st);
+      else CU(cudaMemcpyAsync(W.WP.p, vj, vb, cudaMemcpyDeviceToDevice, st));
+      M.apply();
+      CU(cudaMemcpyAsync(Z.as<unsigned char>() + zsz * slab * j, W.WP.p, zsz * slab, cudaMemcpyDeviceToDevice, st));
+      const double* zj = W.WP.as<double>();
+      if (W.f32) {
+        launch_convert<float, double>(N, R, W.WP.as<float>(), R, tmp.as<double>(), R, st);
+        zj = tmp.as<double>();
+      }
+      launch_mv_dot_e(h->gi, h->stencil_w.as<double>(), zj, w, R, partials, counter, W.pq, st);
+      launch_multi_dot(N, R, Vd, slab, j + 1, w, mpart.as<double>(), mcnt.as<unsigned>(), h1, st);
+      launch_multi_axpy(N, R, Vd, slab, j + 1, h1, w, st);
+      launch_multi_dot(N, R, Vd, slab, j + 1, w, mpart.as<double>(), mcnt.as<unsigned>(), h2, st);
+      launch_multi_axpy(N, R, Vd, slab, j + 1, h2, w, st);
+      launch_sqnorm(N, R, w, partials, counter, W.rr, st);
+      launch_normalize(N, R, w, W.rr, w, hn, st);
+      CU(cudaMemcpyAsync(hh.data(), h1, sizeof(double) * (2 * (m + 1) + 1) * R, cudaMemcpyDeviceToHost, st));
+      CU(cudaStreamSynchronize(st));
+      CU(cudaGetLastError());
+      const double* hh1 = hh.data();
+      const double* hh2 = hh1 + (m + 1) * R;
+      const double* hhn = hh2 + (m + 1) * R;
+      bool conv = true;
+      for (int c = 0; c < R; ++c) {
+        if (hthr[c] >= 1e299) continue;
+        double* col = H.data() + ((size_t)c * m + j) * (m + 1);   // column j of column c's H
+        for (int i = 0; i <= j; ++i) col[i] = hh1[i * R + c] + hh2[i * R + c];
+        col[j + 1] = hhn[c];
+        double* cc = cs.data() + (size_t)c * m;
+        double* ss = sn.data() + (size_t)c * m;
+        for (int i = 0; i < j; ++i) {   // earlier rotations
+          const double t = cc[i] * col[i] + ss[i] * col[i + 1];
+          col[i + 1] = -ss[i] * col[i] + cc[i] * col[i + 1];
+          col[i] = t;
+        }
+        const double rho = std::hypot(col[j], col[j + 1]);
+        cc[j] = rho > 0.0 ? col[j] / rho : 1.0;
+        ss[j] = rho > 0.0 ? col[j + 1] / rho : 0.0;
+        col[j] = rho;
+        col[j + 1] = 0.0;
+        double* gc = g.data() + (size_t)c * (m + 1);
+        gc[j + 1] = -ss[j] * gc[j];
+        gc[j] = cc[j] * gc[j];
+        if (!(gc[j + 1] * gc[j + 1] <= hthr[c])) conv = false;
+      }
+      ++j;
+      if (conv) break;
+    }
+    // y = H(0:j, 0:j)^-1 g(0:j) per column, D += Z y, true residual
+    for (int c = 0; c < R; ++c) {
+      const double* gc = g.data() + (size_t)c * (m + 1);
+      for (int i = j - 1; i >= 0; --i) {
+        double s2 = gc[i];
+        for (int k = i + 1; k < j; ++k) s2 -= H[((size_t)c * m + k) * (m + 1) + i] * y[(size_t)k * R + c];
+        const double d = H[((size_t)c * m + i) * (m + 1) + i];
+        y[(size_t)i * R + c] = (hthr[c] < 1e299 && d != 0.0) ? s2 / d : 0.0;
+      }
+    }
+    CU(cudaMemcpyAsync(yb.p, y.data(), sizeof(double) * j * R, cudaMemcpyHostToDevice, st));
+    if (W.f32) launch_zy_add<float>(N, R, Z.as<float>(), slab, j, yb.as<double>(), W.D.as<double>(), st);
+    else launch_zy_add<double>(N, R, Z.as<double>(), slab, j, yb.as<double>(), W.D.as<double>(), st);
+    launch_residual(h->gi, h->a_stag.as<double>(), h->bnode.as<double>(), W.bin.as<double>(), W.D.as<double>(),
+                    W.Rv.as<double>(), R, partials, counter, W.rr, st);
+    CU(cudaStreamSynchronize(st));   // y is read before the next cycle rewrites it
+  }
   M.settle();
   return it;
 }
@@ -1131,7 +1284,8 @@ int solve_chunk(hif_handle* h, const double* rhs, double* x, double* xlo, int nr
   CU(cudaMemcpyAsync(W.Rv.p, W.f.p, vb, cudaMemcpyDeviceToDevice, st));
   CU(cudaStreamSynchronize(st));
   hr = hb;
-  int iters = 0, outer = 0;
+  int iters = 0, outer = 0, gmres_iters = 0;
+  bool use_gmres = h->solver == HIF_SOLVER_GMRES;
   bool converged = false;
   double relmax = 0.0;
   while (true) {
@@ -1149,7 +1303,21 @@ int solve_chunk(hif_handle* h, const double* rhs, double* x, double* xlo, int nr
       const double tau = std::max(0.5 * tol * std::sqrt(hb[c] / hr[c]), 1e-9);
       hthr[c] = tau * tau * hr[c];
     }
-    iters += inner_pcg(h, W, M, hthr, maxit - iters);
+    if (use_gmres) {
+      CU(cudaMemcpyAsync(W.bin.p, W.Rv.p, vb, cudaMemcpyDeviceToDevice, st));
+      const int g = inner_gmres(h, W, M, hthr, maxit - iters);
+      iters += g;
+      gmres_iters += g;
+    } else {
+      bool broke = false;
+      iters += inner_pcg(h, W, M, hthr, maxit - iters, h->solver == HIF_SOLVER_AUTO ? &broke : nullptr);
+      if (broke) {   // F^-1 indefinite or CG stalled: this step again with GMRES (W.bin holds its right-hand side)
+        use_gmres = true;
+        const int g = inner_gmres(h, W, M, hthr, maxit - iters);
+        iters += g;
+        gmres_iters += g;
+      }
+    }
     CU(cudaGetLastError());
     launch_dd_add(N, R, W.xh.as<double>(), W.xl.as<double>(), W.D.as<double>(), st);
     launch_dd_residual(h->gi, h->a_stag.as<double>(), h->bnode.as<double>(), W.f.as<double>(),
@@ -1171,6 +1339,7 @@ int solve_chunk(hif_handle* h, const double* rhs, double* x, double* xlo, int nr
   for (int c = 0; c < nr; ++c) rel64 = std::max(rel64, hb[c] > 0 ? std::sqrt(h64[c] / hb[c]) : 0.0);
   if (info) {
     info->iters = std::max(info->iters, iters);
+    info->gmres_iters = std::max(info->gmres_iters, gmres_iters);
     info->outer = std::max(info->outer, outer);
     info->converged = info->converged && converged;
     info->relres_max = std::max(info->relres_max, relmax);
@@ -1355,7 +1524,7 @@ int hif_solve(hif_handle* h, const double* rhs, double* x, double* x_lo, int nrh
   if (!h || !rhs || !x) return set_error(HIF_ERR_ARG, "NULL argument");
   if (nrhs < 1 || ld < nrhs) return set_error(HIF_ERR_ARG, "need 1 <= nrhs <= ld");
   if (!(tol > 0.0) || maxit < 0) return set_error(HIF_ERR_ARG, "need tol > 0 and maxit >= 0");
-  hif_solve_info loc{0, 0, 1, 0.0, 0.0};
+  hif_solve_info loc{0, 0, 1, 0.0, 0.0, 0};
   int rc = HIF_OK;
   try {
     const int64_t N = h->G.N;
@@ -1380,8 +1549,17 @@ int hif_solve(hif_handle* h, const double* rhs, double* x, double* x_lo, int nrh
     return set_error(e.code, e.msg);
   }
   if (info) *info = loc;
-  if (rc == HIF_ERR_NOCONV) set_error(rc, "CG reached maxit before tol");
+  if (rc == HIF_ERR_NOCONV) set_error(rc, "the iteration reached maxit before tol");
   return rc;
+}
+
+int hif_set_solver(hif_handle* h, int solver, int restart) {
+  if (!h) return set_error(HIF_ERR_ARG, "NULL handle");
+  if (solver < HIF_SOLVER_AUTO || solver > HIF_SOLVER_GMRES) return set_error(HIF_ERR_ARG, "unknown solver");
+  if (restart != 0 && (restart < 2 || restart > 500)) return set_error(HIF_ERR_ARG, "need 2 <= restart <= 500");
+  h->solver = solver;
+  h->gmres_m = restart == 0 ? 50 : restart;
+  return HIF_OK;
 }
 
 int hif_stats(const hif_handle* h, hif_stats_t* s) {

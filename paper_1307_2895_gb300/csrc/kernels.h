@@ -112,6 +112,16 @@ template <typename TZ>
 void launch_update_p_e(int64_t N, int R, double* p, const TZ* z, const double* alpha, const double* rz_old,
                        const double* rzzq, const int* active, int restart, cudaStream_t st);
 void launch_set_active(int nr, const double* rr, const double* thr2, int* active, cudaStream_t st);
+// flexible GMRES: basis slabs V_i = V + i slab (N x R); out[i R + c] = <V_i, w>
+void launch_multi_dot(int64_t N, int R, const double* V, int64_t slab, int nv, const double* w, double* partials,
+                      unsigned* counters, double* out, cudaStream_t st);
+void launch_multi_axpy(int64_t N, int R, const double* V, int64_t slab, int nv, const double* h, double* w,
+                       cudaStream_t st);
+void launch_normalize(int64_t N, int R, const double* w, const double* nrm2, double* v, double* hnorm,
+                      cudaStream_t st);
+template <typename TZ>
+void launch_zy_add(int64_t N, int R, const TZ* Z, int64_t slab, int nv, const double* y, double* d,
+                   cudaStream_t st);
 template <typename TI, typename TO>
 void launch_convert(int64_t N, int nr, const TI* in, int ldi, TO* out, int ldo, cudaStream_t st);
 

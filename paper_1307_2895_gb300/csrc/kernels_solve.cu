@@ -789,6 +789,119 @@ void launch_convert(int64_t N, int nr, const TI* in, int ldi, TO* out, int ldo, 
   note_launches(1);
   k_convert<TI, TO><<<vec_blocks(N * nr), kVecThreads, 0, st>>>(N, nr, in, ldi, out, ldo);
 }
+// ---- flexible GMRES (Arnoldi with classical Gram-Schmidt, twice) ----------
+// Basis slabs: V_i = V + i * slab (N x R, FP64), Z_i = Z + i * slab (the
+// preconditioner's type).  Each column c is an independent GMRES.
+
+// out[i * R + c] = <V_i(:, c), w(:, c)> for i = blockIdx.y; per-i partials and
+// counters, summed by the last block of each i in block order.
+template <int R>
+__global__ void k_multi_dot(int64_t N, const double* __restrict__ V, int64_t slab, const double* __restrict__ w,
+                            double* partials, unsigned* counters, double* out) {
+  __shared__ double shr[kVecThreads];
+  __shared__ bool last;
+  const int i = blockIdx.y;
+  const double* v = V + (int64_t)i * slab;
+  double acc = 0.0;
+  const int64_t n = N * R, stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) acc = fma(v[e], w[e], acc);
+  const int tid = threadIdx.x;
+  shr[tid] = acc;
+  __syncthreads();
+  for (int s = blockDim.x >> 1; s >= R; s >>= 1) {
+    if (tid < s) shr[tid] += shr[tid + s];
+    __syncthreads();
+  }
+  double* part = partials + (int64_t)i * gridDim.x * R;
+  if (tid < R) part[(int64_t)blockIdx.x * R + tid] = shr[tid];
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) last = (atomicAdd(counters + i, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  last_block_sum(part, R, shr, out + (int64_t)i * R);
+  if (tid == 0) counters[i] = 0u;
+}
+
+// w -= sum_{i < nv} h[i * R + c] V_i(:, c)
+template <int R>
+__global__ void k_multi_axpy(int64_t N, const double* __restrict__ V, int64_t slab, int nv,
+                             const double* __restrict__ h, double* __restrict__ w) {
+  const int64_t n = N * R, stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
+    const int c = (int)(e % R);
+    double s = 0.0;
+    for (int i = 0; i < nv; ++i) s = fma(h[i * R + c], V[(int64_t)i * slab + e], s);
+    w[e] -= s;
+  }
+}
+
+// v = w / ||w|| per column from nrm2 (a zero column stays zero); hnorm[c] =
+// ||w(:, c)|| when hnorm is not null
+template <int R>
+__global__ void k_normalize(int64_t N, const double* __restrict__ w, const double* __restrict__ nrm2,
+                            double* __restrict__ v, double* hnorm) {
+  const int64_t n = N * R, stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = (int)(e % R);   // fixed per thread: the stride is a multiple of R
+  const double nr = sqrt(nrm2[c]);
+  const double inv = nr > 0.0 ? 1.0 / nr : 0.0;
+  if (hnorm && blockIdx.x == 0 && threadIdx.x < R) hnorm[threadIdx.x] = sqrt(nrm2[threadIdx.x]);
+  for (; e < n; e += stride) v[e] = w[e] * inv;
+}
+
+// d += sum_{i < nv} y[i * R + c] Z_i(:, c)
+template <int R, typename TZ>
+__global__ void k_zy_add(int64_t N, const TZ* __restrict__ Z, int64_t slab, int nv, const double* __restrict__ y,
+                         double* __restrict__ d) {
+  const int64_t n = N * R, stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += stride) {
+    const int c = (int)(e % R);
+    double s = d[e];
+    for (int i = 0; i < nv; ++i) s = fma(y[i * R + c], widen<TZ>(Z[(int64_t)i * slab + e]), s);
+    d[e] = s;
+  }
+}
+
+static inline int gmres_blocks(int64_t n) {
+  // a multiple of every R in {1,..,16} (256 threads per block); 2 blocks per SM
+  // for the reductions, which run one grid row per basis vector
+  const int64_t b = (n + kVecThreads - 1) / kVecThreads;
+  return (int)(b < 304 ? (b > 0 ? b : 1) : 304);
+}
+
+void launch_multi_dot(int64_t N, int R, const double* V, int64_t slab, int nv, const double* w, double* partials,
+                      unsigned* counters, double* out, cudaStream_t st) {
+  if (nv <= 0) return;
+  note_launches(1);
+  DISPATCH_POW2(R, (k_multi_dot<R><<<dim3(gmres_blocks(N * R), nv), kVecThreads, 0, st>>>(N, V, slab, w, partials,
+                                                                                         counters, out)));
+}
+
+void launch_multi_axpy(int64_t N, int R, const double* V, int64_t slab, int nv, const double* h, double* w,
+                       cudaStream_t st) {
+  if (nv <= 0) return;
+  note_launches(1);
+  DISPATCH_POW2(R, (k_multi_axpy<R><<<elem_blocks(N * R), kVecThreads, 0, st>>>(N, V, slab, nv, h, w)));
+}
+
+void launch_normalize(int64_t N, int R, const double* w, const double* nrm2, double* v, double* hnorm,
+                      cudaStream_t st) {
+  note_launches(1);
+  DISPATCH_POW2(R, (k_normalize<R><<<elem_blocks(N * R), kVecThreads, 0, st>>>(N, w, nrm2, v, hnorm)));
+}
+
+template <typename TZ>
+void launch_zy_add(int64_t N, int R, const TZ* Z, int64_t slab, int nv, const double* y, double* d,
+                   cudaStream_t st) {
+  if (nv <= 0) return;
+  note_launches(1);
+  DISPATCH_POW2(R, (k_zy_add<R, TZ><<<elem_blocks(N * R), kVecThreads, 0, st>>>(N, Z, slab, nv, y, d)));
+}
+template void launch_zy_add<double>(int64_t, int, const double*, int64_t, int, const double*, double*, cudaStream_t);
+template void launch_zy_add<float>(int64_t, int, const float*, int64_t, int, const double*, double*, cudaStream_t);
+
 template void launch_convert<double, double>(int64_t, int, const double*, int, double*, int, cudaStream_t);
 template void launch_convert<double, float>(int64_t, int, const double*, int, float*, int, cudaStream_t);
 template void launch_convert<float, double>(int64_t, int, const float*, int, double*, int, cudaStream_t);

@@ -20,6 +20,7 @@ HIF_OK, HIF_ERR_ARG, HIF_ERR_NOT_SPD, HIF_ERR_NOCONV, HIF_ERR_TIMEOUT, HIF_ERR_C
 VARIANTS = {"mf": 0, "hifde": 1}
 ID_MODES = {"qr": 0, "rand": 1, "learned": 2}
 MLP_FEATURES, MLP_PARAMS = 10, 4929
+SOLVERS = {"auto": 0, "cg": 1, "gmres": 2}
 PRECISIONS = {"fp64": 0, "mixed": 1, "fp32_apply": 2}
 APPLY_F, APPLY_FINV = 0, 1
 
@@ -42,7 +43,8 @@ class _Opts(ctypes.Structure):
 
 class _SolveInfo(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("outer", ctypes.c_int), ("converged", ctypes.c_int),
-                ("relres_max", ctypes.c_double), ("relres_fp64_max", ctypes.c_double)]
+                ("relres_max", ctypes.c_double), ("relres_fp64_max", ctypes.c_double),
+                ("gmres_iters", ctypes.c_int)]
 
 
 class _Stats(ctypes.Structure):
@@ -63,7 +65,8 @@ class _Profile(ctypes.Structure):
 _LIB = None
 EXPORTS = ["hif_factor", "hif_apply", "hif_solve", "hif_matvec", "hif_stats", "hif_structure",
            "hif_profile", "hif_kernel_launches", "hif_residual_norms_noalloc", "hif_front_log", "hif_mlp_grad",
-           "hif_mlp_train", "hif_mlp_predict", "hif_schur_update_f32", "hif_factor_batch", "hif_solve_batch", "hif_free", "hif_last_error"]
+           "hif_mlp_train", "hif_mlp_predict", "hif_schur_update_f32", "hif_factor_batch", "hif_solve_batch", "hif_set_solver", "hif_free",
+           "hif_last_error"]
 
 
 def library_path() -> str:
@@ -114,6 +117,8 @@ def load(build_if_missing: bool = False):
     lib.hif_factor_batch.restype = i
     lib.hif_solve_batch.argtypes = [i, vp, vp, vp, vp, d, i, ctypes.POINTER(_SolveInfo), i]
     lib.hif_solve_batch.restype = i
+    lib.hif_set_solver.argtypes = [vp, i, i]
+    lib.hif_set_solver.restype = i
     lib.hif_free.argtypes = [vp]
     lib.hif_free.restype = None
     lib.hif_last_error.argtypes = []
@@ -192,9 +197,15 @@ class Factorization:
         _check(self._lib.hif_matvec(self._live(), _ptr(x2), _ptr(y), x2.shape[1], x2.shape[1]), self._lib)
         return y.reshape(x.shape)
 
+    def set_solver(self, solver: str = "auto", restart: int = 0) -> None:
+        """hif_set_solver: inner solver of later solves ("auto": CG with a
+        GMRES fallback on breakdown, "cg", "gmres"), GMRES restart length."""
+        _check(self._lib.hif_set_solver(self._live(), SOLVERS[solver], restart), self._lib)
+
     def solve(self, rhs, tol: float = 1e-12, maxit: int = 200, raise_on_noconv: bool = False,
               want_lo: bool = False, out=None):
-        """PCG with F^-1 as preconditioner (double-double refinement); returns
+        """PCG (or GMRES, see set_solver) with F^-1 as preconditioner
+        (double-double refinement); returns
         (x, info dict) or (x_hi, x_lo, info) with ``want_lo``.  ``out`` (same
         shape as rhs, contiguous float64) receives x if given."""
         r2 = _as_2d(rhs)
@@ -206,7 +217,7 @@ class Factorization:
         if rc != HIF_ERR_NOCONV or raise_on_noconv:
             _check(rc, self._lib)
         d = dict(iters=info.iters, outer=info.outer, converged=bool(info.converged),
-                 relres_max=info.relres_max, relres_fp64_max=info.relres_fp64_max)
+                 relres_max=info.relres_max, relres_fp64_max=info.relres_fp64_max, gmres_iters=info.gmres_iters)
         if want_lo:
             return x.reshape(rhs.shape), xlo.reshape(rhs.shape), d
         return x.reshape(rhs.shape), d
@@ -385,5 +396,5 @@ def solve_batch(facts, rhs_list, tol: float = 1e-12, maxit: int = 1000, nthreads
         i = infos[p]
         out.append((xs[p].reshape(rhs_list[p].shape),
                     dict(iters=i.iters, outer=i.outer, converged=bool(i.converged), relres_max=i.relres_max,
-                         relres_fp64_max=i.relres_fp64_max)))
+                         relres_fp64_max=i.relres_fp64_max, gmres_iters=i.gmres_iters)))
     return out
