@@ -207,6 +207,20 @@ int hif_matvec(hif_handle* h, const double* x, double* y, int nrhs, int ld);
 
 /* hif_stats -- sizes and counts of the factorization (Section 5 columns). */
 /*
+ * hif_estimate -- the a posteriori error estimates of Section 5 by power
+ * iteration from the start vector x0 (N values, host or device; the paper
+ * starts from a uniform random vector), each norm estimate ||op x_k|| with
+ * x_{k+1} = op x_k / ||op x_k||, stopped when two successive estimates differ
+ * by at most rtol of the newer one (the paper: 1e-2) or after maxit products:
+ *   e_a = ||A - F|| / ||A||   (A: the stencil operator in FP64; F applied as
+ *                              stored, FP32 in the FP32 apply modes)
+ *   e_s = ||I - A F^-1|| = ||(I - F^-1 A)(I - A F^-1)||^(1/2)
+ * (A and F are symmetric).  HIF_ERR_ARG: NULL argument, rtol <= 0 or
+ * maxit < 1.
+ */
+int hif_estimate(hif_handle* h, const double* x0, double rtol, int maxit, double* e_a, double* e_s);
+
+/*
  * hif_set_solver -- the inner solver of later hif_solve calls on h:
  * HIF_SOLVER_* (default AUTO) and the GMRES restart length (0 -> 50,
  * else 2..500).  Flexible GMRES (Saad, 1993) right-preconditioned by F^-1:

@@ -1369,6 +1369,71 @@ int check_dev_err(hif_handle* h) {
 // ===========================================================================
 // C ABI
 // ===========================================================================
+// Power iteration ||op|| = lim ||op x|| / ||x|| (Section 5) on device
+// N-vectors, from x0, stopped when two successive estimates differ by at most
+// rtol of the newer one (or after maxit products).
+struct PowerNorm {
+  hif_handle* h;
+  int64_t N;
+  cudaStream_t st;
+  DevBuf x, y, t, u, wf, part, cnt, nrm, one;
+  explicit PowerNorm(hif_handle* h_) : h(h_), N(h_->G.N), st(h_->st) {
+    const size_t vb = sizeof(double) * N;
+    x.alloc(vb, st); y.alloc(vb, st); t.alloc(vb, st); u.alloc(vb, st);
+    if (h->precision != HIF_PREC_FP64) wf.alloc(sizeof(float) * N, st);
+    part.alloc(sizeof(double) * kVecBlocksMax, st);
+    cnt.alloc(sizeof(unsigned), st);
+    nrm.alloc(sizeof(double), st);
+    one.alloc(sizeof(double), st);
+    CU(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned), st));
+    const double o = 1.0;
+    CU(cudaMemcpyAsync(one.p, &o, sizeof(double), cudaMemcpyHostToDevice, st));
+    CU(cudaStreamSynchronize(st));
+  }
+  void matvec(const double* in, double* out) {
+    launch_matvec(h->gi, h->a_stag.as<double>(), h->bnode.as<double>(), in, 1, out, 1, 1, st);
+  }
+  void fac(int mode, const double* in, double* out) {   // out = F in or F^-1 in
+    if (out != in) CU(cudaMemcpyAsync(out, in, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+    if (h->precision != HIF_PREC_FP64) {
+      launch_convert<double, float>(N, 1, out, 1, wf.as<float>(), 1, st);
+      run_apply<float>(h, mode, wf.as<float>(), 1);
+      launch_convert<float, double>(N, 1, wf.as<float>(), 1, out, 1, st);
+    } else {
+      run_apply<double>(h, mode, out, 1);
+    }
+  }
+  void sub(double* w, const double* v) {   // w -= v
+    launch_multi_axpy(N, 1, v, 0, 1, one.as<double>(), w, st);
+  }
+  double norm(const double* v) {
+    launch_sqnorm(N, 1, v, part.as<double>(), cnt.as<unsigned>(), nrm.as<double>(), st);
+    double n2 = 0.0;
+    CU(cudaMemcpyAsync(&n2, nrm.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    return std::sqrt(n2);
+  }
+  // op(in, out) must not write `in`
+  template <typename Op>
+  double run(const double* x0, double rtol, int maxit, Op op, int& iters) {
+    double* X = x.as<double>();
+    double* Y = y.as<double>();
+    CU(cudaMemcpyAsync(X, x0, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+    norm(X);
+    launch_normalize(N, 1, X, nrm.as<double>(), X, nullptr, st);
+    double est = 0.0;
+    for (iters = 1; iters <= maxit; ++iters) {
+      op(X, Y);
+      const double ny = norm(Y);
+      if (ny == 0.0) return 0.0;
+      if (est > 0.0 && std::fabs(ny - est) <= rtol * ny) return ny;
+      est = ny;
+      launch_normalize(N, 1, Y, nrm.as<double>(), X, nullptr, st);
+    }
+    return est;
+  }
+};
+
 extern "C" {
 
 const char* hif_last_error(void) { return g_last_error.c_str(); }
@@ -1491,6 +1556,50 @@ int hif_apply(hif_handle* h, int mode, const double* x, double* y, int nrhs, int
     CU(cudaGetLastError());
     CU(cudaStreamSynchronize(st));
     if (h->profile) resolve_profile(h);
+    check_dev_err(h);
+  } catch (const HifError& e) {
+    return set_error(e.code, e.msg);
+  }
+  return HIF_OK;
+}
+
+int hif_estimate(hif_handle* h, const double* x0, double rtol, int maxit, double* e_a, double* e_s) {
+  if (!h || !x0 || !e_a || !e_s) return set_error(HIF_ERR_ARG, "NULL argument");
+  if (!(rtol > 0.0) || maxit < 1) return set_error(HIF_ERR_ARG, "need rtol > 0 and maxit >= 1");
+  try {
+    const int64_t N = h->G.N;
+    cudaStream_t st = h->st;
+    DevBuf v0, tmp;
+    v0.alloc(sizeof(double) * N, st);
+    stage_in(x0, 1, 1, N, v0.as<double>(), st, tmp);
+    PowerNorm P(h);
+    double* T = P.t.as<double>();
+    int it = 0;
+    const double nA = P.run(v0.as<double>(), rtol, maxit, [&](const double* in, double* out) { P.matvec(in, out); },
+                            it);
+    const double nE = P.run(v0.as<double>(), rtol, maxit,
+                            [&](const double* in, double* out) {   // (A - F) in
+                              P.fac(HIF_APPLY_F, in, T);
+                              P.matvec(in, out);
+                              P.sub(out, T);
+                            },
+                            it);
+    double* U = P.u.as<double>();
+    const size_t vb = sizeof(double) * N;
+    const double nM = P.run(v0.as<double>(), rtol, maxit,
+                            [&](const double* in, double* out) {   // (I - F^-1 A)(I - A F^-1) in
+                              P.fac(HIF_APPLY_FINV, in, T);
+                              P.matvec(T, out);                    // A F^-1 in
+                              CU(cudaMemcpyAsync(U, in, vb, cudaMemcpyDeviceToDevice, st));
+                              P.sub(U, out);                       // w = in - A F^-1 in
+                              P.matvec(U, T);                      // A w
+                              P.fac(HIF_APPLY_FINV, T, T);         // F^-1 A w
+                              CU(cudaMemcpyAsync(out, U, vb, cudaMemcpyDeviceToDevice, st));
+                              P.sub(out, T);                       // w - F^-1 A w
+                            },
+                            it);
+    *e_a = nA > 0.0 ? nE / nA : 0.0;
+    *e_s = std::sqrt(nM);
     check_dev_err(h);
   } catch (const HifError& e) {
     return set_error(e.code, e.msg);

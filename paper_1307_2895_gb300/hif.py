@@ -65,7 +65,7 @@ class _Profile(ctypes.Structure):
 _LIB = None
 EXPORTS = ["hif_factor", "hif_apply", "hif_solve", "hif_matvec", "hif_stats", "hif_structure",
            "hif_profile", "hif_kernel_launches", "hif_residual_norms_noalloc", "hif_front_log", "hif_mlp_grad",
-           "hif_mlp_train", "hif_mlp_predict", "hif_schur_update_f32", "hif_factor_batch", "hif_solve_batch", "hif_set_solver", "hif_free",
+           "hif_mlp_train", "hif_mlp_predict", "hif_schur_update_f32", "hif_factor_batch", "hif_solve_batch", "hif_set_solver", "hif_estimate", "hif_free",
            "hif_last_error"]
 
 
@@ -119,6 +119,8 @@ def load(build_if_missing: bool = False):
     lib.hif_solve_batch.restype = i
     lib.hif_set_solver.argtypes = [vp, i, i]
     lib.hif_set_solver.restype = i
+    lib.hif_estimate.argtypes = [vp, vp, d, i, ctypes.POINTER(d), ctypes.POINTER(d)]
+    lib.hif_estimate.restype = i
     lib.hif_free.argtypes = [vp]
     lib.hif_free.restype = None
     lib.hif_last_error.argtypes = []
@@ -196,6 +198,13 @@ class Factorization:
         y = _empty_like(x, x2.shape)
         _check(self._lib.hif_matvec(self._live(), _ptr(x2), _ptr(y), x2.shape[1], x2.shape[1]), self._lib)
         return y.reshape(x.shape)
+
+    def estimate(self, x0, rtol: float = 1e-2, maxit: int = 200):
+        """hif_estimate: (e_a, e_s) by power iteration from x0 (Section 5)."""
+        ea, es = ctypes.c_double(), ctypes.c_double()
+        _check(self._lib.hif_estimate(self._live(), _ptr(x0), rtol, maxit, ctypes.byref(ea), ctypes.byref(es)),
+               self._lib)
+        return ea.value, es.value
 
     def set_solver(self, solver: str = "auto", restart: int = 0) -> None:
         """hif_set_solver: inner solver of later solves ("auto": CG with a

@@ -74,3 +74,10 @@ def test_schur_update_argument_errors_without_gpu():
     assert lib.hif_schur_update_f32(1, 4, 4, None, None, 3, None) == hif.HIF_ERR_ARG   # NULL U
     assert lib.hif_schur_update_f32(3, 0, 4, None, None, 3, None) == hif.HIF_OK        # nothing to do
 
+
+def test_estimate_and_solver_argument_errors_without_gpu():
+    lib = hif.load()
+    ea, es = ctypes.c_double(), ctypes.c_double()
+    assert lib.hif_estimate(None, None, 1e-2, 10, ctypes.byref(ea), ctypes.byref(es)) == hif.HIF_ERR_ARG
+    assert lib.hif_set_solver(None, 0, 0) == hif.HIF_ERR_ARG
+
