@@ -106,6 +106,12 @@ typedef struct hif_opts {
                            parts (exact split, about FP32 accuracy), 2 -> two
                            parts (about 2^-21), 1 -> plain TF32, < 0 -> FP32 on
                            the SIMT pipes.  Ignored in the FP64 modes.          */
+  int autotune;         /* 0: the first F^-1 application that meets a sweep
+                           launch shape (operation, type, right-hand sides,
+                           blocks, largest block) times candidate shapes
+                           (threads per block, shared-memory staging) on a
+                           scratch copy and keeps the fastest, process-wide;
+                           < 0: the built-in shapes.                            */
 } hif_opts;
 
 typedef struct hif_handle hif_handle;
@@ -219,6 +225,16 @@ int hif_matvec(hif_handle* h, const double* x, double* y, int nrhs, int ld);
  * maxit < 1.
  */
 int hif_estimate(hif_handle* h, const double* x0, double rtol, int maxit, double* e_a, double* e_s);
+
+/*
+ * hif_autotune_table -- the sweep launch shapes chosen so far by the
+ * autotuner (hif_opts.autotune), process-wide.  *count receives the number
+ * of entries; if out is not NULL, min(cap, count) rows of 9 ints are written:
+ * operation (0 up, 1 down), element bytes, right-hand sides, blocks, largest
+ * np, largest nq, front flag, then the choice: threads per block (0: built-in)
+ * and staging (-1: built-in, 0: off).  HIF_ERR_ARG: NULL count.
+ */
+int hif_autotune_table(int* out, long long cap, long long* count);
 
 /*
  * hif_set_solver -- the inner solver of later hif_solve calls on h:

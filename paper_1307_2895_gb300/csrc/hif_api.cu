@@ -165,6 +165,7 @@ struct hif_handle {
   int big_cell = 192;   // cells with at least this many interior DOFs use the tiled elimination
   bool coop_qr = true;  // large fronts: pivoted QR by co-resident block groups
   int tc_split = 3;     // FP32 tiled elimination on the tensor cores: TF32 parts per value (1..3), 0 = SIMT
+  bool autotune = true; // time the sweep launch shapes on first use
   int id_mode = HIF_ID_QR;
   int oversample = 10;
   unsigned long long seed = 0;
@@ -786,6 +787,76 @@ void demote_factor(hif_handle* h) {
   h->apply_bytes /= 2.0;
 }
 
+// ---------------------------------------------------------------------------
+// Autotuner of the sweep launch shapes.  A launch is identified by what the
+// kernels' speed depends on: operation, element type, right-hand sides,
+// number of blocks and the largest block (np, nq).  The first eager F^-1
+// application that meets a shape times every candidate shape three times on
+// a scratch copy of the vectors (CUDA events on the library's stream) and
+// keeps the fastest; the built-in shape wins unless another is at least 2%
+// faster.  Choices are process-wide, so later factorizations of the same
+// grid reuse them, and nothing is timed while a graph is being captured.
+// ---------------------------------------------------------------------------
+struct TuneKey {
+  int op, tsize, nrhs, nblocks, max_np, max_nq, is_front;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(op, tsize, nrhs, nblocks, max_np, max_nq, is_front) <
+           std::tie(o.op, o.tsize, o.nrhs, o.nblocks, o.max_np, o.max_nq, o.is_front);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, SweepShape> g_tune;
+
+template <typename T>
+SweepShape tuned_shape(hif_handle* h, int op, const SweepLevel& S, int is_front, const T* fac, const T* x,
+                       int nrhs) {
+  const TuneKey key{op, (int)sizeof(T), nrhs, S.nblocks, S.max_np, S.max_nq, is_front};
+  {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) return it->second;
+  }
+  cudaStream_t st = h->st;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  CU(cudaStreamIsCapturing(st, &cap));
+  if (cap != cudaStreamCaptureStatusNone) return SweepShape{};
+  const size_t xb = sizeof(T) * (size_t)h->G.N * nrhs;
+  DevBuf xs;
+  xs.alloc(xb, st);
+  cudaEvent_t e0, e1;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  SweepShape best{};
+  float best_ms = 0.f;
+  bool first = true;
+  for (int staged : {-1, 0})
+    for (int threads : {0, 64, 128, 256, 512}) {
+      const SweepShape cand{threads, staged};
+      float ms = 1e30f;
+      for (int rep = 0; rep < 3; ++rep) {
+        CU(cudaMemcpyAsync(xs.p, x, xb, cudaMemcpyDeviceToDevice, st));
+        CU(cudaEventRecord(e0, st));
+        launch_sweep<T>(op, S.desc, S.nblocks, S.ipool, fac, xs.as<T>(), nrhs, nrhs, is_front, S.max_np, S.max_nq,
+                        h->dev_err.as<int>(), st, cand);
+        CU(cudaEventRecord(e1, st));
+        CU(cudaEventSynchronize(e1));
+        float t = 0.f;
+        CU(cudaEventElapsedTime(&t, e0, e1));
+        ms = std::min(ms, t);
+      }
+      if (first || ms < 0.98f * best_ms) {
+        best = cand;
+        best_ms = ms;
+        first = false;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  g_tune[key] = best;
+  return best;
+}
+
 template <typename T>
 void run_apply(hif_handle* h, int mode, T* x, int nrhs) {
   const int L = h->G.L;
@@ -805,8 +876,10 @@ void run_apply(hif_handle* h, int mode, T* x, int nrhs) {
       }
       CU(cudaEventRecord(h->ev_pool[h->ev_used], st));
     }
+    const SweepShape shape =
+        (h->autotune && mode == HIF_APPLY_FINV) ? tuned_shape<T>(h, op, S, is_front, fac, x, nrhs) : SweepShape{};
     launch_sweep<T>(op, S.desc, S.nblocks, S.ipool, fac, x, nrhs, nrhs, is_front, S.max_np, S.max_nq,
-                    h->dev_err.as<int>(), st);
+                    h->dev_err.as<int>(), st, shape);
     if (prof) {
       CU(cudaEventRecord(h->ev_pool[h->ev_used + 1], st));
       h->ev_used += 2;
@@ -1478,6 +1551,7 @@ int hif_factor(const hif_grid* grid, const double* a_stag, const double* b, cons
     h->seed = opts ? opts->seed : 0;
     if (opts && opts->big_cell != 0) h->big_cell = opts->big_cell < 0 ? 0x7fffffff : opts->big_cell;
     if (opts) h->tc_split = opts->tensor_cores < 0 ? 0 : opts->tensor_cores == 0 ? 3 : std::min(opts->tensor_cores, 3);
+    if (opts) h->autotune = opts->autotune >= 0;
     if (h->id_mode == HIF_ID_LEARNED && !(opts && opts->rank_model))
       throw HifError(HIF_ERR_ARG, "HIF_ID_LEARNED needs opts.rank_model");
     h->st = opts ? (cudaStream_t)opts->stream : nullptr;
@@ -1660,6 +1734,23 @@ int hif_solve(hif_handle* h, const double* rhs, double* x, double* x_lo, int nrh
   if (info) *info = loc;
   if (rc == HIF_ERR_NOCONV) set_error(rc, "the iteration reached maxit before tol");
   return rc;
+}
+
+int hif_autotune_table(int* out, long long cap, long long* count) {
+  if (!count) return set_error(HIF_ERR_ARG, "NULL count");
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  *count = (long long)g_tune.size();
+  if (!out) return HIF_OK;
+  long long k = 0;
+  for (const auto& kv : g_tune) {
+    if (k >= cap) break;
+    const TuneKey& t = kv.first;
+    const int row[9] = {t.op, t.tsize, t.nrhs, t.nblocks, t.max_np, t.max_nq, t.is_front, kv.second.threads,
+                        kv.second.staged};
+    std::copy(row, row + 9, out + 9 * k);
+    ++k;
+  }
+  return HIF_OK;
 }
 
 int hif_set_solver(hif_handle* h, int solver, int restart) {

@@ -71,9 +71,17 @@ void launch_sketch_sizes(const FrontDesc* fronts, int nfronts, const float* pred
                          int* sketch, cudaStream_t st);
 
 // apply sweeps (kernels_apply.cu); op: 0 up, 1 down, 2 fwd_up, 3 fwd_down
+// Launch shape of a sweep launch: threads per block (0: one per row and
+// column group of the largest block, 32..256) and whether blocks stage their
+// factor in shared memory (-1: when it fits, 0: never).
+struct SweepShape {
+  int threads = 0;
+  int staged = -1;
+};
 template <typename T>
 void launch_sweep(int op, const ApplyDesc* blocks, int nblocks, const int* ipool, const T* fac, T* x,
-                  int nrhs, int ldx, int is_front, int max_np, int max_nq, int* err, cudaStream_t st);
+                  int nrhs, int ldx, int is_front, int max_np, int max_nq, int* err, cudaStream_t st,
+                  SweepShape shape = SweepShape{});
 
 // stencil operator and CG vector operations (kernels_solve.cu)
 void launch_matvec(GridInfo g, const double* a_stag, const double* b, const double* x, int ldx,

@@ -430,10 +430,10 @@ static size_t stage_smem(int max_np, int max_nq, int is_front) {
 template <typename T, int R>
 static void launch_sweep_R(int op, const ApplyDesc* blocks, int nblocks, const int* ipool,
                            const T* fac, T* x, int nr, int ldx, int is_front, int max_np,
-                           int max_nq, int* err, cudaStream_t st) {
+                           int max_nq, int* err, cudaStream_t st, SweepShape shape) {
   const size_t vsm = vec_smem<T>(R, max_np, max_nq);
   const size_t ssm = stage_smem<T>(max_np, max_nq, is_front);
-  const int staged = (op <= 1) && (vsm + ssm <= kStageCap);
+  const int staged = (op <= 1) && (vsm + ssm <= kStageCap) && shape.staged != 0;
   const size_t smem = vsm + (staged ? ssm : 0);
   void (*fn)(const ApplyDesc*, const int*, const T*, T*, int, int, int, int, int*) = nullptr;
   switch (op) {
@@ -456,6 +456,7 @@ static void launch_sweep_R(int op, const ApplyDesc* blocks, int nblocks, const i
   int work = (max_np > max_nq ? max_np : max_nq) * NG;
   int threads = ((work + 31) / 32) * 32;
   threads = threads < 32 ? 32 : (threads > 256 ? 256 : threads);
+  if (shape.threads > 0) threads = shape.threads;
   note_launches(1);
   if (op <= 1) {
     cudaLaunchConfig_t cfg = {};
@@ -483,26 +484,27 @@ int sweep_chunk(int max_np, int max_nq, int nrhs) {
 
 template <typename T>
 void launch_sweep(int op, const ApplyDesc* blocks, int nblocks, const int* ipool, const T* fac,
-                  T* x, int nrhs, int ldx, int is_front, int max_np, int max_nq, int* err, cudaStream_t st) {
+                  T* x, int nrhs, int ldx, int is_front, int max_np, int max_nq, int* err, cudaStream_t st,
+                  SweepShape shape) {
   if (nblocks == 0) return;
   const int R = sweep_chunk<T>(max_np, max_nq, nrhs);
   for (int r0 = 0; r0 < nrhs; r0 += R) {
     const int nr = (nrhs - r0) < R ? (nrhs - r0) : R;
     T* xr = x + r0;
     switch (R) {
-      case 32: launch_sweep_R<T, 32>(op, blocks, nblocks, ipool, fac, xr, nr, ldx, is_front, max_np, max_nq, err, st); break;
-      case 16: launch_sweep_R<T, 16>(op, blocks, nblocks, ipool, fac, xr, nr, ldx, is_front, max_np, max_nq, err, st); break;
-      case 8: launch_sweep_R<T, 8>(op, blocks, nblocks, ipool, fac, xr, nr, ldx, is_front, max_np, max_nq, err, st); break;
-      case 4: launch_sweep_R<T, 4>(op, blocks, nblocks, ipool, fac, xr, nr, ldx, is_front, max_np, max_nq, err, st); break;
-      case 2: launch_sweep_R<T, 2>(op, blocks, nblocks, ipool, fac, xr, nr, ldx, is_front, max_np, max_nq, err, st); break;
-      default: launch_sweep_R<T, 1>(op, blocks, nblocks, ipool, fac, xr, nr, ldx, is_front, max_np, max_nq, err, st); break;
+      case 32: launch_sweep_R<T, 32>(op, blocks, nblocks, ipool, fac, xr, nr, ldx, is_front, max_np, max_nq, err, st, shape); break;
+      case 16: launch_sweep_R<T, 16>(op, blocks, nblocks, ipool, fac, xr, nr, ldx, is_front, max_np, max_nq, err, st, shape); break;
+      case 8: launch_sweep_R<T, 8>(op, blocks, nblocks, ipool, fac, xr, nr, ldx, is_front, max_np, max_nq, err, st, shape); break;
+      case 4: launch_sweep_R<T, 4>(op, blocks, nblocks, ipool, fac, xr, nr, ldx, is_front, max_np, max_nq, err, st, shape); break;
+      case 2: launch_sweep_R<T, 2>(op, blocks, nblocks, ipool, fac, xr, nr, ldx, is_front, max_np, max_nq, err, st, shape); break;
+      default: launch_sweep_R<T, 1>(op, blocks, nblocks, ipool, fac, xr, nr, ldx, is_front, max_np, max_nq, err, st, shape); break;
     }
   }
 }
 
 template void launch_sweep<double>(int, const ApplyDesc*, int, const int*, const double*, double*,
-                                   int, int, int, int, int, int*, cudaStream_t);
+                                   int, int, int, int, int, int*, cudaStream_t, SweepShape);
 template void launch_sweep<float>(int, const ApplyDesc*, int, const int*, const float*, float*,
-                                  int, int, int, int, int, int*, cudaStream_t);
+                                  int, int, int, int, int, int*, cudaStream_t, SweepShape);
 
 }  // namespace hif

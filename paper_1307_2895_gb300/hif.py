@@ -38,7 +38,8 @@ class _Grid(ctypes.Structure):
 class _Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("skip_levels", ctypes.c_int), ("id_mode", ctypes.c_int),
                 ("oversample", ctypes.c_int), ("stream", ctypes.c_void_p), ("rank_model", ctypes.c_void_p),
-                ("seed", ctypes.c_ulonglong), ("big_cell", ctypes.c_int), ("tensor_cores", ctypes.c_int)]
+                ("seed", ctypes.c_ulonglong), ("big_cell", ctypes.c_int), ("tensor_cores", ctypes.c_int),
+                ("autotune", ctypes.c_int)]
 
 
 class _SolveInfo(ctypes.Structure):
@@ -65,7 +66,7 @@ class _Profile(ctypes.Structure):
 _LIB = None
 EXPORTS = ["hif_factor", "hif_apply", "hif_solve", "hif_matvec", "hif_stats", "hif_structure",
            "hif_profile", "hif_kernel_launches", "hif_residual_norms_noalloc", "hif_front_log", "hif_mlp_grad",
-           "hif_mlp_train", "hif_mlp_predict", "hif_schur_update_f32", "hif_factor_batch", "hif_solve_batch", "hif_set_solver", "hif_estimate", "hif_free",
+           "hif_mlp_train", "hif_mlp_predict", "hif_schur_update_f32", "hif_factor_batch", "hif_solve_batch", "hif_set_solver", "hif_estimate", "hif_autotune_table", "hif_free",
            "hif_last_error"]
 
 
@@ -121,6 +122,8 @@ def load(build_if_missing: bool = False):
     lib.hif_set_solver.restype = i
     lib.hif_estimate.argtypes = [vp, vp, d, i, ctypes.POINTER(d), ctypes.POINTER(d)]
     lib.hif_estimate.restype = i
+    lib.hif_autotune_table.argtypes = [vp, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)]
+    lib.hif_autotune_table.restype = i
     lib.hif_free.argtypes = [vp]
     lib.hif_free.restype = None
     lib.hif_last_error.argtypes = []
@@ -333,6 +336,17 @@ def mlp_predict(X, params, stream=None):
     return y
 
 
+def autotune_table():
+    """hif_autotune_table: rows (op, elem_bytes, nrhs, nblocks, max_np, max_nq,
+    is_front, threads, staged) of the sweep shapes chosen so far."""
+    lib = load()
+    n = ctypes.c_longlong()
+    _check(lib.hif_autotune_table(None, 0, ctypes.byref(n)), lib)
+    buf = np.zeros((max(n.value, 1), 9), dtype=np.int32)
+    _check(lib.hif_autotune_table(buf.ctypes.data, n.value, ctypes.byref(n)), lib)
+    return buf[:n.value]
+
+
 def schur_update(G, U, split: int = 3, stream=None):
     """hif_schur_update_f32: U_b -= G_b G_b^T in place on the tensor cores
     (CUDA float32 tensors G of shape (nb, m, k) and U of shape (nb, m, m))."""
@@ -347,14 +361,15 @@ def schur_update(G, U, split: int = 3, stream=None):
 
 def factor(dim: int, n: int, a_stag, b, eps: float, variant: str = "hifde", precision: str = "fp64",
            leaf: int = 8, skip_levels: int = 0, stream=None, id_mode: str = "qr", rank_model=None,
-           oversample: int = 10, seed: int = 0, big_cell: int = 0, tensor_cores: int = 0) -> Factorization:
+           oversample: int = 10, seed: int = 0, big_cell: int = 0, tensor_cores: int = 0,
+           autotune: bool = True) -> Factorization:
     """hif_factor: MF or HIF-DE of the stencil operator defined by (a_stag, b).
     tensor_cores (mixed precision): 0 three-part TF32 split (about FP32),
     2 two-part, 1 plain TF32, -1 FP32 on the SIMT pipes."""
     lib = load()
     grid = _Grid(dim, n, leaf, VARIANTS[variant])
     opts = _Opts(PRECISIONS[precision], skip_levels, ID_MODES[id_mode], oversample, _stream_ptr(stream),
-                 _ptr(rank_model, "float32"), seed, big_cell, tensor_cores)
+                 _ptr(rank_model, "float32"), seed, big_cell, tensor_cores, 0 if autotune else -1)
     h = ctypes.c_void_p()
     rc = lib.hif_factor(ctypes.byref(grid), _ptr(a_stag), _ptr(b), None, float(eps), ctypes.byref(opts),
                         ctypes.byref(h))
@@ -363,7 +378,7 @@ def factor(dim: int, n: int, a_stag, b, eps: float, variant: str = "hifde", prec
 
 
 def factor_batch(problems, eps: float, variant: str = "hifde", precision: str = "fp64", leaf: int = 8,
-                 nthreads: int = 8, big_cell: int = 0, tensor_cores: int = 0):
+                 nthreads: int = 8, big_cell: int = 0, tensor_cores: int = 0, autotune: bool = True):
     """hif_factor_batch: problems = [(dim, n, a_stag, b), ...], factored
     concurrently (one stream each); returns one Factorization per problem."""
     lib = load()
@@ -372,7 +387,8 @@ def factor_batch(problems, eps: float, variant: str = "hifde", precision: str = 
     pa = (ctypes.c_void_p * m)(*[_ptr(a) for _, _, a, _ in problems])
     pb = (ctypes.c_void_p * m)(*[_ptr(b) for _, _, _, b in problems])
     pe = (ctypes.c_double * m)(*([float(eps)] * m))
-    opts = _Opts(PRECISIONS[precision], 0, ID_MODES["qr"], 10, None, None, 0, big_cell, tensor_cores)
+    opts = _Opts(PRECISIONS[precision], 0, ID_MODES["qr"], 10, None, None, 0, big_cell, tensor_cores,
+                 0 if autotune else -1)
     hs = (ctypes.c_void_p * m)()
     rc = lib.hif_factor_batch(m, grids, pa, pb, pe, ctypes.byref(opts), nthreads, hs)
     facts = [Factorization(ctypes.c_void_p(hs[p]), lib, (problems[p][1] - 1) ** problems[p][0]) if hs[p] else None

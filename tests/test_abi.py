@@ -81,3 +81,10 @@ def test_estimate_and_solver_argument_errors_without_gpu():
     assert lib.hif_estimate(None, None, 1e-2, 10, ctypes.byref(ea), ctypes.byref(es)) == hif.HIF_ERR_ARG
     assert lib.hif_set_solver(None, 0, 0) == hif.HIF_ERR_ARG
 
+
+def test_autotune_table_without_gpu():
+    lib = hif.load()
+    assert lib.hif_autotune_table(None, 0, None) == hif.HIF_ERR_ARG
+    n = ctypes.c_longlong(-1)
+    assert lib.hif_autotune_table(None, 0, ctypes.byref(n)) == hif.HIF_OK and n.value == 0
+
