@@ -1005,11 +1005,9 @@ struct Precond {
       return;
     }
     if (!exec) {
-      // capture without sweep events: a replay is timed as one unit
-      if (h->profile) {
-        CU(cudaStreamSynchronize(h->st));
-        resolve_profile(h);
-      }
+      // capture without sweep events: a replay is timed as one unit.  The
+      // events of the eager application stay in the pool; they are resolved
+      // with the replays' after the solve has synchronized (settle).
       const int prof = h->profile;
       const double b0 = h->prof_bytes;
       const long long l0 = h->prof_launches;
