@@ -196,7 +196,8 @@ struct hif_handle {
   long long graph_launches = 0;
   // pinned ring of per-iteration squared residual norms (inner CG), so that
   // iterations can run in batches between host checks
-  double* rr_ring = nullptr;
+  double* rr_ring = nullptr;       // mapped pinned memory
+  double* rr_ring_dev = nullptr;   // its device address
   cudaEvent_t it_ev[2] = {nullptr, nullptr};
   // inner solver of the refinement steps (HIF_SOLVER_*) and GMRES restart length
   int solver = HIF_SOLVER_AUTO;
@@ -1071,22 +1072,26 @@ struct Precond {
   }
 };
 
+// ring: device pointer of this iteration's row of the host ring (rr, then
+// r.z), or null (the last block of the reductions writes it, and the next
+// active flags, so no copy or flag kernel is queued)
 template <typename TZ>
 void cg_step_kernels(hif_handle* h, SolveWork& W, TZ* wp, int par, int restart, int phase,
-                     double* partials, unsigned* counter) {
+                     double* partials, unsigned* counter, double* ring = nullptr) {
   const int64_t N = W.N;
   const int R = W.R;
   cudaStream_t st = h->st;
   if (phase == 0) {
-    launch_dot2_e<TZ>(N, R, W.Rv.as<double>(), wp, W.Q.as<double>(), partials, counter, W.rzzq[par], st);
+    launch_dot2_e<TZ>(N, R, W.Rv.as<double>(), wp, W.Q.as<double>(), partials, counter, W.rzzq[par], st,
+                      ring ? ring + R : nullptr);
     launch_update_p_e<TZ>(N, R, W.P.as<double>(), wp, W.alpha, W.rzzq[par ^ 1], W.rzzq[par], W.active,
                           restart, st);
   } else {
     launch_mv_dot_e(h->gi, h->stencil_w.as<double>(), W.P.as<double>(), W.Q.as<double>(), R, partials, counter,
                     W.pq, st);
     launch_axpy2_e<TZ>(N, R, W.D.as<double>(), W.Rv.as<double>(), W.P.as<double>(), W.Q.as<double>(),
-                       W.rzzq[par], W.pq, W.active, W.alpha, partials, counter, W.rr, wp, st);
-    launch_set_active(R, W.rr, W.thr2, W.active, st);
+                       W.rzzq[par], W.pq, W.active, W.alpha, partials, counter, W.rr, wp, st, W.thr2, W.active,
+                       ring);
   }
 }
 
@@ -1108,7 +1113,10 @@ int inner_pcg(hif_handle* h, SolveWork& W, Precond& M, const std::vector<double>
   double* partials = W.part.as<double>();
   unsigned* counter = W.cnt.as<unsigned>();
   const size_t vb = sizeof(double) * N * R;
-  if (!h->rr_ring) CU(cudaHostAlloc(&h->rr_ring, sizeof(double) * kRingRows * kRingCols, cudaHostAllocDefault));
+  if (!h->rr_ring) {
+    CU(cudaHostAlloc(&h->rr_ring, sizeof(double) * kRingRows * kRingCols, cudaHostAllocMapped));
+    CU(cudaHostGetDevicePointer(reinterpret_cast<void**>(&h->rr_ring_dev), h->rr_ring, 0));
+  }
   if (!h->it_ev[0]) {
     CU(cudaEventCreateWithFlags(&h->it_ev[0], cudaEventDisableTiming));
     CU(cudaEventCreateWithFlags(&h->it_ev[1], cudaEventDisableTiming));
@@ -1133,17 +1141,14 @@ int inner_pcg(hif_handle* h, SolveWork& W, Precond& M, const std::vector<double>
   };
   // queue one iteration; false when maxit stops it after the preconditioner
   auto issue = [&]() -> bool {
+    double* row = h->rr_ring_dev + (size_t)(issued % kRingRows) * kRingCols;
     M.apply();
-    if (W.f32) cg_step_kernels<float>(h, W, W.WP.as<float>(), par, restart, 0, partials, counter);
-    else cg_step_kernels<double>(h, W, W.WP.as<double>(), par, restart, 0, partials, counter);
+    if (W.f32) cg_step_kernels<float>(h, W, W.WP.as<float>(), par, restart, 0, partials, counter, row);
+    else cg_step_kernels<double>(h, W, W.WP.as<double>(), par, restart, 0, partials, counter, row);
     restart = 0;
     if (issued >= maxit) return false;
-    if (W.f32) cg_step_kernels<float>(h, W, W.WP.as<float>(), par, 0, 1, partials, counter);
-    else cg_step_kernels<double>(h, W, W.WP.as<double>(), par, 0, 1, partials, counter);
-    CU(cudaMemcpyAsync(h->rr_ring + (size_t)(issued % kRingRows) * kRingCols, W.rr, sizeof(double) * R,
-                       cudaMemcpyDeviceToHost, st));
-    CU(cudaMemcpyAsync(h->rr_ring + (size_t)(issued % kRingRows) * kRingCols + R, W.rzzq[par], sizeof(double) * R,
-                       cudaMemcpyDeviceToHost, st));
+    if (W.f32) cg_step_kernels<float>(h, W, W.WP.as<float>(), par, 0, 1, partials, counter, row);
+    else cg_step_kernels<double>(h, W, W.WP.as<double>(), par, 0, 1, partials, counter, row);
     CU(cudaEventRecord(h->it_ev[issued & 1], st));
     ++issued;
     par ^= 1;

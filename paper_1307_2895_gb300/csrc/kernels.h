@@ -112,10 +112,11 @@ void launch_mv_dot_e(GridInfo g, const double* W, const double* p, double* q, in
 template <typename TZ>
 void launch_axpy2_e(int64_t N, int R, double* x, double* r, const double* p, const double* q,
                     const double* rz, const double* pq, const int* active, double* alpha, double* partials,
-                    unsigned* counter, double* rr, TZ* zin, cudaStream_t st);
+                    unsigned* counter, double* rr, TZ* zin, cudaStream_t st, const double* thr2 = nullptr,
+                    int* active_next = nullptr, double* ring_rr = nullptr);
 template <typename TZ>
 void launch_dot2_e(int64_t N, int R, const double* r, const TZ* z, const double* q, double* partials,
-                   unsigned* counter, double* out, cudaStream_t st);
+                   unsigned* counter, double* out, cudaStream_t st, double* ring_rz = nullptr);
 template <typename TZ>
 void launch_update_p_e(int64_t N, int R, double* p, const TZ* z, const double* alpha, const double* rz_old,
                        const double* rzzq, const int* active, int restart, cudaStream_t st);

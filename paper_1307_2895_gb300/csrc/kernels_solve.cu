@@ -279,8 +279,10 @@ __global__ void k_sqnorm(int64_t N, int nr, const double* __restrict__ v, double
 // One thread per (unknown, column) element e = i * R + c of an N x R vector
 // (R a power of two, so a grid-stride thread keeps one column); reductions
 // sum threads of equal column in a shared-memory tree, then across blocks.
+// Returns true in the last block, after out[] is written and visible to the
+// whole block (its threads may then act on the sums).
 template <int R, int NG>
-__device__ void grid_reduce_cols(const double (&acc)[NG], double* partials, unsigned* counter,
+__device__ bool grid_reduce_cols(const double (&acc)[NG], double* partials, unsigned* counter,
                                  double* out) {
   __shared__ double shr[NG][kVecThreads];
   __shared__ bool last;
@@ -301,10 +303,12 @@ __device__ void grid_reduce_cols(const double (&acc)[NG], double* partials, unsi
   __syncthreads();
   if (tid == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
   __syncthreads();
-  if (!last) return;
+  if (!last) return false;
   __threadfence();
   last_block_sum(partials, NG * R, &shr[0][0], out);
   if (tid == 0) *counter = 0u;
+  __syncthreads();
+  return true;
 }
 
 // Stencil weights, computed once per problem: W[i*S + 0] = diagonal,
@@ -403,7 +407,8 @@ template <int R, typename TZ>
 __global__ void k_axpy2_e(int64_t N, double* __restrict__ x, double* __restrict__ r,
                           const double* __restrict__ p, const double* __restrict__ q,
                           const double* rz, const double* pq, const int* active, double* alpha_out,
-                          double* partials, unsigned* counter, double* rr, TZ* __restrict__ zin) {
+                          double* partials, unsigned* counter, double* rr, TZ* __restrict__ zin,
+                          const double* thr2, int* active_next, double* ring_rr) {
   const int c = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) % R);
   const double a = (active[c] && pq[c] != 0.0) ? rz[c] / pq[c] : 0.0;
   if (blockIdx.x == 0 && threadIdx.x < R) alpha_out[threadIdx.x] = a;
@@ -435,13 +440,23 @@ __global__ void k_axpy2_e(int64_t N, double* __restrict__ x, double* __restrict_
     zin[e] = (TZ)rv;
     acc[0] = fma(rv, rv, acc[0]);
   }
-  grid_reduce_cols<R, 1>(acc, partials, counter, rr);
+  // the last block (every block has read active[] by then): the columns still
+  // above their threshold, and the sums for the host's ring (mapped memory)
+  if (grid_reduce_cols<R, 1>(acc, partials, counter, rr) && threadIdx.x < R) {
+    const int cc = threadIdx.x;
+    if (active_next) active_next[cc] = rr[cc] > thr2[cc] ? 1 : 0;
+    if (ring_rr) {
+      ring_rr[cc] = rr[cc];
+      __threadfence_system();
+    }
+  }
 }
 
 // out = [r.z | z.q]
 template <int R, typename TZ>
 __global__ void k_dot2_e(int64_t N, const double* __restrict__ r, const TZ* __restrict__ z,
-                         const double* __restrict__ q, double* partials, unsigned* counter, double* out) {
+                         const double* __restrict__ q, double* partials, unsigned* counter, double* out,
+                         double* ring_rz) {
   double acc[2] = {0.0, 0.0};
   const int64_t n = N * R, stride = (int64_t)gridDim.x * blockDim.x;
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -464,7 +479,10 @@ __global__ void k_dot2_e(int64_t N, const double* __restrict__ r, const TZ* __re
     acc[0] = fma(r[e], zv, acc[0]);
     acc[1] = fma(zv, q[e], acc[1]);
   }
-  grid_reduce_cols<R, 2>(acc, partials, counter, out);
+  if (grid_reduce_cols<R, 2>(acc, partials, counter, out) && ring_rz && threadIdx.x < R) {
+    ring_rz[threadIdx.x] = out[threadIdx.x];   // r.z for the host's breakdown check
+    __threadfence_system();
+  }
 }
 
 // beta = -alpha zq / rz_old (flexible / Polak-Ribiere form); p = z + beta p
@@ -742,18 +760,19 @@ void launch_mv_dot_e(GridInfo g, const double* W, const double* p, double* q, in
 template <typename TZ>
 void launch_axpy2_e(int64_t N, int R_, double* x, double* r, const double* p, const double* q,
                     const double* rz, const double* pq, const int* active, double* alpha, double* partials,
-                    unsigned* counter, double* rr, TZ* zin, cudaStream_t st) {
+                    unsigned* counter, double* rr, TZ* zin, cudaStream_t st, const double* thr2,
+                    int* active_next, double* ring_rr) {
   note_launches(1);
   DISPATCH_POW2(R_, k_axpy2_e<R, TZ><<<elem_blocks(N * R), kVecThreads, 0, st>>>(
-      N, x, r, p, q, rz, pq, active, alpha, partials, counter, rr, zin));
+      N, x, r, p, q, rz, pq, active, alpha, partials, counter, rr, zin, thr2, active_next, ring_rr));
 }
 
 template <typename TZ>
 void launch_dot2_e(int64_t N, int R_, const double* r, const TZ* z, const double* q, double* partials,
-                   unsigned* counter, double* out, cudaStream_t st) {
+                   unsigned* counter, double* out, cudaStream_t st, double* ring_rz) {
   note_launches(1);
   DISPATCH_POW2(R_, k_dot2_e<R, TZ><<<elem_blocks(N * R), kVecThreads, 0, st>>>(N, r, z, q, partials, counter,
-                                                                                 out));
+                                                                                 out, ring_rz));
 }
 
 template <typename TZ>
@@ -766,14 +785,14 @@ void launch_update_p_e(int64_t N, int R_, double* p, const TZ* z, const double* 
 
 template void launch_axpy2_e<double>(int64_t, int, double*, double*, const double*, const double*,
                                      const double*, const double*, const int*, double*, double*,
-                                     unsigned*, double*, double*, cudaStream_t);
+                                     unsigned*, double*, double*, cudaStream_t, const double*, int*, double*);
 template void launch_axpy2_e<float>(int64_t, int, double*, double*, const double*, const double*,
                                     const double*, const double*, const int*, double*, double*,
-                                    unsigned*, double*, float*, cudaStream_t);
+                                    unsigned*, double*, float*, cudaStream_t, const double*, int*, double*);
 template void launch_dot2_e<double>(int64_t, int, const double*, const double*, const double*, double*,
-                                    unsigned*, double*, cudaStream_t);
+                                    unsigned*, double*, cudaStream_t, double*);
 template void launch_dot2_e<float>(int64_t, int, const double*, const float*, const double*, double*,
-                                   unsigned*, double*, cudaStream_t);
+                                   unsigned*, double*, cudaStream_t, double*);
 template void launch_update_p_e<double>(int64_t, int, double*, const double*, const double*, const double*,
                                         const double*, const int*, int, cudaStream_t);
 template void launch_update_p_e<float>(int64_t, int, double*, const float*, const double*, const double*,
