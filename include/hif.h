@@ -178,7 +178,8 @@ int hif_apply(hif_handle* h, int mode, const double* x, double* y, int nrhs, int
 
 /*
  * hif_solve -- preconditioned CG (Section 5) on A x = rhs with F^-1 as the
- * preconditioner, one independent iteration per column, started from x = 0,
+ * preconditioner (or GMRES, see hif_set_solver), one independent iteration
+ * per column, started from x = 0,
  * until ||rhs_r - A x_r||_2 <= tol ||rhs_r||_2 for every column, or maxit
  * inner iterations.  The iterate is kept in double-double, x = x_hi + x_lo,
  * and the residual is evaluated in double-double from the bond form of the
@@ -188,7 +189,9 @@ int hif_apply(hif_handle* h, int mode, const double* x, double* y, int nrhs, int
  * x_lo.  CG runs in FP64 on corrections (iterative refinement, each step to
  * max(tol ||rhs|| / (2 ||r||), 1e-9) relative).  x receives x_hi; x_lo may be
  * NULL.  info may be NULL.  Returns HIF_ERR_NOCONV if maxit is reached (x
- * then holds the last iterate).
+ * then holds the last iterate).  F^-1 is applied eagerly on the first
+ * iteration and then replayed from a CUDA graph; the environment variable
+ * HIF_NO_GRAPH=1 keeps every application eager (for diagnosis).
  */
 int hif_solve(hif_handle* h, const double* rhs, double* x, double* x_lo, int nrhs,
               int ld, double tol, int maxit, hif_solve_info* info);
