@@ -14,6 +14,30 @@ namespace hif {
 
 constexpr int kVecThreads = 256;
 
+// Programmatic dependent launch of the CG vector kernels: a kernel waits for
+// its predecessor in the stream to complete (and its writes to be visible)
+// before it reads anything, then lets its own successor launch, so that the
+// successor's launch overlaps this kernel instead of following it.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+static void launch_pdl(void (*kernel)(KArgs...), int grid, int block, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 static inline int vec_blocks(int64_t n) {
   const int64_t b = (n + kVecThreads - 1) / kVecThreads;
   return (int)(b < kVecBlocksMax ? (b > 0 ? b : 1) : kVecBlocksMax);
@@ -378,6 +402,7 @@ __device__ __forceinline__ double stencil_w(const double* __restrict__ W, int m,
 template <int R, int DIM>
 __global__ void k_mv_dot_e(const double* __restrict__ W, int m, int64_t N, const double* __restrict__ p,
                            double* __restrict__ q, double* partials, unsigned* counter, double* pq) {
+  pdl_enter();
   double acc[1] = {0.0};
   const int64_t n = N * R, stride = (int64_t)gridDim.x * blockDim.x;
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -409,6 +434,7 @@ __global__ void k_axpy2_e(int64_t N, double* __restrict__ x, double* __restrict_
                           const double* rz, const double* pq, const int* active, double* alpha_out,
                           double* partials, unsigned* counter, double* rr, TZ* __restrict__ zin,
                           const double* thr2, int* active_next, double* ring_rr) {
+  pdl_enter();
   const int c = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) % R);
   const double a = (active[c] && pq[c] != 0.0) ? rz[c] / pq[c] : 0.0;
   if (blockIdx.x == 0 && threadIdx.x < R) alpha_out[threadIdx.x] = a;
@@ -457,6 +483,7 @@ template <int R, typename TZ>
 __global__ void k_dot2_e(int64_t N, const double* __restrict__ r, const TZ* __restrict__ z,
                          const double* __restrict__ q, double* partials, unsigned* counter, double* out,
                          double* ring_rz) {
+  pdl_enter();
   double acc[2] = {0.0, 0.0};
   const int64_t n = N * R, stride = (int64_t)gridDim.x * blockDim.x;
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -490,6 +517,7 @@ template <int R, typename TZ>
 __global__ void k_update_p_e(int64_t N, double* __restrict__ p, const TZ* __restrict__ z,
                              const double* alpha, const double* rz_old, const double* rzzq,
                              const int* active, int restart) {
+  pdl_enter();
   const int c = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) % R);
   if (!active[c]) return;
   const bool rs = restart || rz_old[c] == 0.0;
@@ -750,11 +778,11 @@ void launch_mv_dot_e(GridInfo g, const double* W, const double* p, double* q, in
   const int64_t N = grid_n(g);
   note_launches(1);
   if (g.dim == 2)
-    DISPATCH_POW2(R_, (k_mv_dot_e<R, 2><<<elem_blocks(N * R), kVecThreads, 0, st>>>(W, g.m, N, p, q, partials,
-                                                                                    counter, pq)));
+    DISPATCH_POW2(R_, (launch_pdl(k_mv_dot_e<R, 2>, elem_blocks(N * R), kVecThreads, st, W, g.m, N, p, q,
+                                  partials, counter, pq)));
   else
-    DISPATCH_POW2(R_, (k_mv_dot_e<R, 3><<<elem_blocks(N * R), kVecThreads, 0, st>>>(W, g.m, N, p, q, partials,
-                                                                                    counter, pq)));
+    DISPATCH_POW2(R_, (launch_pdl(k_mv_dot_e<R, 3>, elem_blocks(N * R), kVecThreads, st, W, g.m, N, p, q,
+                                  partials, counter, pq)));
 }
 
 template <typename TZ>
@@ -763,24 +791,24 @@ void launch_axpy2_e(int64_t N, int R_, double* x, double* r, const double* p, co
                     unsigned* counter, double* rr, TZ* zin, cudaStream_t st, const double* thr2,
                     int* active_next, double* ring_rr) {
   note_launches(1);
-  DISPATCH_POW2(R_, k_axpy2_e<R, TZ><<<elem_blocks(N * R), kVecThreads, 0, st>>>(
-      N, x, r, p, q, rz, pq, active, alpha, partials, counter, rr, zin, thr2, active_next, ring_rr));
+  DISPATCH_POW2(R_, launch_pdl(k_axpy2_e<R, TZ>, elem_blocks(N * R), kVecThreads, st, N, x, r, p, q, rz, pq,
+                               active, alpha, partials, counter, rr, zin, thr2, active_next, ring_rr));
 }
 
 template <typename TZ>
 void launch_dot2_e(int64_t N, int R_, const double* r, const TZ* z, const double* q, double* partials,
                    unsigned* counter, double* out, cudaStream_t st, double* ring_rz) {
   note_launches(1);
-  DISPATCH_POW2(R_, k_dot2_e<R, TZ><<<elem_blocks(N * R), kVecThreads, 0, st>>>(N, r, z, q, partials, counter,
-                                                                                 out, ring_rz));
+  DISPATCH_POW2(R_, launch_pdl(k_dot2_e<R, TZ>, elem_blocks(N * R), kVecThreads, st, N, r, z, q, partials,
+                               counter, out, ring_rz));
 }
 
 template <typename TZ>
 void launch_update_p_e(int64_t N, int R_, double* p, const TZ* z, const double* alpha, const double* rz_old,
                        const double* rzzq, const int* active, int restart, cudaStream_t st) {
   note_launches(1);
-  DISPATCH_POW2(R_, k_update_p_e<R, TZ><<<elem_blocks(N * R), kVecThreads, 0, st>>>(N, p, z, alpha, rz_old,
-                                                                                      rzzq, active, restart));
+  DISPATCH_POW2(R_, launch_pdl(k_update_p_e<R, TZ>, elem_blocks(N * R), kVecThreads, st, N, p, z, alpha, rz_old,
+                               rzzq, active, restart));
 }
 
 template void launch_axpy2_e<double>(int64_t, int, double*, double*, const double*, const double*,
