@@ -1175,20 +1175,39 @@ int inner_pcg(hif_handle* h, SolveWork& W, Precond& M, const std::vector<double>
     }
     return false;
   };
+  // The iteration queued behind the one that converges runs for nothing;
+  // when the last two known residuals predict (at their ratio) that the
+  // iteration in flight converges, the next one is held back until its
+  // result is known (a wrong guess costs one host round trip).
+  std::vector<double> last(R, -1.0), prev(R, -1.0);
+  auto predicted = [&]() {
+    for (int c = 0; c < R; ++c) {
+      if (hthr[c] >= 1e299) continue;
+      if (!(last[c] > 0.0 && prev[c] > 0.0)) return false;
+      if (last[c] * (last[c] / prev[c]) > hthr[c]) return false;
+    }
+    return true;
+  };
   bool head = issue();                 // iteration `it` queued
   while (true) {
     if (!head) break;                  // maxit
-    const bool ahead = issue();        // iteration it + 1 queued behind it
+    bool ahead = false, held = false;
+    if (predicted()) held = true;
+    else ahead = issue();              // iteration it + 1 queued behind it
     CU(cudaGetLastError());
     CU(cudaEventSynchronize(h->it_ev[it & 1]));
     const double* row = h->rr_ring + (size_t)(it % kRingRows) * kRingCols;
+    for (int c = 0; c < R; ++c) {
+      prev[c] = last[c];
+      last[c] = row[c];
+    }
     ++it;
     if (broke && breakdown(row)) {
       *broke = true;
       break;
     }
     if (!converged_row(row)) {
-      head = ahead;
+      head = held ? issue() : ahead;
       continue;
     }
     // every column below its threshold after iteration `it`; the queued
@@ -1203,6 +1222,8 @@ int inner_pcg(hif_handle* h, SolveWork& W, Precond& M, const std::vector<double>
     to_wp();
     restart = 1;
     issued = it;
+    std::fill(last.begin(), last.end(), -1.0);
+    std::fill(prev.begin(), prev.end(), -1.0);
     head = issue();
   }
   CU(cudaStreamSynchronize(st));
