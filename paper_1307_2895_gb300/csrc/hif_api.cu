@@ -62,6 +62,28 @@ struct HifError {
     }                                                                                     \
   } while (0)
 
+// The library's stream-ordered allocations come from the current device's
+// default memory pool.  By default that pool returns its memory to the
+// system at every synchronization, and the factorization synchronizes once
+// per level, so every level would map its buffers afresh; keeping freed
+// memory in the pool (a property of this process's pool only) makes the
+// next allocations reuse it.
+void keep_pool_memory() {
+  static std::mutex mu;
+  static std::vector<int> done;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  std::lock_guard<std::mutex> g(mu);
+  if (std::find(done.begin(), done.end(), dev) != done.end()) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  cudaGetLastError();
+  done.push_back(dev);
+}
+
 // Stream-ordered device buffer.
 struct DevBuf {
   void* p = nullptr;
@@ -1559,6 +1581,7 @@ int hif_factor(const hif_grid* grid, const double* a_stag, const double* b, cons
   if (leaf < 2) return set_error(HIF_ERR_ARG, "leaf must be >= 2");
   hif_handle* h = new hif_handle();
   try {
+    keep_pool_memory();
     h->G.init(grid->dim, grid->n, leaf);
     if ((int64_t)h->G.N > (int64_t)0x7fffffff) throw HifError(HIF_ERR_ARG, "grid too large");
     h->gi.dim = grid->dim;
