@@ -216,8 +216,9 @@ struct hif_handle {
   // sweep bytes and launches of one replay of the preconditioner graph
   double graph_bytes = 0.0;
   long long graph_launches = 0;
-  // pinned ring of per-iteration squared residual norms (inner CG), so that
-  // iterations can run in batches between host checks
+  // ring of per-iteration squared residual norms and r.z (inner CG), written
+  // by the last block of the iteration's reductions, so that the host checks
+  // an iteration while the next one runs
   double* rr_ring = nullptr;       // mapped pinned memory
   double* rr_ring_dev = nullptr;   // its device address
   cudaEvent_t it_ev[2] = {nullptr, nullptr};
@@ -1120,10 +1121,11 @@ void cg_step_kernels(hif_handle* h, SolveWork& W, TZ* wp, int par, int restart, 
 // Inner PCG on A D = Rv (FP64 recurrences, preconditioner F^-1).  Columns whose
 // squared residual is above thr2 are active; a column that drops below it is
 // frozen on the device (its updates stop).  The host checks iteration k's
-// residuals (copied to a pinned ring, waited for by an event) while
-// iteration k + 1 is already queued, so the GPU does not idle on the host;
-// when iteration k converged every column, the queued iteration changed
-// nothing.  Stops when the FP64 true residual confirms the recursive one.
+// residuals (written to a ring in mapped pinned memory by the kernels,
+// waited for by an event) while iteration k + 1 is already queued, so the GPU
+// does not idle on the host; when iteration k converged every column, the
+// queued iteration changed nothing.  Stops when the FP64 true residual
+// confirms the recursive one.
 constexpr int kRingRows = 4;
 constexpr int kRingCols = 32;   // rr (R <= 16 values), then r.z of the same iteration
 
