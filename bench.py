@@ -259,7 +259,7 @@ def run_gpu(args, rank, world, local_rank):
     achieved = (sweep_bytes / sweep_launches) / (sweep_ms / sweep_launches / 1e3) / 1e9 if sweep_ms > 0 else None
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None, "traffic": _sweep_traffic(),
-            "kernel": "k_apply_up/k_apply_down (F^-1 sweeps)", "peak_kind": peak_kind,
+            "kernel": "k_apply_up/k_apply_down/k_apply_root (F^-1 sweeps)", "peak_kind": peak_kind,
             "avg_launch_us": 1e3 * sweep_ms / max(sweep_launches, 1),
             "bytes_per_launch": sweep_bytes / max(sweep_launches, 1),
             "share_of_step": sweep_ms / sum(ms) if sum(ms) > 0 else None}

@@ -908,7 +908,8 @@ void run_apply(hif_handle* h, int mode, T* x, int nrhs) {
       CU(cudaEventRecord(h->ev_pool[h->ev_used + 1], st));
       h->ev_used += 2;
       h->prof_launches += 1;
-      h->prof_bytes += sizeof(T) * (S.fac_elems + 2.0 * S.vec_rows * nrhs);
+      // the fused root launch (op 4) does the work of an up and a down sweep
+      h->prof_bytes += (op == 4 ? 2.0 : 1.0) * sizeof(T) * (S.fac_elems + 2.0 * S.vec_rows * nrhs);
     }
   };
   auto facp = [&](const SweepLevel& S) -> const T* {
@@ -919,8 +920,12 @@ void run_apply(hif_handle* h, int mode, T* x, int nrhs) {
     sweep(h->cells[l], up, 0, facp(h->cells[l]));
     sweep(h->fronts[l], up, 1, facp(h->fronts[l]));
   }
-  sweep(h->root, up, 0, facp(h->root));
-  sweep(h->root, down, 0, facp(h->root));
+  if (mode == HIF_APPLY_FINV) {
+    sweep(h->root, 4, 0, facp(h->root));   // D^-1: the root's up and down sweeps in one launch
+  } else {
+    sweep(h->root, up, 0, facp(h->root));
+    sweep(h->root, down, 0, facp(h->root));
+  }
   for (int l = L - 1; l >= 0; --l) {
     sweep(h->fronts[l], down, 1, facp(h->fronts[l]));
     sweep(h->cells[l], down, 0, facp(h->cells[l]));
@@ -1057,14 +1062,14 @@ struct Precond {
       h->graph_bytes = 0.0;
       h->graph_launches = 0;
       const double esz = W.f32 ? sizeof(float) : sizeof(double);
-      auto add = [&](const SweepLevel& S) {
+      auto add = [&](const SweepLevel& S, int launches) {
         if (S.nblocks == 0) return;
         h->graph_bytes += 2.0 * esz * (S.fac_elems + 2.0 * S.vec_rows * W.R);
-        h->graph_launches += 2;
+        h->graph_launches += launches;
       };
-      for (const auto& S : h->cells) add(S);
-      for (const auto& S : h->fronts) add(S);
-      add(h->root);
+      for (const auto& S : h->cells) add(S, 2);
+      for (const auto& S : h->fronts) add(S, 2);
+      add(h->root, 1);   // up and down of the root in one launch
       h->prof_bytes = b0;
       h->prof_launches = l0;
     }

@@ -325,6 +325,24 @@ __global__ void k_apply_down(const ApplyDesc* __restrict__ blocks, const int* __
   });
 }
 
+// The root (a cell without boundary): D^-1 x = Linv^T (Linv x) by one block,
+// the up body then the down body, in one launch instead of two.  The down
+// body reads Linv from global memory (the up body's staging copy leaves it in
+// L2) and the rows the up body wrote (same block, after the barrier).
+template <typename T, int R>
+__global__ void k_apply_root(const ApplyDesc* __restrict__ blocks, const int* __restrict__ ipool,
+                             const T* __restrict__ fac, T* __restrict__ x, int nr, int ldx,
+                             int is_front, int staged, int* err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const ApplyDesc bd = blocks[0];
+  sweep_up_block<T, R, false>(bd, ipool, fac, x, nr, ldx, 0, staged, err, smem_raw, [] {
+    pdl_wait_then_release();
+    return true;
+  });
+  __syncthreads();
+  sweep_down_block<T, R, false>(bd, ipool, fac, x, nr, ldx, 0, 0, err, smem_raw, [] { return true; });
+}
+
 // ---- forward operator F (used by the error estimates; not staged) ----------
 template <typename T, int R>
 __global__ void k_fwd_up(const ApplyDesc* __restrict__ blocks, const int* __restrict__ ipool,
@@ -433,18 +451,20 @@ static void launch_sweep_R(int op, const ApplyDesc* blocks, int nblocks, const i
                            int max_nq, int* err, cudaStream_t st, SweepShape shape) {
   const size_t vsm = vec_smem<T>(R, max_np, max_nq);
   const size_t ssm = stage_smem<T>(max_np, max_nq, is_front);
-  const int staged = (op <= 1) && (vsm + ssm <= kStageCap) && shape.staged != 0;
+  const bool finv = op <= 1 || op == 4;   // F^-1 sweeps (4: the fused root)
+  const int staged = finv && (vsm + ssm <= kStageCap) && shape.staged != 0;
   const size_t smem = vsm + (staged ? ssm : 0);
   void (*fn)(const ApplyDesc*, const int*, const T*, T*, int, int, int, int, int*) = nullptr;
   switch (op) {
     case 0: fn = k_apply_up<T, R>; break;
     case 1: fn = k_apply_down<T, R>; break;
     case 2: fn = k_fwd_up<T, R>; break;
-    default: fn = k_fwd_down<T, R>; break;
+    case 3: fn = k_fwd_down<T, R>; break;
+    default: fn = k_apply_root<T, R>; break;
   }
   // raise the dynamic shared-memory limit and prefer the largest shared
   // carveout once per kernel (not again while a stream capture records it)
-  static std::atomic<bool> attr_set[4] = {false, false, false, false};
+  static std::atomic<bool> attr_set[5] = {false, false, false, false, false};
   if (!attr_set[op]) {
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSweepSmemCap);
     cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
@@ -458,7 +478,7 @@ static void launch_sweep_R(int op, const ApplyDesc* blocks, int nblocks, const i
   threads = threads < 32 ? 32 : (threads > 256 ? 256 : threads);
   if (shape.threads > 0) threads = shape.threads;
   note_launches(1);
-  if (op <= 1) {
+  if (finv) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(nblocks);
     cfg.blockDim = dim3(threads);
