@@ -1,0 +1,87 @@
+"""Pins of the oracle's HIF-DE in 3D with edge skeletonization
+(oracle.hifde.factor3x, Section 4.5) on the CPU.
+
+* Every DOF is eliminated exactly once: by a cell (Lemma 2.1), as a
+  redundant DOF of a face or edge group (Lemma 2.4), or in the root.
+* eps -> 0: the factorization reproduces the dense solve (the IDs keep
+  everything above 1e-14 of the leading pivot).
+* e_a = O(eps) and PCG with F^-1 converges in few iterations.
+* Table 7 / 8, hifde3x at 31^3 (tests/golden/paper_table7_example4_hifde3x.txt),
+  edge skeletonization from level 1 (the paper's rule of thumb): |s_L|
+  within 15% of the paper's (361 / 978 against 331 / 931); e_a within a
+  factor of 5 (7.5e-4 / 1.05e-6 against 3.6e-3 / 9.8e-7); PCG iterations at
+  most the paper's n_i + 2.  Starting the edges at level 0 keeps about 1.5x
+  the paper's root (509 / 1441): the thick separators it causes at level 1.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import hifde, stencil
+from paper_1307_2895_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _lap(n):
+    a, b = inputs.constant_coefficients(3, n)
+    return stencil.assemble(3, n, a, b)
+
+
+def _eliminated(F):
+    out = []
+    for lev in F.levels:
+        for rec in lev.cells:
+            out.extend(rec.p.tolist())
+        for fr in lev.fronts:
+            out.extend(fr.rd.tolist())
+    return out
+
+
+@pytest.mark.parametrize("eps", [1e-3, 1e-6])
+def test_every_dof_eliminated_once(eps):
+    n = 16
+    A = _lap(n)
+    F = hifde.factor3x(A, n, eps, edge_start=0)
+    elim = _eliminated(F) + F.root.tolist()
+    assert sorted(elim) == list(range((n - 1) ** 3))
+    # the edge levels compress: the root is smaller than hifde3's
+    assert len(F.root) < len(hifde.factor(A, 3, n, eps).root)
+
+
+def test_eps_to_zero_matches_dense_solve():
+    n = 16
+    a, b = inputs.high_contrast_coefficients(3, n, seed=11, low=1e-2, high=1e2)
+    A = stencil.assemble(3, n, a, b)
+    F = hifde.factor3x(A, n, 1e-14, edge_start=0)   # one level: edges at level 0 too
+    f = inputs.rhs(3, n, 2, seed=4)
+    xd = np.linalg.solve(A.toarray(), f)
+    x = F.apply_inverse(f)
+    assert np.linalg.norm(x - xd) <= 1e-9 * np.linalg.norm(xd)
+    y = F.apply(xd)
+    assert np.linalg.norm(y - f) <= 1e-9 * np.linalg.norm(f)
+
+
+def test_table7_hifde3x_31():
+    rows = []
+    with open(os.path.join(GOLDEN, "paper_table7_example4_hifde3x.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                e, s, ea, ni = line.split()
+                rows.append((float(e), int(s), float(ea), int(ni)))
+    n = 32
+    A = _lap(n)
+    x0 = inputs.power_start(3, n)
+    f = inputs.rhs(3, n, 1, seed=0)
+    prev = None
+    for eps, sL, ea_paper, ni in rows:
+        F = hifde.factor3x(A, n, eps)
+        assert abs(len(F.root) - sL) <= 0.15 * sL, (eps, len(F.root), sL)
+        ea, es = hifde.power_estimates(A, F, x0)
+        assert ea_paper / 5 <= ea <= 5 * ea_paper, (eps, ea, ea_paper)
+        x, it, rel = hifde.pcg(A, F, f, tol=1e-12, maxit=100)
+        assert rel[0] <= 1e-12 and it[0] <= ni + 2
+        if prev is not None:
+            assert ea < prev
+        prev = ea
