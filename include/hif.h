@@ -164,6 +164,10 @@ typedef struct hif_stats_t {
  * ignored for MF.  bc_vals must be NULL (zero Dirichlet data; nonzero data
  * belong in the right-hand side).  On success *out owns the factor in
  * device memory; release it with hif_free.
+ * Device memory: the factor and the work buffers are stream-ordered
+ * allocations from the current device's default memory pool; the library
+ * sets that pool to keep up to 8 GB of freed memory for reuse (the
+ * factorization allocates and frees per level).
  */
 int hif_factor(const hif_grid* grid, const double* a_stag, const double* b,
                const double* bc_vals, double eps, const hif_opts* opts,

@@ -65,9 +65,12 @@ struct HifError {
 // The library's stream-ordered allocations come from the current device's
 // default memory pool.  By default that pool returns its memory to the
 // system at every synchronization, and the factorization synchronizes once
-// per level, so every level would map its buffers afresh; keeping freed
-// memory in the pool (a property of this process's pool only) makes the
-// next allocations reuse it.
+// per level, so every level would map its buffers afresh; keeping up to
+// kPoolKeep bytes of freed memory in the pool (a property of this process's
+// pool only) makes the next allocations reuse it, while larger working sets
+// (big 3D factorizations) still go back to the system for other users of the
+// device, such as a framework's own allocator.
+constexpr uint64_t kPoolKeep = uint64_t(8) << 30;
 void keep_pool_memory() {
   static std::mutex mu;
   static std::vector<int> done;
@@ -77,7 +80,7 @@ void keep_pool_memory() {
   if (std::find(done.begin(), done.end(), dev) != done.end()) return;
   cudaMemPool_t pool;
   if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
-    uint64_t keep = UINT64_MAX;
+    uint64_t keep = kPoolKeep;
     cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
   }
   cudaGetLastError();

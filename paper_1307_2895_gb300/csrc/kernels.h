@@ -1,10 +1,37 @@
 // Host-side launchers of the device kernels.
 #pragma once
+#include <cuda_runtime.h>
+
 #include <vector>
 
 #include "hif_internal.h"
 
 namespace hif {
+
+// The largest shared memory a block may opt in to on the current device.
+inline int smem_optin_max() {
+  static const int v = [] {
+    int dev = 0, x = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&x, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return x > 0 ? x : 48 * 1024;
+  }();
+  return v;
+}
+
+// Raise kern's dynamic shared-memory limit to all the device allows next to
+// the kernel's static shared memory (their sum may not exceed the opt-in
+// maximum).  The value is fixed per kernel: host threads that launch the
+// same kernel with different sizes (the batched API) must not set the limit
+// to their own launch's size, or one would lower it under another's launch.
+template <typename K>
+inline void raise_smem_limit(K kern) {
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) return;
+  const int lim = smem_optin_max() - (int)fa.sharedSizeBytes;
+  if (lim > 0) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+}
+
 
 // factorization (kernels_factor.cu)
 template <typename T>

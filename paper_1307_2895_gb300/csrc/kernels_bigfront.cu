@@ -621,7 +621,7 @@ void launch_bigfront_id(const FrontDesc* fronts, const int* big, int nbig, const
   }
   const int smem = (int)(sizeof(double) * (max_nc + max_nN) + sizeof(int) * 2 * max_nc + 64);
   if (smem > 48 * 1024)
-    cudaFuncSetAttribute(k_bf_id<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    raise_smem_limit(k_bf_id<T>);
   // groups of the multi-block QR: blocks per front in proportion to its QR
   // work (|N| |c|^2), at least 32 columns per block, all co-resident
   const int csmem = (int)(sizeof(double) * max_nN + 64);
@@ -631,7 +631,7 @@ void launch_bigfront_id(const FrontDesc* fronts, const int* big, int nbig, const
   int64_t sc_elems = 0;
   if (coop) {
     if (csmem > 48 * 1024)
-      cudaFuncSetAttribute(k_bf_qr_coop<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, csmem);
+      raise_smem_limit(k_bf_qr_coop<T>);
     int nb = 0, dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);

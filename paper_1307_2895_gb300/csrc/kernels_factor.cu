@@ -415,7 +415,7 @@ void launch_cell_factor(const CellDesc* cells, const int* sel, int ncells, T* wo
   if (need > cap_bytes) need = 0;
   const int smem = (int)need;
   if (smem > 48 * 1024)
-    cudaFuncSetAttribute(k_cell_factor<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    raise_smem_limit(k_cell_factor<T>);
   note_launches(1);
   k_cell_factor<T><<<ncells, 256, smem, st>>>(cells, sel, work, fac, status, smem / (int)sizeof(T), (T)tau);
 }
@@ -428,7 +428,7 @@ void launch_front(const FrontDesc* fronts, int nfronts, const CellDesc* cells, c
   if (nfronts == 0) return;
   const int smem = (int)(sizeof(double) * (max_nc + max_nN) + sizeof(int) * 2 * max_nc + 64);
   if (smem > 48 * 1024)
-    cudaFuncSetAttribute(k_front<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    raise_smem_limit(k_front<T>);
   note_launches(1);
   k_front<T><<<nfronts, 256, smem, st>>>(fronts, cells, ipool, obuf, fwork, fac, cwork, eps, status, (T)tau,
                                          sketch, seed, sel);

@@ -660,7 +660,7 @@ static inline int64_t grid_n(GridInfo g) { return (int64_t)g.m * g.m * (g.dim ==
 
 template <typename K>
 static void set_smem(K kern, size_t smem) {
-  if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (smem > 48 * 1024) raise_smem_limit(kern);
 }
 
 #define DISPATCH_R(nr, ...)                                     \
