@@ -31,7 +31,7 @@ What each function follows:
 * :func:`power_estimates` -- the a posteriori estimates ``e_a``, ``e_s`` of
   Section 5 by power iteration to 1e-2 relative precision.
 
-Readings where the paper leaves a choice (each also listed in the design doc):
+Readings where the paper leaves a choice:
 
 * index sets are ordered by ascending global index; the skeleton set is kept
   in pivot order; ``T`` has rows in skeleton order and columns in ascending
