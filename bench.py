@@ -14,6 +14,16 @@ Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
 on a bounded sample of the same workload instead.  With N > 1 (torchrun) every
 rank runs an independent replica of the workload (the method has no exchange
 step for one problem on one GPU): value = DOF of all ranks / max rank time.
+
+Other workloads, one JSON line each:
+
+    python bench.py --workload3d laplace3d_n64|contrast3d_n128 [--eps E]
+                    [--precision fp64|mixed|fp32_apply] [--tensor-cores 0|1|2|3|-1]
+    python bench.py --batched          # 64 independent 2D problems, 32 RHS each
+    python bench.py --tc-roofline      # the tensor-core Schur update alone
+
+and the profiling helpers ``--ncu-apply K`` / ``--ncu-solve K`` (fixed launch
+shapes, for ncu captures).
 """
 import os
 
