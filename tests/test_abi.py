@@ -58,7 +58,7 @@ def test_product_path_does_not_import_oracle():
 def test_batch_argument_errors():
     """The batch entry points reject bad arguments before touching a GPU."""
     from paper_1307_2895_gb300 import hif
-    lib = hif.load()
+    lib = hif.load(build_if_missing=True)
     assert lib.hif_factor_batch(-1, None, None, None, None, None, 1, None) == hif.HIF_ERR_ARG
     assert lib.hif_solve_batch(-1, None, None, None, None, 1e-12, 10, None, 1) == hif.HIF_ERR_ARG
     assert lib.hif_factor_batch(0, None, None, None, None, None, 1, None) == 0
@@ -66,7 +66,7 @@ def test_batch_argument_errors():
 
 def test_schur_update_argument_errors_without_gpu():
     """hif_schur_update_f32 rejects bad sizes and splits before any CUDA call."""
-    lib = hif.load()
+    lib = hif.load(build_if_missing=True)
     assert lib.hif_schur_update_f32(1, 4, 4, None, None, 0, None) == hif.HIF_ERR_ARG
     assert lib.hif_schur_update_f32(1, 4, 4, None, None, 4, None) == hif.HIF_ERR_ARG
     assert lib.hif_schur_update_f32(-1, 4, 4, None, None, 3, None) == hif.HIF_ERR_ARG
@@ -76,14 +76,14 @@ def test_schur_update_argument_errors_without_gpu():
 
 
 def test_estimate_and_solver_argument_errors_without_gpu():
-    lib = hif.load()
+    lib = hif.load(build_if_missing=True)
     ea, es = ctypes.c_double(), ctypes.c_double()
     assert lib.hif_estimate(None, None, 1e-2, 10, ctypes.byref(ea), ctypes.byref(es)) == hif.HIF_ERR_ARG
     assert lib.hif_set_solver(None, 0, 0) == hif.HIF_ERR_ARG
 
 
 def test_autotune_table_without_gpu():
-    lib = hif.load()
+    lib = hif.load(build_if_missing=True)
     assert lib.hif_autotune_table(None, 0, None) == hif.HIF_ERR_ARG
     n = ctypes.c_longlong(-1)
     assert lib.hif_autotune_table(None, 0, ctypes.byref(n)) == hif.HIF_OK and n.value == 0
