@@ -1,0 +1,82 @@
+// Host symbolic stage of HIF-DE in 3D with edge skeletonization
+// (Section 4.5, Algorithm 4.2): the sparsity pattern of the active matrix
+// A_l and the index sets of every level built from it.
+//
+// Pattern.  Two active DOFs are coupled when they are 7-point stencil
+// neighbours or when a live clique holds both.  The elimination of a set p
+// (Lemma 2.1) makes its neighbours q = p^N a clique (B_qq is dense) and
+// removes p; the skeletonization of a group c with skeleton s (Lemma 2.4)
+// makes s a clique (B_ss) when it also has redundant DOFs r = c \ s, and
+// removes r (their couplings outside c are dropped with the ID's residual).
+// No coupling between two active DOFs is ever removed.
+//
+// Index sets of level l (S = 2^l m, K = 2^(L-l) cells per axis; distances
+// exact in doubled grid units; a DOF with two or more nearest centers joins
+// no set):
+//   * cells: Voronoi cells of the active DOFs about the cell centers
+//     ((j - 1/2) S per axis, j = 1..K), then, cell by cell in ascending
+//     linear index (x fastest) and DOF by DOF in ascending index, every DOF
+//     coupled to a DOF that is at that moment in another cell leaves its
+//     cell;
+//   * faces (kind 1): Voronoi cells about the face centers (j S on the
+//     normal axis, j = 1..K-1, (j - 1/2) S on the other two; the x-, y-,
+//     z-normal faces are families 0, 1, 2);
+//   * edges (kind 2): the same about the edge centers ((j - 1/2) S along the
+//     edge, j S on the other two; edges along x, y, z are families 0, 1, 2).
+// Which DOFs a group keeps comes from the numerical ID and is an input.
+#pragma once
+#include <cstdint>
+#include <vector>
+
+namespace hif {
+
+class Symbolic3x {
+ public:
+  // Grid of n intervals per axis, N = (n-1)^3 DOFs (x fastest); L = the
+  // nearest integer to log2(n / leaf), at least 1; m = floor(n / 2^L).
+  Symbolic3x(int n, int leaf);
+
+  int levels() const { return L_; }
+  int leaf_width() const { return m_; }
+  int dofs() const { return N_; }
+  bool is_active(int i) const { return active_[i] != 0; }
+  // Active DOFs, ascending.
+  const std::vector<int>& active();
+
+  // Level l's cells after peeling, each ascending, in ascending linear cell
+  // index (empty cells omitted).
+  std::vector<std::vector<int>> cells(int l);
+  // Face (kind 1) or edge (kind 2) groups of level l, each ascending, in
+  // ascending (family, x index, y index, z index) order.
+  std::vector<std::vector<int>> groups(int l, int kind);
+  // c^N: active DOFs outside c coupled to a DOF of c, ascending.
+  std::vector<int> neighbors(const std::vector<int>& c) const;
+
+  // Lemma 2.1 on the active set p.
+  void eliminate(const std::vector<int>& p);
+  // Lemma 2.4 on group c with skeleton s (a subset of c).  Returns false,
+  // changing nothing, when c holds an inactive DOF or s is not in c.
+  bool skeletonize(const std::vector<int>& c, const std::vector<int>& s);
+
+ private:
+  struct Key {
+    int fam, i[3];
+  };
+  // Nearest center of the union of families (per family, a list of
+  // positions per axis, doubled units); false on a tie.
+  bool voronoi(int g, const std::vector<std::vector<int>>* fams, int nfam, Key& k) const;
+  void add_clique(const std::vector<int>& members);
+  void remove(const std::vector<int>& dofs);
+
+  int n_, m_, L_, N_;
+  std::vector<char> active_;
+  std::vector<int> active_list_;
+  bool active_dirty_ = false;
+  std::vector<std::vector<int>> clique_;   // active members (compacted on removal)
+  std::vector<std::vector<int>> of_;       // cliques holding each DOF (may list dead ones)
+  std::vector<int> mark_;                  // scratch stamps for set unions
+  mutable std::vector<int> seen_;
+  mutable int stamp_ = 0;
+};
+
+}  // namespace hif
