@@ -187,6 +187,27 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------------------
+# replicas over N ranks (weak scaling, no data-path collective)
+# ---------------------------------------------------------------------------
+def max_over_ranks(secs: float, world: int, device=None) -> float:
+    """The slowest rank's time: an all-reduce MAX of one number over the
+    default process group (the local time when world == 1)."""
+    if world <= 1:
+        return secs
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([secs], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_step: int, steps: int, world: int, tmax_s: float) -> float:
+    """Whole-job throughput of `world` independent replicas: the units every
+    rank processed in `steps` steps over the slowest rank's time."""
+    return world * steps * units_per_step / tmax_s
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 def run_gpu(args, rank, world, local_rank):
@@ -251,14 +272,9 @@ def run_gpu(args, rank, world, local_rank):
     clocks.start()
     ms, infos, profs, stats, launches = timed(prec, args.steps, args.warmup, profile=True)
     clocks.stop()
-    tot_s = sum(ms) / 1e3
-    tmax = tot_s
-    if world > 1:
-        t = torch.tensor([tot_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tmax = float(t.item())
+    tmax = max_over_ranks(sum(ms) / 1e3, world, dev)
     dofs_per_step = N * nrhs
-    value = world * args.steps * dofs_per_step / tmax
+    value = replica_throughput(dofs_per_step, args.steps, world, tmax)
     conv = all(i["converged"] and i["relres_max"] <= TOL for i in infos)
 
     # roofline of the dominant kernels (apply sweeps of F^-1), live events
@@ -301,7 +317,8 @@ def run_gpu(args, rank, world, local_rank):
             torch.cuda.synchronize()
             if i > 0:
                 e_ms.append(1e3 * (time.perf_counter() - t0))
-        e2e = {"value": world * len(e_ms) * dofs_per_step / (sum(e_ms) / 1e3), "unit": "DOF/s",
+        e_max = max_over_ranks(sum(e_ms) / 1e3, world, dev)
+        e2e = {"value": replica_throughput(dofs_per_step, len(e_ms), world, e_max), "unit": "DOF/s",
                "h2d_bytes_per_step": int(a_h.numel() * 8 + b_h.numel() * 8 + f_h.numel() * 8),
                "d2h_bytes_per_step": int(x_h.numel() * 8)}
 
