@@ -8,8 +8,9 @@
 // (G, then per group: ns, s...), then, when l >= edge_start, the edge
 // groups' skeletons in the same form.
 // out.bin (int32 stream), per level: ncells, per cell: np, p..., nq, q...;
-// nfaces, per face: nc, c...; when l >= edge_start, nedges, per edge:
-// nc, c...; at the end: nroot, root....  On a group-count mismatch or a
+// nfaces, per face: nc, c..., nN, N... (c^N before any group of the level
+// is skeletonized); when l >= edge_start, nedges, per edge: the same; at the
+// end: nroot, root....  On a group-count mismatch or a
 // rejected skeleton, what was built so far is written and the exit code is 4.
 #include <cstdint>
 #include <cstdio>
@@ -60,7 +61,10 @@ int main(int argc, char** argv) {
       if (kind == 2 && l < edge_start) break;
       const std::vector<std::vector<int>> g = S.groups(l, kind);
       o.push_back((int32_t)g.size());
-      for (const std::vector<int>& c : g) put(o, c);
+      for (const std::vector<int>& c : g) {   // all IDs of a fractional level see the same A
+        put(o, c);
+        put(o, S.neighbors(c));
+      }
       if (take() != (int)g.size()) return write_out(argv[5], o, 4);
       for (const std::vector<int>& c : g) {
         const int ns = take();

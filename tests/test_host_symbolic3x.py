@@ -11,7 +11,8 @@ follows the stored entries of the numerical A_l:
 * per level, the peeled cells (the oracle's eliminated sets p, in order) and
   their neighbours q = p^N at elimination (Lemma 2.1);
 * the face groups, then the edge groups (the oracle's front sets c, in key
-  order);
+  order), and the neighbour set c^N of each, whose block A_{c^N, c} the ID
+  compresses (recorded from the oracle's own neighbour queries);
 * the DOFs left for the root (s_L).
 
 The cases: 15^3 with edges from level 0 (one level) at two tolerances;
@@ -92,53 +93,70 @@ def _parse(v, L, edge_start):
         for _ in range(int(take(1)[0])):
             p = lst()
             cells.append((p, lst()))
-        faces = [lst() for _ in range(int(take(1)[0]))]
-        edges = [lst() for _ in range(int(take(1)[0]))] if ell >= edge_start else []
+        faces = [(lst(), lst()) for _ in range(int(take(1)[0]))]
+        edges = [(lst(), lst()) for _ in range(int(take(1)[0]))] if ell >= edge_start else []
         levels.append((cells, faces, edges))
     root = lst()
     assert k == v.size
     return levels, root
 
 
-def _compare(F, levels, root):
+def _compare(F, levels, root, queried):
     for ell, (cells, faces, edges) in enumerate(levels):
         lc, le = F.levels[2 * ell], F.levels[2 * ell + 1]
         assert len(cells) == len(lc.cells), f"level {ell}: cell count"
         for (p, q), rec in zip(cells, lc.cells):
             assert p == rec.p.tolist(), f"level {ell}: cell differs"
             assert q == rec.q.tolist(), f"level {ell}: neighbours differ"
-        assert [fr.c.tolist() for fr in lc.fronts] == faces, f"level {ell}: face groups differ"
-        assert [fr.c.tolist() for fr in le.fronts] == edges, f"level {ell}: edge groups differ"
+        for kind, groups, lev in (("face", faces, lc), ("edge", edges, le)):
+            assert [fr.c.tolist() for fr in lev.fronts] == [c for c, _ in groups], f"level {ell}: {kind} groups differ"
+            for c, N in groups:
+                assert queried[tuple(c)] == N, f"level {ell}: {kind} group neighbours differ"
     assert root == F.root.tolist()
 
 
-def _case(harness, tmp_path, A, n, eps, edge_start):
+def _recording_neighbors(monkeypatch):
+    """Wrap the oracle's neighbour query to keep c -> c^N of every call."""
+    seen = {}
+    orig = hifde.ActiveMatrix.neighbors
+
+    def rec(self, c):
+        out = orig(self, c)
+        seen[tuple(int(v) for v in c)] = list(out)
+        return out
+
+    monkeypatch.setattr(hifde.ActiveMatrix, "neighbors", rec)
+    return seen
+
+
+def _case(harness, tmp_path, monkeypatch, A, n, eps, edge_start):
+    queried = _recording_neighbors(monkeypatch)
     F = hifde.factor3x(A, n, eps, edge_start=edge_start)
     rc, v = _run(harness, tmp_path, n, edge_start, _skeletons(F, edge_start))
     assert rc == 0
     levels, root = _parse(v, F.L, edge_start)
-    _compare(F, levels, root)
+    _compare(F, levels, root, queried)
     return F
 
 
 @pytest.mark.parametrize("eps", [1e-3, 1e-9])
-def test_one_level_edges_from_level0(harness, tmp_path, eps):
+def test_one_level_edges_from_level0(harness, tmp_path, monkeypatch, eps):
     n = 16
     a, b = inputs.constant_coefficients(3, n)
-    _case(harness, tmp_path, stencil.assemble(3, n, a, b), n, eps, 0)
+    _case(harness, tmp_path, monkeypatch, stencil.assemble(3, n, a, b), n, eps, 0)
 
 
-def test_two_levels_edges_from_level1(harness, tmp_path):
+def test_two_levels_edges_from_level1(harness, tmp_path, monkeypatch):
     n = 32
     a, b = inputs.constant_coefficients(3, n)
-    F = _case(harness, tmp_path, stencil.assemble(3, n, a, b), n, 1e-3, 1)
+    F = _case(harness, tmp_path, monkeypatch, stencil.assemble(3, n, a, b), n, 1e-3, 1)
     assert F.L == 2 and len(F.levels[3].fronts) > 0
 
 
-def test_high_contrast_two_levels(harness, tmp_path):
+def test_high_contrast_two_levels(harness, tmp_path, monkeypatch):
     n = 32
     a, b = inputs.high_contrast_coefficients(3, n, seed=5, low=1e-2, high=1e2)
-    F = _case(harness, tmp_path, stencil.assemble(3, n, a, b), n, 1e-6, 0)
+    F = _case(harness, tmp_path, monkeypatch, stencil.assemble(3, n, a, b), n, 1e-6, 0)
     # level 1 (S = 16): the Voronoi members are the DOFs active at its start
     # with no coordinate on the plane 16; the peel removed some of them
     act1 = F.root.tolist()
