@@ -3,6 +3,9 @@
 
 * Every DOF is eliminated exactly once: by a cell (Lemma 2.1), as a
   redundant DOF of a face or edge group (Lemma 2.4), or in the root.
+* Before the first edge level it reduces to hifde3 (Section 4.2): with edges
+  from level 1, level 0 and level 1's cells and faces equal hifde3's, DOF
+  for DOF and skeleton for skeleton (15^3: the whole factorization).
 * eps -> 0: the factorization reproduces the dense solve (the IDs keep
   everything above 1e-14 of the leading pivot).
 * e_a = O(eps) and PCG with F^-1 converges in few iterations.
@@ -111,3 +114,36 @@ def test_table9_hifde3x_31_contrast():
     x, it, rel = hifde.pcg(A, F, inputs.rhs(3, n, 1, seed=0), tol=1e-12, maxit=100)
     assert rel[0] <= 1e-12 and it[0] <= ni + 3
 
+
+
+def _same_level(la, lb):
+    if len(la.cells) != len(lb.cells) or len(la.fronts) != len(lb.fronts):
+        return False
+    for x, y in zip(la.cells, lb.cells):
+        if not (np.array_equal(x.p, y.p) and np.array_equal(x.q, y.q)):
+            return False
+    sa = {tuple(f.c.tolist()): f.sk.tolist() for f in la.fronts}
+    sb = {tuple(f.c.tolist()): f.sk.tolist() for f in lb.fronts}
+    return sa == sb
+
+
+@pytest.mark.parametrize("n", [16, 24])
+def test_reduces_to_hifde3_before_the_first_edges(n):
+    """Before any edge is skeletonized, the Voronoi cells about the cell
+    centers are the boxes' interiors and the Voronoi cells about the face
+    centers the faces' strict interiors (ties fall on the separators), and
+    no DOF is peeled: with edges from level 1, factor3x's level 0 and level
+    1's cells and faces are hifde3's (Section 4.2) DOF for DOF and skeleton
+    for skeleton; with one level (15^3) the whole factorization is."""
+    a, b = inputs.high_contrast_coefficients(3, n, seed=7, low=1e-2, high=1e2)
+    A = stencil.assemble(3, n, a, b)
+    F3 = hifde.factor(A, 3, n, 1e-6)
+    Fx = hifde.factor3x(A, n, 1e-6, edge_start=1)
+    assert F3.L == Fx.L
+    for ell in range(min(F3.L, 2)):
+        assert _same_level(F3.levels[ell], Fx.levels[2 * ell]), ell
+    if F3.L == 1:
+        assert not Fx.levels[1].fronts
+        assert np.array_equal(F3.root, Fx.root)
+    else:
+        assert Fx.levels[3].fronts          # the first edge groups: where the two part
