@@ -1634,9 +1634,16 @@ int hif_factor(const hif_grid* grid, const double* a_stag, const double* b, cons
     }
     h->stencil_w.alloc(sizeof(double) * h->G.N * (2 * grid->dim + 1), h->st);
     launch_stencil_weights(h->gi, h->a_stag.as<double>(), h->bnode.as<double>(), h->stencil_w.as<double>(), h->st);
-    cudaEvent_t e0, e1;
-    CU(cudaEventCreate(&e0));
-    CU(cudaEventCreate(&e1));
+    struct Events {   // destroyed on every exit, the failures included
+      cudaEvent_t e[2] = {nullptr, nullptr};
+      ~Events() {
+        for (cudaEvent_t x : e)
+          if (x) cudaEventDestroy(x);
+      }
+    } ev;
+    CU(cudaEventCreate(&ev.e[0]));
+    CU(cudaEventCreate(&ev.e[1]));
+    cudaEvent_t e0 = ev.e[0], e1 = ev.e[1];
     CU(cudaEventRecord(e0, h->st));
     if (prec == HIF_PREC_MIXED) {
       Factorizer<float> f(h);
@@ -1651,13 +1658,11 @@ int hif_factor(const hif_grid* grid, const double* a_stag, const double* b, cons
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     h->t_factor_ms = ms;
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
   } catch (const HifError& e) {
-    delete h;
+    hif_free(h);   // also ends the handle's own stream
     return set_error(e.code, e.msg);
   } catch (const std::bad_alloc&) {
-    delete h;
+    hif_free(h);
     return set_error(HIF_ERR_OOM, "host allocation failed");
   }
   *out = h;

@@ -1,12 +1,14 @@
 """The C-ABI library builds, loads and exports every entry point of
 include/hif.h; argument errors come back as status codes (no GPU needed:
-these calls return before any CUDA work)."""
+these calls return before any CUDA work), and on a machine without a GPU a
+factorization with valid arguments fails cleanly at its first CUDA call."""
 import ctypes
 import os
 import re
 
 import numpy as np
 import pytest
+import torch
 
 from paper_1307_2895_gb300 import build, hif
 
@@ -88,3 +90,19 @@ def test_autotune_table_without_gpu():
     n = ctypes.c_longlong(-1)
     assert lib.hif_autotune_table(None, 0, ctypes.byref(n)) == hif.HIF_OK and n.value == 0
 
+
+
+@pytest.mark.skipif(torch.cuda.is_available(), reason="checks the failure path of a machine without a GPU")
+def test_factor_failure_after_handle_creation_without_gpu():
+    """Valid arguments on a machine without a GPU: the handle is created, the
+    first CUDA call fails, and hif_factor frees the handle (its stream and
+    events included) and returns HIF_ERR_CUDA with a NULL handle."""
+    lib = hif.load(build_if_missing=True)
+    n = 16
+    a, b = np.ones(2 * n * (n - 1)), np.zeros((n - 1) ** 2)
+    grid = hif._Grid(2, n, 8, 1)
+    for _ in range(3):
+        h = ctypes.c_void_p(1)
+        rc = lib.hif_factor(ctypes.byref(grid), a.ctypes.data, b.ctypes.data, None, 1e-6, None, ctypes.byref(h))
+        assert rc in (hif.HIF_ERR_CUDA, hif.HIF_ERR_OOM) and h.value is None
+        assert lib.hif_last_error()
