@@ -162,7 +162,7 @@ typedef struct hif_stats_t {
  * (3D) with an ID of relative precision eps (Lemma 2.4, Section 4.3), and
  * finally factor D = A_L (Cholesky).  eps must be > 0 for HIFDE; it is
  * ignored for MF.  bc_vals must be NULL (zero Dirichlet data; nonzero data
- * belong in the right-hand side).  On success *out owns the factor in
+ * belong in the right-hand side: hif_rhs_from_bc).  On success *out owns the factor in
  * device memory; release it with hif_free.
  * Device memory: the factor and the work buffers are stream-ordered
  * allocations from the current device's default memory pool; the library
@@ -217,6 +217,28 @@ int hif_solve_batch(int nprob, hif_handle* const* hs, const double* const* rhs, 
 
 /* hif_matvec -- y = A x with the stencil of the factored problem (FP64). */
 int hif_matvec(hif_handle* h, const double* x, double* y, int nrhs, int ld);
+
+/*
+ * hif_rhs_from_bc -- nonzero Dirichlet data.  In the stencil equation of
+ * Section 3.1 / 3.2 at an interior node x_j, a neighbour x_k on the boundary
+ * contributes -(1/h^2) a_jk u_k with u_k = g_k known; this call moves that term
+ * to the right-hand side: rhs[j] += (1/h^2) a_jk g_k for every such pair, per
+ * node axis by axis (x, y, z), the lower neighbour before the upper one.
+ * Then A x = rhs is the problem with boundary values g (hif_factor with
+ * bc_vals = NULL; A does not depend on g).
+ * grid: dim and n as for hif_factor (leaf and variant are not read).
+ * a_stag: the staggered coefficients of hif_factor.
+ * bc_vals: g at every node of the (n+1)^dim grid, coordinates 0..n with x
+ *   fastest, nrhs columns with row stride ld; only boundary nodes (a
+ *   coordinate 0 or n) are read.
+ * rhs: N x nrhs, row stride ld, updated in place.
+ * All three in host memory (the work touches only the O(n^(dim-1)) nodes
+ * next to the boundary); device pointers give HIF_ERR_ARG.
+ * Errors: HIF_ERR_ARG for NULL pointers, dim not 2 or 3, n < 4 or > 32768,
+ * nrhs < 1 or ld < nrhs, N > 2^31 - 1.
+ */
+int hif_rhs_from_bc(const hif_grid* grid, const double* a_stag, const double* bc_vals,
+                    double* rhs, int nrhs, int ld);
 
 /* hif_stats -- sizes and counts of the factorization (Section 5 columns). */
 /*

@@ -16,8 +16,13 @@ matrix of ``assemble`` rounds each diagonal entry (a sum of 2 dim bond terms
 and b) to FP64, which on an ill-conditioned problem alone moves the relative
 residual of an accurate solution far above 1e-12.
 
+``rhs_from_bc`` moves nonzero Dirichlet values to the right-hand side.
+
 Pinned by: the closed-form eigenpairs of the constant-coefficient Laplacian
-(``tests/test_oracle_stencil.py``) and symmetry / row-sum identities; the
+(``tests/test_oracle_stencil.py``) and symmetry / row-sum identities;
+``rhs_from_bc`` by harmonic quadratics, which the stencil reproduces exactly,
+and by one-dimensional solutions of constant flux under a variable
+coefficient, along each axis; the
 bond-form residual by agreement with the CSR product where the diagonal is
 exact in FP64, and by exact solutions of small systems refined in longdouble.
 """
@@ -79,6 +84,38 @@ def assemble(dim: int, n: int, a_stag, b) -> sp.csr_matrix:
     A = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                       shape=(N, N))
     return A.tocsr()
+
+
+def rhs_from_bc(dim: int, n: int, a_stag, g, f) -> np.ndarray:
+    """Right-hand side for nonzero Dirichlet values ``g`` on the boundary nodes.
+
+    In the stencil equation above, a neighbour x_k of the interior node x_j
+    that lies on the boundary contributes ``-(1/h^2) a_{jk} u_k`` with the known
+    value ``u_k = g_k``; moved to the right, it adds ``(1/h^2) a_{jk} g_k`` to
+    ``f_j``.  ``g``: values at all ``(n+1)^dim`` grid nodes (coordinates 0..n, x
+    fastest; only boundary nodes are read), shape ``((n+1)^dim,)`` or
+    ``((n+1)^dim, nrhs)``; ``f``: ``(N,)`` or ``(N, nrhs)``.  Per node the terms
+    are added axis by axis, the lower neighbour before the upper one."""
+    m = n - 1
+    inv_h2 = float(n) ** 2
+    blocks = _stag_blocks(dim, n, a_stag)
+    g = np.asarray(g, dtype=np.float64)
+    out = np.array(f, dtype=np.float64, copy=True)
+    X = coords(dim, n)
+    for j in range(X.shape[0]):
+        c = [int(v) for v in X[j]]
+        for axis in range(dim):
+            for side, bond, bcoord in ((c[axis] == 1, 0, 0), (c[axis] == m, n - 1, n)):
+                if not side:
+                    continue
+                # the bond coefficient: numpy axes run z, y, x; bond index on `axis`
+                at = tuple(bond if (dim - 1 - p) == axis else c[dim - 1 - p] - 1 for p in range(dim))
+                a = blocks[axis][at]
+                k = list(c)
+                k[axis] = bcoord
+                lin = sum(k[q] * (n + 1) ** q for q in range(dim))
+                out[j] += inv_h2 * a * g[lin]
+    return out
 
 
 def coords(dim: int, n: int) -> np.ndarray:

@@ -1764,6 +1764,49 @@ int hif_matvec(hif_handle* h, const double* x, double* y, int nrhs, int ld) {
   return HIF_OK;
 }
 
+// Boundary terms of the stencil equation (Sections 3.1, 3.2) moved to the
+// right-hand side.  Only interior nodes with a coordinate 1 or n-1 have a
+// boundary neighbour: the x loop visits x = 1 and x = n-1 alone on rows whose
+// y (and z) are away from the boundary.
+int hif_rhs_from_bc(const hif_grid* grid, const double* a_stag, const double* bc_vals, double* rhs, int nrhs,
+                    int ld) {
+  if (!grid || !a_stag || !bc_vals || !rhs) return set_error(HIF_ERR_ARG, "NULL argument");
+  const int dim = grid->dim, n = grid->n;
+  if (dim != 2 && dim != 3) return set_error(HIF_ERR_ARG, "dim must be 2 or 3");
+  if (n < 4 || n > 1 << 15) return set_error(HIF_ERR_ARG, "n out of range");
+  if (nrhs < 1 || ld < nrhs) return set_error(HIF_ERR_ARG, "need 1 <= nrhs <= ld");
+  const int m = n - 1;
+  if ((dim == 3 ? (int64_t)m * m * m : (int64_t)m * m) > (int64_t)0x7fffffff)
+    return set_error(HIF_ERR_ARG, "grid too large");
+  if (is_device_ptr(a_stag) || is_device_ptr(bc_vals) || is_device_ptr(rhs))
+    return set_error(HIF_ERR_ARG, "a_stag, bc_vals and rhs must be in host memory");
+  const double inv_h2 = (double)n * (double)n;
+  const int64_t blk = (int64_t)n * (dim == 3 ? (int64_t)m * m : m);   // coefficients of one axis
+  int c[3] = {1, 1, 1};
+  const int zmax = dim == 3 ? m : 1;
+  for (c[2] = 1; c[2] <= zmax; ++c[2])
+    for (c[1] = 1; c[1] <= m; ++c[1]) {
+      const bool near = c[1] == 1 || c[1] == m || (dim == 3 && (c[2] == 1 || c[2] == m));
+      for (c[0] = 1; c[0] <= m; c[0] = (near || c[0] == m) ? c[0] + 1 : m) {
+        const int64_t j = (c[0] - 1) + (int64_t)m * ((c[1] - 1) + (int64_t)m * (dim == 3 ? c[2] - 1 : 0));
+        for (int ax = 0; ax < dim; ++ax)
+          for (int side = 0; side < 2; ++side) {
+            if (c[ax] != (side == 0 ? 1 : m)) continue;
+            // coefficient of the bond to the boundary: extent n on ax (bond 0 or
+            // n-1), m on the other axes; boundary node: coordinate 0 or n on ax
+            int64_t ai = 0, gi = 0;
+            for (int q = dim - 1; q >= 0; --q) {
+              ai = ai * (q == ax ? n : m) + (q == ax ? (side == 0 ? 0 : n - 1) : c[q] - 1);
+              gi = gi * (n + 1) + (q == ax ? (side == 0 ? 0 : n) : c[q]);
+            }
+            const double w = inv_h2 * a_stag[ax * blk + ai];
+            for (int r = 0; r < nrhs; ++r) rhs[j * ld + r] += w * bc_vals[gi * ld + r];
+          }
+      }
+    }
+  return HIF_OK;
+}
+
 int hif_solve(hif_handle* h, const double* rhs, double* x, double* x_lo, int nrhs, int ld, double tol,
               int maxit, hif_solve_info* info) {
   if (!h || !rhs || !x) return set_error(HIF_ERR_ARG, "NULL argument");

@@ -64,10 +64,10 @@ class _Profile(ctypes.Structure):
 
 
 _LIB = None
-EXPORTS = ["hif_factor", "hif_apply", "hif_solve", "hif_matvec", "hif_stats", "hif_structure",
+EXPORTS = ["hif_factor", "hif_apply", "hif_solve", "hif_matvec", "hif_rhs_from_bc", "hif_stats", "hif_structure",
            "hif_profile", "hif_kernel_launches", "hif_residual_norms_noalloc", "hif_front_log", "hif_mlp_grad",
-           "hif_mlp_train", "hif_mlp_predict", "hif_schur_update_f32", "hif_factor_batch", "hif_solve_batch", "hif_set_solver", "hif_estimate", "hif_autotune_table", "hif_free",
-           "hif_last_error"]
+           "hif_mlp_train", "hif_mlp_predict", "hif_schur_update_f32", "hif_factor_batch", "hif_solve_batch",
+           "hif_set_solver", "hif_estimate", "hif_autotune_table", "hif_free", "hif_last_error"]
 
 
 def library_path() -> str:
@@ -94,6 +94,8 @@ def load(build_if_missing: bool = False):
     lib.hif_solve.restype = i
     lib.hif_matvec.argtypes = [vp, vp, vp, i, i]
     lib.hif_matvec.restype = i
+    lib.hif_rhs_from_bc.argtypes = [ctypes.POINTER(_Grid), vp, vp, vp, i, i]
+    lib.hif_rhs_from_bc.restype = i
     lib.hif_stats.argtypes = [vp, ctypes.POINTER(_Stats)]
     lib.hif_stats.restype = i
     lib.hif_structure.argtypes = [vp, vp, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)]
@@ -357,6 +359,30 @@ def schur_update(G, U, split: int = 3, stream=None):
     _check(lib.hif_schur_update_f32(nb, m, k, _ptr(G, "float32"), _ptr(U, "float32"), split,
                                     _stream_ptr(stream)), lib)
     return U
+
+
+def rhs_from_bc(dim: int, n: int, a_stag, bc_vals, f):
+    """hif_rhs_from_bc: ``f`` plus the stencil's boundary terms for nonzero
+    Dirichlet values.  ``bc_vals``: values at all ``(n+1)^dim`` grid nodes
+    (coordinates 0..n, x fastest; only boundary nodes are read), shape
+    ``((n+1)^dim,)`` or ``((n+1)^dim, nrhs)``; ``f``: ``(N,)`` or ``(N, nrhs)``.
+    Host arrays (numpy, or CPU tensors); returns a new float64 numpy array of
+    ``f``'s shape, the right-hand side of the problem with those boundary values."""
+    lib = load()
+    N = (n - 1) ** dim
+    f_np = np.asarray(f.cpu() if _is_torch(f) else f, dtype=np.float64)
+    out = np.array(f_np, dtype=np.float64, order="C", copy=True).reshape(N, -1)
+    g = np.ascontiguousarray(bc_vals.cpu() if _is_torch(bc_vals) else bc_vals, dtype=np.float64)
+    g = g.reshape((n + 1) ** dim, -1)
+    a = np.ascontiguousarray(a_stag.cpu() if _is_torch(a_stag) else a_stag, dtype=np.float64).ravel()
+    if a.size != dim * n * (n - 1) ** (dim - 1):
+        raise ValueError("a_stag has the wrong length")
+    if g.shape[1] != out.shape[1]:
+        raise ValueError("bc_vals and f need the same number of columns")
+    grid = _Grid(dim, n, 8, VARIANTS["hifde"])
+    _check(lib.hif_rhs_from_bc(ctypes.byref(grid), a.ctypes.data, g.ctypes.data, out.ctypes.data, out.shape[1],
+                               out.shape[1]), lib)
+    return out.reshape(f_np.shape)
 
 
 def factor(dim: int, n: int, a_stag, b, eps: float, variant: str = "hifde", precision: str = "fp64",

@@ -1,5 +1,6 @@
 """Pins of the oracle's stencil (Section 3.1 / 3.2) and of the input generators."""
 import numpy as np
+import scipy.sparse.linalg as spla
 import pytest
 
 from oracle import stencil
@@ -122,3 +123,73 @@ def test_residual_ext_of_refined_solution():
     xl = (x - xh.astype(L)).astype(np.float64)
     assert stencil.residual_ext(dim, n, a, b, f, xh, xl).max() <= 1e-13
     assert stencil.residual_ext(dim, n, a, b, f, xh).max() <= 1e-9
+
+
+def _grid_values(dim, n, fn):
+    """fn(x, y[, z]) at all (n+1)^dim nodes (coordinates 0..n, x fastest), h = 1/n."""
+    c = np.meshgrid(*[np.arange(n + 1)] * dim, indexing="ij")
+    c = [ci.transpose(*reversed(range(dim))).ravel() / n for ci in c]
+    return fn(*c)
+
+
+def _interior(dim, n, full):
+    X = stencil.coords(dim, n)
+    return full[sum(X[:, q] * (n + 1) ** q for q in range(dim))]
+
+
+@pytest.mark.parametrize("dim,n", [(2, 16), (2, 21), (3, 12)])
+def test_rhs_from_bc_harmonic_quadratic(dim, n):
+    """a = 1, b = 0: the stencil's second differences are exact on quadratics,
+    so with g = u for a harmonic quadratic u, A x = rhs_from_bc(g, 0) has the
+    solution x = u at the interior nodes."""
+    if dim == 2:
+        u = lambda x, y: x * x - y * y + 0.3 * x * y + 0.5 * x - 0.2
+    else:
+        u = lambda x, y, z: x * x + y * y - 2 * z * z + 0.7 * x * z - 0.4 * y + 0.1
+    a, b = inputs.constant_coefficients(dim, n)
+    g = _grid_values(dim, n, u)
+    rhs = stencil.rhs_from_bc(dim, n, a, g, np.zeros((n - 1) ** dim))
+    x = spla.spsolve(stencil.assemble(dim, n, a, b).tocsc(), rhs)
+    ui = _interior(dim, n, g)
+    assert np.abs(x - ui).max() <= 1e-12 * np.abs(ui).max()
+
+
+@pytest.mark.parametrize("dim,axis", [(2, 0), (2, 1), (3, 0), (3, 1), (3, 2)])
+def test_rhs_from_bc_constant_flux(dim, axis):
+    """b = 0, a along `axis` a function of the bond index alone, the other
+    coefficients arbitrary: u_k = sum_{i<k} 1/a_{i+1/2} (unit flux through
+    every bond, constant across the other axes) solves the equation at every
+    interior node, so with g = u every boundary term, on every axis, must be
+    moved to the right-hand side with its own bond coefficient."""
+    n = 12
+    m = n - 1
+    rng = np.random.default_rng(3 + axis)
+    prof = rng.uniform(0.1, 10.0, size=n)             # a at bonds k + 1/2, k = 0..n-1
+    blocks = []
+    for ax in range(dim):
+        shape = [n if (dim - 1 - p) == ax else m for p in range(dim)]
+        if ax == axis:
+            view = [1] * dim
+            view[dim - 1 - ax] = n
+            blocks.append(np.broadcast_to(prof.reshape(view), shape).ravel())
+        else:
+            blocks.append(rng.uniform(0.1, 10.0, size=int(np.prod(shape))))
+    a = np.concatenate(blocks)
+    U = np.concatenate([[0.0], np.cumsum(1.0 / prof)])  # u at coordinates 0..n
+    c = np.meshgrid(*[np.arange(n + 1)] * dim, indexing="ij")
+    g = U[c[axis].transpose(*reversed(range(dim))).ravel()]
+    rhs = stencil.rhs_from_bc(dim, n, a, g, np.zeros(m ** dim))
+    x = spla.spsolve(stencil.assemble(dim, n, a, np.zeros(m ** dim)).tocsc(), rhs)
+    ui = _interior(dim, n, g)
+    assert np.abs(x - ui).max() <= 1e-11 * np.abs(ui).max()
+
+
+def test_rhs_from_bc_zero_data_and_columns():
+    dim, n = 2, 10
+    a, b = inputs.high_contrast_coefficients(dim, n, seed=2, low=1e-2, high=1e2)
+    f = np.arange(2 * (n - 1) ** dim, dtype=float).reshape(-1, 2)
+    assert np.array_equal(stencil.rhs_from_bc(dim, n, a, np.zeros(((n + 1) ** dim, 2)), f), f)
+    g = np.random.default_rng(0).standard_normal(((n + 1) ** dim, 2))
+    both = stencil.rhs_from_bc(dim, n, a, g, f)
+    for r in range(2):
+        assert np.array_equal(both[:, r], stencil.rhs_from_bc(dim, n, a, g[:, r], f[:, r]))
