@@ -207,6 +207,21 @@ def replica_throughput(units_per_step: int, steps: int, world: int, tmax_s: floa
     return world * steps * units_per_step / tmax_s
 
 
+def shard_problems(sizes, world: int):
+    """Independent problems onto `world` ranks by largest-first bin packing:
+    in descending size (ties: lower index first), each problem goes to the
+    rank with the least work so far (ties: lower rank).  Returns, per rank,
+    its problem indices in ascending order; every problem lands on exactly
+    one rank and no data moves between ranks afterwards."""
+    load = [0] * world
+    parts = [[] for _ in range(world)]
+    for p in sorted(range(len(sizes)), key=lambda i: (-sizes[i], i)):
+        r = min(range(world), key=lambda k: (load[k], k))
+        parts[r].append(p)
+        load[r] += sizes[p]
+    return [sorted(x) for x in parts]
+
+
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
@@ -376,20 +391,30 @@ def _sweep_traffic():
     return val if (val is not None and cap_sha == sha) else None
 
 
-def run_batched(args):
+def run_batched(args, rank: int = 0, world: int = 1, local_rank: int = 0):
     """The batched workload (64 independent 2D problems, 32 RHS each) through
-    hif_factor_batch / hif_solve_batch; one JSON line, DOF x RHS per second."""
+    hif_factor_batch / hif_solve_batch; one JSON line, DOF x RHS per second.
+    With N ranks the problems are sharded (shard_problems, weighted by
+    DOF x RHS) and each rank factors and solves its own; value = all
+    problems' units over the slowest rank's time."""
     import torch
     from paper_1307_2895_gb300 import hif, inputs
+    torch.cuda.set_device(local_rank)
     hif.load()
-    probs = inputs.batched_problems(64, seed=0)
+    allp = inputs.batched_problems(64, seed=0)
+    units_all = [(p["n"] - 1) ** 2 * p["nrhs"] for p in allp]
+    mine = shard_problems(units_all, world)[rank]
+    probs = [allp[i] for i in mine]
     rhs = [inputs.rhs(2, p["n"], p["nrhs"], seed=p["seed"]) for p in probs]
     spec = [(p["dim"], p["n"], p["a_stag"], p["b"]) for p in probs]
-    units = sum((p["n"] - 1) ** 2 * p["nrhs"] for p in probs)
+    units = sum(units_all)
     ms = []
     conv = True
     for step in range(args.warmup + args.steps):
         torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
         t0 = time.perf_counter()
         facts = hif.factor_batch(spec, 1e-6, precision=args.precision, nthreads=8)
         try:
@@ -401,16 +426,23 @@ def run_batched(args):
         if step >= args.warmup:
             ms.append(1e3 * (time.perf_counter() - t0))
             conv = conv and all(r[1]["converged"] and r[1]["relres_max"] <= TOL for r in res)
-    t = sum(ms) / 1e3
+    dev = torch.device("cuda", local_rank)
+    t = max_over_ranks(sum(ms) / 1e3, world, dev)
+    conv = max_over_ranks(0.0 if conv else 1.0, world, dev) == 0.0   # every rank converged
+    if rank != 0:
+        return 0
     print(json.dumps({"metric": "factor+solve DOF x RHS/s at rel. residual 1e-12, 64 independent problems",
-                      "value": units * args.steps / t, "unit": "DOF*RHS/s", "n_gpus": 1, "steps": args.steps,
+                      "value": units * args.steps / t, "unit": "DOF*RHS/s", "n_gpus": world, "steps": args.steps,
                       "warmup": args.warmup, "ms_per_step": t * 1e3 / args.steps, "higher_is_better": True,
                       "dtype": "f64+f32", "data": "synthetic", "converged": conv,
                       "config": {"workload": "64 x 2D contrast 1e2/1e4/1e6, interior edges log-uniform 127..1023 "
                                              "(sum N = %d), 32 RHS each, eps=1e-6" % sum((p["n"] - 1) ** 2
                                                                                           for p in probs),
-                                 "precision": args.precision, "parallelism": "8 host threads, one stream "
-                                                                             "per problem"}}), flush=True)
+                                 "precision": args.precision,
+                                 "parallelism": "8 host threads, one stream per problem" + (
+                                     "; problems sharded over %d ranks (largest first)" % world if world > 1
+                                     else "")},
+                      "scaling": "strong"}), flush=True)
     return 0
 
 
@@ -593,8 +625,6 @@ def main():
         return run_apply_only(args)
     if args.ncu_solve:
         return run_solve_only(args)
-    if args.batched:
-        return run_batched(args)
     if args.workload3d:
         return run_3d(args)
     if args.tc_roofline:
@@ -613,6 +643,8 @@ def main():
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
     try:
+        if args.batched:
+            return run_batched(args, rank, world, local_rank)
         return run_gpu(args, rank, world, local_rank)
     finally:
         if world > 1:

@@ -2,8 +2,11 @@
 
 Several GPUs run independent replicas of the workload (weak scaling, no
 data-path collective): the value is the units of all ranks over the slowest
-rank's time, the time reduced by one all-reduce MAX.  The reference arm runs
-on rank 0 only; the other ranks exit 0 without work or output.
+rank's time, the time reduced by one all-reduce MAX.  The batched workload's
+independent problems are sharded instead (largest first onto the least
+loaded rank); "every rank converged" is the same MAX reduction.  The
+reference arm runs on rank 0 only; the other ranks exit 0 without work or
+output.
 """
 import json
 import os
@@ -72,3 +75,53 @@ def test_reference_arm_two_ranks_torchrun():
     assert rec["impl"] == "reference" and rec["n_gpus"] == 2 and rec["steps"] == 1
     assert rec["value"] > 0 and rec["e2e"]["value"] == rec["value"]
     assert rec["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_shard_problems_largest_first():
+    """Every problem on exactly one rank; the largest-first rule keeps the
+    heaviest rank within one problem of the lightest; deterministic; one
+    rank gets everything."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import bench
+    m = np.random.default_rng(0).integers(127, 1024, size=64)
+    sizes = [int(v) ** 2 * 32 for v in m]            # DOF x RHS of 64 problems, 32 RHS each
+    assert bench.shard_problems(sizes, 1) == [list(range(64))]
+    for world in (2, 3, 4, 8):
+        parts = bench.shard_problems(sizes, world)
+        assert parts == bench.shard_problems(sizes, world)
+        assert sorted(i for part in parts for i in part) == list(range(64))
+        loads = [sum(sizes[i] for i in part) for part in parts]
+        assert max(loads) - min(loads) <= max(sizes)
+    # by hand, sizes 3 5 2 4 3 onto two ranks (loads after each step):
+    # #1 (5) -> r0 (5, 0); #3 (4) -> r1 (5, 4); #0 (3) -> r1 (5, 7);
+    # #4 (3) -> r0 (8, 7); #2 (2) -> r1 (8, 9)
+    assert bench.shard_problems([3, 5, 2, 4, 3], 2) == [[1, 4], [0, 2, 3]]
+
+
+def test_batched_all_converged_reduction_gloo():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_conv_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+    assert all(p.exitcode == 0 for p in procs)
+    got = sorted(q.get(timeout=5) for _ in range(2))
+    assert got == [(0, False), (1, False)]      # rank 1 did not converge: nobody reports converged
+
+
+def _conv_main(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        conv = rank == 0
+        q.put((rank, bench.max_over_ranks(0.0 if conv else 1.0, world) == 0.0))
+    finally:
+        dist.destroy_process_group()
