@@ -1046,7 +1046,14 @@ struct Precond {
       h->profile = 0;
       cudaGraph_t g = nullptr;
       CU(cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal));
-      eager();
+      try {
+        eager();
+      } catch (...) {   // leave the stream out of capture mode for later calls
+        if (cudaStreamEndCapture(h->st, &g) == cudaSuccess && g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        h->profile = prof;
+        throw;
+      }
       const cudaError_t ce = cudaStreamEndCapture(h->st, &g);
       h->profile = prof;
       cudaError_t e = ce;
