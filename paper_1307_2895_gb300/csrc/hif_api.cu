@@ -157,9 +157,17 @@ struct LevelFronts {
 
 // Rank-independent structure of level 0 of one grid (cells and the fronts of
 // level 1/2 depend only on dim, n and the leaf size): built once, then shared
-// read-only by every factorization of that grid.  Device copies live for the
-// rest of the process.
+// read-only by every factorization of that grid.  Its device copies are freed
+// with it, when neither the cache nor any handle holds it any more.
 struct Level0 {
+  Level0() = default;
+  Level0(const Level0&) = delete;
+  Level0& operator=(const Level0&) = delete;
+  ~Level0() {
+    void* dev[] = {d_cls0, d_cdesc, d_cipool, d_capply, d_fdesc, d_fip};
+    for (void* p : dev)
+      if (p) cudaFree(p);
+  }
   std::vector<HostCell> cells;
   std::vector<CellDesc> cdesc;
   int64_t work_elems = 0, fac_elems = 0;
@@ -350,7 +358,8 @@ T* dev_copy(const std::vector<T>& v) {
 }
 
 std::mutex g_l0_mutex;
-std::map<std::tuple<int, int, int, int>, std::shared_ptr<Level0>> g_l0_cache;
+// never destroyed: no device frees run while the process exits
+auto& g_l0_cache = *new std::map<std::tuple<int, int, int, int>, std::shared_ptr<Level0>>();
 
 std::shared_ptr<const Level0> get_level0(const Geometry& G) {
   int dev = 0;
@@ -385,7 +394,8 @@ std::shared_ptr<const Level0> get_level0(const Geometry& G) {
   L0->d_capply = dev_copy(ad);
   L0->d_fdesc = dev_copy(*L0->fdesc);
   L0->d_fip = dev_copy(fip);
-  if (g_l0_cache.size() >= 16) g_l0_cache.clear();   // handles keep their own reference
+  // handles keep their own reference; an evicted entry is freed with its last handle
+  if (g_l0_cache.size() >= 64) g_l0_cache.clear();
   g_l0_cache[key] = L0;
   return L0;
 }
