@@ -177,7 +177,8 @@ def _stream_ptr(stream) -> Optional[int]:
 
 
 class Factorization:
-    """Handle of one factorization (``hif_factor``); free with :meth:`free`."""
+    """Handle of one factorization (``hif_factor``); free with :meth:`free`, or
+    use it as a context manager (``with hif.factor(...) as F:``)."""
 
     def __init__(self, handle, lib, N: int):
         self._h = handle
@@ -281,6 +282,12 @@ class Factorization:
         if self._h:
             self._lib.hif_free(self._h)
             self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc) -> None:
+        self.free()
 
     def __del__(self):
         try:

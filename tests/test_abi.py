@@ -106,3 +106,21 @@ def test_factor_failure_after_handle_creation_without_gpu():
         rc = lib.hif_factor(ctypes.byref(grid), a.ctypes.data, b.ctypes.data, None, 1e-6, None, ctypes.byref(h))
         assert rc in (hif.HIF_ERR_CUDA, hif.HIF_ERR_OOM) and h.value is None
         assert lib.hif_last_error()
+
+
+def test_factorization_context_manager_frees_once():
+    """with ... as F frees the handle on exit (hif_free once), after which any
+    use raises; a second free is a no-op."""
+    calls = []
+
+    class _Lib:
+        def hif_free(self, h):
+            calls.append(h)
+
+    with hif.Factorization(ctypes.c_void_p(1234), _Lib(), 10) as F:
+        assert F._live().value == 1234
+    assert len(calls) == 1 and calls[0].value == 1234
+    with pytest.raises(RuntimeError):
+        F._live()
+    F.free()
+    assert len(calls) == 1
