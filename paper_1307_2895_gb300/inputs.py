@@ -123,7 +123,11 @@ def high_contrast_coefficients(dim: int, n: int, seed: int, low: float, high: fl
     2. Separable normalized Gaussian smoothing of width ``width_h * h``
        (``2*width_h`` lattice units), truncated at four widths, reflecting
        boundary.
-    3. Values above ``threshold`` become ``high``, the others ``low``.
+    3. Values above ``threshold`` become ``high``, the others ``low``.  The
+       recipe splits at the median of the smoothed values; 0.5, the mean of
+       U[0,1), about which the smoothed field is symmetric, is the default
+       here, so one realization's high share is near but not exactly one half
+       (51.9% for the 511 x 511 field of seed 2).
 
     Returns ``(a_stag, b)`` with ``b = 0``.
     """
