@@ -163,3 +163,33 @@ def test_planted_dropped_stencil_term_is_caught():
     v = np.sin(np.pi * X[:, 0]) * np.sin(np.pi * X[:, 1])
     lam = (8.0 / h ** 2) * np.sin(np.pi * h / 2) ** 2
     assert np.linalg.norm(A.tocsr() @ v - lam * v) > 1e-6 * lam * np.linalg.norm(v)
+
+
+@pytest.mark.parametrize("dim,n,eps,field", [(2, 16, 1e-3, "lap"), (2, 32, 1e-4, "contrast"),
+                                             (3, 8, 1e-2, "lap"), (3, 12, 1e-3, "contrast")])
+def test_power_estimates_against_exact_norms(dim, n, eps, field):
+    """e_a and e_s of Section 5 against the exact 2-norms of A - F, A and
+    I - A F^-1 (dense F and F^-1 from applying them to the identity): each
+    power iteration stops at 1e-2 relative change, so each estimated norm is
+    at most the true one and, on these problems, within 15% of it; e_a, a
+    quotient of two such estimates, within 15% either way."""
+    if field == "lap":
+        a, b = inputs.constant_coefficients(dim, n)
+    else:
+        a, b = inputs.high_contrast_coefficients(dim, n, seed=3, low=1e-2, high=1e2)
+    A = stencil.assemble(dim, n, a, b)
+    F = hifde.factor(A, dim, n, eps)
+    I = np.eye(A.shape[0])
+    Ad = A.toarray()
+    nA = np.linalg.norm(Ad, 2)
+    nE = np.linalg.norm(Ad - F.apply(I), 2)
+    es_x = np.linalg.norm(I - Ad @ F.apply_inverse(I), 2)
+    x0 = inputs.power_start(dim, n)
+    est_A = hifde.power_norm(lambda v: A @ v, x0)
+    est_E = hifde.power_norm(lambda v: A @ v - F.apply(v), x0)
+    assert 0.85 * nA <= est_A <= nA * (1 + 1e-12)
+    assert 0.85 * nE <= est_E <= nE * (1 + 1e-9)
+    ea, es = hifde.power_estimates(A, F, x0)
+    assert ea == pytest.approx(est_E / est_A, rel=1e-12)
+    assert 0.85 <= ea / (nE / nA) <= 1.15
+    assert 0.85 * es_x <= es <= es_x * (1 + 1e-9)
