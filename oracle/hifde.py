@@ -48,7 +48,8 @@ Readings where the paper leaves a choice:
 Parity status: MF, the stencil, Lemma 2.1, Lemma 2.4, the ID, F and F^-1 are
 pinned by the ``-m "not gpu"`` tests (dense LU, closed forms, exact low rank,
 LAPACK's pivoted QR, invariants); the power estimates by the exact 2-norms of
-dense A - F, A and I - A F^-1 on small grids.
+dense A - F, A and I - A F^-1 on small grids; PCG by scipy's preconditioned
+CG, iterate by iterate.
 """
 from __future__ import annotations
 

@@ -193,3 +193,23 @@ def test_power_estimates_against_exact_norms(dim, n, eps, field):
     assert ea == pytest.approx(est_E / est_A, rel=1e-12)
     assert 0.85 <= ea / (nE / nA) <= 1.15
     assert 0.85 * es_x <= es <= es_x * (1 + 1e-9)
+
+
+@pytest.mark.parametrize("dim,n,eps", [(2, 32, 1e-2), (3, 12, 1e-1)])
+def test_pcg_iterates_match_scipy_cg(dim, n, eps):
+    """The oracle's PCG (Section 5) and scipy's preconditioned CG, the same
+    textbook recurrences with M^-1 = F^-1, produce the same iterate after
+    every step k (a loose eps keeps several steps before convergence)."""
+    import scipy.sparse.linalg as spla
+    a, b = inputs.high_contrast_coefficients(dim, n, seed=8, low=1e-1, high=1e1)
+    A = stencil.assemble(dim, n, a, b)
+    F = hifde.factor(A, dim, n, eps)
+    f = inputs.rhs(dim, n, 1, seed=2)[:, 0]
+    M = spla.LinearOperator(A.shape, matvec=lambda v: F.apply_inverse(np.asarray(v).ravel()))
+    seen = []
+    spla.cg(A, f, rtol=1e-15, atol=0.0, maxiter=6, M=M, callback=lambda xk: seen.append(xk.copy()))
+    assert len(seen) == 6
+    for k, xs in enumerate(seen, start=1):
+        x, it, _ = hifde.pcg(A, F, f, tol=1e-15, maxit=k)
+        assert it[0] == k
+        assert np.linalg.norm(x - xs) <= 1e-10 * np.linalg.norm(xs), k
