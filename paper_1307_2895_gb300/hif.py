@@ -161,6 +161,27 @@ def _as_2d(x):
     return x.reshape(x.shape[0], -1)
 
 
+def _numel(x) -> int:
+    return int(x.numel()) if _is_torch(x) else int(np.size(x))
+
+
+def _need(x, count: int, what: str) -> None:
+    """The library reads `count` elements from x: refuse any other length."""
+    if x is not None and _numel(x) != count:
+        raise ValueError(f"{what} has {_numel(x)} elements, expected {count}")
+
+
+def _need_problem(dim: int, n: int, a_stag, b) -> None:
+    if dim in (2, 3) and n >= 2:
+        _need(a_stag, dim * n * (n - 1) ** (dim - 1), "a_stag")
+        _need(b, (n - 1) ** dim, "b")
+
+
+def _need_rows(x2, N: int, what: str) -> None:
+    if x2.shape[0] != N:
+        raise ValueError(f"{what} has {x2.shape[0]} rows, expected N = {N}")
+
+
 def _empty_like(x, shape):
     if _is_torch(x):
         import torch
@@ -193,6 +214,7 @@ class Factorization:
     def apply(self, x, inverse: bool = True):
         """y = F^-1 x (inverse=True) or F x; x has shape (N,) or (N, nrhs)."""
         x2 = _as_2d(x)
+        _need_rows(x2, self.N, "x")
         y = _empty_like(x, x2.shape)
         rc = self._lib.hif_apply(self._live(), APPLY_FINV if inverse else APPLY_F, _ptr(x2), _ptr(y),
                                  x2.shape[1], x2.shape[1])
@@ -201,12 +223,14 @@ class Factorization:
 
     def matvec(self, x):
         x2 = _as_2d(x)
+        _need_rows(x2, self.N, "x")
         y = _empty_like(x, x2.shape)
         _check(self._lib.hif_matvec(self._live(), _ptr(x2), _ptr(y), x2.shape[1], x2.shape[1]), self._lib)
         return y.reshape(x.shape)
 
     def estimate(self, x0, rtol: float = 1e-2, maxit: int = 200):
         """hif_estimate: (e_a, e_s) by power iteration from x0 (Section 5)."""
+        _need(x0, self.N, "x0")
         ea, es = ctypes.c_double(), ctypes.c_double()
         _check(self._lib.hif_estimate(self._live(), _ptr(x0), rtol, maxit, ctypes.byref(ea), ctypes.byref(es)),
                self._lib)
@@ -224,6 +248,8 @@ class Factorization:
         (x, info dict) or (x_hi, x_lo, info) with ``want_lo``.  ``out`` (same
         shape as rhs, contiguous float64) receives x if given."""
         r2 = _as_2d(rhs)
+        _need_rows(r2, self.N, "rhs")
+        _need(out, self.N * r2.shape[1], "out")
         x = _empty_like(rhs, r2.shape) if out is None else out.reshape(r2.shape)
         xlo = _empty_like(rhs, r2.shape) if want_lo else None
         info = _SolveInfo()
@@ -400,6 +426,8 @@ def factor(dim: int, n: int, a_stag, b, eps: float, variant: str = "hifde", prec
     tensor_cores (mixed precision): 0 three-part TF32 split (about FP32),
     2 two-part, 1 plain TF32, -1 FP32 on the SIMT pipes."""
     lib = load()
+    _need_problem(dim, n, a_stag, b)
+    _need(rank_model, MLP_PARAMS, "rank_model")
     grid = _Grid(dim, n, leaf, VARIANTS[variant])
     opts = _Opts(PRECISIONS[precision], skip_levels, ID_MODES[id_mode], oversample, _stream_ptr(stream),
                  _ptr(rank_model, "float32"), seed, big_cell, tensor_cores, 0 if autotune else -1)
@@ -416,6 +444,8 @@ def factor_batch(problems, eps: float, variant: str = "hifde", precision: str = 
     concurrently (one stream each); returns one Factorization per problem."""
     lib = load()
     m = len(problems)
+    for d, n, a, b in problems:
+        _need_problem(d, n, a, b)
     grids = (_Grid * m)(*[_Grid(d, n, leaf, VARIANTS[variant]) for d, n, _, _ in problems])
     pa = (ctypes.c_void_p * m)(*[_ptr(a) for _, _, a, _ in problems])
     pb = (ctypes.c_void_p * m)(*[_ptr(b) for _, _, _, b in problems])
@@ -439,7 +469,11 @@ def solve_batch(facts, rhs_list, tol: float = 1e-12, maxit: int = 1000, nthreads
     factorization, solved concurrently; returns [(x, info dict), ...]."""
     lib = load()
     m = len(facts)
+    if len(rhs_list) != m:
+        raise ValueError("one right-hand side array per factorization")
     r2 = [_as_2d(r) for r in rhs_list]
+    for F, q in zip(facts, r2):
+        _need_rows(q, F.N, "rhs")
     xs = [_empty_like(r, q.shape) for r, q in zip(rhs_list, r2)]
     hs = (ctypes.c_void_p * m)(*[F._live() for F in facts])
     pr = (ctypes.c_void_p * m)(*[_ptr(q) for q in r2])

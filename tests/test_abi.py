@@ -124,3 +124,29 @@ def test_factorization_context_manager_frees_once():
         F._live()
     F.free()
     assert len(calls) == 1
+
+
+def test_binding_refuses_wrong_lengths_before_the_library():
+    """The library reads as many elements as the grid implies; the binding
+    raises ValueError for any other length before calling it."""
+    n = 16
+    a, b = np.ones(2 * n * (n - 1)), np.zeros((n - 1) ** 2)
+    with pytest.raises(ValueError, match="a_stag"):
+        hif.factor(2, n, a[:-1], b, 1e-6)
+    with pytest.raises(ValueError, match="b has"):
+        hif.factor(2, n, a, np.zeros((n - 1) ** 2 + 1), 1e-6)
+    with pytest.raises(ValueError, match="rank_model"):
+        hif.factor(2, n, a, b, 1e-6, id_mode="learned", rank_model=np.zeros(7, dtype=np.float32))
+    with pytest.raises(ValueError, match="a_stag"):
+        hif.factor_batch([(2, n, a, b), (2, n, a[:10], b)], 1e-6)
+
+    class _NoLib:      # any library call would fail with AttributeError
+        pass
+
+    F = hif.Factorization(ctypes.c_void_p(1), _NoLib(), (n - 1) ** 2)
+    bad = np.zeros(((n - 1) ** 2 + 3, 2))
+    for call in (lambda: F.apply(bad), lambda: F.matvec(bad), lambda: F.solve(bad),
+                 lambda: F.estimate(np.zeros(5)), lambda: F.solve(np.zeros((n - 1) ** 2), out=np.zeros(3))):
+        with pytest.raises(ValueError):
+            call()
+    F._h = None        # nothing to free
