@@ -20,6 +20,7 @@ Other workloads, one JSON line each:
     python bench.py --workload3d laplace3d_n64|contrast3d_n128 [--eps E]
                     [--precision fp64|mixed|fp32_apply] [--tensor-cores 0|1|2|3|-1]
     python bench.py --batched          # 64 independent 2D problems, 32 RHS each
+                                       # (under torchrun: problems sharded over the ranks)
     python bench.py --tc-roofline      # the tensor-core Schur update alone
 
 and the profiling helpers ``--ncu-apply K`` / ``--ncu-solve K`` (fixed launch
