@@ -32,7 +32,7 @@ inline void nearest(int64_t x2, const std::vector<int>& pos, int& idx, int64_t& 
 
 }  // namespace
 
-Symbolic3x::Symbolic3x(int n, int leaf) : n_(n) {
+Symbolic3x::Symbolic3x(int n, int leaf, bool implicit_stencil) : n_(n), implicit_(implicit_stencil) {
   L_ = std::max(1, (int)std::lround(std::log2((double)n / leaf)));
   m_ = n >> L_;
   const int e = n - 1;
@@ -90,15 +90,17 @@ bool Symbolic3x::voronoi(int g, const std::vector<std::vector<int>>* fams, int n
 // Calls fn(j) for every active DOF j coupled to i (possibly more than once;
 // j == i may appear).
 template <typename Fn>
-static inline void for_each_coupled(int i, int n, const std::vector<char>& active,
+static inline void for_each_coupled(int i, int n, bool implicit, const std::vector<char>& active,
                                     const std::vector<std::vector<int>>& clique,
                                     const std::vector<std::vector<int>>& of, Fn&& fn) {
-  const int e = n - 1;
-  const int x[3] = {i % e, (i / e) % e, i / (e * e)};
-  const int step[3] = {1, e, e * e};
-  for (int a = 0; a < 3; ++a) {
-    if (x[a] > 0 && active[i - step[a]]) fn(i - step[a]);
-    if (x[a] < e - 1 && active[i + step[a]]) fn(i + step[a]);
+  if (implicit) {
+    const int e = n - 1;
+    const int x[3] = {i % e, (i / e) % e, i / (e * e)};
+    const int step[3] = {1, e, e * e};
+    for (int a = 0; a < 3; ++a) {
+      if (x[a] > 0 && active[i - step[a]]) fn(i - step[a]);
+      if (x[a] < e - 1 && active[i + step[a]]) fn(i + step[a]);
+    }
   }
   for (int id : of[i]) {
     const std::vector<int>& c = clique[id];
@@ -118,7 +120,7 @@ std::vector<int> Symbolic3x::neighbors(const std::vector<int>& c) const {
   for (int i : c) seen_[i] = in_c;
   std::vector<int> out;
   for (int i : c)
-    for_each_coupled(i, n_, active_, clique_, of_, [&](int j) {
+    for_each_coupled(i, n_, implicit_, active_, clique_, of_, [&](int j) {
       if (seen_[j] != in_c && seen_[j] != in_out) {
         seen_[j] = in_out;
         out.push_back(j);
@@ -168,7 +170,7 @@ std::vector<std::vector<int>> Symbolic3x::cells(int l) {
     for (int s = start[c]; s < start[c + 1]; ++s) {
       const int i = members[s];
       bool ext = false;
-      for_each_coupled(i, n_, active_, clique_, of_, [&](int j) {
+      for_each_coupled(i, n_, implicit_, active_, clique_, of_, [&](int j) {
         if (mark_[j] >= 0 && mark_[j] != c) ext = true;
       });
       if (ext)
@@ -231,12 +233,26 @@ std::vector<std::vector<int>> Symbolic3x::groups(int l, int kind) {
   return out;
 }
 
-void Symbolic3x::add_clique(const std::vector<int>& members) {
+int Symbolic3x::add_clique(const std::vector<int>& members) {
   const int id = (int)clique_.size();
   clique_.push_back(members);
+  clique_live_.push_back(members.empty() ? 0 : 1);
   for (int i : members) of_[i].push_back(id);
+  return id;
 }
 
+std::vector<int> Symbolic3x::touching(const std::vector<int>& c) const {
+  std::vector<int> ids;
+  for (int i : c)
+    for (int id : of_[i])
+      if (clique_live_[id]) ids.push_back(id);
+  std::sort(ids.begin(), ids.end());
+  ids.erase(std::unique(ids.begin(), ids.end()), ids.end());
+  return ids;
+}
+
+// Deactivates the DOFs and drops them from their cliques (the others keep
+// their order; a clique left empty dies).
 void Symbolic3x::remove(const std::vector<int>& dofs) {
   std::vector<int> touched;
   for (int d : dofs) {
@@ -249,20 +265,27 @@ void Symbolic3x::remove(const std::vector<int>& dofs) {
   for (int id : touched) {
     std::vector<int>& c = clique_[id];
     c.erase(std::remove_if(c.begin(), c.end(), [&](int j) { return !active_[j]; }), c.end());
-    if (c.size() < 2) std::vector<int>().swap(c);
+    if (c.empty()) {
+      std::vector<int>().swap(c);
+      clique_live_[id] = 0;
+    }
   }
   active_dirty_ = true;
 }
 
-void Symbolic3x::eliminate(const std::vector<int>& p) {
+int Symbolic3x::eliminate(const std::vector<int>& p) {
   const std::vector<int> q = neighbors(p);
+  for (int id : touching(p)) {   // all inside p and q: absorbed by the new clique
+    std::vector<int>().swap(clique_[id]);
+    clique_live_[id] = 0;
+  }
   remove(p);
-  if (q.size() >= 2) add_clique(q);
+  return q.empty() ? -1 : add_clique(q);
 }
 
-bool Symbolic3x::skeletonize(const std::vector<int>& c, const std::vector<int>& s) {
+int Symbolic3x::skeletonize(const std::vector<int>& c, const std::vector<int>& s) {
   for (int i : c)
-    if (i < 0 || i >= N_ || !active_[i]) return false;
+    if (i < 0 || i >= N_ || !active_[i]) return -2;
   if (stamp_ > INT_MAX - 4) {
     std::fill(seen_.begin(), seen_.end(), 0);
     stamp_ = 0;
@@ -271,16 +294,15 @@ bool Symbolic3x::skeletonize(const std::vector<int>& c, const std::vector<int>& 
   const int in_c = stamp_ - 1, in_s = stamp_;
   for (int i : c) seen_[i] = in_c;
   for (int i : s) {
-    if (i < 0 || i >= N_ || seen_[i] != in_c) return false;
+    if (i < 0 || i >= N_ || seen_[i] != in_c) return -2;
     seen_[i] = in_s;
   }
   std::vector<int> r;
   for (int i : c)
     if (seen_[i] == in_c) r.push_back(i);
-  if (r.empty()) return true;
+  if (r.empty()) return -1;
   remove(r);
-  if (s.size() >= 2) add_clique(s);
-  return true;
+  return s.empty() ? -1 : add_clique(s);
 }
 
 }  // namespace hif

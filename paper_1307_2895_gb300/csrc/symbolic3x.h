@@ -2,13 +2,22 @@
 // (Section 4.5, Algorithm 4.2): the sparsity pattern of the active matrix
 // A_l and the index sets of every level built from it.
 //
-// Pattern.  Two active DOFs are coupled when they are 7-point stencil
-// neighbours or when a live clique holds both.  The elimination of a set p
-// (Lemma 2.1) makes its neighbours q = p^N a clique (B_qq is dense) and
-// removes p; the skeletonization of a group c with skeleton s (Lemma 2.4)
-// makes s a clique (B_ss) when it also has redundant DOFs r = c \ s, and
-// removes r (their couplings outside c are dropped with the ID's residual).
-// No coupling between two active DOFs is ever removed.
+// Pattern.  Two active DOFs are coupled when a live clique of two or more
+// members holds both, or (with the implicit stencil) when they are 7-point
+// stencil neighbours.  The elimination of a set p (Lemma 2.1) absorbs every
+// clique touching p (each lies in p and its neighbours q = p^N) into one
+// clique on q (B_qq is dense) and removes p; the skeletonization of a group
+// c with skeleton s (Lemma 2.4) removes the redundant DOFs r = c \ s from
+// every clique (their couplings outside c are dropped with the ID's
+// residual) and adds a clique on s (the update of A_ss).  No coupling
+// between two active DOFs is ever removed.
+//
+// Cliques have identities and ordered members, so that A_l can be held as a
+// sum of dense matrices, one per live clique (the stencil's bonds and
+// diagonal included, as cliques of two and one): eliminate returns the id of
+// the clique that replaces the absorbed ones, skeletonize that of the new
+// skeleton clique, and a clique that loses members keeps the others in
+// their order.
 //
 // Index sets of level l (S = 2^l m, K = 2^(L-l) cells per axis; distances
 // exact in doubled grid units; a DOF with two or more nearest centers joins
@@ -34,7 +43,10 @@ class Symbolic3x {
  public:
   // Grid of n intervals per axis, N = (n-1)^3 DOFs (x fastest); L = the
   // nearest integer to log2(n / leaf), at least 1; m = floor(n / 2^L).
-  Symbolic3x(int n, int leaf);
+  // implicit_stencil: the 7-point couplings belong to the pattern without
+  // cliques (pattern-only use); otherwise every coupling comes from cliques
+  // the caller adds.
+  Symbolic3x(int n, int leaf, bool implicit_stencil = true);
 
   int levels() const { return L_; }
   int leaf_width() const { return m_; }
@@ -52,11 +64,23 @@ class Symbolic3x {
   // c^N: active DOFs outside c coupled to a DOF of c, ascending.
   std::vector<int> neighbors(const std::vector<int>& c) const;
 
-  // Lemma 2.1 on the active set p.
-  void eliminate(const std::vector<int>& p);
-  // Lemma 2.4 on group c with skeleton s (a subset of c).  Returns false,
-  // changing nothing, when c holds an inactive DOF or s is not in c.
-  bool skeletonize(const std::vector<int>& c, const std::vector<int>& s);
+  // A clique on the given active DOFs, in the order given; returns its id.
+  int add_clique(const std::vector<int>& members);
+  // Ids of the live cliques with a member in c, ascending.
+  std::vector<int> touching(const std::vector<int>& c) const;
+  // Members of clique id in their order (empty once it is dead).
+  const std::vector<int>& members(int id) const { return clique_[id]; }
+  bool live(int id) const { return clique_live_[id] != 0; }
+
+  // Lemma 2.1 on the active set p: the cliques touching p die and one clique
+  // on q = p^N (ascending) replaces them.  Returns its id, or -1 (q empty).
+  int eliminate(const std::vector<int>& p);
+  // Lemma 2.4 on group c with skeleton s (a subset of c): r = c \ s leaves
+  // every clique (a clique left empty dies); when r and s are both
+  // non-empty a clique on s (in the order given) is added and its id
+  // returned, else -1.  Returns -2, changing nothing, when c holds an
+  // inactive DOF or s is not in c.
+  int skeletonize(const std::vector<int>& c, const std::vector<int>& s);
 
  private:
   struct Key {
@@ -65,14 +89,15 @@ class Symbolic3x {
   // Nearest center of the union of families (per family, a list of
   // positions per axis, doubled units); false on a tie.
   bool voronoi(int g, const std::vector<std::vector<int>>* fams, int nfam, Key& k) const;
-  void add_clique(const std::vector<int>& members);
   void remove(const std::vector<int>& dofs);
 
   int n_, m_, L_, N_;
+  bool implicit_;
   std::vector<char> active_;
   std::vector<int> active_list_;
   bool active_dirty_ = false;
   std::vector<std::vector<int>> clique_;   // active members (compacted on removal)
+  std::vector<char> clique_live_;
   std::vector<std::vector<int>> of_;       // cliques holding each DOF (may list dead ones)
   std::vector<int> mark_;                  // scratch stamps for set unions
   mutable std::vector<int> seen_;

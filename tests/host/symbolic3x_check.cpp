@@ -71,7 +71,7 @@ int main(int argc, char** argv) {
         if (ns < 0) return write_out(argv[5], o, 4);
         std::vector<int> s(ns);
         for (int& v : s) v = take();
-        if (!S.skeletonize(c, s)) return write_out(argv[5], o, 4);
+        if (S.skeletonize(c, s) == -2) return write_out(argv[5], o, 4);
       }
     }
   }
