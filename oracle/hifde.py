@@ -49,7 +49,8 @@ Parity status: MF, the stencil, Lemma 2.1, Lemma 2.4, the ID, F and F^-1 are
 pinned by the ``-m "not gpu"`` tests (dense LU, closed forms, exact low rank,
 LAPACK's pivoted QR, invariants); the power estimates by the exact 2-norms of
 dense A - F, A and I - A F^-1 on small grids; PCG by scipy's preconditioned
-CG, iterate by iterate.
+CG, iterate by iterate; F itself by the closed-form eigenpairs of the
+Laplacian (F v = lambda v to O(eps), the lowest modes included).
 """
 from __future__ import annotations
 

@@ -213,3 +213,22 @@ def test_pcg_iterates_match_scipy_cg(dim, n, eps):
         x, it, _ = hifde.pcg(A, F, f, tol=1e-15, maxit=k)
         assert it[0] == k
         assert np.linalg.norm(x - xs) <= 1e-10 * np.linalg.norm(xs), k
+
+
+@pytest.mark.parametrize("dim,n,eps", [(2, 32, 1e-6), (2, 64, 1e-6), (2, 32, 1e-9), (3, 16, 1e-3), (3, 16, 1e-6)])
+def test_factor_on_closed_form_eigenmodes(dim, n, eps):
+    """a = 1, b = 0: on the discrete sine modes v (A v = lambda v with the
+    closed-form lambda of Section 5's Laplacian), F v = lambda v up to
+    O(eps) relative to lambda, the lowest modes included (where A's own
+    scale would allow eps kappa): at most 20 eps on these grids."""
+    a, b = inputs.constant_coefficients(dim, n)
+    A = stencil.assemble(dim, n, a, b)
+    F = hifde.factor(A, dim, n, eps)
+    h = 1.0 / n
+    X = stencil.coords(dim, n) / n
+    for idx in [(1,) * dim, (2,) + (1,) * (dim - 1), (3,) + (1,) * (dim - 1), (n // 2,) * dim, (n - 1,) * dim]:
+        v = np.ones(X.shape[0])
+        for ax, i in enumerate(idx):
+            v *= np.sin(i * np.pi * X[:, ax])
+        lam = (4.0 / h ** 2) * np.sum(np.sin(np.array(idx) * np.pi * h / 2) ** 2)
+        assert np.linalg.norm(F.apply(v) - lam * v) <= 20 * eps * lam * np.linalg.norm(v), idx
