@@ -20,9 +20,11 @@ result goes to; a small numpy model of the matrices follows it:
 Each gathered block must equal the oracle's at the same step (1e-9 of its
 largest entry; the two sum the same terms in other orders): A_pp (as
 L L^T) and A_qp of every cell, the ID block of every group (recorded from the
-oracle's own calls), B_sr and B_rr (as L L^T), and the root matrix D.  Cases:
-15^3 with edges from level 0 and 23^3 (two levels) with edges from level 1,
-on a high-contrast field; the planted mistakes of the module's last test
+oracle's own calls), B_sr and B_rr (as L L^T), and the root matrix D.  Cases,
+on a high-contrast field: 15^3 with edges from level 0 (one level); 23^3
+(two levels) with edges from level 1, and from level 0, where the level-0
+edge cliques make the peel remove 249 DOFs from level 1's cells; the
+planted mistakes of the module's last test
 (a cell gathered without one of its cliques, cliques that keep r after a
 skeletonization) fail it.
 """
@@ -266,7 +268,7 @@ def _run(capi, n, eps, edge_start, field_seed, plant=None):
         plan.close()
 
 
-@pytest.mark.parametrize("n,edge_start", [(16, 0), (24, 1)])
+@pytest.mark.parametrize("n,edge_start", [(16, 0), (24, 1), (24, 0)])
 def test_clique_plan_reproduces_oracle_blocks(capi, n, edge_start):
     _run(capi, n, 1e-6, edge_start, field_seed=5)
 
