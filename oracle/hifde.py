@@ -55,7 +55,7 @@ Laplacian (F v = lambda v to O(eps), the lowest modes included).
 from __future__ import annotations
 
 import dataclasses
-from typing import Dict, List, Optional, Tuple
+from typing import Dict, List
 
 import numpy as np
 import scipy.linalg as sla

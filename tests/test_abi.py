@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 import torch
 
-from paper_1307_2895_gb300 import build, hif
+from paper_1307_2895_gb300 import hif
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 

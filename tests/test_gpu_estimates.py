@@ -12,7 +12,6 @@ C ABI.
 """
 import os
 
-import numpy as np
 import pytest
 
 from oracle import hifde, stencil

@@ -2,7 +2,6 @@
 Lemma 2.1 (sparse elimination), Lemma 2.2 / Cor. 2.3 (ID), Lemma 2.4
 (skeletonization)."""
 import numpy as np
-import pytest
 import scipy.linalg as sla
 import scipy.sparse as sp
 

@@ -7,7 +7,6 @@ It must return the same squared residual norms as the existing entry points
 second call reuses the library's fixed scratch left by the first), and must
 not change the device's free memory.  This file is collected last on purpose.
 """
-import numpy as np
 import pytest
 
 from paper_1307_2895_gb300 import inputs
