@@ -43,6 +43,7 @@ Symbolic3x::Symbolic3x(int n, int leaf, bool implicit_stencil) : n_(n), implicit
   of_.resize(N_);
   mark_.assign(N_, -1);
   seen_.assign(N_, 0);
+  pos_.assign(N_, -1);
 }
 
 const std::vector<int>& Symbolic3x::active() {
@@ -249,6 +250,29 @@ std::vector<int> Symbolic3x::touching(const std::vector<int>& c) const {
   std::sort(ids.begin(), ids.end());
   ids.erase(std::unique(ids.begin(), ids.end()), ids.end());
   return ids;
+}
+
+bool Symbolic3x::gather_plan(const std::vector<std::vector<int>>& keys, const std::vector<std::vector<int>>& order,
+                             GatherPlan& out) const {
+  out = GatherPlan();
+  const size_t nt = std::min(keys.size(), order.size());
+  out.start.push_back(0);
+  bool ok = true;
+  for (size_t t = 0; t < nt && ok; ++t) {
+    out.dim.push_back((int)order[t].size());
+    for (size_t k = 0; k < order[t].size(); ++k) pos_[order[t][k]] = (int)k;
+    for (int id : touching(keys[t])) {
+      out.clique.push_back(id);
+      out.map_start.push_back((int)out.map.size());
+      for (int g : clique_[id]) {
+        if (pos_[g] < 0) ok = false;
+        out.map.push_back(pos_[g]);
+      }
+    }
+    out.start.push_back((int)out.clique.size());
+    for (int g : order[t]) pos_[g] = -1;
+  }
+  return ok;
 }
 
 // Deactivates the DOFs and drops them from their cliques (the others keep

@@ -39,6 +39,14 @@
 
 namespace hif {
 
+// Flat description of one batch of gathers (a launch's worth of blocks):
+// target t's dense block, of side dim[t], is the sum over its contributions
+// k in [start[t], start[t+1]) of the matrix of clique clique[k], whose
+// member i lands on row and column map[map_start[k] + i] of the block.
+struct GatherPlan {
+  std::vector<int> dim, start, clique, map_start, map;
+};
+
 class Symbolic3x {
  public:
   // Grid of n intervals per axis, N = (n-1)^3 DOFs (x fastest); L = the
@@ -72,6 +80,13 @@ class Symbolic3x {
   const std::vector<int>& members(int id) const { return clique_[id]; }
   bool live(int id) const { return clique_live_[id] != 0; }
 
+  // The gathers of a batch: for target t, the live cliques touching keys[t]
+  // (ascending ids), each member placed at its position in order[t].
+  // Returns false (out unspecified) when a member of such a clique is not in
+  // order[t]: the block would not hold the clique.
+  bool gather_plan(const std::vector<std::vector<int>>& keys, const std::vector<std::vector<int>>& order,
+                   GatherPlan& out) const;
+
   // Lemma 2.1 on the active set p: the cliques touching p die and one clique
   // on q = p^N (ascending) replaces them.  Returns its id, or -1 (q empty).
   int eliminate(const std::vector<int>& p);
@@ -100,6 +115,7 @@ class Symbolic3x {
   std::vector<char> clique_live_;
   std::vector<std::vector<int>> of_;       // cliques holding each DOF (may list dead ones)
   std::vector<int> mark_;                  // scratch stamps for set unions
+  mutable std::vector<int> pos_;           // scratch: position of a DOF in a block's order, or -1
   mutable std::vector<int> seen_;
   mutable int stamp_ = 0;
 };

@@ -57,6 +57,20 @@ void s3x_active(void* h) {
   Handle* H = static_cast<Handle*>(h);
   H->last = {H->S.active()};
 }
+// Gather plan of nt targets given flattened key and order lists (offsets of
+// nt + 1 entries); leaves dim, start, clique, map_start, map as the lists.
+int s3x_gather_plan(void* h, int nt, const int* keys, const int* key_off, const int* order, const int* ord_off) {
+  Handle* H = static_cast<Handle*>(h);
+  std::vector<std::vector<int>> K(nt), O(nt);
+  for (int t = 0; t < nt; ++t) {
+    K[t].assign(keys + key_off[t], keys + key_off[t + 1]);
+    O[t].assign(order + ord_off[t], order + ord_off[t + 1]);
+  }
+  hif::GatherPlan g;
+  const bool ok = H->S.gather_plan(K, O, g);
+  H->last = {g.dim, g.start, g.clique, g.map_start, g.map};
+  return ok ? 1 : 0;
+}
 int s3x_eliminate(void* h, const int* p, int k) { return static_cast<Handle*>(h)->S.eliminate(ids(p, k)); }
 int s3x_skeletonize(void* h, const int* c, int kc, const int* s, int ks) {
   return static_cast<Handle*>(h)->S.skeletonize(ids(c, kc), ids(s, ks));

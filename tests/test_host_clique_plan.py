@@ -17,6 +17,11 @@ result goes to; a small numpy model of the matrices follows it:
   holds -B_sr B_rr^-1 B_rs, and r leaves every clique (its entries dropped);
 * the root: the sum of the live cliques on s_L.
 
+Every block is also gathered through the flat plan of its batch (all cells
+of a level, all groups of a fractional level: Symbolic3x::gather_plan),
+applied as a gather launch would apply it; the result must equal the direct
+sum bit for bit.
+
 Each gathered block must equal the oracle's at the same step (1e-9 of its
 largest entry; the two sum the same terms in other orders): A_pp (as
 L L^T) and A_qp of every cell, the ID block of every group (recorded from the
@@ -60,7 +65,7 @@ def capi(tmp_path_factory):
            "s3x_add_clique": ([vp, ip, i], i), "s3x_cells": ([vp, i], None), "s3x_groups": ([vp, i, i], None),
            "s3x_neighbors": ([vp, ip, i], None), "s3x_touching": ([vp, ip, i], None),
            "s3x_members": ([vp, i], None), "s3x_active": ([vp], None), "s3x_eliminate": ([vp, ip, i], i),
-           "s3x_skeletonize": ([vp, ip, i, ip, i], i)}
+           "s3x_skeletonize": ([vp, ip, i, ip, i], i), "s3x_gather_plan": ([vp, i, ip, ip, ip, ip], i)}
     for name, (args, res) in sig.items():
         getattr(lib, name).argtypes = args
         getattr(lib, name).restype = res
@@ -118,6 +123,16 @@ class Plan:
         self.lib.s3x_active(self.h)
         return self._lists()[0]
 
+    def gather_plan(self, keys, orders):
+        """(ok, dim, start, clique, map_start, map) of one batch of gathers."""
+        def flat(lists):
+            off = np.concatenate([[0], np.cumsum([len(x) for x in lists])]).astype(int)
+            return self._arr([g for x in lists for g in x])[0], self._arr(off)[0]
+        kf, ko = flat(keys)
+        of, oo = flat(orders)
+        ok = self.lib.s3x_gather_plan(self.h, len(keys), kf, ko, of, oo)
+        return (ok == 1,) + tuple(self._lists())
+
     def eliminate(self, p):
         return self.lib.s3x_eliminate(self.h, *self._arr(p))
 
@@ -167,6 +182,21 @@ def _gather(store, ids, order):
     return F
 
 
+def _gather_batch(store, plan_out):
+    """What a gather launch computes from the flat plan: one block per target."""
+    ok, dim, start, clique, map_start, mp = plan_out
+    assert ok
+    blocks = []
+    for t, d in enumerate(dim):
+        F = np.zeros((d, d))
+        for k in range(start[t], start[t + 1]):
+            M = store[clique[k]][1]
+            ix = mp[map_start[k]:map_start[k] + M.shape[0]]
+            F[np.ix_(ix, ix)] += M
+        blocks.append(F)
+    return blocks
+
+
 def _close(X, Y, what):
     scale = max(np.abs(Y).max(), 1e-300)
     assert np.abs(X - Y).max() <= 1e-9 * scale, (what, np.abs(X - Y).max() / scale)
@@ -212,11 +242,13 @@ def _run(capi, n, eps, edge_start, field_seed, plant=None):
             lc = F.levels[2 * ell]
             cells = plan.cells(ell)
             assert len(cells) == len(lc.cells)
-            for p, rec in zip(cells, lc.cells):
-                q = plan.neighbors(p)
+            qs = [plan.neighbors(p) for p in cells]   # kept cells are never coupled: one batch
+            batch = _gather_batch(store, plan.gather_plan(cells, [p + q for p, q in zip(cells, qs)]))
+            for p, q, rec, Fb in zip(cells, qs, lc.cells, batch):
                 assert p == rec.p.tolist() and q == rec.q.tolist()
                 ids = plan.touching(p)
                 Fm = _gather(store, ids if plant != "drop_contribution" else ids[:-1], p + q)
+                assert plant or np.array_equal(Fb, Fm)
                 k = len(p)
                 _close(Fm[:k, :k], rec.L @ rec.L.T, "A_pp")
                 if q:
@@ -233,10 +265,12 @@ def _run(capi, n, eps, edge_start, field_seed, plant=None):
                 groups = plan.groups(ell, kind)
                 assert [fr.c.tolist() for fr in lev.fronts] == groups
                 gathered = []
-                for c in groups:                       # every ID block from the same A_l
-                    N = plan.neighbors(c)
+                Ns = [plan.neighbors(c) for c in groups]
+                batch = _gather_batch(store, plan.gather_plan(groups, [c + N for c, N in zip(groups, Ns)]))
+                for c, N, Fb in zip(groups, Ns, batch):  # every ID block from the same A_l
                     ids = plan.touching(c)
                     Fm = _gather(store, ids, c + N)
+                    assert np.array_equal(Fb, Fm)
                     _close(Fm[len(c):, :len(c)], recorded[k_id], "A_{c^N, c}")
                     k_id += 1
                     gathered.append((ids, Fm[:len(c), :len(c)]))
@@ -277,3 +311,21 @@ def test_clique_plan_reproduces_oracle_blocks(capi, n, edge_start):
 def test_clique_plan_planted_mistakes_fail(capi, plant):
     with pytest.raises((AssertionError, KeyError, ValueError)):
         _run(capi, 16, 1e-6, 0, field_seed=5, plant=plant)
+
+
+def test_gather_plan_refuses_a_block_that_misses_a_member(capi):
+    """A target whose order lacks a member of a clique touching its keys
+    (here a cell gathered on p alone, without q) is refused."""
+    n = 16
+    a, b = inputs.high_contrast_coefficients(3, n, seed=5, low=1e-2, high=1e2)
+    plan = Plan(capi, n)
+    try:
+        for mem, _ in _initial_cliques(n, a, b):
+            plan.add(mem)
+        p = plan.cells(0)[0]
+        q = plan.neighbors(p)
+        assert q
+        assert plan.gather_plan([p], [p + q])[0]
+        assert not plan.gather_plan([p], [p])[0]
+    finally:
+        plan.close()
