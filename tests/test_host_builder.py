@@ -18,7 +18,8 @@ positions of the oracle (oracle.hifde.level_separators):
   each of its 2^dim children at level l - 1.
 
 The grids (511^2, 63^3) are large enough for the builders' parallel paths;
-n = 40 and 3D n = 24 have rounded separators.  Level 1 starts from an alive set with the
+n = 40 and 3D n = 24 have rounded separators; n = 4 (cells of one DOF) and
+2D n = 5 are the smallest trees (one level).  Level 1 starts from an alive set with the
 level-0 interiors and a pseudo-random 30% of the front DOFs removed, as
 skeletonization removes redundant DOFs.
 """
@@ -167,11 +168,13 @@ def _level1_alive(dim, n, cells0, fronts0):
     return np.nonzero(~dead)[0].astype(np.int64)
 
 
-@pytest.mark.parametrize("dim,n", [(2, 512), (3, 64), (2, 40), (3, 24)])
+@pytest.mark.parametrize("dim,n", [(2, 512), (3, 64), (2, 40), (3, 24), (2, 4), (3, 4), (2, 5)])
 def test_builder_matches_definitions(harness, tmp_path, dim, n):
     alive0 = np.arange((n - 1) ** dim, dtype=np.int64)
     cells0, fronts0, _ = _run(harness, tmp_path, dim, n, 0, alive0)
     _check(dim, n, 0, alive0, cells0, fronts0, _reference(dim, n, 0, alive0))
+    if hifde.tree_levels(n, 8) < 2:
+        return                                   # one level: no level 1 to build
     alive1 = _level1_alive(dim, n, cells0, fronts0)
     cells1, fronts1, maps1 = _run(harness, tmp_path, dim, n, 1, alive1, prev_alive=alive0)
     _check(dim, n, 1, alive1, cells1, fronts1, _reference(dim, n, 1, alive1))

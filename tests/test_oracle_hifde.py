@@ -232,3 +232,20 @@ def test_factor_on_closed_form_eigenmodes(dim, n, eps):
             v *= np.sin(i * np.pi * X[:, ax])
         lam = (4.0 / h ** 2) * np.sum(np.sin(np.array(idx) * np.pi * h / 2) ** 2)
         assert np.linalg.norm(F.apply(v) - lam * v) <= 20 * eps * lam * np.linalg.norm(v), idx
+
+
+@pytest.mark.parametrize("dim,n", [(2, 4), (2, 5), (3, 4), (3, 5)])
+@pytest.mark.parametrize("eps", [0.0, 1e-6])
+def test_smallest_grids_match_dense_solve(dim, n, eps):
+    """The smallest trees (one level; at n = 4 every cell holds one DOF and
+    every front one DOF): F^-1 b equals the dense solve to rounding, and
+    every DOF is eliminated once."""
+    a, b = inputs.high_contrast_coefficients(dim, n, seed=1, low=1e-2, high=1e2)
+    A = stencil.assemble(dim, n, a, b)
+    f = inputs.rhs(dim, n, 2)
+    F = hifde.factor(A, dim, n, eps)
+    xd = np.linalg.solve(A.toarray(), f)
+    assert np.linalg.norm(F.apply_inverse(f) - xd) <= 1e-12 * np.linalg.norm(xd)
+    done = [g for lev in F.levels for rec in lev.cells for g in rec.p.tolist()]
+    done += [g for lev in F.levels for fr in lev.fronts for g in fr.rd.tolist()]
+    assert sorted(done + F.root.tolist()) == list(range((n - 1) ** dim))
