@@ -181,3 +181,12 @@ def test_rejects_foreign_skeleton(harness, tmp_path):
     skel[2] = gone
     rc, _ = _run(harness, tmp_path, n, 0, skel)
     assert rc == 4
+
+
+@pytest.mark.parametrize("n", [4, 5, 10])
+def test_smallest_and_ragged_grids(harness, tmp_path, monkeypatch, n):
+    """One-level trees: n = 4 (cells of one DOF), and n = 5 and 10, which are
+    not 2^L m (the last cells and groups are cut short), with edges from
+    level 0."""
+    a, b = inputs.high_contrast_coefficients(3, n, seed=5, low=1e-2, high=1e2)
+    _case(harness, tmp_path, monkeypatch, stencil.assemble(3, n, a, b), n, 1e-6, 0)
