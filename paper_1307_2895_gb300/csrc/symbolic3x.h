@@ -33,6 +33,10 @@
 //   * edges (kind 2): the same about the edge centers ((j - 1/2) S along the
 //     edge, j S on the other two; edges along x, y, z are families 0, 1, 2).
 // Which DOFs a group keeps comes from the numerical ID and is an input.
+//
+// One object serves one factorization; its calls share scratch state and
+// must not run concurrently (cells and groups use the host thread pool
+// internally).
 #pragma once
 #include <cstdint>
 #include <vector>
@@ -114,7 +118,7 @@ class Symbolic3x {
   std::vector<std::vector<int>> clique_;   // active members (compacted on removal)
   std::vector<char> clique_live_;
   std::vector<std::vector<int>> of_;       // cliques holding each DOF (may list dead ones)
-  std::vector<int> mark_;                  // scratch stamps for set unions
+  std::vector<int> mark_;                  // scratch: a DOF's current cell during the peel, or -1
   mutable std::vector<int> pos_;           // scratch: position of a DOF in a block's order, or -1
   mutable std::vector<int> seen_;
   mutable int stamp_ = 0;
