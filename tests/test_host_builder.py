@@ -155,13 +155,13 @@ def _check(dim, n, level, alive, cells, fronts, ref):
         assert F["pos2"] == [p2.get(g, -1) for g in allg]
 
 
-def _level1_alive(dim, n, cells0, fronts0):
+def _level1_alive(dim, n, cells0, fronts0, seed=7):
     """Level-0 interiors gone, and about 30% of every level-0 front."""
     N = (n - 1) ** dim
     dead = np.zeros(N, dtype=bool)
     for I, _ in cells0:
         dead[I] = True
-    rng = np.random.default_rng(7)
+    rng = np.random.default_rng(seed)
     for F in fronts0:
         c = np.asarray(F["c"])
         dead[c[rng.random(c.size) < 0.3]] = True
@@ -186,3 +186,15 @@ def test_builder_matches_definitions(harness, tmp_path, dim, n):
         for row, g in zip(m, I + B):
             assert row[:2 ** dim].tolist() == [p.get(g, -1) for p in pos]
             assert (row[2 ** dim:] == -1).all()
+
+
+@pytest.mark.parametrize("dim,n", [(2, 40), (3, 24)])
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_builder_level1_other_removals(harness, tmp_path, dim, n, seed):
+    """Level 1 after other pseudo-random removals of level-0 front DOFs, on
+    the grids with rounded separators."""
+    alive0 = np.arange((n - 1) ** dim, dtype=np.int64)
+    cells0, fronts0, _ = _run(harness, tmp_path, dim, n, 0, alive0)
+    alive1 = _level1_alive(dim, n, cells0, fronts0, seed=seed)
+    cells1, fronts1, _ = _run(harness, tmp_path, dim, n, 1, alive1, prev_alive=alive0)
+    _check(dim, n, 1, alive1, cells1, fronts1, _reference(dim, n, 1, alive1))
