@@ -123,14 +123,16 @@ def _read_golden(name):
 @pytest.mark.parametrize("row", [0, 1])
 def test_paper_table7_soft_pin(row):
     """Example 4 at 31^3 (Table 7 / 8): |s_L| within 10% of the paper's, e_a
-    within a factor 10 (the paper's tree details differ slightly)."""
-    eps, sL, ea_paper, _ = _read_golden("paper_table7_example4.txt")[row]
+    within a factor 10 and e_s within a factor 5 (the paper's tree details
+    differ slightly; e_s also carries kappa(A))."""
+    eps, sL, ea_paper, _, es_paper = _read_golden("paper_table7_example4.txt")[row]
     dim, n = 3, 32
     A = _problem(dim, n)
     F = hifde.factor(A, dim, n, eps)
     assert abs(len(F.root) - sL) <= 0.1 * sL
-    ea, _ = hifde.power_estimates(A, F, inputs.power_start(dim, n))
+    ea, es = hifde.power_estimates(A, F, inputs.power_start(dim, n))
     assert ea_paper / 10 <= ea <= ea_paper * 10
+    assert es_paper / 5 <= es <= es_paper * 5
 
 
 # ---- planted mistakes: the pins above must catch them ---------------------
