@@ -49,7 +49,9 @@ typedef enum hif_status {
   HIF_ERR_NOCONV = 3,    /* the iteration reached maxit; info is still filled   */
   HIF_ERR_TIMEOUT = 4,   /* a bounded device wait ran out                       */
   HIF_ERR_CUDA = 5,      /* a CUDA runtime call failed                          */
-  HIF_ERR_OOM = 6        /* device allocation failed                            */
+  HIF_ERR_OOM = 6,       /* a device or host allocation failed                  */
+  HIF_ERR_HOST = 7       /* another host-side failure (e.g. a thread could not  */
+                         /* start); hif_last_error() names it                   */
 } hif_status;
 
 /* Variants (Section 5 names): MF = mf2/mf3 (Algorithm 3.1, exact),

@@ -1589,6 +1589,21 @@ static int set_error(int code, const std::string& msg) {
   return code;
 }
 
+// Every entry point that can throw ends its try block with these handlers, so
+// that no C++ exception leaves the C ABI: the library's own errors keep their
+// status, a failed host allocation is HIF_ERR_OOM and any other host-side
+// failure (a thread that cannot start, say) is HIF_ERR_HOST.
+#define HIF_CATCH                                                                     \
+  catch (const HifError& e) {                                                         \
+    return set_error(e.code, e.msg);                                                  \
+  }                                                                                   \
+  catch (const std::bad_alloc&) {                                                     \
+    return set_error(HIF_ERR_OOM, "host allocation failed");                          \
+  }                                                                                   \
+  catch (const std::exception& e) {                                                   \
+    return set_error(HIF_ERR_HOST, std::string("host error: ") + e.what());           \
+  }
+
 int hif_factor(const hif_grid* grid, const double* a_stag, const double* b, const double* bc_vals,
                double eps, const hif_opts* opts, hif_handle** out) {
   if (!out) return set_error(HIF_ERR_ARG, "out is NULL");
@@ -1681,6 +1696,9 @@ int hif_factor(const hif_grid* grid, const double* a_stag, const double* b, cons
   } catch (const std::bad_alloc&) {
     hif_free(h);
     return set_error(HIF_ERR_OOM, "host allocation failed");
+  } catch (const std::exception& e) {
+    hif_free(h);
+    return set_error(HIF_ERR_HOST, std::string("host error: ") + e.what());
   }
   *out = h;
   g_last_error.clear();
@@ -1710,9 +1728,7 @@ int hif_apply(hif_handle* h, int mode, const double* x, double* y, int nrhs, int
     CU(cudaStreamSynchronize(st));
     if (h->profile) resolve_profile(h);
     check_dev_err(h);
-  } catch (const HifError& e) {
-    return set_error(e.code, e.msg);
-  }
+  } HIF_CATCH
   return HIF_OK;
 }
 
@@ -1754,9 +1770,7 @@ int hif_estimate(hif_handle* h, const double* x0, double rtol, int maxit, double
     *e_a = nA > 0.0 ? nE / nA : 0.0;
     *e_s = std::sqrt(nM);
     check_dev_err(h);
-  } catch (const HifError& e) {
-    return set_error(e.code, e.msg);
-  }
+  } HIF_CATCH
   return HIF_OK;
 }
 
@@ -1775,9 +1789,7 @@ int hif_matvec(hif_handle* h, const double* x, double* y, int nrhs, int ld) {
     stage_out(v.as<double>(), nrhs, ld, N, y, st, tmp);
     CU(cudaGetLastError());
     CU(cudaStreamSynchronize(st));
-  } catch (const HifError& e) {
-    return set_error(e.code, e.msg);
-  }
+  } HIF_CATCH
   return HIF_OK;
 }
 
@@ -1850,9 +1862,7 @@ int hif_solve(hif_handle* h, const double* rhs, double* x, double* x_lo, int nrh
     CU(cudaStreamSynchronize(st));
     if (h->profile) resolve_profile(h);
     check_dev_err(h);
-  } catch (const HifError& e) {
-    return set_error(e.code, e.msg);
-  }
+  } HIF_CATCH
   if (info) *info = loc;
   if (rc == HIF_ERR_NOCONV) set_error(rc, "the iteration reached maxit before tol");
   return rc;
@@ -1968,13 +1978,22 @@ static int run_batch(int nprob, int nthreads, const std::function<int(int)>& tas
         if (p < first) {
           first = p;
           first_rc = rc;
-          first_msg = g_last_error;
+          try {   // nothing may leave a thread's function
+            first_msg = g_last_error;
+          } catch (...) {
+            first_msg.clear();
+          }
         }
       }
     }
   };
   std::vector<std::thread> pool;
-  for (int t = 1; t < nthreads; ++t) pool.emplace_back(worker);
+  try {
+    for (int t = 1; t < nthreads; ++t) pool.emplace_back(worker);
+  } catch (const std::exception&) {
+    // fewer threads: the tasks are pulled from one counter, so the threads
+    // that did start (and this one) take them all
+  }
   worker();
   for (std::thread& t : pool) t.join();
   if (first_rc != HIF_OK) return set_error(first_rc, first_msg);
@@ -1986,20 +2005,24 @@ int hif_factor_batch(int nprob, const hif_grid* grids, const double* const* a_st
   if (nprob < 0 || (nprob > 0 && (!grids || !a_stag || !b || !eps || !out)))
     return set_error(HIF_ERR_ARG, "bad batch arguments");
   for (int p = 0; p < nprob; ++p) out[p] = nullptr;
-  return run_batch(nprob, nthreads, [&](int p) {
-    hif_opts o{};
-    if (opts) o = *opts;
-    o.stream = nullptr;
-    return hif_factor(&grids[p], a_stag[p], b[p], nullptr, eps[p], &o, &out[p]);
-  });
+  try {
+    return run_batch(nprob, nthreads, [&](int p) {
+      hif_opts o{};
+      if (opts) o = *opts;
+      o.stream = nullptr;
+      return hif_factor(&grids[p], a_stag[p], b[p], nullptr, eps[p], &o, &out[p]);
+    });
+  } HIF_CATCH
 }
 
 int hif_solve_batch(int nprob, hif_handle* const* hs, const double* const* rhs, double* const* x,
                     const int* nrhs, double tol, int maxit, hif_solve_info* infos, int nthreads) {
   if (nprob < 0 || (nprob > 0 && (!hs || !rhs || !x || !nrhs))) return set_error(HIF_ERR_ARG, "bad batch arguments");
-  return run_batch(nprob, nthreads, [&](int p) {
-    return hif_solve(hs[p], rhs[p], x[p], nullptr, nrhs[p], nrhs[p], tol, maxit, infos ? &infos[p] : nullptr);
-  });
+  try {
+    return run_batch(nprob, nthreads, [&](int p) {
+      return hif_solve(hs[p], rhs[p], x[p], nullptr, nrhs[p], nrhs[p], tol, maxit, infos ? &infos[p] : nullptr);
+    });
+  } HIF_CATCH
 }
 
 int hif_front_log(const hif_handle* h, float* feats, int32_t* ranks, int32_t* sizes, long long cap,
@@ -2022,9 +2045,7 @@ int hif_front_log(const hif_handle* h, float* feats, int32_t* ranks, int32_t* si
       p += (long long)m;
     }
     CU(cudaStreamSynchronize(h->st));
-  } catch (const HifError& e) {
-    return set_error(e.code, e.msg);
-  }
+  } HIF_CATCH
   return HIF_OK;
 }
 
@@ -2040,9 +2061,7 @@ int hif_mlp_grad(const float* X, const float* target, int n, const float* params
     mlp_grad(X, target, nullptr, n, 1.0f / n, params, partial.as<float>(), ploss.as<float>(), grad, loss, st);
     CU(cudaGetLastError());
     CU(cudaStreamSynchronize(st));
-  } catch (const HifError& e) {
-    return set_error(e.code, e.msg);
-  }
+  } HIF_CATCH
   return HIF_OK;
 }
 
@@ -2090,9 +2109,7 @@ int hif_mlp_train(const float* X, const float* target, int n, float* params, int
       CU(cudaMemcpyAsync(loss_hist, lossd.p, sizeof(float) * steps, cudaMemcpyDeviceToDevice, st));
     CU(cudaGetLastError());
     CU(cudaStreamSynchronize(st));
-  } catch (const HifError& e) {
-    return set_error(e.code, e.msg);
-  }
+  } HIF_CATCH
   return HIF_OK;
 }
 
@@ -2113,9 +2130,7 @@ int hif_schur_update_f32(int nb, int m, int k, const float* G, float* U, int spl
     CU(cudaMemcpyAsync(&hs, status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
     if (hs & 32) throw HifError(HIF_ERR_TIMEOUT, "a bounded wait for tensor-core MMAs ran out");
-  } catch (const HifError& e) {
-    return set_error(e.code, e.msg);
-  }
+  } HIF_CATCH
   return HIF_OK;
 }
 
@@ -2129,9 +2144,7 @@ int hif_mlp_predict(const float* X, int n, const float* params, float* y, void* 
     mlp_predict(X, n, w.p, y, st);
     CU(cudaGetLastError());
     CU(cudaStreamSynchronize(st));
-  } catch (const HifError& e) {
-    return set_error(e.code, e.msg);
-  }
+  } HIF_CATCH
   return HIF_OK;
 }
 

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <atomic>
 #include <condition_variable>
+#include <exception>
 #include <mutex>
 #include <thread>
 #include <vector>
@@ -13,16 +14,27 @@ namespace {
 
 // One parallel_tasks call: lives on the caller's stack; a worker touches it
 // only while registered (users > 0), and the caller returns only after every
-// task has run and every registered worker has left.
+// task has run and every registered worker has left.  A task that throws
+// still counts as run; the first exception is kept and rethrown to the
+// caller once the job is over.
 struct Job {
   const std::function<void(int)>* fn;
   int ntasks;
+  std::mutex* m;   // the pool mutex
   std::atomic<int> next{0};
   int done = 0;    // tasks finished (guarded by the pool mutex)
   int users = 0;   // workers registered on the job (guarded by the pool mutex)
+  std::exception_ptr error;   // first exception of a task (guarded by the pool mutex)
   int run_some() {
     int mine = 0;
-    for (int t; (t = next.fetch_add(1)) < ntasks; ++mine) (*fn)(t);
+    for (int t; (t = next.fetch_add(1)) < ntasks; ++mine) {
+      try {
+        (*fn)(t);
+      } catch (...) {
+        std::lock_guard<std::mutex> g(*m);
+        if (!error) error = std::current_exception();
+      }
+    }
     return mine;
   }
 };
@@ -30,7 +42,11 @@ struct Job {
 class Pool {
  public:
   explicit Pool(int nthreads) {
-    for (int i = 1; i < nthreads; ++i) workers_.emplace_back([this] { work(); });
+    try {
+      for (int i = 1; i < nthreads; ++i) workers_.emplace_back([this] { work(); });
+    } catch (const std::exception&) {
+      // a thread that cannot start: the pool runs with those that did
+    }
   }
   int size() const { return (int)workers_.size() + 1; }
 
@@ -43,6 +59,7 @@ class Pool {
     Job j;
     j.fn = &fn;
     j.ntasks = ntasks;
+    j.m = &m_;
     {
       std::lock_guard<std::mutex> g(m_);
       cur_ = &j;
@@ -54,6 +71,7 @@ class Pool {
     j.done += mine;
     cur_ = nullptr;   // late wakers find no job
     cv_done_.wait(lk, [&] { return j.done == j.ntasks && j.users == 0; });
+    if (j.error) std::rethrow_exception(j.error);
   }
 
  private:

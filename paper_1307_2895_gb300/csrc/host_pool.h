@@ -13,7 +13,8 @@ namespace hif {
 int host_threads();
 
 // fn(t) for t = 0 .. ntasks-1, each exactly once, in any order and on any of
-// the pool's threads; returns when all have returned.
+// the pool's threads; returns when all have returned.  If tasks throw, the
+// others still run and the first exception is rethrown here afterwards.
 void parallel_tasks(int ntasks, const std::function<void(int)>& fn);
 
 // Tasks for `work` items: about one per `grain` items, at most host_threads().

@@ -16,7 +16,7 @@ import numpy as np
 
 from . import build as _build
 
-HIF_OK, HIF_ERR_ARG, HIF_ERR_NOT_SPD, HIF_ERR_NOCONV, HIF_ERR_TIMEOUT, HIF_ERR_CUDA, HIF_ERR_OOM = range(7)
+HIF_OK, HIF_ERR_ARG, HIF_ERR_NOT_SPD, HIF_ERR_NOCONV, HIF_ERR_TIMEOUT, HIF_ERR_CUDA, HIF_ERR_OOM, HIF_ERR_HOST = range(8)
 VARIANTS = {"mf": 0, "hifde": 1}
 ID_MODES = {"qr": 0, "rand": 1, "learned": 2}
 MLP_FEATURES, MLP_PARAMS = 10, 4929
