@@ -114,19 +114,40 @@ static inline void for_each_coupled(int i, int n, bool implicit, const std::vect
 std::vector<int> Symbolic3x::neighbors(const std::vector<int>& c) const {
   if (stamp_ > INT_MAX - 4) {
     std::fill(seen_.begin(), seen_.end(), 0);
+    std::fill(clique_seen_.begin(), clique_seen_.end(), 0);
     stamp_ = 0;
   }
   stamp_ += 2;
   const int in_c = stamp_ - 1, in_out = stamp_;
   for (int i : c) seen_[i] = in_c;
   std::vector<int> out;
-  for (int i : c)
-    for_each_coupled(i, n_, implicit_, active_, clique_, of_, [&](int j) {
-      if (seen_[j] != in_c && seen_[j] != in_out) {
-        seen_[j] = in_out;
-        out.push_back(j);
+  auto add = [&](int j) {
+    if (seen_[j] != in_c && seen_[j] != in_out) {
+      seen_[j] = in_out;
+      out.push_back(j);
+    }
+  };
+  if (implicit_) {
+    const int e = n_ - 1;
+    const int step[3] = {1, e, e * e};
+    for (int i : c) {
+      const int x[3] = {i % e, (i / e) % e, i / (e * e)};
+      for (int a = 0; a < 3; ++a) {
+        if (x[a] > 0 && active_[i - step[a]]) add(i - step[a]);
+        if (x[a] < e - 1 && active_[i + step[a]]) add(i + step[a]);
       }
-    });
+    }
+  }
+  // every clique touching c once (a clique holds many members of c)
+  for (int i : c)
+    for (int id : of_[i]) {
+      if (clique_seen_[id] == in_out) continue;
+      clique_seen_[id] = in_out;
+      const std::vector<int>& m = clique_[id];
+      if (m.size() < 2) continue;
+      for (int j : m)
+        if (active_[j]) add(j);
+    }
   std::sort(out.begin(), out.end());
   return out;
 }
@@ -238,6 +259,7 @@ int Symbolic3x::add_clique(const std::vector<int>& members) {
   const int id = (int)clique_.size();
   clique_.push_back(members);
   clique_live_.push_back(members.empty() ? 0 : 1);
+  clique_seen_.push_back(0);
   for (int i : members) of_[i].push_back(id);
   return id;
 }

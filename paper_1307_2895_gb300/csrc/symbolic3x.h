@@ -121,6 +121,7 @@ class Symbolic3x {
   std::vector<int> mark_;                  // scratch: a DOF's current cell during the peel, or -1
   mutable std::vector<int> pos_;           // scratch: position of a DOF in a block's order, or -1
   mutable std::vector<int> seen_;
+  mutable std::vector<int> clique_seen_;   // scratch stamps per clique
   mutable int stamp_ = 0;
 };
 
