@@ -88,29 +88,6 @@ bool Symbolic3x::voronoi(int g, const std::vector<std::vector<int>>* fams, int n
   return nbest == 1 && !best_tie;
 }
 
-// Calls fn(j) for every active DOF j coupled to i (possibly more than once;
-// j == i may appear).
-template <typename Fn>
-static inline void for_each_coupled(int i, int n, bool implicit, const std::vector<char>& active,
-                                    const std::vector<std::vector<int>>& clique,
-                                    const std::vector<std::vector<int>>& of, Fn&& fn) {
-  if (implicit) {
-    const int e = n - 1;
-    const int x[3] = {i % e, (i / e) % e, i / (e * e)};
-    const int step[3] = {1, e, e * e};
-    for (int a = 0; a < 3; ++a) {
-      if (x[a] > 0 && active[i - step[a]]) fn(i - step[a]);
-      if (x[a] < e - 1 && active[i + step[a]]) fn(i + step[a]);
-    }
-  }
-  for (int id : of[i]) {
-    const std::vector<int>& c = clique[id];
-    if (c.size() < 2) continue;
-    for (int j : c)
-      if (active[j]) fn(j);
-  }
-}
-
 std::vector<int> Symbolic3x::neighbors(const std::vector<int>& c) const {
   if (stamp_ > INT_MAX - 4) {
     std::fill(seen_.begin(), seen_.end(), 0);
@@ -186,15 +163,45 @@ std::vector<std::vector<int>> Symbolic3x::cells(int l) {
         mark_[act[r]] = lin[r];
       }
   }
+  // Only a clique whose members start in two or more cells can make a DOF
+  // leave (the peel only takes members away): mark those once.
+  std::vector<char> mixed(clique_.size(), 0);
+  for (size_t id = 0; id < clique_.size(); ++id) {
+    int first = -1;
+    for (int j : clique_[id]) {
+      const int cj = mark_[j];
+      if (cj < 0) continue;
+      if (first < 0) {
+        first = cj;
+      } else if (cj != first) {
+        mixed[id] = 1;
+        break;
+      }
+    }
+  }
   // peel, cell by cell: a DOF coupled to a current member of another cell leaves
+  const int e = n_ - 1;
+  const int step[3] = {1, e, e * e};
   for (int c = 0; c < nc; ++c) {
     std::vector<int> keep;
     for (int s = start[c]; s < start[c + 1]; ++s) {
       const int i = members[s];
       bool ext = false;
-      for_each_coupled(i, n_, implicit_, active_, clique_, of_, [&](int j) {
-        if (mark_[j] >= 0 && mark_[j] != c) ext = true;
-      });
+      auto other = [&](int j) { return active_[j] && mark_[j] >= 0 && mark_[j] != c; };
+      if (implicit_) {
+        const int x[3] = {i % e, (i / e) % e, i / (e * e)};
+        for (int a = 0; a < 3 && !ext; ++a)
+          ext = (x[a] > 0 && other(i - step[a])) || (x[a] < e - 1 && other(i + step[a]));
+      }
+      for (size_t k = 0; k < of_[i].size() && !ext; ++k) {
+        const int id = of_[i][k];
+        if (!mixed[id]) continue;
+        for (int j : clique_[id])
+          if (other(j)) {
+            ext = true;
+            break;
+          }
+      }
       if (ext)
         mark_[i] = -1;
       else
