@@ -90,7 +90,7 @@ void build_cells(const Geometry& G, int l, const std::vector<int>& alive, std::v
   // those of the tasks before it, so I and B come out ascending, exactly as
   // one pass over alive would make them.
   const int64_t na = (int64_t)alive.size();
-  const int T = task_count(na, 16384);
+  const int T = task_count(na, 4096);
   std::vector<std::vector<int>> nI(T, std::vector<int>(ncells, 0)), nB(T, std::vector<int>(ncells, 0));
   auto each = [&](int t, auto&& on_interior, auto&& on_boundary) {
     int64_t lo, hi;
@@ -194,7 +194,7 @@ void build_fronts(const Geometry& G, int l, const std::vector<int>& alive,
   // As in build_cells: contiguous ranges of alive per task, positions
   // assigned in task order, so every F.c is ascending.
   const int64_t na = (int64_t)alive.size();
-  const int T = task_count(na, 16384);
+  const int T = task_count(na, 4096);
   std::vector<std::vector<int>> cnt(T, std::vector<int>(nslot, 0));
   parallel_tasks(T, [&](int t) {
     int64_t lo, hi;
