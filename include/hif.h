@@ -79,9 +79,11 @@ typedef struct hif_grid {
 
 /* ID modes (Section 4.3): the pivoted-QR ID of A_{N,c}; or an ID of the
  * Gaussian sketch Phi A_{N,c} with ell = k_hat + oversample rows, accepted only
- * if ||A_r - A_s T||_F <= eps ||A||_F and k < ell (else the pivoted-QR ID of
- * A_{N,c}), with k_hat = ceil(|c|/2) (RAND) or predicted per front by the
- * rank MLP (LEARNED, opts.rank_model required). */
+ * if every column of the residual A_{N,r} - A_{N,s} T has 2-norm at most
+ * eps times the largest column 2-norm of A_{N,c} (the quantities the
+ * pivoted QR's stopping rule compares, Section 2.2) and k < ell (else the
+ * pivoted-QR ID of A_{N,c}), with k_hat = ceil(|c|/2) (RAND) or predicted per
+ * front by the rank MLP (LEARNED, opts.rank_model required). */
 enum { HIF_ID_QR = 0, HIF_ID_RAND = 1, HIF_ID_LEARNED = 2 };
 
 typedef struct hif_opts {
@@ -315,9 +317,10 @@ long long hif_kernel_launches(void);
  * The paper has no counterpart: this serves callers that cannot call
  * cudaMalloc where they check a solution (inside another library's allocator
  * callback or memory-managed region, or where an allocation must not
- * synchronize the device).  All pointers are device pointers: a_stag, b as
- * for hif_factor; f and x are N x nrhs with row stride ld; rnorm2 receives
- * nrhs doubles.  Work is queued on stream (a cudaStream_t, NULL = legacy
+ * synchronize the device).  All pointers must be device (or managed) memory:
+ * a_stag, b as for hif_factor; f and x are N x nrhs with row stride ld;
+ * rnorm2 receives nrhs doubles.  Nothing is staged: a pointer the CUDA
+ * runtime does not report as device or managed memory gives HIF_ERR_ARG.  Work is queued on stream (a cudaStream_t, NULL = legacy
  * default stream); the call returns once the kernels are queued.
  * Limits: 1 <= nrhs <= 16 per call (HIF_ERR_ARG otherwise).  The reduction
  * scratch is one fixed 38 KB device array of the library, held by every GPU

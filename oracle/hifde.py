@@ -384,6 +384,8 @@ class Factor:
     root: np.ndarray           # s_L (ascending)
     D: np.ndarray              # A_L restricted to s_L
     Dchol: np.ndarray          # its Cholesky factor
+    sketched: int = 0          # fronts whose sketched ID passed the check
+    fallback: int = 0          # fronts whose sketched ID failed it
 
     # ---- Eq. (4.2): F^-1 = V_0 V_1/2 ... D^-1 ... V_1/2^T V_0^T
     def apply_inverse(self, b: np.ndarray) -> np.ndarray:
@@ -441,7 +443,7 @@ def _front_key(dim, x, on_sep, seps):
 
 
 def factor(A_csr, dim: int, n: int, eps: float, leaf: int = 8,
-           skip_levels: int = 0) -> Factor:
+           skip_levels: int = 0, sketch=None) -> Factor:
     """Algorithm 4.1 (HIF-DE; ``eps > 0``) or Algorithm 3.1 (MF; ``eps == 0``).
 
     Level l: eliminate the active DOFs strictly inside each level-l cell
@@ -449,12 +451,21 @@ def factor(A_csr, dim: int, n: int, eps: float, leaf: int = 8,
     (skipped when ``eps == 0`` or ``l < skip_levels``): group the active DOFs
     with exactly one coordinate on a level-l separator by front (2D edge or
     3D face interior), compute every front's ID from ``A_{l+1/2}``, then
-    skeletonize the fronts (Lemma 2.4).  Finally ``D = A_L`` on ``s_L``."""
+    skeletonize the fronts (Lemma 2.4).  Finally ``D = A_L`` on ``s_L``.
+
+    ``sketch`` (optional) supplies the random numbers of the randomized ID
+    (Section 4.3): ``sketch(l, c, rows)`` returns the Gaussian sampling
+    matrix for front ``c`` (ascending DOF ids) whose ID block has the rows
+    ``rows`` (ascending DOF ids), or None to use the pivoted-QR ID.  A
+    sketched ID that fails :func:`oracle.learned.randomized_id`'s check falls
+    back to the pivoted-QR ID of the block itself.  The counts of accepted
+    and rejected sketches are kept on the result."""
     from .stencil import coords as _coords
     A = ActiveMatrix(A_csr)
     X = _coords(dim, n)
     L = tree_levels(n, leaf)
     levels: List[Level] = []
+    n_sketched = n_fallback = 0
     for ell in range(L):
         seps = level_separators(n, L, ell)
         act = np.array(A.active(), dtype=np.int64)
@@ -490,14 +501,29 @@ def factor(A_csr, dim: int, n: int, eps: float, leaf: int = 8,
             for key in keys:                           # all IDs from A_{l+1/2}
                 c = sorted(groups[key])
                 nb = A.neighbors(c)
-                ids.append(interp_decomp(A.block(nb, c), eps))
+                M = A.block(nb, c)
+                Phi = sketch(ell, c, nb) if sketch is not None else None
+                idr = None
+                if Phi is not None:
+                    from .learned import randomized_id
+                    ids_s, ok = randomized_id(M, eps, Phi)
+                    if ok:
+                        idr = ids_s
+                        n_sketched += 1
+                    else:
+                        n_fallback += 1
+                if idr is None:
+                    idr = interp_decomp(M, eps)
+                    if Phi is not None and ids_s.near_threshold:
+                        idr = dataclasses.replace(idr, near_threshold=True)
+                ids.append(idr)
             for key, idr in zip(keys, ids):
                 fronts.append(skeletonize(A, sorted(groups[key]), idr))
         levels.append(Level(ell, cells, fronts, keys))
     root = np.array(A.active(), dtype=np.int64)
     D = A.block(root.tolist(), root.tolist())
     Dchol = np.linalg.cholesky(D) if len(root) else np.zeros((0, 0))
-    return Factor(dim, n, L, eps, levels, root, D, Dchol)
+    return Factor(dim, n, L, eps, levels, root, D, Dchol, n_sketched, n_fallback)
 
 
 # --------------------------------------------------------------------------

@@ -23,6 +23,8 @@ interpolate to rounding) and by its fallback on an undersized sketch.
 """
 from __future__ import annotations
 
+import dataclasses
+
 import numpy as np
 
 from .hifde import interp_decomp
@@ -33,13 +35,19 @@ HUBER_DELTA = 1.0
 def randomized_id(M: np.ndarray, eps: float, Phi: np.ndarray):
     """ID of M from the sketch Y = Phi M.  Returns (IDResult, ok) where ok says
     the residual check passed (column norms, see the module docstring) and the
-    sketch was not saturated (k < ell)."""
+    sketch was not saturated (k < ell).  The result's near_threshold flag is
+    also set when the largest residual column norm lies within 1e-8
+    (relative) of the acceptance bound, a decision that rounding order could
+    flip."""
     Y = Phi @ M
     idr = interp_decomp(Y, eps)
     k, ell = len(idr.sk), Phi.shape[0]
     E = M[:, idr.rd] - M[:, idr.sk] @ idr.T
     e = np.linalg.norm(E, axis=0).max() if E.size else 0.0
-    ok = bool(k < ell and e <= eps * np.linalg.norm(M, axis=0).max())
+    bound = eps * np.linalg.norm(M, axis=0).max()
+    ok = bool(k < ell and e <= bound)
+    if k < ell and abs(e - bound) <= 1e-8 * bound:
+        idr = dataclasses.replace(idr, near_threshold=True)
     return idr, ok
 
 

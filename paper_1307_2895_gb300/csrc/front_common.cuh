@@ -123,22 +123,25 @@ __device__ void blk_id_T(const T* A, int m, const int* perm, int k, int nc, T* T
   __syncthreads();
 }
 
-// Standard normal from two splitmix64 outputs of a counter (Box-Muller).
-__device__ __forceinline__ uint64_t smix64(uint64_t z) {
-  z += 0x9E3779B97F4A7C15ull;
+// splitmix64 (Steele, Lea and Flood, 2014): output number c >= 1 of the
+// stream seeded with s is the mixing function of the state s + c * gamma.
+__device__ __forceinline__ uint64_t smix_at(uint64_t s, uint64_t c) {
+  uint64_t z = s + c * 0x9E3779B97F4A7C15ull;
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
   return z ^ (z >> 31);
 }
-__device__ __forceinline__ float gauss01(uint64_t key) {
-  const uint64_t a = smix64(key * 2), b = smix64(key * 2 + 1);
-  const float u1 = ((float)(a >> 40) + 0.5f) * (1.0f / 16777216.0f);
-  const float u2 = (float)(b >> 40) * (1.0f / 16777216.0f);
-  return sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+// Standard normal number e of the stream seeded with key: Box-Muller (cosine
+// branch) of u1 = 1 - U(2e + 1) in (0, 1] and u2 = U(2e + 2), U(c) the top 53
+// bits of output c over 2^53.
+__device__ __forceinline__ double sketch_normal(uint64_t key, uint64_t e) {
+  const double u1 = 1.0 - (double)(smix_at(key, 2 * e + 1) >> 11) * 0x1p-53;
+  const double u2 = (double)(smix_at(key, 2 * e + 2) >> 11) * 0x1p-53;
+  return sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
 }
-
-
-// Key of front f's Gaussian stream at one fractional level.
-__device__ __forceinline__ uint64_t sketch_key(uint64_t seed, int f) { return smix64(seed ^ ((uint64_t)f << 32)); }
+// Key of the front whose smallest DOF id is c0 (see SketchStream).
+__device__ __forceinline__ uint64_t sketch_key(const SketchStream& ss, int c0) {
+  return smix_at(ss.seed, ss.level_base + (uint64_t)c0 + 1);
+}
 
 }  // namespace hif

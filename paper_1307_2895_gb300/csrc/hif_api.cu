@@ -337,6 +337,7 @@ void prepare_fronts(const std::vector<HostFront>& fr, std::vector<FrontDesc>& fd
     ip.insert(ip.end(), F.c.begin(), F.c.end());
     ip.insert(ip.end(), F.pos1.begin(), F.pos1.end());
     ip.insert(ip.end(), F.pos2.begin(), F.pos2.end());
+    ip.insert(ip.end(), F.N.begin(), F.N.end());
     d.out = out_elems;
     out_elems += 1 + 2 * d.nc;
     d.work = work_elems;
@@ -640,7 +641,7 @@ struct Factorizer {
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
     CU(cudaEventRecord(e0, st));
-    const uint64_t seed = h->seed * 0x9E3779B97F4A7C15ull + (uint64_t)l;
+    const SketchStream ss{(uint64_t)h->seed, (uint64_t)l * (uint64_t)G.N, (uint64_t)G.N};
     // fronts with at least max(big_cell, kBigFrontMin) DOFs: the multi-block
     // skeletonization (its elimination scratch needs |c|^2 >= cell_x_elems(|c|))
     const int big_front = std::max(h->big_cell, kBigFrontMin);
@@ -661,7 +662,7 @@ struct Factorizer {
     const int ne = nbig ? bigfront_resid_strips(big_nc) : 0;
     if (big.empty()) {
       launch_front<T>(d_fd, nf, d_cdesc, d_ip, obuf.as<int>(), fwork.as<T>(), sw.fac.as<T>(), cwork.as<T>(), h->eps,
-                      status.as<int>(), max_nc, max_nN, tau, sketch.as<int>(), seed, nullptr, st);
+                      status.as<int>(), max_nc, max_nN, tau, sketch.as<int>(), ss, nullptr, st);
     } else {
       if (!small.empty()) {
         upload(d_sel, small, st);
@@ -671,7 +672,7 @@ struct Factorizer {
           snN = std::max(snN, fd[f].nN);
         }
         launch_front<T>(d_fd, (int)small.size(), d_cdesc, d_ip, obuf.as<int>(), fwork.as<T>(), sw.fac.as<T>(),
-                        cwork.as<T>(), h->eps, status.as<int>(), snc, snN, tau, sketch.as<int>(), seed,
+                        cwork.as<T>(), h->eps, status.as<int>(), snc, snN, tau, sketch.as<int>(), ss,
                         d_sel.as<int>(), st);
       }
       upload(d_big, big, st);
@@ -684,7 +685,7 @@ struct Factorizer {
         bnN[b] = fd[big[b]].nN;
       }
       launch_bigfront_id<T>(d_fd, d_big.as<int>(), nbig, d_cdesc, d_ip, cwork.as<T>(), fwork.as<T>(), sw.fac.as<T>(),
-                            obuf.as<int>(), sketch.as<int>(), seed, h->eps, status.as<int>(), bstate.as<int>(),
+                            obuf.as<int>(), sketch.as<int>(), ss, h->eps, status.as<int>(), bstate.as<int>(),
                             m2part.as<double>(), nm, e2part.as<double>(), ne, big_nc, big_nN,
                             sketch.p ? big_nc : 0, bnc.data(), bnN.data(), h->coop_qr, st);
     }

@@ -33,7 +33,7 @@ struct CellDesc {
 struct FrontDesc {
   int nc, nN;          // |c| and |c^N|
   int P1, P2;          // adjacent cells (indices into the level's cell array)
-  int64_t ids;         // int pool: ids_c[nc] | pos1[nc+nN] | pos2[nc+nN]  (c first, then N)
+  int64_t ids;         // int pool: ids_c[nc] | pos1[nc+nN] | pos2[nc+nN] (c first, then N) | ids_N[nN]
   int64_t work;        // work pool: M[nN*nc] (column-major) | A_cc[nc*nc] | 3 scratch nc*nc
   int64_t fac;         // factor pool (capacity for nc): Linv (packed) | G | T | L (packed)
   int64_t out;         // output buffer: k | perm[nc] | ids_sr[nc]
@@ -60,6 +60,19 @@ struct ApplyDesc {
   int np, nq;
   int64_t ids;         // int pool: ids_p[np] then ids_q[nq]
   int64_t Linv, L, G, T;   // factor pool offsets (T = -1 for cells)
+};
+
+// Gaussian stream of the randomized ID (Section 4.3) at one fractional level
+// l: front c's sketch matrix is Phi[r][j] = normal(key_c, r * nglob + j) for
+// sketch row r and global DOF id j of a row of A_{N,c}, with key_c the
+// splitmix64 output number level_base + c_0 + 1 of the stream seeded with
+// `seed` (level_base = l * nglob, c_0 = the front's smallest DOF id, nglob =
+// N) and normal(key, e) the Box-Muller cosine branch, in FP64, of the
+// uniforms (top 53 bits) of outputs 2e + 1 and 2e + 2 of the stream seeded
+// with key.  Indexed by DOF ids, so Phi A_{N,c} does not depend on the order
+// of N or on rows that are structurally zero.
+struct SketchStream {
+  uint64_t seed, level_base, nglob;
 };
 
 // Rank-prediction MLP: kFeat input features per front, hidden width kHid.

@@ -61,7 +61,7 @@ template <typename T>
 void launch_front(const FrontDesc* fronts, int nfronts, const CellDesc* cells, const int* ipool, int* obuf,
                   T* fwork,
                   T* fac, T* cwork, double eps, int* status, int max_nc, int max_nN, double tau,
-                  const int* sketch, uint64_t seed, const int* sel, cudaStream_t st);
+                  const int* sketch, SketchStream ss, const int* sel, cudaStream_t st);
 
 // skeletonization of large fronts (kernels_bigfront.cu): the ID (writes T
 // and the front's outputs; h_nc / h_nN: host copies of the fronts' sizes, for
@@ -70,7 +70,7 @@ void launch_front(const FrontDesc* fronts, int nfronts, const CellDesc* cells, c
 // tiled elimination the B_ss scatter.
 template <typename T>
 void launch_bigfront_id(const FrontDesc* fronts, const int* big, int nbig, const CellDesc* cells, const int* ipool,
-                        const T* cwork, T* fwork, T* fac, int* obuf, const int* sketch, uint64_t seed, double eps,
+                        const T* cwork, T* fwork, T* fac, int* obuf, const int* sketch, SketchStream ss, double eps,
                         int* status, int* state, double* m2part, int nm, double* e2part, int ne, int max_nc,
                         int max_nN, int max_ell, const int* h_nc, const int* h_nN, bool coop_ok, cudaStream_t st);
 template <typename T>

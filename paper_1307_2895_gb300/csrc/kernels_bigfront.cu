@@ -114,11 +114,11 @@ __global__ void k_bf_colmax(const FrontDesc* __restrict__ fronts, const int* __r
   }
 }
 
-// ---- sketch: Y = Phi M (ell x nc), Phi_{r,i} = gauss01(key_f + r nN + i)
+// ---- sketch: Y = Phi M (ell x nc), Phi from the front's stream (SketchStream)
 template <typename T>
 __global__ void __launch_bounds__(TT) k_bf_sketch(const FrontDesc* __restrict__ fronts, const int* __restrict__ big,
-                                                  const int* __restrict__ sketch, T* __restrict__ fwork,
-                                                  uint64_t seed) {
+                                                  const int* __restrict__ sketch, const int* __restrict__ ipool,
+                                                  T* __restrict__ fwork, SketchStream ss) {
   __shared__ TileSmem<T> sm;
   const int f = big[blockIdx.y];
   const FrontDesc fd = fronts[f];
@@ -129,7 +129,9 @@ __global__ void __launch_bounds__(TT) k_bf_sketch(const FrontDesc* __restrict__ 
   const int tcn = (nc + TB - 1) / TB;
   if ((int)blockIdx.x >= ((ell + TB - 1) / TB) * tcn) return;
   const int r0 = (blockIdx.x / tcn) * TB, c0 = (blockIdx.x % tcn) * TB;
-  const uint64_t key0 = sketch_key(seed, f);
+  const int* idc = ipool + fd.ids;
+  const int* idN = idc + nc + 2 * (nc + nN);     // global ids of the rows of M
+  const uint64_t key0 = sketch_key(ss, idc[0]);
   const T* M = fwork + v.M;
   T* Y = fwork + v.Y;
   T acc[4][4];
@@ -137,7 +139,7 @@ __global__ void __launch_bounds__(TT) k_bf_sketch(const FrontDesc* __restrict__ 
   tile_mma<T, true>(
       sm, acc, nN,
       [&](int r, int k) {
-        return (r0 + r < ell) ? (T)gauss01(key0 + (uint64_t)(r0 + r) * (uint64_t)nN + (uint64_t)k) : T(0);
+        return (r0 + r < ell) ? (T)sketch_normal(key0, (uint64_t)(r0 + r) * ss.nglob + (uint64_t)idN[k]) : T(0);
       },
       [&](int k, int c) { return (c0 + c < nc) ? M[(int64_t)(c0 + c) * nN + k] : T(0); });
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -603,7 +605,7 @@ static int chunk_blocks(int64_t n, int cap) {
 
 template <typename T>
 void launch_bigfront_id(const FrontDesc* fronts, const int* big, int nbig, const CellDesc* cells, const int* ipool,
-                        const T* cwork, T* fwork, T* fac, int* obuf, const int* sketch, uint64_t seed, double eps,
+                        const T* cwork, T* fwork, T* fac, int* obuf, const int* sketch, SketchStream ss, double eps,
                         int* status, int* state, double* m2part, int nm, double* e2part, int ne, int max_nc,
                         int max_nN, int max_ell, const int* h_nc, const int* h_nN, bool coop_ok, cudaStream_t st) {
   if (nbig == 0) return;
@@ -616,7 +618,7 @@ void launch_bigfront_id(const FrontDesc* fronts, const int* big, int nbig, const
     k_bf_colmax<T><<<dim3(nm, nbig), 256, 0, st>>>(fronts, big, fwork, m2part);
     ++nl;
     const int tiles = ((max_ell + TB - 1) / TB) * ((max_nc + TB - 1) / TB);
-    k_bf_sketch<T><<<dim3(tiles, nbig), TT, 0, st>>>(fronts, big, sketch, fwork, seed);
+    k_bf_sketch<T><<<dim3(tiles, nbig), TT, 0, st>>>(fronts, big, sketch, ipool, fwork, ss);
     ++nl;
   }
   const int smem = (int)(sizeof(double) * (max_nc + max_nN) + sizeof(int) * 2 * max_nc + 64);
@@ -750,7 +752,7 @@ int bigfront_resid_strips(int max_nc) { return (max_nc + TB - 1) / TB; }
 
 #define HIF_BF_INST(T)                                                                                          \
   template void launch_bigfront_id<T>(const FrontDesc*, const int*, int, const CellDesc*, const int*, const T*, \
-                                      T*, T*, int*, const int*, uint64_t, double, int*, int*, double*, int,     \
+                                      T*, T*, int*, const int*, SketchStream, double, int*, int*, double*, int, \
                                       double*, int, int, int, int, const int*, const int*, bool, cudaStream_t); \
   template void launch_bigfront_form<T>(const FrontDesc*, const int*, int, const int*, T*, const T*, int, int,  \
                                         cudaStream_t);                                                           \

@@ -204,7 +204,7 @@ template <typename T>
 __global__ void k_front(const FrontDesc* __restrict__ fronts, const CellDesc* __restrict__ cells,
                         const int* __restrict__ ipool, int* __restrict__ obuf, T* __restrict__ fwork,
                         T* __restrict__ fac, T* __restrict__ cwork, double eps, int* status, T tau,
-                        const int* __restrict__ sketch, uint64_t seed, const int* __restrict__ sel) {
+                        const int* __restrict__ sketch, SketchStream ss, const int* __restrict__ sel) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int fi = sel ? sel[blockIdx.x] : (int)blockIdx.x;
   const FrontDesc fd = fronts[fi];
@@ -254,8 +254,12 @@ __global__ void k_front(const FrontDesc* __restrict__ fronts, const CellDesc* __
   const int ell = sketch ? sketch[fi] : 0;
   int k = -1;
   if (ell > 0 && ell < nc && ell < nN) {
-    const uint64_t key0 = sketch_key(seed, fi);
-    for (int64_t e = threadIdx.x; e < (int64_t)ell * nN; e += blockDim.x) PH[e] = (T)gauss01(key0 + (uint64_t)e);
+    const uint64_t key0 = sketch_key(ss, idc[0]);
+    const int* idN = pos2 + nc + nN;       // global ids of the rows of A_{N,c}
+    for (int64_t e = threadIdx.x; e < (int64_t)ell * nN; e += blockDim.x) {
+      const int r = (int)(e / nN), i = (int)(e % nN);
+      PH[e] = (T)sketch_normal(key0, (uint64_t)r * ss.nglob + (uint64_t)idN[i]);
+    }
     __syncthreads();
     T* Y = S3;                             // ell x nc, column-major (ld ell)
     for (int64_t e = threadIdx.x; e < (int64_t)ell * nc; e += blockDim.x) {
@@ -424,14 +428,14 @@ template <typename T>
 void launch_front(const FrontDesc* fronts, int nfronts, const CellDesc* cells, const int* ipool, int* obuf,
                   T* fwork,
                   T* fac, T* cwork, double eps, int* status, int max_nc, int max_nN, double tau,
-                  const int* sketch, uint64_t seed, const int* sel, cudaStream_t st) {
+                  const int* sketch, SketchStream ss, const int* sel, cudaStream_t st) {
   if (nfronts == 0) return;
   const int smem = (int)(sizeof(double) * (max_nc + max_nN) + sizeof(int) * 2 * max_nc + 64);
   if (smem > 48 * 1024)
     raise_smem_limit(k_front<T>);
   note_launches(1);
   k_front<T><<<nfronts, 256, smem, st>>>(fronts, cells, ipool, obuf, fwork, fac, cwork, eps, status, (T)tau,
-                                         sketch, seed, sel);
+                                         sketch, ss, sel);
 }
 
 template void launch_leaf_assemble<double>(const CellDesc*, int, const int*, double*, GridInfo,
@@ -449,10 +453,10 @@ template void launch_cell_factor<double>(const CellDesc*, const int*, int, doubl
 template void launch_cell_factor<float>(const CellDesc*, const int*, int, float*, float*, int*, int, double,
                                         cudaStream_t);
 template void launch_front<double>(const FrontDesc*, int, const CellDesc*, const int*, int*, double*, double*,
-                                   double*, double, int*, int, int, double, const int*, uint64_t, const int*,
+                                   double*, double, int*, int, int, double, const int*, SketchStream, const int*,
                                    cudaStream_t);
 template void launch_front<float>(const FrontDesc*, int, const CellDesc*, const int*, int*, float*, float*,
-                                  float*, double, int*, int, int, double, const int*, uint64_t, const int*,
+                                  float*, double, int*, int, int, double, const int*, SketchStream, const int*,
                                   cudaStream_t);
 
 // ---------------------------------------------------------------------------

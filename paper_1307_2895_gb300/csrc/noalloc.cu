@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstdio>
 #include <mutex>
 
 #include "../../include/hif.h"
@@ -124,6 +125,18 @@ int na_fail(int code, const char* msg) {
   return code;
 }
 
+// True if the CUDA runtime reports p as device or managed memory.  The query
+// allocates nothing; a pointer it cannot classify (host memory, or no device
+// at all) is not device memory.
+bool na_on_device(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
 }  // namespace
 
 extern "C" int hif_residual_norms_noalloc(int dim, int n, const double* a_stag, const double* b,
@@ -135,6 +148,17 @@ extern "C" int hif_residual_norms_noalloc(int dim, int n, const double* a_stag, 
   if (nrhs < 1 || nrhs > kNaMaxRhs)
     return na_fail(HIF_ERR_ARG, "nrhs must be in 1..16 (the fixed scratch holds 16 columns per call)");
   if (ld < nrhs) return na_fail(HIF_ERR_ARG, "need ld >= nrhs");
+  // The kernel dereferences every array directly (nothing is staged here), so
+  // host memory is an argument error, not a fault on the device.
+  const void* ptrs[5] = {a_stag, b, f, x, rnorm2};
+  const char* names[5] = {"a_stag", "b", "f", "x", "rnorm2"};
+  for (int i = 0; i < 5; ++i) {
+    if (!na_on_device(ptrs[i])) {
+      static thread_local char msg[96];
+      snprintf(msg, sizeof msg, "%s is not device memory (this entry point stages nothing)", names[i]);
+      return na_fail(HIF_ERR_ARG, msg);
+    }
+  }
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
     return na_fail(HIF_ERR_CUDA, "no usable current CUDA device");

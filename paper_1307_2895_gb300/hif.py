@@ -326,7 +326,16 @@ def residual_norms_noalloc(dim: int, n: int, a_stag, b, f, x, out, stream=None) 
     """hif_residual_norms_noalloc on CUDA tensors: out[r] = ||f_r - A x_r||^2.
     Allocates nothing on the device (the library's fixed scratch is used)."""
     lib = load()
+    for v, what in ((a_stag, "a_stag"), (b, "b"), (f, "f"), (x, "x"), (out, "out")):
+        if not (_is_torch(v) and v.is_cuda):
+            raise TypeError(f"{what} must be a CUDA tensor (this entry point stages nothing)")
     f2, x2 = _as_2d(f), _as_2d(x)
+    _need_problem(dim, n, a_stag, b)
+    if dim in (2, 3) and n >= 2:
+        _need_rows(f2, (n - 1) ** dim, "f")
+    if tuple(x2.shape) != tuple(f2.shape):
+        raise ValueError(f"x has shape {tuple(x2.shape)}, f has {tuple(f2.shape)}")
+    _need(out, f2.shape[1], "out")
     rc = lib.hif_residual_norms_noalloc(dim, n, _ptr(a_stag), _ptr(b), _ptr(f2), _ptr(x2), f2.shape[1],
                                         f2.shape[1], _ptr(out), _stream_ptr(stream))
     _check(rc, lib)

@@ -69,6 +69,38 @@ def standard_normal(seed: int, count: int, offset: int = 0) -> np.ndarray:
     return z[:count]
 
 
+def splitmix64_at(seed: int, counters) -> np.ndarray:
+    """splitmix64 outputs number ``counters`` (each >= 1) of the stream seeded
+    with ``seed`` (array-valued counterpart of :func:`splitmix64`)."""
+    with np.errstate(over="ignore"):
+        c = np.asarray(counters, dtype=np.uint64)
+        z = (np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + c * np.uint64(0x9E3779B97F4A7C15)) & _MASK64
+        z = ((z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)) & _MASK64
+        z = ((z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)) & _MASK64
+        return z ^ (z >> np.uint64(31))
+
+
+def sketch_matrix(seed: int, level: int, nglob: int, c0: int, ell: int, rows) -> np.ndarray:
+    """Gaussian sampling matrix of the randomized ID drawn by the CUDA path for
+    one front (random numbers of the method, generated here from the same
+    published definitions so that a checker can rebuild them).
+
+    The front is identified by its fractional level and its smallest DOF id
+    ``c0``; its key is splitmix64 output number ``level * nglob + c0 + 1`` of
+    the stream seeded with ``seed``.  Entry (r, i) belongs to sketch row r and
+    to the DOF ``rows[i]`` (global id): with e = r * nglob + rows[i], it is
+    the cosine branch of the Box-Muller transform of u1 = 1 - U(2e + 1) and
+    u2 = U(2e + 2), where U(c) is the top 53 bits of output c of the stream
+    seeded with the key, over 2^53.  Returns an (ell, len(rows)) array."""
+    key = int(splitmix64_at(seed, [level * nglob + c0 + 1])[0])
+    rows = np.asarray(rows, dtype=np.uint64)
+    e = (np.arange(ell, dtype=np.uint64)[:, None] * np.uint64(nglob) + rows[None, :]).ravel()
+    u1 = 1.0 - (splitmix64_at(key, 2 * e + np.uint64(1)) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+    u2 = (splitmix64_at(key, 2 * e + np.uint64(2)) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+    z = np.sqrt(-2.0 * np.log(u1)) * np.cos(6.283185307179586 * u2)
+    return z.reshape(ell, len(rows))
+
+
 def num_dofs(dim: int, n: int) -> int:
     return (n - 1) ** dim
 

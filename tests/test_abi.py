@@ -150,3 +150,24 @@ def test_binding_refuses_wrong_lengths_before_the_library():
         with pytest.raises(ValueError):
             call()
     F._h = None        # nothing to free
+
+
+def test_noalloc_refuses_host_pointers_without_gpu():
+    """hif_residual_norms_noalloc dereferences its arrays on the device, so a
+    host pointer is refused with HIF_ERR_ARG before any launch."""
+    lib = hif.load(build_if_missing=True)
+    n = 16
+    a, b = np.ones(2 * n * (n - 1)), np.zeros((n - 1) ** 2)
+    f = np.zeros(((n - 1) ** 2, 2))
+    out = np.zeros(2)
+    rc = lib.hif_residual_norms_noalloc(2, n, a.ctypes.data, b.ctypes.data, f.ctypes.data, f.ctypes.data, 2, 2,
+                                        out.ctypes.data, None)
+    assert rc == hif.HIF_ERR_ARG and b"not device memory" in lib.hif_last_error()
+
+
+def test_noalloc_binding_refuses_host_arrays_and_wrong_lengths():
+    n = 16
+    a, b = np.ones(2 * n * (n - 1)), np.zeros((n - 1) ** 2)
+    f = np.zeros(((n - 1) ** 2, 2))
+    with pytest.raises(TypeError):
+        hif.residual_norms_noalloc(2, n, a, b, f, f, np.zeros(2))

@@ -1,7 +1,4 @@
-"""Edge cases of the CUDA path against the FP64 oracle, not yet run on a GPU.
-
-They run only with HIF_EDGE_CHECKS=1 (and -m gpu): each joins the default
-GPU suite once it has passed on a GPU.
+"""Edge cases of the CUDA path against the FP64 oracle.
 
 * The smallest trees: n = 4 (cells and fronts of one DOF) and n = 5 (a
   ragged grid) in 2D and 3D: front sets, skeletons and |s_L| equal to the
@@ -13,7 +10,6 @@ GPU suite once it has passed on a GPU.
   neither read nor written.
 """
 import ctypes
-import os
 
 import numpy as np
 import pytest
@@ -21,9 +17,7 @@ import pytest
 from oracle import hifde, stencil
 from paper_1307_2895_gb300 import inputs
 
-pytestmark = [pytest.mark.gpu,
-              pytest.mark.skipif(os.environ.get("HIF_EDGE_CHECKS") != "1",
-                                 reason="edge cases not yet run on a GPU (set HIF_EDGE_CHECKS=1)")]
+pytestmark = pytest.mark.gpu
 
 
 def _contrast(dim, n):

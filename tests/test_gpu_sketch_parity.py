@@ -1,0 +1,88 @@
+"""Randomized ID on the GPU against the oracle's randomized ID (Section 4.3).
+
+The sampling matrix of each front is drawn by the CUDA path from a
+counter-based stream (splitmix64 and the Box-Muller transform, keyed by the
+seed, the fractional level, the front's smallest DOF id, the sketch row and
+the DOF id of each row of A_{N,c}); the host rebuilds it from the same
+published definitions (``inputs.sketch_matrix``) and hands it to the oracle.
+Both sides then take every decision in FP64: the pivoted QR of the sketch
+and its rank, the acceptance check on A_{N,c} itself, and on a failed check
+the pivoted-QR ID of A_{N,c}.  Required: identical skeletons (pivot order)
+and ranks on every front whose decisions the oracle does not flag as lying
+within 1e-8 of a threshold, identical counts of accepted and rejected
+sketches and |s_L|, and F^-1 x within 1e-10 when nothing is flagged.  Covers
+the one-block front kernel (2D, 3D level-0 faces) and the multi-block one
+(3D level-1 faces of 128+ DOFs).
+"""
+import numpy as np
+import pytest
+
+from oracle import hifde, stencil
+from paper_1307_2895_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+SEED = 7
+
+
+def _fields(dim, n, field):
+    if field == "lap":
+        return inputs.constant_coefficients(dim, n)
+    return inputs.high_contrast_coefficients(dim, n, seed=11, low=1e-2, high=1e2)
+
+
+def _phi(N, oversample):
+    def phi(level, c, rows):
+        nc = len(c)
+        ell = max(1, (nc + 1) // 2) + oversample       # k_hat = ceil(|c|/2) in the model-free mode
+        if not (ell < nc and ell < len(rows)):
+            return None
+        return inputs.sketch_matrix(SEED, level, N, c[0], ell, rows)
+    return phi
+
+
+@pytest.mark.parametrize("dim,n,field,eps,oversample,big_cell", [
+    (2, 64, "lap", 1e-6, 2, 0),
+    (2, 64, "contrast", 1e-6, 2, 0),
+    (2, 128, "contrast", 1e-9, 3, 0),
+    (3, 32, "lap", 1e-3, 10, 128),
+    (3, 20, "contrast", 1e-4, 4, 128),
+])
+def test_sketched_id_matches_oracle(hiflib, dim, n, field, eps, oversample, big_cell):
+    from paper_1307_2895_gb300 import hif
+    a, b = _fields(dim, n, field)
+    A = stencil.assemble(dim, n, a, b)
+    N = (n - 1) ** dim
+    F = hifde.factor(A, dim, n, eps, sketch=_phi(N, oversample))
+    x = inputs.rhs(dim, n, 2, seed=5)
+    G = hif.factor(dim, n, a, b, eps, precision="fp64", id_mode="rand", oversample=oversample, seed=SEED,
+                   big_cell=big_cell)
+    try:
+        fronts, root = G.structure()
+        st = G.stats()
+        yi = G.apply(x, inverse=True)
+    finally:
+        G.free()
+    assert F.sketched > 0 and F.fallback >= 0
+    got = {(lev, tuple(c)): sk for lev, c, sk in fronts}
+    ostruct, oroot = F.skeleton_structure()
+    flagged, compared, nbig = 0, 0, 0
+    for lev, d in enumerate(ostruct):
+        near = {tuple(fr.c.tolist()) for fr in F.levels[lev].fronts if fr.near_threshold}
+        for key, (c, sk, k) in d.items():
+            if tuple(c) in near:
+                flagged += 1
+                continue
+            compared += 1
+            nbig += len(c) >= 128
+            assert got.get((lev, tuple(c))) == sk, f"level {lev} front {c[:4]}...: skeletons differ"
+    assert flagged <= max(1, compared // 100)
+    if big_cell:
+        assert nbig > 0
+    if flagged == 0:
+        assert root == oroot
+        assert (st["sketched_fronts"], st["fallback_fronts"]) == (F.sketched, F.fallback)
+        oi = F.apply_inverse(x)
+        assert np.linalg.norm(yi - oi) <= 1e-10 * np.linalg.norm(oi)
+        err = np.abs(yi - oi).max() / np.abs(oi).max()
+        assert err <= 1e-10

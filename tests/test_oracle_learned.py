@@ -74,3 +74,37 @@ def test_randomized_id_undersized_sketch_is_rejected():
     Phi = inputs.standard_normal(4, 4 * m).reshape(4, m)
     idr, ok = learned.randomized_id(M, 1e-6, Phi)
     assert not ok
+
+
+def test_factor_with_identity_sketch_is_the_plain_factorization():
+    """Phi = I makes the sketch the block itself: every front's randomized ID
+    is its pivoted-QR ID and passes the check, so the factorization is the
+    plain one (same skeletons in pivot order, same root)."""
+    from oracle import hifde, stencil
+    from paper_1307_2895_gb300 import inputs
+    dim, n, eps = 2, 32, 1e-6
+    a, b = inputs.high_contrast_coefficients(dim, n, seed=11, low=1e-2, high=1e2)
+    A = stencil.assemble(dim, n, a, b)
+    F0 = hifde.factor(A, dim, n, eps)
+    F1 = hifde.factor(A, dim, n, eps, sketch=lambda l, c, rows: np.eye(len(rows)) if len(rows) > len(c) else None)
+    s0, r0 = F0.skeleton_structure()
+    s1, r1 = F1.skeleton_structure()
+    assert s0 == s1 and r0 == r1
+    assert F1.sketched > 0 and F1.fallback == 0
+
+
+def test_factor_with_undersized_sketch_falls_back_everywhere():
+    """A one-row sketch saturates (k = ell) on every front of rank > 1 or
+    fails the check: each such front falls back to the pivoted-QR ID, so the
+    skeletons are the plain ones and the rejections are counted."""
+    from oracle import hifde, stencil
+    from paper_1307_2895_gb300 import inputs
+    dim, n, eps = 2, 32, 1e-6
+    a, b = inputs.high_contrast_coefficients(dim, n, seed=11, low=1e-2, high=1e2)
+    A = stencil.assemble(dim, n, a, b)
+    F0 = hifde.factor(A, dim, n, eps)
+    rng = np.random.default_rng(0)
+    F1 = hifde.factor(A, dim, n, eps, sketch=lambda l, c, rows: rng.standard_normal((1, len(rows))))
+    assert F1.skeleton_structure() == F0.skeleton_structure()
+    nfronts = sum(len(lev.fronts) for lev in F1.levels)
+    assert F1.sketched == 0 and F1.fallback == nfronts
