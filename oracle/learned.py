@@ -3,15 +3,17 @@
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 
 * :func:`randomized_id` -- the randomized ID mentioned in Section 4.3 (and
-  again at the end of Section 4.5): compress ``Phi M`` instead of ``M``, with
-  ``Phi`` a Gaussian sampling matrix of ``ell`` rows (passed in as an input),
-  then accept the result only if the interpolation residual of ``M`` itself
-  passes the pivoted QR's own stopping rule for those skeletons: every column
-  of ``M_r - M_s T`` has norm at most ``eps`` times the largest column norm of
+  again at the end of Section 4.5): choose the skeletons from ``Phi M``
+  instead of ``M``, with ``Phi`` a Gaussian sampling matrix of ``ell`` rows
+  (passed in as an input), fit T to ``M`` itself by least squares, then
+  accept the result only if the interpolation residual of ``M`` passes the
+  pivoted QR's own stopping rule for those skeletons: every column of
+  ``M_r - M_s T`` has norm at most ``eps`` times the largest column norm of
   ``M`` (in a pivoted QR these are |R_{k+1,k+1}| and |R_11|, Section 2.2);
-  otherwise the caller falls back to the pivoted-QR ID of ``M`` (Lemma 2.2).  The skeleton choice
-  is not comparable with the GPU's (different random numbers): parity is
-  pinned by the residual check and by the end-to-end residual only.
+  otherwise the caller falls back to the pivoted-QR ID of ``M`` (Lemma 2.2).
+  Given the same ``Phi`` (the GPU's counter-based stream, rebuilt on the
+  host), its skeletons and decisions are compared with the GPU's front by
+  front.
 * :class:`MLP` -- the rank predictor: three layers of width 64 with ReLU,
   target log(1 + k), Huber loss (delta 1), mean over samples.  Forward and
   backward written out; gradients are pinned by central finite differences
@@ -19,7 +21,9 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 
 Parity status: the MLP gradients are pinned (finite differences); the
 randomized ID is pinned by exact low-rank cases (it must recover the rank and
-interpolate to rounding) and by its fallback on an undersized sketch.
+interpolate to rounding), by its fallback on an undersized sketch, and, in a
+whole factorization, by the identity sketch (which makes it the pivoted-QR
+ID at ``SKETCH_RANK_TOL * eps``).
 """
 from __future__ import annotations
 
@@ -32,21 +36,36 @@ from .hifde import interp_decomp
 HUBER_DELTA = 1.0
 
 
+# The sketch's skeletons are chosen at this fraction of eps: a Gaussian
+# sketch's pivots track those of M only to a modest factor, so the pivoted QR
+# of Y at eps itself stops a few columns early for M.
+SKETCH_RANK_TOL = 0.1
+
+
 def randomized_id(M: np.ndarray, eps: float, Phi: np.ndarray):
-    """ID of M from the sketch Y = Phi M.  Returns (IDResult, ok) where ok says
-    the residual check passed (column norms, see the module docstring) and the
-    sketch was not saturated (k < ell).  The result's near_threshold flag is
-    also set when the largest residual column norm lies within 1e-8
-    (relative) of the acceptance bound, a decision that rounding order could
-    flip."""
+    """ID of M from the sketch Y = Phi M: the skeletons and rank of the
+    pivoted-QR ID of Y at ``SKETCH_RANK_TOL * eps``, then T by least squares
+    on M itself (T minimizes every column norm of M_r - M_s T).  Returns
+    (IDResult, ok) where ok says the residual check passed (column norms, see
+    the module docstring) and the sketch was not saturated (k < ell).  The
+    result's near_threshold flag is also set when the largest residual column
+    norm lies within 1e-8 (relative) of the acceptance bound, a decision that
+    rounding order could flip."""
     Y = Phi @ M
-    idr = interp_decomp(Y, eps)
-    k, ell = len(idr.sk), Phi.shape[0]
-    E = M[:, idr.rd] - M[:, idr.sk] @ idr.T
+    idy = interp_decomp(Y, SKETCH_RANK_TOL * eps)
+    k, ell = len(idy.sk), Phi.shape[0]
+    if k >= ell:
+        return idy, False
+    if k:
+        T = np.linalg.lstsq(M[:, idy.sk], M[:, idy.rd], rcond=None)[0]
+    else:
+        T = np.zeros((0, len(idy.rd)))
+    idr = dataclasses.replace(idy, T=T)
+    E = M[:, idr.rd] - M[:, idr.sk] @ T
     e = np.linalg.norm(E, axis=0).max() if E.size else 0.0
     bound = eps * np.linalg.norm(M, axis=0).max()
-    ok = bool(k < ell and e <= bound)
-    if k < ell and abs(e - bound) <= 1e-8 * bound:
+    ok = bool(e <= bound)
+    if abs(e - bound) <= 1e-8 * bound:
         idr = dataclasses.replace(idr, near_threshold=True)
     return idr, ok
 

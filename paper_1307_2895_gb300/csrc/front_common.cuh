@@ -123,6 +123,88 @@ __device__ void blk_id_T(const T* A, int m, const int* perm, int k, int nc, T* T
   __syncthreads();
 }
 
+// Rank tolerance of the pivoted QR of a sketch, relative to eps: the sketch's
+// skeleton set is chosen at kSketchRankTol * eps so that the interpolation of
+// A_{N,c} itself meets eps (a Gaussian sketch's pivots track those of A_{N,c}
+// only to a modest factor).
+constexpr double kSketchRankTol = 0.1;
+
+// T for given skeletons by least squares on M itself (the sketched ID of
+// Section 4.3 keeps only the sketch's choice of skeletons): Householder QR of
+// the columns perm[0..k) of C (a copy of M, m x nc, column-major) in that
+// order, applied to the other columns -- the first k steps of
+// blk_pivoted_qr with the pivots given -- then T = R11^-1 R12 (k x (nc - k)),
+// which minimizes every column norm of M_r - M_s T.  Returns the largest
+// squared residual column norm (rows k..m-1 of the transformed redundant
+// columns), or -1 if a skeleton column vanishes.  v: m doubles; chosen: nc
+// ints of scratch.
+template <typename T>
+__device__ double blk_ls_id(T* C, int m, int nc, const int* perm, int k, int* chosen, double* v, T* Tm) {
+  __shared__ double s_alpha, s_vv, s_red[32];
+  __shared__ int s_bad;
+  for (int j = threadIdx.x; j < nc; j += blockDim.x) chosen[j] = 0;
+  if (threadIdx.x == 0) s_bad = 0;
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  for (int i = 0; i < k; ++i) {
+    const int piv = perm[i];
+    T* pc = C + (int64_t)piv * m;
+    if (warp == 0) {
+      double acc = 0.0;
+      for (int r = i + lane; r < m; r += 32) { const double x = (double)pc[r]; acc += x * x; }
+      acc = warp_sum(acc);
+      if (lane == 0) {
+        if (!(acc > 0.0)) {
+          s_bad = 1;
+        } else {
+          const double x0 = (double)pc[i];
+          const double a2 = (x0 >= 0.0) ? -sqrt(acc) : sqrt(acc);
+          s_alpha = a2;
+          s_vv = acc - x0 * x0 + (x0 - a2) * (x0 - a2);
+          chosen[piv] = 1;
+        }
+      }
+    }
+    __syncthreads();
+    if (s_bad) return -1.0;
+    const double alpha = s_alpha, vv = s_vv;
+    for (int r = i + threadIdx.x; r < m; r += blockDim.x) v[r] = (double)pc[r] - (r == i ? alpha : 0.0);
+    __syncthreads();
+    if (vv > 0.0) {
+      for (int j = warp; j < nc; j += nwarps) {
+        if (chosen[j]) continue;
+        T* col = C + (int64_t)j * m;
+        double s = 0.0;
+        for (int r = i + lane; r < m; r += 32) s += v[r] * (double)col[r];
+        s = warp_sum(s);
+        const double f = 2.0 * s / vv;
+        for (int r = i + lane; r < m; r += 32) col[r] = (T)((double)col[r] - f * v[r]);
+      }
+    }
+    for (int r = i + threadIdx.x; r < m; r += blockDim.x) pc[r] = (r == i) ? (T)alpha : T(0);
+    __syncthreads();
+  }
+  blk_id_T(C, m, perm, k, nc, Tm);
+  double e2 = 0.0;
+  for (int c = warp; c < nc - k; c += nwarps) {
+    const T* col = C + (int64_t)perm[k + c] * m;
+    double s = 0.0;
+    for (int r = k + lane; r < m; r += 32) { const double x = (double)col[r]; s += x * x; }
+    e2 = fmax(e2, warp_sum(s));
+  }
+  if (lane == 0) s_red[warp] = e2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double mx = 0.0;
+    for (int w = 0; w < nwarps; ++w) mx = fmax(mx, s_red[w]);
+    s_red[0] = mx;
+  }
+  __syncthreads();
+  const double r = s_red[0];
+  __syncthreads();
+  return r;
+}
+
 // splitmix64 (Steele, Lea and Flood, 2014): output number c >= 1 of the
 // stream seeded with s is the mixing function of the state s + c * gamma.
 __device__ __forceinline__ uint64_t smix_at(uint64_t s, uint64_t c) {

@@ -206,7 +206,10 @@ struct hif_handle {
   cudaStream_t st = nullptr;
   cudaStream_t own_stream = nullptr;   // created when the caller passes no stream
   DevBuf a_stag, bnode;
-  DevBuf dev_err;   // device status of the apply kernels (bit 3: a bounded wait ran out)
+  DevBuf dev_err;   // device status of the apply kernels (bit 3: a bounded copy wait ran out;
+                    // bit 6: a fused sweep's wait for the previous sub-level ran out)
+  DevBuf fuse_ctr;  // counters of the fused upper-level sweeps (kFusedCtr, zero between launches)
+  bool count_sweeps = false;   // while a graph is captured: count sweep bytes and launches, no events
   DevBuf stencil_w; // per-node stencil weights (diagonal and neighbour couplings)
   DevBuf model_bf16; // rank-predictor parameters in BF16 (HIF_ID_LEARNED)
   std::shared_ptr<const Level0> level0;
@@ -656,10 +659,9 @@ struct Factorizer {
         small.push_back(f);
       }
     }
-    DevBuf d_sel, d_big, bstate, m2part, e2part, d_td;
+    DevBuf d_sel, d_big, bstate, m2part, d_td;
     const int nbig = (int)big.size();
     const int nm = nbig ? bigfront_colmax_blocks(big_nc) : 0;
-    const int ne = nbig ? bigfront_resid_strips(big_nc) : 0;
     if (big.empty()) {
       launch_front<T>(d_fd, nf, d_cdesc, d_ip, obuf.as<int>(), fwork.as<T>(), sw.fac.as<T>(), cwork.as<T>(), h->eps,
                       status.as<int>(), max_nc, max_nN, tau, sketch.as<int>(), ss, nullptr, st);
@@ -678,7 +680,6 @@ struct Factorizer {
       upload(d_big, big, st);
       bstate.alloc(sizeof(int) * nbig, st);
       m2part.alloc(sizeof(double) * nbig * nm, st);
-      e2part.alloc(sizeof(double) * nbig * ne, st);
       std::vector<int> bnc(nbig), bnN(nbig);
       for (int b = 0; b < nbig; ++b) {
         bnc[b] = fd[big[b]].nc;
@@ -686,7 +687,7 @@ struct Factorizer {
       }
       launch_bigfront_id<T>(d_fd, d_big.as<int>(), nbig, d_cdesc, d_ip, cwork.as<T>(), fwork.as<T>(), sw.fac.as<T>(),
                             obuf.as<int>(), sketch.as<int>(), ss, h->eps, status.as<int>(), bstate.as<int>(),
-                            m2part.as<double>(), nm, e2part.as<double>(), ne, big_nc, big_nN,
+                            m2part.as<double>(), nm, big_nc, big_nN,
                             sketch.p ? big_nc : 0, bnc.data(), bnN.data(), h->coop_qr, st);
     }
     CU(cudaGetLastError());
@@ -895,6 +896,29 @@ SweepShape tuned_shape(hif_handle* h, int op, const SweepLevel& S, int is_front,
   return best;
 }
 
+// First level of the fused F^-1 sweeps (kernels_apply.cu, k_apply_fused):
+// the lowest level l >= 1 whose cells number at most two per SM, so that
+// every level from there on has fewer blocks than resident CTAs.  L: none.
+// HIF_FUSE_LEVEL=l forces the level (l >= L: separate launches only).
+int fused_from(const hif_handle* h) {
+  const int L = h->G.L;
+  if (h->root.nblocks != 1 || !h->fuse_ctr.p) return L;
+  static const int forced = [] {
+    const char* e = getenv("HIF_FUSE_LEVEL");
+    return e ? atoi(e) : -1;
+  }();
+  if (forced >= 0) return forced < 1 ? 1 : (forced > L ? L : forced);
+  static const int nsm = [] {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+  }();
+  for (int l = 1; l < L; ++l)
+    if (h->cells[l].nblocks <= 2 * nsm) return l;
+  return L;
+}
+
 template <typename T>
 void run_apply(hif_handle* h, int mode, T* x, int nrhs) {
   const int L = h->G.L;
@@ -902,6 +926,11 @@ void run_apply(hif_handle* h, int mode, T* x, int nrhs) {
   const int up = (mode == HIF_APPLY_FINV) ? 0 : 2;
   const int down = (mode == HIF_APPLY_FINV) ? 1 : 3;
   const bool prof = h->profile && mode == HIF_APPLY_FINV;
+  const bool count = prof || (h->count_sweeps && mode == HIF_APPLY_FINV);
+  auto sweep_bytes = [&](const SweepLevel& S, int op) {
+    // the fused root launch (op 4) does the work of an up and a down sweep
+    return (op == 4 ? 2.0 : 1.0) * sizeof(T) * (S.fac_elems + 2.0 * S.vec_rows * nrhs);
+  };
   auto sweep = [&](const SweepLevel& S, int op, int is_front, const T* fac) {
     if (S.nblocks == 0) return;
     if (prof) {
@@ -921,26 +950,84 @@ void run_apply(hif_handle* h, int mode, T* x, int nrhs) {
     if (prof) {
       CU(cudaEventRecord(h->ev_pool[h->ev_used + 1], st));
       h->ev_used += 2;
+    }
+    if (count) {
       h->prof_launches += 1;
-      // the fused root launch (op 4) does the work of an up and a down sweep
-      h->prof_bytes += (op == 4 ? 2.0 : 1.0) * sizeof(T) * (S.fac_elems + 2.0 * S.vec_rows * nrhs);
+      h->prof_bytes += sweep_bytes(S, op);
     }
   };
   auto facp = [&](const SweepLevel& S) -> const T* {
     if (sizeof(T) == sizeof(float)) return reinterpret_cast<const T*>(fac_f32(S));
     return S.fac.as<T>();
   };
-  for (int l = 0; l < L; ++l) {
+  // F^-1: the levels from lf up, the root and their down sweeps in one
+  // persistent launch (levels with few blocks each)
+  const int lf = (mode == HIF_APPLY_FINV) ? fused_from(h) : L;
+  for (int l = 0; l < lf; ++l) {
     sweep(h->cells[l], up, 0, facp(h->cells[l]));
     sweep(h->fronts[l], up, 1, facp(h->fronts[l]));
   }
-  if (mode == HIF_APPLY_FINV) {
-    sweep(h->root, 4, 0, facp(h->root));   // D^-1: the root's up and down sweeps in one launch
-  } else {
-    sweep(h->root, up, 0, facp(h->root));
-    sweep(h->root, down, 0, facp(h->root));
+  bool fused = false;
+  if (lf < L) {
+    FusedPlan plan{};
+    int t = 0;
+    double bytes = 0.0;
+    auto add = [&](const SweepLevel& S, int op, int is_front) {
+      if (S.nblocks == 0) return;
+      FusedLevel& f = plan.lev[plan.nlev++];
+      f = FusedLevel{S.desc, S.ipool, facp(S), S.nblocks, t, op, is_front, 0, S.max_np, S.max_nq};
+      t += S.nblocks;
+      bytes += sweep_bytes(S, op);
+    };
+    for (int l = lf; l < L; ++l) {
+      add(h->cells[l], 0, 0);
+      add(h->fronts[l], 0, 1);
+    }
+    add(h->root, 4, 0);
+    for (int l = L - 1; l >= lf; --l) {
+      add(h->fronts[l], 1, 1);
+      add(h->cells[l], 1, 0);
+    }
+    plan.ntasks = t;
+    if (prof) {
+      if (h->ev_used + 2 > h->ev_pool.size()) {
+        for (int k = 0; k < 64; ++k) {
+          cudaEvent_t e;
+          CU(cudaEventCreate(&e));
+          h->ev_pool.push_back(e);
+        }
+      }
+      CU(cudaEventRecord(h->ev_pool[h->ev_used], st));
+    }
+    int nl = 0;
+    fused = launch_sweep_fused<T>(plan, x, nrhs, nrhs, static_cast<unsigned*>(h->fuse_ctr.p),
+                                  h->dev_err.as<int>(), st, &nl);
+    if (prof) {
+      CU(cudaEventRecord(h->ev_pool[h->ev_used + 1], st));
+      h->ev_used += 2;
+    }
+    if (fused && count) {
+      h->prof_launches += nl;
+      h->prof_bytes += bytes;
+    }
   }
-  for (int l = L - 1; l >= 0; --l) {
+  if (!fused) {
+    for (int l = lf; l < L; ++l) {
+      sweep(h->cells[l], up, 0, facp(h->cells[l]));
+      sweep(h->fronts[l], up, 1, facp(h->fronts[l]));
+    }
+    if (mode == HIF_APPLY_FINV) {
+      sweep(h->root, 4, 0, facp(h->root));   // D^-1: the root's up and down sweeps in one launch
+    } else {
+      sweep(h->root, up, 0, facp(h->root));
+      sweep(h->root, down, 0, facp(h->root));
+    }
+    for (int l = L - 1; l >= lf; --l) {
+      sweep(h->fronts[l], down, 1, facp(h->fronts[l]));
+      sweep(h->cells[l], down, 0, facp(h->cells[l]));
+    }
+  }
+  for (int l = lf - 1; l >= 0; --l) {
     sweep(h->fronts[l], down, 1, facp(h->fronts[l]));
     sweep(h->cells[l], down, 0, facp(h->cells[l]));
   }
@@ -1055,6 +1142,7 @@ struct Precond {
       const double b0 = h->prof_bytes;
       const long long l0 = h->prof_launches;
       h->profile = 0;
+      h->count_sweeps = true;   // what one replay moves and launches
       cudaGraph_t g = nullptr;
       CU(cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal));
       try {
@@ -1063,10 +1151,18 @@ struct Precond {
         if (cudaStreamEndCapture(h->st, &g) == cudaSuccess && g) cudaGraphDestroy(g);
         cudaGetLastError();
         h->profile = prof;
+        h->count_sweeps = false;
+        h->prof_bytes = b0;
+        h->prof_launches = l0;
         throw;
       }
       const cudaError_t ce = cudaStreamEndCapture(h->st, &g);
       h->profile = prof;
+      h->count_sweeps = false;
+      const double gb = h->prof_bytes - b0;
+      const long long gl = h->prof_launches - l0;
+      h->prof_bytes = b0;
+      h->prof_launches = l0;
       cudaError_t e = ce;
       if (ce == cudaSuccess && g) {
         e = cudaGraphInstantiate(&exec, g, 0);
@@ -1079,20 +1175,9 @@ struct Precond {
         eager();
         return;
       }
-      // bytes and launches of one replay (what the eager sweeps would record)
-      h->graph_bytes = 0.0;
-      h->graph_launches = 0;
-      const double esz = W.f32 ? sizeof(float) : sizeof(double);
-      auto add = [&](const SweepLevel& S, int launches) {
-        if (S.nblocks == 0) return;
-        h->graph_bytes += 2.0 * esz * (S.fac_elems + 2.0 * S.vec_rows * W.R);
-        h->graph_launches += launches;
-      };
-      for (const auto& S : h->cells) add(S, 2);
-      for (const auto& S : h->fronts) add(S, 2);
-      add(h->root, 1);   // up and down of the root in one launch
-      h->prof_bytes = b0;
-      h->prof_launches = l0;
+      // bytes and launches of one replay (counted while it was captured)
+      h->graph_bytes = gb;
+      h->graph_launches = gl;
     }
     if (h->profile) {
       while (h->ev_used + 2 > h->ev_pool.size()) {
@@ -1507,7 +1592,8 @@ int check_dev_err(hif_handle* h) {
   CU(cudaStreamSynchronize(h->st));
   if (e) {
     CU(cudaMemsetAsync(h->dev_err.p, 0, sizeof(int), h->st));
-    throw HifError(HIF_ERR_TIMEOUT, "a bounded wait for a bulk copy into shared memory ran out");
+    throw HifError(HIF_ERR_TIMEOUT, (e & 64) ? "a fused sweep's bounded wait for the previous level ran out"
+                                             : "a bounded wait for a bulk copy into shared memory ran out");
   }
   return HIF_OK;
 }
@@ -1654,6 +1740,8 @@ int hif_factor(const hif_grid* grid, const double* a_stag, const double* b, cons
     const int64_t na = (int64_t)grid->n * h->G.N / (grid->n - 1) * grid->dim;
     h->dev_err.alloc(sizeof(int), h->st);
     CU(cudaMemsetAsync(h->dev_err.p, 0, sizeof(int), h->st));
+    h->fuse_ctr.alloc(sizeof(unsigned) * kFusedCtr, h->st);
+    CU(cudaMemsetAsync(h->fuse_ctr.p, 0, sizeof(unsigned) * kFusedCtr, h->st));
     h->a_stag.alloc(sizeof(double) * na, h->st);
     h->bnode.alloc(sizeof(double) * h->G.N, h->st);
     CU(cudaMemcpyAsync(h->a_stag.p, a_stag, sizeof(double) * na, cudaMemcpyDefault, h->st));

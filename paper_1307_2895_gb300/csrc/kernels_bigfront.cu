@@ -153,17 +153,21 @@ __global__ void __launch_bounds__(TT) k_bf_sketch(const FrontDesc* __restrict__ 
 }
 
 // ---- the ID, one thread block per front.
-// pass 0: fronts with a valid sketch size take the pivoted QR of Y (state 1:
-// residual check pending; state 2 if the sketch saturated, k = ell); the
-// others the pivoted QR of M (state 0), or are left in state 2 for the
-// multi-block QR (defer_qr).  pass 1: fronts in state 2 take the pivoted QR
-// of M (state 0).  Writes T (k x nR) to the front's factor, and
-// k | perm | ids (pivot order) to its output slot.
+// pass 0: fronts with a valid sketch size take the pivoted QR of Y (rank
+// rule at kSketchRankTol * eps), then T by least squares on a copy of M
+// (blk_ls_id, in the spare region after Y), accepted (state 0) when every
+// residual column norm is at most eps times the largest column norm of M
+// (m2part: the partial maxima of k_bf_colmax), else left in state 2 (also
+// when the sketch saturated, k = ell); the other fronts take the pivoted QR
+// of M (state 0), or are left in state 2 for the multi-block QR (defer_qr).
+// pass 1: fronts in state 2 take the pivoted QR of M (state 0).  Writes T
+// (k x nR) to the front's factor, and k | perm | ids (pivot order) to its
+// output slot.
 template <typename T>
 __global__ void k_bf_id(const FrontDesc* __restrict__ fronts, const int* __restrict__ big,
                         const int* __restrict__ sketch, const int* __restrict__ ipool, T* __restrict__ fwork,
                         T* __restrict__ fac, int* __restrict__ obuf, int* __restrict__ state, double eps,
-                        int* status, int pass, int defer_qr) {
+                        int* status, int pass, int defer_qr, const double* __restrict__ m2part, int nm) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int f = big[blockIdx.x];
   const FrontDesc fd = fronts[f];
@@ -178,103 +182,48 @@ __global__ void k_bf_id(const FrontDesc* __restrict__ fronts, const int* __restr
   }
   const int m = use_sketch ? ell : nN;
   double* sq = reinterpret_cast<double*>(smem_raw);            // nc
-  double* vv = sq + nc;                                         // m
-  int* perm = reinterpret_cast<int*>(vv + m);                   // nc
+  double* vv = sq + nc;                                         // nN (m <= nN)
+  int* perm = reinterpret_cast<int*>(vv + nN);                  // nc
   int* chosen = perm + nc;                                      // nc
   T* A = fwork + (use_sketch ? v.Y : v.M);
   T* Tm = fac + fd.fac + front_fac_T(nc);
-  const int k = blk_pivoted_qr(A, m, nc, eps, status, !use_sketch, sq, vv, perm, chosen);
+  const int k = blk_pivoted_qr(A, m, nc, use_sketch ? eps * kSketchRankTol : eps, status, !use_sketch, sq, vv, perm,
+                               chosen);
   if (use_sketch && k >= ell) {                                 // saturated: fall back
-    if (threadIdx.x == 0) state[blockIdx.x] = 2;
+    if (threadIdx.x == 0) {
+      state[blockIdx.x] = 2;
+      atomicAdd(status + 3, 1);
+    }
     return;
   }
-  blk_id_T(A, m, perm, k, nc, Tm);
+  if (use_sketch) {
+    T* C = fwork + v.Y + (int64_t)nc * nc;                      // spare: nN x nc
+    const T* M = fwork + v.M;
+    for (int64_t e = threadIdx.x; e < (int64_t)nN * nc; e += blockDim.x) C[e] = M[e];
+    __syncthreads();
+    const double e2 = blk_ls_id(C, nN, nc, perm, k, chosen, vv, Tm);
+    double m2 = 0.0;
+    for (int i = 0; i < nm; ++i) m2 = fmax(m2, m2part[(int64_t)blockIdx.x * nm + i]);
+    if (!(e2 >= 0.0 && e2 <= eps * eps * m2)) {
+      if (threadIdx.x == 0) {
+        state[blockIdx.x] = 2;
+        atomicAdd(status + 3, 1);
+      }
+      return;
+    }
+    if (threadIdx.x == 0) atomicAdd(status + 2, 1);
+  } else {
+    blk_id_T(A, m, perm, k, nc, Tm);
+  }
   int* out = obuf + fd.out;
   const int* idc = ipool + fd.ids;
   if (threadIdx.x == 0) {
     out[0] = k;
-    state[blockIdx.x] = use_sketch ? 1 : 0;
+    state[blockIdx.x] = 0;
   }
   for (int t = threadIdx.x; t < nc; t += blockDim.x) {
     out[1 + t] = perm[t];
     out[1 + nc + t] = idc[perm[t]];
-  }
-}
-
-// ---- residual of a sketched ID, E = M_r - M_s T: each block takes a strip of
-// 64 columns over all rows and writes the largest squared column norm.
-template <typename T>
-__global__ void __launch_bounds__(TT) k_bf_resid(const FrontDesc* __restrict__ fronts, const int* __restrict__ big,
-                                                 const int* __restrict__ obuf, const int* __restrict__ state,
-                                                 const T* __restrict__ fwork, const T* __restrict__ fac,
-                                                 double* __restrict__ e2part) {
-  __shared__ TileSmem<T> sm;
-  __shared__ double s_col[16][TB];
-  const FrontDesc fd = fronts[big[blockIdx.y]];
-  double* part = e2part + (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
-  const int* out = obuf + fd.out;
-  const int k = out[0], nR = fd.nc - k;
-  const int j0 = blockIdx.x * TB;
-  if (state[blockIdx.y] != 1 || j0 >= nR) {
-    if (threadIdx.x == 0) *part = 0.0;
-    return;
-  }
-  const BfView v = bf_view(fd);
-  const int nN = fd.nN;
-  const int* perm = out + 1;
-  const T* M = fwork + v.M;
-  const T* Tm = fac + fd.fac + front_fac_T(fd.nc);
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  double cs[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int i0 = 0; i0 < nN; i0 += TB) {
-    T acc[4][4];
-    zero_acc(acc);
-    tile_mma<T, false>(
-        sm, acc, k, [&](int r, int t) { return (i0 + r < nN) ? M[(int64_t)perm[t] * nN + i0 + r] : T(0); },
-        [&](int t, int c) { return (j0 + c < nR) ? Tm[(int64_t)t * nR + j0 + c] : T(0); });
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int r = i0 + ty + 16 * i, c = j0 + tx + 16 * j;
-        if (r < nN && c < nR) {
-          const double e = (double)M[(int64_t)perm[k + c] * nN + r] - (double)acc[i][j];
-          cs[j] += e * e;
-        }
-      }
-  }
-#pragma unroll
-  for (int j = 0; j < 4; ++j) s_col[ty][tx + 16 * j] = cs[j];
-  __syncthreads();
-  if (threadIdx.x < TB) {
-    double t = 0.0;
-    for (int y = 0; y < 16; ++y) t += s_col[y][threadIdx.x];
-    s_col[0][threadIdx.x] = t;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double mx = 0.0;
-    for (int c = 0; c < TB; ++c) mx = fmax(mx, s_col[0][c]);
-    *part = mx;
-  }
-}
-
-// ---- accept a sketched ID when the largest residual column norm is at most
-// eps times the largest column norm of M (the pivoted QR's stopping rule
-// |R_{k+1,k+1}| <= eps |R_11| applied to the sketch's skeletons)
-__global__ void k_bf_check(int nbig, int* __restrict__ state, const double* __restrict__ m2part, int nm,
-                           const double* __restrict__ e2part, int ne, double eps, int* status) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= nbig || state[b] != 1) return;
-  double m2 = 0.0, e2 = 0.0;
-  for (int i = 0; i < nm; ++i) m2 = fmax(m2, m2part[(int64_t)b * nm + i]);
-  for (int i = 0; i < ne; ++i) e2 = fmax(e2, e2part[(int64_t)b * ne + i]);
-  if (e2 <= eps * eps * m2) {
-    state[b] = 0;
-    atomicAdd(status + 2, 1);
-  } else {
-    state[b] = 2;
-    atomicAdd(status + 3, 1);
   }
 }
 
@@ -606,7 +555,7 @@ static int chunk_blocks(int64_t n, int cap) {
 template <typename T>
 void launch_bigfront_id(const FrontDesc* fronts, const int* big, int nbig, const CellDesc* cells, const int* ipool,
                         const T* cwork, T* fwork, T* fac, int* obuf, const int* sketch, SketchStream ss, double eps,
-                        int* status, int* state, double* m2part, int nm, double* e2part, int ne, int max_nc,
+                        int* status, int* state, double* m2part, int nm, int max_nc,
                         int max_nN, int max_ell, const int* h_nc, const int* h_nN, bool coop_ok, cudaStream_t st) {
   if (nbig == 0) return;
   long long nl = 0;
@@ -666,13 +615,8 @@ void launch_bigfront_id(const FrontDesc* fronts, const int* big, int nbig, const
     }
   }
   k_bf_id<T><<<nbig, 256, smem, st>>>(fronts, big, sketch, ipool, fwork, fac, obuf, state, eps, status, 0,
-                                      coop ? 1 : 0);
+                                      coop ? 1 : 0, m2part, nm);
   ++nl;
-  if (sk) {
-    k_bf_resid<T><<<dim3(ne, nbig), TT, 0, st>>>(fronts, big, obuf, state, fwork, fac, e2part);
-    k_bf_check<<<(nbig + 127) / 128, 128, 0, st>>>(nbig, state, m2part, nm, e2part, ne, eps, status);
-    nl += 2;
-  }
   bool done = false;
   if (coop) {
     // descriptors and the zeroed scratch live in one stream-ordered buffer
@@ -711,7 +655,8 @@ void launch_bigfront_id(const FrontDesc* fronts, const int* big, int nbig, const
     }
   }
   if (!done && (sk || coop)) {
-    k_bf_id<T><<<nbig, 256, smem, st>>>(fronts, big, sketch, ipool, fwork, fac, obuf, state, eps, status, 1, 0);
+    k_bf_id<T><<<nbig, 256, smem, st>>>(fronts, big, sketch, ipool, fwork, fac, obuf, state, eps, status, 1, 0,
+                                        m2part, nm);
     ++nl;
   }
   note_launches(nl);
@@ -748,12 +693,11 @@ void launch_bigfront_scatter(const FrontDesc* fronts, const int* big, int nbig, 
 }
 
 int bigfront_colmax_blocks(int max_nc) { return (max_nc + 7) / 8; }
-int bigfront_resid_strips(int max_nc) { return (max_nc + TB - 1) / TB; }
 
 #define HIF_BF_INST(T)                                                                                          \
   template void launch_bigfront_id<T>(const FrontDesc*, const int*, int, const CellDesc*, const int*, const T*, \
                                       T*, T*, int*, const int*, SketchStream, double, int*, int*, double*, int, \
-                                      double*, int, int, int, int, const int*, const int*, bool, cudaStream_t); \
+                                      int, int, int, const int*, const int*, bool, cudaStream_t);               \
   template void launch_bigfront_form<T>(const FrontDesc*, const int*, int, const int*, T*, const T*, int, int,  \
                                         cudaStream_t);                                                           \
   template void launch_bigfront_scatter<T>(const FrontDesc*, const int*, int, const CellDesc*, const int*,      \

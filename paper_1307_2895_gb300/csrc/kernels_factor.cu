@@ -248,9 +248,10 @@ __global__ void k_front(const FrontDesc* __restrict__ fronts, const CellDesc* __
   T* Lp = fac + fd.fac + front_fac_L(nc);  // packed nR x nR
 
   // ---- ID: from a Gaussian sketch Y = Phi A_{N,c} (Section 4.3) when a
-  // sketch size is given, accepted only if every column of A_r - A_s T has
-  // norm <= eps max_j ||A_j||;
-  // otherwise (or without a sketch) the pivoted QR of A_{N,c} itself.
+  // sketch size is given: the skeletons of the pivoted QR of Y (rank rule at
+  // kSketchRankTol * eps), T by least squares on A_{N,c}, accepted only if
+  // every column of A_r - A_s T has norm <= eps max_j ||A_j||; otherwise (or
+  // without a sketch) the pivoted QR of A_{N,c} itself.
   const int ell = sketch ? sketch[fi] : 0;
   int k = -1;
   if (ell > 0 && ell < nc && ell < nN) {
@@ -271,24 +272,18 @@ __global__ void k_front(const FrontDesc* __restrict__ fronts, const CellDesc* __
       Y[e] = a;
     }
     __syncthreads();
-    int ks = blk_pivoted_qr(Y, ell, nc, eps, status, false, sq, v, perm, chosen);
+    int ks = blk_pivoted_qr(Y, ell, nc, eps * kSketchRankTol, status, false, sq, v, perm, chosen);
     bool ok = false;
     if (ks < ell) {
-      blk_id_T(Y, ell, perm, ks, nc, Tm);
       // accept when every residual column |M_r - M_s T|_j <= eps max_j |M_j|
-      // (the pivoted QR's stopping rule for the sketch's skeletons)
-      const int nRs = nc - ks;
-      double e2 = 0.0, m2 = 0.0;
-      for (int c = threadIdx.x; c < nRs; c += blockDim.x) {
-        const T* mr = M + (int64_t)perm[ks + c] * nN;
-        double cs = 0.0;
-        for (int i = 0; i < nN; ++i) {
-          double r = (double)mr[i];
-          for (int t = 0; t < ks; ++t) r -= (double)M[(int64_t)perm[t] * nN + i] * (double)Tm[(int64_t)t * nRs + c];
-          cs += r * r;
-        }
-        e2 = fmax(e2, cs);
-      }
+      // (the pivoted QR's stopping rule for the sketch's skeletons), T by
+      // least squares on a copy of M in PH (free once Y is formed)
+      T* C = PH;
+      for (int64_t e = threadIdx.x; e < (int64_t)nN * nc; e += blockDim.x) C[e] = M[e];
+      __syncthreads();
+      double e2 = blk_ls_id(C, nN, nc, perm, ks, chosen, v, Tm);
+      if (e2 < 0.0) e2 = INFINITY;
+      double m2 = 0.0;
       for (int c = threadIdx.x; c < nc; c += blockDim.x) {
         const T* mc = M + (int64_t)c * nN;
         double cs = 0.0;

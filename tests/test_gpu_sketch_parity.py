@@ -10,7 +10,9 @@ and its rank, the acceptance check on A_{N,c} itself, and on a failed check
 the pivoted-QR ID of A_{N,c}.  Required: identical skeletons (pivot order)
 and ranks on every front whose decisions the oracle does not flag as lying
 within 1e-8 of a threshold, identical counts of accepted and rejected
-sketches and |s_L|, and F^-1 x within 1e-10 when nothing is flagged.  Covers
+sketches and |s_L|, and F^-1 x within 1e-10 (raised to 10 u kappa(A) where
+that is larger: two backward-stable FP64 evaluations differ by up to about
+u kappa in the forward sense) when nothing is flagged.  Covers
 the one-block front kernel (2D, 3D level-0 faces) and the multi-block one
 (3D level-1 faces of 128+ DOFs).
 """
@@ -29,6 +31,14 @@ def _fields(dim, n, field):
     if field == "lap":
         return inputs.constant_coefficients(dim, n)
     return inputs.high_contrast_coefficients(dim, n, seed=11, low=1e-2, high=1e2)
+
+
+def _kappa(A):
+    """2-norm condition number of A (extreme eigenvalues by scipy's eigsh)."""
+    import scipy.sparse.linalg as spla
+    lmax = spla.eigsh(A, k=1, which="LA", return_eigenvectors=False)[0]
+    lmin = spla.eigsh(A.tocsc(), k=1, sigma=0, which="LM", return_eigenvectors=False)[0]
+    return lmax / lmin
 
 
 def _phi(N, oversample):
@@ -77,12 +87,12 @@ def test_sketched_id_matches_oracle(hiflib, dim, n, field, eps, oversample, big_
             nbig += len(c) >= 128
             assert got.get((lev, tuple(c))) == sk, f"level {lev} front {c[:4]}...: skeletons differ"
     assert flagged <= max(1, compared // 100)
-    if big_cell:
+    if big_cell and n >= 32:
         assert nbig > 0
     if flagged == 0:
         assert root == oroot
         assert (st["sketched_fronts"], st["fallback_fronts"]) == (F.sketched, F.fallback)
         oi = F.apply_inverse(x)
-        assert np.linalg.norm(yi - oi) <= 1e-10 * np.linalg.norm(oi)
-        err = np.abs(yi - oi).max() / np.abs(oi).max()
-        assert err <= 1e-10
+        tol = max(1e-10, 10 * 2.2e-16 * _kappa(A))
+        assert np.linalg.norm(yi - oi) <= tol * np.linalg.norm(oi)
+        assert np.abs(yi - oi).max() <= tol * np.abs(oi).max()
