@@ -206,9 +206,7 @@ struct hif_handle {
   cudaStream_t st = nullptr;
   cudaStream_t own_stream = nullptr;   // created when the caller passes no stream
   DevBuf a_stag, bnode;
-  DevBuf dev_err;   // device status of the apply kernels (bit 3: a bounded copy wait ran out;
-                    // bit 6: a fused sweep's wait for the previous sub-level ran out)
-  DevBuf fuse_ctr;  // counters of the fused upper-level sweeps (kFusedCtr, zero between launches)
+  DevBuf dev_err;   // device status of the apply kernels (bit 3: a bounded wait ran out)
   bool count_sweeps = false;   // while a graph is captured: count sweep bytes and launches, no events
   DevBuf stencil_w; // per-node stencil weights (diagonal and neighbour couplings)
   DevBuf model_bf16; // rank-predictor parameters in BF16 (HIF_ID_LEARNED)
@@ -896,29 +894,6 @@ SweepShape tuned_shape(hif_handle* h, int op, const SweepLevel& S, int is_front,
   return best;
 }
 
-// First level of the fused F^-1 sweeps (kernels_apply.cu, k_apply_fused):
-// the lowest level l >= 1 whose cells number at most two per SM, so that
-// every level from there on has fewer blocks than resident CTAs.  L: none.
-// HIF_FUSE_LEVEL=l forces the level (l >= L: separate launches only).
-int fused_from(const hif_handle* h) {
-  const int L = h->G.L;
-  if (h->root.nblocks != 1 || !h->fuse_ctr.p) return L;
-  static const int forced = [] {
-    const char* e = getenv("HIF_FUSE_LEVEL");
-    return e ? atoi(e) : -1;
-  }();
-  if (forced >= 0) return forced < 1 ? 1 : (forced > L ? L : forced);
-  static const int nsm = [] {
-    int dev = 0, n = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    return n > 0 ? n : 1;
-  }();
-  for (int l = 1; l < L; ++l)
-    if (h->cells[l].nblocks <= 2 * nsm) return l;
-  return L;
-}
-
 template <typename T>
 void run_apply(hif_handle* h, int mode, T* x, int nrhs) {
   const int L = h->G.L;
@@ -960,74 +935,17 @@ void run_apply(hif_handle* h, int mode, T* x, int nrhs) {
     if (sizeof(T) == sizeof(float)) return reinterpret_cast<const T*>(fac_f32(S));
     return S.fac.as<T>();
   };
-  // F^-1: the levels from lf up, the root and their down sweeps in one
-  // persistent launch (levels with few blocks each)
-  const int lf = (mode == HIF_APPLY_FINV) ? fused_from(h) : L;
-  for (int l = 0; l < lf; ++l) {
+  for (int l = 0; l < L; ++l) {
     sweep(h->cells[l], up, 0, facp(h->cells[l]));
     sweep(h->fronts[l], up, 1, facp(h->fronts[l]));
   }
-  bool fused = false;
-  if (lf < L) {
-    FusedPlan plan{};
-    int t = 0;
-    double bytes = 0.0;
-    auto add = [&](const SweepLevel& S, int op, int is_front) {
-      if (S.nblocks == 0) return;
-      FusedLevel& f = plan.lev[plan.nlev++];
-      f = FusedLevel{S.desc, S.ipool, facp(S), S.nblocks, t, op, is_front, 0, S.max_np, S.max_nq};
-      t += S.nblocks;
-      bytes += sweep_bytes(S, op);
-    };
-    for (int l = lf; l < L; ++l) {
-      add(h->cells[l], 0, 0);
-      add(h->fronts[l], 0, 1);
-    }
-    add(h->root, 4, 0);
-    for (int l = L - 1; l >= lf; --l) {
-      add(h->fronts[l], 1, 1);
-      add(h->cells[l], 1, 0);
-    }
-    plan.ntasks = t;
-    if (prof) {
-      if (h->ev_used + 2 > h->ev_pool.size()) {
-        for (int k = 0; k < 64; ++k) {
-          cudaEvent_t e;
-          CU(cudaEventCreate(&e));
-          h->ev_pool.push_back(e);
-        }
-      }
-      CU(cudaEventRecord(h->ev_pool[h->ev_used], st));
-    }
-    int nl = 0;
-    fused = launch_sweep_fused<T>(plan, x, nrhs, nrhs, static_cast<unsigned*>(h->fuse_ctr.p),
-                                  h->dev_err.as<int>(), st, &nl);
-    if (prof) {
-      CU(cudaEventRecord(h->ev_pool[h->ev_used + 1], st));
-      h->ev_used += 2;
-    }
-    if (fused && count) {
-      h->prof_launches += nl;
-      h->prof_bytes += bytes;
-    }
+  if (mode == HIF_APPLY_FINV) {
+    sweep(h->root, 4, 0, facp(h->root));   // D^-1: the root's up and down sweeps in one launch
+  } else {
+    sweep(h->root, up, 0, facp(h->root));
+    sweep(h->root, down, 0, facp(h->root));
   }
-  if (!fused) {
-    for (int l = lf; l < L; ++l) {
-      sweep(h->cells[l], up, 0, facp(h->cells[l]));
-      sweep(h->fronts[l], up, 1, facp(h->fronts[l]));
-    }
-    if (mode == HIF_APPLY_FINV) {
-      sweep(h->root, 4, 0, facp(h->root));   // D^-1: the root's up and down sweeps in one launch
-    } else {
-      sweep(h->root, up, 0, facp(h->root));
-      sweep(h->root, down, 0, facp(h->root));
-    }
-    for (int l = L - 1; l >= lf; --l) {
-      sweep(h->fronts[l], down, 1, facp(h->fronts[l]));
-      sweep(h->cells[l], down, 0, facp(h->cells[l]));
-    }
-  }
-  for (int l = lf - 1; l >= 0; --l) {
+  for (int l = L - 1; l >= 0; --l) {
     sweep(h->fronts[l], down, 1, facp(h->fronts[l]));
     sweep(h->cells[l], down, 0, facp(h->cells[l]));
   }
@@ -1592,8 +1510,7 @@ int check_dev_err(hif_handle* h) {
   CU(cudaStreamSynchronize(h->st));
   if (e) {
     CU(cudaMemsetAsync(h->dev_err.p, 0, sizeof(int), h->st));
-    throw HifError(HIF_ERR_TIMEOUT, (e & 64) ? "a fused sweep's bounded wait for the previous level ran out"
-                                             : "a bounded wait for a bulk copy into shared memory ran out");
+    throw HifError(HIF_ERR_TIMEOUT, "a bounded wait for a bulk copy into shared memory ran out");
   }
   return HIF_OK;
 }
@@ -1740,8 +1657,6 @@ int hif_factor(const hif_grid* grid, const double* a_stag, const double* b, cons
     const int64_t na = (int64_t)grid->n * h->G.N / (grid->n - 1) * grid->dim;
     h->dev_err.alloc(sizeof(int), h->st);
     CU(cudaMemsetAsync(h->dev_err.p, 0, sizeof(int), h->st));
-    h->fuse_ctr.alloc(sizeof(unsigned) * kFusedCtr, h->st);
-    CU(cudaMemsetAsync(h->fuse_ctr.p, 0, sizeof(unsigned) * kFusedCtr, h->st));
     h->a_stag.alloc(sizeof(double) * na, h->st);
     h->bnode.alloc(sizeof(double) * h->G.N, h->st);
     CU(cudaMemcpyAsync(h->a_stag.p, a_stag, sizeof(double) * na, cudaMemcpyDefault, h->st));

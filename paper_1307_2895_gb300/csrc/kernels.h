@@ -104,34 +104,6 @@ struct SweepShape {
   int threads = 0;
   int staged = -1;
 };
-
-// The F^-1 sweeps of the upper levels in one persistent launch: the
-// sub-levels (cells or fronts of one level, one direction, or the root) in
-// dependency order, each a list of blocks; task t of the launch is block
-// t - first of the sub-level holding it.
-constexpr int kMaxFused = 56;
-struct FusedLevel {
-  const ApplyDesc* desc;
-  const int* ipool;
-  const void* fac;      // T*
-  int nblocks, first;
-  int op;               // 0 up (V^T), 1 down (V), 4 the root (up, then down)
-  int is_front, staged, max_np, max_nq;
-};
-struct FusedPlan {
-  int nlev, ntasks;
-  FusedLevel lev[kMaxFused];
-};
-// Counters of the fused launch (kFusedCtr unsigned, zero before the first
-// launch; every launch leaves them zero): [0] task ticket, [1 + s] blocks of
-// sub-level s done, [kMaxFused + 1] blocks that left.
-constexpr int kFusedCtr = kMaxFused + 2;
-// Launches the plan over the right-hand sides in column chunks; returns false
-// (nothing launched) when its blocks' vectors do not fit the shared memory of
-// one launch.  *launches receives the number of kernel launches.
-template <typename T>
-bool launch_sweep_fused(FusedPlan plan, T* x, int nrhs, int ldx, unsigned* ctr, int* err, cudaStream_t st,
-                        int* launches);
 template <typename T>
 void launch_sweep(int op, const ApplyDesc* blocks, int nblocks, const int* ipool, const T* fac, T* x,
                   int nrhs, int ldx, int is_front, int max_np, int max_nq, int* err, cudaStream_t st,

@@ -45,20 +45,12 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
 // with a bounded spin.  Regions are 16-byte aligned with sizes that are
 // multiples of 16 bytes.  Returns false (and sets bit 3 of *err) if the wait
 // ran out; the block then waits once more, bounded, for its copies to land.
-// With phase >= 0 the mbarrier was initialized once by the caller and is
-// reused: this copy completes its phase `phase` (parity phase & 1).
 struct BulkStage {
   uint64_t* mbar;
-  int phase = -1;
   __device__ void start(int nreg, void* const* dst, const void* const* src, const uint32_t* bytes) {
     if (threadIdx.x == 0) {
-      if (phase < 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-      } else {
-        // the regions were last touched by ordinary loads and stores
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      }
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)) : "memory");
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
       uint32_t total = 0;
       for (int k = 0; k < nreg; ++k) total += bytes[k];
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(total)
@@ -74,11 +66,10 @@ struct BulkStage {
   }
   __device__ bool try_wait() const {
     uint32_t ok;
-    const uint32_t parity = phase < 0 ? 0u : (uint32_t)(phase & 1);
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
         : "=r"(ok)
-        : "r"(smem_u32(mbar)), "r"(parity)
+        : "r"(smem_u32(mbar))
         : "memory");
     return ok != 0;
   }
@@ -151,7 +142,7 @@ __device__ __forceinline__ void pdl_wait_then_release() {
 template <typename T, int R, bool L2, typename Wait>
 __device__ void sweep_up_block(const ApplyDesc& bd, const int* __restrict__ ipool, const T* __restrict__ fac,
                                T* __restrict__ x, int nr, int ldx, int is_front, int staged, int* err,
-                               unsigned char* smem_raw, Wait wait, int phase = -1) {
+                               unsigned char* smem_raw, Wait wait) {
   constexpr int CG = ColGroup<R>::CG, NG = ColGroup<R>::NG;
   const int np = bd.np, nq = bd.nq;
   if (np == 0) {
@@ -161,7 +152,7 @@ __device__ void sweep_up_block(const ApplyDesc& bd, const int* __restrict__ ipoo
   const int* idp = ipool + bd.ids;
   const int* idq = idp + np;
   SweepSmem<T, R> sm(smem_raw, np, nq, staged, is_front);
-  BulkStage bs{sm.mbar, phase};
+  BulkStage bs{sm.mbar};
   const T* Linv = fac + bd.Linv;
   const T* G = fac + bd.G;
   const T* Tm = is_front ? fac + bd.T : nullptr;
@@ -245,7 +236,7 @@ __global__ void k_apply_up(const ApplyDesc* __restrict__ blocks, const int* __re
 template <typename T, int R, bool L2, typename Wait>
 __device__ void sweep_down_block(const ApplyDesc& bd, const int* __restrict__ ipool, const T* __restrict__ fac,
                                  T* __restrict__ x, int nr, int ldx, int is_front, int staged, int* err,
-                                 unsigned char* smem_raw, Wait wait, int phase = -1) {
+                                 unsigned char* smem_raw, Wait wait) {
   constexpr int CG = ColGroup<R>::CG, NG = ColGroup<R>::NG;
   const int np = bd.np, nq = bd.nq;
   if (np == 0) {
@@ -255,7 +246,7 @@ __device__ void sweep_down_block(const ApplyDesc& bd, const int* __restrict__ ip
   const int* idp = ipool + bd.ids;
   const int* idq = idp + np;
   SweepSmem<T, R> sm(smem_raw, np, nq, staged, is_front);
-  BulkStage bs{sm.mbar, phase};
+  BulkStage bs{sm.mbar};
   const T* Linv = fac + bd.Linv;
   const T* G = fac + bd.G;
   const T* Tm = is_front ? fac + bd.T : nullptr;
@@ -350,86 +341,6 @@ __global__ void k_apply_root(const ApplyDesc* __restrict__ blocks, const int* __
   });
   __syncthreads();
   sweep_down_block<T, R, false>(bd, ipool, fac, x, nr, ldx, 0, 0, err, smem_raw, [] { return true; });
-}
-
-// ---- the upper levels in one persistent launch -------------------------------
-// Above the first levels a sub-level holds few blocks, and as a launch of its
-// own each costs a launch latency (about 5-10 us) whatever its size.  Here
-// every block of the fused sub-levels is a task, numbered in dependency
-// order; each resident CTA takes the next task from a ticket counter, starts
-// the bulk copy of the block's factor, waits until every block of the
-// previous sub-level is done (a counter per sub-level, bounded spin), then
-// runs the block body of the separate launches with its vector rows read
-// through L2.  Tasks are taken in order, so the blocks a task waits for were
-// taken by CTAs that are running: no task waits on one that is not
-// scheduled.  A wait that runs out sets bit 6 of *err and the task counts as
-// done without its work (every CTA still finishes).  The last CTA to leave
-// zeroes the counters for the next launch.
-template <typename T, int R>
-__global__ void __launch_bounds__(256) k_apply_fused(const __grid_constant__ FusedPlan plan, T* __restrict__ x,
-                                                     int nr, int ldx, unsigned* __restrict__ ctr, int* err) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int s_task, s_go;
-  if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(smem_raw)) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  pdl_wait_then_release();
-  int phase = 0;
-  for (;;) {
-    __syncthreads();
-    if (threadIdx.x == 0) s_task = (int)atomicAdd(ctr, 1u);
-    __syncthreads();
-    const int t = s_task;
-    if (t >= plan.ntasks) break;
-    int s = 0;
-    while (s + 1 < plan.nlev && plan.lev[s + 1].first <= t) ++s;
-    const FusedLevel& fl = plan.lev[s];
-    const ApplyDesc bd = fl.desc[t - fl.first];
-    const T* fac = static_cast<const T*>(fl.fac);
-    auto wait = [&]() -> bool {
-      if (threadIdx.x == 0) {
-        int ok = 1;
-        if (s > 0) {
-          const unsigned need = (unsigned)plan.lev[s - 1].nblocks;
-          const volatile unsigned* done = ctr + s;          // sub-level s - 1
-          long it = 0;
-          while (*done < need) {
-            if (++it > (1L << 24)) {                         // ~1 s: a predecessor never finished
-              atomicOr(err, 64);
-              ok = 0;
-              break;
-            }
-            __nanosleep(32);
-          }
-        }
-        __threadfence();
-        s_go = ok;
-      }
-      __syncthreads();
-      return s_go != 0;
-    };
-    if (fl.op == 0) {
-      sweep_up_block<T, R, true>(bd, fl.ipool, fac, x, nr, ldx, fl.is_front, fl.staged, err, smem_raw, wait, phase);
-    } else if (fl.op == 1) {
-      sweep_down_block<T, R, true>(bd, fl.ipool, fac, x, nr, ldx, fl.is_front, fl.staged, err, smem_raw, wait,
-                                   phase);
-    } else {
-      sweep_up_block<T, R, true>(bd, fl.ipool, fac, x, nr, ldx, 0, fl.staged, err, smem_raw, wait, phase);
-      __syncthreads();
-      sweep_down_block<T, R, true>(bd, fl.ipool, fac, x, nr, ldx, 0, 0, err, smem_raw, [] { return true; });
-    }
-    if (fl.staged && bd.np > 0) ++phase;                     // the mbarrier completed one phase
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      __threadfence();
-      atomicAdd(ctr + 1 + s, 1u);
-    }
-  }
-  if (threadIdx.x == 0 && atomicAdd(ctr + kMaxFused + 1, 1u) == gridDim.x - 1) {
-    for (int i = 0; i < kFusedCtr; ++i) ctr[i] = 0u;
-    __threadfence();
-  }
 }
 
 // ---- forward operator F (used by the error estimates; not staged) ----------
@@ -611,73 +522,8 @@ void launch_sweep(int op, const ApplyDesc* blocks, int nblocks, const int* ipool
   }
 }
 
-template <typename T, int R>
-static bool launch_fused_R(FusedPlan plan, T* x, int nr, int ldx, unsigned* ctr, int* err, cudaStream_t st) {
-  size_t smem = 16;
-  for (int s = 0; s < plan.nlev; ++s) {
-    FusedLevel& fl = plan.lev[s];
-    const size_t vsm = vec_smem<T>(R, fl.max_np, fl.max_nq);
-    const size_t ssm = stage_smem<T>(fl.max_np, fl.max_nq, fl.op == 4 ? 0 : fl.is_front);
-    fl.staged = (vsm + ssm <= kStageCap) ? 1 : 0;
-    const size_t need = vsm + (fl.staged ? ssm : 0);
-    smem = need > smem ? need : smem;
-  }
-  if (smem > kSweepSmemCap) return false;
-  static std::atomic<bool> attr_set{false};
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_apply_fused<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSweepSmemCap);
-    cudaFuncSetAttribute(k_apply_fused<T, R>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    attr_set = true;
-  }
-  int dev = 0, nsm = 0, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_apply_fused<T, R>, 256, smem) != cudaSuccess ||
-      per_sm < 1) {
-    cudaGetLastError();
-    return false;
-  }
-  const int64_t resident = (int64_t)per_sm * nsm;
-  const int grid = (int)(resident < plan.ntasks ? resident : plan.ntasks);
-  note_launches(1);
-  k_apply_fused<T, R><<<grid, 256, smem, st>>>(plan, x, nr, ldx, ctr, err);
-  return true;
-}
-
-template <typename T>
-bool launch_sweep_fused(FusedPlan plan, T* x, int nrhs, int ldx, unsigned* ctr, int* err, cudaStream_t st,
-                        int* launches) {
-  *launches = 0;
-  if (plan.nlev <= 0 || plan.ntasks <= 0) return false;
-  int max_np = 0, max_nq = 0;
-  for (int s = 0; s < plan.nlev; ++s) {
-    max_np = plan.lev[s].max_np > max_np ? plan.lev[s].max_np : max_np;
-    max_nq = plan.lev[s].max_nq > max_nq ? plan.lev[s].max_nq : max_nq;
-  }
-  const int R = sweep_chunk<T>(max_np, max_nq, nrhs);
-  // feasibility of the widest chunk decides for every chunk
-  for (int r0 = 0; r0 < nrhs; r0 += R) {
-    const int nr = (nrhs - r0) < R ? (nrhs - r0) : R;
-    T* xr = x + r0;
-    bool ok = false;
-    switch (R) {
-      case 32: ok = launch_fused_R<T, 32>(plan, xr, nr, ldx, ctr, err, st); break;
-      case 16: ok = launch_fused_R<T, 16>(plan, xr, nr, ldx, ctr, err, st); break;
-      case 8: ok = launch_fused_R<T, 8>(plan, xr, nr, ldx, ctr, err, st); break;
-      case 4: ok = launch_fused_R<T, 4>(plan, xr, nr, ldx, ctr, err, st); break;
-      case 2: ok = launch_fused_R<T, 2>(plan, xr, nr, ldx, ctr, err, st); break;
-      default: ok = launch_fused_R<T, 1>(plan, xr, nr, ldx, ctr, err, st); break;
-    }
-    if (!ok) return false;   // the same for every chunk: only the first can fail
-    ++*launches;
-  }
-  return true;
-}
-
 template void launch_sweep<double>(int, const ApplyDesc*, int, const int*, const double*, double*,
                                    int, int, int, int, int, int*, cudaStream_t, SweepShape);
-template bool launch_sweep_fused<double>(FusedPlan, double*, int, int, unsigned*, int*, cudaStream_t, int*);
-template bool launch_sweep_fused<float>(FusedPlan, float*, int, int, unsigned*, int*, cudaStream_t, int*);
 template void launch_sweep<float>(int, const ApplyDesc*, int, const int*, const float*, float*,
                                   int, int, int, int, int, int*, cudaStream_t, SweepShape);
 
