@@ -55,8 +55,17 @@ typedef enum hif_status {
 } hif_status;
 
 /* Variants (Section 5 names): MF = mf2/mf3 (Algorithm 3.1, exact),
- * HIFDE = hifde2/hifde3 (Algorithm 4.1; faces only in 3D). */
-enum { HIF_VARIANT_MF = 0, HIF_VARIANT_HIFDE = 1 };
+ * HIFDE = hifde2/hifde3 (Algorithm 4.1; faces only in 3D), HIFDE3X = hifde3x
+ * (Section 4.5, Algorithm 4.2, dim 3 only): after the cells and faces of a
+ * level, the edges are skeletonized too (from level 1 on, the paper's rule of
+ * thumb read as skipping level 0), and from level 2 on the cells are built
+ * algebraically (Voronoi cells of the active DOFs about the cell centers,
+ * peeled so that no two are coupled) and the faces and edges are Voronoi
+ * groups about their centers; a DOF equidistant to two or more nearest
+ * centers joins no group.  Needs n divisible by 2^L; from level 1's edges on
+ * the active matrix is held as one dense matrix of the DOFs active at that
+ * point (HIF_ERR_ARG if that would exceed 48 GB). */
+enum { HIF_VARIANT_MF = 0, HIF_VARIANT_HIFDE = 1, HIF_VARIANT_HIFDE3X = 2 };
 
 /* Arithmetic of the factorization.  FP64: every block operation in double.
  * MIXED: cell and front blocks, the factor and the apply of F^-1 in float;
@@ -287,6 +296,8 @@ int hif_stats(const hif_handle* h, hif_stats_t* st);
  * hif_structure -- the skeleton structure, for parity checks against the
  * oracle.  Writes int32 records, one per skeletonized front in level order:
  *   level, |c|, k, c[0..|c|-1] (ascending global indices),
+ * (level: l for the fronts of level l + 1/2; for HIFDE3X 2l for the faces of
+ * level l + 1/3 and 2l + 1 for the edges of level l + 2/3)
  *   s[0..k-1] (skeleton global indices in pivot order)
  * followed by the terminator -1 and then |s_L|.  If buf is NULL or cap is too
  * small, nothing is written; *needed receives the number of int32 required.
@@ -310,6 +321,28 @@ int hif_profile(hif_handle* h, int enable, hif_profile_t* out);
 
 /* hif_kernel_launches -- kernels launched by this library in this process. */
 long long hif_kernel_launches(void);
+
+/*
+ * hif_wait_selftest -- exercises one of the library's bounded device waits
+ * on an object that nothing completes, with a short bound, and reports it
+ * through the same status path as the real wait (no counterpart in the
+ * paper; it checks the failure detection of the apply sweeps, the
+ * multi-block pivoted QR and the tensor-core Schur update without faulting
+ * or hanging the GPU):
+ *   which 0: the wait for a bulk copy into shared memory (F^-1 sweeps), a
+ *            phase whose bytes are announced and never copied; limit = polls;
+ *   which 1: the group barrier of the multi-block QR, one block of a group of
+ *            two; limit = polls;
+ *   which 2: the wait for tensor-core MMAs, a CTA holding its tensor memory
+ *            and issuing no MMA (it frees the memory after the wait gives
+ *            up); limit = nanoseconds.
+ * limit must lie in 1 .. the production bound (2^26, 2^22 polls; 1e9 ns).
+ * Returns HIF_ERR_TIMEOUT with the real wait's message when the wait gave up
+ * (the expected outcome), HIF_OK if it completed, HIF_ERR_ARG for a bad
+ * which or limit.  Work is issued on stream (NULL: the legacy default
+ * stream) and the call returns after it has completed.
+ */
+int hif_wait_selftest(int which, long long limit, void* stream);
 
 /*
  * hif_residual_norms_noalloc -- rnorm2[r] = ||f_r - A x_r||_2^2 (FP64) for the

@@ -34,6 +34,7 @@
 #include "hif_internal.h"
 #include "host_pool.h"
 #include "kernels.h"
+#include "symbolic3x.h"
 
 using namespace hif;
 
@@ -211,7 +212,8 @@ struct hif_handle {
   DevBuf stencil_w; // per-node stencil weights (diagonal and neighbour couplings)
   DevBuf model_bf16; // rank-predictor parameters in BF16 (HIF_ID_LEARNED)
   std::shared_ptr<const Level0> level0;
-  std::vector<SweepLevel> cells, fronts;   // levels 0..L-1
+  std::vector<SweepLevel> cells, fronts;   // levels 0..L-1 (fronts: 2D edges, 3D faces)
+  std::vector<SweepLevel> edges;           // levels 0..L-1: hifde3x's edge groups (level l + 2/3)
   SweepLevel root;                         // level L
   std::vector<LevelFronts> finfo;
   int root_size = 0, n_cells = 0, n_fronts = 0, max_rank = 0, near = 0, clamped = 0;
@@ -402,6 +404,16 @@ std::shared_ptr<const Level0> get_level0(const Geometry& G) {
   return L0;
 }
 
+// The bounded device waits report through status bits; each maps to one
+// timeout message, the same wherever the wait runs.
+constexpr int kWaitBulk = 8, kWaitGroup = 16, kWaitMma = 32;
+void throw_wait_status(int bits) {
+  if (bits & kWaitBulk) throw HifError(HIF_ERR_TIMEOUT, "a bounded wait for a bulk copy into shared memory ran out");
+  if (bits & kWaitGroup)
+    throw HifError(HIF_ERR_TIMEOUT, "a bounded group-barrier wait of the multi-block pivoted QR ran out");
+  if (bits & kWaitMma) throw HifError(HIF_ERR_TIMEOUT, "a bounded wait for tensor-core MMAs ran out");
+}
+
 template <typename T>
 struct Factorizer {
   hif_handle* h;
@@ -414,8 +426,181 @@ struct Factorizer {
   // (including the FP64 root, whose entries carry FP32 rounding), none in FP64
   double tau = 0.0;
 
+  // hifde3x: the symbolic stage that follows the factorization (pattern of
+  // A_l and every index set from level 1's edges on)
+  bool x3 = false;
+  std::unique_ptr<Symbolic3x> sym;
+
   explicit Factorizer(hif_handle* h_) : h(h_), G(h_->G), st(h_->st) {
     tau = (h_->precision == HIF_PREC_MIXED) ? 4e-6 : 0.0;
+  }
+
+  // The symbolic stage follows the box levels: cells eliminated, then the
+  // fronts skeletonized with the skeletons the IDs chose (pivot order).
+  void sym_cells(const std::vector<HostCell>& cells) {
+    if (!sym) return;
+    for (const HostCell& c : cells)
+      if (!c.I.empty()) sym->eliminate(c.I);
+  }
+  void sym_fronts() {
+    if (!sym) return;
+    const LevelFronts& info = h->finfo.back();
+    const std::vector<HostFront>& fr = *info.fr;
+    const std::vector<FrontDesc>& fd = *info.fd;
+    for (size_t f = 0; f < fr.size(); ++f) {
+      const int* out = info.out.data() + fd[f].out;
+      const std::vector<int> s(out + 1 + fd[f].nc, out + 1 + fd[f].nc + out[0]);
+      if (sym->skeletonize(fr[f].c, s) == -2) throw HifError(HIF_ERR_HOST, "symbolic stage out of step with the IDs");
+    }
+  }
+
+  // hifde3x from level 1's edges on (Section 4.5, Algorithm 4.2), on A_l held
+  // as one dense matrix of the DOFs active at the hand-over (kernels_dense3x.cu):
+  // the edges of level 1, then per level l >= 2 the algebraic cells (Lemma
+  // 2.1), the faces and the edges (Lemma 2.4), then the root.  cd1 / d_cd1 /
+  // ip1 / work1: the level-1 cells, their ids and their update matrices
+  // after the level-1 faces.
+  static constexpr double kDenseMaxBytes = 48e9;
+  void dense_stage(const std::vector<CellDesc>& cd1, const CellDesc* d_cd1, const int* ip1, DevBuf& work1) {
+    const int L = G.L;
+    const std::vector<int> act = sym->active();
+    const int64_t n_act = (int64_t)act.size();
+    if ((double)n_act * (double)n_act * sizeof(T) > kDenseMaxBytes)
+      throw HifError(HIF_ERR_ARG, "hifde3x keeps its upper levels as one dense matrix of the DOFs active after "
+                                  "level 1's faces: too many of them for this grid");
+    std::vector<int> hmap(G.N, -1);
+    for (int64_t i = 0; i < n_act; ++i) hmap[act[i]] = (int)i;
+    DevBuf dmap, Abuf;
+    upload(dmap, hmap, st);
+    Abuf.alloc((size_t)(n_act * n_act) * sizeof(T), st);
+    CU(cudaMemsetAsync(Abuf.p, 0, Abuf.bytes, st));
+    int max_nB = 0;
+    for (const CellDesc& c : cd1) max_nB = std::max(max_nB, c.nB);
+    launch_dense_from_cells<T, T>(d_cd1, (int)cd1.size(), ip1, work1.as<T>(), max_nB, dmap.as<int>(),
+                                  Abuf.as<T>(), n_act, st);
+    CU(cudaGetLastError());
+    work1.release();
+    // the front kernels see A through one cell without interior: U = A, ld = n_act
+    CellDesc whole{};
+    whole.nI = 0;
+    whole.nB = (int)n_act;
+    whole.cmap = -1;
+    for (int s = 0; s < kMaxChild; ++s) whole.child[s] = -1;
+    DevBuf d_whole;
+    upload(d_whole, std::vector<CellDesc>{whole}, st);
+    std::vector<int> no_alive;
+    auto groups = [&](int l, int kind) {
+      const std::vector<std::vector<int>> gs = sym->groups(l, kind);
+      if (gs.empty()) return;
+      auto fr = std::make_shared<std::vector<HostFront>>(gs.size());
+      for (size_t g = 0; g < gs.size(); ++g) {   // (the symbolic stage's queries share scratch: one at a time)
+        HostFront& F = (*fr)[g];
+        F.axis = kind;
+        F.P1 = F.P2 = 0;
+        F.c = gs[g];
+        F.N = sym->neighbors(F.c);
+        F.pos1.resize(F.c.size() + F.N.size());
+        for (size_t i = 0; i < F.c.size(); ++i) F.pos1[i] = hmap[F.c[i]];
+        for (size_t i = 0; i < F.N.size(); ++i) F.pos1[F.c.size() + i] = hmap[F.N[i]];
+        F.pos2.assign(F.pos1.size(), -1);
+      }
+      auto fd = std::make_shared<std::vector<FrontDesc>>();
+      std::vector<int> ip;
+      int64_t fw = 0, ff = 0, fo = 0;
+      int mnc = 0, mnN = 0;
+      prepare_fronts(*fr, *fd, ip, fw, ff, fo, mnc, mnN);
+      DevBuf d_fd, d_ip;
+      upload(d_fd, *fd, st);
+      upload(d_ip, ip, st);
+      const size_t nfi = h->finfo.size();
+      run_fronts(l, d_whole.as<CellDesc>(), Abuf, no_alive, fr, fd, d_fd.as<FrontDesc>(), d_ip.as<int>(), fw, ff, fo,
+                 mnc, mnN, kind == 1 ? h->fronts[l] : h->edges[l], 2 * l + (kind == 2 ? 1 : 0));
+      if (h->finfo.size() > nfi) sym_fronts();
+    };
+    groups(1, 2);
+    for (int l = 2; l < L; ++l) {
+      const std::vector<std::vector<int>> P = sym->cells(l);
+      std::vector<std::vector<int>> Q(P.size());
+      for (size_t i = 0; i < P.size(); ++i) Q[i] = sym->neighbors(P[i]);
+      std::vector<CellDesc> cd(P.size());
+      std::vector<int> ip;
+      int64_t we = 0, fe = 0;
+      int max_nF = 0;
+      for (size_t i = 0; i < P.size(); ++i) {
+        CellDesc& d = cd[i];
+        d.nI = (int)P[i].size();
+        d.nB = (int)Q[i].size();
+        d.cell_lin = (int)i;
+        d.ids = (int64_t)ip.size();
+        ip.insert(ip.end(), P[i].begin(), P[i].end());
+        ip.insert(ip.end(), Q[i].begin(), Q[i].end());
+        d.F = we;
+        we += (int64_t)d.nI * d.nI + (int64_t)d.nB * d.nI + (int64_t)d.nB * d.nB + cell_x_elems(d.nI);
+        d.fac = fe;
+        fe += cell_fac_size(d.nI, d.nB);
+        d.cmap = -1;
+        for (int s = 0; s < kMaxChild; ++s) d.child[s] = -1;
+        max_nF = std::max(max_nF, d.nI + d.nB);
+      }
+      SweepLevel& sw = h->cells[l];
+      DevBuf ddesc, cw, selbuf, tdbuf;
+      upload(ddesc, cd, st);
+      upload(sw.ipool_own, ip, st);
+      sw.ipool = sw.ipool_own.as<int>();
+      cw.alloc((size_t)we * sizeof(T), st);
+      sw.fac.alloc((size_t)fe * sizeof(T), st);
+      const CellDesc* dd = ddesc.as<CellDesc>();
+      launch_dense_cells<T>(0, dd, (int)cd.size(), sw.ipool, max_nF, dmap.as<int>(), Abuf.as<T>(), n_act,
+                            cw.as<T>(), st);
+      factor_cells<T>(cd, dd, cw.as<T>(), sw.fac.as<T>(), selbuf, tdbuf);
+      launch_dense_cells<T>(1, dd, (int)cd.size(), sw.ipool, max_nF, dmap.as<int>(), Abuf.as<T>(), n_act,
+                            cw.as<T>(), st);
+      CU(cudaGetLastError());
+      std::vector<ApplyDesc> ad;
+      cell_apply_descs(cd, ad, sw.max_np, sw.max_nq, sw.fac_elems, sw.vec_rows);
+      sw.nblocks = (int)ad.size();
+      upload(sw.desc_own, ad, st);
+      sw.desc = sw.desc_own.as<ApplyDesc>();
+      account_cells(cd, sizeof(T));
+      for (const std::vector<int>& p : P)
+        if (!p.empty()) sym->eliminate(p);
+      groups(l, 1);
+      groups(l, 2);
+    }
+    // the root: D = A on the DOFs still active, factored in FP64
+    const std::vector<int> rt = sym->active();
+    std::vector<CellDesc> cd(1);
+    CellDesc& r = cd[0];
+    r.nI = (int)rt.size();
+    r.nB = 0;
+    r.ids = 0;
+    r.F = 0;
+    r.fac = 0;
+    r.cmap = -1;
+    for (int s = 0; s < kMaxChild; ++s) r.child[s] = -1;
+    SweepLevel& sw = h->root;
+    DevBuf ddesc, rw, selbuf, tdbuf;
+    upload(ddesc, cd, st);
+    upload(sw.ipool_own, rt, st);
+    sw.ipool = sw.ipool_own.as<int>();
+    const int64_t fe = cell_fac_size(r.nI, 0);
+    rw.alloc((size_t)((int64_t)r.nI * r.nI + cell_x_elems(r.nI)) * sizeof(double), st);
+    sw.fac.alloc((size_t)fe * sizeof(double), st);
+    launch_dense_gather_root<T, double>(sw.ipool, r.nI, dmap.as<int>(), Abuf.as<T>(), n_act, rw.as<double>(), st);
+    Abuf.release();
+    factor_cells<double>(cd, ddesc.as<CellDesc>(), rw.as<double>(), sw.fac.as<double>(), selbuf, tdbuf);
+    CU(cudaGetLastError());
+    std::vector<ApplyDesc> ad;
+    cell_apply_descs(cd, ad, sw.max_np, sw.max_nq, sw.fac_elems, sw.vec_rows);
+    sw.nblocks = (int)ad.size();
+    upload(sw.desc_own, ad, st);
+    sw.desc = sw.desc_own.as<ApplyDesc>();
+    account_cells(cd, sizeof(double));
+    h->root_size = r.nI;
+    if (sizeof(T) == sizeof(float) && fe > 0) {
+      sw.fac32.alloc((size_t)fe * sizeof(float), st);
+      launch_convert<double, float>(fe, 1, sw.fac.as<double>(), 1, sw.fac32.as<float>(), 1, st);
+    }
   }
 
   // Interior elimination of one level: cells with at least h->big_cell
@@ -489,7 +674,13 @@ struct Factorizer {
     dead.assign(G.N, 0);
     h->cells.resize(L);
     h->fronts.resize(L);
-    const bool skel = (h->variant == HIF_VARIANT_HIFDE) && h->eps > 0.0;
+    h->edges.resize(L);
+    const bool skel = (h->variant != HIF_VARIANT_MF) && h->eps > 0.0;
+    // hifde3x: its levels 0 and 1 (cells and faces) are hifde3's (Section 4.5
+    // skips the edges of level 0); the host replays them on the symbolic
+    // stage, which then gives every later index set
+    x3 = h->variant == HIF_VARIANT_HIFDE3X && L >= 2;
+    if (x3) sym.reset(new Symbolic3x(G.n, G.leaf, true));
     std::shared_ptr<const Level0> L0 = get_level0(G);
     h->level0 = L0;
 
@@ -513,11 +704,14 @@ struct Factorizer {
       sw.fac_elems = L0->cap_fac_elems;
       sw.vec_rows = L0->cap_vec_rows;
       account_cells(L0->cdesc, sizeof(T));
+      sym_cells(L0->cells);
     }
     std::vector<int> alive = L0->alive1;
     if (skel && 0 >= h->skip_levels) {
+      const size_t nfi = h->finfo.size();
       run_fronts(0, L0->d_cdesc, work, alive, L0->fronts, L0->fdesc, L0->d_fdesc, L0->d_fip, L0->fwork_elems,
-                 L0->ffac_elems, L0->fout_elems, L0->max_nc, L0->max_nN);
+                 L0->ffac_elems, L0->fout_elems, L0->max_nc, L0->max_nN, h->fronts[0], 0);
+      if (h->finfo.size() > nfi) sym_fronts();
     }
     const std::vector<HostCell>* prev_cells = &L0->cells;
     const CellDesc* prev_ddesc = L0->d_cdesc;
@@ -573,6 +767,7 @@ struct Factorizer {
         work.release();
         break;
       }
+      sym_cells(cells);
       {   // the eliminated interiors leave the active set
         for (const HostCell& c : cells)
           for (int g : c.I) dead[g] = 1;
@@ -593,7 +788,14 @@ struct Factorizer {
         DevBuf d_fd, d_ip;
         upload(d_fd, *fd, st);
         upload(d_ip, ip, st);
-        run_fronts(l, dd, work, alive, fr, fd, d_fd.as<FrontDesc>(), d_ip.as<int>(), fw, ff, fo, mnc, mnN);
+        const size_t nfi = h->finfo.size();
+        run_fronts(l, dd, work, alive, fr, fd, d_fd.as<FrontDesc>(), d_ip.as<int>(), fw, ff, fo, mnc, mnN,
+                   h->fronts[l], x3 ? 2 * l : l);
+        if (h->finfo.size() > nfi) sym_fronts();
+      }
+      if (x3 && l == 1) {   // hifde3x: the assembled upper levels from level 1's edges on
+        dense_stage(cdesc, dd, sw.ipool, work);
+        break;
       }
       prev_cells = &cells;
       prev_ddesc = dd;
@@ -607,26 +809,27 @@ struct Factorizer {
     h->sketched = hs2[2];
     h->fallback = hs2[3];
     if (hs & 1) throw HifError(HIF_ERR_NOT_SPD, "non-positive pivot in a diagonal-block Cholesky");
-    if (hs & 16) throw HifError(HIF_ERR_TIMEOUT, "a bounded group-barrier wait of the multi-block pivoted QR ran out");
-    if (hs & 32) throw HifError(HIF_ERR_TIMEOUT, "a bounded wait for tensor-core MMAs ran out");
+    throw_wait_status(hs & (kWaitGroup | kWaitMma));
   }
 
   // One launch for every front of level l + 1/2, then read back ranks and
   // skeletons, build the apply descriptors and drop the redundant DOFs.
+  // sw: the sweep level the fronts' factor goes to; frac: the fractional
+  // level recorded for hif_structure (l, or 2l / 2l + 1 for hifde3x's faces
+  // and edges).
   void run_fronts(int l, const CellDesc* d_cdesc, DevBuf& cwork, std::vector<int>& alive,
                   std::shared_ptr<const std::vector<HostFront>> fr, std::shared_ptr<const std::vector<FrontDesc>> fdp,
                   const FrontDesc* d_fd, const int* d_ip, int64_t work_elems, int64_t fac_elems,
-                  int64_t out_elems, int max_nc, int max_nN) {
+                  int64_t out_elems, int max_nc, int max_nN, SweepLevel& sw, int frac) {
     const std::vector<FrontDesc>& fd = *fdp;
     const int nf = (int)fd.size();
-    SweepLevel& sw = h->fronts[l];
     if (nf == 0) return;
     DevBuf fwork, obuf, pred, sketch;
     fwork.alloc((size_t)work_elems * sizeof(T), st);
     obuf.alloc((size_t)out_elems * sizeof(int), st);
     sw.fac.alloc((size_t)fac_elems * sizeof(T), st);
     LevelFronts info;
-    info.level = l;
+    info.level = frac;
     info.feats.alloc((size_t)nf * kFeat * sizeof(float), st);
     launch_front_features(d_fd, nf, d_ip, h->stencil_w.as<double>(), G.dim, G.n, l, h->eps, info.feats.as<float>(),
                           st);
@@ -819,6 +1022,7 @@ void demote_factor(hif_handle* h) {
   };
   for (auto& S : h->cells) demote(S);
   for (auto& S : h->fronts) demote(S);
+  for (auto& S : h->edges) demote(S);
   demote(h->root);
   h->factor_bytes /= 2;
   h->apply_bytes /= 2.0;
@@ -938,6 +1142,7 @@ void run_apply(hif_handle* h, int mode, T* x, int nrhs) {
   for (int l = 0; l < L; ++l) {
     sweep(h->cells[l], up, 0, facp(h->cells[l]));
     sweep(h->fronts[l], up, 1, facp(h->fronts[l]));
+    if (l < (int)h->edges.size()) sweep(h->edges[l], up, 1, facp(h->edges[l]));
   }
   if (mode == HIF_APPLY_FINV) {
     sweep(h->root, 4, 0, facp(h->root));   // D^-1: the root's up and down sweeps in one launch
@@ -946,6 +1151,7 @@ void run_apply(hif_handle* h, int mode, T* x, int nrhs) {
     sweep(h->root, down, 0, facp(h->root));
   }
   for (int l = L - 1; l >= 0; --l) {
+    if (l < (int)h->edges.size()) sweep(h->edges[l], down, 1, facp(h->edges[l]));
     sweep(h->fronts[l], down, 1, facp(h->fronts[l]));
     sweep(h->cells[l], down, 0, facp(h->cells[l]));
   }
@@ -1510,7 +1716,7 @@ int check_dev_err(hif_handle* h) {
   CU(cudaStreamSynchronize(h->st));
   if (e) {
     CU(cudaMemsetAsync(h->dev_err.p, 0, sizeof(int), h->st));
-    throw HifError(HIF_ERR_TIMEOUT, "a bounded wait for a bulk copy into shared memory ran out");
+    throw_wait_status(kWaitBulk);
   }
   return HIF_OK;
 }
@@ -1615,10 +1821,12 @@ int hif_factor(const hif_grid* grid, const double* a_stag, const double* b, cons
   if (!grid || !a_stag || !b) return set_error(HIF_ERR_ARG, "grid, a_stag and b are required");
   if (grid->dim != 2 && grid->dim != 3) return set_error(HIF_ERR_ARG, "dim must be 2 or 3");
   if (grid->n < 4 || grid->n > 1 << 15) return set_error(HIF_ERR_ARG, "n out of range");
-  if (grid->variant != HIF_VARIANT_MF && grid->variant != HIF_VARIANT_HIFDE)
+  if (grid->variant != HIF_VARIANT_MF && grid->variant != HIF_VARIANT_HIFDE && grid->variant != HIF_VARIANT_HIFDE3X)
     return set_error(HIF_ERR_ARG, "unknown variant");
+  if (grid->variant == HIF_VARIANT_HIFDE3X && grid->dim != 3)
+    return set_error(HIF_ERR_ARG, "HIFDE3X is the 3D variant (dim must be 3)");
   if (bc_vals) return set_error(HIF_ERR_ARG, "only zero Dirichlet data (bc_vals = NULL) is supported");
-  if (grid->variant == HIF_VARIANT_HIFDE && !(eps > 0.0 && eps < 1.0))
+  if (grid->variant != HIF_VARIANT_MF && !(eps > 0.0 && eps < 1.0))
     return set_error(HIF_ERR_ARG, "eps must be in (0, 1) for HIF-DE");
   const int prec = opts ? opts->precision : HIF_PREC_FP64;
   if (prec != HIF_PREC_FP64 && prec != HIF_PREC_MIXED && prec != HIF_PREC_FP32_APPLY)
@@ -1636,7 +1844,14 @@ int hif_factor(const hif_grid* grid, const double* a_stag, const double* b, cons
     h->gi.inv_h2 = (double)grid->n * (double)grid->n;
     h->precision = prec;
     h->variant = grid->variant;
-    h->eps = grid->variant == HIF_VARIANT_HIFDE ? eps : 0.0;
+    h->eps = grid->variant != HIF_VARIANT_MF ? eps : 0.0;
+    if (grid->variant == HIF_VARIANT_HIFDE3X) {
+      // Section 4.5's cells, faces and edges are Voronoi cells about the
+      // centers of a tree of 2^L boxes of equal width
+      if (grid->n % (1 << h->G.L) != 0)
+        throw HifError(HIF_ERR_ARG, "HIFDE3X needs n divisible by 2^L (boxes of equal width)");
+      if (opts && opts->skip_levels > 0) throw HifError(HIF_ERR_ARG, "HIFDE3X skips no levels");
+    }
     h->skip_levels = opts ? std::max(0, opts->skip_levels) : 0;
     h->id_mode = opts ? opts->id_mode : HIF_ID_QR;
     if (h->id_mode < HIF_ID_QR || h->id_mode > HIF_ID_LEARNED) throw HifError(HIF_ERR_ARG, "unknown id_mode");
@@ -1962,6 +2177,31 @@ int hif_profile(hif_handle* h, int enable, hif_profile_t* out) {
 
 long long hif_kernel_launches(void) { return g_launches.load(); }
 
+int hif_wait_selftest(int which, long long limit, void* stream) {
+  if (which < 0 || which > 2)
+    return set_error(HIF_ERR_ARG, "which must be 0 (bulk copy), 1 (group barrier) or 2 (tensor-core MMAs)");
+  const long long cap = which == 0 ? (1LL << 26) : which == 1 ? (1LL << 22) : 1000000000LL;
+  if (limit < 1 || limit > cap) return set_error(HIF_ERR_ARG, "limit must be in 1 .. the wait's own bound");
+  try {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    DevBuf buf;
+    buf.alloc(4 * sizeof(int), st);
+    CU(cudaMemsetAsync(buf.p, 0, 4 * sizeof(int), st));
+    int* bits = buf.as<int>();
+    if (which == 0) launch_wait_test_bulk(bits, (long)limit, st);
+    else if (which == 1) launch_wait_test_group(reinterpret_cast<unsigned*>(bits + 2), bits, (long)limit, st);
+    else launch_wait_test_mma(bits, (uint64_t)limit, st);
+    CU(cudaGetLastError());
+    int e = 0;
+    CU(cudaMemcpyAsync(&e, bits, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    throw_wait_status(e);
+    set_last_error("");
+    return HIF_OK;
+  }
+  HIF_CATCH
+}
+
 // Batches: one problem per task, tasks pulled by a small pool of host threads
 // (each handle works on its own stream, so different problems overlap).
 static int run_batch(int nprob, int nthreads, const std::function<int(int)>& task) {
@@ -2133,7 +2373,7 @@ int hif_schur_update_f32(int nb, int m, int k, const float* G, float* U, int spl
     int hs = 0;
     CU(cudaMemcpyAsync(&hs, status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
-    if (hs & 32) throw HifError(HIF_ERR_TIMEOUT, "a bounded wait for tensor-core MMAs ran out");
+    throw_wait_status(hs & kWaitMma);
   } HIF_CATCH
   return HIF_OK;
 }

@@ -82,6 +82,26 @@ void launch_bigfront_scatter(const FrontDesc* fronts, const int* big, int nbig, 
                              cudaStream_t st);
 int bigfront_colmax_blocks(int max_nc);
 
+// assembled upper levels of hifde3x (kernels_dense3x.cu): A is n_act x
+// n_act, row-major; map[g] is the row of global DOF g (-1: not held)
+template <typename TU, typename TA>
+void launch_dense_from_cells(const CellDesc* cells, int ncells, const int* ipool, const TU* work, int max_nB,
+                             const int* map, TA* A, int64_t n_act, cudaStream_t st);
+// phase 0: gather F_II = A_pp, F_BI = A_qp, F_BB = 0; phase 1: A_qq += F_BB
+template <typename T>
+void launch_dense_cells(int phase, const CellDesc* cells, int ncells, const int* ipool, int max_nF,
+                        const int* map, T* A, int64_t n_act, T* work, cudaStream_t st);
+template <typename TA, typename TD>
+void launch_dense_gather_root(const int* ids, int n, const int* map, const TA* A, int64_t n_act, TD* D,
+                              cudaStream_t st);
+
+// checks of the bounded device waits (each on an object nothing completes):
+// the sweeps' bulk-copy wait (bit 3 of *err), the group barrier of the
+// multi-block QR (bit 4), the tensor-core MMA wait (bit 5, with its TMEM freed)
+void launch_wait_test_bulk(int* err, long polls, cudaStream_t st);
+void launch_wait_test_group(unsigned* bar, int* err, long polls, cudaStream_t st);
+void launch_wait_test_mma(int* status, uint64_t ns, cudaStream_t st);
+
 // rank-prediction MLP (kernels_mlp.cu); idx may be NULL (samples 0..nb-1)
 void mlp_grad(const float* X, const float* t, const int* idx, int nb, float inv_n, const float* prm,
               float* partial, float* ploss, float* grad, float* loss, cudaStream_t st);

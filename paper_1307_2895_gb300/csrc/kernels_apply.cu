@@ -73,11 +73,11 @@ struct BulkStage {
         : "memory");
     return ok != 0;
   }
-  __device__ bool wait(int* err) const {
-    for (long it = 0; it < (1L << 26); ++it)
+  __device__ bool wait(int* err, long polls = 1L << 26) const {
+    for (long it = 0; it < polls; ++it)
       if (try_wait()) return true;
     if (err) atomicOr(err, 8);
-    for (long it = 0; it < (1L << 26); ++it)
+    for (long it = 0; it < polls; ++it)
       if (try_wait()) break;
     return false;
   }
@@ -341,6 +341,27 @@ __global__ void k_apply_root(const ApplyDesc* __restrict__ blocks, const int* __
   });
   __syncthreads();
   sweep_down_block<T, R, false>(bd, ipool, fac, x, nr, ldx, 0, 0, err, smem_raw, [] { return true; });
+}
+
+// ---- check of the bounded wait: a bulk-copy phase that no copy completes
+// (the transaction count is announced, nothing is copied), waited for with
+// `polls` polls; the wait gives up, sets bit 3 of *err and returns.
+__global__ void k_wait_test_bulk(int* err, long polls) {
+  __shared__ __align__(16) uint64_t mbar;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(16u)
+                 : "memory");
+  }
+  __syncthreads();
+  BulkStage bs{&mbar};
+  bs.wait(err, polls);
+}
+
+void launch_wait_test_bulk(int* err, long polls, cudaStream_t st) {
+  note_launches(1);
+  k_wait_test_bulk<<<1, 32, 0, st>>>(err, polls);
 }
 
 // ---- forward operator F (used by the error estimates; not staged) ----------

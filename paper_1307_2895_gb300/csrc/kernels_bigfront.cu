@@ -353,7 +353,7 @@ __global__ void k_bf_scatter(const FrontDesc* __restrict__ fronts, const int* __
     const int i = (int)(e / k), j = (int)(e % k);
     const int ci = perm[i], cj = perm[j];
     U1[(int64_t)pos1[ci] * ld1 + pos1[cj]] = FBB[e];
-    U2[(int64_t)pos2[ci] * ld2 + pos2[cj]] = T(0);
+    if (pos2[ci] >= 0 && pos2[cj] >= 0) U2[(int64_t)pos2[ci] * ld2 + pos2[cj]] = T(0);
   }
 }
 
@@ -369,7 +369,7 @@ __global__ void k_bf_scatter(const FrontDesc* __restrict__ fronts, const int* __
 // pivots, R and T are those of the one-block kernel bit for bit.
 // Scratch per front: sq[2][nc] | diagR[nc] (double) | chosen[nc] (int) |
 // barrier[2] (unsigned), zeroed before the launch.
-__device__ bool group_barrier(unsigned* bar, int G, int* err) {
+__device__ bool group_barrier(unsigned* bar, int G, int* err, long polls = 1L << 22) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -384,7 +384,7 @@ __device__ bool group_barrier(unsigned* bar, int G, int* err) {
     } else {
       long it = 0;
       while (*vgen == gen) {
-        if (++it > (1L << 22)) {   // ~0.1-1 s: a member never arrived
+        if (++it > polls) {        // ~0.1-1 s: a member never arrived
           atomicOr(err, 16);
           s_ok = 0;
           break;
@@ -396,6 +396,16 @@ __device__ bool group_barrier(unsigned* bar, int G, int* err) {
   }
   __syncthreads();
   return s_ok != 0;
+}
+
+// ---- check of the bounded wait: one block of a group of two (the other
+// never arrives) waits at the group barrier with `polls` polls; the wait
+// gives up, sets bit 4 of *err and returns.  bar: two zeroed unsigned.
+__global__ void k_wait_test_group(unsigned* bar, int* err, long polls) { group_barrier(bar, 2, err, polls); }
+
+void launch_wait_test_group(unsigned* bar, int* err, long polls, cudaStream_t st) {
+  note_launches(1);
+  k_wait_test_group<<<1, 64, 0, st>>>(bar, err, polls);
 }
 
 __host__ __device__ inline int64_t coop_scratch_elems(int nc) { return 3 * (int64_t)nc + ((int64_t)nc + 4) / 2 + 2; }

@@ -366,8 +366,10 @@ __global__ void k_front(const FrontDesc* __restrict__ fronts, const CellDesc* __
         const T b = Acc[(int64_t)ci * nc + cj] - s;
         U1[(int64_t)pos1[ci] * ld1 + pos1[cj]] = b;
         U1[(int64_t)pos1[cj] * ld1 + pos1[ci]] = b;
-        U2[(int64_t)pos2[ci] * ld2 + pos2[cj]] = T(0);
-        U2[(int64_t)pos2[cj] * ld2 + pos2[ci]] = T(0);
+        if (pos2[ci] >= 0 && pos2[cj] >= 0) {   // (no second cell in the assembled upper levels)
+          U2[(int64_t)pos2[ci] * ld2 + pos2[cj]] = T(0);
+          U2[(int64_t)pos2[cj] * ld2 + pos2[ci]] = T(0);
+        }
       }
     }
   }

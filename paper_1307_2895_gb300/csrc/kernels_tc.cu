@@ -110,12 +110,13 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Wait for the completion of the phase of parity `parity`; false after kWaitNs.
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// Wait for the completion of the phase of parity `parity`; false after ns
+// nanoseconds of the global timer.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t ns = kWaitNs) {
   if (mbar_try(bar, parity)) return true;
   const uint64_t t0 = gtimer();
   while (!mbar_try(bar, parity))
-    if (gtimer() - t0 > kWaitNs) return false;
+    if (gtimer() - t0 > ns) return false;
   return true;
 }
 
@@ -200,6 +201,7 @@ struct TcCta {
   uint32_t tmem;
   int* status;
   bool ok;
+  uint64_t wait_ns = kWaitNs;   // bound of the waits for the MMAs
   float acc[kAccCols];
 
   __device__ void init(uint8_t* raw, int* st) {
@@ -235,9 +237,9 @@ struct TcCta {
   // add chunk c (its four partial sums, accumulator set c & 1) to the registers
   __device__ void drain(int c) {
     const uint32_t bar = su32(bars + (c & 1)), par = (uint32_t)((c >> 1) & 1);
-    if (!mbar_wait(bar, par)) {
+    if (!mbar_wait(bar, par, wait_ns)) {
       fail();
-      mbar_wait(bar, par);
+      mbar_wait(bar, par, wait_ns);
     }
     fence_after();
     const int warp = threadIdx.x >> 5;
@@ -468,6 +470,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_tc_syrk_flat(const float* __res
   syrk_block<PARTS>(G + b * m * k, k, k, U + b * m * m, m, a, bt, status, tc_smem);
 }
 
+// ---- check of the bounded wait: a CTA takes its tensor memory and its
+// barriers as the Schur update does, issues no MMA, and drains chunk 0 with
+// waits of `ns` nanoseconds; the wait gives up (bit 5 of *status), and the
+// CTA frees its tensor memory and returns.
+__global__ void __launch_bounds__(kThreads, 1) k_wait_test_mma(int* status, uint64_t ns) {
+  extern __shared__ uint8_t tc_smem[];
+  TcCta<1> cta;
+  cta.init(tc_smem, status);
+  cta.wait_ns = ns;
+  cta.drain(0);
+  cta.finish();
+}
+
 template <int PARTS>
 void set_smem_attr() {
   static std::atomic<bool> done{false};
@@ -531,6 +546,16 @@ long long tc_syrk(const TDesc* td, int nsel, int max_nB, float* work, int parts,
   if (parts >= 3) return syrk<3>(td, nsel, max_nB, work, status, st);
   if (parts == 2) return syrk<2>(td, nsel, max_nB, work, status, st);
   return syrk<1>(td, nsel, max_nB, work, status, st);
+}
+
+void launch_wait_test_mma(int* status, uint64_t ns, cudaStream_t st) {
+  static std::atomic<bool> done{false};
+  if (!done) {
+    cudaFuncSetAttribute(k_wait_test_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes(1));
+    done = true;
+  }
+  note_launches(1);
+  k_wait_test_mma<<<1, kThreads, smem_bytes(1), st>>>(status, ns);
 }
 
 void tc_syrk_flat(int nb, int m, int k, const float* G, float* U, int parts, int* status, cudaStream_t st) {

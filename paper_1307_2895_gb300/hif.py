@@ -17,7 +17,7 @@ import numpy as np
 from . import build as _build
 
 HIF_OK, HIF_ERR_ARG, HIF_ERR_NOT_SPD, HIF_ERR_NOCONV, HIF_ERR_TIMEOUT, HIF_ERR_CUDA, HIF_ERR_OOM, HIF_ERR_HOST = range(8)
-VARIANTS = {"mf": 0, "hifde": 1}
+VARIANTS = {"mf": 0, "hifde": 1, "hifde3x": 2}
 ID_MODES = {"qr": 0, "rand": 1, "learned": 2}
 MLP_FEATURES, MLP_PARAMS = 10, 4929
 SOLVERS = {"auto": 0, "cg": 1, "gmres": 2}
@@ -67,7 +67,7 @@ _LIB = None
 EXPORTS = ["hif_factor", "hif_apply", "hif_solve", "hif_matvec", "hif_rhs_from_bc", "hif_stats", "hif_structure",
            "hif_profile", "hif_kernel_launches", "hif_residual_norms_noalloc", "hif_front_log", "hif_mlp_grad",
            "hif_mlp_train", "hif_mlp_predict", "hif_schur_update_f32", "hif_factor_batch", "hif_solve_batch",
-           "hif_set_solver", "hif_estimate", "hif_autotune_table", "hif_free", "hif_last_error"]
+           "hif_set_solver", "hif_estimate", "hif_autotune_table", "hif_wait_selftest", "hif_free", "hif_last_error"]
 
 
 def library_path() -> str:
@@ -104,6 +104,8 @@ def load(build_if_missing: bool = False):
     lib.hif_profile.restype = i
     lib.hif_kernel_launches.argtypes = []
     lib.hif_kernel_launches.restype = ctypes.c_longlong
+    lib.hif_wait_selftest.argtypes = [i, ctypes.c_longlong, vp]
+    lib.hif_wait_selftest.restype = i
     lib.hif_residual_norms_noalloc.argtypes = [i, i, vp, vp, vp, vp, i, i, vp, vp]
     lib.hif_residual_norms_noalloc.restype = i
     lib.hif_front_log.argtypes = [vp, vp, vp, vp, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)]
@@ -339,6 +341,14 @@ def residual_norms_noalloc(dim: int, n: int, a_stag, b, f, x, out, stream=None) 
     rc = lib.hif_residual_norms_noalloc(dim, n, _ptr(a_stag), _ptr(b), _ptr(f2), _ptr(x2), f2.shape[1],
                                         f2.shape[1], _ptr(out), _stream_ptr(stream))
     _check(rc, lib)
+
+
+def wait_selftest(which: str, limit: int, stream=None) -> None:
+    """hif_wait_selftest: run one bounded device wait ("bulk", "group" or
+    "mma") on an object nothing completes; raises HifError (HIF_ERR_TIMEOUT
+    when the wait gave up, as it should)."""
+    lib = load()
+    _check(lib.hif_wait_selftest({"bulk": 0, "group": 1, "mma": 2}[which], int(limit), _stream_ptr(stream)), lib)
 
 
 def kernel_launches() -> int:

@@ -171,3 +171,13 @@ def test_noalloc_binding_refuses_host_arrays_and_wrong_lengths():
     f = np.zeros(((n - 1) ** 2, 2))
     with pytest.raises(TypeError):
         hif.residual_norms_noalloc(2, n, a, b, f, f, np.zeros(2))
+
+
+def test_wait_selftest_argument_errors_without_gpu():
+    """hif_wait_selftest refuses an unknown wait and a bound outside 1 .. the
+    real wait's own, before any CUDA call."""
+    lib = hif.load(build_if_missing=True)
+    assert lib.hif_wait_selftest(3, 100, None) == hif.HIF_ERR_ARG
+    assert lib.hif_wait_selftest(0, 0, None) == hif.HIF_ERR_ARG
+    assert lib.hif_wait_selftest(1, (1 << 22) + 1, None) == hif.HIF_ERR_ARG
+    assert lib.hif_wait_selftest(2, 2_000_000_000, None) == hif.HIF_ERR_ARG
