@@ -17,7 +17,7 @@ step for one problem on one GPU): value = DOF of all ranks / max rank time.
 
 Other workloads, one JSON line each:
 
-    python bench.py --workload3d laplace3d_n64|contrast3d_n128 [--eps E]
+    python bench.py --workload3d laplace3d_n64|contrast3d_n128 [--eps E] [--variant hifde|hifde3x]
                     [--precision fp64|mixed|fp32_apply] [--tensor-cores 0|1|2|3|-1]
     python bench.py --batched          # 64 independent 2D problems, 32 RHS each
                                        # (under torchrun: problems sharded over the ranks)
@@ -404,6 +404,10 @@ def run_gpu(args, rank, world, local_rank):
         except Exception as exc:  # the oracle leg must not hide the GPU result
             cpu = {"error": repr(exc)}
 
+    others = None
+    if rank == 0 and world == 1 and not args.skip_others:
+        others = other_workloads()
+
     if rank != 0:
         return 0
     last = infos[-1]
@@ -424,6 +428,7 @@ def run_gpu(args, rank, world, local_rank):
         "plain_fp64": plain,
         "speedup_vs_plain_fp64": (value / world / plain["value"]) if plain else None,
         "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu, "err_vs_oracle": err,
+        "other_workloads": others,
         "clocks": clocks.summary(),
     }
     print(json.dumps(line), flush=True)
@@ -451,12 +456,12 @@ def _sweep_traffic():
     return val if (val is not None and cap_sha == sha) else None
 
 
-def run_batched(args, rank: int = 0, world: int = 1, local_rank: int = 0):
+def measure_batched(precision: str, steps: int, warmup: int, rank: int = 0, world: int = 1, local_rank: int = 0):
     """The batched workload (64 independent 2D problems, 32 RHS each) through
-    hif_factor_batch / hif_solve_batch; one JSON line, DOF x RHS per second.
-    With N ranks the problems are sharded (shard_problems, weighted by
-    DOF x RHS) and each rank factors and solves its own; value = all
-    problems' units over the slowest rank's time."""
+    hif_factor_batch / hif_solve_batch: DOF x RHS per second.  With N ranks
+    the problems are sharded (shard_problems, weighted by DOF x RHS) and each
+    rank factors and solves its own; value = all problems' units over the
+    slowest rank's time."""
     import torch
     from paper_1307_2895_gb300 import hif, inputs
     torch.cuda.set_device(local_rank)
@@ -470,39 +475,42 @@ def run_batched(args, rank: int = 0, world: int = 1, local_rank: int = 0):
     units = sum(units_all)
     ms = []
     conv = True
-    for step in range(args.warmup + args.steps):
+    for step in range(warmup + steps):
         torch.cuda.synchronize()
         if world > 1:
             import torch.distributed as dist
             dist.barrier()
         t0 = time.perf_counter()
-        facts = hif.factor_batch(spec, 1e-6, precision=args.precision, nthreads=8)
+        facts = hif.factor_batch(spec, 1e-6, precision=precision, nthreads=8)
         try:
             res = hif.solve_batch(facts, rhs, tol=TOL, maxit=2000, nthreads=8)
         finally:
             for F in facts:
                 F.free()
         torch.cuda.synchronize()
-        if step >= args.warmup:
+        if step >= warmup:
             ms.append(1e3 * (time.perf_counter() - t0))
             conv = conv and all(r[1]["converged"] and r[1]["relres_max"] <= TOL for r in res)
     dev = torch.device("cuda", local_rank)
     t = max_over_ranks(sum(ms) / 1e3, world, dev)
     conv = max_over_ranks(0.0 if conv else 1.0, world, dev) == 0.0   # every rank converged
-    if rank != 0:
-        return 0
-    print(json.dumps({"metric": "factor+solve DOF x RHS/s at rel. residual 1e-12, 64 independent problems",
-                      "value": units * args.steps / t, "unit": "DOF*RHS/s", "n_gpus": world, "steps": args.steps,
-                      "warmup": args.warmup, "ms_per_step": t * 1e3 / args.steps, "higher_is_better": True,
-                      "dtype": "f64+f32", "data": "synthetic", "converged": conv,
-                      "config": {"workload": "64 x 2D contrast 1e2/1e4/1e6, interior edges log-uniform 127..1023 "
-                                             "(sum N = %d), 32 RHS each, eps=1e-6" % sum((p["n"] - 1) ** 2
-                                                                                          for p in probs),
-                                 "precision": args.precision,
-                                 "parallelism": "8 host threads, one stream per problem" + (
-                                     "; problems sharded over %d ranks (largest first)" % world if world > 1
-                                     else "")},
-                      "scaling": "strong"}), flush=True)
+    return {"metric": "factor+solve DOF x RHS/s at rel. residual 1e-12, 64 independent problems",
+            "value": units * steps / t, "unit": "DOF*RHS/s", "n_gpus": world, "steps": steps,
+            "warmup": warmup, "ms_per_step": t * 1e3 / steps, "higher_is_better": True,
+            "dtype": "f64+f32", "data": "synthetic", "converged": conv,
+            "config": {"workload": "64 x 2D contrast 1e2/1e4/1e6, interior edges log-uniform 127..1023 "
+                                   "(sum N = %d), 32 RHS each, eps=1e-6" % sum((p["n"] - 1) ** 2 for p in allp),
+                       "precision": precision,
+                       "parallelism": "8 host threads, one stream per problem" + (
+                           "; problems sharded over %d ranks (largest first)" % world if world > 1 else "")},
+            "scaling": "strong"}
+
+
+def run_batched(args, rank: int = 0, world: int = 1, local_rank: int = 0):
+    """One JSON line of measure_batched (rank 0)."""
+    line = measure_batched(args.precision, args.steps, args.warmup, rank, world, local_rank)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     return 0
 
 
@@ -555,27 +563,28 @@ def tc_roofline(split: int = 3, nb: int = 16, m: int = 1024, k: int = 2048, reps
                          "frac": achieved / peak, "peak_source": how, "traffic": None}}
 
 
-def run_3d(args):
+def measure_3d(workload: str, eps: float, variant: str, precision: str, steps: int, warmup: int,
+               tensor_cores: int = 0):
     """A 3D workload: factor + 4-RHS PCG to 1e-12 per step, wall clock with a
-    device synchronize on both sides (the factorization's host work included);
-    one JSON line with the factor and solve times, iterations and |s_L|, and
-    in the mixed mode the tensor-core Schur update timed alone."""
+    device synchronize on both sides (the factorization's host work
+    included).  Returns the figures of one JSON object."""
     import torch
     from paper_1307_2895_gb300 import hif, inputs
     hif.load()
-    w = inputs.workload(args.workload3d)
+    w = inputs.workload(workload)
     n, nrhs = w["n"], w["nrhs"]
-    eps = args.eps if args.eps > 0 else w["eps"]
+    eps = eps if eps > 0 else w["eps"]
     dev = torch.device("cuda", 0)
     st = torch.cuda.Stream(device=dev)
     a = torch.from_numpy(w["a_stag"]).to(dev)
     b = torch.from_numpy(w["b"]).to(dev)
     f = torch.from_numpy(inputs.rhs(3, n, nrhs, seed=0)).to(dev)
     fac, sol, infos, stats = [], [], [], []
-    for step in range(args.warmup + args.steps):
+    for step in range(warmup + steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        G = hif.factor(3, n, a, b, eps, precision=args.precision, stream=st, tensor_cores=args.tensor_cores)
+        G = hif.factor(3, n, a, b, eps, variant=variant, precision=precision, stream=st,
+                       tensor_cores=tensor_cores)
         try:
             torch.cuda.synchronize()
             t1 = time.perf_counter()
@@ -585,28 +594,60 @@ def run_3d(args):
             s = G.stats()
         finally:
             G.free()
-        if step >= args.warmup:
+        if step >= warmup:
             fac.append(t1 - t0)
             sol.append(t2 - t1)
             infos.append(info)
             stats.append(s)
     t = sum(fac) + sum(sol)
     N = (n - 1) ** 3
-    line = {"metric": "factor+solve DOF x RHS/s at rel. residual 1e-12 (3D)",
-            "value": N * nrhs * args.steps / t, "unit": "DOF*RHS/s", "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
-            "dtype": {"fp64": "f64", "mixed": "f32+f64", "fp32_apply": "f64+f32"}[args.precision],
+    return {"metric": "factor+solve DOF x RHS/s at rel. residual 1e-12 (3D)",
+            "value": N * nrhs * steps / t, "unit": "DOF*RHS/s", "n_gpus": 1, "steps": steps,
+            "warmup": warmup, "ms_per_step": 1e3 * t / steps, "higher_is_better": True,
+            "dtype": {"fp64": "f64", "mixed": "f32+f64", "fp32_apply": "f64+f32"}[precision],
             "data": "synthetic",
-            "config": {"workload": f"{args.workload3d}: {n - 1}^3, eps={eps:g}, {nrhs} RHS",
-                       "precision": args.precision, "tensor_cores": args.tensor_cores},
+            "config": {"workload": f"{workload}: {n - 1}^3, eps={eps:g}, {nrhs} RHS",
+                       "variant": {"hifde": "hifde3", "hifde3x": "hifde3x"}[variant], "precision": precision,
+                       "tensor_cores": tensor_cores},
             "factor_ms": 1e3 * sum(fac) / len(fac), "solve_ms": 1e3 * sum(sol) / len(sol),
             "t_fronts_ms": stats[-1]["t_fronts_ms"], "root_size": stats[-1]["root_size"],
             "cg_iters": infos[-1]["iters"], "relres_max": max(i["relres_max"] for i in infos),
             "converged": all(i["converged"] for i in infos)}
+
+
+def run_3d(args):
+    """One JSON line of measure_3d; in the mixed mode also the tensor-core
+    Schur update timed alone."""
+    line = measure_3d(args.workload3d, args.eps, args.variant, args.precision, args.steps, args.warmup,
+                      args.tensor_cores)
     if args.precision == "mixed" and args.tensor_cores >= 0:
         line["tensor_core_kernel"] = tc_roofline(split=args.tensor_cores or 3)
     print(json.dumps(line), flush=True)
     return 0
+
+
+def other_workloads():
+    """The other configurations of the method, one step each after one
+    warm-up (outside the headline's timed region): the 3D Laplacian 63^3 with
+    hifde3x at eps 1e-3 and 1e-6 (Example 4; Table 7 gives |s_L| 578 / 2466
+    and 11 / 3 iterations), the 3D high-contrast 127^3 (Example 5 recipe)
+    with hifde3, and the 64 independent 2D problems."""
+    out = {}
+    for eps in (1e-3, 1e-6):
+        try:
+            r = measure_3d("laplace3d_n64", eps, "hifde3x", "fp32_apply", 1, 1)
+            out[f"laplace3d_n64_hifde3x_eps{eps:g}"] = r
+        except Exception as exc:
+            out[f"laplace3d_n64_hifde3x_eps{eps:g}"] = {"error": repr(exc)}
+    try:
+        out["contrast3d_n128_hifde3"] = measure_3d("contrast3d_n128", 0.0, "hifde", "fp32_apply", 1, 1)
+    except Exception as exc:
+        out["contrast3d_n128_hifde3"] = {"error": repr(exc)}
+    try:
+        out["batched_64x2d"] = measure_batched("fp32_apply", 1, 1)
+    except Exception as exc:
+        out["batched_64x2d"] = {"error": repr(exc)}
+    return out
 
 
 def run_solve_only(args):
@@ -667,11 +708,15 @@ def main():
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-others", action="store_true",
+                    help="leave out the other configurations (3D 63^3 hifde3x, 127^3, the batched problems)")
     ap.add_argument("--batched", action="store_true",
                     help="time the batched workload (64 independent problems) instead of the headline one")
     ap.add_argument("--workload3d", default="", choices=["", "laplace3d_n64", "contrast3d_n128"],
                     help="time a 3D workload (factor + PCG) instead of the headline one")
     ap.add_argument("--eps", type=float, default=0.0, help="3D workloads: eps (default: the workload's)")
+    ap.add_argument("--variant", default="hifde", choices=["hifde", "hifde3x"],
+                    help="3D workloads: hifde3 (faces) or hifde3x (faces and edges, Section 4.5)")
     ap.add_argument("--tensor-cores", type=int, default=0, choices=[0, 1, 2, 3, -1],
                     help="mixed precision: 0 or 3 three-part TF32 split, 2 two-part, 1 plain TF32, -1 SIMT FP32")
     ap.add_argument("--tc-roofline", action="store_true",
