@@ -125,6 +125,18 @@ typedef struct hif_opts {
                            (threads per block, shared-memory staging) on a
                            scratch copy and keeps the fastest, process-wide;
                            < 0: the built-in shapes.                            */
+  int edge_start;       /* HIFDE3X: the first level whose edges are
+                           skeletonized (Section 4.5's rule of thumb: skip
+                           edge skeletonization while it does not pay for the
+                           thicker separators it causes): 0 -> level 1, k > 0
+                           -> level k (k >= L: no edges, the result is
+                           hifde3's), -1 -> level 0.  Ignored otherwise.       */
+  int sketch_power;     /* HIF_ID_RAND / LEARNED: power iterations on the
+                           sketch, Y = Phi A (A^T A)^q (the end of Section 4.5
+                           suggests them for inaccurate sketches), q in 0..2;
+                           the sketch's rank rule is then applied at
+                           (eps/10)^(2q+1), which must stay well above the
+                           FP64 rounding level (q = 1 for eps >= 1e-4).       */
 } hif_opts;
 
 typedef struct hif_handle hif_handle;

@@ -443,7 +443,7 @@ def _front_key(dim, x, on_sep, seps):
 
 
 def factor(A_csr, dim: int, n: int, eps: float, leaf: int = 8,
-           skip_levels: int = 0, sketch=None) -> Factor:
+           skip_levels: int = 0, sketch=None, sketch_power: int = 0) -> Factor:
     """Algorithm 4.1 (HIF-DE; ``eps > 0``) or Algorithm 3.1 (MF; ``eps == 0``).
 
     Level l: eliminate the active DOFs strictly inside each level-l cell
@@ -458,8 +458,9 @@ def factor(A_csr, dim: int, n: int, eps: float, leaf: int = 8,
     matrix for front ``c`` (ascending DOF ids) whose ID block has the rows
     ``rows`` (ascending DOF ids), or None to use the pivoted-QR ID.  A
     sketched ID that fails :func:`oracle.learned.randomized_id`'s check falls
-    back to the pivoted-QR ID of the block itself.  The counts of accepted
-    and rejected sketches are kept on the result."""
+    back to the pivoted-QR ID of the block itself (``sketch_power`` power
+    iterations on the sketch).  The counts of accepted and rejected sketches
+    are kept on the result."""
     from .stencil import coords as _coords
     A = ActiveMatrix(A_csr)
     X = _coords(dim, n)
@@ -506,7 +507,7 @@ def factor(A_csr, dim: int, n: int, eps: float, leaf: int = 8,
                 idr = None
                 if Phi is not None:
                     from .learned import randomized_id
-                    ids_s, ok = randomized_id(M, eps, Phi)
+                    ids_s, ok = randomized_id(M, eps, Phi, sketch_power)
                     if ok:
                         idr = ids_s
                         n_sketched += 1

@@ -42,9 +42,11 @@ HUBER_DELTA = 1.0
 SKETCH_RANK_TOL = 0.1
 
 
-def randomized_id(M: np.ndarray, eps: float, Phi: np.ndarray):
-    """ID of M from the sketch Y = Phi M: the skeletons and rank of the
-    pivoted-QR ID of Y at ``SKETCH_RANK_TOL * eps``, then T by least squares
+def randomized_id(M: np.ndarray, eps: float, Phi: np.ndarray, power: int = 0):
+    """ID of M from the sketch Y = Phi M (M^T M)^power (the power iterations
+    the end of Section 4.5 suggests for inaccurate sketches): the skeletons
+    and rank of the pivoted-QR ID of Y at (SKETCH_RANK_TOL * eps)^(2 power +
+    1) (Y's singular values are M's to that power), then T by least squares
     on M itself (T minimizes every column norm of M_r - M_s T).  Returns
     (IDResult, ok) where ok says the residual check passed (column norms, see
     the module docstring) and the sketch was not saturated (k < ell).  The
@@ -52,7 +54,9 @@ def randomized_id(M: np.ndarray, eps: float, Phi: np.ndarray):
     norm lies within 1e-8 (relative) of the acceptance bound, a decision that
     rounding order could flip."""
     Y = Phi @ M
-    idy = interp_decomp(Y, SKETCH_RANK_TOL * eps)
+    for _ in range(power):
+        Y = (Y @ M.T) @ M
+    idy = interp_decomp(Y, (SKETCH_RANK_TOL * eps) ** (2 * power + 1))
     k, ell = len(idy.sk), Phi.shape[0]
     if k >= ell:
         return idy, False

@@ -221,6 +221,15 @@ __device__ __forceinline__ double sketch_normal(uint64_t key, uint64_t e) {
   const double u2 = (double)(smix_at(key, 2 * e + 2) >> 11) * 0x1p-53;
   return sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2);
 }
+// Rank tolerance of the pivoted QR of a sketch with `power` power
+// iterations: Y's singular values are A's to the power 2 power + 1.
+__device__ __forceinline__ double sketch_rank_tol(double eps, int power) {
+  const double t = eps * kSketchRankTol;
+  double r = t;
+  for (int p = 0; p < power; ++p) r *= t * t;
+  return r;
+}
+
 // Key of the front whose smallest DOF id is c0 (see SketchStream).
 __device__ __forceinline__ uint64_t sketch_key(const SketchStream& ss, int c0) {
   return smix_at(ss.seed, ss.level_base + (uint64_t)c0 + 1);

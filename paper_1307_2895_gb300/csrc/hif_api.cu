@@ -196,6 +196,8 @@ struct hif_handle {
   int precision = HIF_PREC_FP64;
   int variant = HIF_VARIANT_HIFDE;
   int skip_levels = 0;
+  int edge_start = 1;   // HIFDE3X: first level whose edges are skeletonized
+  int sketch_power = 0; // power iterations on the randomized ID's sketch
   int big_cell = 192;   // cells with at least this many interior DOFs use the tiled elimination
   bool coop_qr = true;  // large fronts: pivoted QR by co-resident block groups
   int tc_split = 3;     // FP32 tiled elimination on the tensor cores: TF32 parts per value (1..3), 0 = SIMT
@@ -209,6 +211,7 @@ struct hif_handle {
   DevBuf a_stag, bnode;
   DevBuf dev_err;   // device status of the apply kernels (bit 3: a bounded wait ran out)
   bool count_sweeps = false;   // while a graph is captured: count sweep bytes and launches, no events
+  DevBuf root_scratch;         // the multi-block root apply's y and z (2 |s_L| kRootChunk doubles)
   DevBuf stencil_w; // per-node stencil weights (diagonal and neighbour couplings)
   DevBuf model_bf16; // rank-predictor parameters in BF16 (HIF_ID_LEARNED)
   std::shared_ptr<const Level0> level0;
@@ -454,20 +457,21 @@ struct Factorizer {
     }
   }
 
-  // hifde3x from level 1's edges on (Section 4.5, Algorithm 4.2), on A_l held
+  // hifde3x from level e's edges on (Section 4.5, Algorithm 4.2), on A_l held
   // as one dense matrix of the DOFs active at the hand-over (kernels_dense3x.cu):
-  // the edges of level 1, then per level l >= 2 the algebraic cells (Lemma
+  // the edges of level e, then per level l > e the algebraic cells (Lemma
   // 2.1), the faces and the edges (Lemma 2.4), then the root.  cd1 / d_cd1 /
-  // ip1 / work1: the level-1 cells, their ids and their update matrices
-  // after the level-1 faces.
+  // ip1 / work1: the level-e cells, their ids and their update matrices
+  // after the level-e faces.
   static constexpr double kDenseMaxBytes = 48e9;
-  void dense_stage(const std::vector<CellDesc>& cd1, const CellDesc* d_cd1, const int* ip1, DevBuf& work1) {
+  void dense_stage(int e, const std::vector<CellDesc>& cd1, const CellDesc* d_cd1, const int* ip1,
+                   DevBuf& work1) {
     const int L = G.L;
     const std::vector<int> act = sym->active();
     const int64_t n_act = (int64_t)act.size();
     if ((double)n_act * (double)n_act * sizeof(T) > kDenseMaxBytes)
       throw HifError(HIF_ERR_ARG, "hifde3x keeps its upper levels as one dense matrix of the DOFs active after "
-                                  "level 1's faces: too many of them for this grid");
+                                  "the faces of its first edge level: too many of them for this grid");
     std::vector<int> hmap(G.N, -1);
     for (int64_t i = 0; i < n_act; ++i) hmap[act[i]] = (int)i;
     DevBuf dmap, Abuf;
@@ -517,8 +521,8 @@ struct Factorizer {
                  mnc, mnN, kind == 1 ? h->fronts[l] : h->edges[l], 2 * l + (kind == 2 ? 1 : 0));
       if (h->finfo.size() > nfi) sym_fronts();
     };
-    groups(1, 2);
-    for (int l = 2; l < L; ++l) {
+    groups(e, 2);
+    for (int l = e + 1; l < L; ++l) {
       const std::vector<std::vector<int>> P = sym->cells(l);
       std::vector<std::vector<int>> Q(P.size());
       for (size_t i = 0; i < P.size(); ++i) Q[i] = sym->neighbors(P[i]);
@@ -676,10 +680,10 @@ struct Factorizer {
     h->fronts.resize(L);
     h->edges.resize(L);
     const bool skel = (h->variant != HIF_VARIANT_MF) && h->eps > 0.0;
-    // hifde3x: its levels 0 and 1 (cells and faces) are hifde3's (Section 4.5
-    // skips the edges of level 0); the host replays them on the symbolic
-    // stage, which then gives every later index set
-    x3 = h->variant == HIF_VARIANT_HIFDE3X && L >= 2;
+    // hifde3x: its levels up to the first one with edges (cells and faces)
+    // are hifde3's; the host replays them on the symbolic stage, which then
+    // gives every later index set
+    x3 = h->variant == HIF_VARIANT_HIFDE3X && h->edge_start < L;
     if (x3) sym.reset(new Symbolic3x(G.n, G.leaf, true));
     std::shared_ptr<const Level0> L0 = get_level0(G);
     h->level0 = L0;
@@ -712,6 +716,11 @@ struct Factorizer {
       run_fronts(0, L0->d_cdesc, work, alive, L0->fronts, L0->fdesc, L0->d_fdesc, L0->d_fip, L0->fwork_elems,
                  L0->ffac_elems, L0->fout_elems, L0->max_nc, L0->max_nN, h->fronts[0], 0);
       if (h->finfo.size() > nfi) sym_fronts();
+    }
+    if (x3 && h->edge_start == 0) {   // hifde3x with edges from level 0 on
+      dense_stage(0, L0->cdesc, L0->d_cdesc, L0->d_cipool, work);
+      finish_status();
+      return;
     }
     const std::vector<HostCell>* prev_cells = &L0->cells;
     const CellDesc* prev_ddesc = L0->d_cdesc;
@@ -790,17 +799,23 @@ struct Factorizer {
         upload(d_ip, ip, st);
         const size_t nfi = h->finfo.size();
         run_fronts(l, dd, work, alive, fr, fd, d_fd.as<FrontDesc>(), d_ip.as<int>(), fw, ff, fo, mnc, mnN,
-                   h->fronts[l], x3 ? 2 * l : l);
+                   h->fronts[l], h->variant == HIF_VARIANT_HIFDE3X ? 2 * l : l);
         if (h->finfo.size() > nfi) sym_fronts();
       }
-      if (x3 && l == 1) {   // hifde3x: the assembled upper levels from level 1's edges on
-        dense_stage(cdesc, dd, sw.ipool, work);
+      if (x3 && l == h->edge_start) {   // hifde3x: the assembled upper levels from these edges on
+        dense_stage(l, cdesc, dd, sw.ipool, work);
         break;
       }
       prev_cells = &cells;
       prev_ddesc = dd;
       prev_work.swap(work);
     }
+    finish_status();
+  }
+
+  // The factorization's device status: counts for hif_stats, then the
+  // failures (a non-positive pivot, a bounded wait that ran out).
+  void finish_status() {
     int hs2[4] = {0, 0, 0, 0};
     CU(cudaMemcpyAsync(hs2, status.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
@@ -845,7 +860,7 @@ struct Factorizer {
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
     CU(cudaEventRecord(e0, st));
-    const SketchStream ss{(uint64_t)h->seed, (uint64_t)l * (uint64_t)G.N, (uint64_t)G.N};
+    const SketchStream ss{(uint64_t)h->seed, (uint64_t)l * (uint64_t)G.N, (uint64_t)G.N, h->sketch_power};
     // fronts with at least max(big_cell, kBigFrontMin) DOFs: the multi-block
     // skeletonization (its elimination scratch needs |c|^2 >= cell_x_elems(|c|))
     const int big_front = std::max(h->big_cell, kBigFrontMin);
@@ -1144,7 +1159,29 @@ void run_apply(hif_handle* h, int mode, T* x, int nrhs) {
     sweep(h->fronts[l], up, 1, facp(h->fronts[l]));
     if (l < (int)h->edges.size()) sweep(h->edges[l], up, 1, facp(h->edges[l]));
   }
-  if (mode == HIF_APPLY_FINV) {
+  if (mode == HIF_APPLY_FINV && h->root.nblocks == 1 && h->root.max_np >= kRootMulti && h->root_scratch.p) {
+    // a large root: D^-1 by all SMs (the root's factor and ids start at 0)
+    const SweepLevel& S = h->root;
+    if (prof) {
+      if (h->ev_used + 2 > h->ev_pool.size()) {
+        for (int k = 0; k < 64; ++k) {
+          cudaEvent_t e;
+          CU(cudaEventCreate(&e));
+          h->ev_pool.push_back(e);
+        }
+      }
+      CU(cudaEventRecord(h->ev_pool[h->ev_used], st));
+    }
+    const int nl = launch_root_apply<T>(S.max_np, S.ipool, facp(S), x, nrhs, nrhs, h->root_scratch.as<T>(), st);
+    if (prof) {
+      CU(cudaEventRecord(h->ev_pool[h->ev_used + 1], st));
+      h->ev_used += 2;
+    }
+    if (count) {
+      h->prof_launches += nl;
+      h->prof_bytes += sweep_bytes(S, 4);
+    }
+  } else if (mode == HIF_APPLY_FINV) {
     sweep(h->root, 4, 0, facp(h->root));   // D^-1: the root's up and down sweeps in one launch
   } else {
     sweep(h->root, up, 0, facp(h->root));
@@ -1211,7 +1248,7 @@ struct SolveWork {
   int R = 0;
   bool f32 = false;
   DevBuf f, bin, xh, xl, D, Rv, P, Q, WP, part, scal, cnt;
-  double *rzzq[2], *pq, *rr, *alpha, *thr2, *bn2, *rn2;
+  double *rzzq[2], *pq, *rr, *alpha, *beta, *thr2, *bn2, *rn2;
   int* active;
   void init(int64_t N_, int R_, bool f32_, cudaStream_t st) {
     N = N_;
@@ -1228,7 +1265,7 @@ struct SolveWork {
     CU(cudaMemsetAsync(scal.p, 0, sizeof(double) * 12 * R, st));
     double* s = scal.as<double>();
     rzzq[0] = s; rzzq[1] = s + 2 * R; pq = s + 4 * R; rr = s + 5 * R; alpha = s + 6 * R;
-    thr2 = s + 7 * R; bn2 = s + 8 * R; rn2 = s + 9 * R;
+    thr2 = s + 7 * R; bn2 = s + 8 * R; rn2 = s + 9 * R; beta = s + 10 * R;
     active = reinterpret_cast<int*>(s + 12 * R);
   }
 };
@@ -1341,15 +1378,13 @@ void cg_step_kernels(hif_handle* h, SolveWork& W, TZ* wp, int par, int restart, 
   cudaStream_t st = h->st;
   if (phase == 0) {
     launch_dot2_e<TZ>(N, R, W.Rv.as<double>(), wp, W.Q.as<double>(), partials, counter, W.rzzq[par], st,
-                      ring ? ring + R : nullptr);
-    launch_update_p_e<TZ>(N, R, W.P.as<double>(), wp, W.alpha, W.rzzq[par ^ 1], W.rzzq[par], W.active,
-                          restart, st);
+                      ring ? ring + R : nullptr, W.alpha, W.rzzq[par ^ 1], W.beta);
+    launch_update_p_e<TZ>(N, R, W.P.as<double>(), wp, W.beta, W.rzzq[par ^ 1], W.active, restart, st);
   } else {
     launch_mv_dot_e(h->gi, h->stencil_w.as<double>(), W.P.as<double>(), W.Q.as<double>(), R, partials, counter,
-                    W.pq, st);
-    launch_axpy2_e<TZ>(N, R, W.D.as<double>(), W.Rv.as<double>(), W.P.as<double>(), W.Q.as<double>(),
-                       W.rzzq[par], W.pq, W.active, W.alpha, partials, counter, W.rr, wp, st, W.thr2, W.active,
-                       ring);
+                    W.pq, st, W.rzzq[par], W.active, W.alpha);
+    launch_axpy2_e<TZ>(N, R, W.D.as<double>(), W.Rv.as<double>(), W.P.as<double>(), W.Q.as<double>(), W.alpha,
+                       partials, counter, W.rr, wp, st, W.thr2, W.active, ring);
   }
 }
 
@@ -1860,6 +1895,10 @@ int hif_factor(const hif_grid* grid, const double* a_stag, const double* b, cons
     if (opts && opts->big_cell != 0) h->big_cell = opts->big_cell < 0 ? 0x7fffffff : opts->big_cell;
     if (opts) h->tc_split = opts->tensor_cores < 0 ? 0 : opts->tensor_cores == 0 ? 3 : std::min(opts->tensor_cores, 3);
     if (opts) h->autotune = opts->autotune >= 0;
+    if (opts) h->edge_start = opts->edge_start == 0 ? 1 : (opts->edge_start < 0 ? 0 : opts->edge_start);
+    if (opts && (opts->sketch_power < 0 || opts->sketch_power > 2))
+      throw HifError(HIF_ERR_ARG, "sketch_power must be 0, 1 or 2");
+    if (opts) h->sketch_power = opts->sketch_power;
     if (h->id_mode == HIF_ID_LEARNED && !(opts && opts->rank_model))
       throw HifError(HIF_ERR_ARG, "HIF_ID_LEARNED needs opts.rank_model");
     h->st = opts ? (cudaStream_t)opts->stream : nullptr;
@@ -1904,6 +1943,8 @@ int hif_factor(const hif_grid* grid, const double* a_stag, const double* b, cons
       f.run();
     }
     if (prec == HIF_PREC_FP32_APPLY) demote_factor(h);
+    if (h->root_size >= kRootMulti)
+      h->root_scratch.alloc(sizeof(double) * 2 * (size_t)h->root_size * kRootChunk, h->st);
     CU(cudaEventRecord(e1, h->st));
     CU(cudaEventSynchronize(e1));
     float ms = 0.f;

@@ -70,9 +70,11 @@ struct ApplyDesc {
 // N) and normal(key, e) the Box-Muller cosine branch, in FP64, of the
 // uniforms (top 53 bits) of outputs 2e + 1 and 2e + 2 of the stream seeded
 // with key.  Indexed by DOF ids, so Phi A_{N,c} does not depend on the order
-// of N or on rows that are structurally zero.
+// of N or on rows that are structurally zero.  power: power iterations on
+// the sketch, Y = Phi A (A^T A)^power.
 struct SketchStream {
   uint64_t seed, level_base, nglob;
+  int power;
 };
 
 // Rank-prediction MLP: kFeat input features per front, hidden width kHid.

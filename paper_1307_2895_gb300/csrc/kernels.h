@@ -102,6 +102,15 @@ void launch_wait_test_bulk(int* err, long polls, cudaStream_t st);
 void launch_wait_test_group(unsigned* bar, int* err, long polls, cudaStream_t st);
 void launch_wait_test_mma(int* status, uint64_t ns, cudaStream_t st);
 
+// D^-1 of a root of at least kRootMulti DOFs by the whole GPU (kernels_root.cu):
+// x_root <- L^-T L^-1 x_root on the rows ids[0..np) of x (N x nrhs, row stride
+// ldx), in column chunks of kRootChunk; scratch: 2 np kRootChunk elements.
+// Returns the number of launches.
+constexpr int kRootMulti = 256;
+constexpr int kRootChunk = 8;
+template <typename T>
+int launch_root_apply(int np, const int* ids, const T* Linv, T* x, int nrhs, int ldx, T* scratch, cudaStream_t st);
+
 // rank-prediction MLP (kernels_mlp.cu); idx may be NULL (samples 0..nb-1)
 void mlp_grad(const float* X, const float* t, const int* idx, int nb, float inv_n, const float* prm,
               float* partial, float* ploss, float* grad, float* loss, cudaStream_t st);
@@ -153,19 +162,22 @@ void launch_dd_residual(GridInfo g, const double* a_stag, const double* bn, cons
 void launch_dd_add(int64_t N, int nr, double* xh, double* xl, const double* d, cudaStream_t st);
 // element-parallel CG kernels on N x R vectors, R in {1, 2, 4, 8, 16}
 void launch_stencil_weights(GridInfo g, const double* a_stag, const double* b, double* W, cudaStream_t st);
+// q = A p, pq = p.q; with alpha (may be NULL): alpha = rz / pq on the active columns
 void launch_mv_dot_e(GridInfo g, const double* W, const double* p, double* q, int R, double* partials,
-                     unsigned* counter, double* pq, cudaStream_t st);
+                     unsigned* counter, double* pq, cudaStream_t st, const double* rz = nullptr,
+                     const int* active = nullptr, double* alpha = nullptr);
 template <typename TZ>
 void launch_axpy2_e(int64_t N, int R, double* x, double* r, const double* p, const double* q,
-                    const double* rz, const double* pq, const int* active, double* alpha, double* partials,
-                    unsigned* counter, double* rr, TZ* zin, cudaStream_t st, const double* thr2 = nullptr,
-                    int* active_next = nullptr, double* ring_rr = nullptr);
+                    const double* alpha, double* partials, unsigned* counter, double* rr, TZ* zin, cudaStream_t st,
+                    const double* thr2 = nullptr, int* active_next = nullptr, double* ring_rr = nullptr);
+// out = [r.z | z.q]; beta = -alpha zq / rz_old
 template <typename TZ>
 void launch_dot2_e(int64_t N, int R, const double* r, const TZ* z, const double* q, double* partials,
-                   unsigned* counter, double* out, cudaStream_t st, double* ring_rz = nullptr);
+                   unsigned* counter, double* out, cudaStream_t st, double* ring_rz, const double* alpha,
+                   const double* rz_old, double* beta);
 template <typename TZ>
-void launch_update_p_e(int64_t N, int R, double* p, const TZ* z, const double* alpha, const double* rz_old,
-                       const double* rzzq, const int* active, int restart, cudaStream_t st);
+void launch_update_p_e(int64_t N, int R, double* p, const TZ* z, const double* beta, const double* rz_old,
+                       const int* active, int restart, cudaStream_t st);
 void launch_set_active(int nr, const double* rr, const double* thr2, int* active, cudaStream_t st);
 // flexible GMRES: basis slabs V_i = V + i slab (N x R); out[i R + c] = <V_i, w>
 void launch_multi_dot(int64_t N, int R, const double* V, int64_t slab, int nv, const double* w, double* partials,

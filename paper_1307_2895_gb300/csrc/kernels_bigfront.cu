@@ -152,6 +152,68 @@ __global__ void __launch_bounds__(TT) k_bf_sketch(const FrontDesc* __restrict__ 
     }
 }
 
+// ---- power iteration on the sketch: Z = Y M^T (ell x nN, row-major, in the
+// spare region after Y), then Y = Z M (ell x nc, column-major)
+template <typename T>
+__global__ void __launch_bounds__(TT) k_bf_power_z(const FrontDesc* __restrict__ fronts, const int* __restrict__ big,
+                                                   const int* __restrict__ sketch, T* __restrict__ fwork) {
+  __shared__ TileSmem<T> sm;
+  const FrontDesc fd = fronts[big[blockIdx.y]];
+  const BfView v = bf_view(fd);
+  const int nc = fd.nc, nN = fd.nN;
+  const int ell = sketch ? sketch[big[blockIdx.y]] : 0;
+  if (ell <= 0 || ell >= nc || ell >= nN) return;
+  const int tcn = (nN + TB - 1) / TB;
+  if ((int)blockIdx.x >= ((ell + TB - 1) / TB) * tcn) return;
+  const int r0 = (blockIdx.x / tcn) * TB, c0 = (blockIdx.x % tcn) * TB;
+  const T* M = fwork + v.M;
+  const T* Y = fwork + v.Y;
+  T* Z = fwork + v.Y + (int64_t)nc * nc;
+  T acc[4][4];
+  zero_acc(acc);
+  tile_mma<T, false>(
+      sm, acc, nc, [&](int r, int j) { return (r0 + r < ell) ? Y[(int64_t)j * ell + r0 + r] : T(0); },
+      [&](int j, int i) { return (c0 + i < nN) ? M[(int64_t)j * nN + c0 + i] : T(0); });
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = r0 + ty + 16 * i, c = c0 + tx + 16 * j;
+      if (r < ell && c < nN) Z[(int64_t)r * nN + c] = acc[i][j];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TT) k_bf_power_y(const FrontDesc* __restrict__ fronts, const int* __restrict__ big,
+                                                   const int* __restrict__ sketch, T* __restrict__ fwork) {
+  __shared__ TileSmem<T> sm;
+  const FrontDesc fd = fronts[big[blockIdx.y]];
+  const BfView v = bf_view(fd);
+  const int nc = fd.nc, nN = fd.nN;
+  const int ell = sketch ? sketch[big[blockIdx.y]] : 0;
+  if (ell <= 0 || ell >= nc || ell >= nN) return;
+  const int tcn = (nc + TB - 1) / TB;
+  if ((int)blockIdx.x >= ((ell + TB - 1) / TB) * tcn) return;
+  const int r0 = (blockIdx.x / tcn) * TB, c0 = (blockIdx.x % tcn) * TB;
+  const T* M = fwork + v.M;
+  const T* Z = fwork + v.Y + (int64_t)nc * nc;
+  T* Y = fwork + v.Y;
+  T acc[4][4];
+  zero_acc(acc);
+  tile_mma<T, true>(
+      sm, acc, nN, [&](int r, int i) { return (r0 + r < ell) ? Z[(int64_t)(r0 + r) * nN + i] : T(0); },
+      [&](int i, int c) { return (c0 + c < nc) ? M[(int64_t)(c0 + c) * nN + i] : T(0); });
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = r0 + ty + 16 * i, c = c0 + tx + 16 * j;
+      if (r < ell && c < nc) Y[(int64_t)c * ell + r] = acc[i][j];
+    }
+}
+
 // ---- the ID, one thread block per front.
 // pass 0: fronts with a valid sketch size take the pivoted QR of Y (rank
 // rule at kSketchRankTol * eps), then T by least squares on a copy of M
@@ -167,7 +229,8 @@ template <typename T>
 __global__ void k_bf_id(const FrontDesc* __restrict__ fronts, const int* __restrict__ big,
                         const int* __restrict__ sketch, const int* __restrict__ ipool, T* __restrict__ fwork,
                         T* __restrict__ fac, int* __restrict__ obuf, int* __restrict__ state, double eps,
-                        int* status, int pass, int defer_qr, const double* __restrict__ m2part, int nm) {
+                        int* status, int pass, int defer_qr, const double* __restrict__ m2part, int nm,
+                        int power) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int f = big[blockIdx.x];
   const FrontDesc fd = fronts[f];
@@ -187,8 +250,8 @@ __global__ void k_bf_id(const FrontDesc* __restrict__ fronts, const int* __restr
   int* chosen = perm + nc;                                      // nc
   T* A = fwork + (use_sketch ? v.Y : v.M);
   T* Tm = fac + fd.fac + front_fac_T(nc);
-  const int k = blk_pivoted_qr(A, m, nc, use_sketch ? eps * kSketchRankTol : eps, status, !use_sketch, sq, vv, perm,
-                               chosen);
+  const int k = blk_pivoted_qr(A, m, nc, use_sketch ? sketch_rank_tol(eps, power) : eps, status, !use_sketch, sq,
+                               vv, perm, chosen);
   if (use_sketch && k >= ell) {                                 // saturated: fall back
     if (threadIdx.x == 0) {
       state[blockIdx.x] = 2;
@@ -579,6 +642,12 @@ void launch_bigfront_id(const FrontDesc* fronts, const int* big, int nbig, const
     const int tiles = ((max_ell + TB - 1) / TB) * ((max_nc + TB - 1) / TB);
     k_bf_sketch<T><<<dim3(tiles, nbig), TT, 0, st>>>(fronts, big, sketch, ipool, fwork, ss);
     ++nl;
+    const int ztiles = ((max_ell + TB - 1) / TB) * ((max_nN + TB - 1) / TB);
+    for (int g = 0; g < ss.power; ++g) {
+      k_bf_power_z<T><<<dim3(ztiles, nbig), TT, 0, st>>>(fronts, big, sketch, fwork);
+      k_bf_power_y<T><<<dim3(tiles, nbig), TT, 0, st>>>(fronts, big, sketch, fwork);
+      nl += 2;
+    }
   }
   const int smem = (int)(sizeof(double) * (max_nc + max_nN) + sizeof(int) * 2 * max_nc + 64);
   if (smem > 48 * 1024)
@@ -625,7 +694,7 @@ void launch_bigfront_id(const FrontDesc* fronts, const int* big, int nbig, const
     }
   }
   k_bf_id<T><<<nbig, 256, smem, st>>>(fronts, big, sketch, ipool, fwork, fac, obuf, state, eps, status, 0,
-                                      coop ? 1 : 0, m2part, nm);
+                                      coop ? 1 : 0, m2part, nm, ss.power);
   ++nl;
   bool done = false;
   if (coop) {
@@ -666,7 +735,7 @@ void launch_bigfront_id(const FrontDesc* fronts, const int* big, int nbig, const
   }
   if (!done && (sk || coop)) {
     k_bf_id<T><<<nbig, 256, smem, st>>>(fronts, big, sketch, ipool, fwork, fac, obuf, state, eps, status, 1, 0,
-                                        m2part, nm);
+                                        m2part, nm, ss.power);
     ++nl;
   }
   note_launches(nl);

@@ -272,7 +272,26 @@ __global__ void k_front(const FrontDesc* __restrict__ fronts, const CellDesc* __
       Y[e] = a;
     }
     __syncthreads();
-    int ks = blk_pivoted_qr(Y, ell, nc, eps * kSketchRankTol, status, false, sq, v, perm, chosen);
+    // power iterations Y <- (Y M^T) M, Z = Y M^T in PH (ell x nN, row-major)
+    for (int g = 0; g < ss.power; ++g) {
+      for (int64_t e = threadIdx.x; e < (int64_t)ell * nN; e += blockDim.x) {
+        const int r = (int)(e / nN), i = (int)(e % nN);
+        T a = T(0);
+        for (int j = 0; j < nc; ++j) a += Y[(int64_t)j * ell + r] * M[(int64_t)j * nN + i];
+        PH[e] = a;
+      }
+      __syncthreads();
+      for (int64_t e = threadIdx.x; e < (int64_t)ell * nc; e += blockDim.x) {
+        const int j = (int)(e / ell), r = (int)(e % ell);
+        const T* ph = PH + (int64_t)r * nN;
+        const T* mc = M + (int64_t)j * nN;
+        T a = T(0);
+        for (int i = 0; i < nN; ++i) a += ph[i] * mc[i];
+        Y[e] = a;
+      }
+      __syncthreads();
+    }
+    int ks = blk_pivoted_qr(Y, ell, nc, sketch_rank_tol(eps, ss.power), status, false, sq, v, perm, chosen);
     bool ok = false;
     if (ks < ell) {
       // accept when every residual column |M_r - M_s T|_j <= eps max_j |M_j|

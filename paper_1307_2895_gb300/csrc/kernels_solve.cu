@@ -379,6 +379,30 @@ __device__ __forceinline__ double widen<float>(float v) {
   return __longlong_as_double((long long)(sgn | (ex << 52) | man));
 }
 
+// Narrowing double -> TZ; for float, round-to-nearest-even on the integer
+// pipes when the result is a normal float (the same value as the hardware
+// conversion), the hardware conversion otherwise (zero, subnormal, overflow,
+// infinity, NaN).
+template <typename TZ>
+__device__ __forceinline__ TZ narrow(double v) { return (TZ)v; }
+template <>
+__device__ __forceinline__ float narrow<float>(double v) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  const unsigned e = (unsigned)(u >> 52) & 0x7ffu;
+  if (e < 897u || e > 1150u) return (float)v;          // float exponent outside 1..254
+  const unsigned long long man = u & 0xFFFFFFFFFFFFFull;
+  unsigned m = (unsigned)(man >> 29);
+  const unsigned rem = (unsigned)(man & 0x1FFFFFFFull), half = 0x10000000u;
+  if (rem > half || (rem == half && (m & 1u))) ++m;
+  unsigned fe = e - 896u;
+  if (m == 0x800000u) {                                 // the rounding carried into the exponent
+    m = 0u;
+    ++fe;
+  }
+  if (fe >= 255u) return (float)v;                      // rounds to infinity
+  return __uint_as_float(((unsigned)(u >> 63) << 31) | (fe << 23) | m);
+}
+
 // (A x)[e] for element e = gid * R + c from the weights (boundary neighbours
 // have weight +0.0 exactly and are read at the node itself; the test is on
 // the bits, off the FP64 pipe)
@@ -399,9 +423,14 @@ __device__ __forceinline__ double stencil_w(const double* __restrict__ W, int m,
   return y;
 }
 
+// q = A p and pq = p.q per column; with alpha_out, the last block also sets
+// alpha = rz / pq on the active columns (0 elsewhere), once per column, so
+// that the update kernel divides nothing (FP64 division is a long sequence
+// on this GPU's narrow FP64 pipe).
 template <int R, int DIM>
 __global__ void k_mv_dot_e(const double* __restrict__ W, int m, int64_t N, const double* __restrict__ p,
-                           double* __restrict__ q, double* partials, unsigned* counter, double* pq) {
+                           double* __restrict__ q, double* partials, unsigned* counter, double* pq,
+                           const double* rz, const int* active, double* alpha_out) {
   pdl_enter();
   double acc[1] = {0.0};
   const int64_t n = N * R, stride = (int64_t)gridDim.x * blockDim.x;
@@ -424,20 +453,22 @@ __global__ void k_mv_dot_e(const double* __restrict__ W, int m, int64_t N, const
     q[e] = v;
     acc[0] = fma(v, p[e], acc[0]);
   }
-  grid_reduce_cols<R, 1>(acc, partials, counter, pq);
+  if (grid_reduce_cols<R, 1>(acc, partials, counter, pq) && alpha_out && threadIdx.x < R) {
+    const int c = threadIdx.x;
+    alpha_out[c] = (active[c] && pq[c] != 0.0) ? rz[c] / pq[c] : 0.0;
+  }
 }
 
-// alpha = rz/pq (active columns); x += alpha p; r -= alpha q; rr = r.r; zin = (TZ) r
+// x += alpha p; r -= alpha q (alpha from k_mv_dot_e, 0 on frozen columns);
+// rr = r.r; zin = (TZ) r
 template <int R, typename TZ>
 __global__ void k_axpy2_e(int64_t N, double* __restrict__ x, double* __restrict__ r,
-                          const double* __restrict__ p, const double* __restrict__ q,
-                          const double* rz, const double* pq, const int* active, double* alpha_out,
+                          const double* __restrict__ p, const double* __restrict__ q, const double* alpha,
                           double* partials, unsigned* counter, double* rr, TZ* __restrict__ zin,
                           const double* thr2, int* active_next, double* ring_rr) {
   pdl_enter();
   const int c = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) % R);
-  const double a = (active[c] && pq[c] != 0.0) ? rz[c] / pq[c] : 0.0;
-  if (blockIdx.x == 0 && threadIdx.x < R) alpha_out[threadIdx.x] = a;
+  const double a = alpha[c];
   double acc[1] = {0.0};
   const int64_t n = N * R, stride = (int64_t)gridDim.x * blockDim.x;
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -455,7 +486,7 @@ __global__ void k_axpy2_e(int64_t N, double* __restrict__ x, double* __restrict_
       x[e + u * stride] = fma(a, pv[u], xv[u]);
       const double rn = fma(-a, qv[u], rv[u]);
       r[e + u * stride] = rn;
-      zin[e + u * stride] = (TZ)rn;
+      zin[e + u * stride] = narrow<TZ>(rn);
       acc[0] = fma(rn, rn, acc[0]);
     }
   }
@@ -463,7 +494,7 @@ __global__ void k_axpy2_e(int64_t N, double* __restrict__ x, double* __restrict_
     x[e] = fma(a, p[e], x[e]);
     const double rv = fma(-a, q[e], r[e]);
     r[e] = rv;
-    zin[e] = (TZ)rv;
+    zin[e] = narrow<TZ>(rv);
     acc[0] = fma(rv, rv, acc[0]);
   }
   // the last block (every block has read active[] by then): the columns still
@@ -478,11 +509,12 @@ __global__ void k_axpy2_e(int64_t N, double* __restrict__ x, double* __restrict_
   }
 }
 
-// out = [r.z | z.q]
+// out = [r.z | z.q]; the last block also sets beta = -alpha zq / rz_old per
+// column (the flexible / Polak-Ribiere form; 0 where rz_old is 0)
 template <int R, typename TZ>
 __global__ void k_dot2_e(int64_t N, const double* __restrict__ r, const TZ* __restrict__ z,
                          const double* __restrict__ q, double* partials, unsigned* counter, double* out,
-                         double* ring_rz) {
+                         double* ring_rz, const double* alpha, const double* rz_old, double* beta_out) {
   pdl_enter();
   double acc[2] = {0.0, 0.0};
   const int64_t n = N * R, stride = (int64_t)gridDim.x * blockDim.x;
@@ -506,22 +538,25 @@ __global__ void k_dot2_e(int64_t N, const double* __restrict__ r, const TZ* __re
     acc[0] = fma(r[e], zv, acc[0]);
     acc[1] = fma(zv, q[e], acc[1]);
   }
-  if (grid_reduce_cols<R, 2>(acc, partials, counter, out) && ring_rz && threadIdx.x < R) {
-    ring_rz[threadIdx.x] = out[threadIdx.x];   // r.z for the host's breakdown check
-    __threadfence_system();
+  if (grid_reduce_cols<R, 2>(acc, partials, counter, out) && threadIdx.x < R) {
+    const int c = threadIdx.x;
+    beta_out[c] = rz_old[c] != 0.0 ? -alpha[c] * out[R + c] / rz_old[c] : 0.0;
+    if (ring_rz) {
+      ring_rz[c] = out[c];   // r.z for the host's breakdown check
+      __threadfence_system();
+    }
   }
 }
 
-// beta = -alpha zq / rz_old (flexible / Polak-Ribiere form); p = z + beta p
+// p = z + beta p (beta from k_dot2_e; p = z on a restart)
 template <int R, typename TZ>
 __global__ void k_update_p_e(int64_t N, double* __restrict__ p, const TZ* __restrict__ z,
-                             const double* alpha, const double* rz_old, const double* rzzq,
-                             const int* active, int restart) {
+                             const double* betav, const double* rz_old, const int* active, int restart) {
   pdl_enter();
   const int c = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) % R);
   if (!active[c]) return;
   const bool rs = restart || rz_old[c] == 0.0;
-  const double beta = rs ? 0.0 : -alpha[c] * rzzq[R + c] / rz_old[c];
+  const double beta = rs ? 0.0 : betav[c];
   const int64_t n = N * R, stride = (int64_t)gridDim.x * blockDim.x;
   int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   for (; e + 3 * stride < n; e += 4 * stride) {
@@ -774,57 +809,60 @@ void launch_stencil_weights(GridInfo g, const double* a_stag, const double* b, d
 }
 
 void launch_mv_dot_e(GridInfo g, const double* W, const double* p, double* q, int R_, double* partials,
-                     unsigned* counter, double* pq, cudaStream_t st) {
+                     unsigned* counter, double* pq, cudaStream_t st, const double* rz, const int* active,
+                     double* alpha) {
   const int64_t N = grid_n(g);
   note_launches(1);
   if (g.dim == 2)
     DISPATCH_POW2(R_, (launch_pdl(k_mv_dot_e<R, 2>, elem_blocks(N * R), kVecThreads, st, W, g.m, N, p, q,
-                                  partials, counter, pq)));
+                                  partials, counter, pq, rz, active, alpha)));
   else
     DISPATCH_POW2(R_, (launch_pdl(k_mv_dot_e<R, 3>, elem_blocks(N * R), kVecThreads, st, W, g.m, N, p, q,
-                                  partials, counter, pq)));
+                                  partials, counter, pq, rz, active, alpha)));
 }
 
 template <typename TZ>
 void launch_axpy2_e(int64_t N, int R_, double* x, double* r, const double* p, const double* q,
-                    const double* rz, const double* pq, const int* active, double* alpha, double* partials,
-                    unsigned* counter, double* rr, TZ* zin, cudaStream_t st, const double* thr2,
-                    int* active_next, double* ring_rr) {
+                    const double* alpha, double* partials, unsigned* counter, double* rr, TZ* zin, cudaStream_t st,
+                    const double* thr2, int* active_next, double* ring_rr) {
   note_launches(1);
-  DISPATCH_POW2(R_, launch_pdl(k_axpy2_e<R, TZ>, elem_blocks(N * R), kVecThreads, st, N, x, r, p, q, rz, pq,
-                               active, alpha, partials, counter, rr, zin, thr2, active_next, ring_rr));
+  DISPATCH_POW2(R_, launch_pdl(k_axpy2_e<R, TZ>, elem_blocks(N * R), kVecThreads, st, N, x, r, p, q, alpha,
+                               partials, counter, rr, zin, thr2, active_next, ring_rr));
 }
 
 template <typename TZ>
 void launch_dot2_e(int64_t N, int R_, const double* r, const TZ* z, const double* q, double* partials,
-                   unsigned* counter, double* out, cudaStream_t st, double* ring_rz) {
+                   unsigned* counter, double* out, cudaStream_t st, double* ring_rz, const double* alpha,
+                   const double* rz_old, double* beta) {
   note_launches(1);
   DISPATCH_POW2(R_, launch_pdl(k_dot2_e<R, TZ>, elem_blocks(N * R), kVecThreads, st, N, r, z, q, partials,
-                               counter, out, ring_rz));
+                               counter, out, ring_rz, alpha, rz_old, beta));
 }
 
 template <typename TZ>
-void launch_update_p_e(int64_t N, int R_, double* p, const TZ* z, const double* alpha, const double* rz_old,
-                       const double* rzzq, const int* active, int restart, cudaStream_t st) {
+void launch_update_p_e(int64_t N, int R_, double* p, const TZ* z, const double* beta, const double* rz_old,
+                       const int* active, int restart, cudaStream_t st) {
   note_launches(1);
-  DISPATCH_POW2(R_, launch_pdl(k_update_p_e<R, TZ>, elem_blocks(N * R), kVecThreads, st, N, p, z, alpha, rz_old,
-                               rzzq, active, restart));
+  DISPATCH_POW2(R_, launch_pdl(k_update_p_e<R, TZ>, elem_blocks(N * R), kVecThreads, st, N, p, z, beta, rz_old,
+                               active, restart));
 }
 
 template void launch_axpy2_e<double>(int64_t, int, double*, double*, const double*, const double*,
-                                     const double*, const double*, const int*, double*, double*,
-                                     unsigned*, double*, double*, cudaStream_t, const double*, int*, double*);
+                                     const double*, double*, unsigned*, double*, double*, cudaStream_t,
+                                     const double*, int*, double*);
 template void launch_axpy2_e<float>(int64_t, int, double*, double*, const double*, const double*,
-                                    const double*, const double*, const int*, double*, double*,
-                                    unsigned*, double*, float*, cudaStream_t, const double*, int*, double*);
+                                    const double*, double*, unsigned*, double*, float*, cudaStream_t,
+                                    const double*, int*, double*);
 template void launch_dot2_e<double>(int64_t, int, const double*, const double*, const double*, double*,
-                                    unsigned*, double*, cudaStream_t, double*);
+                                    unsigned*, double*, cudaStream_t, double*, const double*, const double*,
+                                    double*);
 template void launch_dot2_e<float>(int64_t, int, const double*, const float*, const double*, double*,
-                                   unsigned*, double*, cudaStream_t, double*);
+                                   unsigned*, double*, cudaStream_t, double*, const double*, const double*,
+                                   double*);
 template void launch_update_p_e<double>(int64_t, int, double*, const double*, const double*, const double*,
-                                        const double*, const int*, int, cudaStream_t);
+                                        const int*, int, cudaStream_t);
 template void launch_update_p_e<float>(int64_t, int, double*, const float*, const double*, const double*,
-                                       const double*, const int*, int, cudaStream_t);
+                                       const int*, int, cudaStream_t);
 
 void launch_set_active(int nr, const double* rr, const double* thr2, int* active, cudaStream_t st) {
   note_launches(1);

@@ -181,3 +181,14 @@ def test_wait_selftest_argument_errors_without_gpu():
     assert lib.hif_wait_selftest(0, 0, None) == hif.HIF_ERR_ARG
     assert lib.hif_wait_selftest(1, (1 << 22) + 1, None) == hif.HIF_ERR_ARG
     assert lib.hif_wait_selftest(2, 2_000_000_000, None) == hif.HIF_ERR_ARG
+
+
+def test_sketch_power_argument_error_without_gpu():
+    lib = hif.load(build_if_missing=True)
+    a, b = np.ones(2 * 16 * 15), np.zeros(225)
+    h = ctypes.c_void_p()
+    grid = hif._Grid(2, 16, 8, 1)
+    opts = hif._Opts(0, 0, 1, 10, None, None, 0, 0, 0, 0, 0, 3)
+    rc = lib.hif_factor(ctypes.byref(grid), a.ctypes.data, b.ctypes.data, None, 1e-6, ctypes.byref(opts),
+                        ctypes.byref(h))
+    assert rc == hif.HIF_ERR_ARG and b"sketch_power" in lib.hif_last_error()

@@ -85,6 +85,35 @@ def test_hifde3x_matches_oracle(hiflib, n, field, eps, big_cell):
         assert np.abs(y - o).max() <= tol * np.abs(o).max()
 
 
+@pytest.mark.parametrize("n,edge_start", [(16, 0), (32, 0), (32, 2), pytest.param(48, 2, marks=pytest.mark.slow)])
+def test_hifde3x_edge_start_matches_oracle(hiflib, n, edge_start):
+    """The rule of thumb's option (Section 4.5): edges from level 0 (the
+    assembled stage starts after level 0's faces) or from level 2 (31^3: none
+    at all, the result is hifde3's; 47^3: levels 0-2 are hifde3's)."""
+    from paper_1307_2895_gb300 import hif
+    eps = 1e-3
+    a, b = _fields(n, "lap")
+    A = stencil.assemble(3, n, a, b)
+    F = hifde.factor3x(A, n, eps, edge_start=edge_start)
+    x = inputs.rhs(3, n, 2, seed=5)
+    G = hif.factor(3, n, a, b, eps, variant="hifde3x", precision="fp64", edge_start=edge_start)
+    try:
+        fronts, root = G.structure()
+        yi = G.apply(x, inverse=True)
+    finally:
+        G.free()
+    ostruct, oroot = F.skeleton_structure()
+    got = {(lev, tuple(c)): sk for lev, c, sk in fronts}
+    nexp = 0
+    for lev, dd in enumerate(ostruct):
+        for key, (c, sk, k) in dd.items():
+            nexp += 1
+            assert got.get((lev, tuple(c))) == sk, f"fractional level {lev} group {c[:4]}...: skeletons differ"
+    assert len(fronts) == nexp and root == oroot
+    oi = F.apply_inverse(x)
+    assert np.linalg.norm(yi - oi) <= 1e-10 * np.linalg.norm(oi)
+
+
 def test_hifde3x_pcg_reaches_1e12(hiflib):
     """FP32-stored factor of hifde3x as the preconditioner: PCG to 1e-12,
     re-checked on the host in extended precision."""

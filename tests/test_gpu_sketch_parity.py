@@ -51,22 +51,24 @@ def _phi(N, oversample):
     return phi
 
 
-@pytest.mark.parametrize("dim,n,field,eps,oversample,big_cell", [
-    (2, 64, "lap", 1e-6, 2, 0),
-    (2, 64, "contrast", 1e-6, 2, 0),
-    (2, 128, "contrast", 1e-9, 3, 0),
-    (3, 32, "lap", 1e-3, 10, 128),
-    (3, 20, "contrast", 1e-4, 4, 128),
+@pytest.mark.parametrize("dim,n,field,eps,oversample,big_cell,power", [
+    (2, 64, "lap", 1e-6, 2, 0, 0),
+    (2, 64, "contrast", 1e-6, 2, 0, 0),
+    (2, 128, "contrast", 1e-9, 3, 0, 0),
+    (3, 32, "lap", 1e-3, 10, 128, 0),
+    (3, 20, "contrast", 1e-4, 4, 128, 0),
+    (2, 64, "contrast", 1e-3, 2, 0, 1),      # power iterations on the sketch (Section 4.5)
+    (3, 32, "lap", 1e-3, 10, 128, 1),
 ])
-def test_sketched_id_matches_oracle(hiflib, dim, n, field, eps, oversample, big_cell):
+def test_sketched_id_matches_oracle(hiflib, dim, n, field, eps, oversample, big_cell, power):
     from paper_1307_2895_gb300 import hif
     a, b = _fields(dim, n, field)
     A = stencil.assemble(dim, n, a, b)
     N = (n - 1) ** dim
-    F = hifde.factor(A, dim, n, eps, sketch=_phi(N, oversample))
+    F = hifde.factor(A, dim, n, eps, sketch=_phi(N, oversample), sketch_power=power)
     x = inputs.rhs(dim, n, 2, seed=5)
     G = hif.factor(dim, n, a, b, eps, precision="fp64", id_mode="rand", oversample=oversample, seed=SEED,
-                   big_cell=big_cell)
+                   big_cell=big_cell, sketch_power=power)
     try:
         fronts, root = G.structure()
         st = G.stats()

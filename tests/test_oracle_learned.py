@@ -124,3 +124,25 @@ def test_factor_with_undersized_sketch_falls_back_everywhere():
     assert F1.skeleton_structure() == F0.skeleton_structure()
     nfronts = sum(len(lev.fronts) for lev in F1.levels)
     assert F1.sketched == 0 and F1.fallback == nfronts
+
+
+def test_power_sketch_recovers_a_slowly_decaying_spectrum():
+    """Power iterations (Section 4.5's remedy for inaccurate sketches): with
+    one power iteration the rank rule is applied at (eps/10)^3 to Y, whose
+    singular values are M's cubed, and recovers the numerical rank k of a
+    matrix with a gap at k; with two, (eps/10)^5 = 1e-20 lies below FP64
+    resolution, the sketch saturates and the ID falls back (the option is
+    meaningful only while that threshold stays well above 1e-16)."""
+    rng = np.random.default_rng(3)
+    m, n, k, eps = 300, 120, 20, 1e-3
+    U, _ = np.linalg.qr(rng.standard_normal((m, n)))
+    V, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    s = np.concatenate([np.logspace(0, -2, k), 1e-5 * np.logspace(0, -1, n - k)])
+    M = (U * s) @ V.T
+    Phi = inputs.standard_normal(9, (k + 4) * m).reshape(k + 4, m)
+    idp, okp = learned.randomized_id(M, eps, Phi, power=1)
+    assert okp and len(idp.sk) == k
+    E = M[:, idp.rd] - M[:, idp.sk] @ idp.T
+    assert np.linalg.norm(E, axis=0).max() <= eps * np.linalg.norm(M, axis=0).max()
+    id2, ok2 = learned.randomized_id(M, eps, Phi, power=2)
+    assert not ok2 and len(id2.sk) == k + 4
