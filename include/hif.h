@@ -45,7 +45,9 @@ extern "C" {
 typedef enum hif_status {
   HIF_OK = 0,
   HIF_ERR_ARG = 1,       /* invalid argument (grid, sizes, pointers)            */
-  HIF_ERR_NOT_SPD = 2,   /* a non-positive pivot in a diagonal-block Cholesky   */
+  HIF_ERR_NOT_SPD = 2,   /* a zero or non-finite pivot in a diagonal block, or a
+                            negative one where only Cholesky applies (the tiled
+                            elimination of large blocks)                        */
   HIF_ERR_NOCONV = 3,    /* the iteration reached maxit; info is still filled   */
   HIF_ERR_TIMEOUT = 4,   /* a bounded device wait ran out                       */
   HIF_ERR_CUDA = 5,      /* a CUDA runtime call failed                          */
@@ -67,7 +69,16 @@ typedef enum hif_status {
  * point (HIF_ERR_ARG if that would exceed 48 GB). */
 enum { HIF_VARIANT_MF = 0, HIF_VARIANT_HIFDE = 1, HIF_VARIANT_HIFDE3X = 2 };
 
-/* Arithmetic of the factorization.  FP64: every block operation in double.
+/* Diagonal blocks (A_pp of Lemma 2.1, B_rr of Lemma 2.4, the root D) are
+ * factored by Cholesky when positive definite; a negative pivot (an
+ * indefinite A, e.g. the Helmholtz operator b = -k^2 of Section 5's
+ * Examples 3 and 6) makes that block an LDL^T decomposition with 1 x 1
+ * pivots in order, D = diag(+-1), in the blocks one thread block factors
+ * (every 2D block at the sizes here; 3D blocks below big_cell DOFs) and in
+ * the FP64 modes.  F^-1 is then not positive definite: solve with GMRES
+ * (hif_set_solver; HIF_SOLVER_AUTO switches on CG's breakdown).
+ *
+ * Arithmetic of the factorization.  FP64: every block operation in double.
  * MIXED: cell and front blocks, the factor and the apply of F^-1 in float;
  * the root block D is factored in double; the ID's column norms and pivot
  * tests are accumulated in double; diagonal-block Cholesky pivots that fall
@@ -178,6 +189,8 @@ typedef struct hif_stats_t {
   double factor_flops;         /* algorithmic flops of the factorization         */
   double apply_bytes;          /* factor bytes read by one apply of F^-1         */
   double t_factor_ms;          /* device time of the last hif_factor             */
+  int negative_pivots;         /* pivots < 0: diagonal blocks of an indefinite A
+                                  factored as L D L^T, D = diag(+-1)            */
 } hif_stats_t;
 
 /*

@@ -162,13 +162,53 @@ class ActiveMatrix:
 # Lemma 2.1: sparse elimination
 # --------------------------------------------------------------------------
 
+def ldl_signed(A: np.ndarray):
+    """A = L diag(s) L^T with L lower triangular and s_j = +-1: the LDL^T
+    decomposition with 1 x 1 pivots taken in order, its D = diag(s) |D| split
+    as |D|^(1/2) into L (so L = L_unit |D|^(1/2)).  Right-looking: pivot d_jj,
+    s_j = sign(d_jj), l_jj = |d_jj|^(1/2), column below divided by s_j l_jj
+    (so that s_j l_ij l_jj is the entry), trailing block minus s_j l l^T.
+    Raises LinAlgError on a zero pivot."""
+    n = A.shape[0]
+    W = np.array(A, dtype=np.float64, copy=True)
+    L = np.zeros((n, n))
+    s = np.ones(n)
+    for j in range(n):
+        d = W[j, j]
+        if d == 0.0 or not np.isfinite(d):
+            raise np.linalg.LinAlgError("zero pivot in the LDL^T decomposition")
+        s[j] = 1.0 if d > 0 else -1.0
+        L[j, j] = np.sqrt(abs(d))
+        L[j + 1:, j] = W[j + 1:, j] / (s[j] * L[j, j])
+        W[j + 1:, j + 1:] -= s[j] * np.outer(L[j + 1:, j], L[j + 1:, j])
+    return L, s
+
+
+def factor_block(M: np.ndarray):
+    """A diagonal block's factor (Section 5: Cholesky when SPD, an LDL^T
+    decomposition otherwise): (L, s) with M = L diag(s) L^T, s = None when
+    the Cholesky decomposition exists (all signs +1)."""
+    try:
+        return np.linalg.cholesky(M), None
+    except np.linalg.LinAlgError:
+        return ldl_signed(M)
+
+
 @dataclasses.dataclass
 class CellRecord:
-    """Elimination operator S_p of Lemma 2.1 with A_pp = L L^T (D_p = I)."""
+    """Elimination operator S_p of Lemma 2.1 with A_pp = L D_p L^T, D_p =
+    diag(sgn) (sgn None: D_p = I, the Cholesky case).  The up step applies
+    D_p^-1 = D_p to the eliminated values, so that F^-1 is the product of
+    the up steps, the root and the down steps."""
     p: np.ndarray      # eliminated indices (ascending)
     q: np.ndarray      # neighbour indices c^N (ascending)
-    L: np.ndarray      # lower Cholesky factor of A_pp
+    L: np.ndarray      # lower triangular factor of A_pp
     Aqp: np.ndarray    # A_qp at the time of elimination
+    sgn: np.ndarray = None   # diagonal of D_p (+-1), None when all +1
+
+
+def _sgn(rec, v):
+    return v if rec.sgn is None else rec.sgn.reshape((-1,) + (1,) * (v.ndim - 1)) * v
 
 
 def eliminate(A: ActiveMatrix, p: List[int]) -> CellRecord:
@@ -176,47 +216,47 @@ def eliminate(A: ActiveMatrix, p: List[int]) -> CellRecord:
     q = A.neighbors(p)
     App = A.block(p, p)
     Aqp = A.block(q, p)
-    L = np.linalg.cholesky(App)
+    L, sgn = factor_block(App)
     if q:
-        # A_qp A_pp^{-1} A_qp^T through the Cholesky factor: (A_qp L^-T)(A_qp L^-T)^T
+        # A_qp A_pp^{-1} A_qp^T through the factor: (A_qp L^-T) D_p (A_qp L^-T)^T
         Y = sla.solve_triangular(L, Aqp.T, lower=True)        # L^-1 A_qp^T
-        A.add_block(q, q, -(Y.T @ Y))
+        A.add_block(q, q, -(Y.T @ (Y if sgn is None else sgn[:, None] * Y)))
     A.remove(p)
-    return CellRecord(np.array(p, dtype=np.int64), np.array(q, dtype=np.int64), L, Aqp)
+    return CellRecord(np.array(p, dtype=np.int64), np.array(q, dtype=np.int64), L, Aqp, sgn)
 
 
 def apply_S_T(rec: CellRecord, x: np.ndarray) -> None:
-    """x <- S_p^T x  (in place, x may have several columns).
-
-    S_p^T = [[L^-1, 0], [-A_qp A_pp^-1, I]] on (p, q)."""
-    xp = sla.solve_triangular(rec.L, x[rec.p], lower=True)
+    """x <- D_p^-1 S_p^T x on p and S_p^T x on q (in place, x may have several
+    columns).  S_p^T = [[L^-1, 0], [-A_qp A_pp^-1, I]] on (p, q)."""
+    xp = _sgn(rec, sla.solve_triangular(rec.L, x[rec.p], lower=True))
     if len(rec.q):
         x[rec.q] -= rec.Aqp @ sla.solve_triangular(rec.L, xp, lower=True, trans="T")
     x[rec.p] = xp
 
 
 def apply_S(rec: CellRecord, x: np.ndarray) -> None:
-    """x <- S_p x:  x_p <- L^-T (x_p - L^-1 A_qp^T x_q)."""
+    """x <- S_p x:  x_p <- L^-T (x_p - D_p^-1 L^-1 A_qp^T x_q)."""
     xp = x[rec.p]
     if len(rec.q):
-        xp = xp - sla.solve_triangular(rec.L, rec.Aqp.T @ x[rec.q], lower=True)
+        xp = xp - _sgn(rec, sla.solve_triangular(rec.L, rec.Aqp.T @ x[rec.q], lower=True))
     x[rec.p] = sla.solve_triangular(rec.L, xp, lower=True, trans="T")
 
 
 def apply_S_inv(rec: CellRecord, x: np.ndarray) -> None:
-    """x <- S_p^{-1} x with S_p^{-1} = [[L^T, L^-1 A_qp^T], [0, I]]."""
+    """x <- S_p^{-1} x with S_p^{-1} = [[L^T, D_p^-1 L^-1 A_qp^T], [0, I]] (the
+    inverse of apply_S)."""
     xp = rec.L.T @ x[rec.p]
     if len(rec.q):
-        xp = xp + sla.solve_triangular(rec.L, rec.Aqp.T @ x[rec.q], lower=True)
+        xp = xp + _sgn(rec, sla.solve_triangular(rec.L, rec.Aqp.T @ x[rec.q], lower=True))
     x[rec.p] = xp
 
 
 def apply_S_inv_T(rec: CellRecord, x: np.ndarray) -> None:
-    """x <- S_p^{-T} x with S_p^{-T} = [[L, 0], [A_qp L^-T, I]]."""
+    """The inverse of apply_S_T: x_q += A_qp L^-T x_p; x_p <- L D_p x_p."""
     xp = x[rec.p].copy()
     if len(rec.q):
         x[rec.q] += rec.Aqp @ sla.solve_triangular(rec.L, xp, lower=True, trans="T")
-    x[rec.p] = rec.L @ xp
+    x[rec.p] = rec.L @ _sgn(rec, xp)
 
 
 # --------------------------------------------------------------------------
@@ -295,9 +335,10 @@ class FrontRecord:
     sk: np.ndarray     # skeleton indices (global, pivot order)
     rd: np.ndarray     # redundant indices (global, ascending)
     T: np.ndarray      # k x |rd|
-    L: np.ndarray      # Cholesky factor of B_rr
+    L: np.ndarray      # lower triangular factor of B_rr (B_rr = L D L^T)
     Bsr: np.ndarray    # B_sr
     near_threshold: bool = False
+    sgn: np.ndarray = None   # diagonal of D (+-1), None when B_rr is SPD
 
 
 def skeletonize(A: ActiveMatrix, c: List[int], idr: IDResult) -> FrontRecord:
@@ -313,16 +354,16 @@ def skeletonize(A: ActiveMatrix, c: List[int], idr: IDResult) -> FrontRecord:
     T = idr.T
     Brr = Arr - T.T @ Asr - Asr.T @ T + T.T @ Ass @ T
     Bsr = Asr - Ass @ T
-    L = np.linalg.cholesky(Brr) if len(rd_l) else np.zeros((0, 0))
+    L, sgn = factor_block(Brr) if len(rd_l) else (np.zeros((0, 0)), None)
     if len(rd_l) and len(sk_l):
         Y = sla.solve_triangular(L, Bsr.T, lower=True)          # L^-1 B_sr^T
-        A.set_block(sk_l, sk_l, Ass - Y.T @ Y)
+        A.set_block(sk_l, sk_l, Ass - Y.T @ (Y if sgn is None else sgn[:, None] * Y))
     A.remove(rd_l)
-    return FrontRecord(c_arr, sk, rd, T, L, Bsr, idr.near_threshold)
+    return FrontRecord(c_arr, sk, rd, T, L, Bsr, idr.near_threshold, sgn)
 
 
 def _front_as_cell(fr: FrontRecord) -> CellRecord:
-    return CellRecord(fr.rd, fr.sk, fr.L, fr.Bsr)
+    return CellRecord(fr.rd, fr.sk, fr.L, fr.Bsr, fr.sgn)
 
 
 def apply_U_T(fr: FrontRecord, x: np.ndarray) -> None:
@@ -383,9 +424,10 @@ class Factor:
     levels: List[Level]
     root: np.ndarray           # s_L (ascending)
     D: np.ndarray              # A_L restricted to s_L
-    Dchol: np.ndarray          # its Cholesky factor
+    Dchol: np.ndarray          # its lower triangular factor (D = Dchol diag(Dsgn) Dchol^T)
     sketched: int = 0          # fronts whose sketched ID passed the check
     fallback: int = 0          # fronts whose sketched ID failed it
+    Dsgn: np.ndarray = None    # signs of D's LDL^T decomposition (None: Cholesky)
 
     # ---- Eq. (4.2): F^-1 = V_0 V_1/2 ... D^-1 ... V_1/2^T V_0^T
     def apply_inverse(self, b: np.ndarray) -> np.ndarray:
@@ -396,7 +438,10 @@ class Factor:
             for fr in lev.fronts:
                 apply_U_T(fr, x)
         if len(self.root):
-            x[self.root] = sla.cho_solve((self.Dchol, True), x[self.root])
+            y = sla.solve_triangular(self.Dchol, x[self.root], lower=True)
+            if self.Dsgn is not None:
+                y = self.Dsgn.reshape((-1,) + (1,) * (y.ndim - 1)) * y
+            x[self.root] = sla.solve_triangular(self.Dchol, y, lower=True, trans="T")
         for lev in reversed(self.levels):             # V, coarsest first
             for fr in lev.fronts:
                 apply_U(fr, x)
@@ -523,8 +568,8 @@ def factor(A_csr, dim: int, n: int, eps: float, leaf: int = 8,
         levels.append(Level(ell, cells, fronts, keys))
     root = np.array(A.active(), dtype=np.int64)
     D = A.block(root.tolist(), root.tolist())
-    Dchol = np.linalg.cholesky(D) if len(root) else np.zeros((0, 0))
-    return Factor(dim, n, L, eps, levels, root, D, Dchol, n_sketched, n_fallback)
+    Dchol, Dsgn = factor_block(D) if len(root) else (np.zeros((0, 0)), None)
+    return Factor(dim, n, L, eps, levels, root, D, Dchol, n_sketched, n_fallback, Dsgn)
 
 
 # --------------------------------------------------------------------------
@@ -661,8 +706,8 @@ def factor3x(A_csr, n: int, eps: float, leaf: int = 8, edge_start: int = 1) -> F
         levels.append(Level(ell, [], efr, ekeys))
     root = np.array(A.active(), dtype=np.int64)
     D = A.block(root.tolist(), root.tolist())
-    Dchol = np.linalg.cholesky(D) if len(root) else np.zeros((0, 0))
-    return Factor(3, n, L, eps, levels, root, D, Dchol)
+    Dchol, Dsgn = factor_block(D) if len(root) else (np.zeros((0, 0)), None)
+    return Factor(3, n, L, eps, levels, root, D, Dchol, 0, 0, Dsgn)
 
 
 # --------------------------------------------------------------------------

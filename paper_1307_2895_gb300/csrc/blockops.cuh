@@ -35,9 +35,20 @@ template <> __device__ __forceinline__ float dsqrt<float>(float x) { return sqrt
 // original diagonal entries (a diagonal tile of a larger matrix whose
 // earlier panels have already been eliminated); the upper triangle is then
 // left untouched.
+// sgn (tau == 0 only): an indefinite block is factored as A = L D L^T with
+// D = diag(sgn), sgn_j = +-1 (Section 5: LDL^T when A is not SPD; 1 x 1
+// pivots in order, |D| split into L): a negative pivot d gives sgn_j = -1,
+// l_jj = sqrt(-d), the column below divided by -l_jj and the trailing update
+// A -= sgn_j l l^T; it is counted in status[4].  Only a zero or non-finite
+// pivot sets bit 0.  With every pivot positive the arithmetic is that of the
+// Cholesky decomposition exactly.  Returns true (in every thread) if a pivot
+// was negative.
 template <typename T>
-__device__ void blk_cholesky(T* A, int n, int ld, int* status, T tau = T(0), const T* d0v = nullptr) {
-  __shared__ T s_piv, s_dmax;
+__device__ bool blk_cholesky(T* A, int n, int ld, int* status, T tau = T(0), const T* d0v = nullptr,
+                             T* sgn = nullptr) {
+  __shared__ T s_piv, s_dmax, s_sgn;
+  __shared__ int s_neg;
+  if (threadIdx.x == 0) s_neg = 0;
   if (tau > T(0)) {
     if (!d0v)
       for (int j = 1 + threadIdx.x; j < n; j += blockDim.x)
@@ -55,6 +66,7 @@ __device__ void blk_cholesky(T* A, int n, int ld, int* status, T tau = T(0), con
   for (int j = 0; j < n; ++j) {
     if (threadIdx.x == 0) {
       T d = A[(int64_t)j * ld + j];
+      T s = T(1);
       if (tau > T(0)) {
         T d0 = d0v ? d0v[j] : (j == 0) ? d : A[(int64_t)(j - 1) * ld + j];
         if (!(d0 > T(0)) || !isfinite((double)d0)) d0 = s_dmax;
@@ -66,16 +78,23 @@ __device__ void blk_cholesky(T* A, int n, int ld, int* status, T tau = T(0), con
           const T floor_d = dsqrt(tau) * d0;
           d = (isfinite((double)d) && fabs((double)d) > (double)floor_d) ? (T)fabs((double)d) : floor_d;
         }
+      } else if (sgn && d < T(0) && isfinite((double)d)) {
+        atomicAdd(status + 4, 1);
+        s = T(-1);
+        d = -d;
+        s_neg = 1;
       } else if (!(d > T(0)) || !isfinite((double)d)) {
         atomicOr(status, 1);
         d = T(1);
       }
       d = dsqrt(d);
       A[(int64_t)j * ld + j] = d;
-      s_piv = T(1) / d;
+      s_piv = s / d;
+      s_sgn = s;
+      if (sgn) sgn[j] = s;
     }
     __syncthreads();
-    const T r = s_piv;
+    const T r = s_piv, sj = s_sgn;
     for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[(int64_t)i * ld + j] *= r;
     __syncthreads();
     const int m = n - j - 1;
@@ -84,10 +103,11 @@ __device__ void blk_cholesky(T* A, int n, int ld, int* status, T tau = T(0), con
       int a, b;
       tri_decode(e, a, b);
       const int i = j + 1 + a, k = j + 1 + b;
-      A[(int64_t)i * ld + k] -= A[(int64_t)i * ld + j] * A[(int64_t)k * ld + j];
+      A[(int64_t)i * ld + k] -= (sj * A[(int64_t)i * ld + j]) * A[(int64_t)k * ld + j];
     }
     __syncthreads();
   }
+  return s_neg != 0;
 }
 
 // X = L^{-1} for lower-triangular L (n x n).  X is written in full (zeros
@@ -133,9 +153,9 @@ __device__ void blk_mul_linvT(const T* A, int lda, const T* Linv, int ldl, int m
   __syncthreads();
 }
 
-// C (m x m, full symmetric) -= G G^T, G m x kk.
+// C (m x m, full symmetric) -= G diag(sgn) G^T, G m x kk (sgn NULL: all +1).
 template <typename T>
-__device__ void blk_syrk_sub(T* C, int ldc, const T* G, int ldg, int m, int kk) {
+__device__ void blk_syrk_sub(T* C, int ldc, const T* G, int ldg, int m, int kk, const T* sgn = nullptr) {
   const int64_t tot = (int64_t)m * (m + 1) / 2;
   for (int64_t e = threadIdx.x; e < tot; e += blockDim.x) {
     int i, j;
@@ -143,10 +163,23 @@ __device__ void blk_syrk_sub(T* C, int ldc, const T* G, int ldg, int m, int kk) 
     const T* gi = G + (int64_t)i * ldg;
     const T* gj = G + (int64_t)j * ldg;
     T s = T(0);
-    for (int t = 0; t < kk; ++t) s += gi[t] * gj[t];
+    if (sgn)
+      for (int t = 0; t < kk; ++t) s += (gi[t] * sgn[t]) * gj[t];
+    else
+      for (int t = 0; t < kk; ++t) s += gi[t] * gj[t];
     const T v = C[(int64_t)i * ldc + j] - s;
     C[(int64_t)i * ldc + j] = v;
     C[(int64_t)j * ldc + i] = v;
+  }
+  __syncthreads();
+}
+
+// Columns of G (m x n) times sgn (G <- G diag(sgn)).
+template <typename T>
+__device__ void blk_scale_cols(T* G, int ldg, int m, int n, const T* sgn) {
+  for (int64_t e = threadIdx.x; e < (int64_t)m * n; e += blockDim.x) {
+    const int i = (int)(e / n), j = (int)(e % n);
+    G[(int64_t)i * ldg + j] *= sgn[j];
   }
   __syncthreads();
 }

@@ -221,6 +221,7 @@ struct hif_handle {
   std::vector<LevelFronts> finfo;
   int root_size = 0, n_cells = 0, n_fronts = 0, max_rank = 0, near = 0, clamped = 0;
   int sketched = 0, fallback = 0;
+  int negative = 0;     // negative pivots (LDL^T of indefinite diagonal blocks)
   double t_fronts_ms = 0.0;
   long long factor_bytes = 0;
   double factor_flops = 0.0, apply_bytes = 0.0, t_factor_ms = 0.0;
@@ -314,6 +315,7 @@ void cell_apply_descs(const std::vector<CellDesc>& cd, std::vector<ApplyDesc>& a
     a.G = c.fac + cell_fac_G(c.nI);
     a.L = c.fac + cell_fac_L(c.nI, c.nB);
     a.T = -1;
+    a.S = c.fac + cell_fac_S(c.nI, c.nB);
     ad.push_back(a);
     max_np = std::max(max_np, c.nI);
     max_nq = std::max(max_nq, c.nB);
@@ -647,6 +649,7 @@ struct Factorizer {
       t.Linv = c.fac;
       t.G = c.fac + cell_fac_G(c.nI);
       t.Lp = c.fac + cell_fac_L(c.nI, c.nB);
+      t.S = c.fac + cell_fac_S(c.nI, c.nB);
     }
     upload(tdbuf, td, st);
     launch_tiled_elim<U>(tdbuf.as<TDesc>(), (int)big.size(), max_bI, max_bB, work, fac, status.as<int>(), tau, st,
@@ -673,8 +676,8 @@ struct Factorizer {
 
   void run() {
     const int L = G.L, nchild = 1 << G.dim;
-    status.alloc(4 * sizeof(int), st);
-    CU(cudaMemsetAsync(status.p, 0, 4 * sizeof(int), st));
+    status.alloc(8 * sizeof(int), st);
+    CU(cudaMemsetAsync(status.p, 0, 8 * sizeof(int), st));
     dead.assign(G.N, 0);
     h->cells.resize(L);
     h->fronts.resize(L);
@@ -816,13 +819,14 @@ struct Factorizer {
   // The factorization's device status: counts for hif_stats, then the
   // failures (a non-positive pivot, a bounded wait that ran out).
   void finish_status() {
-    int hs2[4] = {0, 0, 0, 0};
-    CU(cudaMemcpyAsync(hs2, status.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    int hs2[5] = {0, 0, 0, 0, 0};
+    CU(cudaMemcpyAsync(hs2, status.p, 5 * sizeof(int), cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
     const int hs = hs2[0];
     h->clamped = hs2[1];
     h->sketched = hs2[2];
     h->fallback = hs2[3];
+    h->negative = hs2[4];
     if (hs & 1) throw HifError(HIF_ERR_NOT_SPD, "non-positive pivot in a diagonal-block Cholesky");
     throw_wait_status(hs & (kWaitGroup | kWaitMma));
   }
@@ -935,6 +939,7 @@ struct Factorizer {
         t.Linv = d.fac;
         t.G = d.fac + front_fac_G(d.nc);
         t.Lp = d.fac + front_fac_L(d.nc);
+        t.S = d.fac + front_fac_S(d.nc);
         td.push_back(t);
       }
       launch_bigfront_form<T>(d_fd, d_big.as<int>(), nbig, obuf.as<int>(), fwork.as<T>(), sw.fac.as<T>(), max_k,
@@ -987,6 +992,7 @@ struct Factorizer {
       a.G = d.fac + front_fac_G(d.nc);
       a.T = d.fac + front_fac_T(d.nc);
       a.L = d.fac + front_fac_L(d.nc);
+      a.S = d.fac + front_fac_S(d.nc);
       sw.max_np = std::max(sw.max_np, nR);
       sw.max_nq = std::max(sw.max_nq, k);
       if (nR > 0) {
@@ -1172,7 +1178,8 @@ void run_apply(hif_handle* h, int mode, T* x, int nrhs) {
       }
       CU(cudaEventRecord(h->ev_pool[h->ev_used], st));
     }
-    const int nl = launch_root_apply<T>(S.max_np, S.ipool, facp(S), x, nrhs, nrhs, h->root_scratch.as<T>(), st);
+    const int nl = launch_root_apply<T>(S.max_np, S.ipool, facp(S), facp(S) + cell_fac_S(S.max_np, 0), x, nrhs,
+                                        nrhs, h->root_scratch.as<T>(), st);
     if (prof) {
       CU(cudaEventRecord(h->ev_pool[h->ev_used + 1], st));
       h->ev_used += 2;
@@ -2166,6 +2173,7 @@ int hif_stats(const hif_handle* h, hif_stats_t* s) {
   s->near_threshold_fronts = h->near;
   s->clamped_pivots = h->clamped;
   s->sketched_fronts = h->sketched;
+  s->negative_pivots = h->negative;
   s->fallback_fronts = h->fallback;
   s->t_fronts_ms = h->t_fronts_ms;
   s->factor_bytes = h->factor_bytes;

@@ -48,7 +48,7 @@ struct FrontDesc {
 struct TDesc {
   int nI, nB;
   int64_t FII, FBI, FBB, X;
-  int64_t Linv, G, Lp;
+  int64_t Linv, G, Lp, S;   // S: the diagonal block's signs (all +1 on this path)
 };
 
 // Block of the factor as the apply sweeps see it.  Cell: p = I, q = B.
@@ -56,10 +56,15 @@ struct TDesc {
 // Linv and L are lower triangular, packed by rows (entry (i, t), t <= i, at
 // i (i + 1) / 2 + t); G and T are row-major nq x np.  Every region starts on
 // a 16-byte boundary (sizes rounded up to 4 elements).
+// A_pp = L D L^T with D = diag(S) (+1 / -1, Section 5's LDL^T of an
+// indefinite diagonal block; all +1 when A_pp is SPD); L^-1 is stored, G is
+// A_qp L^-T D (so that x_q -= G y with y = L^-1 x_p), and the up sweep stores
+// D y as the block's p values.
 struct ApplyDesc {
   int np, nq;
   int64_t ids;         // int pool: ids_p[np] then ids_q[nq]
   int64_t Linv, L, G, T;   // factor pool offsets (T = -1 for cells)
+  int64_t S;           // factor pool offset of the signs (np values)
 };
 
 // Gaussian stream of the randomized ID (Section 4.3) at one fractional level
@@ -91,10 +96,13 @@ void set_last_error(const char* msg);
 // Factor-pool sizes (elements, rounded up to 4 so every region is 16-byte aligned).
 __host__ __device__ inline int64_t pad4(int64_t x) { return (x + 3) & ~int64_t(3); }
 __host__ __device__ inline int64_t packed_size(int64_t n) { return pad4(n * (n + 1) / 2); }
-// cell: Linv | G | L
+// cell: Linv | G | L | S
 __host__ __device__ inline int64_t cell_fac_G(int nI) { return packed_size(nI); }
 __host__ __device__ inline int64_t cell_fac_L(int nI, int nB) { return packed_size(nI) + pad4((int64_t)nB * nI); }
-__host__ __device__ inline int64_t cell_fac_size(int nI, int nB) { return 2 * packed_size(nI) + pad4((int64_t)nB * nI); }
+__host__ __device__ inline int64_t cell_fac_S(int nI, int nB) { return 2 * packed_size(nI) + pad4((int64_t)nB * nI); }
+__host__ __device__ inline int64_t cell_fac_size(int nI, int nB) {
+  return 2 * packed_size(nI) + pad4((int64_t)nB * nI) + pad4(nI);
+}
 // Largest grid of the reducing vector kernels (8 blocks of 256 threads per
 // SM of a 152-SM GB300: enough loads in flight to stream HBM); the solver's
 // partial-sum buffer holds 4 values per block and right-hand side.
@@ -113,11 +121,14 @@ __host__ __device__ inline int64_t cell_x_elems(int nI) {
   const int64_t s = (int64_t)nI * nI;
   return pad4(s > t ? s : t);
 }
-// front with capacity nc: Linv | G | T | L
+// front with capacity nc: Linv | G | T | L | S
 __host__ __device__ inline int64_t front_fac_G(int nc) { return packed_size(nc); }
 __host__ __device__ inline int64_t front_fac_T(int nc) { return packed_size(nc) + pad4((int64_t)nc * nc); }
 __host__ __device__ inline int64_t front_fac_L(int nc) { return packed_size(nc) + 2 * pad4((int64_t)nc * nc); }
-__host__ __device__ inline int64_t front_fac_size(int nc) { return 2 * packed_size(nc) + 2 * pad4((int64_t)nc * nc); }
+__host__ __device__ inline int64_t front_fac_S(int nc) { return 2 * packed_size(nc) + 2 * pad4((int64_t)nc * nc); }
+__host__ __device__ inline int64_t front_fac_size(int nc) {
+  return 2 * packed_size(nc) + 2 * pad4((int64_t)nc * nc) + pad4(nc);
+}
 
 struct GridInfo {
   int dim, n, m;       // m = n - 1 nodes per axis

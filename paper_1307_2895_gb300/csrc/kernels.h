@@ -103,13 +103,14 @@ void launch_wait_test_group(unsigned* bar, int* err, long polls, cudaStream_t st
 void launch_wait_test_mma(int* status, uint64_t ns, cudaStream_t st);
 
 // D^-1 of a root of at least kRootMulti DOFs by the whole GPU (kernels_root.cu):
-// x_root <- L^-T L^-1 x_root on the rows ids[0..np) of x (N x nrhs, row stride
-// ldx), in column chunks of kRootChunk; scratch: 2 np kRootChunk elements.
-// Returns the number of launches.
+// x_root <- L^-T S L^-1 x_root (S = diag(sgn)) on the rows ids[0..np) of x
+// (N x nrhs, row stride ldx), in column chunks of kRootChunk; scratch:
+// 2 np kRootChunk elements.  Returns the number of launches.
 constexpr int kRootMulti = 256;
 constexpr int kRootChunk = 8;
 template <typename T>
-int launch_root_apply(int np, const int* ids, const T* Linv, T* x, int nrhs, int ldx, T* scratch, cudaStream_t st);
+int launch_root_apply(int np, const int* ids, const T* Linv, const T* sgn, T* x, int nrhs, int ldx, T* scratch,
+                      cudaStream_t st);
 
 // rank-prediction MLP (kernels_mlp.cu); idx may be NULL (samples 0..nb-1)
 void mlp_grad(const float* X, const float* t, const int* idx, int nb, float inv_n, const float* prm,

@@ -3,12 +3,15 @@
 // processed R at a time.  Vectors: N x nrhs row-major, row stride ldx.
 //
 // F^-1 = V_0 V_1/2 ... D^-1 ... V_1/2^T V_0^T, per block (p eliminated,
-// q its neighbours; fronts carry T, cells do not):
-//   up   (V^T):  [front] x_p -= T^T x_q;  y_p = Linv x_p;  x_q -= G y_p
+// q its neighbours; fronts carry T, cells do not; A_pp = L D_p L^T with
+// D_p = diag(S), all +1 for an SPD block, and G = A_qp L^-T D_p):
+//   up   (V^T, then D_p^-1 on p):  [front] x_p -= T^T x_q;  y_p = Linv x_p;
+//                                  x_q -= G y_p;  x_p = S y_p
 //   down (V):    x_p = Linv^T (x_p - G^T x_q);  [front] x_q -= T x_p
 // F = V_0^-T ... D ... V_0^-1:
 //   fwd_up   (V^-1):  [front] x_q += T x_p;  x_p = L^T x_p + G^T x_q
-//   fwd_down (V^-T):  x_q += G x_p;  x_p = L x_p;  [front] x_p += T^T x_q
+//   fwd_down (D_p, then V^-T):  x_p = S x_p;  x_q += G x_p;  x_p = L x_p;
+//                               [front] x_p += T^T x_q
 // Cells of one level share boundary DOFs, so their x_q updates use atomics;
 // the DOFs of a front belong to it alone.
 //
@@ -194,10 +197,11 @@ __device__ void sweep_up_block(const ApplyDesc& bd, const int* __restrict__ ipoo
       for (int c = 0; c < CG; ++c) acc[c] += lv * xv[c];
       xv += R;
     }
+    const T sg = fac[bd.S + i];                   // the sign of D_p's entry (LDL^T), +1 if SPD
 #pragma unroll
     for (int c = 0; c < CG; ++c) {
       yp[i * R + c0 + c] = acc[c];
-      if (c0 + c < nr) x[(int64_t)idp[i] * ldx + c0 + c] = acc[c];
+      if (c0 + c < nr) x[(int64_t)idp[i] * ldx + c0 + c] = sg * acc[c];
     }
   }
   __syncthreads();
@@ -425,6 +429,8 @@ __global__ void k_fwd_down(const ApplyDesc* __restrict__ blocks, const int* __re
   const T* G = fac + bd.G;
   gather<T, R>(xp, x, idp, np, nr, ldx);
   if (is_front) gather<T, R>(xq, x, idq, nq, nr, ldx);
+  __syncthreads();
+  for (int e = threadIdx.x; e < np * R; e += blockDim.x) xp[e] *= fac[bd.S + e / R];   // D_p
   __syncthreads();
   for (int e = threadIdx.x; e < nq * R; e += blockDim.x) {   // x_q += G x_p
     const int s2 = e / R, r = e % R;

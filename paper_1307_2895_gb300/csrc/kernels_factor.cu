@@ -175,6 +175,7 @@ __global__ void k_cell_factor(const CellDesc* __restrict__ cells, const int* __r
   T* Linv = fac + cd.fac;
   T* G = fac + cd.fac + cell_fac_G(nI);
   T* Lp = fac + cd.fac + cell_fac_L(nI, nB);
+  T* Sg = fac + cd.fac + cell_fac_S(nI, nB);   // signs of D (LDL^T of an indefinite F_II)
   const int64_t n2 = (int64_t)nI * nI;
   T* A = FII;
   T* X = Xg;
@@ -185,13 +186,14 @@ __global__ void k_cell_factor(const CellDesc* __restrict__ cells, const int* __r
     A = sm;
   }
   if (A != FII) blk_copy(FII, nI, A, nI, nI, nI);
-  blk_cholesky(A, nI, nI, status, tau);
+  const bool neg = blk_cholesky(A, nI, nI, status, tau, (const T*)nullptr, Sg);
   blk_tri_inverse(A, nI, nI, X, nI);
   blk_pack_lower(A, nI, Lp, nI);
   blk_pack_lower(X, nI, Linv, nI);
   if (nB > 0) {
-    blk_mul_linvT(FBI, nI, X, nI, nB, nI, G, nI);
-    blk_syrk_sub(FBB, nB, G, nI, nB, nI);
+    blk_mul_linvT(FBI, nI, X, nI, nB, nI, G, nI);          // W = F_BI L^-T
+    blk_syrk_sub(FBB, nB, G, nI, nB, nI, neg ? Sg : (const T*)nullptr);   // F_BB -= W D W^T
+    if (neg) blk_scale_cols(G, nI, nB, nI, Sg);           // the stored G is W D
   }
 }
 
@@ -366,21 +368,25 @@ __global__ void k_front(const FrontDesc* __restrict__ fronts, const CellDesc* __
   }
   __syncthreads();
   if (nR > 0) {
-    blk_cholesky(S3, nR, nR, status, tau);
+    T* Sg = fac + fd.fac + front_fac_S(nc);   // signs of D (LDL^T of an indefinite B_rr)
+    const bool neg = blk_cholesky(S3, nR, nR, status, tau, (const T*)nullptr, Sg);
     T* X = S1;                             // W is no longer needed
     blk_tri_inverse(S3, nR, nR, X, nR);
     blk_pack_lower(S3, nR, Lp, nR);
     blk_pack_lower(X, nR, Linvp, nR);
     if (k > 0) {
       blk_mul_linvT(S2, nR, X, nR, k, nR, G, nR);
-      // B_ss = A_ss - G G^T -> P1's update (skeleton block), zero in P2's
+      // B_ss = A_ss - G D G^T -> P1's update (skeleton block), zero in P2's
       for (int64_t e = threadIdx.x; e < (int64_t)k * (k + 1) / 2; e += blockDim.x) {
         int i, j;
         tri_decode(e, i, j);               // j <= i; B_ss is symmetric
         const T* gi = G + (int64_t)i * nR;
         const T* gj = G + (int64_t)j * nR;
         T s = T(0);
-        for (int t = 0; t < nR; ++t) s += gi[t] * gj[t];
+        if (neg)
+          for (int t = 0; t < nR; ++t) s += (gi[t] * Sg[t]) * gj[t];
+        else
+          for (int t = 0; t < nR; ++t) s += gi[t] * gj[t];
         const int ci = perm[i], cj = perm[j];
         const T b = Acc[(int64_t)ci * nc + cj] - s;
         U1[(int64_t)pos1[ci] * ld1 + pos1[cj]] = b;
@@ -390,6 +396,8 @@ __global__ void k_front(const FrontDesc* __restrict__ fronts, const CellDesc* __
           U2[(int64_t)pos2[cj] * ld2 + pos2[ci]] = T(0);
         }
       }
+      __syncthreads();
+      if (neg) blk_scale_cols(G, nR, k, nR, Sg);          // the stored G is B_sr L^-T D
     }
   }
   // ---- outputs

@@ -1,9 +1,10 @@
 // D^-1 of a large root (Eq. 4.2's middle factor) by the whole GPU.  The
-// root D = L L^T is stored as L^-1, lower triangular and packed by rows (row
-// i at i (i + 1) / 2).  The sweep kernel applies a block with one thread
-// block, which for a 3D root of thousands of DOFs leaves one SM streaming
-// megabytes; here D^-1 x = L^-T (L^-1 x) is three launches over all SMs:
-//   k_root_lower:   y = L^-1 x_root, one warp per row (coalesced row reads,
+// root D = L S L^T (S = diag(sgn), all +1 when D is SPD) is stored as L^-1,
+// lower triangular and packed by rows (row i at i (i + 1) / 2), and sgn.
+// The sweep kernel applies a block with one thread block, which for a 3D
+// root of thousands of DOFs leaves one SM streaming megabytes; here
+// D^-1 x = L^-T S (L^-1 x) is three launches over all SMs:
+//   k_root_lower:   y = S L^-1 x_root, one warp per row (coalesced row reads,
 //                   lane-strided dot products, warp sums); also zeroes z;
 //   k_root_upper:   z = L^-T y as column strips: a block takes 64 columns and
 //                   256 rows, reads each row's 64 entries in one coalesced
@@ -25,8 +26,8 @@ __device__ __forceinline__ T warp_sum_t(T v) {
 
 template <typename T, int R>
 __global__ void __launch_bounds__(256) k_root_lower(int np, const int* __restrict__ ids, const T* __restrict__ Linv,
-                                                    const T* __restrict__ x, int nr, int ldx, T* __restrict__ y,
-                                                    T* __restrict__ z) {
+                                                    const T* __restrict__ sgn, const T* __restrict__ x, int nr,
+                                                    int ldx, T* __restrict__ y, T* __restrict__ z) {
   const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   for (int64_t e = gt; e < (int64_t)np * R; e += (int64_t)gridDim.x * blockDim.x) z[e] = T(0);
   const int i = (int)(gt >> 5), lane = threadIdx.x & 31;
@@ -41,10 +42,11 @@ __global__ void __launch_bounds__(256) k_root_lower(int np, const int* __restric
 #pragma unroll
     for (int c = 0; c < R; ++c) acc[c] += lv * (c < nr ? xr[c] : T(0));
   }
+  const T sg = sgn[i];                            // D = diag(sgn) (LDL^T of an indefinite root)
 #pragma unroll
   for (int c = 0; c < R; ++c) {
     const T s = warp_sum_t(acc[c]);
-    if (lane == c) y[(int64_t)i * R + c] = s;
+    if (lane == c) y[(int64_t)i * R + c] = sg * s;
   }
 }
 
@@ -91,9 +93,10 @@ __global__ void k_root_scatter(int np, const int* __restrict__ ids, const T* __r
 }
 
 template <typename T, int R>
-static void root_chunk(int np, const int* ids, const T* Linv, T* x, int nr, int ldx, T* y, T* z, cudaStream_t st) {
+static void root_chunk(int np, const int* ids, const T* Linv, const T* sgn, T* x, int nr, int ldx, T* y, T* z,
+                       cudaStream_t st) {
   const int lower_blocks = (int)(((int64_t)np * 32 + 255) / 256);
-  k_root_lower<T, R><<<lower_blocks, 256, 0, st>>>(np, ids, Linv, x, nr, ldx, y, z);
+  k_root_lower<T, R><<<lower_blocks, 256, 0, st>>>(np, ids, Linv, sgn, x, nr, ldx, y, z);
   k_root_upper<T, R><<<dim3((np + 63) / 64, (np + 255) / 256), 256, 0, st>>>(np, Linv, y, z);
   const int64_t n = (int64_t)np * nr;
   const int sb = (int)((n + 255) / 256 < 2048 ? (n + 255) / 256 : 2048);
@@ -102,23 +105,26 @@ static void root_chunk(int np, const int* ids, const T* Linv, T* x, int nr, int 
 }
 
 template <typename T>
-int launch_root_apply(int np, const int* ids, const T* Linv, T* x, int nrhs, int ldx, T* scratch, cudaStream_t st) {
+int launch_root_apply(int np, const int* ids, const T* Linv, const T* sgn, T* x, int nrhs, int ldx, T* scratch,
+                      cudaStream_t st) {
   if (np <= 0 || nrhs <= 0) return 0;
   int launches = 0;
   for (int r0 = 0; r0 < nrhs; r0 += kRootChunk) {
     const int nr = (nrhs - r0) < kRootChunk ? (nrhs - r0) : kRootChunk;
     T* y = scratch;
     T* z = scratch + (int64_t)np * kRootChunk;
-    if (nr > 4) root_chunk<T, 8>(np, ids, Linv, x + r0, nr, ldx, y, z, st);
-    else if (nr > 2) root_chunk<T, 4>(np, ids, Linv, x + r0, nr, ldx, y, z, st);
-    else if (nr > 1) root_chunk<T, 2>(np, ids, Linv, x + r0, nr, ldx, y, z, st);
-    else root_chunk<T, 1>(np, ids, Linv, x + r0, nr, ldx, y, z, st);
+    if (nr > 4) root_chunk<T, 8>(np, ids, Linv, sgn, x + r0, nr, ldx, y, z, st);
+    else if (nr > 2) root_chunk<T, 4>(np, ids, Linv, sgn, x + r0, nr, ldx, y, z, st);
+    else if (nr > 1) root_chunk<T, 2>(np, ids, Linv, sgn, x + r0, nr, ldx, y, z, st);
+    else root_chunk<T, 1>(np, ids, Linv, sgn, x + r0, nr, ldx, y, z, st);
     launches += 3;
   }
   return launches;
 }
 
-template int launch_root_apply<double>(int, const int*, const double*, double*, int, int, double*, cudaStream_t);
-template int launch_root_apply<float>(int, const int*, const float*, float*, int, int, float*, cudaStream_t);
+template int launch_root_apply<double>(int, const int*, const double*, const double*, double*, int, int, double*,
+                                       cudaStream_t);
+template int launch_root_apply<float>(int, const int*, const float*, const float*, float*, int, int, float*,
+                                      cudaStream_t);
 
 }  // namespace hif

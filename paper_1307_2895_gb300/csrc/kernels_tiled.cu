@@ -5,15 +5,20 @@
 // 64 x 64 tiles and each step of a blocked right-looking Cholesky runs as one
 // launch over the tiles of all the level's large cells:
 //
-//   for each panel p:  L_pp = chol(A_pp), D_p = L_pp^{-1}          (k_tl_potrf)
-//                      [A; F_BI]_{i,p} <- [A; F_BI]_{i,p} D_p^T     (k_tl_trsm)
-//                      A_ij, F_BI,j -= L_ip L_jp^T  (j > p)         (k_tl_update)
-//   U = F_BB - G G^T with G = F_BI L^{-T} (the stacked panels)      (k_tl_syrk)
+//   for each panel p:  A_pp = L_pp S_p L_pp^T, D_p = L_pp^{-1}      (k_tl_potrf)
+//                      [A; F_BI]_{i,p} <- [A; F_BI]_{i,p} D_p^T S_p (k_tl_trsm)
+//                      A_ij, F_BI,j -= L_ip S_p L_jp^T  (j > p)     (k_tl_update)
+//   U = F_BB - G S G^T with G = F_BI L^{-T} S (the stacked panels)  (k_tl_syrk)
 //   Linv_ij = -D_i sum_{k=j}^{i-1} L_ik Linv_kj  (row block i)      (k_tl_linv)
 //   pack L and G into the factor                                    (k_tl_pack)
 //
+// S = diag(+-1) holds the signs of the pivots: all +1 (Cholesky) on a
+// positive definite block; an indefinite one (the Helmholtz operator's) gets
+// the signed LDL^T of blk_cholesky, 1 x 1 pivots in order, with the signs
+// written to the factor by k_tl_potrf.  The mixed mode's safeguarded pivots
+// are positive, so its tensor-core panels carry no signs.
 // Results are those of k_cell_factor up to rounding order: the same L, Linv,
-// G and Schur complement.  Scratch (the D_p tiles and the original diagonal
+// S, G and Schur complement.  Scratch (the D_p tiles and the original diagonal
 // for the pivot safeguard) lives in the problem's X region of the work pool.
 // Each problem is described by a TDesc (a large cell, or the redundant block
 // of a large front).
@@ -55,7 +60,7 @@ __global__ void k_tl_potrf(const TDesc* __restrict__ td, int p,
   }
   __syncthreads();
   const T* d0 = (tau > T(0)) ? work + c.X + (int64_t)c.P * TB * TB + o : nullptr;
-  blk_cholesky(A, w, TB, status, tau, d0);
+  blk_cholesky(A, w, TB, status, tau, d0, fac + c.S + o);   // signs of the panel's pivots
   blk_tri_inverse(A, w, TB, X, TB);
   T* D = work + c.X + (int64_t)p * TB * TB;
   T* Linv = fac + c.Linv;
@@ -73,7 +78,7 @@ __global__ void k_tl_potrf(const TDesc* __restrict__ td, int p,
 // Panel p: row tiles below the diagonal (F_II rows, then F_BI rows) times D_p^T.
 template <typename T>
 __global__ void __launch_bounds__(TT) k_tl_trsm(const TDesc* __restrict__ td,
-                                                int p, T* __restrict__ work) {
+                                                int p, T* __restrict__ work, const T* __restrict__ fac) {
   __shared__ TileSmem<T> sm;
   const TCell c = tcell(td[blockIdx.y]);
   if (p >= c.P) return;
@@ -93,6 +98,7 @@ __global__ void __launch_bounds__(TT) k_tl_trsm(const TDesc* __restrict__ td,
     rows = min(TB, c.nB - r0);
   }
   const T* D = work + c.X + (int64_t)p * TB * TB;
+  const T* sg = fac + c.S + o;
   const int ld = c.nI;
   T acc[4][4];
   zero_acc(acc);
@@ -105,7 +111,7 @@ __global__ void __launch_bounds__(TT) k_tl_trsm(const TDesc* __restrict__ td,
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int r = ty + 16 * i, q = tx + 16 * j;
-      if (r < rows && q < w) M[(int64_t)r * ld + o + q] = acc[i][j];
+      if (r < rows && q < w) M[(int64_t)r * ld + o + q] = acc[i][j] * sg[q];
     }
 }
 
@@ -113,7 +119,7 @@ __global__ void __launch_bounds__(TT) k_tl_trsm(const TDesc* __restrict__ td,
 // all row tiles of F_BI.
 template <typename T>
 __global__ void __launch_bounds__(TT) k_tl_update(const TDesc* __restrict__ td,
-                                                  int p, T* __restrict__ work) {
+                                                  int p, T* __restrict__ work, const T* __restrict__ fac) {
   __shared__ TileSmem<T> sm;
   const TCell c = tcell(td[blockIdx.y]);
   if (p >= c.P) return;
@@ -143,11 +149,12 @@ __global__ void __launch_bounds__(TT) k_tl_update(const TDesc* __restrict__ td,
     rows = min(TB, c.nB - rb * TB);
   }
   const T* Lcol = work + c.FII + (int64_t)j * TB * ld;
+  const T* sg = fac + c.S + o;
   const int cols = min(TB, c.nI - j * TB);
   T acc[4][4];
   zero_acc(acc);
   tile_mma<T, true>(
-      sm, acc, w, [&](int r, int k) { return r < rows ? Lrow[(int64_t)r * ld + o + k] : T(0); },
+      sm, acc, w, [&](int r, int k) { return r < rows ? Lrow[(int64_t)r * ld + o + k] * sg[k] : T(0); },
       [&](int k, int q) { return q < cols ? Lcol[(int64_t)q * ld + o + k] : T(0); });
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int oc = j * TB;
@@ -160,11 +167,11 @@ __global__ void __launch_bounds__(TT) k_tl_update(const TDesc* __restrict__ td,
     }
 }
 
-// U = F_BB - G G^T (G = F_BI after the panels), tile (i, j >= ... ) with
+// U = F_BB - G S G^T (G = F_BI after the panels), tile (i, j >= ... ) with
 // i >= j, mirrored into (j, i).
 template <typename T>
 __global__ void __launch_bounds__(TT) k_tl_syrk(const TDesc* __restrict__ td,
-                                                T* __restrict__ work) {
+                                                T* __restrict__ work, const T* __restrict__ fac) {
   __shared__ TileSmem<T> sm;
   const TCell c = tcell(td[blockIdx.y]);
   const int64_t t = blockIdx.x;
@@ -175,10 +182,11 @@ __global__ void __launch_bounds__(TT) k_tl_syrk(const TDesc* __restrict__ td,
   const T* Gi = work + c.FBI + (int64_t)a * TB * ld;
   const T* Gj = work + c.FBI + (int64_t)b * TB * ld;
   const int ri = min(TB, c.nB - a * TB), rj = min(TB, c.nB - b * TB);
+  const T* sg = fac + c.S;
   T acc[4][4];
   zero_acc(acc);
   tile_mma<T, true>(
-      sm, acc, c.nI, [&](int r, int k) { return r < ri ? Gi[(int64_t)r * ld + k] : T(0); },
+      sm, acc, c.nI, [&](int r, int k) { return r < ri ? Gi[(int64_t)r * ld + k] * sg[k] : T(0); },
       [&](int k, int q) { return q < rj ? Gj[(int64_t)q * ld + k] : T(0); });
   T* U = work + c.FBB;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -290,15 +298,15 @@ void launch_tiled_elim(const TDesc* td, int nsel, int max_nI, int max_nB, T* wor
       continue;
     }
     const int below = P - p - 1;
-    if (below + RB > 0) k_tl_trsm<T><<<dim3(below + RB, nsel), TT, 0, st>>>(td, p, work);
+    if (below + RB > 0) k_tl_trsm<T><<<dim3(below + RB, nsel), TT, 0, st>>>(td, p, work, fac);
     const int64_t nup = (int64_t)below * (below + 1) / 2 + (int64_t)RB * below;
-    if (nup > 0) k_tl_update<T><<<dim3((unsigned)nup, nsel), TT, 0, st>>>(td, p, work);
+    if (nup > 0) k_tl_update<T><<<dim3((unsigned)nup, nsel), TT, 0, st>>>(td, p, work, fac);
     nl += (below + RB > 0) + (nup > 0);
   }
   if (tc) {
     nl += tc_syrk(td, nsel, max_nB, reinterpret_cast<float*>(work), tc_split, status, st);
   } else if (RB > 0) {
-    k_tl_syrk<T><<<dim3((unsigned)((int64_t)RB * (RB + 1) / 2), nsel), TT, 0, st>>>(td, work);
+    k_tl_syrk<T><<<dim3((unsigned)((int64_t)RB * (RB + 1) / 2), nsel), TT, 0, st>>>(td, work, fac);
     ++nl;
   }
   for (int i = 1; i < P; ++i) {

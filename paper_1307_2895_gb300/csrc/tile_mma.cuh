@@ -67,7 +67,7 @@ __device__ __forceinline__ void tile_mma(TileSmem<T>& sm, T (&acc)[4][4], int K,
 // large front) with its tile counts: P panels of F_II, RB row tiles of F_BI.
 struct TCell {
   int nI, nB, P, RB;
-  int64_t FII, FBI, FBB, X, Linv, G, Lp;
+  int64_t FII, FBI, FBB, X, Linv, G, Lp, S;
 };
 
 __device__ __forceinline__ TCell tcell(const TDesc& d) {
@@ -83,6 +83,7 @@ __device__ __forceinline__ TCell tcell(const TDesc& d) {
   c.Linv = d.Linv;
   c.G = d.G;
   c.Lp = d.Lp;
+  c.S = d.S;
   return c;
 }
 

@@ -55,7 +55,8 @@ class _Stats(ctypes.Structure):
                 ("clamped_pivots", ctypes.c_int), ("sketched_fronts", ctypes.c_int),
                 ("fallback_fronts", ctypes.c_int), ("t_fronts_ms", ctypes.c_double),
                 ("factor_bytes", ctypes.c_longlong), ("factor_flops", ctypes.c_double),
-                ("apply_bytes", ctypes.c_double), ("t_factor_ms", ctypes.c_double)]
+                ("apply_bytes", ctypes.c_double), ("t_factor_ms", ctypes.c_double),
+                ("negative_pivots", ctypes.c_int)]
 
 
 class _Profile(ctypes.Structure):

@@ -121,6 +121,24 @@ def constant_coefficients(dim: int, n: int, a: float = 1.0, b: float = 0.0):
     return np.full(size, float(a)), np.full(num_dofs(dim, n), float(b))
 
 
+def helmholtz_coefficients(dim: int, n: int, dofs_per_wavelength: float, perturb: float = 0.0,
+                           seed: int = 0):
+    """a(x) = 1, b(x) = -k^2 with k = 2 pi kappa and kappa = n / dofs_per_wavelength
+    wavelengths across the domain (Examples 3 and 6 keep 32 and 8 DOFs per
+    wavelength as n grows).  The operator is indefinite once k^2 exceeds the
+    Laplacian's smallest eigenvalue d pi^2.
+
+    ``perturb`` > 0 replaces a(x) = 1 by 1 + perturb (2 U - 1) with i.i.d.
+    U[0,1) samples (stream ``seed``) on the staggered points: the grid's
+    symmetries then no longer make columns of a front exactly equal in norm."""
+    kappa = n / float(dofs_per_wavelength)
+    k = 2.0 * math.pi * kappa
+    a, b = constant_coefficients(dim, n, a=1.0, b=-k * k)
+    if perturb > 0.0:
+        a = 1.0 + perturb * (2.0 * uniform01(seed, a.size) - 1.0)
+    return a, b
+
+
 def _gaussian_taps(sigma: float, radius: int) -> np.ndarray:
     k = np.arange(-radius, radius + 1, dtype=np.float64)
     w = np.exp(-0.5 * (k / sigma) ** 2)
