@@ -12,7 +12,8 @@ where larger), in the 2-norm and element-wise.
 
 Cases: 15^3 (one level: hifde3 itself, no edges), 23^3 and 31^3 (two levels:
 level 1's edges, the first assembled step; 31^3 also with every group of 128+
-DOFs through the multi-block ID), 31^3 high contrast, and 47^3 (three
+DOFs through the multi-block ID), 31^3 high contrast, the indefinite
+Helmholtz operator at 23^3 and 31^3 (LDL^T blocks), and 47^3 (three
 levels: the algebraic cells of level 2, its faces and edges, with cells of
 192+ interior DOFs through the tiled elimination).
 """
@@ -28,14 +29,16 @@ pytestmark = pytest.mark.gpu
 def _fields(n, field):
     if field == "lap":
         return inputs.constant_coefficients(3, n)
+    if field == "helm":   # Example 6 at 8 DOFs per wavelength, a = 1 +- 10% (no symmetric pivot ties)
+        return inputs.helmholtz_coefficients(3, n, 8, perturb=0.1, seed=7)
     return inputs.high_contrast_coefficients(3, n, seed=5, low=1e-2, high=1e2)
 
 
 def _kappa(A):
     import scipy.sparse.linalg as spla
-    lmax = spla.eigsh(A, k=1, which="LA", return_eigenvectors=False)[0]
+    lmax = spla.eigsh(A, k=1, which="LM", return_eigenvectors=False)[0]
     lmin = spla.eigsh(A.tocsc(), k=1, sigma=0, which="LM", return_eigenvectors=False)[0]
-    return lmax / lmin
+    return abs(lmax) / abs(lmin)
 
 
 CASES = [
@@ -44,6 +47,8 @@ CASES = [
     (32, "lap", 1e-3, 0),
     (32, "lap", 1e-6, 128),
     (32, "contrast", 1e-6, 0),
+    (24, "helm", 1e-6, 0),
+    (32, "helm", 1e-6, 0),
     pytest.param(48, "lap", 1e-3, 0, marks=pytest.mark.slow),
 ]
 
