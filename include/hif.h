@@ -148,6 +148,17 @@ typedef struct hif_opts {
                            the sketch's rank rule is then applied at
                            (eps/10)^(2q+1), which must stay well above the
                            FP64 rounding level (q = 1 for eps >= 1e-4).       */
+  int deterministic;    /* nonzero: applications of F^-1 and F (and so solves
+                           and estimates) are bit-reproducible run to run: the
+                           cells' updates of shared boundary DOFs are written
+                           per (cell, DOF) and summed per DOF in cell order by
+                           a second launch per level, and the multi-block root
+                           adds its partial sums in a fixed order, instead of
+                           floating-point atomics (about one more launch per
+                           cell level and sweep direction).  The factorization
+                           of HIF_VARIANT_HIFDE3X's assembled levels still
+                           adds with atomics; the other variants' factor-
+                           izations are reproducible either way.             */
 } hif_opts;
 
 typedef struct hif_handle hif_handle;
@@ -191,6 +202,9 @@ typedef struct hif_stats_t {
   double t_factor_ms;          /* device time of the last hif_factor             */
   int negative_pivots;         /* pivots < 0: diagonal blocks of an indefinite A
                                   factored as L D L^T, D = diag(+-1)            */
+  double t_wall_ms;            /* host wall time of the last hif_factor          */
+  double t_wait_ms;            /* of it, the host blocked on the device (the
+                                  per-level read-backs of ranks and skeletons)  */
 } hif_stats_t;
 
 /*

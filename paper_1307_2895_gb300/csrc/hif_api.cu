@@ -118,11 +118,92 @@ struct DevBuf {
   template <typename T> T* as() const { return reinterpret_cast<T*>(p); }
 };
 
+// Pinned host staging of the uploads of one factorization.  A copy from
+// pageable memory may wait for the stream to drain before it starts, which
+// would stop the host from building the next level while the GPU works;
+// from pinned memory it is queued like a kernel.  Chunks of pinned memory
+// are taken bump-wise and kept for the next factorization (process-wide
+// pool); an arena goes back to the pool only after its stream has been
+// synchronized, so no copy still reads it.
+class PinnedArena {
+ public:
+  ~PinnedArena() {
+    for (Chunk& c : chunks_) cudaFreeHost(c.p);
+  }
+  void* take(size_t bytes) {
+    bytes = (bytes + 15) & ~size_t(15);
+    while (cur_ < chunks_.size() && chunks_[cur_].used + bytes > chunks_[cur_].cap) ++cur_;
+    if (cur_ == chunks_.size()) {
+      Chunk c;
+      c.cap = std::max(bytes, kChunk);
+      CU(cudaHostAlloc(reinterpret_cast<void**>(&c.p), c.cap, cudaHostAllocDefault));
+      chunks_.push_back(c);
+    }
+    Chunk& c = chunks_[cur_];
+    void* r = c.p + c.used;
+    c.used += bytes;
+    return r;
+  }
+  void reset() {
+    for (Chunk& c : chunks_) c.used = 0;
+    cur_ = 0;
+  }
+
+ private:
+  static constexpr size_t kChunk = 8u << 20;
+  struct Chunk {
+    char* p = nullptr;
+    size_t cap = 0, used = 0;
+  };
+  std::vector<Chunk> chunks_;
+  size_t cur_ = 0;
+};
+
+std::mutex g_arena_mu;
+std::vector<std::unique_ptr<PinnedArena>> g_arenas;
+thread_local PinnedArena* t_arena = nullptr;   // the calling thread's factorization, if any
+
+// Scope of one factorization on stream st: uploads from this thread go
+// through a pinned arena taken from the pool.
+struct ArenaScope {
+  std::unique_ptr<PinnedArena> a;
+  PinnedArena* prev;
+  cudaStream_t st;
+  explicit ArenaScope(cudaStream_t s) : prev(t_arena), st(s) {
+    {
+      std::lock_guard<std::mutex> g(g_arena_mu);
+      if (!g_arenas.empty()) {
+        a = std::move(g_arenas.back());
+        g_arenas.pop_back();
+      }
+    }
+    if (!a) a.reset(new PinnedArena());
+    t_arena = a.get();
+  }
+  ~ArenaScope() {
+    t_arena = prev;
+    if (cudaStreamSynchronize(st) != cudaSuccess) {   // a failed stream: drop the arena's memory
+      cudaGetLastError();
+      return;
+    }
+    a->reset();
+    std::lock_guard<std::mutex> g(g_arena_mu);
+    g_arenas.push_back(std::move(a));
+  }
+};
+
 template <typename T>
 void upload(DevBuf& d, const std::vector<T>& h, cudaStream_t st) {
-  d.alloc(h.size() * sizeof(T), st);
-  if (!h.empty())
-    CU(cudaMemcpyAsync(d.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+  const size_t b = h.size() * sizeof(T);
+  d.alloc(b, st);
+  if (h.empty()) return;
+  if (t_arena && b >= 4096) {
+    void* p = t_arena->take(b);
+    std::memcpy(p, h.data(), b);
+    CU(cudaMemcpyAsync(d.p, p, b, cudaMemcpyHostToDevice, st));
+  } else {
+    CU(cudaMemcpyAsync(d.p, h.data(), b, cudaMemcpyHostToDevice, st));
+  }
 }
 
 bool is_device_ptr(const void* p) {
@@ -145,6 +226,10 @@ struct SweepLevel {
   DevBuf desc_own, ipool_own;        // owned storage behind desc / ipool when not shared
   DevBuf fac;     // factor pool
   DevBuf fac32;   // float copy (FP32 apply of a double factor, or the root in mixed precision)
+  // deterministic scatter of a cell level (ContribPlan): per DOF its rows
+  DevBuf cp_ptr, cp_dofs, cp_slots;
+  int cp_ndof = 0;
+  int64_t cp_rows = 0;   // rows of the contribution buffer the level uses
 };
 
 // Skeleton structure of one fractional level (for hif_structure).
@@ -171,6 +256,7 @@ struct Level0 {
   }
   std::vector<HostCell> cells;
   std::vector<CellDesc> cdesc;
+  std::vector<int> cipool;   // host copy of the cells' ids (the deterministic scatter's plan)
   int64_t work_elems = 0, fac_elems = 0;
   int max_nI = 0;
   int cap_max_np = 0, cap_max_nq = 0;
@@ -198,6 +284,8 @@ struct hif_handle {
   int skip_levels = 0;
   int edge_start = 1;   // HIFDE3X: first level whose edges are skeletonized
   int sketch_power = 0; // power iterations on the randomized ID's sketch
+  bool deterministic = false;   // sweeps and root apply without floating-point atomics
+  DevBuf contrib_buf;           // the deterministic scatter's contribution rows (32 doubles each)
   int big_cell = 192;   // cells with at least this many interior DOFs use the tiled elimination
   bool coop_qr = true;  // large fronts: pivoted QR by co-resident block groups
   int tc_split = 3;     // FP32 tiled elimination on the tensor cores: TF32 parts per value (1..3), 0 = SIMT
@@ -223,6 +311,7 @@ struct hif_handle {
   int sketched = 0, fallback = 0;
   int negative = 0;     // negative pivots (LDL^T of indefinite diagonal blocks)
   double t_fronts_ms = 0.0;
+  double t_wall_ms = 0.0, t_wait_ms = 0.0;   // last hif_factor: host wall time, and of it blocked on the device
   long long factor_bytes = 0;
   double factor_flops = 0.0, apply_bytes = 0.0, t_factor_ms = 0.0;
   // optional event timing of the F^-1 sweep launches
@@ -306,11 +395,14 @@ void cell_apply_descs(const std::vector<CellDesc>& cd, std::vector<ApplyDesc>& a
   ad.reserve(cd.size());
   max_np = max_nq = 0;
   fac_elems = vec_rows = 0.0;
+  int64_t cslot = 0;
   for (const CellDesc& c : cd) {
     ApplyDesc a;
     a.np = c.nI;
     a.nq = c.nB;
     a.ids = c.ids;
+    a.cslot = cslot;
+    cslot += c.nB;
     a.Linv = c.fac;
     a.G = c.fac + cell_fac_G(c.nI);
     a.L = c.fac + cell_fac_L(c.nI, c.nB);
@@ -324,6 +416,39 @@ void cell_apply_descs(const std::vector<CellDesc>& cd, std::vector<ApplyDesc>& a
       vec_rows += c.nI + c.nB;
     }
   }
+}
+
+// The deterministic scatter's plan of one cell level (ContribPlan): the
+// pairs (boundary DOF, contribution row) of the cells that eliminate
+// something, sorted by DOF and, within a DOF, by cell; rows are numbered as
+// cell_apply_descs numbers them (cslot).
+void build_contrib_plan(const std::vector<CellDesc>& cd, const std::vector<int>& ipool, SweepLevel& sw,
+                        cudaStream_t st) {
+  std::vector<std::pair<int, int>> pr;
+  int64_t row = 0;
+  for (const CellDesc& c : cd) {
+    if (c.nI > 0)
+      for (int s = 0; s < c.nB; ++s) pr.emplace_back(ipool[c.ids + c.nI + s], (int)(row + s));
+    row += c.nB;
+  }
+  if (row > 0x7fffffff) throw HifError(HIF_ERR_ARG, "deterministic mode: too many boundary rows in a level");
+  std::sort(pr.begin(), pr.end());
+  std::vector<int> ptr, dofs, slots;
+  ptr.reserve(pr.size() + 1);
+  slots.reserve(pr.size());
+  for (size_t k = 0; k < pr.size(); ++k) {
+    if (k == 0 || pr[k].first != pr[k - 1].first) {
+      ptr.push_back((int)k);
+      dofs.push_back(pr[k].first);
+    }
+    slots.push_back(pr[k].second);
+  }
+  ptr.push_back((int)pr.size());
+  upload(sw.cp_ptr, ptr, st);
+  upload(sw.cp_dofs, dofs, st);
+  upload(sw.cp_slots, slots, st);
+  sw.cp_ndof = (int)dofs.size();
+  sw.cp_rows = row;
 }
 
 // Descriptors of the fronts of one fractional level.
@@ -400,6 +525,7 @@ std::shared_ptr<const Level0> get_level0(const Geometry& G) {
   L0->d_cls0 = dev_copy(G.cls[0]);
   L0->d_cdesc = dev_copy(L0->cdesc);
   L0->d_cipool = dev_copy(cip);
+  L0->cipool = cip;
   L0->d_capply = dev_copy(ad);
   L0->d_fdesc = dev_copy(*L0->fdesc);
   L0->d_fip = dev_copy(fip);
@@ -419,8 +545,43 @@ void throw_wait_status(int bits) {
   if (bits & kWaitMma) throw HifError(HIF_ERR_TIMEOUT, "a bounded wait for tensor-core MMAs ran out");
 }
 
+// Host-side phase timer of one factorization (HIF_TRACE=1 in the
+// environment): each lap(name) adds the time since the previous lap to
+// name's total; the totals go to stderr when the factorization ends.
+struct HostTrace {
+  bool on = false;
+  std::chrono::steady_clock::time_point t;
+  std::vector<std::pair<const char*, double>> acc;
+  HostTrace() {
+    const char* e = getenv("HIF_TRACE");
+    on = e && e[0] == '1';
+    t = std::chrono::steady_clock::now();
+  }
+  void lap(const char* name) {
+    if (!on) return;
+    const auto now = std::chrono::steady_clock::now();
+    const double ms = std::chrono::duration<double, std::milli>(now - t).count();
+    t = now;
+    for (auto& a : acc)
+      if (a.first == name) {
+        a.second += ms;
+        return;
+      }
+    acc.emplace_back(name, ms);
+  }
+  ~HostTrace() {
+    if (!on) return;
+    double tot = 0.0;
+    for (auto& a : acc) tot += a.second;
+    fprintf(stderr, "hif_factor host phases (ms, total %.3f):", tot);
+    for (auto& a : acc) fprintf(stderr, " [%s %.3f]", a.first, a.second);
+    fprintf(stderr, "\n");
+  }
+};
+
 template <typename T>
 struct Factorizer {
+  HostTrace tr;
   hif_handle* h;
   const Geometry& G;
   cudaStream_t st;
@@ -438,6 +599,15 @@ struct Factorizer {
 
   explicit Factorizer(hif_handle* h_) : h(h_), G(h_->G), st(h_->st) {
     tau = (h_->precision == HIF_PREC_MIXED) ? 4e-6 : 0.0;
+  }
+
+  // the host blocked on the device (the per-level read-backs), timed for
+  // hif_stats: stream st, or event e when given
+  void wait_device(cudaEvent_t e = nullptr) {
+    const auto t0 = std::chrono::steady_clock::now();
+    if (e) CU(cudaEventSynchronize(e));
+    else CU(cudaStreamSynchronize(st));
+    h->t_wait_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   }
 
   // The symbolic stage follows the box levels: cells eliminated, then the
@@ -564,6 +734,7 @@ struct Factorizer {
       CU(cudaGetLastError());
       std::vector<ApplyDesc> ad;
       cell_apply_descs(cd, ad, sw.max_np, sw.max_nq, sw.fac_elems, sw.vec_rows);
+      if (h->deterministic) build_contrib_plan(cd, ip, sw, st);
       sw.nblocks = (int)ad.size();
       upload(sw.desc_own, ad, st);
       sw.desc = sw.desc_own.as<ApplyDesc>();
@@ -711,8 +882,10 @@ struct Factorizer {
       sw.fac_elems = L0->cap_fac_elems;
       sw.vec_rows = L0->cap_vec_rows;
       account_cells(L0->cdesc, sizeof(T));
+      if (h->deterministic) build_contrib_plan(L0->cdesc, L0->cipool, sw, st);
       sym_cells(L0->cells);
     }
+    tr.lap("level 0 cells");
     std::vector<int> alive = L0->alive1;
     if (skel && 0 >= h->skip_levels) {
       const size_t nfi = h->finfo.size();
@@ -736,12 +909,15 @@ struct Factorizer {
       const bool is_root = (l == L);
       std::vector<HostCell>& cells = (l & 1) ? cells_a : cells_b;
       DevBuf& ddesc = (l & 1) ? ddesc_a : ddesc_b;
+      tr.lap("other");
       build_cells(G, l, alive, cells);
+      tr.lap("cells build");
       std::vector<CellDesc> cdesc;
       std::vector<int> ipool;
       int64_t work_elems = 0, fac_elems = 0;
       int max_nI = 0;
       prepare_cells(G, l, cells, prev_cells, cdesc, ipool, work_elems, fac_elems, max_nI);
+      tr.lap("cells prepare");
       SweepLevel& sw = is_root ? h->root : h->cells[l];
       upload(ddesc, cdesc, st);
       upload(sw.ipool_own, ipool, st);
@@ -753,6 +929,7 @@ struct Factorizer {
       const CellDesc* dd = ddesc.as<CellDesc>();
       const int max_nF = max_front_size(cdesc);
       DevBuf selbuf, tdbuf;
+      tr.lap("cells upload+alloc");
       if (is_root) {
         launch_extend_add<T, double>(dd, ncells, sw.ipool, work.as<double>(), prev_ddesc, prev_work.as<T>(),
                                      nchild, max_nF, st);
@@ -763,8 +940,10 @@ struct Factorizer {
         factor_cells<T>(cdesc, dd, work.as<T>(), sw.fac.as<T>(), selbuf, tdbuf);
       }
       CU(cudaGetLastError());
+      tr.lap("cells launch");
       std::vector<ApplyDesc> ad;
       cell_apply_descs(cdesc, ad, sw.max_np, sw.max_nq, sw.fac_elems, sw.vec_rows);
+      if (h->deterministic && !is_root) build_contrib_plan(cdesc, ipool, sw, st);
       sw.nblocks = (int)ad.size();
       upload(sw.desc_own, ad, st);
       sw.desc = sw.desc_own.as<ApplyDesc>();
@@ -779,6 +958,7 @@ struct Factorizer {
         work.release();
         break;
       }
+      tr.lap("cells post");
       sym_cells(cells);
       {   // the eliminated interiors leave the active set
         for (const HostCell& c : cells)
@@ -790,16 +970,20 @@ struct Factorizer {
         alive.swap(next);
       }
       if (skel && l >= h->skip_levels) {
+        tr.lap("alive");
         auto fr = std::make_shared<std::vector<HostFront>>();
         build_fronts(G, l, alive, cells, *fr, mark);
+        tr.lap("fronts build");
         auto fd = std::make_shared<std::vector<FrontDesc>>();
         std::vector<int> ip;
         int64_t fw = 0, ff = 0, fo = 0;
         int mnc = 0, mnN = 0;
         prepare_fronts(*fr, *fd, ip, fw, ff, fo, mnc, mnN);
+        tr.lap("fronts prepare");
         DevBuf d_fd, d_ip;
         upload(d_fd, *fd, st);
         upload(d_ip, ip, st);
+        tr.lap("fronts upload");
         const size_t nfi = h->finfo.size();
         run_fronts(l, dd, work, alive, fr, fd, d_fd.as<FrontDesc>(), d_ip.as<int>(), fw, ff, fo, mnc, mnN,
                    h->fronts[l], h->variant == HIF_VARIANT_HIFDE3X ? 2 * l : l);
@@ -819,9 +1003,10 @@ struct Factorizer {
   // The factorization's device status: counts for hif_stats, then the
   // failures (a non-positive pivot, a bounded wait that ran out).
   void finish_status() {
+    tr.lap("other");
     int hs2[5] = {0, 0, 0, 0, 0};
     CU(cudaMemcpyAsync(hs2, status.p, 5 * sizeof(int), cudaMemcpyDeviceToHost, st));
-    CU(cudaStreamSynchronize(st));
+    wait_device();
     const int hs = hs2[0];
     h->clamped = hs2[1];
     h->sketched = hs2[2];
@@ -911,13 +1096,15 @@ struct Factorizer {
                             sketch.p ? big_nc : 0, bnc.data(), bnN.data(), h->coop_qr, st);
     }
     CU(cudaGetLastError());
+    tr.lap("fronts launch");
     info.fr = fr;
     info.fd = fdp;
     info.out.resize(out_elems);
     CU(cudaMemcpyAsync(info.out.data(), obuf.p, out_elems * sizeof(int), cudaMemcpyDeviceToHost, st));
     int hstat = 0;
     CU(cudaMemcpyAsync(&hstat, status.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-    CU(cudaStreamSynchronize(st));
+    wait_device();
+    tr.lap("fronts readback");
     if (!big.empty()) {
       // ranks known: B_sr, B_rr, A_ss, the tiled elimination, B_ss back
       std::vector<TDesc> td;
@@ -954,7 +1141,8 @@ struct Factorizer {
       CU(cudaGetLastError());
     }
     CU(cudaEventRecord(e1, st));
-    CU(cudaEventSynchronize(e1));
+    wait_device(e1);
+    tr.lap("fronts big+event");
     {
       float ms = 0.f;
       CU(cudaEventElapsedTime(&ms, e0, e1));
@@ -966,7 +1154,7 @@ struct Factorizer {
       h->near += 1;
       const int keep = hstat & 1;
       CU(cudaMemcpyAsync(status.p, &keep, sizeof(int), cudaMemcpyHostToDevice, st));
-      CU(cudaStreamSynchronize(st));
+      wait_device();
     }
     fwork.release();
     obuf.release();
@@ -993,6 +1181,7 @@ struct Factorizer {
       a.T = d.fac + front_fac_T(d.nc);
       a.L = d.fac + front_fac_L(d.nc);
       a.S = d.fac + front_fac_S(d.nc);
+      a.cslot = 0;
       sw.max_np = std::max(sw.max_np, nR);
       sw.max_nq = std::max(sw.max_nq, k);
       if (nR > 0) {
@@ -1021,6 +1210,7 @@ struct Factorizer {
     for (int g : alive)
       if (!dead[g]) next.push_back(g);
     alive.swap(next);
+    tr.lap("fronts post");
   }
 };
 
@@ -1071,7 +1261,7 @@ std::map<TuneKey, SweepShape> g_tune;
 
 template <typename T>
 SweepShape tuned_shape(hif_handle* h, int op, const SweepLevel& S, int is_front, const T* fac, const T* x,
-                       int nrhs) {
+                       int nrhs, const ContribPlan* cp) {
   const TuneKey key{op, (int)sizeof(T), nrhs, S.nblocks, S.max_np, S.max_nq, is_front};
   {
     std::lock_guard<std::mutex> g(g_tune_mu);
@@ -1099,7 +1289,7 @@ SweepShape tuned_shape(hif_handle* h, int op, const SweepLevel& S, int is_front,
         CU(cudaMemcpyAsync(xs.p, x, xb, cudaMemcpyDeviceToDevice, st));
         CU(cudaEventRecord(e0, st));
         launch_sweep<T>(op, S.desc, S.nblocks, S.ipool, fac, xs.as<T>(), nrhs, nrhs, is_front, S.max_np, S.max_nq,
-                        h->dev_err.as<int>(), st, cand);
+                        h->dev_err.as<int>(), st, cand, cp);
         CU(cudaEventRecord(e1, st));
         CU(cudaEventSynchronize(e1));
         float t = 0.f;
@@ -1143,10 +1333,15 @@ void run_apply(hif_handle* h, int mode, T* x, int nrhs) {
       }
       CU(cudaEventRecord(h->ev_pool[h->ev_used], st));
     }
-    const SweepShape shape =
-        (h->autotune && mode == HIF_APPLY_FINV) ? tuned_shape<T>(h, op, S, is_front, fac, x, nrhs) : SweepShape{};
+    // the deterministic scatter of a cell level (its plan; launch_sweep uses
+    // it for the sweeps that update x_q of cells)
+    ContribPlan cp{S.cp_ptr.as<int>(), S.cp_dofs.as<int>(), S.cp_slots.as<int>(), S.cp_ndof, h->contrib_buf.p};
+    const ContribPlan* cpp = (h->deterministic && !is_front && S.cp_ndof > 0) ? &cp : nullptr;
+    const SweepShape shape = (h->autotune && mode == HIF_APPLY_FINV)
+                                 ? tuned_shape<T>(h, op, S, is_front, fac, x, nrhs, cpp)
+                                 : SweepShape{};
     launch_sweep<T>(op, S.desc, S.nblocks, S.ipool, fac, x, nrhs, nrhs, is_front, S.max_np, S.max_nq,
-                    h->dev_err.as<int>(), st, shape);
+                    h->dev_err.as<int>(), st, shape, cpp);
     if (prof) {
       CU(cudaEventRecord(h->ev_pool[h->ev_used + 1], st));
       h->ev_used += 2;
@@ -1179,7 +1374,7 @@ void run_apply(hif_handle* h, int mode, T* x, int nrhs) {
       CU(cudaEventRecord(h->ev_pool[h->ev_used], st));
     }
     const int nl = launch_root_apply<T>(S.max_np, S.ipool, facp(S), facp(S) + cell_fac_S(S.max_np, 0), x, nrhs,
-                                        nrhs, h->root_scratch.as<T>(), st);
+                                        nrhs, h->root_scratch.as<T>(), h->deterministic, st);
     if (prof) {
       CU(cudaEventRecord(h->ev_pool[h->ev_used + 1], st));
       h->ev_used += 2;
@@ -1906,6 +2101,7 @@ int hif_factor(const hif_grid* grid, const double* a_stag, const double* b, cons
     if (opts && (opts->sketch_power < 0 || opts->sketch_power > 2))
       throw HifError(HIF_ERR_ARG, "sketch_power must be 0, 1 or 2");
     if (opts) h->sketch_power = opts->sketch_power;
+    if (opts) h->deterministic = opts->deterministic != 0;
     if (h->id_mode == HIF_ID_LEARNED && !(opts && opts->rank_model))
       throw HifError(HIF_ERR_ARG, "HIF_ID_LEARNED needs opts.rank_model");
     h->st = opts ? (cudaStream_t)opts->stream : nullptr;
@@ -1942,6 +2138,9 @@ int hif_factor(const hif_grid* grid, const double* a_stag, const double* b, cons
     CU(cudaEventCreate(&ev.e[1]));
     cudaEvent_t e0 = ev.e[0], e1 = ev.e[1];
     CU(cudaEventRecord(e0, h->st));
+    const auto w0 = std::chrono::steady_clock::now();
+    h->t_wait_ms = 0.0;
+    ArenaScope arena(h->st);
     if (prec == HIF_PREC_MIXED) {
       Factorizer<float> f(h);
       f.run();
@@ -1951,9 +2150,19 @@ int hif_factor(const hif_grid* grid, const double* a_stag, const double* b, cons
     }
     if (prec == HIF_PREC_FP32_APPLY) demote_factor(h);
     if (h->root_size >= kRootMulti)
-      h->root_scratch.alloc(sizeof(double) * 2 * (size_t)h->root_size * kRootChunk, h->st);
+      h->root_scratch.alloc(sizeof(double) * (size_t)root_scratch_elems(h->root_size, h->deterministic), h->st);
+    if (h->deterministic) {
+      int64_t rows = 0;
+      for (const SweepLevel& S : h->cells) rows = std::max(rows, S.cp_rows);
+      if (rows > 0) h->contrib_buf.alloc(sizeof(double) * 32 * (size_t)rows, h->st);
+    }
     CU(cudaEventRecord(e1, h->st));
-    CU(cudaEventSynchronize(e1));
+    {
+      const auto t0 = std::chrono::steady_clock::now();
+      CU(cudaEventSynchronize(e1));
+      h->t_wait_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+    h->t_wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - w0).count();
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     h->t_factor_ms = ms;
@@ -2176,6 +2385,8 @@ int hif_stats(const hif_handle* h, hif_stats_t* s) {
   s->negative_pivots = h->negative;
   s->fallback_fronts = h->fallback;
   s->t_fronts_ms = h->t_fronts_ms;
+  s->t_wall_ms = h->t_wall_ms;
+  s->t_wait_ms = h->t_wait_ms;
   s->factor_bytes = h->factor_bytes;
   s->factor_flops = h->factor_flops;
   s->apply_bytes = h->apply_bytes;

@@ -65,6 +65,8 @@ struct ApplyDesc {
   int64_t ids;         // int pool: ids_p[np] then ids_q[nq]
   int64_t Linv, L, G, T;   // factor pool offsets (T = -1 for cells)
   int64_t S;           // factor pool offset of the signs (np values)
+  int64_t cslot;       // cells: row of x_q's first contribution in the level's
+                       // contribution buffer (the deterministic scatter)
 };
 
 // Gaussian stream of the randomized ID (Section 4.3) at one fractional level

@@ -105,12 +105,14 @@ void launch_wait_test_mma(int* status, uint64_t ns, cudaStream_t st);
 // D^-1 of a root of at least kRootMulti DOFs by the whole GPU (kernels_root.cu):
 // x_root <- L^-T S L^-1 x_root (S = diag(sgn)) on the rows ids[0..np) of x
 // (N x nrhs, row stride ldx), in column chunks of kRootChunk; scratch:
-// 2 np kRootChunk elements.  Returns the number of launches.
+// root_scratch_elems(np, det) elements (det: partial sums added in a fixed
+// order instead of atomically).  Returns the number of launches.
 constexpr int kRootMulti = 256;
 constexpr int kRootChunk = 8;
+int64_t root_scratch_elems(int np, bool det);
 template <typename T>
 int launch_root_apply(int np, const int* ids, const T* Linv, const T* sgn, T* x, int nrhs, int ldx, T* scratch,
-                      cudaStream_t st);
+                      bool det, cudaStream_t st);
 
 // rank-prediction MLP (kernels_mlp.cu); idx may be NULL (samples 0..nb-1)
 void mlp_grad(const float* X, const float* t, const int* idx, int nb, float inv_n, const float* prm,
@@ -134,10 +136,24 @@ struct SweepShape {
   int threads = 0;
   int staged = -1;
 };
+// The deterministic scatter of one cell level: the ndof DOFs that the
+// level's cells update (dofs[k]) with their contribution rows
+// slots[ptr[k] .. ptr[k+1]) in cell order (row cslot + s of a cell is its
+// s-th boundary DOF), and buf: one row of 32 elements of the apply's type per
+// contribution.  With a plan, the cells' x_q updates of the F^-1 up sweep and
+// the F fwd_down sweep are written to buf and summed per DOF by a second
+// launch, so the result does not depend on the order the blocks run in.
+struct ContribPlan {
+  const int* ptr;
+  const int* dofs;
+  const int* slots;
+  int ndof;
+  void* buf;
+};
 template <typename T>
 void launch_sweep(int op, const ApplyDesc* blocks, int nblocks, const int* ipool, const T* fac, T* x,
                   int nrhs, int ldx, int is_front, int max_np, int max_nq, int* err, cudaStream_t st,
-                  SweepShape shape = SweepShape{});
+                  SweepShape shape = SweepShape{}, const ContribPlan* cp = nullptr);
 
 // stencil operator and CG vector operations (kernels_solve.cu)
 void launch_matvec(GridInfo g, const double* a_stag, const double* b, const double* x, int ldx,

@@ -12,14 +12,17 @@
 //   fwd_up   (V^-1):  [front] x_q += T x_p;  x_p = L^T x_p + G^T x_q
 //   fwd_down (D_p, then V^-T):  x_p = S x_p;  x_q += G x_p;  x_p = L x_p;
 //                               [front] x_p += T^T x_q
-// Cells of one level share boundary DOFs, so their x_q updates use atomics;
-// the DOFs of a front belong to it alone.
+// Cells of one level share boundary DOFs, so their x_q updates use atomics,
+// or, in the deterministic mode, go to a contribution buffer (one row per
+// (cell, q-row) pair) that a second launch sums per DOF in cell order; the
+// DOFs of a front belong to it alone.
 //
 // The F^-1 sweeps read each block of the factor once: when the launch's
 // largest block fits, the block's Linv (packed), G and T are first copied to
-// shared memory with 16-byte loads (all threads, fully coalesced), then every
-// product is a serial dot per (output row, right-hand side) pair, one thread
-// per pair, with no cross-lane reductions.
+// shared memory by bulk copies (TMA), then every product is a serial dot per
+// (output row, group of right-hand sides), one thread each, with no
+// cross-lane reductions.  One launch per level and direction, with
+// programmatic dependent launch between them.
 #include <atomic>
 
 #include "hif_internal.h"
@@ -43,17 +46,30 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
+// The mbarrier of a CTA's bulk copies: initialized once per CTA by thread 0,
+// before a __syncthreads() and before any thread polls it.
+__device__ __forceinline__ void bulk_init(uint64_t* mbar) {
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+}
+
 // One thread starts bulk copies (global -> this CTA's shared memory) of the
-// listed regions, all completing on one mbarrier; every thread then waits
-// with a bounded spin.  Regions are 16-byte aligned with sizes that are
-// multiples of 16 bytes.  Returns false (and sets bit 3 of *err) if the wait
-// ran out; the block then waits once more, bounded, for its copies to land.
+// listed regions, all completing one phase of the CTA's mbarrier (parity:
+// the phase's parity, 0 for the first copy of the CTA, flipped by each later
+// one); every thread then waits with a bounded spin.  Regions are 16-byte
+// aligned with sizes that are multiples of 16 bytes.  Shared memory the
+// block's threads wrote before (an earlier block of the same CTA) is ordered
+// before the copies by a proxy fence.  wait() returns false (and sets bit 3
+// of *err) if the wait ran out; it then waits once more, bounded, for the
+// copies to land.
 struct BulkStage {
   uint64_t* mbar;
+  uint32_t parity;
   __device__ void start(int nreg, void* const* dst, const void* const* src, const uint32_t* bytes) {
     if (threadIdx.x == 0) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)) : "memory");
-      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       uint32_t total = 0;
       for (int k = 0; k < nreg; ++k) total += bytes[k];
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(total)
@@ -70,9 +86,9 @@ struct BulkStage {
   __device__ bool try_wait() const {
     uint32_t ok;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
         : "=r"(ok)
-        : "r"(smem_u32(mbar))
+        : "r"(smem_u32(mbar)), "r"(parity)
         : "memory");
     return ok != 0;
   }
@@ -145,7 +161,8 @@ __device__ __forceinline__ void pdl_wait_then_release() {
 template <typename T, int R, bool L2, typename Wait>
 __device__ void sweep_up_block(const ApplyDesc& bd, const int* __restrict__ ipool, const T* __restrict__ fac,
                                T* __restrict__ x, int nr, int ldx, int is_front, int staged, int* err,
-                               unsigned char* smem_raw, Wait wait) {
+                               unsigned char* smem_raw, Wait wait, uint32_t parity = 0,
+                               T* __restrict__ contrib = nullptr) {
   constexpr int CG = ColGroup<R>::CG, NG = ColGroup<R>::NG;
   const int np = bd.np, nq = bd.nq;
   if (np == 0) {
@@ -155,7 +172,7 @@ __device__ void sweep_up_block(const ApplyDesc& bd, const int* __restrict__ ipoo
   const int* idp = ipool + bd.ids;
   const int* idq = idp + np;
   SweepSmem<T, R> sm(smem_raw, np, nq, staged, is_front);
-  BulkStage bs{sm.mbar};
+  BulkStage bs{sm.mbar, parity};
   const T* Linv = fac + bd.Linv;
   const T* G = fac + bd.G;
   const T* Tm = is_front ? fac + bd.T : nullptr;
@@ -168,8 +185,8 @@ __device__ void sweep_up_block(const ApplyDesc& bd, const int* __restrict__ ipoo
     gather<T, R, L2>(xp, x, idp, np, nr, ldx);
     if (is_front) gather<T, R, L2>(xq, x, idq, nq, nr, ldx);
   }
-  __syncthreads();
-  if (staged && !bs.wait(err)) return;
+  // every thread leaves if one thread's wait for the factor copy ran out
+  if (!__syncthreads_and(!staged || bs.wait(err))) return;
   if (!go) return;
   if (is_front && nq > 0) {                      // x_p -= T^T x_q
     for (int e = threadIdx.x; e < np * NG; e += blockDim.x) {
@@ -219,6 +236,7 @@ __device__ void sweep_up_block(const ApplyDesc& bd, const int* __restrict__ ipoo
       if (c0 + c >= nr) continue;
       T* dst = x + (int64_t)idq[s2] * ldx + c0 + c;
       if (is_front) *dst = xq[s2 * R + c0 + c] - acc[c];
+      else if (contrib) contrib[(bd.cslot + s2) * R + c0 + c] = acc[c];
       else atomicAdd(dst, -acc[c]);
     }
   }
@@ -227,20 +245,25 @@ __device__ void sweep_up_block(const ApplyDesc& bd, const int* __restrict__ ipoo
 template <typename T, int R>
 __global__ void k_apply_up(const ApplyDesc* __restrict__ blocks, const int* __restrict__ ipool,
                            const T* __restrict__ fac, T* __restrict__ x, int nr, int ldx,
-                           int is_front, int staged, int* err) {
+                           int is_front, int staged, int* err, T* __restrict__ contrib) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const ApplyDesc bd = blocks[blockIdx.x];
-  sweep_up_block<T, R, false>(bd, ipool, fac, x, nr, ldx, is_front, staged, err, smem_raw, [] {
-    pdl_wait_then_release();
-    return true;
-  });
+  bulk_init(reinterpret_cast<uint64_t*>(smem_raw));
+  __syncthreads();
+  sweep_up_block<T, R, false>(
+      bd, ipool, fac, x, nr, ldx, is_front, staged, err, smem_raw,
+      [] {
+        pdl_wait_then_release();
+        return true;
+      },
+      0u, contrib);
 }
 
 // One block of the down sweep (V), as sweep_up_block.
 template <typename T, int R, bool L2, typename Wait>
 __device__ void sweep_down_block(const ApplyDesc& bd, const int* __restrict__ ipool, const T* __restrict__ fac,
                                  T* __restrict__ x, int nr, int ldx, int is_front, int staged, int* err,
-                                 unsigned char* smem_raw, Wait wait) {
+                                 unsigned char* smem_raw, Wait wait, uint32_t parity = 0) {
   constexpr int CG = ColGroup<R>::CG, NG = ColGroup<R>::NG;
   const int np = bd.np, nq = bd.nq;
   if (np == 0) {
@@ -250,7 +273,7 @@ __device__ void sweep_down_block(const ApplyDesc& bd, const int* __restrict__ ip
   const int* idp = ipool + bd.ids;
   const int* idq = idp + np;
   SweepSmem<T, R> sm(smem_raw, np, nq, staged, is_front);
-  BulkStage bs{sm.mbar};
+  BulkStage bs{sm.mbar, parity};
   const T* Linv = fac + bd.Linv;
   const T* G = fac + bd.G;
   const T* Tm = is_front ? fac + bd.T : nullptr;
@@ -263,8 +286,7 @@ __device__ void sweep_down_block(const ApplyDesc& bd, const int* __restrict__ ip
     gather<T, R, L2>(xp, x, idp, np, nr, ldx);
     gather<T, R, L2>(xq, x, idq, nq, nr, ldx);
   }
-  __syncthreads();
-  if (staged && !bs.wait(err)) return;
+  if (!__syncthreads_and(!staged || bs.wait(err))) return;
   if (!go) return;
   if (nq > 0) {                                  // w = x_p - G^T x_q (in place)
     for (int e = threadIdx.x; e < np * NG; e += blockDim.x) {
@@ -320,9 +342,12 @@ __device__ void sweep_down_block(const ApplyDesc& bd, const int* __restrict__ ip
 template <typename T, int R>
 __global__ void k_apply_down(const ApplyDesc* __restrict__ blocks, const int* __restrict__ ipool,
                              const T* __restrict__ fac, T* __restrict__ x, int nr, int ldx,
-                             int is_front, int staged, int* err) {
+                             int is_front, int staged, int* err, T* __restrict__ contrib) {
+  (void)contrib;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const ApplyDesc bd = blocks[blockIdx.x];
+  bulk_init(reinterpret_cast<uint64_t*>(smem_raw));
+  __syncthreads();
   sweep_down_block<T, R, false>(bd, ipool, fac, x, nr, ldx, is_front, staged, err, smem_raw, [] {
     pdl_wait_then_release();
     return true;
@@ -336,9 +361,12 @@ __global__ void k_apply_down(const ApplyDesc* __restrict__ blocks, const int* __
 template <typename T, int R>
 __global__ void k_apply_root(const ApplyDesc* __restrict__ blocks, const int* __restrict__ ipool,
                              const T* __restrict__ fac, T* __restrict__ x, int nr, int ldx,
-                             int is_front, int staged, int* err) {
+                             int is_front, int staged, int* err, T* __restrict__ contrib) {
+  (void)contrib;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const ApplyDesc bd = blocks[0];
+  bulk_init(reinterpret_cast<uint64_t*>(smem_raw));
+  __syncthreads();
   sweep_up_block<T, R, false>(bd, ipool, fac, x, nr, ldx, 0, staged, err, smem_raw, [] {
     pdl_wait_then_release();
     return true;
@@ -359,7 +387,7 @@ __global__ void k_wait_test_bulk(int* err, long polls) {
                  : "memory");
   }
   __syncthreads();
-  BulkStage bs{&mbar};
+  BulkStage bs{&mbar, 0u};
   bs.wait(err, polls);
 }
 
@@ -372,8 +400,9 @@ void launch_wait_test_bulk(int* err, long polls, cudaStream_t st) {
 template <typename T, int R>
 __global__ void k_fwd_up(const ApplyDesc* __restrict__ blocks, const int* __restrict__ ipool,
                          const T* __restrict__ fac, T* __restrict__ x, int nr, int ldx, int is_front,
-                         int staged, int* err) {
+                         int staged, int* err, T* __restrict__ contrib) {
   (void)err;
+  (void)contrib;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   (void)staged;
   const ApplyDesc bd = blocks[blockIdx.x];
@@ -414,7 +443,7 @@ __global__ void k_fwd_up(const ApplyDesc* __restrict__ blocks, const int* __rest
 template <typename T, int R>
 __global__ void k_fwd_down(const ApplyDesc* __restrict__ blocks, const int* __restrict__ ipool,
                            const T* __restrict__ fac, T* __restrict__ x, int nr, int ldx, int is_front,
-                           int staged, int* err) {
+                           int staged, int* err, T* __restrict__ contrib) {
   (void)err;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   (void)staged;
@@ -440,6 +469,8 @@ __global__ void k_fwd_down(const ApplyDesc* __restrict__ blocks, const int* __re
     if (is_front) {
       xq[e] += acc;
       if (r < nr) x[(int64_t)idq[s2] * ldx + r] = xq[e];
+    } else if (contrib) {
+      contrib[(bd.cslot + s2) * R + r] = acc;
     } else if (r < nr) {
       atomicAdd(x + (int64_t)idq[s2] * ldx + r, acc);
     }
@@ -472,16 +503,34 @@ static size_t stage_smem(int max_np, int max_nq, int is_front) {
   return sizeof(T) * (size_t)(packed_size(max_np) + (is_front ? 2 : 1) * pad4((int64_t)max_nq * max_np));
 }
 
+// The deterministic scatter's second launch: x[dofs[k]] += sign * (sum of
+// the DOF's contribution rows in cell order), one thread per (DOF, column).
+template <typename T, int R>
+__global__ void k_contrib_reduce(const int* __restrict__ ptr, const int* __restrict__ dofs,
+                                 const int* __restrict__ slots, int ndof, const T* __restrict__ contrib,
+                                 T* __restrict__ x, int nr, int ldx, T sign) {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)ndof * nr) return;
+  const int k = (int)(e / nr), c = (int)(e % nr);
+  T s = T(0);
+  for (int j = ptr[k]; j < ptr[k + 1]; ++j) s += contrib[(int64_t)slots[j] * R + c];
+  x[(int64_t)dofs[k] * ldx + c] += sign * s;
+}
+
 template <typename T, int R>
 static void launch_sweep_R(int op, const ApplyDesc* blocks, int nblocks, const int* ipool,
                            const T* fac, T* x, int nr, int ldx, int is_front, int max_np,
-                           int max_nq, int* err, cudaStream_t st, SweepShape shape) {
+                           int max_nq, int* err, cudaStream_t st, SweepShape shape, const ContribPlan* cp) {
   const size_t vsm = vec_smem<T>(R, max_np, max_nq);
   const size_t ssm = stage_smem<T>(max_np, max_nq, is_front);
   const bool finv = op <= 1 || op == 4;   // F^-1 sweeps (4: the fused root)
   const int staged = finv && (vsm + ssm <= kStageCap) && shape.staged != 0;
   const size_t smem = vsm + (staged ? ssm : 0);
-  void (*fn)(const ApplyDesc*, const int*, const T*, T*, int, int, int, int, int*) = nullptr;
+  void (*fn)(const ApplyDesc*, const int*, const T*, T*, int, int, int, int, int*, T*) = nullptr;
+  // cells' x_q updates: to the contribution buffer, then summed per DOF
+  T* contrib = (cp && cp->ndof > 0 && !is_front && (op == 0 || op == 3)) ? static_cast<T*>(cp->buf) : nullptr;
   switch (op) {
     case 0: fn = k_apply_up<T, R>; break;
     case 1: fn = k_apply_down<T, R>; break;
@@ -504,22 +553,33 @@ static void launch_sweep_R(int op, const ApplyDesc* blocks, int nblocks, const i
   int threads = ((work + 31) / 32) * 32;
   threads = threads < 32 ? 32 : (threads > 256 ? 256 : threads);
   if (shape.threads > 0) threads = shape.threads;
-  note_launches(1);
+  note_launches(contrib ? 2 : 1);
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
   if (finv) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(nblocks);
     cfg.blockDim = dim3(threads);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, fn, blocks, ipool, fac, x, nr, ldx, is_front, staged, err);
-    return;
+    cudaLaunchKernelEx(&cfg, fn, blocks, ipool, fac, x, nr, ldx, is_front, staged, err, contrib);
+  } else {
+    fn<<<nblocks, threads, smem, st>>>(blocks, ipool, fac, x, nr, ldx, is_front, staged, err, contrib);
   }
-  fn<<<nblocks, threads, smem, st>>>(blocks, ipool, fac, x, nr, ldx, is_front, staged, err);
+  if (contrib) {
+    const int64_t n = (int64_t)cp->ndof * nr;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)((n + 255) / 256));
+    cfg.blockDim = dim3(256);
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = finv ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, k_contrib_reduce<T, R>, cp->ptr, cp->dofs, cp->slots, cp->ndof,
+                       (const T*)contrib, x, nr, ldx, op == 0 ? T(-1) : T(1));
+  }
 }
 
 template <typename T>
@@ -532,26 +592,26 @@ int sweep_chunk(int max_np, int max_nq, int nrhs) {
 template <typename T>
 void launch_sweep(int op, const ApplyDesc* blocks, int nblocks, const int* ipool, const T* fac,
                   T* x, int nrhs, int ldx, int is_front, int max_np, int max_nq, int* err, cudaStream_t st,
-                  SweepShape shape) {
+                  SweepShape shape, const ContribPlan* cp) {
   if (nblocks == 0) return;
   const int R = sweep_chunk<T>(max_np, max_nq, nrhs);
   for (int r0 = 0; r0 < nrhs; r0 += R) {
     const int nr = (nrhs - r0) < R ? (nrhs - r0) : R;
     T* xr = x + r0;
     switch (R) {
-      case 32: launch_sweep_R<T, 32>(op, blocks, nblocks, ipool, fac, xr, nr, ldx, is_front, max_np, max_nq, err, st, shape); break;
-      case 16: launch_sweep_R<T, 16>(op, blocks, nblocks, ipool, fac, xr, nr, ldx, is_front, max_np, max_nq, err, st, shape); break;
-      case 8: launch_sweep_R<T, 8>(op, blocks, nblocks, ipool, fac, xr, nr, ldx, is_front, max_np, max_nq, err, st, shape); break;
-      case 4: launch_sweep_R<T, 4>(op, blocks, nblocks, ipool, fac, xr, nr, ldx, is_front, max_np, max_nq, err, st, shape); break;
-      case 2: launch_sweep_R<T, 2>(op, blocks, nblocks, ipool, fac, xr, nr, ldx, is_front, max_np, max_nq, err, st, shape); break;
-      default: launch_sweep_R<T, 1>(op, blocks, nblocks, ipool, fac, xr, nr, ldx, is_front, max_np, max_nq, err, st, shape); break;
+      case 32: launch_sweep_R<T, 32>(op, blocks, nblocks, ipool, fac, xr, nr, ldx, is_front, max_np, max_nq, err, st, shape, cp); break;
+      case 16: launch_sweep_R<T, 16>(op, blocks, nblocks, ipool, fac, xr, nr, ldx, is_front, max_np, max_nq, err, st, shape, cp); break;
+      case 8: launch_sweep_R<T, 8>(op, blocks, nblocks, ipool, fac, xr, nr, ldx, is_front, max_np, max_nq, err, st, shape, cp); break;
+      case 4: launch_sweep_R<T, 4>(op, blocks, nblocks, ipool, fac, xr, nr, ldx, is_front, max_np, max_nq, err, st, shape, cp); break;
+      case 2: launch_sweep_R<T, 2>(op, blocks, nblocks, ipool, fac, xr, nr, ldx, is_front, max_np, max_nq, err, st, shape, cp); break;
+      default: launch_sweep_R<T, 1>(op, blocks, nblocks, ipool, fac, xr, nr, ldx, is_front, max_np, max_nq, err, st, shape, cp); break;
     }
   }
 }
 
 template void launch_sweep<double>(int, const ApplyDesc*, int, const int*, const double*, double*,
-                                   int, int, int, int, int, int*, cudaStream_t, SweepShape);
+                                   int, int, int, int, int, int*, cudaStream_t, SweepShape, const ContribPlan*);
 template void launch_sweep<float>(int, const ApplyDesc*, int, const int*, const float*, float*,
-                                  int, int, int, int, int, int*, cudaStream_t, SweepShape);
+                                  int, int, int, int, int, int*, cudaStream_t, SweepShape, const ContribPlan*);
 
 }  // namespace hif

@@ -14,6 +14,14 @@ least a tenth of the paper's): a factor-3 lower bound, set first, failed at
 eps = 1e-12, where the estimate reads 1.6e-12 against the paper's 4.8e-12,
 i.e. a more accurate factorization.  The FP64 factorization throughout (eps
 down to 1e-12).
+
+hifde3x at 63^3 skeletonizes edges from level 2 (of levels 0..2).  Section 5
+skips the first few fractional levels "in select cases" without naming
+them; with edges from level 1, as at 31^3 and for the Laplacian at 63^3,
+this build gets |s_L| 3824 and e_a 1.0e-5 against the paper's 2934 and
+2.0e-6, and with edges from level 2 it gets 2936 and 2.0e-6 (measured on a
+GB300 before the row was written into this test), so that is the reading
+taken for Example 6.
 """
 import os
 
@@ -32,11 +40,11 @@ def _rows(name):
         return [line.split() for line in fh if line.strip() and not line.startswith("#")]
 
 
-def _check(dim, n, ppw, eps, variant, sL, ea_p, ni):
+def _check(dim, n, ppw, eps, variant, sL, ea_p, ni, edge_start=1):
     from paper_1307_2895_gb300 import hif
     a, b = inputs.helmholtz_coefficients(dim, n, ppw)
     f = inputs.rhs(dim, n, 2, seed=0)
-    F = hif.factor(dim, n, a, b, eps, precision="fp64", variant=variant)
+    F = hif.factor(dim, n, a, b, eps, precision="fp64", variant=variant, edge_start=edge_start)
     try:
         st = F.stats()
         ea, es = F.estimate(inputs.power_start(dim, n), rtol=1e-2)
@@ -65,4 +73,6 @@ def test_helmholtz2d_1023_matches_paper_tables5_6(hiflib, row):
 @pytest.mark.parametrize("row", range(6))
 def test_helmholtz3d_matches_paper_tables11_12(hiflib, row):
     variant, n, eps, sL, ea, es, ni = _rows("paper_table11_example6.txt")[row]
-    _check(3, int(n), 8, float(eps), "hifde" if variant == "hifde3" else "hifde3x", int(sL), float(ea), int(ni))
+    x3 = variant == "hifde3x"
+    _check(3, int(n), 8, float(eps), "hifde3x" if x3 else "hifde", int(sL), float(ea), int(ni),
+           edge_start=2 if (x3 and int(n) == 64) else 1)
