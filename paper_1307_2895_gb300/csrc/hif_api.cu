@@ -601,6 +601,25 @@ struct Factorizer {
     tau = (h_->precision == HIF_PREC_MIXED) ? 4e-6 : 0.0;
   }
 
+  // cells built ahead from a superset of the active DOFs: drop the DOFs
+  // marked dead since (lists stay ascending)
+  void drop_dead(std::vector<HostCell>& cells) {
+    const int nc = (int)cells.size();
+    const int ntask = task_count(nc, 64);
+    parallel_tasks(ntask, [&](int t) {
+      int64_t c0, c1;
+      task_range(nc, ntask, t, c0, c1);
+      for (int64_t c = c0; c < c1; ++c) {
+        for (std::vector<int>* v : {&cells[c].I, &cells[c].B}) {
+          size_t w = 0;
+          for (size_t r = 0; r < v->size(); ++r)
+            if (!dead[(*v)[r]]) (*v)[w++] = (*v)[r];
+          v->resize(w);
+        }
+      }
+    });
+  }
+
   // the host blocked on the device (the per-level read-backs), timed for
   // hif_stats: stream st, or event e when given
   void wait_device(cudaEvent_t e = nullptr) {
@@ -787,7 +806,7 @@ struct Factorizer {
   void factor_cells(const std::vector<CellDesc>& cd, const CellDesc* d_cd, U* work, U* fac, DevBuf& selbuf,
                     DevBuf& tdbuf) {
     std::vector<int> small, big;
-    int max_small = 0, max_bI = 0, max_bB = 0;
+    int max_small = 0, max_sB = 0, max_bI = 0, max_bB = 0;
     for (int i = 0; i < (int)cd.size(); ++i) {
       if (cd[i].nI >= h->big_cell && cd[i].nI > 0) {
         big.push_back(i);
@@ -796,16 +815,18 @@ struct Factorizer {
       } else {
         small.push_back(i);
         max_small = std::max(max_small, cd[i].nI);
+        max_sB = std::max(max_sB, cd[i].nB);
       }
     }
     if (big.empty()) {
-      launch_cell_factor<U>(d_cd, nullptr, (int)cd.size(), work, fac, status.as<int>(), max_small, tau, st);
+      launch_cell_factor<U>(d_cd, nullptr, (int)cd.size(), work, fac, status.as<int>(), max_small, max_sB, tau,
+                            st);
       return;
     }
     if (!small.empty()) {
       upload(selbuf, small, st);
-      launch_cell_factor<U>(d_cd, selbuf.as<int>(), (int)small.size(), work, fac, status.as<int>(), max_small, tau,
-                            st);
+      launch_cell_factor<U>(d_cd, selbuf.as<int>(), (int)small.size(), work, fac, status.as<int>(), max_small,
+                            max_sB, tau, st);
     }
     std::vector<TDesc> td(big.size());
     for (size_t b = 0; b < big.size(); ++b) {
@@ -887,10 +908,24 @@ struct Factorizer {
     }
     tr.lap("level 0 cells");
     std::vector<int> alive = L0->alive1;
+    // Host work overlapped with the fronts on the GPU (hifde2 / hifde3):
+    // level l + 1's cells are built from the DOFs active before the fronts
+    // of level l (their redundant DOFs are dropped once the ranks are read
+    // back, which gives the same lists), and level l's apply descriptors are
+    // built after level l + 1's cells have been launched.
+    const bool overlap = !x3;
+    std::vector<HostCell> cells_a, cells_b;
+    int spec_level = -1;   // the level whose cells were built ahead
+    auto build_ahead = [&](int l1) {
+      if (l1 > L) return;
+      build_cells(G, l1, alive, (l1 & 1) ? cells_a : cells_b);
+      spec_level = l1;
+    };
     if (skel && 0 >= h->skip_levels) {
       const size_t nfi = h->finfo.size();
       run_fronts(0, L0->d_cdesc, work, alive, L0->fronts, L0->fdesc, L0->d_fdesc, L0->d_fip, L0->fwork_elems,
-                 L0->ffac_elems, L0->fout_elems, L0->max_nc, L0->max_nN, h->fronts[0], 0);
+                 L0->ffac_elems, L0->fout_elems, L0->max_nc, L0->max_nN, h->fronts[0], 0, overlap,
+                 overlap ? std::function<void()>([&] { build_ahead(1); }) : nullptr);
       if (h->finfo.size() > nfi) sym_fronts();
     }
     if (x3 && h->edge_start == 0) {   // hifde3x with edges from level 0 on
@@ -900,7 +935,6 @@ struct Factorizer {
     }
     const std::vector<HostCell>* prev_cells = &L0->cells;
     const CellDesc* prev_ddesc = L0->d_cdesc;
-    std::vector<HostCell> cells_a, cells_b;
     DevBuf ddesc_a, ddesc_b;
     prev_work.swap(work);
 
@@ -910,7 +944,9 @@ struct Factorizer {
       std::vector<HostCell>& cells = (l & 1) ? cells_a : cells_b;
       DevBuf& ddesc = (l & 1) ? ddesc_a : ddesc_b;
       tr.lap("other");
-      build_cells(G, l, alive, cells);
+      if (spec_level == l) drop_dead(cells);   // built ahead: without the redundant DOFs
+      else build_cells(G, l, alive, cells);
+      spec_level = -1;
       tr.lap("cells build");
       std::vector<CellDesc> cdesc;
       std::vector<int> ipool;
@@ -941,6 +977,7 @@ struct Factorizer {
       }
       CU(cudaGetLastError());
       tr.lap("cells launch");
+      finish_fronts();   // the previous fronts' apply descriptors, deferred
       std::vector<ApplyDesc> ad;
       cell_apply_descs(cdesc, ad, sw.max_np, sw.max_nq, sw.fac_elems, sw.vec_rows);
       if (h->deterministic && !is_root) build_contrib_plan(cdesc, ipool, sw, st);
@@ -986,7 +1023,8 @@ struct Factorizer {
         tr.lap("fronts upload");
         const size_t nfi = h->finfo.size();
         run_fronts(l, dd, work, alive, fr, fd, d_fd.as<FrontDesc>(), d_ip.as<int>(), fw, ff, fo, mnc, mnN,
-                   h->fronts[l], h->variant == HIF_VARIANT_HIFDE3X ? 2 * l : l);
+                   h->fronts[l], h->variant == HIF_VARIANT_HIFDE3X ? 2 * l : l, overlap,
+                   overlap ? std::function<void()>([&, l] { build_ahead(l + 1); }) : nullptr);
         if (h->finfo.size() > nfi) sym_fronts();
       }
       if (x3 && l == h->edge_start) {   // hifde3x: the assembled upper levels from these edges on
@@ -1003,6 +1041,7 @@ struct Factorizer {
   // The factorization's device status: counts for hif_stats, then the
   // failures (a non-positive pivot, a bounded wait that ran out).
   void finish_status() {
+    finish_fronts();
     tr.lap("other");
     int hs2[5] = {0, 0, 0, 0, 0};
     CU(cudaMemcpyAsync(hs2, status.p, 5 * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1024,7 +1063,8 @@ struct Factorizer {
   void run_fronts(int l, const CellDesc* d_cdesc, DevBuf& cwork, std::vector<int>& alive,
                   std::shared_ptr<const std::vector<HostFront>> fr, std::shared_ptr<const std::vector<FrontDesc>> fdp,
                   const FrontDesc* d_fd, const int* d_ip, int64_t work_elems, int64_t fac_elems,
-                  int64_t out_elems, int max_nc, int max_nN, SweepLevel& sw, int frac) {
+                  int64_t out_elems, int max_nc, int max_nN, SweepLevel& sw, int frac, bool defer = false,
+                  const std::function<void()>& overlap = nullptr) {
     const std::vector<FrontDesc>& fd = *fdp;
     const int nf = (int)fd.size();
     if (nf == 0) return;
@@ -1097,6 +1137,10 @@ struct Factorizer {
     }
     CU(cudaGetLastError());
     tr.lap("fronts launch");
+    if (overlap) {   // host work that needs no result of these fronts, while they run
+      overlap();
+      tr.lap("overlap");
+    }
     info.fr = fr;
     info.fd = fdp;
     info.out.resize(out_elems);
@@ -1158,7 +1202,38 @@ struct Factorizer {
     }
     fwork.release();
     obuf.release();
-    // apply descriptors: p = redundant (ascending), q = skeletons (pivot order)
+    // the redundant DOFs leave the active set: marked now (the next level's
+    // cells need it); the apply descriptors follow in finish_fronts, at once
+    // or, deferred, after the next level's cells are launched
+    for (int f = 0; f < nf; ++f) {
+      const FrontDesc& d = fd[f];
+      const int* out = info.out.data() + d.out;
+      const int* ids_sr = out + 1 + d.nc;
+      for (int t = out[0]; t < d.nc; ++t) dead[ids_sr[t]] = 1;
+    }
+    h->finfo.push_back(std::move(info));
+    pend = Pending{true, &sw, &alive, h->finfo.size() - 1, !defer};
+    tr.lap("fronts readback post");
+    if (!defer) finish_fronts();
+  }
+
+  // Apply descriptors of the last skeletonized fractional level: p =
+  // redundant (ascending), q = skeletons (pivot order); and, unless the
+  // caller drops the dead DOFs itself, the active set without them.
+  struct Pending {
+    bool on = false;
+    SweepLevel* sw = nullptr;
+    std::vector<int>* alive = nullptr;
+    size_t idx = 0;
+    bool filter_alive = true;
+  } pend;
+  void finish_fronts() {
+    if (!pend.on) return;
+    pend.on = false;
+    SweepLevel& sw = *pend.sw;
+    const LevelFronts& info = h->finfo[pend.idx];
+    const std::vector<FrontDesc>& fd = *info.fd;
+    const int nf = (int)fd.size();
     std::vector<ApplyDesc> ad(nf);
     std::vector<int> aip;
     sw.max_np = sw.max_nq = 0;
@@ -1188,7 +1263,6 @@ struct Factorizer {
         sw.fac_elems += 0.5 * nR * (nR + 1.0) + 2.0 * k * nR;
         sw.vec_rows += nR + k;
       }
-      for (int t = k; t < d.nc; ++t) dead[ids_sr[t]] = 1;
       h->n_fronts += 1;
       h->max_rank = std::max(h->max_rank, k);
       const double nc = d.nc, nN = d.nN, kk = k, nr = nR;
@@ -1199,17 +1273,19 @@ struct Factorizer {
       h->apply_bytes += 2.0 * esz * (2 * kk * nr + nr * (nr + 1) / 2);
       h->factor_bytes += (long long)(esz * (2 * kk * nr + nr * (nr + 1) / 2));
     }
-    h->finfo.push_back(std::move(info));
     sw.nblocks = nf;
     upload(sw.desc_own, ad, st);
     upload(sw.ipool_own, aip, st);
     sw.desc = sw.desc_own.as<ApplyDesc>();
     sw.ipool = sw.ipool_own.as<int>();
-    std::vector<int> next;
-    next.reserve(alive.size());
-    for (int g : alive)
-      if (!dead[g]) next.push_back(g);
-    alive.swap(next);
+    if (pend.filter_alive) {
+      std::vector<int>& alive = *pend.alive;
+      std::vector<int> next;
+      next.reserve(alive.size());
+      for (int g : alive)
+        if (!dead[g]) next.push_back(g);
+      alive.swap(next);
+    }
     tr.lap("fronts post");
   }
 };

@@ -41,10 +41,11 @@ void launch_leaf_assemble(const CellDesc* cells, int ncells, const int* ipool, T
 template <typename TU, typename TF>
 void launch_extend_add(const CellDesc* cells, int ncells, const int* ipool, TF* work,
                        const CellDesc* pcells, const TU* pwork, int nchild, int max_nF, cudaStream_t st);
-// sel (may be NULL: cells 0..ncells-1) lists the cells to factor
+// sel (may be NULL: cells 0..ncells-1) lists the cells to factor; max_nI /
+// max_nB over the listed cells
 template <typename T>
 void launch_cell_factor(const CellDesc* cells, const int* sel, int ncells, T* work, T* fac, int* status,
-                        int max_nI, double tau, cudaStream_t st);
+                        int max_nI, int max_nB, double tau, cudaStream_t st);
 // tiled multi-block elimination of the problems td[0..n) (kernels_tiled.cu)
 template <typename T>
 void launch_tiled_elim(const TDesc* td, int n, int max_nI, int max_nB, T* work, T* fac, int* status, double tau,

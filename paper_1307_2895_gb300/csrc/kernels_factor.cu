@@ -179,7 +179,12 @@ __global__ void k_cell_factor(const CellDesc* __restrict__ cells, const int* __r
   const int64_t n2 = (int64_t)nI * nI;
   T* A = FII;
   T* X = Xg;
-  if (2 * n2 <= smem_elems) {
+  T* W = G;                                  // W = F_BI L^-T, in shared memory when it fits
+  if (2 * n2 + (int64_t)nB * nI <= smem_elems) {
+    A = sm;
+    X = sm + n2;
+    W = sm + 2 * n2;
+  } else if (2 * n2 <= smem_elems) {
     A = sm;
     X = sm + n2;
   } else if (n2 <= smem_elems) {
@@ -191,9 +196,10 @@ __global__ void k_cell_factor(const CellDesc* __restrict__ cells, const int* __r
   blk_pack_lower(A, nI, Lp, nI);
   blk_pack_lower(X, nI, Linv, nI);
   if (nB > 0) {
-    blk_mul_linvT(FBI, nI, X, nI, nB, nI, G, nI);          // W = F_BI L^-T
-    blk_syrk_sub(FBB, nB, G, nI, nB, nI, neg ? Sg : (const T*)nullptr);   // F_BB -= W D W^T
-    if (neg) blk_scale_cols(G, nI, nB, nI, Sg);           // the stored G is W D
+    blk_mul_linvT(FBI, nI, X, nI, nB, nI, W, nI);          // W = F_BI L^-T
+    blk_syrk_sub(FBB, nB, W, nI, nB, nI, neg ? Sg : (const T*)nullptr);   // F_BB -= W D W^T
+    if (neg) blk_scale_cols(W, nI, nB, nI, Sg);           // the stored G is W D
+    if (W != G) blk_copy(W, nI, G, nI, nB, nI);
   }
 }
 
@@ -435,10 +441,13 @@ void launch_extend_add(const CellDesc* cells, int ncells, const int* ipool, TF* 
 
 template <typename T>
 void launch_cell_factor(const CellDesc* cells, const int* sel, int ncells, T* work, T* fac, int* status,
-                        int max_nI, double tau, cudaStream_t st) {
+                        int max_nI, int max_nB, double tau, cudaStream_t st) {
   if (ncells == 0) return;
   const int cap_bytes = 200 * 1024;
-  int64_t need = 2LL * max_nI * max_nI * (int64_t)sizeof(T);
+  // L, L^-1 and W = F_BI L^-T in shared memory when they fit (the Schur
+  // update then reads W's rows from shared memory), else L and L^-1, else L
+  int64_t need = (2LL * max_nI * max_nI + (int64_t)max_nB * max_nI) * (int64_t)sizeof(T);
+  if (need > cap_bytes) need = 2LL * max_nI * max_nI * (int64_t)sizeof(T);
   if (need > cap_bytes) need = (int64_t)max_nI * max_nI * (int64_t)sizeof(T);
   if (need > cap_bytes) need = 0;
   const int smem = (int)need;
@@ -472,9 +481,9 @@ template void launch_extend_add<float, float>(const CellDesc*, int, const int*, 
                                               const CellDesc*, const float*, int, int, cudaStream_t);
 template void launch_extend_add<float, double>(const CellDesc*, int, const int*, double*,
                                                const CellDesc*, const float*, int, int, cudaStream_t);
-template void launch_cell_factor<double>(const CellDesc*, const int*, int, double*, double*, int*, int, double,
-                                         cudaStream_t);
-template void launch_cell_factor<float>(const CellDesc*, const int*, int, float*, float*, int*, int, double,
+template void launch_cell_factor<double>(const CellDesc*, const int*, int, double*, double*, int*, int, int,
+                                         double, cudaStream_t);
+template void launch_cell_factor<float>(const CellDesc*, const int*, int, float*, float*, int*, int, int, double,
                                         cudaStream_t);
 template void launch_front<double>(const FrontDesc*, int, const CellDesc*, const int*, int*, double*, double*,
                                    double*, double, int*, int, int, double, const int*, SketchStream, const int*,
