@@ -17,12 +17,13 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libhif.so")
-SOURCES = ["kernels_factor.cu", "kernels_apply.cu", "kernels_solve.cu", "hif_api.cu", "geometry.cpp",
+SOURCES = ["kernels_factor.cu", "kernels_apply.cu", "kernels_solve.cu", "hif_api.cu", "hif_factor.cu",
+           "hif_apply.cu", "hif_solve.cu", "geometry.cpp",
            "noalloc.cu", "kernels_mlp.cu", "kernels_tiled.cu", "kernels_bigfront.cu", "kernels_tc.cu",
            "host_pool.cpp", "symbolic3x.cpp", "kernels_dense3x.cu",
            "kernels_root.cu"]
 HEADERS = ["hif_internal.h", "kernels.h", "blockops.cuh", "geometry.h", "tile_mma.cuh", "front_common.cuh",
-           "host_pool.h", "symbolic3x.h"]
+           "host_pool.h", "symbolic3x.h", "hif_host.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
