@@ -445,8 +445,11 @@ void launch_cell_factor(const CellDesc* cells, const int* sel, int ncells, T* wo
   if (ncells == 0) return;
   const int cap_bytes = 200 * 1024;
   // L, L^-1 and W = F_BI L^-T in shared memory when they fit (the Schur
-  // update then reads W's rows from shared memory), else L and L^-1, else L
-  int64_t need = (2LL * max_nI * max_nI + (int64_t)max_nB * max_nI) * (int64_t)sizeof(T);
+  // update then reads W's rows from shared memory), else L and L^-1, else L.
+  // W only when it is large: the many small leaf cells run faster with more
+  // blocks resident per SM than with W's rows in shared memory.
+  const bool w_smem = (int64_t)max_nB * max_nI * (int64_t)sizeof(T) > 16 * 1024;
+  int64_t need = (2LL * max_nI * max_nI + (w_smem ? (int64_t)max_nB * max_nI : 0)) * (int64_t)sizeof(T);
   if (need > cap_bytes) need = 2LL * max_nI * max_nI * (int64_t)sizeof(T);
   if (need > cap_bytes) need = (int64_t)max_nI * max_nI * (int64_t)sizeof(T);
   if (need > cap_bytes) need = 0;
