@@ -159,6 +159,13 @@ typedef struct hif_opts {
                            of HIF_VARIANT_HIFDE3X's assembled levels still
                            adds with atomics; the other variants' factor-
                            izations are reproducible either way.             */
+  long long big_apply;  /* applications of F^-1: blocks with np (np + 2 nq)
+                           >= big_apply elements (np eliminated, nq
+                           neighbour DOFs) are applied by many thread blocks
+                           each, in the pattern of the large root, the others
+                           one block each; 0 -> 2^20, < 0 -> never.  Not in
+                           the deterministic mode.  Same result up to
+                           rounding order.                                   */
 } hif_opts;
 
 typedef struct hif_handle hif_handle;

@@ -19,6 +19,39 @@ bool is_device_ptr(const void* p) {
 // ---------------------------------------------------------------------------
 // apply of F^-1 / F on a packed N x nrhs work vector of the factor's type
 // ---------------------------------------------------------------------------
+void split_big(hif_handle* h, SweepLevel& sw, const std::vector<ApplyDesc>& ad, cudaStream_t st) {
+  sw.nbig = sw.nsmall = 0;
+  sw.big_scr = 0;
+  if (h->big_apply <= 0 || h->deterministic) return;
+  std::vector<ApplyDesc> small;
+  std::vector<BigBlock> big;
+  int snp = 0, snq = 0, bnp = 0, bnq = 0;
+  int64_t scr = 0;
+  for (const ApplyDesc& a : ad) {
+    const int64_t elems = (int64_t)a.np * ((int64_t)a.np + 2 * (int64_t)a.nq);
+    if (a.np > 0 && elems >= h->big_apply) {
+      big.push_back(BigBlock{a, scr});
+      scr += 2 * (int64_t)a.np * kBigChunk;
+      bnp = std::max(bnp, a.np);
+      bnq = std::max(bnq, a.nq);
+    } else {
+      small.push_back(a);
+      snp = std::max(snp, a.np);
+      snq = std::max(snq, a.nq);
+    }
+  }
+  if (big.empty()) return;
+  upload(sw.small_desc, small, st);
+  upload(sw.big_desc, big, st);
+  sw.nsmall = (int)small.size();
+  sw.small_max_np = snp;
+  sw.small_max_nq = snq;
+  sw.nbig = (int)big.size();
+  sw.big_max_np = bnp;
+  sw.big_max_nq = bnq;
+  sw.big_scr = scr;
+}
+
 // The factor as the float apply reads it: the float copy when there is one.
 const float* fac_f32(const SweepLevel& S) {
   return S.fac32.p ? S.fac32.as<float>() : S.fac.as<float>();
@@ -61,8 +94,16 @@ struct TuneKey {
 std::mutex g_tune_mu;
 std::map<TuneKey, SweepShape> g_tune;
 
+// The launch's blocks: desc[0..nblocks) with ids in ipool, largest np / nq.
+struct SweepBlocks {
+  const ApplyDesc* desc;
+  int nblocks;
+  const int* ipool;
+  int max_np, max_nq;
+};
+
 template <typename T>
-SweepShape tuned_shape(hif_handle* h, int op, const SweepLevel& S, int is_front, const T* fac, const T* x,
+SweepShape tuned_shape(hif_handle* h, int op, const SweepBlocks& S, int is_front, const T* fac, const T* x,
                        int nrhs, const ContribPlan* cp) {
   const TuneKey key{op, (int)sizeof(T), nrhs, S.nblocks, S.max_np, S.max_nq, is_front};
   {
@@ -125,6 +166,11 @@ void run_apply(hif_handle* h, int mode, T* x, int nrhs) {
   };
   auto sweep = [&](const SweepLevel& S, int op, int is_front, const T* fac) {
     if (S.nblocks == 0) return;
+    // F^-1 with large blocks: those by the many-block kernels, the others as usual
+    const bool big = (op == 0 || op == 1) && S.nbig > 0 && h->big_scratch.p;
+    const SweepBlocks B = big ? SweepBlocks{S.small_desc.as<ApplyDesc>(), S.nsmall, S.ipool, S.small_max_np,
+                                            S.small_max_nq}
+                              : SweepBlocks{S.desc, S.nblocks, S.ipool, S.max_np, S.max_nq};
     if (prof) {
       if (h->ev_used + 2 > h->ev_pool.size()) {
         for (int k = 0; k < 64; ++k) {
@@ -139,17 +185,23 @@ void run_apply(hif_handle* h, int mode, T* x, int nrhs) {
     // it for the sweeps that update x_q of cells)
     ContribPlan cp{S.cp_ptr.as<int>(), S.cp_dofs.as<int>(), S.cp_slots.as<int>(), S.cp_ndof, h->contrib_buf.p};
     const ContribPlan* cpp = (h->deterministic && !is_front && S.cp_ndof > 0) ? &cp : nullptr;
-    const SweepShape shape = (h->autotune && mode == HIF_APPLY_FINV)
-                                 ? tuned_shape<T>(h, op, S, is_front, fac, x, nrhs, cpp)
-                                 : SweepShape{};
-    launch_sweep<T>(op, S.desc, S.nblocks, S.ipool, fac, x, nrhs, nrhs, is_front, S.max_np, S.max_nq,
-                    h->dev_err.as<int>(), st, shape, cpp);
+    if (B.nblocks > 0) {
+      const SweepShape shape = (h->autotune && mode == HIF_APPLY_FINV)
+                                   ? tuned_shape<T>(h, op, B, is_front, fac, x, nrhs, cpp)
+                                   : SweepShape{};
+      launch_sweep<T>(op, B.desc, B.nblocks, B.ipool, fac, x, nrhs, nrhs, is_front, B.max_np, B.max_nq,
+                      h->dev_err.as<int>(), st, shape, cpp);
+    }
+    int nl_big = 0;
+    if (big)
+      nl_big = launch_big_sweep<T>(op, S.big_desc.as<BigBlock>(), S.nbig, S.big_max_np, S.big_max_nq, is_front,
+                                   S.ipool, fac, x, nrhs, nrhs, h->big_scratch.as<T>(), S.big_scr, st);
     if (prof) {
       CU(cudaEventRecord(h->ev_pool[h->ev_used + 1], st));
       h->ev_used += 2;
     }
     if (count) {
-      h->prof_launches += 1;
+      h->prof_launches += (B.nblocks > 0 ? 1 : 0) + nl_big;
       h->prof_bytes += sweep_bytes(S, op);
     }
   };

@@ -463,6 +463,7 @@ struct Factorizer {
       sw.nblocks = (int)ad.size();
       upload(sw.desc_own, ad, st);
       sw.desc = sw.desc_own.as<ApplyDesc>();
+      split_big(h, sw, ad, st);
       account_cells(cd, sizeof(T));
       for (const std::vector<int>& p : P)
         if (!p.empty()) sym->eliminate(p);
@@ -690,6 +691,7 @@ struct Factorizer {
       sw.nblocks = (int)ad.size();
       upload(sw.desc_own, ad, st);
       sw.desc = sw.desc_own.as<ApplyDesc>();
+      if (!is_root) split_big(h, sw, ad, st);
       account_cells(cdesc, esz);
       prev_work.release();           // the level l-1 updates have been consumed
       if (is_root) {
@@ -983,6 +985,7 @@ struct Factorizer {
     upload(sw.desc_own, ad, st);
     upload(sw.ipool_own, aip, st);
     sw.desc = sw.desc_own.as<ApplyDesc>();
+    split_big(h, sw, ad, st);
     sw.ipool = sw.ipool_own.as<int>();
     if (pend.filter_alive) {
       std::vector<int>& alive = *pend.alive;
@@ -1051,6 +1054,7 @@ int hif_factor(const hif_grid* grid, const double* a_stag, const double* b, cons
       throw HifError(HIF_ERR_ARG, "sketch_power must be 0, 1 or 2");
     if (opts) h->sketch_power = opts->sketch_power;
     if (opts) h->deterministic = opts->deterministic != 0;
+    if (opts && opts->big_apply != 0) h->big_apply = opts->big_apply < 0 ? 0 : opts->big_apply;
     if (h->id_mode == HIF_ID_LEARNED && !(opts && opts->rank_model))
       throw HifError(HIF_ERR_ARG, "HIF_ID_LEARNED needs opts.rank_model");
     h->st = opts ? (cudaStream_t)opts->stream : nullptr;
@@ -1100,6 +1104,12 @@ int hif_factor(const hif_grid* grid, const double* a_stag, const double* b, cons
     if (prec == HIF_PREC_FP32_APPLY) demote_factor(h);
     if (h->root_size >= kRootMulti)
       h->root_scratch.alloc(sizeof(double) * (size_t)root_scratch_elems(h->root_size, h->deterministic), h->st);
+    {   // scratch of the levels' large blocks (F^-1 by many thread blocks)
+      int64_t big = 0;
+      for (auto* v : {&h->cells, &h->fronts, &h->edges})
+        for (const SweepLevel& S : *v) big = std::max(big, S.big_scr);
+      if (big > 0) h->big_scratch.alloc(sizeof(double) * (size_t)big, h->st);
+    }
     if (h->deterministic) {
       int64_t rows = 0;
       for (const SweepLevel& S : h->cells) rows = std::max(rows, S.cp_rows);

@@ -193,6 +193,13 @@ struct SweepLevel {
   DevBuf cp_ptr, cp_dofs, cp_slots;
   int cp_ndof = 0;
   int64_t cp_rows = 0;   // rows of the contribution buffer the level uses
+  // F^-1 with large blocks (nbig > 0): the other blocks' descriptors for the
+  // one-block launch, and the large ones (BigBlock) for the many-block one
+  int nsmall = 0, small_max_np = 0, small_max_nq = 0;
+  DevBuf small_desc;
+  int nbig = 0, big_max_np = 0, big_max_nq = 0;
+  DevBuf big_desc;
+  int64_t big_scr = 0;   // scratch elements of the large blocks
 };
 
 // Skeleton structure of one fractional level (for hif_structure).
@@ -276,6 +283,9 @@ struct hif_handle {
   int edge_start = 1;   // HIFDE3X: first level whose edges are skeletonized
   int sketch_power = 0; // power iterations on the randomized ID's sketch
   bool deterministic = false;   // sweeps and root apply without floating-point atomics
+  int64_t big_apply = int64_t(1) << 20;   // F^-1: blocks with np (np + 2 nq) >= this many elements by
+                                          // many thread blocks (0: none)
+  DevBuf big_scratch;           // their scratch (the largest level's, doubles)
   DevBuf contrib_buf;           // the deterministic scatter's contribution rows (32 doubles each)
   int big_cell = 192;   // cells with at least this many interior DOFs use the tiled elimination
   bool coop_qr = true;  // large fronts: pivoted QR by co-resident block groups
@@ -335,6 +345,10 @@ namespace hif {
 namespace host {
 
 // hif_apply.cu
+// Separates the large blocks of a level (np (np + 2 nq) >= h->big_apply
+// elements, F^-1 only, not in the deterministic mode) from the others; ad:
+// the level's descriptors as uploaded to sw.desc.
+void split_big(hif_handle* h, SweepLevel& sw, const std::vector<ApplyDesc>& ad, cudaStream_t st);
 const float* fac_f32(const SweepLevel& S);   // the factor as the float apply reads it
 void demote_factor(hif_handle* h);            // FP32_APPLY: float copy of every block
 template <typename T>

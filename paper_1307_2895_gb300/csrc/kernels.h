@@ -156,6 +156,20 @@ void launch_sweep(int op, const ApplyDesc* blocks, int nblocks, const int* ipool
                   int nrhs, int ldx, int is_front, int max_np, int max_nq, int* err, cudaStream_t st,
                   SweepShape shape = SweepShape{}, const ContribPlan* cp = nullptr);
 
+// F^-1 sweeps of the large blocks of a level by many thread blocks each
+// (kernels_bigapply.cu): one BigBlock per block, scr = the offset of its
+// scratch (2 np kBigChunk elements); dir 0 up, 1 down; max_np / max_nq over
+// the blocks; scratch_elems: the level's scratch, zeroed here per chunk of
+// kBigChunk right-hand sides.  Returns the launches made.
+struct BigBlock {
+  ApplyDesc d;
+  int64_t scr;
+};
+constexpr int kBigChunk = 8;
+template <typename T>
+int launch_big_sweep(int dir, const BigBlock* bbs, int nbig, int max_np, int max_nq, int is_front, const int* ipool,
+                     const T* fac, T* x, int nrhs, int ldx, T* scratch, int64_t scratch_elems, cudaStream_t st);
+
 // stencil operator and CG vector operations (kernels_solve.cu)
 void launch_matvec(GridInfo g, const double* a_stag, const double* b, const double* x, int ldx,
                    double* y, int ldy, int nr, cudaStream_t st);
