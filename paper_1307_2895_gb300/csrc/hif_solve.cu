@@ -71,6 +71,7 @@ struct Precond {
       h->profile = 0;
       h->count_sweeps = true;   // what one replay moves and launches
       cudaGraph_t g = nullptr;
+      const long long k0 = hif_kernel_launches();
       CU(cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal));
       try {
         eager();
@@ -84,6 +85,8 @@ struct Precond {
         throw;
       }
       const cudaError_t ce = cudaStreamEndCapture(h->st, &g);
+      graph_kernels = hif_kernel_launches() - k0;   // the kernels one replay runs
+      note_launches(-graph_kernels);                 // recorded, not run, by the capture
       h->profile = prof;
       h->count_sweeps = false;
       const double gb = h->prof_bytes - b0;
@@ -115,6 +118,7 @@ struct Precond {
       CU(cudaEventRecord(h->ev_pool[h->ev_used], h->st));
     }
     CU(cudaGraphLaunch(exec, h->st));
+    note_launches(graph_kernels);   // the launch counter counts every kernel a replay runs
     if (h->profile) {
       CU(cudaEventRecord(h->ev_pool[h->ev_used + 1], h->st));
       h->ev_used += 2;
@@ -123,6 +127,7 @@ struct Precond {
     CU(cudaGetLastError());
   }
   int pending_graphs = 0;
+  long long graph_kernels = 0;
   // after the stream is synchronized: every recorded replay (and eager sweep)
   void settle() {
     if (!h->profile) return;
