@@ -121,9 +121,9 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(self.samples)}
 
 
-def _workload_arrays():
+def _workload_arrays(name: str = "contrast2d_n512"):
     from paper_1307_2895_gb300 import inputs
-    w = inputs.workload("contrast2d_n512")
+    w = inputs.workload(name)
     f = inputs.rhs(w["dim"], w["n"], w["nrhs"], seed=0)
     return w, f
 
@@ -674,20 +674,25 @@ def run_solve_only(args):
 
 
 def run_apply_only(args):
-    """Factor the workload once and run a number of F^-1 applies (8 RHS):
-    the command ncu captures the sweep kernels of.  The built-in launch shapes
-    (no autotuning), so that the n-th sweep launch is the same every run; the
-    bytes a launch moves do not depend on its shape."""
+    """Factor the workload once and run a number of F^-1 applies (its RHS
+    count: 8 for the 2D headline, 4 for the 3D ones): the command ncu captures
+    the sweep kernels of.  The built-in launch shapes (no autotuning), so that
+    the n-th sweep launch is the same every run; the bytes a launch moves do
+    not depend on its shape.  With --workload3d the 3D workload (and
+    --variant, --eps) instead of the headline one."""
     import torch
     from paper_1307_2895_gb300 import hif
     hif.load()
-    w, f_np = _workload_arrays()
+    w, f_np = _workload_arrays(args.workload3d or "contrast2d_n512")
+    eps = args.eps if (args.workload3d and args.eps > 0) else w["eps"]
+    variant = args.variant if args.workload3d else "hifde"
     dev = torch.device("cuda", 0)
     st = torch.cuda.Stream(device=dev)
     a = torch.from_numpy(w["a_stag"]).to(dev)
     b = torch.from_numpy(w["b"]).to(dev)
     f = torch.from_numpy(f_np).to(dev)
-    G = hif.factor(w["dim"], w["n"], a, b, w["eps"], precision=args.precision, stream=st, autotune=False)
+    G = hif.factor(w["dim"], w["n"], a, b, eps, precision=args.precision, stream=st, autotune=False,
+                   variant=variant)
     try:
         for _ in range(args.ncu_apply):
             G.apply(f)

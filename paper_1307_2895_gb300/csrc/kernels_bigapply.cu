@@ -7,11 +7,11 @@
 // multi-block root apply (kernels_root.cu):
 //
 //   up   [front] acc = T^T x_q            column strips, atomics into acc
-//        y = Linv (x_p - acc)             one warp per row of Linv
-//        x_q -= G y; x_p = S y            one warp per row of G (and of x_p)
+//        y = Linv (x_p - acc)             32-row x 256-column tiles, atomics into y
+//        x_q -= G y; x_p = S y            tiles of G, atomics into x_q
 //   down acc = G^T x_q                    column strips, atomics into acc
 //        z = Linv^T (x_p - acc)           column strips, atomics into z
-//        x_p = z; [front] x_q -= T z      one warp per row of T (and of x_p)
+//        x_p = z; [front] x_q -= T z      tiles of T, atomics into x_q
 //
 // (G, T: nq x np row-major; Linv: np x np lower, packed by rows; S: the
 // signs of D_p.)  Each block has 2 np kBigChunk elements of scratch at
@@ -54,6 +54,7 @@ __global__ void __launch_bounds__(256) k_big_tmv(const BigBlock* __restrict__ bb
 #pragma unroll
   for (int c = 0; c < R; ++c) acc[c] = T(0);
   if (j < np) {
+#pragma unroll 4
     for (int s = s0 + rg; s < s1; s += 4) {
       const T m = M[(int64_t)s * np + j];
       const T* xr = x + (int64_t)idq[s] * ldx;
@@ -71,66 +72,123 @@ __global__ void __launch_bounds__(256) k_big_tmv(const BigBlock* __restrict__ bb
   }
 }
 
-// up: y_i = sum_{t <= i} Linv[i][t] (x_p[t] - acc[t]), one warp per row.
+// Row-times-vector products over one tile of M: the CTA's 32 rows (warp w:
+// rows r0 + 8k + w, k < 4) and the columns [t0, t1).  acc[k][c] =
+// sum_t M[i][t] v[t][c], over t <= i when M is the packed lower Linv and over
+// all t when M is nq x np row-major, summed across the warp.  v (produced
+// element-wise by stage(t, c)) is staged in shared memory, read once by the
+// CTA, and each staged v[t] is loaded into registers once for the warp's four
+// rows.  The kernels below give each tile its own CTA (grid x: row blocks ×
+// column chunks) and add the partial sums atomically.
+constexpr int kRowsPerCta = 32;
+constexpr int kRowsPerWarp = kRowsPerCta / 8;
+constexpr int kRowChunk = 256;
+template <typename T, int R, typename Stage>
+__device__ __forceinline__ void staged_rows(T (*ws)[R], const T* __restrict__ M, bool lower, int np, int nrows,
+                                            int r0, int t0, int t1, Stage stage, T (&acc)[kRowsPerWarp][R]) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int e = threadIdx.x; e < (t1 - t0) * R; e += blockDim.x) ws[e / R][e % R] = stage(t0 + e / R, e % R);
+  const T* rowp[kRowsPerWarp];
+  int rlen[kRowsPerWarp];
+#pragma unroll
+  for (int k = 0; k < kRowsPerWarp; ++k) {
+    const int i = r0 + k * 8 + warp;
+    rowp[k] = M + (lower ? tri_b(i) : (int64_t)i * np);
+    rlen[k] = (i < nrows) ? (lower ? (i + 1 < t1 ? i + 1 : t1) : t1) : 0;
+#pragma unroll
+    for (int c = 0; c < R; ++c) acc[k][c] = T(0);
+  }
+  __syncthreads();
+  for (int t = t0 + lane; t < t1; t += 32) {
+    T v[R];
+#pragma unroll
+    for (int c = 0; c < R; ++c) v[c] = ws[t - t0][c];
+#pragma unroll
+    for (int k = 0; k < kRowsPerWarp; ++k) {
+      if (t < rlen[k]) {
+        const T m = rowp[k][t];
+#pragma unroll
+        for (int c = 0; c < R; ++c) acc[k][c] += m * v[c];
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kRowsPerWarp; ++k)
+#pragma unroll
+    for (int c = 0; c < R; ++c) acc[k][c] = warp_sum_b(acc[k][c]);
+}
+
+// up: y_i += sum_{t0 <= t < t1, t <= i} Linv[i][t] (x_p[t] - acc[t]) for one
+// tile (tiles wholly above the diagonal return at once).
 template <typename T, int R>
 __global__ void __launch_bounds__(256) k_big_lower(const BigBlock* __restrict__ bbs, const int* __restrict__ ipool,
                                                    const T* __restrict__ fac, const T* __restrict__ x, int nr,
                                                    int ldx, T* __restrict__ scratch) {
+  __shared__ T ws[kRowChunk][R];
   const BigBlock bb = bbs[blockIdx.y];
   const int np = bb.d.np;
-  const int i = (int)blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (i >= np) return;
+  const int nrb = (np + kRowsPerCta - 1) / kRowsPerCta, ncb = (np + kRowChunk - 1) / kRowChunk;
+  const int rb = (int)(blockIdx.x % nrb), cb = (int)(blockIdx.x / nrb);
+  if (cb >= ncb) return;
+  const int r0 = rb * kRowsPerCta, t0 = cb * kRowChunk;
+  const int rend = (r0 + kRowsPerCta < np) ? r0 + kRowsPerCta : np;
+  if (t0 >= rend) return;
+  const int t1 = (t0 + kRowChunk < rend) ? t0 + kRowChunk : rend;
   const int* idp = ipool + bb.d.ids;
-  const T* l = fac + bb.d.Linv + tri_b(i);
   const T* accv = scratch + bb.scr;
-  T acc[R];
+  T acc[kRowsPerWarp][R];
+  staged_rows<T, R>(ws, fac + bb.d.Linv, true, np, np, r0, t0, t1,
+                    [&](int t, int c) { return (c < nr ? x[(int64_t)idp[t] * ldx + c] : T(0)) - accv[(int64_t)t * R + c]; },
+                    acc);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
-  for (int c = 0; c < R; ++c) acc[c] = T(0);
-  for (int t = lane; t <= i; t += 32) {
-    const T lv = l[t];
-    const T* xr = x + (int64_t)idp[t] * ldx;
+  for (int k = 0; k < kRowsPerWarp; ++k) {
+    const int i = r0 + k * 8 + warp;
+    if (i >= np) continue;
+    T* y = scratch + bb.scr + (int64_t)np * kBigChunk + (int64_t)i * R;
 #pragma unroll
-    for (int c = 0; c < R; ++c) acc[c] += lv * ((c < nr ? xr[c] : T(0)) - accv[(int64_t)t * R + c]);
-  }
-  T* y = scratch + bb.scr + (int64_t)np * kBigChunk + (int64_t)i * R;
-#pragma unroll
-  for (int c = 0; c < R; ++c) {
-    const T s = warp_sum_b(acc[c]);
-    if (lane == c) y[c] = s;
+    for (int c = 0; c < R; ++c)
+      if (lane == c) atomicAdd(y + c, acc[k][c]);
   }
 }
 
-// up: x_q -= G y (fronts own x_q: stored; cells share it: atomics), and
-// x_p = S y; warp w takes row w of G and row w of x_p.
+// up: x_q -= G y over one tile of G, and (first column chunk) x_p = S y for
+// the tile's rows.
 template <typename T, int R>
 __global__ void __launch_bounds__(256) k_big_gy(const BigBlock* __restrict__ bbs, const int* __restrict__ ipool,
-                                                const T* __restrict__ fac, int is_front, T* __restrict__ x, int nr,
-                                                int ldx, const T* __restrict__ scratch) {
+                                                const T* __restrict__ fac, T* __restrict__ x, int nr, int ldx,
+                                                const T* __restrict__ scratch) {
+  __shared__ T ws[kRowChunk][R];
   const BigBlock bb = bbs[blockIdx.y];
   const int np = bb.d.np, nq = bb.d.nq;
-  const int w = (int)blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  const int mrows = np > nq ? np : nq;
+  const int nrb = (mrows + kRowsPerCta - 1) / kRowsPerCta, ncb = (np + kRowChunk - 1) / kRowChunk;
+  const int rb = (int)(blockIdx.x % nrb), cb = (int)(blockIdx.x / nrb);
+  if (cb >= ncb) return;
+  const int r0 = rb * kRowsPerCta, t0 = cb * kRowChunk;
+  const int t1 = (t0 + kRowChunk < np) ? t0 + kRowChunk : np;
   const int* idp = ipool + bb.d.ids;
   const int* idq = idp + np;
   const T* y = scratch + bb.scr + (int64_t)np * kBigChunk;
-  if (w < np && lane < nr) x[(int64_t)idp[w] * ldx + lane] = fac[bb.d.S + w] * y[(int64_t)w * R + lane];
-  if (w >= nq) return;
-  const T* g = fac + bb.d.G + (int64_t)w * np;
-  T acc[R];
-#pragma unroll
-  for (int c = 0; c < R; ++c) acc[c] = T(0);
-  for (int t = lane; t < np; t += 32) {
-    const T gv = g[t];
-#pragma unroll
-    for (int c = 0; c < R; ++c) acc[c] += gv * y[(int64_t)t * R + c];
-  }
-  T* xr = x + (int64_t)idq[w] * ldx;
-#pragma unroll
-  for (int c = 0; c < R; ++c) {
-    const T s = warp_sum_b(acc[c]);
-    if (lane == c && c < nr) {
-      if (is_front) xr[c] = xr[c] - s;
-      else atomicAdd(xr + c, -s);
+  if (cb == 0) {
+    for (int e = threadIdx.x; e < kRowsPerCta * R; e += blockDim.x) {
+      const int r = r0 + e / R, c = e % R;
+      if (r < np && c < nr) x[(int64_t)idp[r] * ldx + c] = fac[bb.d.S + r] * y[(int64_t)r * R + c];
     }
+  }
+  if (r0 >= nq) return;
+  T acc[kRowsPerWarp][R];
+  staged_rows<T, R>(ws, fac + bb.d.G, false, np, nq, r0, t0, t1, [&](int t, int c) { return y[(int64_t)t * R + c]; },
+                    acc);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < kRowsPerWarp; ++k) {
+    const int w = r0 + k * 8 + warp;
+    if (w >= nq) continue;
+    T* xr = x + (int64_t)idq[w] * ldx;
+#pragma unroll
+    for (int c = 0; c < R; ++c)
+      if (lane == c && c < nr) atomicAdd(xr + c, -acc[k][c]);
   }
 }
 
@@ -150,19 +208,26 @@ __global__ void __launch_bounds__(256) k_big_upper(const BigBlock* __restrict__ 
   const int* idp = ipool + bb.d.ids;
   const T* Linv = fac + bb.d.Linv;
   const T* accv = scratch + bb.scr;
+  __shared__ T wsu[256][R];   // w = x_p - acc on the block's 256 rows, read once
   const int jj = threadIdx.x & 63, rg = threadIdx.x >> 6;
   const int j = j0 + jj;
   const int i1 = (i0 + 256 < np) ? i0 + 256 : np;
+  for (int e = threadIdx.x; e < (i1 - i0) * R; e += blockDim.x) {
+    const int i = i0 + e / R, c = e % R;
+    wsu[e / R][c] = (c < nr ? x[(int64_t)idp[i] * ldx + c] : T(0)) - accv[(int64_t)i * R + c];
+  }
+  __syncthreads();
   T acc[R];
 #pragma unroll
   for (int c = 0; c < R; ++c) acc[c] = T(0);
   if (j < np) {
-    for (int i = i0 + rg; i < i1; i += 4) {
-      if (i < j) continue;
+    int i = i0 + rg;
+    if (i < j) i += ((j - i + 3) >> 2) << 2;   // the first row i >= j of this thread's rows
+#pragma unroll 4
+    for (; i < i1; i += 4) {
       const T lv = Linv[tri_b(i) + j];
-      const T* xr = x + (int64_t)idp[i] * ldx;
 #pragma unroll
-      for (int c = 0; c < R; ++c) acc[c] += lv * ((c < nr ? xr[c] : T(0)) - accv[(int64_t)i * R + c]);
+      for (int c = 0; c < R; ++c) acc[c] += lv * wsu[i - i0][c];
     }
   }
 #pragma unroll
@@ -175,33 +240,43 @@ __global__ void __launch_bounds__(256) k_big_upper(const BigBlock* __restrict__ 
   }
 }
 
-// down: x_p = z, and (fronts) x_q -= T z; warp w takes row w of x_p and of T.
+// down: x_p = z for the tile's rows (first column chunk), and (fronts)
+// x_q -= T z over one tile of T.
 template <typename T, int R>
 __global__ void __launch_bounds__(256) k_big_tz(const BigBlock* __restrict__ bbs, const int* __restrict__ ipool,
                                                 const T* __restrict__ fac, int is_front, T* __restrict__ x, int nr,
                                                 int ldx, const T* __restrict__ scratch) {
+  __shared__ T ws[kRowChunk][R];
   const BigBlock bb = bbs[blockIdx.y];
   const int np = bb.d.np, nq = bb.d.nq;
-  const int w = (int)blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  const int mrows = np > nq ? np : nq;
+  const int nrb = (mrows + kRowsPerCta - 1) / kRowsPerCta, ncb = (np + kRowChunk - 1) / kRowChunk;
+  const int rb = (int)(blockIdx.x % nrb), cb = (int)(blockIdx.x / nrb);
+  if (cb >= ncb) return;
+  const int r0 = rb * kRowsPerCta, t0 = cb * kRowChunk;
+  const int t1 = (t0 + kRowChunk < np) ? t0 + kRowChunk : np;
   const int* idp = ipool + bb.d.ids;
   const int* idq = idp + np;
   const T* z = scratch + bb.scr + (int64_t)np * kBigChunk;
-  if (w < np && lane < nr) x[(int64_t)idp[w] * ldx + lane] = z[(int64_t)w * R + lane];
-  if (!is_front || w >= nq) return;
-  const T* tr = fac + bb.d.T + (int64_t)w * np;
-  T acc[R];
-#pragma unroll
-  for (int c = 0; c < R; ++c) acc[c] = T(0);
-  for (int t = lane; t < np; t += 32) {
-    const T tv = tr[t];
-#pragma unroll
-    for (int c = 0; c < R; ++c) acc[c] += tv * z[(int64_t)t * R + c];
+  if (cb == 0) {
+    for (int e = threadIdx.x; e < kRowsPerCta * R; e += blockDim.x) {
+      const int r = r0 + e / R, c = e % R;
+      if (r < np && c < nr) x[(int64_t)idp[r] * ldx + c] = z[(int64_t)r * R + c];
+    }
   }
-  T* xr = x + (int64_t)idq[w] * ldx;
+  if (!is_front || r0 >= nq) return;
+  T acc[kRowsPerWarp][R];
+  staged_rows<T, R>(ws, fac + bb.d.T, false, np, nq, r0, t0, t1, [&](int t, int c) { return z[(int64_t)t * R + c]; },
+                    acc);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
-  for (int c = 0; c < R; ++c) {
-    const T s = warp_sum_b(acc[c]);
-    if (lane == c && c < nr) xr[c] = xr[c] - s;
+  for (int k = 0; k < kRowsPerWarp; ++k) {
+    const int w = r0 + k * 8 + warp;
+    if (w >= nq) continue;
+    T* xr = x + (int64_t)idq[w] * ldx;
+#pragma unroll
+    for (int c = 0; c < R; ++c)
+      if (lane == c && c < nr) atomicAdd(xr + c, -acc[k][c]);
   }
 }
 
@@ -211,17 +286,18 @@ static int big_chunk(int dir, const BigBlock* bbs, int nbig, int max_np, int max
   int nl = 0;
   cudaMemsetAsync(scratch, 0, sizeof(T) * (size_t)scratch_elems, st);
   const unsigned strips = (unsigned)((max_np + 63) / 64);
-  const unsigned rows8 = (unsigned)((max_np + 7) / 8);
+  const unsigned cchunks = (unsigned)((max_np + kRowChunk - 1) / kRowChunk);
+  const unsigned tiles_p = (unsigned)((max_np + kRowsPerCta - 1) / kRowsPerCta) * cchunks;
   const int mx = max_np > max_nq ? max_np : max_nq;
-  const unsigned both8 = (unsigned)((mx + 7) / 8);
+  const unsigned tiles_pq = (unsigned)((mx + kRowsPerCta - 1) / kRowsPerCta) * cchunks;
   if (dir == 0) {
     if (is_front && max_nq > 0) {
       const unsigned gx = strips * (unsigned)((max_nq + 255) / 256);
       k_big_tmv<T, R><<<dim3(gx, nbig), 256, 0, st>>>(bbs, ipool, fac, 1, x, nr, ldx, scratch);
       ++nl;
     }
-    k_big_lower<T, R><<<dim3(rows8, nbig), 256, 0, st>>>(bbs, ipool, fac, x, nr, ldx, scratch);
-    k_big_gy<T, R><<<dim3(both8, nbig), 256, 0, st>>>(bbs, ipool, fac, is_front, x, nr, ldx, scratch);
+    k_big_lower<T, R><<<dim3(tiles_p, nbig), 256, 0, st>>>(bbs, ipool, fac, x, nr, ldx, scratch);
+    k_big_gy<T, R><<<dim3(tiles_pq, nbig), 256, 0, st>>>(bbs, ipool, fac, x, nr, ldx, scratch);
     nl += 2;
   } else {
     if (max_nq > 0) {
@@ -231,7 +307,7 @@ static int big_chunk(int dir, const BigBlock* bbs, int nbig, int max_np, int max
     }
     const unsigned gx = strips * (unsigned)((max_np + 255) / 256);
     k_big_upper<T, R><<<dim3(gx, nbig), 256, 0, st>>>(bbs, ipool, fac, x, nr, ldx, scratch);
-    k_big_tz<T, R><<<dim3(both8, nbig), 256, 0, st>>>(bbs, ipool, fac, is_front, x, nr, ldx, scratch);
+    k_big_tz<T, R><<<dim3(tiles_pq, nbig), 256, 0, st>>>(bbs, ipool, fac, is_front, x, nr, ldx, scratch);
     nl += 2;
   }
   note_launches(nl);
