@@ -19,6 +19,12 @@ What each function follows:
   2D, and in 3D with face skeletonization, Section 4.2), with the accelerated
   compression of Section 4.3 (fronts hold only the strict interior of an edge
   or face; the ID compresses ``(A_{l+1/2})_{c^N, c}``).
+* :func:`svd_skel`, :func:`skeletonize_svd` -- Section 4.4: the SVD
+  ``A_{N,c} = U Sigma V^T`` in place of the ID, ``Q_c = diag(V, I)``, the
+  directions with singular values ``<= eps sigma_1`` eliminated (Lemma 2.1 on
+  ``B_{p1 p1}`` of ``V^T A_cc V``) and their interactions with ``N``
+  dropped; the kept directions live on in the slots of the first ``k`` DOFs
+  of ``c`` with interactions ``A_{N,c} V_2`` (``factor(..., skel="svd")``).
 * :func:`factor3x` -- the 3D variant with edge skeletonization (Section 4.5,
   Algorithm 4.2): cells built algebraically from Voronoi cells about the cell
   centers, faces and edges as Voronoi cells about the face and edge centers.
@@ -43,9 +49,23 @@ Readings where the paper leaves a choice:
   failure; an empty or zero block has rank 0;
 * all fronts of one fractional level compress blocks of ``A_{l+1/2}`` (the
   matrix before any front of that level is skeletonized);
-* corners (2D) and cell edges / corners (3D) belong to no front (Section 4.3).
+* corners (2D) and cell edges / corners (3D) belong to no front (Section 4.3);
+* SVD skeletonization (Section 4.4): rank = number of singular values
+  ``> eps sigma_1``; V's columns in descending singular-value order; the
+  ``k`` kept directions take the slots of the first ``k`` DOFs of ``c``
+  (ascending ids), the others those of the rest; when nothing or everything
+  is dropped (``k = 0`` or ``k = |c|``) no rotation is made (``V = I``: the
+  factorization does not depend on the basis of a block that is wholly kept
+  or wholly eliminated).  Every front of a level takes its SVD from
+  ``A_{l+1/2}`` and the rotations of all fronts apply to it together: the
+  rotations of different fronts act on disjoint index sets and commute, and
+  each front's eliminated directions couple only to its own kept ones.  (The
+  paper's front loop is sequential; with the ID the two orders agree
+  exactly, with the SVD they differ by the truncated interactions.)
 
-Parity status: MF, the stencil, Lemma 2.1, Lemma 2.4, the ID, F and F^-1 are
+Parity status: MF, the stencil, Lemma 2.1, Lemma 2.4, the ID, the SVD
+skeletonization (exact F = A when nothing is truncated, V orthogonal, the
+truncated interactions within eps sigma_1, ||A - F|| of order eps), F and F^-1 are
 pinned by the ``-m "not gpu"`` tests (dense LU, closed forms, exact low rank,
 LAPACK's pivoted QR, invariants); the power estimates by the exact 2-norms of
 dense A - F, A and I - A F^-1 on small grids; PCG by scipy's preconditioned
@@ -367,8 +387,12 @@ def _front_as_cell(fr: FrontRecord) -> CellRecord:
 
 
 def apply_U_T(fr: FrontRecord, x: np.ndarray) -> None:
-    """x <- U_c^T x = S_r^T Q_c^T x;  Q_c^T: x_r <- x_r - T^T x_s."""
+    """x <- U_c^T x = S_r^T Q_c^T x;  Q_c^T: x_r <- x_r - T^T x_s (ID), x_c <- V^T x_c (SVD)."""
     if len(fr.rd) == 0:
+        return
+    if isinstance(fr, SVDFrontRecord):
+        _rotate(fr, x, True)
+        apply_S_T(_svd_as_cell(fr), x)
         return
     if len(fr.sk):
         x[fr.rd] -= fr.T.T @ x[fr.sk]
@@ -376,8 +400,12 @@ def apply_U_T(fr: FrontRecord, x: np.ndarray) -> None:
 
 
 def apply_U(fr: FrontRecord, x: np.ndarray) -> None:
-    """x <- U_c x = Q_c S_r x;  Q_c: x_s <- x_s - T x_r."""
+    """x <- U_c x = Q_c S_r x;  Q_c: x_s <- x_s - T x_r (ID), x_c <- V x_c (SVD)."""
     if len(fr.rd) == 0:
+        return
+    if isinstance(fr, SVDFrontRecord):
+        apply_S(_svd_as_cell(fr), x)
+        _rotate(fr, x, False)
         return
     apply_S(_front_as_cell(fr), x)
     if len(fr.sk):
@@ -385,8 +413,13 @@ def apply_U(fr: FrontRecord, x: np.ndarray) -> None:
 
 
 def apply_U_inv(fr: FrontRecord, x: np.ndarray) -> None:
-    """x <- U_c^{-1} x = S_r^{-1} Q_c^{-1} x;  Q_c^{-1}: x_s <- x_s + T x_r."""
+    """x <- U_c^{-1} x = S_r^{-1} Q_c^{-1} x;  Q_c^{-1}: x_s <- x_s + T x_r (ID),
+    x_c <- V^T x_c (SVD: Q_c^{-1} = Q_c^T)."""
     if len(fr.rd) == 0:
+        return
+    if isinstance(fr, SVDFrontRecord):
+        _rotate(fr, x, True)
+        apply_S_inv(_svd_as_cell(fr), x)
         return
     if len(fr.sk):
         x[fr.sk] += fr.T @ x[fr.rd]
@@ -394,12 +427,96 @@ def apply_U_inv(fr: FrontRecord, x: np.ndarray) -> None:
 
 
 def apply_U_inv_T(fr: FrontRecord, x: np.ndarray) -> None:
-    """x <- U_c^{-T} x = Q_c^{-T} S_r^{-T} x;  Q_c^{-T}: x_r <- x_r + T^T x_s."""
+    """x <- U_c^{-T} x = Q_c^{-T} S_r^{-T} x;  Q_c^{-T}: x_r <- x_r + T^T x_s (ID),
+    x_c <- V x_c (SVD)."""
     if len(fr.rd) == 0:
+        return
+    if isinstance(fr, SVDFrontRecord):
+        apply_S_inv_T(_svd_as_cell(fr), x)
+        _rotate(fr, x, False)
         return
     apply_S_inv_T(_front_as_cell(fr), x)
     if len(fr.sk):
         x[fr.rd] += fr.T.T @ x[fr.sk]
+
+
+# --------------------------------------------------------------------------
+# Section 4.4: skeletonization by the SVD
+# --------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class SVDResult:
+    V: np.ndarray         # |c| x |c| orthogonal, columns by descending singular value
+    sigma: np.ndarray     # singular values, descending (min(m, |c|) of them)
+    k: int                # number of singular values > eps sigma_1
+    near_threshold: bool  # a ratio sigma_i / sigma_1 within 1e-8 (relative) of eps
+
+
+def svd_skel(M: np.ndarray, eps: float) -> SVDResult:
+    """M = U Sigma V^T (LAPACK's SVD, the full V); k = #{sigma_i > eps sigma_1};
+    an empty or zero block has rank 0."""
+    m, n = M.shape
+    if m == 0 or n == 0:
+        return SVDResult(np.eye(n), np.zeros(0), 0, False)
+    _, sig, Vt = np.linalg.svd(M, full_matrices=True)
+    if sig[0] == 0.0:
+        return SVDResult(np.eye(n), sig, 0, False)
+    ratio = sig / sig[0]
+    k = int(np.count_nonzero(ratio > eps))
+    near = bool(np.any(np.abs(ratio - eps) <= 1e-8 * eps))
+    return SVDResult(Vt.T.copy(), sig, k, near)
+
+
+@dataclasses.dataclass
+class SVDFrontRecord:
+    """U_c = Q_c S_p1 with Q_c = diag(V, I) (Section 4.4's lemma) and S_p1 the
+    elimination (Lemma 2.1) of the dropped directions p1 against the kept
+    ones p2 only.  Slots: p2 = c[:k] (``sk``), p1 = c[k:] (``rd``); V = None
+    when no rotation is made."""
+    c: np.ndarray
+    sk: np.ndarray
+    rd: np.ndarray
+    V: np.ndarray      # |c| x |c| or None
+    L: np.ndarray      # factor of B_p1p1 (B = V^T A_cc V)
+    Bsr: np.ndarray    # B_p2p1
+    near_threshold: bool = False
+    sgn: np.ndarray = None
+
+
+def skeletonize_svd(A: ActiveMatrix, c: List[int], sv: SVDResult) -> SVDFrontRecord:
+    """Q_c^T A Q_c with the interactions of the dropped directions truncated,
+    then Lemma 2.1 on them (their only remaining neighbours are the kept
+    directions): B~_p2p2 = B_p2p2 - B_p2p1 B_p1p1^-1 B_p1p2."""
+    c_arr = np.array(c, dtype=np.int64)
+    nc, k = len(c), sv.k
+    V = sv.V if 0 < k < nc else None
+    if V is not None:
+        nb = A.neighbors(c)
+        if nb:
+            X = A.block(nb, c) @ V                              # A_{N,c} V
+            A.set_block(nb, c, X)
+            A.set_block(c, nb, X.T)
+        A.set_block(c, c, V.T @ A.block(c, c) @ V)
+    sk, rd = c_arr[:k], c_arr[k:]
+    sk_l, rd_l = sk.tolist(), rd.tolist()
+    B_ss = A.block(sk_l, sk_l)
+    B_sr = A.block(sk_l, rd_l)
+    B_rr = A.block(rd_l, rd_l)
+    L, sgn = factor_block(B_rr) if len(rd_l) else (np.zeros((0, 0)), None)
+    if len(rd_l) and len(sk_l):
+        Y = sla.solve_triangular(L, B_sr.T, lower=True)
+        A.set_block(sk_l, sk_l, B_ss - Y.T @ (Y if sgn is None else sgn[:, None] * Y))
+    A.remove(rd_l)
+    return SVDFrontRecord(c_arr, sk, rd, V, L, B_sr, sv.near_threshold, sgn)
+
+
+def _rotate(fr: SVDFrontRecord, x: np.ndarray, transpose: bool) -> None:
+    if fr.V is not None:
+        x[fr.c] = (fr.V.T if transpose else fr.V) @ x[fr.c]
+
+
+def _svd_as_cell(fr: SVDFrontRecord) -> CellRecord:
+    return CellRecord(fr.rd, fr.sk, fr.L, fr.Bsr, fr.sgn)
 
 
 # --------------------------------------------------------------------------
@@ -488,7 +605,7 @@ def _front_key(dim, x, on_sep, seps):
 
 
 def factor(A_csr, dim: int, n: int, eps: float, leaf: int = 8,
-           skip_levels: int = 0, sketch=None, sketch_power: int = 0) -> Factor:
+           skip_levels: int = 0, sketch=None, sketch_power: int = 0, skel: str = "id") -> Factor:
     """Algorithm 4.1 (HIF-DE; ``eps > 0``) or Algorithm 3.1 (MF; ``eps == 0``).
 
     Level l: eliminate the active DOFs strictly inside each level-l cell
@@ -505,8 +622,15 @@ def factor(A_csr, dim: int, n: int, eps: float, leaf: int = 8,
     sketched ID that fails :func:`oracle.learned.randomized_id`'s check falls
     back to the pivoted-QR ID of the block itself (``sketch_power`` power
     iterations on the sketch).  The counts of accepted and rejected sketches
-    are kept on the result."""
+    are kept on the result.
+
+    ``skel="svd"`` skeletonizes the fronts by the SVD (Section 4.4,
+    :func:`skeletonize_svd`) instead of the ID."""
     from .stencil import coords as _coords
+    if skel not in ("id", "svd"):
+        raise ValueError(f"skel must be 'id' or 'svd', not {skel!r}")
+    if skel == "svd" and sketch is not None:
+        raise ValueError("the randomized ID and the SVD skeletonization are exclusive")
     A = ActiveMatrix(A_csr)
     X = _coords(dim, n)
     L = tree_levels(n, leaf)
@@ -548,6 +672,9 @@ def factor(A_csr, dim: int, n: int, eps: float, leaf: int = 8,
                 c = sorted(groups[key])
                 nb = A.neighbors(c)
                 M = A.block(nb, c)
+                if skel == "svd":
+                    ids.append(svd_skel(M, eps))
+                    continue
                 Phi = sketch(ell, c, nb) if sketch is not None else None
                 idr = None
                 if Phi is not None:
@@ -564,7 +691,10 @@ def factor(A_csr, dim: int, n: int, eps: float, leaf: int = 8,
                         idr = dataclasses.replace(idr, near_threshold=True)
                 ids.append(idr)
             for key, idr in zip(keys, ids):
-                fronts.append(skeletonize(A, sorted(groups[key]), idr))
+                if skel == "svd":
+                    fronts.append(skeletonize_svd(A, sorted(groups[key]), idr))
+                else:
+                    fronts.append(skeletonize(A, sorted(groups[key]), idr))
         levels.append(Level(ell, cells, fronts, keys))
     root = np.array(A.active(), dtype=np.int64)
     D = A.block(root.tolist(), root.tolist())
