@@ -106,6 +106,20 @@ typedef struct hif_grid {
  * front by the rank MLP (LEARNED, opts.rank_model required). */
 enum { HIF_ID_QR = 0, HIF_ID_RAND = 1, HIF_ID_LEARNED = 2 };
 
+/* Skeletonization of the fronts (hif_opts.skel).  ID: the interpolative
+ * decomposition of Lemma 2.2 (id_mode).  SVD: Section 4.4's optimal low-rank
+ * approximation: A_{N,c} = U Sigma V^T, Q_c = diag(V, I); the directions
+ * with sigma <= eps sigma_1 are eliminated (Lemma 2.1 against the kept
+ * directions) with their interactions dropped, and the k kept directions
+ * take the slots of the first k DOFs of c (ascending ids) with interactions
+ * A_{N,c} V_2, written over the cells' update matrices.  All fronts of a
+ * level take their SVD from the matrix before the level and rotate together
+ * (their rotations commute); no rotation when k = 0 or k = |c|.  HIFDE only
+ * (not HIFDE3X: the rotated DOFs have no single position), the FP64 and
+ * FP32_APPLY precisions, HIF_ID_QR; every front runs the one-block kernel
+ * (one-sided Jacobi SVD), whatever its size. */
+enum { HIF_SKEL_ID = 0, HIF_SKEL_SVD = 1 };
+
 typedef struct hif_opts {
   int precision;        /* HIF_PREC_*                                           */
   int skip_levels;      /* fractional levels l + 1/2 skipped for l < skip_levels
@@ -166,6 +180,8 @@ typedef struct hif_opts {
                            one block each; 0 -> 2^20, < 0 -> never.  Not in
                            the deterministic mode.  Same result up to
                            rounding order.                                   */
+  int skel;             /* HIF_SKEL_*: the fronts' low-rank approximation;
+                           0 -> HIF_SKEL_ID                                  */
 } hif_opts;
 
 typedef struct hif_handle hif_handle;

@@ -29,7 +29,7 @@ void split_big(hif_handle* h, SweepLevel& sw, const std::vector<ApplyDesc>& ad, 
   int64_t scr = 0;
   for (const ApplyDesc& a : ad) {
     const int64_t elems = (int64_t)a.np * ((int64_t)a.np + 2 * (int64_t)a.nq);
-    if (a.np > 0 && elems >= h->big_apply) {
+    if (a.np > 0 && a.V < 0 && elems >= h->big_apply) {   // (SVD fronts: one block each)
       big.push_back(BigBlock{a, scr});
       scr += 2 * (int64_t)a.np * kBigChunk;
       bnp = std::max(bnp, a.np);

@@ -9,6 +9,8 @@
 //   device: one launch for every front: ID (Lemma 2.2) + Lemma 2.4
 //   host  : read back the ranks and skeletons, drop the redundant DOFs
 // then the root D = A_L (a level-L cell without boundary, always FP64).
+#include <map>
+
 #include "hif_host.h"
 
 namespace hif {
@@ -813,9 +815,36 @@ struct Factorizer {
       }
     }
     DevBuf d_sel, d_big, bstate, m2part, d_td;
+    DevBuf d_ccell, d_cptr, d_clist;
+    if (h->skel == HIF_SKEL_SVD) big.clear();   // every front by the one-block SVD kernel
     const int nbig = (int)big.size();
     const int nm = nbig ? bigfront_colmax_blocks(big_nc) : 0;
-    if (big.empty()) {
+    if (h->skel == HIF_SKEL_SVD) {
+      // the fronts' SVDs from the update matrices as they stand, then each
+      // bordering cell's update matrix rotated by its fronts
+      std::map<int, std::vector<int>> by_cell;   // cell -> (front, side) pairs
+      for (int f = 0; f < nf; ++f) {
+        const HostFront& F = (*fr)[f];
+        for (int t = 0; t < fd[f].nc; ++t)
+          if (F.pos1[t] < 0 || F.pos2[t] < 0)
+            throw HifError(HIF_ERR_ARG, "HIF_SKEL_SVD: a front without two bordering cells");
+        by_cell[fd[f].P1].insert(by_cell[fd[f].P1].end(), {f, 1});
+        by_cell[fd[f].P2].insert(by_cell[fd[f].P2].end(), {f, 2});
+      }
+      std::vector<int> ccell, cptr{0}, clist;
+      for (const auto& kv : by_cell) {
+        ccell.push_back(kv.first);
+        clist.insert(clist.end(), kv.second.begin(), kv.second.end());
+        cptr.push_back((int)(clist.size() / 2));
+      }
+      upload(d_ccell, ccell, st);
+      upload(d_cptr, cptr, st);
+      upload(d_clist, clist, st);
+      launch_front_svd<T>(d_fd, nf, d_cdesc, d_ip, obuf.as<int>(), fwork.as<T>(), sw.fac.as<T>(), cwork.as<T>(),
+                          h->eps, status.as<int>(), max_nc, tau, st);
+      launch_svd_rotate<T>(d_ccell.as<int>(), d_cptr.as<int>(), d_clist.as<int>(), (int)ccell.size(), d_fd,
+                           d_cdesc, d_ip, obuf.as<int>(), fwork.as<T>(), sw.fac.as<T>(), cwork.as<T>(), max_nc, st);
+    } else if (big.empty()) {
       launch_front<T>(d_fd, nf, d_cdesc, d_ip, obuf.as<int>(), fwork.as<T>(), sw.fac.as<T>(), cwork.as<T>(), h->eps,
                       status.as<int>(), max_nc, max_nN, tau, sketch.as<int>(), ss, nullptr, st);
     } else {
@@ -965,10 +994,12 @@ struct Factorizer {
       a.L = d.fac + front_fac_L(d.nc);
       a.S = d.fac + front_fac_S(d.nc);
       a.cslot = 0;
+      const bool rot = h->skel == HIF_SKEL_SVD && k > 0 && nR > 0;   // the SVD's rotation V (T's slot)
+      a.V = rot ? a.T : -1;
       sw.max_np = std::max(sw.max_np, nR);
       sw.max_nq = std::max(sw.max_nq, k);
       if (nR > 0) {
-        sw.fac_elems += 0.5 * nR * (nR + 1.0) + 2.0 * k * nR;
+        sw.fac_elems += 0.5 * nR * (nR + 1.0) + (rot ? 1.0 * k * nR + (double)d.nc * d.nc : 2.0 * k * nR);
         sw.vec_rows += nR + k;
       }
       h->n_fronts += 1;
@@ -1055,6 +1086,14 @@ int hif_factor(const hif_grid* grid, const double* a_stag, const double* b, cons
     if (opts) h->sketch_power = opts->sketch_power;
     if (opts) h->deterministic = opts->deterministic != 0;
     if (opts && opts->big_apply != 0) h->big_apply = opts->big_apply < 0 ? 0 : opts->big_apply;
+    h->skel = opts ? opts->skel : HIF_SKEL_ID;
+    if (h->skel != HIF_SKEL_ID && h->skel != HIF_SKEL_SVD) throw HifError(HIF_ERR_ARG, "unknown skel");
+    if (h->skel == HIF_SKEL_SVD) {
+      if (grid->variant == HIF_VARIANT_HIFDE3X)
+        throw HifError(HIF_ERR_ARG, "HIF_SKEL_SVD: not with HIFDE3X (the rotated DOFs have no single position)");
+      if (prec == HIF_PREC_MIXED) throw HifError(HIF_ERR_ARG, "HIF_SKEL_SVD: FP64 or FP32_APPLY precision only");
+      if (h->id_mode != HIF_ID_QR) throw HifError(HIF_ERR_ARG, "HIF_SKEL_SVD excludes the randomized ID");
+    }
     if (h->id_mode == HIF_ID_LEARNED && !(opts && opts->rank_model))
       throw HifError(HIF_ERR_ARG, "HIF_ID_LEARNED needs opts.rank_model");
     h->st = opts ? (cudaStream_t)opts->stream : nullptr;

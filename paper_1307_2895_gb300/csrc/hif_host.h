@@ -283,6 +283,7 @@ struct hif_handle {
   int edge_start = 1;   // HIFDE3X: first level whose edges are skeletonized
   int sketch_power = 0; // power iterations on the randomized ID's sketch
   bool deterministic = false;   // sweeps and root apply without floating-point atomics
+  int skel = HIF_SKEL_ID;       // fronts skeletonized by the ID or by the SVD (Section 4.4)
   int64_t big_apply = int64_t(1) << 20;   // F^-1: blocks with np (np + 2 nq) >= this many elements by
                                           // many thread blocks (0: none)
   DevBuf big_scratch;           // their scratch (the largest level's, doubles)

@@ -52,7 +52,12 @@ struct TDesc {
 };
 
 // Block of the factor as the apply sweeps see it.  Cell: p = I, q = B.
-// Front: p = redundant set r, q = skeleton set s, with T (nq x np).
+// Front: p = redundant set r, q = skeleton set s, with T (nq x np); or, for
+// a front skeletonized by the SVD (Section 4.4), p = the dropped directions
+// and q = the kept ones in the slots of the front's DOFs (q first), with the
+// rotation V ((nq + np) x (nq + np), row-major, rows by slot, columns by
+// direction) in the place of T: x_c <- V^T x_c before the elimination of
+// the up sweep, x_c <- V x_c after that of the down sweep.
 // Linv and L are lower triangular, packed by rows (entry (i, t), t <= i, at
 // i (i + 1) / 2 + t); G and T are row-major nq x np.  Every region starts on
 // a 16-byte boundary (sizes rounded up to 4 elements).
@@ -67,6 +72,7 @@ struct ApplyDesc {
   int64_t S;           // factor pool offset of the signs (np values)
   int64_t cslot;       // cells: row of x_q's first contribution in the level's
                        // contribution buffer (the deterministic scatter)
+  int64_t V = -1;      // SVD fronts: factor pool offset of V (-1: none)
 };
 
 // Gaussian stream of the randomized ID (Section 4.3) at one fractional level

@@ -64,6 +64,19 @@ void launch_front(const FrontDesc* fronts, int nfronts, const CellDesc* cells, c
                   T* fac, T* cwork, double eps, int* status, int max_nc, int max_nN, double tau,
                   const int* sketch, SketchStream ss, const int* sel, cudaStream_t st);
 
+// skeletonization by the SVD (kernels_svdfront.cu, Section 4.4): every front
+// of a level (one block each), then the rotation of the update matrices of
+// the cells ccell[0..ncells) by their fronts (cptr / clist: (front, side)
+// pairs per cell, side 1 = P1, 2 = P2)
+template <typename T>
+void launch_front_svd(const FrontDesc* fronts, int nfronts, const CellDesc* cells, const int* ipool, int* obuf,
+                      T* fwork, T* fac, const T* cwork, double eps, int* status, int max_nc, double tau,
+                      cudaStream_t st);
+template <typename T>
+void launch_svd_rotate(const int* ccell, const int* cptr, const int* clist, int ncells, const FrontDesc* fronts,
+                       const CellDesc* cells, const int* ipool, const int* obuf, const T* fwork, const T* fac,
+                       T* cwork, int max_nc, cudaStream_t st);
+
 // skeletonization of large fronts (kernels_bigfront.cu): the ID (writes T
 // and the front's outputs; h_nc / h_nN: host copies of the fronts' sizes, for
 // the block groups of the multi-block pivoted QR, used when coop_ok), then,

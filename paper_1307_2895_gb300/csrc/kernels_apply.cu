@@ -136,6 +136,30 @@ struct SweepSmem {
 // group of CG consecutive right-hand sides (register accumulators).
 template <int R> struct ColGroup { static constexpr int CG = R < 2 ? R : 2; static constexpr int NG = R / CG; };
 
+// The rotation of a front skeletonized by the SVD on its slots, x_c = [x_q;
+// x_p] (R columns): oq / op <- the q / p rows of V^T x_c (transpose) or of
+// V x_c; V is (nq + np) x (nq + np), row-major, read from global memory.
+// The outputs are distinct from the inputs; the caller synchronizes.
+template <typename T, int R>
+__device__ void svd_rotate(const T* __restrict__ V, int np, int nq, const T* xq, const T* xp, T* oq, T* op,
+                           bool transpose) {
+  const int nc = np + nq;
+  for (int e = threadIdx.x; e < nc * R; e += blockDim.x) {
+    const int j = e / R, r = e % R;
+    T acc = T(0);
+    if (transpose) {
+      for (int t = 0; t < nq; ++t) acc += V[(int64_t)t * nc + j] * xq[t * R + r];
+      for (int t = 0; t < np; ++t) acc += V[(int64_t)(nq + t) * nc + j] * xp[t * R + r];
+    } else {
+      const T* v = V + (int64_t)j * nc;
+      for (int t = 0; t < nq; ++t) acc += v[t] * xq[t * R + r];
+      for (int t = 0; t < np; ++t) acc += v[nq + t] * xp[t * R + r];
+    }
+    if (j < nq) oq[j * R + r] = acc;
+    else op[(j - nq) * R + r] = acc;
+  }
+}
+
 template <typename T, int R>
 __device__ __forceinline__ void stage_factor(SweepSmem<T, R>& sm, BulkStage& bs, const T*& Linv, const T*& G,
                                              const T*& Tm, int np, int nq, bool front) {
@@ -188,7 +212,14 @@ __device__ void sweep_up_block(const ApplyDesc& bd, const int* __restrict__ ipoo
   // every thread leaves if one thread's wait for the factor copy ran out
   if (!__syncthreads_and(!staged || bs.wait(err))) return;
   if (!go) return;
-  if (is_front && nq > 0) {                      // x_p -= T^T x_q
+  if (is_front && bd.V >= 0) {                   // SVD front: x_c <- V^T x_c
+    T* tq = xq + pad4((int64_t)nq * R);
+    svd_rotate<T, R>(fac + bd.V, np, nq, xq, xp, tq, yp, true);
+    __syncthreads();
+    for (int e = threadIdx.x; e < np * R; e += blockDim.x) xp[e] = yp[e];
+    for (int e = threadIdx.x; e < nq * R; e += blockDim.x) xq[e] = tq[e];
+    __syncthreads();
+  } else if (is_front && nq > 0) {               // x_p -= T^T x_q
     for (int e = threadIdx.x; e < np * NG; e += blockDim.x) {
       const int i = e / NG, c0 = (e % NG) * CG;
       T acc[CG] = {};
@@ -282,6 +313,7 @@ __device__ void sweep_down_block(const ApplyDesc& bd, const int* __restrict__ ip
   T* xp = sm.xp;
   T* zp = sm.yp;
   T* xq = sm.xq;
+  const bool svd = is_front && bd.V >= 0;
   if (go) {
     gather<T, R, L2>(xp, x, idp, np, nr, ldx);
     gather<T, R, L2>(xq, x, idq, nq, nr, ldx);
@@ -318,10 +350,19 @@ __device__ void sweep_down_block(const ApplyDesc& bd, const int* __restrict__ ip
 #pragma unroll
     for (int c = 0; c < CG; ++c) {
       zp[i * R + c0 + c] = acc[c];
-      if (c0 + c < nr) x[(int64_t)idp[i] * ldx + c0 + c] = acc[c];
+      if (!svd && c0 + c < nr) x[(int64_t)idp[i] * ldx + c0 + c] = acc[c];
     }
   }
-  if (is_front && nq > 0) {                      // x_q -= T z
+  if (svd) {                                     // SVD front: x_c <- V x_c
+    __syncthreads();
+    T* tq = xq + pad4((int64_t)nq * R);
+    svd_rotate<T, R>(fac + bd.V, np, nq, xq, zp, tq, xp, false);
+    __syncthreads();
+    for (int e = threadIdx.x; e < nq * R; e += blockDim.x)
+      if (e % R < nr) x[(int64_t)idq[e / R] * ldx + e % R] = tq[e];
+    for (int e = threadIdx.x; e < np * R; e += blockDim.x)
+      if (e % R < nr) x[(int64_t)idp[e / R] * ldx + e % R] = xp[e];
+  } else if (is_front && nq > 0) {               // x_q -= T z
     __syncthreads();
     for (int e = threadIdx.x; e < nq * NG; e += blockDim.x) {
       const int s2 = e / NG, c0 = (e % NG) * CG;
@@ -418,7 +459,17 @@ __global__ void k_fwd_up(const ApplyDesc* __restrict__ blocks, const int* __rest
   gather<T, R>(xp, x, idp, np, nr, ldx);
   gather<T, R>(xq, x, idq, nq, nr, ldx);
   __syncthreads();
-  if (is_front && nq > 0) {       // x_q += T x_p
+  if (is_front && bd.V >= 0) {    // SVD front: x_c <- V^T x_c (Q_c^-1 = Q_c^T)
+    T* tp = tq + pad4((int64_t)nq * R);
+    svd_rotate<T, R>(fac + bd.V, np, nq, xq, xp, tq, tp, true);
+    __syncthreads();
+    for (int e = threadIdx.x; e < nq * R; e += blockDim.x) {
+      xq[e] = tq[e];
+      if (e % R < nr) x[(int64_t)idq[e / R] * ldx + e % R] = tq[e];
+    }
+    for (int e = threadIdx.x; e < np * R; e += blockDim.x) xp[e] = tp[e];
+    __syncthreads();
+  } else if (is_front && nq > 0) {       // x_q += T x_p
     const T* Tm = fac + bd.T;
     for (int e = threadIdx.x; e < nq * R; e += blockDim.x) {
       const int s2 = e / R, r = e % R;
@@ -454,6 +505,9 @@ __global__ void k_fwd_down(const ApplyDesc* __restrict__ blocks, const int* __re
   const int* idq = idp + np;
   T* xp = reinterpret_cast<T*>(smem_raw);
   T* xq = xp + pad4((int64_t)np * R);
+  T* oq = xq + pad4((int64_t)nq * R);   // SVD fronts: the rotated q rows
+  T* tp = oq + pad4((int64_t)nq * R);   // SVD fronts: L x_p before the rotation
+  const bool svd = is_front && bd.V >= 0;
   const T* Lp = fac + bd.L;
   const T* G = fac + bd.G;
   gather<T, R>(xp, x, idp, np, nr, ldx);
@@ -468,7 +522,7 @@ __global__ void k_fwd_down(const ApplyDesc* __restrict__ blocks, const int* __re
     for (int c = 0; c < np; ++c) acc += g[c] * xp[c * R + r];
     if (is_front) {
       xq[e] += acc;
-      if (r < nr) x[(int64_t)idq[s2] * ldx + r] = xq[e];
+      if (!svd && r < nr) x[(int64_t)idq[s2] * ldx + r] = xq[e];
     } else if (contrib) {
       contrib[(bd.cslot + s2) * R + r] = acc;
     } else if (r < nr) {
@@ -481,11 +535,24 @@ __global__ void k_fwd_down(const ApplyDesc* __restrict__ blocks, const int* __re
     const T* l = Lp + tri(i);
     T acc = T(0);
     for (int t = 0; t <= i; ++t) acc += l[t] * xp[t * R + r];
+    if (svd) {
+      tp[e] = acc;
+      continue;
+    }
     if (is_front) {
       const T* Tm = fac + bd.T;
       for (int s2 = 0; s2 < nq; ++s2) acc += Tm[(int64_t)s2 * np + i] * xq[s2 * R + r];
     }
     if (r < nr) x[(int64_t)idp[i] * ldx + r] = acc;
+  }
+  if (svd) {                      // x_c <- V x_c (Q_c^-T = Q_c)
+    __syncthreads();
+    svd_rotate<T, R>(fac + bd.V, np, nq, xq, tp, oq, xp, false);
+    __syncthreads();
+    for (int e = threadIdx.x; e < nq * R; e += blockDim.x)
+      if (e % R < nr) x[(int64_t)idq[e / R] * ldx + e % R] = oq[e];
+    for (int e = threadIdx.x; e < np * R; e += blockDim.x)
+      if (e % R < nr) x[(int64_t)idp[e / R] * ldx + e % R] = xp[e];
   }
 }
 

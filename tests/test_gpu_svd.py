@@ -1,0 +1,93 @@
+"""Fronts skeletonized by the SVD (Section 4.4; hif_opts.skel =
+HIF_SKEL_SVD) against the oracle's SVD variant (``hifde.factor(...,
+skel="svd")``): per front the same rank, so the same kept slots (the first k
+DOFs of the front), the same |s_L|, and F^-1 x, F x element-wise within
+1e-10 of the largest entry in FP64.  The front's SVD is a one-sided Jacobi
+iteration on the GPU and LAPACK's in the oracle: the singular values agree
+to about 1e-14 sigma_1, so the ranks agree away from the threshold (the
+cases have no near-threshold front), and the factorization does not depend
+on the basis chosen inside the kept or the dropped directions.  Cases: 2D
+high-contrast at 31^2, 63^2 and 127^2 (rotations at every level), the 3D
+high-contrast 15^3 (faces), and one 2D case with the factor stored and
+applied in FP32 (fp32_apply), held element-wise to the FP32 apply bound
+d u32 kappa(A), d = 2(2L + 1) + 1 factors of Eq. 4.2.
+"""
+import numpy as np
+import pytest
+
+from oracle import hifde, stencil
+from paper_1307_2895_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+CASES = [(2, 32, 1e-6), (2, 64, 1e-6), (2, 128, 1e-3), (3, 16, 1e-3)]
+
+
+def _problem(dim, n):
+    a, b = inputs.high_contrast_coefficients(dim, n, seed=3, low=1e-2, high=1e2)
+    return a, b, stencil.assemble(dim, n, a, b)
+
+
+@pytest.mark.parametrize("dim,n,eps", CASES)
+def test_svd_fronts_match_oracle(hiflib, dim, n, eps):
+    from paper_1307_2895_gb300 import hif
+    a, b, A = _problem(dim, n)
+    F = hifde.factor(A, dim, n, eps, skel="svd")
+    nrot = sum(1 for lev in F.levels for fr in lev.fronts if fr.V is not None)
+    assert nrot > 0
+    x = inputs.rhs(dim, n, 5, seed=9)
+    G = hif.factor(dim, n, a, b, eps, precision="fp64", skel="svd")
+    try:
+        fronts, root = G.structure()
+        st = G.stats()
+        yi = G.apply(x, inverse=True)
+        yf = G.apply(x, inverse=False)
+    finally:
+        G.free()
+    ostruct, oroot = F.skeleton_structure()
+    got = {(lev, tuple(c)): sk for lev, c, sk in fronts}
+    nfr = 0
+    for lev, d in enumerate(ostruct):
+        for key, (c, sk, k) in d.items():
+            assert got.get((lev, tuple(c))) == sk, f"level {lev} front {c[:4]}...: ranks differ"
+            nfr += 1
+    assert nfr == len(fronts)
+    assert root == oroot and st["root_size"] == oroot
+    assert st["near_threshold_fronts"] == 0
+    oi, of = F.apply_inverse(x), F.apply(x)
+    ei = np.abs(yi - oi).max() / np.abs(oi).max()
+    ef = np.abs(yf - of).max() / np.abs(of).max()
+    print(f"SVD {dim}D n={n} eps={eps:g}: {nrot} rotated fronts, |s_L| {root}, "
+          f"F^-1 x {ei:.2e}, F x {ef:.2e}")
+    assert ei <= 1e-10
+    assert ef <= 1e-10
+
+
+def test_svd_fronts_fp32_apply(hiflib):
+    from paper_1307_2895_gb300 import hif
+    dim, n, eps = 2, 64, 1e-6
+    a, b, A = _problem(dim, n)
+    F = hifde.factor(A, dim, n, eps, skel="svd")
+    x = inputs.rhs(dim, n, 3, seed=4)
+    G = hif.factor(dim, n, a, b, eps, precision="fp32_apply", skel="svd")
+    try:
+        yi = G.apply(x, inverse=True)
+    finally:
+        G.free()
+    oi = F.apply_inverse(x)
+    kappa = np.linalg.cond(A.toarray())
+    bound = (2 * (2 * F.L + 1) + 1) * 2.0 ** -24 * kappa   # d u32 kappa(A), d factors of Eq. 4.2
+    elem = np.abs(yi - oi).max() / np.abs(oi).max()
+    print(f"SVD fp32_apply 2D n={n}: element-wise {elem:.2e}, bound d u32 kappa = {bound:.2e}")
+    assert elem <= bound
+
+
+def test_svd_option_errors(hiflib):
+    from paper_1307_2895_gb300 import hif
+    a, b = inputs.constant_coefficients(3, 16)
+    with pytest.raises(Exception):
+        hif.factor(3, 16, a, b, 1e-3, variant="hifde3x", skel="svd")
+    with pytest.raises(Exception):
+        hif.factor(3, 16, a, b, 1e-3, precision="mixed", skel="svd")
+    with pytest.raises(Exception):
+        hif.factor(3, 16, a, b, 1e-3, id_mode="rand", skel="svd")
