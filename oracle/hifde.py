@@ -25,6 +25,11 @@ What each function follows:
   ``B_{p1 p1}`` of ``V^T A_cc V``) and their interactions with ``N``
   dropped; the kept directions live on in the slots of the first ``k`` DOFs
   of ``c`` with interactions ``A_{N,c} V_2`` (``factor(..., skel="svd")``).
+* :func:`eliminate_two_sided`, :func:`skeletonize_two_sided` -- the
+  unsymmetric generalization of Section 6: two-sided elimination operators
+  ``R_p`` and ``S_p`` from ``A_pp = L U`` (LU without pivoting, L unit lower),
+  and the ID of the stacked ``[A_{N,c}; A_{c,N}^T]``, whose ``T`` serves both
+  sides (``factor(..., two_sided=True)``).
 * :func:`factor3x` -- the 3D variant with edge skeletonization (Section 4.5,
   Algorithm 4.2): cells built algebraically from Voronoi cells about the cell
   centers, faces and edges as Voronoi cells about the face and edge centers.
@@ -63,9 +68,19 @@ Readings where the paper leaves a choice:
   paper's front loop is sequential; with the ID the two orders agree
   exactly, with the SVD they differ by the truncated interactions.)
 
+* two-sided variant (Section 6): rows and columns of a front share one ID
+  (of the stacked block), so the transform is ``Q_c^T A Q_c`` as in the
+  symmetric case; the redundant DOFs are eliminated by LU against the
+  skeletons (``B_ss <- A_ss - B_sr B_rr^-1 B_rs``); the root by LU.  For a
+  symmetric ``A`` the stacked block's pivoted QR picks the same skeletons as
+  ``A_{N,c}``'s (its column norms are those of ``A_{N,c}`` times sqrt(2)).
+
 Parity status: MF, the stencil, Lemma 2.1, Lemma 2.4, the ID, the SVD
 skeletonization (exact F = A when nothing is truncated, V orthogonal, the
-truncated interactions within eps sigma_1, ||A - F|| of order eps), F and F^-1 are
+truncated interactions within eps sigma_1, ||A - F|| of order eps), the
+two-sided variant (MF exact against a dense solve, exact without truncation,
+the symmetric factor recovered for a symmetric A, ||A - F|| of order eps),
+F and F^-1 are
 pinned by the ``-m "not gpu"`` tests (dense LU, closed forms, exact low rank,
 LAPACK's pivoted QR, invariants); the power estimates by the exact 2-norms of
 dense A - F, A and I - A F^-1 on small grids; PCG by scipy's preconditioned
@@ -248,6 +263,9 @@ def eliminate(A: ActiveMatrix, p: List[int]) -> CellRecord:
 def apply_S_T(rec: CellRecord, x: np.ndarray) -> None:
     """x <- D_p^-1 S_p^T x on p and S_p^T x on q (in place, x may have several
     columns).  S_p^T = [[L^-1, 0], [-A_qp A_pp^-1, I]] on (p, q)."""
+    if isinstance(rec, TwoSidedRecord):
+        apply_R_T(rec, x)
+        return
     xp = _sgn(rec, sla.solve_triangular(rec.L, x[rec.p], lower=True))
     if len(rec.q):
         x[rec.q] -= rec.Aqp @ sla.solve_triangular(rec.L, xp, lower=True, trans="T")
@@ -256,6 +274,9 @@ def apply_S_T(rec: CellRecord, x: np.ndarray) -> None:
 
 def apply_S(rec: CellRecord, x: np.ndarray) -> None:
     """x <- S_p x:  x_p <- L^-T (x_p - D_p^-1 L^-1 A_qp^T x_q)."""
+    if isinstance(rec, TwoSidedRecord):
+        apply_S2(rec, x)
+        return
     xp = x[rec.p]
     if len(rec.q):
         xp = xp - _sgn(rec, sla.solve_triangular(rec.L, rec.Aqp.T @ x[rec.q], lower=True))
@@ -265,6 +286,9 @@ def apply_S(rec: CellRecord, x: np.ndarray) -> None:
 def apply_S_inv(rec: CellRecord, x: np.ndarray) -> None:
     """x <- S_p^{-1} x with S_p^{-1} = [[L^T, D_p^-1 L^-1 A_qp^T], [0, I]] (the
     inverse of apply_S)."""
+    if isinstance(rec, TwoSidedRecord):
+        apply_S2_inv(rec, x)
+        return
     xp = rec.L.T @ x[rec.p]
     if len(rec.q):
         xp = xp + _sgn(rec, sla.solve_triangular(rec.L, rec.Aqp.T @ x[rec.q], lower=True))
@@ -273,10 +297,99 @@ def apply_S_inv(rec: CellRecord, x: np.ndarray) -> None:
 
 def apply_S_inv_T(rec: CellRecord, x: np.ndarray) -> None:
     """The inverse of apply_S_T: x_q += A_qp L^-T x_p; x_p <- L D_p x_p."""
+    if isinstance(rec, TwoSidedRecord):
+        apply_R_inv_T(rec, x)
+        return
     xp = x[rec.p].copy()
     if len(rec.q):
         x[rec.q] += rec.Aqp @ sla.solve_triangular(rec.L, xp, lower=True, trans="T")
     x[rec.p] = rec.L @ _sgn(rec, xp)
+
+
+# --------------------------------------------------------------------------
+# Section 6: two-sided elimination (unsymmetric A)
+# --------------------------------------------------------------------------
+
+def lu_nopivot(A: np.ndarray):
+    """A = L U with L unit lower triangular and U upper triangular, pivots
+    taken in order (right-looking).  Raises LinAlgError on a zero pivot."""
+    n = A.shape[0]
+    W = np.array(A, dtype=np.float64, copy=True)
+    L = np.eye(n)
+    U = np.zeros((n, n))
+    for j in range(n):
+        d = W[j, j]
+        if d == 0.0 or not np.isfinite(d):
+            raise np.linalg.LinAlgError("zero pivot in the LU decomposition")
+        U[j, j:] = W[j, j:]
+        L[j + 1:, j] = W[j + 1:, j] / d
+        W[j + 1:, j + 1:] -= np.outer(L[j + 1:, j], W[j, j + 1:])
+    return L, U
+
+
+@dataclasses.dataclass
+class TwoSidedRecord:
+    """R_p^T = [[L^-1, 0], [-A_qp A_pp^-1, I]] and S_p = [[U^-1, -A_pp^-1
+    A_pq], [0, I]] with A_pp = L U, so that R_p^T A S_p = diag(I, B_qq),
+    B_qq = A_qq - A_qp A_pp^-1 A_pq."""
+    p: np.ndarray
+    q: np.ndarray
+    L: np.ndarray
+    U: np.ndarray
+    Aqp: np.ndarray
+    Apq: np.ndarray
+
+
+def _lsolve(L, v):
+    return sla.solve_triangular(L, v, lower=True, unit_diagonal=True)
+
+
+def _usolve(U, v):
+    return sla.solve_triangular(U, v, lower=False)
+
+
+def eliminate_two_sided(A: ActiveMatrix, p: List[int]) -> TwoSidedRecord:
+    """Lemma 2.1 with two-sided operators: B_qq = A_qq - A_qp A_pp^-1 A_pq."""
+    q = A.neighbors(p)
+    L, U = lu_nopivot(A.block(p, p))
+    Aqp = A.block(q, p)
+    Apq = A.block(p, q)
+    if q:
+        A.add_block(q, q, -(Aqp @ _usolve(U, _lsolve(L, Apq))))
+    A.remove(p)
+    return TwoSidedRecord(np.array(p, dtype=np.int64), np.array(q, dtype=np.int64), L, U, Aqp, Apq)
+
+
+def apply_R_T(rec: TwoSidedRecord, x: np.ndarray) -> None:
+    """x <- R_p^T x:  y_p = L^-1 x_p;  x_q -= A_qp U^-1 y_p;  x_p = y_p."""
+    y = _lsolve(rec.L, x[rec.p])
+    if len(rec.q):
+        x[rec.q] -= rec.Aqp @ _usolve(rec.U, y)
+    x[rec.p] = y
+
+
+def apply_S2(rec: TwoSidedRecord, x: np.ndarray) -> None:
+    """x <- S_p x:  x_p <- U^-1 (x_p - L^-1 A_pq x_q)."""
+    xp = x[rec.p]
+    if len(rec.q):
+        xp = xp - _lsolve(rec.L, rec.Apq @ x[rec.q])
+    x[rec.p] = _usolve(rec.U, xp)
+
+
+def apply_S2_inv(rec: TwoSidedRecord, x: np.ndarray) -> None:
+    """x <- S_p^-1 x with S_p^-1 = [[U, L^-1 A_pq], [0, I]]."""
+    xp = rec.U @ x[rec.p]
+    if len(rec.q):
+        xp = xp + _lsolve(rec.L, rec.Apq @ x[rec.q])
+    x[rec.p] = xp
+
+
+def apply_R_inv_T(rec: TwoSidedRecord, x: np.ndarray) -> None:
+    """x <- R_p^-T x with R_p^-T = [[L, 0], [A_qp U^-1, I]]."""
+    xp = x[rec.p].copy()
+    if len(rec.q):
+        x[rec.q] += rec.Aqp @ _usolve(rec.U, xp)
+    x[rec.p] = rec.L @ xp
 
 
 # --------------------------------------------------------------------------
@@ -383,7 +496,50 @@ def skeletonize(A: ActiveMatrix, c: List[int], idr: IDResult) -> FrontRecord:
 
 
 def _front_as_cell(fr: FrontRecord) -> CellRecord:
+    if isinstance(fr, TwoSidedFrontRecord):
+        return TwoSidedRecord(fr.rd, fr.sk, fr.L, fr.U, fr.Bsr, fr.Brs)
     return CellRecord(fr.rd, fr.sk, fr.L, fr.Bsr, fr.sgn)
+
+
+@dataclasses.dataclass
+class TwoSidedFrontRecord:
+    """Section 6's front: Q_c from the ID of [A_{N,c}; A_{c,N}^T] (one T for
+    rows and columns), then the two-sided elimination of r against s."""
+    c: np.ndarray
+    sk: np.ndarray
+    rd: np.ndarray
+    T: np.ndarray
+    L: np.ndarray      # B_rr = L U
+    U: np.ndarray
+    Bsr: np.ndarray
+    Brs: np.ndarray
+    near_threshold: bool = False
+    sgn: np.ndarray = None
+
+
+def skeletonize_two_sided(A: ActiveMatrix, c: List[int], idr: IDResult) -> TwoSidedFrontRecord:
+    """Q_c^T A Q_c with A_{q,r} and A_{r,q} truncated, then the two-sided
+    elimination of r: B_ss <- B_ss - B_sr B_rr^-1 B_rs."""
+    c_arr = np.array(c, dtype=np.int64)
+    sk = c_arr[idr.sk]
+    rd = c_arr[idr.rd]
+    sk_l, rd_l = sk.tolist(), rd.tolist()
+    Ass = A.block(sk_l, sk_l)
+    Asr = A.block(sk_l, rd_l)
+    Ars = A.block(rd_l, sk_l)
+    Arr = A.block(rd_l, rd_l)
+    T = idr.T
+    Brr = Arr - T.T @ Asr - Ars @ T + T.T @ Ass @ T
+    Bsr = Asr - Ass @ T
+    Brs = Ars - T.T @ Ass
+    if len(rd_l):
+        L, U = lu_nopivot(Brr)
+    else:
+        L, U = np.zeros((0, 0)), np.zeros((0, 0))
+    if len(rd_l) and len(sk_l):
+        A.set_block(sk_l, sk_l, Ass - Bsr @ _usolve(U, _lsolve(L, Brs)))
+    A.remove(rd_l)
+    return TwoSidedFrontRecord(c_arr, sk, rd, T, L, U, Bsr, Brs, idr.near_threshold)
 
 
 def apply_U_T(fr: FrontRecord, x: np.ndarray) -> None:
@@ -545,6 +701,7 @@ class Factor:
     sketched: int = 0          # fronts whose sketched ID passed the check
     fallback: int = 0          # fronts whose sketched ID failed it
     Dsgn: np.ndarray = None    # signs of D's LDL^T decomposition (None: Cholesky)
+    DU: np.ndarray = None      # two-sided variant: D = Dchol DU (Dchol unit lower), None otherwise
 
     # ---- Eq. (4.2): F^-1 = V_0 V_1/2 ... D^-1 ... V_1/2^T V_0^T
     def apply_inverse(self, b: np.ndarray) -> np.ndarray:
@@ -554,7 +711,9 @@ class Factor:
                 apply_S_T(rec, x)
             for fr in lev.fronts:
                 apply_U_T(fr, x)
-        if len(self.root):
+        if len(self.root) and self.DU is not None:
+            x[self.root] = _usolve(self.DU, _lsolve(self.Dchol, x[self.root]))
+        elif len(self.root):
             y = sla.solve_triangular(self.Dchol, x[self.root], lower=True)
             if self.Dsgn is not None:
                 y = self.Dsgn.reshape((-1,) + (1,) * (y.ndim - 1)) * y
@@ -605,7 +764,8 @@ def _front_key(dim, x, on_sep, seps):
 
 
 def factor(A_csr, dim: int, n: int, eps: float, leaf: int = 8,
-           skip_levels: int = 0, sketch=None, sketch_power: int = 0, skel: str = "id") -> Factor:
+           skip_levels: int = 0, sketch=None, sketch_power: int = 0, skel: str = "id",
+           two_sided: bool = False) -> Factor:
     """Algorithm 4.1 (HIF-DE; ``eps > 0``) or Algorithm 3.1 (MF; ``eps == 0``).
 
     Level l: eliminate the active DOFs strictly inside each level-l cell
@@ -625,12 +785,16 @@ def factor(A_csr, dim: int, n: int, eps: float, leaf: int = 8,
     are kept on the result.
 
     ``skel="svd"`` skeletonizes the fronts by the SVD (Section 4.4,
-    :func:`skeletonize_svd`) instead of the ID."""
+    :func:`skeletonize_svd`) instead of the ID.  ``two_sided=True`` is the
+    unsymmetric variant of Section 6 (two-sided elimination by LU, the ID of
+    the stacked ``[A_{N,c}; A_{c,N}^T]``, the root by LU)."""
     from .stencil import coords as _coords
     if skel not in ("id", "svd"):
         raise ValueError(f"skel must be 'id' or 'svd', not {skel!r}")
     if skel == "svd" and sketch is not None:
         raise ValueError("the randomized ID and the SVD skeletonization are exclusive")
+    if two_sided and (skel != "id" or sketch is not None):
+        raise ValueError("the two-sided variant uses the pivoted-QR ID")
     A = ActiveMatrix(A_csr)
     X = _coords(dim, n)
     L = tree_levels(n, leaf)
@@ -653,7 +817,8 @@ def factor(A_csr, dim: int, n: int, eps: float, leaf: int = 8,
                 lin = lin * ncell + iv[:, a]
             for d, cidx in zip(inside.tolist(), lin.tolist()):
                 cell_dofs.setdefault(cidx, []).append(d)
-        cells = [eliminate(A, sorted(cell_dofs[k])) for k in sorted(cell_dofs)]
+        elim = eliminate_two_sided if two_sided else eliminate
+        cells = [elim(A, sorted(cell_dofs[k])) for k in sorted(cell_dofs)]
         # ---- level l + 1/2: fronts
         fronts: List[FrontRecord] = []
         keys: List[tuple] = []
@@ -675,6 +840,9 @@ def factor(A_csr, dim: int, n: int, eps: float, leaf: int = 8,
                 if skel == "svd":
                     ids.append(svd_skel(M, eps))
                     continue
+                if two_sided:                          # rows and columns: one ID (Section 6)
+                    ids.append(interp_decomp(np.vstack([M, A.block(c, nb).T]), eps))
+                    continue
                 Phi = sketch(ell, c, nb) if sketch is not None else None
                 idr = None
                 if Phi is not None:
@@ -693,11 +861,16 @@ def factor(A_csr, dim: int, n: int, eps: float, leaf: int = 8,
             for key, idr in zip(keys, ids):
                 if skel == "svd":
                     fronts.append(skeletonize_svd(A, sorted(groups[key]), idr))
+                elif two_sided:
+                    fronts.append(skeletonize_two_sided(A, sorted(groups[key]), idr))
                 else:
                     fronts.append(skeletonize(A, sorted(groups[key]), idr))
         levels.append(Level(ell, cells, fronts, keys))
     root = np.array(A.active(), dtype=np.int64)
     D = A.block(root.tolist(), root.tolist())
+    if two_sided:
+        DL, DU = lu_nopivot(D) if len(root) else (np.zeros((0, 0)), np.zeros((0, 0)))
+        return Factor(dim, n, L, eps, levels, root, D, DL, n_sketched, n_fallback, None, DU)
     Dchol, Dsgn = factor_block(D) if len(root) else (np.zeros((0, 0)), None)
     return Factor(dim, n, L, eps, levels, root, D, Dchol, n_sketched, n_fallback, Dsgn)
 

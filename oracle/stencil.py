@@ -18,6 +18,12 @@ residual of an accurate solution far above 1e-12.
 
 ``rhs_from_bc`` moves nonzero Dirichlet values to the right-hand side.
 
+``convection`` is the central difference of a constant convection term
+``beta . grad u``: ``(beta_e / 2h) (u_{j+e} - u_{j-e})`` per axis, zero
+Dirichlet values at the boundary; skew-symmetric, so ``assemble(...) +
+convection(...)`` is the unsymmetric operator (with an SPD symmetric part) of
+the two-sided variant the paper's Section 6 sketches.
+
 Pinned by: the closed-form eigenpairs of the constant-coefficient Laplacian
 (``tests/test_oracle_stencil.py``) and symmetry / row-sum identities;
 ``rhs_from_bc`` by harmonic quadratics, which the stencil reproduces exactly,
@@ -84,6 +90,28 @@ def assemble(dim: int, n: int, a_stag, b) -> sp.csr_matrix:
     A = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                       shape=(N, N))
     return A.tocsr()
+
+
+def convection(dim: int, n: int, beta) -> sp.csr_matrix:
+    """C x = (beta . grad) x by central differences, (beta_e / 2h)(x_{j+e} -
+    x_{j-e}) for each axis e (x fastest), neighbours on the boundary dropped
+    (zero Dirichlet values).  C^T = -C."""
+    m = n - 1
+    N = m ** dim
+    idx = np.arange(N).reshape((m,) * dim)
+    rows, cols, vals = [], [], []
+    for axis in range(dim):
+        arr_axis = dim - 1 - axis
+        c = float(beta[axis]) * n / 2.0                 # beta_e / (2h), h = 1/n
+        lo = [slice(None)] * dim
+        hi = [slice(None)] * dim
+        lo[arr_axis] = slice(0, m - 1)
+        hi[arr_axis] = slice(1, m)
+        i_lo, i_hi = idx[tuple(lo)].ravel(), idx[tuple(hi)].ravel()
+        rows += [i_lo, i_hi]
+        cols += [i_hi, i_lo]
+        vals += [np.full(i_lo.size, c), np.full(i_hi.size, -c)]
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(N, N))
 
 
 def rhs_from_bc(dim: int, n: int, a_stag, g, f) -> np.ndarray:
