@@ -9,10 +9,14 @@ shares no code, tables or helpers with the CUDA implementation.
 Modules:
 
 * :mod:`oracle.stencil`  -- five/seven-point variable-coefficient stencil
-  (Section 3.1 and 3.2).
+  (Section 3.1 and 3.2), and a central-difference convection term for the
+  unsymmetric operators of Section 6.
 * :mod:`oracle.hifde`    -- MF (Algorithm 3.1) and HIF-DE (Algorithm 4.1, 2D and
-  3D with face skeletonization), the apply of F and F^-1 (Eq. 3.1 / 4.2),
-  PCG and the power-method error estimates of Section 5.
+  3D with face skeletonization; Algorithm 4.2, hifde3x), the apply of F and
+  F^-1 (Eq. 3.1 / 4.2), the SVD skeletonization (Section 4.4), the two-sided
+  unsymmetric variant (Section 6), PCG, GMRES and the power-method error
+  estimates of Section 5.
+* :mod:`oracle.learned`  -- the randomized ID of Section 4.3 and the rank MLP.
 
 Parity status per function is stated in each module header.
 """
