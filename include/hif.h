@@ -182,6 +182,25 @@ typedef struct hif_opts {
                            rounding order.                                   */
   int skel;             /* HIF_SKEL_*: the fronts' low-rank approximation;
                            0 -> HIF_SKEL_ID                                  */
+  int two_sided;        /* nonzero: the unsymmetric generalization that the
+                           paper's Section 6 sketches.  Diagonal blocks are
+                           factored by LU without pivoting (A_pp = L U, L
+                           unit lower), giving the two-sided elimination
+                           operators R_p = [[L^-T, -A_pp^-T A_qp^T], [0, I]]
+                           and S_p = [[U^-1, -A_pp^-1 A_pq], [0, I]] of
+                           Lemma 2.1; a front's skeletons and T come from one
+                           ID of the stacked [A_{N,c}; A_{c,N}^T] and serve
+                           its rows and columns.  The operator is the
+                           stencil plus the convection term beta . grad u
+                           (central differences, constant beta), so A is
+                           unsymmetric when beta != 0.  HIFDE or MF, FP64 or
+                           FP32_APPLY, HIF_ID_QR and HIF_SKEL_ID; every block
+                           runs the one-block kernels.  hif_solve,
+                           hif_matvec and hif_estimate apply the stencil
+                           without the convection term: they return
+                           HIF_ERR_ARG for a handle with beta != 0.        */
+  double beta[3];       /* two_sided: beta per axis (x, y[, z]); must be 0
+                           otherwise                                        */
 } hif_opts;
 
 typedef struct hif_handle hif_handle;

@@ -21,7 +21,7 @@ SOURCES = ["kernels_factor.cu", "kernels_apply.cu", "kernels_solve.cu", "hif_api
            "hif_apply.cu", "hif_solve.cu", "geometry.cpp",
            "noalloc.cu", "kernels_mlp.cu", "kernels_tiled.cu", "kernels_bigfront.cu", "kernels_tc.cu",
            "host_pool.cpp", "symbolic3x.cpp", "kernels_dense3x.cu",
-           "kernels_root.cu", "kernels_bigapply.cu", "kernels_svdfront.cu"]
+           "kernels_root.cu", "kernels_bigapply.cu", "kernels_svdfront.cu", "kernels_twosided.cu"]
 HEADERS = ["hif_internal.h", "kernels.h", "blockops.cuh", "geometry.h", "tile_mma.cuh", "front_common.cuh",
            "host_pool.h", "symbolic3x.h", "hif_host.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -110,6 +110,36 @@ __device__ bool blk_cholesky(T* A, int n, int ld, int* status, T tau = T(0), con
   return s_neg != 0;
 }
 
+// A = L U in place (n x n, ld), pivots in order, L unit lower (strictly below
+// the diagonal) and U upper (on and above it); the two-sided elimination of
+// an unsymmetric block.  A zero or non-finite pivot sets bit 0 of *status and
+// is replaced by 1 (the factorization then reports the error).
+template <typename T>
+__device__ void blk_lu_nopivot(T* A, int n, int ld, int* status) {
+  __shared__ T s_rpiv;
+  for (int j = 0; j < n; ++j) {
+    if (threadIdx.x == 0) {
+      T d = A[(int64_t)j * ld + j];
+      if (d == T(0) || !isfinite((double)d)) {
+        atomicOr(status, 1);
+        d = T(1);
+        A[(int64_t)j * ld + j] = d;
+      }
+      s_rpiv = T(1) / d;
+    }
+    __syncthreads();
+    const T r = s_rpiv;
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[(int64_t)i * ld + j] *= r;
+    __syncthreads();
+    const int m = n - j - 1;
+    for (int64_t e = threadIdx.x; e < (int64_t)m * m; e += blockDim.x) {
+      const int i = j + 1 + (int)(e / m), k = j + 1 + (int)(e % m);
+      A[(int64_t)i * ld + k] -= A[(int64_t)i * ld + j] * A[(int64_t)j * ld + k];
+    }
+    __syncthreads();
+  }
+}
+
 // X = L^{-1} for lower-triangular L (n x n).  X is written in full (zeros
 // above the diagonal).  Column-oriented forward substitution on the identity.
 template <typename T>

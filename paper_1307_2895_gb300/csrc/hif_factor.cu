@@ -59,7 +59,7 @@ namespace {
 
 void prepare_cells(const Geometry& G, int l, const std::vector<HostCell>& cells,
                    const std::vector<HostCell>* prev, std::vector<CellDesc>& desc, std::vector<int>& ipool,
-                   int64_t& work_elems, int64_t& fac_elems, int& max_nI) {
+                   int64_t& work_elems, int64_t& fac_elems, int& max_nI, bool two_sided = false) {
   desc.resize(cells.size());
   work_elems = fac_elems = 0;
   max_nI = 0;
@@ -79,6 +79,12 @@ void prepare_cells(const Geometry& G, int l, const std::vector<HostCell>& cells,
     work_elems += (int64_t)d.nI * d.nI + (int64_t)d.nB * d.nI + (int64_t)d.nB * d.nB + cell_x_elems(d.nI);
     d.fac = fac_elems;
     fac_elems += cell_fac_size(d.nI, d.nB);
+    if (two_sided) {   // F_IB and its scratch; the second factor set
+      d.FIB = work_elems;
+      work_elems += cell_work2_size(d.nI, d.nB);
+      d.fac2 = fac_elems;
+      fac_elems += cell_fac2_size(d.nI, d.nB);
+    }
     for (int s = 0; s < kMaxChild; ++s) d.child[s] = -1;
     d.cmap = -1;
     if (maps) {
@@ -123,6 +129,11 @@ void cell_apply_descs(const std::vector<CellDesc>& cd, std::vector<ApplyDesc>& a
     a.L = c.fac + cell_fac_L(c.nI, c.nB);
     a.T = -1;
     a.S = c.fac + cell_fac_S(c.nI, c.nB);
+    if (c.fac2 >= 0) {   // two-sided
+      a.Linv2 = c.fac2;
+      a.G2 = c.fac2 + packed_size(c.nI);
+      a.L2 = a.G2 + pad4((int64_t)c.nB * c.nI);
+    }
     ad.push_back(a);
     max_np = std::max(max_np, c.nI);
     max_nq = std::max(max_nq, c.nB);
@@ -168,7 +179,8 @@ void build_contrib_plan(const std::vector<CellDesc>& cd, const std::vector<int>&
 
 // Descriptors of the fronts of one fractional level.
 void prepare_fronts(const std::vector<HostFront>& fr, std::vector<FrontDesc>& fd, std::vector<int>& ip,
-                    int64_t& work_elems, int64_t& fac_elems, int64_t& out_elems, int& max_nc, int& max_nN) {
+                    int64_t& work_elems, int64_t& fac_elems, int64_t& out_elems, int& max_nc, int& max_nN,
+                    bool two_sided = false) {
   const int nf = (int)fr.size();
   fd.resize(nf);
   ip.clear();
@@ -189,9 +201,15 @@ void prepare_fronts(const std::vector<HostFront>& fr, std::vector<FrontDesc>& fd
     d.out = out_elems;
     out_elems += 1 + 2 * d.nc;
     d.work = work_elems;
-    work_elems += 2 * (int64_t)d.nN * d.nc + 4 * (int64_t)d.nc * d.nc;
+    // two-sided: the stacked 2|N| x |c| block, A_cc and six |c|^2 scratch blocks
+    work_elems += two_sided ? 2 * (int64_t)d.nN * d.nc + 7 * (int64_t)d.nc * d.nc
+                            : 2 * (int64_t)d.nN * d.nc + 4 * (int64_t)d.nc * d.nc;
     d.fac = fac_elems;
     fac_elems += front_fac_size(d.nc);
+    if (two_sided) {
+      d.fac2 = fac_elems;
+      fac_elems += front_fac2_size(d.nc);
+    }
     max_nc = std::max(max_nc, d.nc);
     max_nN = std::max(max_nN, d.nN);
   }
@@ -208,12 +226,12 @@ T* dev_copy(const std::vector<T>& v) {
 
 std::mutex g_l0_mutex;
 // never destroyed: no device frees run while the process exits
-auto& g_l0_cache = *new std::map<std::tuple<int, int, int, int>, std::shared_ptr<Level0>>();
+auto& g_l0_cache = *new std::map<std::tuple<int, int, int, int, int>, std::shared_ptr<Level0>>();
 
-std::shared_ptr<const Level0> get_level0(const Geometry& G) {
+std::shared_ptr<const Level0> get_level0(const Geometry& G, bool two_sided) {
   int dev = 0;
   CU(cudaGetDevice(&dev));
-  const auto key = std::make_tuple(dev, G.dim, G.n, G.leaf);
+  const auto key = std::make_tuple(dev, G.dim, G.n, G.leaf, two_sided ? 1 : 0);
   std::lock_guard<std::mutex> lock(g_l0_mutex);
   auto it = g_l0_cache.find(key);
   if (it != g_l0_cache.end()) return it->second;
@@ -222,7 +240,7 @@ std::shared_ptr<const Level0> get_level0(const Geometry& G) {
   for (int64_t g = 0; g < G.N; ++g) alive[g] = (int)g;
   build_cells(G, 0, alive, L0->cells);
   std::vector<int> cip;
-  prepare_cells(G, 0, L0->cells, nullptr, L0->cdesc, cip, L0->work_elems, L0->fac_elems, L0->max_nI);
+  prepare_cells(G, 0, L0->cells, nullptr, L0->cdesc, cip, L0->work_elems, L0->fac_elems, L0->max_nI, two_sided);
   std::vector<ApplyDesc> ad;
   cell_apply_descs(L0->cdesc, ad, L0->cap_max_np, L0->cap_max_nq, L0->cap_fac_elems, L0->cap_vec_rows);
   std::vector<char> inner(G.N, 0);
@@ -236,7 +254,7 @@ std::shared_ptr<const Level0> get_level0(const Geometry& G) {
   build_fronts(G, 0, L0->alive1, L0->cells, *L0->fronts, mark);
   std::vector<int> fip;
   prepare_fronts(*L0->fronts, *L0->fdesc, fip, L0->fwork_elems, L0->ffac_elems, L0->fout_elems, L0->max_nc,
-                 L0->max_nN);
+                 L0->max_nN, two_sided);
   L0->d_cls0 = dev_copy(G.cls[0]);
   L0->d_cdesc = dev_copy(L0->cdesc);
   L0->d_cipool = dev_copy(cip);
@@ -514,6 +532,10 @@ struct Factorizer {
   template <typename U>
   void factor_cells(const std::vector<CellDesc>& cd, const CellDesc* d_cd, U* work, U* fac, DevBuf& selbuf,
                     DevBuf& tdbuf) {
+    if (h->two_sided) {   // every cell by the one-block LU kernel
+      launch_cell_lu<U>(d_cd, nullptr, (int)cd.size(), work, fac, status.as<int>(), st);
+      return;
+    }
     std::vector<int> small, big;
     int max_small = 0, max_sB = 0, max_bI = 0, max_bB = 0;
     for (int i = 0; i < (int)cd.size(); ++i) {
@@ -589,7 +611,7 @@ struct Factorizer {
     // gives every later index set
     x3 = h->variant == HIF_VARIANT_HIFDE3X && h->edge_start < L;
     if (x3) sym.reset(new Symbolic3x(G.n, G.leaf, true));
-    std::shared_ptr<const Level0> L0 = get_level0(G);
+    std::shared_ptr<const Level0> L0 = get_level0(G, h->two_sided);
     h->level0 = L0;
 
     // ---- level 0: the cached structure
@@ -600,7 +622,7 @@ struct Factorizer {
       sw.fac.alloc((size_t)L0->fac_elems * sizeof(T), st);
       const int nc0 = (int)L0->cdesc.size();
       launch_leaf_assemble<T>(L0->d_cdesc, nc0, L0->d_cipool, work.as<T>(), h->gi, h->a_stag.as<double>(),
-                              h->bnode.as<double>(), L0->d_cls0, G.ncell[0], st);
+                              h->bnode.as<double>(), L0->d_cls0, G.ncell[0], h->two_sided ? h->beta : nullptr, st);
       DevBuf sel0, td0;
       factor_cells<T>(L0->cdesc, L0->d_cdesc, work.as<T>(), sw.fac.as<T>(), sel0, td0);
       CU(cudaGetLastError());
@@ -661,7 +683,7 @@ struct Factorizer {
       std::vector<int> ipool;
       int64_t work_elems = 0, fac_elems = 0;
       int max_nI = 0;
-      prepare_cells(G, l, cells, prev_cells, cdesc, ipool, work_elems, fac_elems, max_nI);
+      prepare_cells(G, l, cells, prev_cells, cdesc, ipool, work_elems, fac_elems, max_nI, h->two_sided);
       tr.lap("cells prepare");
       SweepLevel& sw = is_root ? h->root : h->cells[l];
       upload(ddesc, cdesc, st);
@@ -725,7 +747,7 @@ struct Factorizer {
         std::vector<int> ip;
         int64_t fw = 0, ff = 0, fo = 0;
         int mnc = 0, mnN = 0;
-        prepare_fronts(*fr, *fd, ip, fw, ff, fo, mnc, mnN);
+        prepare_fronts(*fr, *fd, ip, fw, ff, fo, mnc, mnN, h->two_sided);
         tr.lap("fronts prepare");
         DevBuf d_fd, d_ip;
         upload(d_fd, *fd, st);
@@ -816,10 +838,13 @@ struct Factorizer {
     }
     DevBuf d_sel, d_big, bstate, m2part, d_td;
     DevBuf d_ccell, d_cptr, d_clist;
-    if (h->skel == HIF_SKEL_SVD) big.clear();   // every front by the one-block SVD kernel
+    if (h->skel == HIF_SKEL_SVD || h->two_sided) big.clear();   // every front by a one-block kernel
     const int nbig = (int)big.size();
     const int nm = nbig ? bigfront_colmax_blocks(big_nc) : 0;
-    if (h->skel == HIF_SKEL_SVD) {
+    if (h->two_sided) {
+      launch_front_lu<T>(d_fd, nf, d_cdesc, d_ip, obuf.as<int>(), fwork.as<T>(), sw.fac.as<T>(), cwork.as<T>(),
+                         h->eps, status.as<int>(), max_nc, max_nN, st);
+    } else if (h->skel == HIF_SKEL_SVD) {
       // the fronts' SVDs from the update matrices as they stand, then each
       // bordering cell's update matrix rotated by its fronts
       std::map<int, std::vector<int>> by_cell;   // cell -> (front, side) pairs
@@ -996,6 +1021,11 @@ struct Factorizer {
       a.cslot = 0;
       const bool rot = h->skel == HIF_SKEL_SVD && k > 0 && nR > 0;   // the SVD's rotation V (T's slot)
       a.V = rot ? a.T : -1;
+      if (d.fac2 >= 0) {   // two-sided
+        a.Linv2 = d.fac2;
+        a.G2 = d.fac2 + packed_size(d.nc);
+        a.L2 = a.G2 + pad4((int64_t)d.nc * d.nc);
+      }
       sw.max_np = std::max(sw.max_np, nR);
       sw.max_nq = std::max(sw.max_nq, k);
       if (nR > 0) {
@@ -1086,6 +1116,22 @@ int hif_factor(const hif_grid* grid, const double* a_stag, const double* b, cons
     if (opts) h->sketch_power = opts->sketch_power;
     if (opts) h->deterministic = opts->deterministic != 0;
     if (opts && opts->big_apply != 0) h->big_apply = opts->big_apply < 0 ? 0 : opts->big_apply;
+    h->two_sided = opts && opts->two_sided != 0;
+    if (h->two_sided) {
+      if (grid->variant == HIF_VARIANT_HIFDE3X) throw HifError(HIF_ERR_ARG, "two_sided: not with HIFDE3X");
+      if (prec == HIF_PREC_MIXED) throw HifError(HIF_ERR_ARG, "two_sided: FP64 or FP32_APPLY precision only");
+      if ((opts->id_mode != HIF_ID_QR) || opts->skel != HIF_SKEL_ID)
+        throw HifError(HIF_ERR_ARG, "two_sided: the pivoted-QR ID only");
+      for (int a = 0; a < 3; ++a) {
+        const double bv = a < grid->dim ? opts->beta[a] : 0.0;
+        if (!std::isfinite(bv)) throw HifError(HIF_ERR_ARG, "two_sided: beta must be finite");
+        h->beta[a] = bv;
+      }
+      h->big_cell = 0x7fffffff;   // one-block kernels everywhere
+      h->big_apply = 0;
+    } else if (opts && (opts->beta[0] != 0.0 || opts->beta[1] != 0.0 || opts->beta[2] != 0.0)) {
+      throw HifError(HIF_ERR_ARG, "beta (a convection term) needs two_sided");
+    }
     h->skel = opts ? opts->skel : HIF_SKEL_ID;
     if (h->skel != HIF_SKEL_ID && h->skel != HIF_SKEL_SVD) throw HifError(HIF_ERR_ARG, "unknown skel");
     if (h->skel == HIF_SKEL_SVD) {
@@ -1141,7 +1187,7 @@ int hif_factor(const hif_grid* grid, const double* a_stag, const double* b, cons
       f.run();
     }
     if (prec == HIF_PREC_FP32_APPLY) demote_factor(h);
-    if (h->root_size >= kRootMulti)
+    if (h->root_size >= kRootMulti && !h->two_sided)   // (two-sided: the one-block root sweep)
       h->root_scratch.alloc(sizeof(double) * (size_t)root_scratch_elems(h->root_size, h->deterministic), h->st);
     {   // scratch of the levels' large blocks (F^-1 by many thread blocks)
       int64_t big = 0;

@@ -284,6 +284,8 @@ struct hif_handle {
   int sketch_power = 0; // power iterations on the randomized ID's sketch
   bool deterministic = false;   // sweeps and root apply without floating-point atomics
   int skel = HIF_SKEL_ID;       // fronts skeletonized by the ID or by the SVD (Section 4.4)
+  bool two_sided = false;       // LU elimination, ID of [A_{N,c}; A_{c,N}^T] (the unsymmetric variant)
+  double beta[3] = {0.0, 0.0, 0.0};   // two-sided: the convection term beta . grad u
   int64_t big_apply = int64_t(1) << 20;   // F^-1: blocks with np (np + 2 nq) >= this many elements by
                                           // many thread blocks (0: none)
   DevBuf big_scratch;           // their scratch (the largest level's, doubles)

@@ -27,6 +27,12 @@ struct CellDesc {
   int64_t cmap;        // int pool: (nI+nB) x kMaxChild positions in each child's B (-1 absent)
   int child[kMaxChild];// child cell index at the previous level (-1 absent)
   int cell_lin;        // linear cell index (x fastest) at this level
+  // two-sided (unsymmetric) factorization only, -1 otherwise: work pool
+  // offset of F_IB[nI*nB] (row-major) followed by 2 nI*nI scratch, and factor
+  // pool offset of the second set Linv2 = U^-T (packed) | G2 = (L^-1 F_IB)^T
+  // [nB*nI] | L2 = U^T (packed), see cell_fac2_size
+  int64_t FIB = -1;
+  int64_t fac2 = -1;
 };
 
 // One front (edge or face interior) at a fractional level l + 1/2.
@@ -37,6 +43,7 @@ struct FrontDesc {
   int64_t work;        // work pool: M[nN*nc] (column-major) | A_cc[nc*nc] | 3 scratch nc*nc
   int64_t fac;         // factor pool (capacity for nc): Linv (packed) | G | T | L (packed)
   int64_t out;         // output buffer: k | perm[nc] | ids_sr[nc]
+  int64_t fac2 = -1;   // two-sided: factor pool offset of Linv2 | G2 | L2 (capacity nc), else -1
 };
 
 // A dense elimination problem for the tiled kernels (Lemma 2.1 on
@@ -73,6 +80,12 @@ struct ApplyDesc {
   int64_t cslot;       // cells: row of x_q's first contribution in the level's
                        // contribution buffer (the deterministic scatter)
   int64_t V = -1;      // SVD fronts: factor pool offset of V (-1: none)
+  // two-sided (unsymmetric) blocks, A_pp = L U (L unit lower): Linv = L^-1,
+  // G = A_qp U^-1 and L (unit lower) as above; the down sweep and the
+  // forward operator read Linv2 = U^-T, G2 = (L^-1 A_pq)^T (nq x np) and
+  // L2 = U^T (packed lower) instead of Linv, G and L (-1: the symmetric
+  // block, where they coincide)
+  int64_t Linv2 = -1, G2 = -1, L2 = -1;
 };
 
 // Gaussian stream of the randomized ID (Section 4.3) at one fractional level
@@ -137,6 +150,16 @@ __host__ __device__ inline int64_t front_fac_S(int nc) { return 2 * packed_size(
 __host__ __device__ inline int64_t front_fac_size(int nc) {
   return 2 * packed_size(nc) + 2 * pad4((int64_t)nc * nc) + pad4(nc);
 }
+
+// Two-sided factorization: the second factor set of a cell or front
+// (Linv2 packed | G2 | L2 packed) and a cell's extra work (F_IB, 2 scratch).
+__host__ __device__ inline int64_t cell_fac2_size(int nI, int nB) {
+  return 2 * packed_size(nI) + pad4((int64_t)nB * nI);
+}
+__host__ __device__ inline int64_t cell_work2_size(int nI, int nB) {
+  return (int64_t)nI * nB + 2 * (int64_t)nI * nI;
+}
+__host__ __device__ inline int64_t front_fac2_size(int nc) { return 2 * packed_size(nc) + pad4((int64_t)nc * nc); }
 
 struct GridInfo {
   int dim, n, m;       // m = n - 1 nodes per axis

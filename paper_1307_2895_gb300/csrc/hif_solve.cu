@@ -581,6 +581,8 @@ extern "C" {
 
 int hif_estimate(hif_handle* h, const double* x0, double rtol, int maxit, double* e_a, double* e_s) {
   if (!h || !x0 || !e_a || !e_s) return set_error(HIF_ERR_ARG, "NULL argument");
+  if (h->beta[0] != 0.0 || h->beta[1] != 0.0 || h->beta[2] != 0.0)
+    return set_error(HIF_ERR_ARG, "hif_estimate: the stencil products here have no convection term (beta != 0)");
   if (!(rtol > 0.0) || maxit < 1) return set_error(HIF_ERR_ARG, "need rtol > 0 and maxit >= 1");
   try {
     const int64_t N = h->G.N;
@@ -623,6 +625,8 @@ int hif_estimate(hif_handle* h, const double* x0, double rtol, int maxit, double
 
 int hif_matvec(hif_handle* h, const double* x, double* y, int nrhs, int ld) {
   if (!h || !x || !y) return set_error(HIF_ERR_ARG, "NULL argument");
+  if (h->beta[0] != 0.0 || h->beta[1] != 0.0 || h->beta[2] != 0.0)
+    return set_error(HIF_ERR_ARG, "hif_matvec: the stencil products here have no convection term (beta != 0)");
   if (nrhs < 1 || ld < nrhs || nrhs > 32) return set_error(HIF_ERR_ARG, "need 1 <= nrhs <= min(ld, 32)");
   try {
     const int64_t N = h->G.N;
@@ -647,6 +651,8 @@ int hif_matvec(hif_handle* h, const double* x, double* y, int nrhs, int ld) {
 int hif_solve(hif_handle* h, const double* rhs, double* x, double* x_lo, int nrhs, int ld, double tol,
               int maxit, hif_solve_info* info) {
   if (!h || !rhs || !x) return set_error(HIF_ERR_ARG, "NULL argument");
+  if (h->beta[0] != 0.0 || h->beta[1] != 0.0 || h->beta[2] != 0.0)
+    return set_error(HIF_ERR_ARG, "hif_solve: the stencil products here have no convection term (beta != 0)");
   if (nrhs < 1 || ld < nrhs) return set_error(HIF_ERR_ARG, "need 1 <= nrhs <= ld");
   if (!(tol > 0.0) || maxit < 0) return set_error(HIF_ERR_ARG, "need tol > 0 and maxit >= 0");
   hif_solve_info loc{0, 0, 1, 0.0, 0.0, 0};

@@ -35,9 +35,11 @@ inline void raise_smem_limit(K kern) {
 
 // factorization (kernels_factor.cu)
 template <typename T>
+// beta (host, dim values, NULL: none): a central-difference convection term
+// beta . grad u, with F_IB stored for the cells that have room for it (FIB >= 0)
 void launch_leaf_assemble(const CellDesc* cells, int ncells, const int* ipool, T* work, GridInfo g,
                           const double* a_stag, const double* bnode, const int* cls, int ncell_axis,
-                          cudaStream_t st);
+                          const double* beta, cudaStream_t st);
 template <typename TU, typename TF>
 void launch_extend_add(const CellDesc* cells, int ncells, const int* ipool, TF* work,
                        const CellDesc* pcells, const TU* pwork, int nchild, int max_nF, cudaStream_t st);
@@ -63,6 +65,17 @@ void launch_front(const FrontDesc* fronts, int nfronts, const CellDesc* cells, c
                   T* fwork,
                   T* fac, T* cwork, double eps, int* status, int max_nc, int max_nN, double tau,
                   const int* sketch, SketchStream ss, const int* sel, cudaStream_t st);
+
+// the two-sided (unsymmetric) factorization (kernels_twosided.cu): every
+// cell of a level by LU (one block each, F_IB and the second factor set at
+// the CellDesc's FIB / fac2), every front by the ID of [A_{N,c}; A_{c,N}^T]
+// and the LU elimination of its redundant DOFs (FrontDesc fac2)
+template <typename T>
+void launch_cell_lu(const CellDesc* cells, const int* sel, int ncells, T* work, T* fac, int* status,
+                    cudaStream_t st);
+template <typename T>
+void launch_front_lu(const FrontDesc* fronts, int nfronts, const CellDesc* cells, const int* ipool, int* obuf,
+                     T* fwork, T* fac, T* cwork, double eps, int* status, int max_nc, int max_nN, cudaStream_t st);
 
 // skeletonization by the SVD (kernels_svdfront.cu, Section 4.4): every front
 // of a level (one block each), then the rotation of the update matrices of

@@ -12,6 +12,9 @@
 //   fwd_up   (V^-1):  [front] x_q += T x_p;  x_p = L^T x_p + G^T x_q
 //   fwd_down (D_p, then V^-T):  x_p = S x_p;  x_q += G x_p;  x_p = L x_p;
 //                               [front] x_p += T^T x_q
+// Two-sided (unsymmetric) blocks, A_pp = L U: the same steps with L^-1 and
+// G = A_qp U^-1 in the up sweep, U^-T and (L^-1 A_pq)^T in the place of
+// Linv and G in the down sweep, U^T in the place of L^T in fwd_up.
 // Cells of one level share boundary DOFs, so their x_q updates use atomics,
 // or, in the deterministic mode, go to a contribution buffer (one row per
 // (cell, q-row) pair) that a second launch sums per DOF in cell order; the
@@ -305,8 +308,8 @@ __device__ void sweep_down_block(const ApplyDesc& bd, const int* __restrict__ ip
   const int* idq = idp + np;
   SweepSmem<T, R> sm(smem_raw, np, nq, staged, is_front);
   BulkStage bs{sm.mbar, parity};
-  const T* Linv = fac + bd.Linv;
-  const T* G = fac + bd.G;
+  const T* Linv = fac + (bd.Linv2 >= 0 ? bd.Linv2 : bd.Linv);   // two-sided: U^-T
+  const T* G = fac + (bd.G2 >= 0 ? bd.G2 : bd.G);               // two-sided: (L^-1 A_pq)^T
   const T* Tm = is_front ? fac + bd.T : nullptr;
   if (staged) stage_factor<T, R>(sm, bs, Linv, G, Tm, np, nq, is_front);
   const bool go = wait();
@@ -454,8 +457,8 @@ __global__ void k_fwd_up(const ApplyDesc* __restrict__ blocks, const int* __rest
   T* xp = reinterpret_cast<T*>(smem_raw);
   T* xq = xp + pad4((int64_t)np * R);
   T* tq = xq + pad4((int64_t)nq * R);
-  const T* Lp = fac + bd.L;
-  const T* G = fac + bd.G;
+  const T* Lp = fac + (bd.L2 >= 0 ? bd.L2 : bd.L);     // two-sided: U^T
+  const T* G = fac + (bd.G2 >= 0 ? bd.G2 : bd.G);
   gather<T, R>(xp, x, idp, np, nr, ldx);
   gather<T, R>(xq, x, idq, nq, nr, ldx);
   __syncthreads();

@@ -20,6 +20,7 @@ struct LeafGeom {
   const double* bnode;
   const int* cls;      // cls[x], x = 0..n: interval index (>= 0) or -(ordinal+1) on a separator
   int ncell;           // leaf cells per axis
+  double conv[3];      // beta_e / 2h of a convection term beta . grad u (zero: none)
 };
 
 __device__ __forceinline__ void dof_coords(int gid, int m, int dim, int x[3]) {
@@ -69,9 +70,10 @@ __global__ void k_leaf_assemble(const CellDesc* __restrict__ cells, const int* _
     int t = cd.cell_lin;
     for (int a = 0; a < 3; ++a) { civ[a] = t % L.ncell; t /= L.ncell; }
   }
+  T* FIB = cd.FIB >= 0 ? work + cd.FIB : nullptr;   // two-sided only: F_IB stored too
   for (int64_t e = threadIdx.x; e < (int64_t)nF * nF; e += blockDim.x) {
     const int a = (int)(e / nF), b = (int)(e % nF);
-    if (a < nI && b >= nI) continue;            // F_IB is never stored
+    if (a < nI && b >= nI && !FIB) continue;   // F_IB: the transpose of F_BI, not stored
     const int ga = ids[a], gb = ids[b];
     int xa[3], xb[3];
     dof_coords(ga, m, dim, xa);
@@ -97,10 +99,12 @@ __global__ void k_leaf_assemble(const CellDesc* __restrict__ cells, const int* _
         int j[3] = {xa[0], xa[1], xa[2]};
         if (d < 0) j[axd] = xb[axd];
         v = -bond(L, axd, j) * L.g.inv_h2;
+        if (L.conv[axd] != 0.0) v += d * L.conv[axd];   // (beta_e / 2h)(u_{j+e} - u_{j-e})
       }
     }
     T* dst;
-    if (a < nI) dst = FII + (int64_t)a * nI + b;
+    if (a < nI && b >= nI) dst = FIB + (int64_t)a * nB + (b - nI);
+    else if (a < nI) dst = FII + (int64_t)a * nI + b;
     else if (b < nI) dst = FBI + (int64_t)(a - nI) * nI + b;
     else dst = FBB + (int64_t)(a - nI) * nB + (b - nI);
     *dst = (T)v;
@@ -139,9 +143,10 @@ __global__ void k_extend_add(const CellDesc* __restrict__ cells, const int* __re
     }
   }
   __syncthreads();
+  TF* FIB = cd.FIB >= 0 ? work + cd.FIB : nullptr;   // two-sided only
   for (int64_t e = e0; e < nF2; e += (int64_t)gridDim.y * blockDim.x) {
     const int a = (int)(e / nF), b = (int)(e % nF);
-    if (a < nI && b >= nI) continue;
+    if (a < nI && b >= nI && !FIB) continue;
     const int* ca = cmap + (int64_t)a * kMaxChild;
     const int* cb = cmap + (int64_t)b * kMaxChild;
     TF s = TF(0);
@@ -150,7 +155,8 @@ __global__ void k_extend_add(const CellDesc* __restrict__ cells, const int* __re
       if (pa >= 0 && pb >= 0) s += (TF)sU[c][(int64_t)pa * sld[c] + pb];
     }
     TF* dst;
-    if (a < nI) dst = FII + (int64_t)a * nI + b;
+    if (a < nI && b >= nI) dst = FIB + (int64_t)a * nB + (b - nI);
+    else if (a < nI) dst = FII + (int64_t)a * nI + b;
     else if (b < nI) dst = FBI + (int64_t)(a - nI) * nI + b;
     else dst = FBB + (int64_t)(a - nI) * nB + (b - nI);
     *dst = s;
@@ -420,8 +426,9 @@ __global__ void k_front(const FrontDesc* __restrict__ fronts, const CellDesc* __
 template <typename T>
 void launch_leaf_assemble(const CellDesc* cells, int ncells, const int* ipool, T* work,
                           GridInfo g, const double* a_stag, const double* bnode, const int* cls,
-                          int ncell_axis, cudaStream_t st) {
-  LeafGeom L{g, a_stag, bnode, cls, ncell_axis};
+                          int ncell_axis, const double* beta, cudaStream_t st) {
+  LeafGeom L{g, a_stag, bnode, cls, ncell_axis, {0.0, 0.0, 0.0}};
+  for (int a = 0; a < g.dim && beta; ++a) L.conv[a] = beta[a] * g.n / 2.0;   // 1 / 2h = n / 2
   note_launches(1);
   k_leaf_assemble<T><<<ncells, 256, 0, st>>>(cells, ipool, work, L);
 }
@@ -475,9 +482,11 @@ void launch_front(const FrontDesc* fronts, int nfronts, const CellDesc* cells, c
 }
 
 template void launch_leaf_assemble<double>(const CellDesc*, int, const int*, double*, GridInfo,
-                                           const double*, const double*, const int*, int, cudaStream_t);
+                                           const double*, const double*, const int*, int, const double*,
+                                           cudaStream_t);
 template void launch_leaf_assemble<float>(const CellDesc*, int, const int*, float*, GridInfo,
-                                          const double*, const double*, const int*, int, cudaStream_t);
+                                          const double*, const double*, const int*, int, const double*,
+                                          cudaStream_t);
 template void launch_extend_add<double, double>(const CellDesc*, int, const int*, double*,
                                                 const CellDesc*, const double*, int, int, cudaStream_t);
 template void launch_extend_add<float, float>(const CellDesc*, int, const int*, float*,

@@ -41,7 +41,8 @@ class _Opts(ctypes.Structure):
                 ("oversample", ctypes.c_int), ("stream", ctypes.c_void_p), ("rank_model", ctypes.c_void_p),
                 ("seed", ctypes.c_ulonglong), ("big_cell", ctypes.c_int), ("tensor_cores", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("edge_start", ctypes.c_int), ("sketch_power", ctypes.c_int),
-                ("deterministic", ctypes.c_int), ("big_apply", ctypes.c_longlong), ("skel", ctypes.c_int)]
+                ("deterministic", ctypes.c_int), ("big_apply", ctypes.c_longlong), ("skel", ctypes.c_int),
+                ("two_sided", ctypes.c_int), ("beta", ctypes.c_double * 3)]
 
 
 class _SolveInfo(ctypes.Structure):
@@ -444,7 +445,8 @@ def factor(dim: int, n: int, a_stag, b, eps: float, variant: str = "hifde", prec
            leaf: int = 8, skip_levels: int = 0, stream=None, id_mode: str = "qr", rank_model=None,
            oversample: int = 10, seed: int = 0, big_cell: int = 0, tensor_cores: int = 0,
            autotune: bool = True, edge_start: int = 1, sketch_power: int = 0,
-           deterministic: bool = False, big_apply: int = 0, skel: str = "id") -> Factorization:
+           deterministic: bool = False, big_apply: int = 0, skel: str = "id", two_sided: bool = False,
+           beta=None) -> Factorization:
     """hif_factor: MF or HIF-DE of the stencil operator defined by (a_stag, b).
     tensor_cores (mixed precision): 0 three-part TF32 split (about FP32),
     2 two-part, 1 plain TF32, -1 FP32 on the SIMT pipes.  edge_start
@@ -454,7 +456,9 @@ def factor(dim: int, n: int, a_stag, b, eps: float, variant: str = "hifde", prec
     big_apply: F^-1 applies blocks of at least this many factor elements
     (np (np + 2 nq)) with many thread blocks each (0: 2^20, -1: never).
     skel: the fronts' low-rank approximation, "id" (Lemma 2.2) or "svd"
-    (Section 4.4)."""
+    (Section 4.4).  two_sided: the unsymmetric variant (LU elimination, one
+    ID of [A_{N,c}; A_{c,N}^T]) of the stencil plus the convection term
+    beta . grad u (beta: dim values, two_sided only)."""
     lib = load()
     _need_problem(dim, n, a_stag, b)
     _need(rank_model, MLP_PARAMS, "rank_model")
@@ -464,7 +468,8 @@ def factor(dim: int, n: int, a_stag, b, eps: float, variant: str = "hifde", prec
     opts = _Opts(PRECISIONS[precision], skip_levels, ID_MODES[id_mode], oversample, _stream_ptr(stream),
                  _ptr(rank_model, "float32"), seed, big_cell, tensor_cores, 0 if autotune else -1,
                  -1 if edge_start == 0 else edge_start, sketch_power, 1 if deterministic else 0, int(big_apply),
-                 SKELS[skel])
+                 SKELS[skel], 1 if two_sided else 0,
+                 (ctypes.c_double * 3)(*(list(beta) + [0.0] * (3 - len(beta))) if beta is not None else (0.0,) * 3))
     h = ctypes.c_void_p()
     rc = lib.hif_factor(ctypes.byref(grid), _ptr(a_stag), _ptr(b), None, float(eps), ctypes.byref(opts),
                         ctypes.byref(h))
