@@ -192,3 +192,32 @@ def test_sketch_power_argument_error_without_gpu():
     rc = lib.hif_factor(ctypes.byref(grid), a.ctypes.data, b.ctypes.data, None, 1e-6, ctypes.byref(opts),
                         ctypes.byref(h))
     assert rc == hif.HIF_ERR_ARG and b"sketch_power" in lib.hif_last_error()
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Every struct the binding passes through the C ABI has the header's
+    size and field offsets (a C++ program compiled with the host compiler
+    prints them from include/hif.h)."""
+    import shutil
+    import subprocess
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no host C++ compiler")
+    pairs = [("hif_grid", hif._Grid), ("hif_opts", hif._Opts), ("hif_solve_info", hif._SolveInfo),
+             ("hif_stats_t", hif._Stats), ("hif_profile_t", hif._Profile)]
+    lines = ['#include <cstddef>', '#include <cstdio>', '#include "hif.h"', 'int main() {']
+    for cname, cls in pairs:
+        lines.append(f'  std::printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'  std::printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append('  return 0;\n}')
+    src = tmp_path / "layout.cpp"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cxx, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, cls in pairs:
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert got[(cname, fname)] == getattr(cls, fname).offset, f"{cname}.{fname}"
