@@ -465,6 +465,10 @@ def factor(dim: int, n: int, a_stag, b, eps: float, variant: str = "hifde", prec
     grid = _Grid(dim, n, leaf, VARIANTS[variant])
     if edge_start < 0:
         raise ValueError("edge_start must be >= 0")
+    if beta is not None:
+        beta = [float(v) for v in beta]
+        if len(beta) != dim:
+            raise ValueError(f"beta has {len(beta)} values, the grid has {dim} axes")
     opts = _Opts(PRECISIONS[precision], skip_levels, ID_MODES[id_mode], oversample, _stream_ptr(stream),
                  _ptr(rank_model, "float32"), seed, big_cell, tensor_cores, 0 if autotune else -1,
                  -1 if edge_start == 0 else edge_start, sketch_power, 1 if deterministic else 0, int(big_apply),

@@ -139,6 +139,8 @@ def test_binding_refuses_wrong_lengths_before_the_library():
         hif.factor(2, n, a, b, 1e-6, id_mode="learned", rank_model=np.zeros(7, dtype=np.float32))
     with pytest.raises(ValueError, match="a_stag"):
         hif.factor_batch([(2, n, a, b), (2, n, a[:10], b)], 1e-6)
+    with pytest.raises(ValueError, match="beta"):
+        hif.factor(2, n, a, b, 1e-6, two_sided=True, beta=(1.0, 2.0, 3.0))
 
     class _NoLib:      # any library call would fail with AttributeError
         pass
