@@ -97,3 +97,22 @@ def test_two_sided_preconditioned_gmres():
     print(f"two-sided 63^2: GMRES {iters[0]} iterations, relres {rel[0]:.1e}")
     assert rel[0] <= 1e-12 and iters[0] <= 6
     assert np.linalg.norm(A @ x.ravel() - b) <= 1e-11 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("dim,n,eps", [(2, 32, 1e-6), (3, 12, 1e-3)])
+def test_two_sided_commutes_with_transposition(dim, n, eps):
+    """Factoring A^T (beta -> -beta) stacks the same two blocks in the other
+    order, so the pivoted QR picks the same skeletons and T, and the
+    factorization is the transpose: F(A^T) = F(A)^T.  A mix-up of the row
+    and column operators (A_qp against A_pq^T, L against U^T) breaks it."""
+    A = _problem(dim, n)
+    At = _problem(dim, n, beta=tuple(-b for b in BETA[dim]))
+    assert abs(At - A.T).max() <= 1e-12 * abs(A).max()
+    F = hifde.factor(A, dim, n, eps, two_sided=True)
+    Ft = hifde.factor(At, dim, n, eps, two_sided=True)
+    assert F.skeleton_structure() == Ft.skeleton_structure()
+    N = A.shape[0]
+    Fd = F.apply(np.eye(N))
+    assert np.abs(Ft.apply(np.eye(N)) - Fd.T).max() <= 1e-12 * np.abs(Fd).max()
+    Fi = F.apply_inverse(np.eye(N))
+    assert np.abs(Ft.apply_inverse(np.eye(N)) - Fi.T).max() <= 1e-10 * np.abs(Fi).max()
