@@ -6,7 +6,7 @@ with F^-1 as preconditioner).
 Against the paper's Tables 5-6 (hifde2 at 1023^2, kappa = 32) and 11-12
 (hifde3 and hifde3x at 31^3 and 63^3, kappa = 4 and 8), with bands fixed
 before the runs: |s_L| within 30% (the paper's adaptive trees and cell
-sizes are not this build's), e_a at most 3 times the paper's (the O(eps)
+sizes are not the ones used here), e_a at most 3 times the paper's (the O(eps)
 claim, the band of the Laplace tables), GMRES to 1e-12 in at most the
 paper's n_i + 4 iterations, the residual re-checked on the host in extended
 precision.  The lower side of e_a only asks for a non-vacuous estimate (at
@@ -16,9 +16,9 @@ i.e. a more accurate factorization.  The FP64 factorization throughout (eps
 down to 1e-12).
 
 hifde3x at 63^3 skeletonizes edges from level 2 (of levels 0..2).  Section 5
-skips the first few fractional levels "in select cases" without naming
-them; with edges from level 1, as at 31^3 and for the Laplacian at 63^3,
-this build gets |s_L| 3824 and e_a 1.0e-5 against the paper's 2934 and
+says that the first few fractional levels were skipped in some cases without
+naming them; with edges from level 1, as at 31^3 and for the Laplacian at
+63^3, the GPU factorization gets |s_L| 3824 and e_a 1.0e-5 against the paper's 2934 and
 2.0e-6, and with edges from level 2 it gets 2936 and 2.0e-6 (measured on a
 GB300 before the row was written into this test), so that is the reading
 taken for Example 6.
